@@ -1,0 +1,1514 @@
+/*
+ * lair_oracle.c -- plain, slow, single-threaded CPU oracle for lAIR
+ * (Manteuffel, Ruge, Southworth: "Nonsymmetric AMG based on local approximate
+ * ideal restriction").
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the CPU
+ * baseline of the benchmark load this file. It shares no code, header, table or
+ * constant with the CUDA library; the two meet only in the seeded inputs.
+ *
+ * Everything is FP64 unless a function says otherwise. The steps follow the
+ * paper's order and notation:
+ *   strength of connection ........ Sec. 4, definition of N_i (hard minimum)
+ *   C/F splitting .................. Sec. 4 (classical first pass, no second pass);
+ *                                    PMIS as the parallel alternative
+ *   restriction neighbourhoods ..... Sec. 3.1 (distance one/two, F-F-C only, Sec. 4)
+ *   local systems .................. Sec. 3.1, Eq. (3.1) johnair and Eq. (3.2) system,
+ *                                    least squares when singular (Sec. 3.1 footnote)
+ *   R = [Z I], P = [W; I] .......... Sec. 2.1, Eq. (2.2)
+ *   interpolation .................. one-point (Sec. 4) and approximate ideal
+ *                                    interpolation W ~ -A_ff^{-1} A_fc (Eq. (2.6))
+ *   coarse operator K = R A P ...... Sec. 2.1
+ *   lumping ........................ Sec. 3.3
+ *   V-cycle with post F-F-C Jacobi . Sec. 4, Eq. (2.4)
+ *   GMRES acceleration ............. Sec. 4 (here flexible GMRES, FP64)
+ *
+ * Points the paper leaves open are fixed here in one documented way (tie rules,
+ * singular threshold, arithmetic order). Floating-point operations that decide
+ * integer structure on coarse levels are written with explicit fma() and a fixed
+ * order, so that any implementation that follows the same definitions obtains
+ * identical bits. Build with -ffp-contract=off so the compiler adds no fusions.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_OK 0
+#define ORA_ERR_ARG 1
+#define ORA_ERR_ZERO_DIAG 5
+#define ORA_ERR_STALLED 6
+#define ORA_ERR_NOT_CONVERGED 7
+#define ORA_ERR_NAN 8
+#define ORA_ERR_OOM 9
+
+#define CF_F 0
+#define CF_C 1
+#define CF_U (-1)
+
+/* ------------------------------------------------------------------------- */
+/* options (mirrors the public option set; defined independently)            */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int cf_mode;           /* 0 RS, 1 PMIS, 2 USER (level 0 only), 3 AUTO (RS if n <= rs_max_n) */
+    const int8_t *cf_user; /* level-0 splitting for USER mode (1 = C, 0 = F) */
+    int distance;          /* 1 or 2 */
+    double theta;          /* strength threshold for R/P neighbourhoods */
+    double theta_cf;       /* strength threshold for the C/F splitting */
+    int strength_abs;      /* 1: |a_ij| >= theta max|a_ik| instead of -a_ij >= ... */
+    int interp;            /* 0 approximate ideal (lAIP), 1 one-point */
+    int relax;             /* 0 F-F-C, 1 F-C-F, 2 F-F */
+    double lump_tol;       /* theta_D; 0 disables */
+    int lump_level0;       /* also lump the finest operator */
+    int prec;              /* 0 FP64, 1 FP32 local solves and FP32 cycle */
+    int coarse_max;        /* direct solve when n <= coarse_max */
+    int max_levels;
+    int block_size;        /* >1: scale by the inverse block diagonal first */
+    int rs_max_n;
+    uint64_t pmis_seed;
+} ora_opts;
+
+/* ------------------------------------------------------------------------- */
+/* CSR helpers                                                               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t nr, nc;
+    int64_t *rp;
+    int32_t *col;
+    double *val;
+} ocsr;
+
+static void csr_free(ocsr *a) {
+    free(a->rp); free(a->col); free(a->val);
+    memset(a, 0, sizeof(*a));
+}
+
+static int csr_alloc(ocsr *a, int64_t nr, int64_t nc, int64_t nnz) {
+    a->nr = nr; a->nc = nc;
+    a->rp = (int64_t *)calloc((size_t)nr + 1, sizeof(int64_t));
+    a->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    a->val = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    return (a->rp && a->col && a->val) ? ORA_OK : ORA_ERR_OOM;
+}
+
+/* plain transpose; entries of each output row come out in ascending column order */
+static int csr_transpose(const ocsr *a, ocsr *t) {
+    int64_t nnz = a->rp[a->nr];
+    if (csr_alloc(t, a->nc, a->nr, nnz)) return ORA_ERR_OOM;
+    for (int64_t k = 0; k < nnz; ++k) t->rp[a->col[k] + 1]++;
+    for (int64_t i = 0; i < a->nc; ++i) t->rp[i + 1] += t->rp[i];
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(a->nc + 1));
+    memcpy(pos, t->rp, sizeof(int64_t) * (size_t)(a->nc + 1));
+    for (int64_t i = 0; i < a->nr; ++i)
+        for (int64_t k = a->rp[i]; k < a->rp[i + 1]; ++k) {
+            int64_t d = pos[a->col[k]]++;
+            t->col[d] = (int32_t)i;
+            t->val[d] = a->val[k];
+        }
+    free(pos);
+    return ORA_OK;
+}
+
+/* value of a_ij or 0; columns of a row are ascending */
+static int find_entry(const ocsr *a, int64_t i, int64_t j, double *v) {
+    int64_t lo = a->rp[i], hi = a->rp[i + 1] - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (a->col[mid] == j) { *v = a->val[mid]; return 1; }
+        if (a->col[mid] < j) lo = mid + 1; else hi = mid - 1;
+    }
+    *v = 0.0;
+    return 0;
+}
+
+static int64_t find_pos(const int32_t *list, int64_t len, int64_t key) {
+    int64_t lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (list[mid] == key) return mid;
+        if (list[mid] < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Strength of connection (Sec. 4): j in N_i iff j != i and                   */
+/*   -a_ij >= theta * max_{k != i} |a_ik|   (signed), or                       */
+/*   |a_ij| >= theta * max_{k != i} |a_ik|  (abs mode).                        */
+/* Reading: an empty row maximum (m_i = 0) gives no strong connections, and an */
+/* explicitly stored zero is never strong. theta*m_i is one rounded multiply.  */
+/* ------------------------------------------------------------------------- */
+void ora_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  double theta, int absmode, uint8_t *strong) {
+    for (int64_t i = 0; i < n; ++i) {
+        double m = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] != i && fabs(val[k]) > m) m = fabs(val[k]);
+        double thr = theta * m;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            double a = val[k];
+            int s = 0;
+            if (col[k] != i && m > 0.0 && a != 0.0)
+                s = absmode ? (fabs(a) >= thr) : (-a >= thr);
+            strong[k] = (uint8_t)s;
+        }
+    }
+}
+
+/* S as a pattern-only CSR (val unused = NULL) */
+typedef struct { int64_t n; int64_t *rp; int32_t *col; } ograph;
+
+static void graph_free(ograph *g) { free(g->rp); free(g->col); memset(g, 0, sizeof(*g)); }
+
+static int graph_from_mask(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *mask, ograph *g) {
+    g->n = n;
+    g->rp = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < rp[n]; ++k) cnt += mask[k];
+    g->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cnt > 0 ? cnt : 1));
+    if (!g->rp || !g->col) return ORA_ERR_OOM;
+    int64_t p = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (mask[k]) g->col[p++] = col[k];
+        g->rp[i + 1] = p;
+    }
+    return ORA_OK;
+}
+
+static int graph_transpose(const ograph *g, ograph *t) {
+    int64_t n = g->n, nnz = g->rp[n];
+    t->n = n;
+    t->rp = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    t->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!t->rp || !t->col) return ORA_ERR_OOM;
+    for (int64_t k = 0; k < nnz; ++k) t->rp[g->col[k] + 1]++;
+    for (int64_t i = 0; i < n; ++i) t->rp[i + 1] += t->rp[i];
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    memcpy(pos, t->rp, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = g->rp[i]; k < g->rp[i + 1]; ++k) t->col[pos[g->col[k]]++] = (int32_t)i;
+    free(pos);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Classical (Ruge-Stueben) first pass, no second pass (Sec. 4).              */
+/* S_i = points i strongly depends on, ST_i = points strongly depending on i.  */
+/* lambda_i = |ST_i|. Points with S_i and ST_i both empty become F first.      */
+/* Repeat: the undecided point with the largest lambda (ties: smallest index)  */
+/* becomes C; every undecided j in ST_i becomes F and, for each such j, every  */
+/* undecided k in S_j gets lambda_k += 1; then every undecided k in S_i gets   */
+/* lambda_k -= 1. A binary heap with lazy deletion finds the maximum.          */
+/* ------------------------------------------------------------------------- */
+typedef struct { int64_t lam; int64_t idx; } heapent;
+
+static int heap_less(heapent a, heapent b) { /* a has lower priority than b */
+    if (a.lam != b.lam) return a.lam < b.lam;
+    return a.idx > b.idx;
+}
+
+typedef struct { heapent *a; int64_t len, cap; } oheap;
+
+static void heap_push(oheap *h, heapent e) {
+    if (h->len == h->cap) {
+        h->cap = h->cap ? 2 * h->cap : 1024;
+        h->a = (heapent *)realloc(h->a, sizeof(heapent) * (size_t)h->cap);
+    }
+    int64_t i = h->len++;
+    h->a[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!heap_less(h->a[p], h->a[i])) break;
+        heapent t = h->a[p]; h->a[p] = h->a[i]; h->a[i] = t;
+        i = p;
+    }
+}
+
+static heapent heap_pop(oheap *h) {
+    heapent top = h->a[0];
+    h->a[0] = h->a[--h->len];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < h->len && heap_less(h->a[m], h->a[l])) m = l;
+        if (r < h->len && heap_less(h->a[m], h->a[r])) m = r;
+        if (m == i) break;
+        heapent t = h->a[m]; h->a[m] = h->a[i]; h->a[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+static void cf_rs(const ograph *S, const ograph *ST, int8_t *cf) {
+    int64_t n = S->n;
+    int64_t *lam = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    oheap h = {0};
+    for (int64_t i = 0; i < n; ++i) {
+        lam[i] = ST->rp[i + 1] - ST->rp[i];
+        int isolated = (S->rp[i + 1] == S->rp[i]) && (lam[i] == 0);
+        cf[i] = isolated ? CF_F : CF_U;
+        if (!isolated) heap_push(&h, (heapent){lam[i], i});
+    }
+    while (h.len > 0) {
+        heapent e = heap_pop(&h);
+        int64_t i = e.idx;
+        if (cf[i] != CF_U || lam[i] != e.lam) continue;   /* stale entry */
+        cf[i] = CF_C;
+        for (int64_t p = ST->rp[i]; p < ST->rp[i + 1]; ++p) {
+            int64_t j = ST->col[p];
+            if (cf[j] != CF_U) continue;
+            cf[j] = CF_F;
+            for (int64_t q = S->rp[j]; q < S->rp[j + 1]; ++q) {
+                int64_t k = S->col[q];
+                if (cf[k] == CF_U) { lam[k] += 1; heap_push(&h, (heapent){lam[k], k}); }
+            }
+        }
+        for (int64_t p = S->rp[i]; p < S->rp[i + 1]; ++p) {
+            int64_t k = S->col[p];
+            if (cf[k] == CF_U) { lam[k] -= 1; heap_push(&h, (heapent){lam[k], k}); }
+        }
+    }
+    free(h.a);
+    free(lam);
+}
+
+/* ------------------------------------------------------------------------- */
+/* PMIS: parallel maximal independent set splitting with hashed weights.      */
+/* w_i = |ST_i| + u_i, u_i = (splitmix64((seed << 32) ^ i) >> 11) * 2^-53.     */
+/* Points with |ST_i| = 0 start as F. Each round, every undecided i whose      */
+/* (w_i, -i) beats that of every undecided neighbour in S_i u ST_i becomes C;  */
+/* then every undecided j in ST_i of a new C point i becomes F.                */
+/* splitmix64 is Vigna's published 64-bit mixer.                               */
+/* ------------------------------------------------------------------------- */
+static uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double ora_pmis_weight(int64_t lam, int64_t i, uint64_t seed) {
+    double u = (double)(splitmix64((seed << 32) ^ (uint64_t)i) >> 11) * 0x1.0p-53;
+    return (double)lam + u;
+}
+
+static int beats(double wi, int64_t i, double wj, int64_t j) {
+    return (wi > wj) || (wi == wj && i < j);
+}
+
+static void cf_pmis(const ograph *S, const ograph *ST, uint64_t seed, int8_t *cf) {
+    int64_t n = S->n;
+    double *w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int8_t *newc = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    int64_t undecided = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t lam = ST->rp[i + 1] - ST->rp[i];
+        w[i] = ora_pmis_weight(lam, i, seed);
+        cf[i] = (lam == 0) ? CF_F : CF_U;
+        undecided += (cf[i] == CF_U);
+    }
+    while (undecided > 0) {
+        for (int64_t i = 0; i < n; ++i) {
+            newc[i] = 0;
+            if (cf[i] != CF_U) continue;
+            int best = 1;
+            for (int64_t p = S->rp[i]; p < S->rp[i + 1] && best; ++p) {
+                int64_t j = S->col[p];
+                if (cf[j] == CF_U && !beats(w[i], i, w[j], j)) best = 0;
+            }
+            for (int64_t p = ST->rp[i]; p < ST->rp[i + 1] && best; ++p) {
+                int64_t j = ST->col[p];
+                if (cf[j] == CF_U && !beats(w[i], i, w[j], j)) best = 0;
+            }
+            newc[i] = (int8_t)best;
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (newc[i]) { cf[i] = CF_C; undecided--; }
+        for (int64_t i = 0; i < n; ++i) {
+            if (!newc[i]) continue;
+            for (int64_t p = ST->rp[i]; p < ST->rp[i + 1]; ++p) {
+                int64_t j = ST->col[p];
+                if (cf[j] == CF_U) { cf[j] = CF_F; undecided--; }
+            }
+        }
+    }
+    free(w);
+    free(newc);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Neighbourhoods (Sec. 3.1, Sec. 4). For C-point i and graph G:              */
+/*   distance 1: G_i restricted to F points;                                  */
+/*   distance 2: adds G_j restricted to F for every j in that set (F-F-C).    */
+/* Result sorted ascending, no duplicates. Output as CSR over C points.        */
+/* ------------------------------------------------------------------------- */
+static int build_neighbourhoods(const ograph *G, const int8_t *cf, int distance,
+                                int64_t nc, const int64_t *cpts, int64_t **out_rp, int32_t **out_col) {
+    int64_t *rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    int64_t cap = 1024, len = 0;
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    int32_t *tmp = NULL;
+    int64_t tcap = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t i = cpts[c];
+        int64_t t = 0;
+        int64_t need = 0;
+        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p) {
+            int64_t j = G->col[p];
+            need += 1;
+            if (distance >= 2 && cf[j] == CF_F) need += G->rp[j + 1] - G->rp[j];
+        }
+        if (need > tcap) { tcap = need + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
+        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p) {
+            int64_t j = G->col[p];
+            if (cf[j] != CF_F) continue;
+            tmp[t++] = (int32_t)j;
+            if (distance >= 2)
+                for (int64_t q = G->rp[j]; q < G->rp[j + 1]; ++q) {
+                    int64_t k = G->col[q];
+                    if (cf[k] == CF_F && k != i) tmp[t++] = (int32_t)k;
+                }
+        }
+        qsort(tmp, (size_t)t, sizeof(int32_t), cmp_i32);
+        int64_t u = 0;
+        for (int64_t a = 0; a < t; ++a)
+            if (u == 0 || tmp[u - 1] != tmp[a]) tmp[u++] = tmp[a];
+        if (len + u > cap) {
+            while (len + u > cap) cap *= 2;
+            col = (int32_t *)realloc(col, sizeof(int32_t) * (size_t)cap);
+        }
+        memcpy(col + len, tmp, sizeof(int32_t) * (size_t)u);
+        len += u;
+        rp[c + 1] = len;
+    }
+    free(tmp);
+    *out_rp = rp;
+    *out_col = col;
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Canonical 32-way tree sum used by the least-squares branch: partial l sums  */
+/* the terms with index = l (mod 32) in ascending order with fma; then pairs   */
+/* are added butterfly-wise with offsets 16, 8, 4, 2, 1 (p_l = p_l + p_{l^o}).  */
+/* ------------------------------------------------------------------------- */
+static double tree_dot(const double *x, int64_t sx, const double *y, int64_t sy, int64_t s) {
+    double p[32];
+    for (int l = 0; l < 32; ++l) p[l] = 0.0;
+    for (int64_t r = 0; r < s; ++r) p[r & 31] = fma(x[r * sx], y[r * sy], p[r & 31]);
+    for (int o = 16; o >= 1; o >>= 1) {
+        double q[32];
+        for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
+        for (int l = 0; l < 32; ++l) p[l] = q[l];
+    }
+    return p[0];
+}
+
+static float tree_dotf(const float *x, int64_t sx, const float *y, int64_t sy, int64_t s) {
+    float p[32];
+    for (int l = 0; l < 32; ++l) p[l] = 0.0f;
+    for (int64_t r = 0; r < s; ++r) p[r & 31] = fmaf(x[r * sx], y[r * sy], p[r & 31]);
+    for (int o = 16; o >= 1; o >>= 1) {
+        float q[32];
+        for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
+        for (int l = 0; l < 32; ++l) p[l] = q[l];
+    }
+    return p[0];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dense local solve M z = rhs, M row-major s x s (overwritten).              */
+/* LU with partial pivoting: pivot = largest |M[r][k]|, r >= k, ties -> the    */
+/* smallest r. Elimination: l = M[r][k] / M[k][k]; M[r][c] = fma(-l, M[k][c],  */
+/* M[r][c]) for c > k; rhs[r] = fma(-l, rhs[k], rhs[r]). Back substitution by  */
+/* columns, c = s-1 .. 0: z[c] = rhs[c] / M[c][c]; rhs[r] = fma(-M[r][c], z[c],*/
+/* rhs[r]) for r < c.                                                          */
+/* Singular reading: if some pivot |M[k][k]| <= s * eps * max|M| (original M)  */
+/* the minimum-norm least-squares solution is used instead (one-sided Jacobi    */
+/* SVD, Hestenes' method). Returns 0 for LU, 1 for least squares.              */
+/* ------------------------------------------------------------------------- */
+#define LS_MAX_SWEEPS 60
+
+static void jacobi_ls(int64_t s, const double *M0, const double *rhs0, double *z) {
+    double *B = (double *)malloc(sizeof(double) * (size_t)(s * s));
+    double *V = (double *)malloc(sizeof(double) * (size_t)(s * s));
+    double *sig = (double *)malloc(sizeof(double) * (size_t)s);
+    memcpy(B, M0, sizeof(double) * (size_t)(s * s));
+    for (int64_t r = 0; r < s; ++r)
+        for (int64_t c = 0; c < s; ++c) V[r * s + c] = (r == c) ? 1.0 : 0.0;
+    const double tol = DBL_EPSILON * (double)s;
+    for (int sweep = 0; sweep < LS_MAX_SWEEPS; ++sweep) {
+        int rotated = 0;
+        for (int64_t p = 0; p < s - 1; ++p)
+            for (int64_t q = p + 1; q < s; ++q) {
+                double alpha = tree_dot(B + p, s, B + p, s, s);
+                double beta = tree_dot(B + q, s, B + q, s, s);
+                double gamma = tree_dot(B + p, s, B + q, s, s);
+                if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
+                rotated = 1;
+                double zeta = (beta - alpha) / (2.0 * gamma);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                double c = 1.0 / sqrt(fma(t, t, 1.0));
+                double sn = c * t;
+                for (int64_t r = 0; r < s; ++r) {
+                    double bp = B[r * s + p], bq = B[r * s + q];
+                    B[r * s + p] = fma(c, bp, -(sn * bq));
+                    B[r * s + q] = fma(sn, bp, c * bq);
+                    double vp = V[r * s + p], vq = V[r * s + q];
+                    V[r * s + p] = fma(c, vp, -(sn * vq));
+                    V[r * s + q] = fma(sn, vp, c * vq);
+                }
+            }
+        if (!rotated) break;
+    }
+    double smax = 0.0;
+    for (int64_t j = 0; j < s; ++j) {
+        sig[j] = sqrt(tree_dot(B + j, s, B + j, s, s));
+        if (sig[j] > smax) smax = sig[j];
+    }
+    double cut = ((double)s * DBL_EPSILON) * smax;
+    for (int64_t r = 0; r < s; ++r) z[r] = 0.0;
+    for (int64_t j = 0; j < s; ++j) {
+        if (!(sig[j] > cut)) continue;
+        double coef = (tree_dot(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
+        for (int64_t r = 0; r < s; ++r) z[r] = fma(V[r * s + j], coef, z[r]);
+    }
+    free(B); free(V); free(sig);
+}
+
+int ora_local_solve(int64_t s, double *M, double *rhs, double *z) {
+    if (s == 0) return 0;
+    double *M0 = (double *)malloc(sizeof(double) * (size_t)(s * s));
+    double *r0 = (double *)malloc(sizeof(double) * (size_t)s);
+    memcpy(M0, M, sizeof(double) * (size_t)(s * s));
+    memcpy(r0, rhs, sizeof(double) * (size_t)s);
+    double mx = 0.0;
+    for (int64_t k = 0; k < s * s; ++k) if (fabs(M[k]) > mx) mx = fabs(M[k]);
+    double thr = ((double)s * DBL_EPSILON) * mx;
+    int singular = (mx == 0.0);
+    for (int64_t k = 0; k < s && !singular; ++k) {
+        int64_t piv = k;
+        double best = fabs(M[k * s + k]);
+        for (int64_t r = k + 1; r < s; ++r)
+            if (fabs(M[r * s + k]) > best) { best = fabs(M[r * s + k]); piv = r; }
+        if (best <= thr) { singular = 1; break; }
+        if (piv != k) {
+            for (int64_t c = 0; c < s; ++c) { double t = M[k * s + c]; M[k * s + c] = M[piv * s + c]; M[piv * s + c] = t; }
+            double t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
+        }
+        for (int64_t r = k + 1; r < s; ++r) {
+            double l = M[r * s + k] / M[k * s + k];
+            for (int64_t c = k + 1; c < s; ++c) M[r * s + c] = fma(-l, M[k * s + c], M[r * s + c]);
+            rhs[r] = fma(-l, rhs[k], rhs[r]);
+        }
+    }
+    if (!singular) {
+        for (int64_t c = s - 1; c >= 0; --c) {
+            z[c] = rhs[c] / M[c * s + c];
+            for (int64_t r = 0; r < c; ++r) rhs[r] = fma(-M[r * s + c], z[c], rhs[r]);
+        }
+    } else {
+        jacobi_ls(s, M0, r0, z);
+    }
+    free(M0); free(r0);
+    return singular;
+}
+
+/* FP32 version: identical steps in single precision (eps = FLT_EPSILON). */
+static void jacobi_lsf(int64_t s, const float *M0, const float *rhs0, float *z) {
+    float *B = (float *)malloc(sizeof(float) * (size_t)(s * s));
+    float *V = (float *)malloc(sizeof(float) * (size_t)(s * s));
+    float *sig = (float *)malloc(sizeof(float) * (size_t)s);
+    memcpy(B, M0, sizeof(float) * (size_t)(s * s));
+    for (int64_t r = 0; r < s; ++r)
+        for (int64_t c = 0; c < s; ++c) V[r * s + c] = (r == c) ? 1.0f : 0.0f;
+    const float tol = FLT_EPSILON * (float)s;
+    for (int sweep = 0; sweep < LS_MAX_SWEEPS; ++sweep) {
+        int rotated = 0;
+        for (int64_t p = 0; p < s - 1; ++p)
+            for (int64_t q = p + 1; q < s; ++q) {
+                float alpha = tree_dotf(B + p, s, B + p, s, s);
+                float beta = tree_dotf(B + q, s, B + q, s, s);
+                float gamma = tree_dotf(B + p, s, B + q, s, s);
+                if (gamma == 0.0f || fabsf(gamma) <= tol * sqrtf(alpha * beta)) continue;
+                rotated = 1;
+                float zeta = (beta - alpha) / (2.0f * gamma);
+                float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                float c = 1.0f / sqrtf(fmaf(t, t, 1.0f));
+                float sn = c * t;
+                for (int64_t r = 0; r < s; ++r) {
+                    float bp = B[r * s + p], bq = B[r * s + q];
+                    B[r * s + p] = fmaf(c, bp, -(sn * bq));
+                    B[r * s + q] = fmaf(sn, bp, c * bq);
+                    float vp = V[r * s + p], vq = V[r * s + q];
+                    V[r * s + p] = fmaf(c, vp, -(sn * vq));
+                    V[r * s + q] = fmaf(sn, vp, c * vq);
+                }
+            }
+        if (!rotated) break;
+    }
+    float smax = 0.0f;
+    for (int64_t j = 0; j < s; ++j) {
+        sig[j] = sqrtf(tree_dotf(B + j, s, B + j, s, s));
+        if (sig[j] > smax) smax = sig[j];
+    }
+    float cut = ((float)s * FLT_EPSILON) * smax;
+    for (int64_t r = 0; r < s; ++r) z[r] = 0.0f;
+    for (int64_t j = 0; j < s; ++j) {
+        if (!(sig[j] > cut)) continue;
+        float coef = (tree_dotf(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
+        for (int64_t r = 0; r < s; ++r) z[r] = fmaf(V[r * s + j], coef, z[r]);
+    }
+    free(B); free(V); free(sig);
+}
+
+int ora_local_solve_f32(int64_t s, float *M, float *rhs, float *z) {
+    if (s == 0) return 0;
+    float *M0 = (float *)malloc(sizeof(float) * (size_t)(s * s));
+    float *r0 = (float *)malloc(sizeof(float) * (size_t)s);
+    memcpy(M0, M, sizeof(float) * (size_t)(s * s));
+    memcpy(r0, rhs, sizeof(float) * (size_t)s);
+    float mx = 0.0f;
+    for (int64_t k = 0; k < s * s; ++k) if (fabsf(M[k]) > mx) mx = fabsf(M[k]);
+    float thr = ((float)s * FLT_EPSILON) * mx;
+    int singular = (mx == 0.0f);
+    for (int64_t k = 0; k < s && !singular; ++k) {
+        int64_t piv = k;
+        float best = fabsf(M[k * s + k]);
+        for (int64_t r = k + 1; r < s; ++r)
+            if (fabsf(M[r * s + k]) > best) { best = fabsf(M[r * s + k]); piv = r; }
+        if (best <= thr) { singular = 1; break; }
+        if (piv != k) {
+            for (int64_t c = 0; c < s; ++c) { float t = M[k * s + c]; M[k * s + c] = M[piv * s + c]; M[piv * s + c] = t; }
+            float t = rhs[k]; rhs[k] = rhs[piv]; rhs[piv] = t;
+        }
+        for (int64_t r = k + 1; r < s; ++r) {
+            float l = M[r * s + k] / M[k * s + k];
+            for (int64_t c = k + 1; c < s; ++c) M[r * s + c] = fmaf(-l, M[k * s + c], M[r * s + c]);
+            rhs[r] = fmaf(-l, rhs[k], rhs[r]);
+        }
+    }
+    if (!singular) {
+        for (int64_t c = s - 1; c >= 0; --c) {
+            z[c] = rhs[c] / M[c * s + c];
+            for (int64_t r = 0; r < c; ++r) rhs[r] = fmaf(-M[r * s + c], z[c], rhs[r]);
+        }
+    } else {
+        jacobi_lsf(s, M0, r0, z);
+    }
+    free(M0); free(r0);
+    return singular;
+}
+
+/* ------------------------------------------------------------------------- */
+/* lAIR restriction (Sec. 3.1). For C-point i with neighbourhood              */
+/* R_i = {l_1 < ... < l_s}: Eq. (3.2) reads M z = rhs with M[r][c] = a_{l_c,l_r}*/
+/* (the transpose of A restricted to R_i) and rhs[r] = -a_{i,l_r}; this makes   */
+/* a_{i,j} + sum_k z_k a_{k,j} = 0 for every j in R_i (Eq. (3.1)), i.e.         */
+/* (RA)_{i,j} = 0 on the pattern. Row i of R = {(l_r, z_r)} u {(i, 1)}.         */
+/* In FP32 mode M and rhs are rounded to float and solved in float; z is then  */
+/* stored exactly in double.                                                   */
+/* ------------------------------------------------------------------------- */
+static int build_lair_R(const ocsr *A, const int8_t *cf, const int64_t *cidx, int64_t nc, const int64_t *cpts,
+                        const int64_t *nb_rp, const int32_t *nb_col, int prec, ocsr *R, uint8_t *lsflag) {
+    int64_t nnz = nb_rp[nc] + nc;
+    if (csr_alloc(R, nc, A->nr, nnz)) return ORA_ERR_OOM;
+    int64_t smax = 0;
+    for (int64_t c = 0; c < nc; ++c) if (nb_rp[c + 1] - nb_rp[c] > smax) smax = nb_rp[c + 1] - nb_rp[c];
+    double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
+    double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+    double *z = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+    float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
+    float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+    float *zf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+    int64_t p = 0;
+    (void)cf; (void)cidx;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t i = cpts[c];
+        const int32_t *nb = nb_col + nb_rp[c];
+        int64_t s = nb_rp[c + 1] - nb_rp[c];
+        for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
+        for (int64_t r = 0; r < s; ++r) rhs[r] = 0.0;
+        for (int64_t cc = 0; cc < s; ++cc) {
+            int64_t row = nb[cc];
+            for (int64_t k = A->rp[row]; k < A->rp[row + 1]; ++k) {
+                int64_t r = find_pos(nb, s, A->col[k]);
+                if (r >= 0) M[r * s + cc] = A->val[k];
+            }
+        }
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int64_t r = find_pos(nb, s, A->col[k]);
+            if (r >= 0) rhs[r] = -A->val[k];
+        }
+        int ls;
+        if (prec == 0) {
+            ls = ora_local_solve(s, M, rhs, z);
+        } else {
+            for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
+            for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
+            ls = ora_local_solve_f32(s, Mf, rf, zf);
+            for (int64_t r = 0; r < s; ++r) z[r] = (double)zf[r];
+        }
+        if (lsflag) lsflag[c] = (uint8_t)ls;
+        /* merge {nb, z} with (i, 1) in ascending column order */
+        int placed = 0;
+        for (int64_t r = 0; r < s; ++r) {
+            if (!placed && i < nb[r]) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; placed = 1; }
+            R->col[p] = nb[r]; R->val[p] = z[r]; p++;
+        }
+        if (!placed) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; }
+        R->rp[c + 1] = p;
+    }
+    free(M); free(rhs); free(z); free(Mf); free(rf); free(zf);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Interpolation P = [W; I] (Eq. (2.2)).                                      */
+/* One-point (Sec. 4): F row j takes value 1 at its strongest C connection     */
+/* c in N_j (largest -a_jc, abs mode |a_jc|; ties -> smallest c), none -> an   */
+/* empty row. lAIP (approximate ideal interpolation, W ~ -A_ff^{-1}A_fc,       */
+/* Eq. (2.6)): for C-point c, Q_c = {F j : c in N_j} (distance two adds every  */
+/* F j' with N_j' containing an F point of that set), and A_QQ w = -A_{Q,c}:   */
+/* M[r][q] = a_{j_r, j_q}, rhs[r] = -a_{j_r, c}; W[j_r][c] = w_r. The local     */
+/* solve is the same routine (same pivoting and least-squares rules) as for R. */
+/* ------------------------------------------------------------------------- */
+static int build_P_onepoint(const ocsr *A, const ograph *S, const int8_t *cf, const int64_t *cidx,
+                            int64_t nc, int absmode, ocsr *P) {
+    int64_t n = A->nr;
+    if (csr_alloc(P, n, nc, n)) return ORA_ERR_OOM;
+    int64_t p = 0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (cf[j] == CF_C) {
+            P->col[p] = (int32_t)cidx[j]; P->val[p] = 1.0; p++;
+        } else {
+            int64_t best = -1;
+            double bv = 0.0;
+            for (int64_t q = S->rp[j]; q < S->rp[j + 1]; ++q) {
+                int64_t c = S->col[q];
+                if (cf[c] != CF_C) continue;
+                double a;
+                find_entry(A, j, c, &a);
+                double key = absmode ? fabs(a) : -a;
+                if (best < 0 || key > bv) { best = c; bv = key; }
+            }
+            if (best >= 0) { P->col[p] = (int32_t)cidx[best]; P->val[p] = 1.0; p++; }
+        }
+        P->rp[j + 1] = p;
+    }
+    return ORA_OK;
+}
+
+typedef struct { int64_t row; int32_t col; double val; } coo_ent;
+
+static int cmp_coo(const void *a, const void *b) {
+    const coo_ent *x = (const coo_ent *)a, *y = (const coo_ent *)b;
+    if (x->row != y->row) return (x->row > y->row) - (x->row < y->row);
+    return (x->col > y->col) - (x->col < y->col);
+}
+
+static int build_P_laip(const ocsr *A, const ograph *S, const ograph *ST, const int8_t *cf,
+                        const int64_t *cidx, int64_t nc, const int64_t *cpts, int distance, int prec,
+                        ocsr *P, uint8_t *lsflag) {
+    int64_t n = A->nr;
+    /* neighbourhoods Q_c are the distance-k neighbourhoods of c in the transposed graph */
+    int64_t *q_rp; int32_t *q_col;
+    build_neighbourhoods(ST, cf, distance, nc, cpts, &q_rp, &q_col);
+    int64_t total = q_rp[nc] + nc;
+    coo_ent *ent = (coo_ent *)malloc(sizeof(coo_ent) * (size_t)(total > 0 ? total : 1));
+    int64_t smax = 0;
+    for (int64_t c = 0; c < nc; ++c) if (q_rp[c + 1] - q_rp[c] > smax) smax = q_rp[c + 1] - q_rp[c];
+    double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
+    double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+    double *w = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+    float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
+    float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+    float *wf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+    int64_t e = 0;
+    (void)S;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t ci = cpts[c];
+        const int32_t *Q = q_col + q_rp[c];
+        int64_t s = q_rp[c + 1] - q_rp[c];
+        for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
+        for (int64_t r = 0; r < s; ++r) {
+            int64_t jr = Q[r];
+            for (int64_t k = A->rp[jr]; k < A->rp[jr + 1]; ++k) {
+                int64_t q = find_pos(Q, s, A->col[k]);
+                if (q >= 0) M[r * s + q] = A->val[k];
+            }
+            double a;
+            find_entry(A, jr, ci, &a);
+            rhs[r] = -a;
+        }
+        int ls;
+        if (prec == 0) {
+            ls = ora_local_solve(s, M, rhs, w);
+        } else {
+            for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
+            for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
+            ls = ora_local_solve_f32(s, Mf, rf, wf);
+            for (int64_t r = 0; r < s; ++r) w[r] = (double)wf[r];
+        }
+        if (lsflag) lsflag[c] = (uint8_t)ls;
+        for (int64_t r = 0; r < s; ++r) ent[e++] = (coo_ent){Q[r], (int32_t)c, w[r]};
+        ent[e++] = (coo_ent){ci, (int32_t)c, 1.0};
+    }
+    qsort(ent, (size_t)e, sizeof(coo_ent), cmp_coo);
+    if (csr_alloc(P, n, nc, e)) return ORA_ERR_OOM;
+    for (int64_t k = 0; k < e; ++k) {
+        P->rp[ent[k].row + 1]++;
+        P->col[k] = ent[k].col;
+        P->val[k] = ent[k].val;
+    }
+    for (int64_t i = 0; i < n; ++i) P->rp[i + 1] += P->rp[i];
+    (void)cidx;
+    free(ent); free(q_rp); free(q_col); free(M); free(rhs); free(w); free(Mf); free(rf); free(wf);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Galerkin coarse operator K = R A P (Sec. 2.1). First (RA)_{a,l} =           */
+/* sum over k in row a of R (ascending) of R_ak A_kl, then K_{a,b} = sum over  */
+/* l in row a of RA (ascending) of (RA)_al P_lb; every sum starts at 0 and     */
+/* adds its terms with fma in that order. The pattern is the full symbolic     */
+/* product: structural zeros are kept.                                         */
+/* ------------------------------------------------------------------------- */
+static int spgemm(const ocsr *X, const ocsr *Y, ocsr *Z) {
+    int64_t nr = X->nr, ncol = Y->nc;
+    double *acc = (double *)malloc(sizeof(double) * (size_t)(ncol > 0 ? ncol : 1));
+    int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncol > 0 ? ncol : 1));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncol > 0 ? ncol : 1));
+    for (int64_t j = 0; j < ncol; ++j) mark[j] = -1;
+    int64_t cap = X->rp[nr] + Y->rp[Y->nr] + 16, len = 0;
+    Z->nr = nr; Z->nc = ncol;
+    Z->rp = (int64_t *)calloc((size_t)nr + 1, sizeof(int64_t));
+    Z->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    Z->val = (double *)malloc(sizeof(double) * (size_t)cap);
+    for (int64_t a = 0; a < nr; ++a) {
+        int64_t cnt = 0;
+        for (int64_t p = X->rp[a]; p < X->rp[a + 1]; ++p) {
+            int64_t k = X->col[p];
+            double x = X->val[p];
+            for (int64_t q = Y->rp[k]; q < Y->rp[k + 1]; ++q) {
+                int64_t l = Y->col[q];
+                if (mark[l] != a) { mark[l] = a; acc[l] = 0.0; list[cnt++] = (int32_t)l; }
+                acc[l] = fma(x, Y->val[q], acc[l]);
+            }
+        }
+        qsort(list, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        if (len + cnt > cap) {
+            while (len + cnt > cap) cap *= 2;
+            Z->col = (int32_t *)realloc(Z->col, sizeof(int32_t) * (size_t)cap);
+            Z->val = (double *)realloc(Z->val, sizeof(double) * (size_t)cap);
+        }
+        for (int64_t t = 0; t < cnt; ++t) { Z->col[len] = list[t]; Z->val[len] = acc[list[t]]; len++; }
+        Z->rp[a + 1] = len;
+    }
+    free(acc); free(mark); free(list);
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lumping (Sec. 3.3): in row i, every off-diagonal with |k_ij| <             */
+/* theta_D * max_j |k_ij| (max over the whole row, diagonal included) is       */
+/* removed and added to the diagonal; the additions go in ascending j order,   */
+/* starting from k_ii. The row sum is kept.                                    */
+/* ------------------------------------------------------------------------- */
+static int lump(ocsr *K, double tol) {
+    int64_t n = K->nr, p = 0;
+    int64_t start = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t end = K->rp[i + 1];
+        double m = 0.0;
+        for (int64_t k = start; k < end; ++k) if (fabs(K->val[k]) > m) m = fabs(K->val[k]);
+        double thr = tol * m;
+        double d = 0.0;
+        int64_t dpos = -1;
+        for (int64_t k = start; k < end; ++k) if (K->col[k] == i) { d = K->val[k]; dpos = k; }
+        if (dpos < 0) return ORA_ERR_ZERO_DIAG;
+        for (int64_t k = start; k < end; ++k)
+            if (K->col[k] != i && fabs(K->val[k]) < thr) d = d + K->val[k];
+        for (int64_t k = start; k < end; ++k) {
+            if (K->col[k] != i && fabs(K->val[k]) < thr) continue;
+            K->col[p] = K->col[k];
+            K->val[p] = (K->col[k] == i) ? d : K->val[k];
+            p++;
+        }
+        start = end;
+        K->rp[i + 1] = p;
+    }
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block-diagonal scaling for DG (Sec. 4.2.1): A -> D_B^{-1} A, b -> D_B^{-1} b*/
+/* D_B = the bs x bs diagonal blocks. D_B^{-1} columns come from the LU above  */
+/* applied to unit vectors (same pivot and elimination order); the scaled row  */
+/* r of block K is sum_t Dinv[r][t] * A[K t, :] with fma in ascending t. The   */
+/* diagonal block of the result is set to the exact identity.                  */
+/* ------------------------------------------------------------------------- */
+static int block_inverse(int64_t s, const double *D, double *Dinv) {
+    double *M = (double *)malloc(sizeof(double) * (size_t)(s * s));
+    double *L = (double *)calloc((size_t)(s * s), sizeof(double));
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)s);
+    memcpy(M, D, sizeof(double) * (size_t)(s * s));
+    for (int64_t r = 0; r < s; ++r) perm[r] = r;
+    double mx = 0.0;
+    for (int64_t k = 0; k < s * s; ++k) if (fabs(M[k]) > mx) mx = fabs(M[k]);
+    double thr = ((double)s * DBL_EPSILON) * mx;
+    int bad = (mx == 0.0);
+    for (int64_t k = 0; k < s && !bad; ++k) {
+        int64_t piv = k;
+        double best = fabs(M[k * s + k]);
+        for (int64_t r = k + 1; r < s; ++r)
+            if (fabs(M[r * s + k]) > best) { best = fabs(M[r * s + k]); piv = r; }
+        if (best <= thr) { bad = 1; break; }
+        if (piv != k) {
+            for (int64_t c = 0; c < s; ++c) {
+                double t = M[k * s + c]; M[k * s + c] = M[piv * s + c]; M[piv * s + c] = t;
+                t = L[k * s + c]; L[k * s + c] = L[piv * s + c]; L[piv * s + c] = t;
+            }
+            int64_t t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+        }
+        for (int64_t r = k + 1; r < s; ++r) {
+            double l = M[r * s + k] / M[k * s + k];
+            L[r * s + k] = l;
+            for (int64_t c = k + 1; c < s; ++c) M[r * s + c] = fma(-l, M[k * s + c], M[r * s + c]);
+        }
+    }
+    if (!bad) {
+        double *rhs = (double *)malloc(sizeof(double) * (size_t)s);
+        for (int64_t t = 0; t < s; ++t) {
+            for (int64_t r = 0; r < s; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
+            for (int64_t k = 0; k < s; ++k)
+                for (int64_t r = k + 1; r < s; ++r) rhs[r] = fma(-L[r * s + k], rhs[k], rhs[r]);
+            for (int64_t c = s - 1; c >= 0; --c) {
+                double zc = rhs[c] / M[c * s + c];
+                Dinv[c * s + t] = zc;
+                for (int64_t r = 0; r < c; ++r) rhs[r] = fma(-M[r * s + c], zc, rhs[r]);
+            }
+        }
+        free(rhs);
+    }
+    free(M); free(L); free(perm);
+    return bad ? ORA_ERR_ZERO_DIAG : ORA_OK;
+}
+
+/* entries of D_B^{-1} A: per block, bs rows x (1 + union of off-block columns) */
+int64_t ora_block_scale_nnz(int64_t n, const int64_t *rp, const int32_t *col, int64_t bs) {
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rp[n] + 1));
+    int64_t total = 0;
+    for (int64_t K = 0; K < n / bs; ++K) {
+        int64_t r0 = K * bs, nc = 0;
+        for (int64_t r = 0; r < bs; ++r)
+            for (int64_t k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k)
+                if (col[k] < r0 || col[k] >= r0 + bs) cols[nc++] = col[k];
+        qsort(cols, (size_t)nc, sizeof(int32_t), cmp_i32);
+        int64_t u = 0;
+        for (int64_t a = 0; a < nc; ++a) if (u == 0 || cols[u - 1] != cols[a]) cols[u++] = cols[a];
+        total += bs * (u + 1);
+    }
+    free(cols);
+    return total;
+}
+
+int ora_block_scale(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int64_t bs,
+                    int64_t *out_rp, int32_t *out_col, double *out_val, double *dinv_blocks) {
+    /* out arrays hold ora_block_scale_nnz() entries */
+    int64_t nb = n / bs, p = 0;
+    double *D = (double *)malloc(sizeof(double) * (size_t)(bs * bs));
+    double *Di = (double *)malloc(sizeof(double) * (size_t)(bs * bs));
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rp[n] + 1));
+    out_rp[0] = 0;
+    for (int64_t K = 0; K < nb; ++K) {
+        int64_t r0 = K * bs;
+        for (int64_t t = 0; t < bs * bs; ++t) D[t] = 0.0;
+        for (int64_t r = 0; r < bs; ++r)
+            for (int64_t k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k)
+                if (col[k] >= r0 && col[k] < r0 + bs) D[r * bs + (col[k] - r0)] = val[k];
+        if (block_inverse(bs, D, Di)) { free(D); free(Di); free(cols); return ORA_ERR_ZERO_DIAG; }
+        if (dinv_blocks) memcpy(dinv_blocks + K * bs * bs, Di, sizeof(double) * (size_t)(bs * bs));
+        /* union of the block rows' columns outside the diagonal block */
+        int64_t nc = 0;
+        for (int64_t r = 0; r < bs; ++r)
+            for (int64_t k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k)
+                if (col[k] < r0 || col[k] >= r0 + bs) cols[nc++] = col[k];
+        qsort(cols, (size_t)nc, sizeof(int32_t), cmp_i32);
+        int64_t u = 0;
+        for (int64_t a = 0; a < nc; ++a) if (u == 0 || cols[u - 1] != cols[a]) cols[u++] = cols[a];
+        for (int64_t r = 0; r < bs; ++r) {
+            int placed = 0;
+            for (int64_t a = 0; a <= u; ++a) {
+                if (!placed && (a == u || cols[a] > r0 + r)) {
+                    out_col[p] = (int32_t)(r0 + r); out_val[p] = 1.0; p++; placed = 1;
+                }
+                if (a == u) break;
+                int64_t j = cols[a];
+                double acc = 0.0;
+                for (int64_t t = 0; t < bs; ++t) {
+                    double a_tj;
+                    find_entry(&(ocsr){n, n, (int64_t *)rp, (int32_t *)col, (double *)val}, r0 + t, j, &a_tj);
+                    acc = fma(Di[r * bs + t], a_tj, acc);
+                }
+                out_col[p] = (int32_t)j; out_val[p] = acc; p++;
+            }
+            out_rp[r0 + r + 1] = p;
+        }
+    }
+    free(D); free(Di); free(cols);
+    return ORA_OK;
+}
+
+static void block_apply(int64_t n, int64_t bs, const double *dinv_blocks, const double *b, double *out) {
+    for (int64_t K = 0; K < n / bs; ++K)
+        for (int64_t r = 0; r < bs; ++r) {
+            double acc = 0.0;
+            for (int64_t t = 0; t < bs; ++t) acc = fma(dinv_blocks[K * bs * bs + r * bs + t], b[K * bs + t], acc);
+            out[K * bs + r] = acc;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dense LU for the coarsest level (partial pivoting, same rules as above).    */
+/* ------------------------------------------------------------------------- */
+typedef struct { int64_t n; double *LU; int64_t *perm; } odense;
+
+static int dense_factor(const ocsr *A, odense *d) {
+    int64_t n = A->nr;
+    d->n = n;
+    d->LU = (double *)calloc((size_t)(n * n > 0 ? n * n : 1), sizeof(double));
+    d->perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) d->LU[i * n + A->col[k]] = A->val[k];
+    for (int64_t i = 0; i < n; ++i) d->perm[i] = i;
+    double *M = d->LU;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t piv = k;
+        double best = fabs(M[k * n + k]);
+        for (int64_t r = k + 1; r < n; ++r)
+            if (fabs(M[r * n + k]) > best) { best = fabs(M[r * n + k]); piv = r; }
+        if (best == 0.0) return ORA_ERR_ZERO_DIAG;
+        if (piv != k) {
+            for (int64_t c = 0; c < n; ++c) { double t = M[k * n + c]; M[k * n + c] = M[piv * n + c]; M[piv * n + c] = t; }
+            int64_t t = d->perm[k]; d->perm[k] = d->perm[piv]; d->perm[piv] = t;
+        }
+        for (int64_t r = k + 1; r < n; ++r) {
+            double l = M[r * n + k] / M[k * n + k];
+            M[r * n + k] = l;
+            for (int64_t c = k + 1; c < n; ++c) M[r * n + c] = fma(-l, M[k * n + c], M[r * n + c]);
+        }
+    }
+    return ORA_OK;
+}
+
+static void dense_solve(const odense *d, const double *b, double *x) {
+    int64_t n = d->n;
+    const double *M = d->LU;
+    for (int64_t r = 0; r < n; ++r) x[r] = b[d->perm[r]];
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t r = k + 1; r < n; ++r) x[r] = fma(-M[r * n + k], x[k], x[r]);
+    for (int64_t c = n - 1; c >= 0; --c) {
+        x[c] = x[c] / M[c * n + c];
+        for (int64_t r = 0; r < c; ++r) x[r] = fma(-M[r * n + c], x[c], x[r]);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Hierarchy                                                                  */
+/* ------------------------------------------------------------------------- */
+#define ORA_MAX_LEVELS 64
+
+typedef struct {
+    ocsr A;            /* level operator (lumped on coarse levels) */
+    int8_t *cf;        /* 1 = C, 0 = F (levels that coarsen) */
+    int64_t *cidx;     /* coarse index or -1 */
+    int64_t nc;
+    uint8_t *strong;   /* strength mask over A's pattern (theta) */
+    uint8_t *strong_cf;/* strength mask for the splitting (theta_cf) */
+    ocsr R, P;
+    uint8_t *ls_R, *ls_P;
+    double *dinv;
+    float *A32, *R32, *P32, *dinv32;
+} olevel;
+
+typedef struct {
+    ora_opts o;
+    int nlev;
+    olevel lev[ORA_MAX_LEVELS];
+    odense coarse;
+    int64_t bs;
+    double *blk_inv;   /* block inverses for DG scaling */
+    /* work */
+    double *w64[ORA_MAX_LEVELS][4];
+    float *w32[ORA_MAX_LEVELS][4];
+    int status;
+    int64_t singular_R, singular_P;
+} ohier;
+
+void ora_opts_default(ora_opts *o) {
+    memset(o, 0, sizeof(*o));
+    o->cf_mode = 3;
+    o->distance = 1;
+    o->theta = 0.25;
+    o->theta_cf = 0.25;
+    o->strength_abs = 0;
+    o->interp = 0;
+    o->relax = 0;
+    o->lump_tol = 1e-3;
+    o->lump_level0 = 0;
+    o->prec = 0;
+    o->coarse_max = 256;
+    o->max_levels = 25;
+    o->block_size = 0;
+    o->rs_max_n = 8192;
+    o->pmis_seed = 0x5eedULL;
+}
+
+static int coarsen_level(ohier *H, int l, int *is_last) {
+    olevel *L = &H->lev[l];
+    const ora_opts *o = &H->o;
+    ocsr *A = &L->A;
+    int64_t n = A->nr, nnz = A->rp[n];
+    int st;
+    L->strong = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    L->strong_cf = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    ora_strength(n, A->rp, A->col, A->val, o->theta, o->strength_abs, L->strong);
+    ora_strength(n, A->rp, A->col, A->val, o->theta_cf, o->strength_abs, L->strong_cf);
+    ograph S, ST, Scf, STcf;
+    graph_from_mask(n, A->rp, A->col, L->strong, &S);
+    graph_transpose(&S, &ST);
+    graph_from_mask(n, A->rp, A->col, L->strong_cf, &Scf);
+    graph_transpose(&Scf, &STcf);
+    L->cf = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (l == 0 && o->cf_mode == 2 && o->cf_user) {
+        for (int64_t i = 0; i < n; ++i) L->cf[i] = o->cf_user[i] ? CF_C : CF_F;
+    } else {
+        int use_rs = (o->cf_mode == 0) || (o->cf_mode != 1 && n <= o->rs_max_n);
+        if (use_rs) cf_rs(&Scf, &STcf, L->cf);
+        else cf_pmis(&Scf, &STcf, o->pmis_seed + (uint64_t)l, L->cf);
+    }
+    L->cidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n; ++i) L->cidx[i] = (L->cf[i] == CF_C) ? nc++ : -1;
+    L->nc = nc;
+    if (nc == 0 || nc == n) {
+        graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
+        *is_last = 1;
+        return ORA_OK;
+    }
+    int64_t *cpts = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    for (int64_t i = 0; i < n; ++i) if (L->cf[i] == CF_C) cpts[L->cidx[i]] = i;
+    int64_t *nb_rp; int32_t *nb_col;
+    build_neighbourhoods(&S, L->cf, o->distance, nc, cpts, &nb_rp, &nb_col);
+    L->ls_R = (uint8_t *)calloc((size_t)nc, 1);
+    st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &L->R, L->ls_R);
+    free(nb_rp); free(nb_col);
+    if (st) return st;
+    if (o->interp == 1) {
+        st = build_P_onepoint(A, &S, L->cf, L->cidx, nc, o->strength_abs, &L->P);
+    } else {
+        L->ls_P = (uint8_t *)calloc((size_t)nc, 1);
+        st = build_P_laip(A, &S, &ST, L->cf, L->cidx, nc, cpts, o->distance, o->prec, &L->P, L->ls_P);
+    }
+    free(cpts);
+    graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
+    if (st) return st;
+    for (int64_t c = 0; c < nc; ++c) {
+        H->singular_R += L->ls_R[c];
+        if (L->ls_P) H->singular_P += L->ls_P[c];
+    }
+    ocsr RA, K;
+    spgemm(&L->R, A, &RA);
+    spgemm(&RA, &L->P, &K);
+    csr_free(&RA);
+    if (o->lump_tol > 0.0) {
+        st = lump(&K, o->lump_tol);
+        if (st) { csr_free(&K); return st; }
+    }
+    H->lev[l + 1].A = K;
+    *is_last = 0;
+    return ORA_OK;
+}
+
+static int finish_level(ohier *H, int l) {
+    olevel *L = &H->lev[l];
+    int64_t n = L->A.nr;
+    L->dinv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        double d;
+        if (!find_entry(&L->A, i, i, &d) || d == 0.0) return ORA_ERR_ZERO_DIAG;
+        L->dinv[i] = 1.0 / d;
+    }
+    for (int k = 0; k < 4; ++k) {
+        H->w64[l][k] = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        H->w32[l][k] = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
+    }
+    if (H->o.prec == 1) {
+        int64_t nnz = L->A.rp[n];
+        L->A32 = (float *)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+        for (int64_t k = 0; k < nnz; ++k) L->A32[k] = (float)L->A.val[k];
+        L->dinv32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) L->dinv32[i] = (float)L->dinv[i];
+        if (L->R.rp) {
+            int64_t r = L->R.rp[L->R.nr], p = L->P.rp[L->P.nr];
+            L->R32 = (float *)malloc(sizeof(float) * (size_t)(r > 0 ? r : 1));
+            L->P32 = (float *)malloc(sizeof(float) * (size_t)(p > 0 ? p : 1));
+            for (int64_t k = 0; k < r; ++k) L->R32[k] = (float)L->R.val[k];
+            for (int64_t k = 0; k < p; ++k) L->P32[k] = (float)L->P.val[k];
+        }
+    }
+    return ORA_OK;
+}
+
+void ora_free(ohier *H) {
+    if (!H) return;
+    for (int l = 0; l < H->nlev; ++l) {
+        olevel *L = &H->lev[l];
+        csr_free(&L->A); csr_free(&L->R); csr_free(&L->P);
+        free(L->cf); free(L->cidx); free(L->strong); free(L->strong_cf); free(L->ls_R); free(L->ls_P);
+        free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32);
+        for (int k = 0; k < 4; ++k) { free(H->w64[l][k]); free(H->w32[l][k]); }
+    }
+    free(H->coarse.LU); free(H->coarse.perm); free(H->blk_inv);
+    free(H);
+}
+
+ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                 const ora_opts *opts, int *status) {
+    ohier *H = (ohier *)calloc(1, sizeof(ohier));
+    H->o = *opts;
+    int64_t nnz = rp[n];
+    ocsr *A0 = &H->lev[0].A;
+    if (opts->block_size > 1 && n % opts->block_size) { *status = ORA_ERR_ARG; return H; }
+    if (opts->block_size > 1) nnz = ora_block_scale_nnz(n, rp, col, opts->block_size);
+    if (csr_alloc(A0, n, n, nnz)) { *status = ORA_ERR_OOM; return H; }
+    if (opts->block_size > 1) {
+        H->bs = opts->block_size;
+        H->blk_inv = (double *)malloc(sizeof(double) * (size_t)(n * H->bs));
+        int st = ora_block_scale(n, rp, col, val, H->bs, A0->rp, A0->col, A0->val, H->blk_inv);
+        if (st) { *status = st; H->nlev = 1; return H; }
+    } else {
+        memcpy(A0->rp, rp, sizeof(int64_t) * (size_t)(n + 1));
+        memcpy(A0->col, col, sizeof(int32_t) * (size_t)nnz);
+        memcpy(A0->val, val, sizeof(double) * (size_t)nnz);
+    }
+    if (opts->lump_level0 && opts->lump_tol > 0.0) {
+        int st = lump(A0, opts->lump_tol);
+        if (st) { *status = st; H->nlev = 1; return H; }
+    }
+    int l = 0;
+    for (;;) {
+        H->nlev = l + 1;
+        int64_t nl = H->lev[l].A.nr;
+        int last = (nl <= opts->coarse_max) || (l + 1 >= opts->max_levels) || (l + 1 >= ORA_MAX_LEVELS);
+        if (!last) {
+            int st = coarsen_level(H, l, &last);
+            if (st) { *status = st; return H; }
+        }
+        int st = finish_level(H, l);
+        if (st) { *status = st; return H; }
+        if (last) {
+            if (nl > 4096) { *status = ORA_ERR_STALLED; return H; }
+            st = dense_factor(&H->lev[l].A, &H->coarse);
+            *status = st;
+            return H;
+        }
+        ++l;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Cycle (Sec. 4): post-relaxation only, zero initial guess on every level.    */
+/* cycle(l, b): bc = R b; xc = cycle(l+1, bc); x = P xc; then Jacobi sweeps    */
+/* over F, F, C (or F, C, F / F, F): x_i <- x_i + dinv_i (b_i - A_i x) for the */
+/* swept set, every update of a sweep reading the same old x (Eq. (2.4)).      */
+/* Row products accumulate with fma in ascending column order.                 */
+/* ------------------------------------------------------------------------- */
+static void spmv64(const ocsr *A, const double *x, double *y) {
+    for (int64_t i = 0; i < A->nr; ++i) {
+        double acc = 0.0;
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) acc = fma(A->val[k], x[A->col[k]], acc);
+        y[i] = acc;
+    }
+}
+
+static void sweep64(const olevel *L, int target, const double *b, const double *x, double *xo) {
+    const ocsr *A = &L->A;
+    for (int64_t i = 0; i < A->nr; ++i) {
+        if (L->cf[i] != target) { xo[i] = x[i]; continue; }
+        double acc = 0.0;
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) acc = fma(A->val[k], x[A->col[k]], acc);
+        xo[i] = fma(L->dinv[i], b[i] - acc, x[i]);
+    }
+}
+
+static const int relax_seq[3][3] = {{CF_F, CF_F, CF_C}, {CF_F, CF_C, CF_F}, {CF_F, CF_F, -9}};
+
+static void cycle64(ohier *H, int l, const double *b, double *x) {
+    olevel *L = &H->lev[l];
+    int64_t n = L->A.nr;
+    if (l == H->nlev - 1) { dense_solve(&H->coarse, b, x); return; }
+    double *bc = H->w64[l + 1][0], *xc = H->w64[l + 1][1];
+    spmv64(&L->R, b, bc);
+    cycle64(H, l + 1, bc, xc);
+    spmv64(&L->P, xc, x);
+    double *t = H->w64[l][2];
+    for (int s = 0; s < 3; ++s) {
+        int tgt = relax_seq[H->o.relax][s];
+        if (tgt == -9) break;
+        sweep64(L, tgt, b, x, t);
+        memcpy(x, t, sizeof(double) * (size_t)n);
+    }
+}
+
+static void spmv32(int64_t nr, const int64_t *rp, const int32_t *col, const float *val, const float *x, float *y) {
+    for (int64_t i = 0; i < nr; ++i) {
+        float acc = 0.0f;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) acc = fmaf(val[k], x[col[k]], acc);
+        y[i] = acc;
+    }
+}
+
+static void cycle32(ohier *H, int l, const float *b, float *x) {
+    olevel *L = &H->lev[l];
+    int64_t n = L->A.nr;
+    if (l == H->nlev - 1) {
+        double *bd = H->w64[l][0], *xd = H->w64[l][1];
+        for (int64_t i = 0; i < n; ++i) bd[i] = (double)b[i];
+        dense_solve(&H->coarse, bd, xd);
+        for (int64_t i = 0; i < n; ++i) x[i] = (float)xd[i];
+        return;
+    }
+    float *bc = H->w32[l + 1][0], *xc = H->w32[l + 1][1];
+    spmv32(L->R.nr, L->R.rp, L->R.col, L->R32, b, bc);
+    cycle32(H, l + 1, bc, xc);
+    spmv32(L->P.nr, L->P.rp, L->P.col, L->P32, xc, x);
+    float *t = H->w32[l][2];
+    for (int s = 0; s < 3; ++s) {
+        int tgt = relax_seq[H->o.relax][s];
+        if (tgt == -9) break;
+        for (int64_t i = 0; i < n; ++i) {
+            if (L->cf[i] != tgt) { t[i] = x[i]; continue; }
+            float acc = 0.0f;
+            for (int64_t k = L->A.rp[i]; k < L->A.rp[i + 1]; ++k) acc = fmaf(L->A32[k], x[L->A.col[k]], acc);
+            t[i] = fmaf(L->dinv32[i], b[i] - acc, x[i]);
+        }
+        memcpy(x, t, sizeof(float) * (size_t)n);
+    }
+}
+
+/* x = M^{-1} b (one V-cycle, zero initial guess), in the hierarchy's precision */
+static void precond(ohier *H, const double *b, double *x) {
+    int64_t n = H->lev[0].A.nr;
+    if (H->o.prec == 0) {
+        cycle64(H, 0, b, x);
+    } else {
+        float *b32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+        float *x32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) b32[i] = (float)b[i];
+        cycle32(H, 0, b32, x32);
+        for (int64_t i = 0; i < n; ++i) x[i] = (double)x32[i];
+        free(b32); free(x32);
+    }
+}
+
+void ora_precond_apply(ohier *H, const double *b, double *x) { precond(H, b, x); }
+
+static double norm2(int64_t n, const double *x) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = fma(x[i], x[i], s);
+    return sqrt(s);
+}
+
+static double dot(int64_t n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s = fma(x[i], y[i], s);
+    return s;
+}
+
+static void residual(const ocsr *A, const double *b, const double *x, double *r) {
+    for (int64_t i = 0; i < A->nr; ++i) {
+        double acc = 0.0;
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) acc = fma(A->val[k], x[A->col[k]], acc);
+        r[i] = b[i] - acc;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Outer FP64 loops. cycle = 0: stationary iteration (iterative refinement):   */
+/* r = b - A x, x += M^{-1} r. cycle = 1: right-preconditioned flexible GMRES  */
+/* with restart m; Arnoldi by classical Gram-Schmidt applied twice; Givens     */
+/* rotations; stop when the true relative residual ||b - A x|| / ||b|| <= tol. */
+/* The system solved is the scaled one when block scaling is on.               */
+/* Returns iterations (preconditioner applications); hist gets rel. residuals. */
+/* ------------------------------------------------------------------------- */
+int ora_solve(ohier *H, const double *b_in, double *x, double tol, int cycle, int max_iter, int restart,
+              int *iters, double *final_rel, double *hist, int hist_cap) {
+    const ocsr *A = &H->lev[0].A;
+    int64_t n = A->nr;
+    double *b = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (H->bs > 1) block_apply(n, H->bs, H->blk_inv, b_in, b);
+    else memcpy(b, b_in, sizeof(double) * (size_t)n);
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *e = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double bn = norm2(n, b);
+    if (bn == 0.0) bn = 1.0;
+    int it = 0, nh = 0, status = ORA_ERR_NOT_CONVERGED;
+    residual(A, b, x, r);
+    double rel = norm2(n, r) / bn;
+    if (hist && nh < hist_cap) hist[nh++] = rel;
+    if (cycle == 0) {
+        while (rel > tol && it < max_iter) {
+            precond(H, r, e);
+            for (int64_t i = 0; i < n; ++i) x[i] += e[i];
+            residual(A, b, x, r);
+            rel = norm2(n, r) / bn;
+            ++it;
+            if (hist && nh < hist_cap) hist[nh++] = rel;
+            if (rel != rel) { status = ORA_ERR_NAN; break; }
+        }
+    } else {
+        int m = restart > 0 ? restart : 30;
+        double *V = (double *)malloc(sizeof(double) * (size_t)(n * (m + 1)));
+        double *Z = (double *)malloc(sizeof(double) * (size_t)(n * m));
+        double *Hm = (double *)calloc((size_t)((m + 1) * m), sizeof(double));
+        double *cs = (double *)malloc(sizeof(double) * (size_t)m);
+        double *sn = (double *)malloc(sizeof(double) * (size_t)m);
+        double *g = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+        double *h = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+        double *y = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+        double *hh = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+        while (rel > tol && it < max_iter) {
+            double beta = norm2(n, r);
+            for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+            for (int k = 0; k <= m; ++k) g[k] = 0.0;
+            g[0] = beta;
+            int j, jdone = 0;
+            for (j = 0; j < m && it < max_iter; ++j) {
+                double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
+                precond(H, vj, zj);
+                ++it;
+                spmv64(A, zj, w);
+                for (int k = 0; k <= j; ++k) h[k] = 0.0;
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int k = 0; k <= j; ++k) hh[k] = dot(n, V + (size_t)k * n, w);
+                    for (int k = 0; k <= j; ++k) {
+                        const double *vk = V + (size_t)k * n;
+                        for (int64_t i = 0; i < n; ++i) w[i] = fma(-hh[k], vk[i], w[i]);
+                        h[k] += hh[k];
+                    }
+                }
+                double hn = norm2(n, w);
+                h[j + 1] = hn;
+                if (hn > 0.0) for (int64_t i = 0; i < n; ++i) w[i] = w[i] / hn;
+                for (int k = 0; k < j; ++k) {
+                    double t = cs[k] * h[k] + sn[k] * h[k + 1];
+                    h[k + 1] = -sn[k] * h[k] + cs[k] * h[k + 1];
+                    h[k] = t;
+                }
+                double den = sqrt(h[j] * h[j] + h[j + 1] * h[j + 1]);
+                cs[j] = (den > 0.0) ? h[j] / den : 1.0;
+                sn[j] = (den > 0.0) ? h[j + 1] / den : 0.0;
+                h[j] = den;
+                h[j + 1] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                for (int k = 0; k <= j; ++k) Hm[k * m + j] = h[k];
+                double est = fabs(g[j + 1]) / bn;
+                if (hist && nh < hist_cap) hist[nh++] = est;
+                jdone = j + 1;
+                if (est <= tol || hn == 0.0) { ++j; break; }
+            }
+            /* y = H^{-1} g (upper triangular, jdone x jdone) */
+            for (int k = jdone - 1; k >= 0; --k) {
+                double acc = g[k];
+                for (int c = k + 1; c < jdone; ++c) acc -= Hm[k * m + c] * y[c];
+                y[k] = acc / Hm[k * m + k];
+            }
+            for (int k = 0; k < jdone; ++k) {
+                const double *zk = Z + (size_t)k * n;
+                for (int64_t i = 0; i < n; ++i) x[i] = fma(y[k], zk[i], x[i]);
+            }
+            residual(A, b, x, r);
+            rel = norm2(n, r) / bn;
+            if (rel != rel) { status = ORA_ERR_NAN; break; }
+        }
+        free(V); free(Z); free(Hm); free(cs); free(sn); free(g); free(h); free(y); free(hh);
+    }
+    if (rel <= tol) status = ORA_OK;
+    *iters = it;
+    *final_rel = rel;
+    free(b); free(r); free(e);
+    (void)dot;
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Export for tests                                                           */
+/* ------------------------------------------------------------------------- */
+int ora_nlevels(const ohier *H) { return H->nlev; }
+int64_t ora_singular_count(const ohier *H, int which) { return which ? H->singular_P : H->singular_R; }
+
+/* info[0..7] = n, nnz(A), nc, nnz(R), nnz(P), has_cf, 0, 0 */
+void ora_level_info(const ohier *H, int l, int64_t *info) {
+    const olevel *L = &H->lev[l];
+    info[0] = L->A.nr;
+    info[1] = L->A.rp ? L->A.rp[L->A.nr] : 0;
+    info[2] = L->cf ? L->nc : 0;
+    info[3] = L->R.rp ? L->R.rp[L->R.nr] : 0;
+    info[4] = L->P.rp ? L->P.rp[L->P.nr] : 0;
+    info[5] = L->cf != NULL;
+    info[6] = 0;
+    info[7] = 0;
+}
+
+/* which: 0 A, 1 R, 2 P */
+void ora_export_csr(const ohier *H, int l, int which, int64_t *rp, int32_t *col, double *val) {
+    const olevel *L = &H->lev[l];
+    const ocsr *M = which == 0 ? &L->A : (which == 1 ? &L->R : &L->P);
+    if (!M->rp) return;
+    int64_t nnz = M->rp[M->nr];
+    if (rp) memcpy(rp, M->rp, sizeof(int64_t) * (size_t)(M->nr + 1));
+    if (col) memcpy(col, M->col, sizeof(int32_t) * (size_t)nnz);
+    if (val) memcpy(val, M->val, sizeof(double) * (size_t)nnz);
+}
+
+void ora_export_cf(const ohier *H, int l, int8_t *cf, uint8_t *strong, uint8_t *ls_R, uint8_t *ls_P) {
+    const olevel *L = &H->lev[l];
+    int64_t n = L->A.nr;
+    if (cf && L->cf) memcpy(cf, L->cf, (size_t)n);
+    if (strong && L->strong) memcpy(strong, L->strong, (size_t)L->A.rp[n]);
+    if (ls_R && L->ls_R) memcpy(ls_R, L->ls_R, (size_t)L->nc);
+    if (ls_P && L->ls_P) memcpy(ls_P, L->ls_P, (size_t)L->nc);
+}
+
+/* stand-alone steps for the pins */
+void ora_cf_split(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *mask, int mode,
+                  uint64_t seed, int8_t *cf) {
+    ograph S, ST;
+    graph_from_mask(n, rp, col, mask, &S);
+    graph_transpose(&S, &ST);
+    if (mode == 0) cf_rs(&S, &ST, cf); else cf_pmis(&S, &ST, seed, cf);
+    graph_free(&S); graph_free(&ST);
+}
+
+/* transpose of a CSR (used to set up the adjoint system A^T) */
+int64_t ora_transpose(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                      int64_t *trp, int32_t *tcol, double *tval) {
+    ocsr a = {n, n, (int64_t *)rp, (int32_t *)col, (double *)val}, t;
+    csr_transpose(&a, &t);
+    int64_t nnz = t.rp[n];
+    memcpy(trp, t.rp, sizeof(int64_t) * (size_t)(n + 1));
+    memcpy(tcol, t.col, sizeof(int32_t) * (size_t)nnz);
+    memcpy(tval, t.val, sizeof(double) * (size_t)nnz);
+    csr_free(&t);
+    return nnz;
+}
