@@ -1,0 +1,187 @@
+/*
+ * lair.h -- C ABI of the GB300 lAIR library (liblair.so).
+ *
+ * lAIR: algebraic multigrid with local approximate ideal restriction and
+ * F-relaxation (Manteuffel, Ruge, Southworth, "Nonsymmetric algebraic multigrid
+ * based on local approximate ideal restriction (lAIR)"). The library builds a
+ * multigrid hierarchy on one GPU and solves A x = b with V-cycles as the
+ * preconditioner of an FP64 outer iteration.
+ *
+ * Conventions that hold for every call:
+ *  - Matrices are CSR: int64 row pointers, int32 column indices sorted
+ *    ascending within each row, no duplicates, diagonal stored, float64 values.
+ *  - The caller owns every buffer it passes. The library copies what it keeps
+ *    (the matrix) and never retains a caller pointer after a call returns.
+ *  - Vectors may live in host memory (pageable or pinned) or device memory; the
+ *    library checks each pointer and copies host data itself.
+ *  - Device work is ordered on the stream given in lair_options.stream; with
+ *    NULL the handle creates its own blocking stream (ordered with the legacy
+ *    default stream). Calls return after their device work has finished.
+ *  - Failures come back as a lair_status, never as an abort or exception;
+ *    lair_last_error() gives a one-line description.
+ *  - No call is thread-safe with respect to the same handle.
+ */
+#ifndef LAIR_H
+#define LAIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAIR_OK = 0,
+    LAIR_ERR_INVALID_ARG = 1,       /* a NULL pointer, a negative size, an unknown option value */
+    LAIR_ERR_NOT_SQUARE = 2,        /* row pointers inconsistent with n / nnz */
+    LAIR_ERR_UNSORTED_CSR = 3,      /* columns not strictly ascending or out of range */
+    LAIR_ERR_DUPLICATE_ENTRY = 4,
+    LAIR_ERR_ZERO_DIAGONAL = 5,     /* missing or zero diagonal (or singular DG block) */
+    LAIR_ERR_COARSENING_STALLED = 6,/* no coarse points and the level is too large for a direct solve */
+    LAIR_ERR_NOT_CONVERGED = 7,     /* max_iter reached above tol (x holds the last iterate) */
+    LAIR_ERR_NAN = 8,               /* a residual norm became NaN or Inf */
+    LAIR_ERR_OOM = 9,               /* device allocation failed */
+    LAIR_ERR_ARENA_OVERFLOW = 10,   /* a size bound of a fixed device buffer was exceeded */
+    LAIR_ERR_DEVICE_TIMEOUT = 11,   /* a bounded device-side wait gave up */
+    LAIR_ERR_CUDA = 12,             /* any other CUDA runtime error */
+    LAIR_ERR_UNSUPPORTED = 13       /* an input beyond a documented limit */
+} lair_status;
+
+/* C/F splitting: classical Ruge-Stueben first pass, no second pass (Sec. 4);
+ * PMIS (hashed-weight parallel independent set); a user array on level 0;
+ * AUTO = first pass when the level has at most rs_max_n points, PMIS above. */
+typedef enum { LAIR_CF_RS = 0, LAIR_CF_PMIS = 1, LAIR_CF_USER = 2, LAIR_CF_AUTO = 3 } lair_cf_mode;
+
+/* Interpolation P = [W; I] (Eq. (2.2)): approximate ideal interpolation
+ * (W ~ -A_ff^{-1} A_fc, Eq. (2.6), by local solves on the transposed
+ * neighbourhoods) or one-point interpolation (Sec. 4). */
+typedef enum { LAIR_P_LAIP = 0, LAIR_P_ONEPOINT = 1 } lair_interp;
+
+/* Post-relaxation after coarse-grid correction (Sec. 4): Jacobi sweeps over
+ * F, F, C points (the paper's choice), F, C, F, or F, F only. */
+typedef enum { LAIR_RELAX_FFC = 0, LAIR_RELAX_FCF = 1, LAIR_RELAX_FF = 2 } lair_relax;
+
+/* LAIR_FP64: everything in double. LAIR_MIXED: local solves, relaxation, the
+ * cycle's residuals and transfers in float; the outer residual, Krylov
+ * orthogonalisation, Galerkin products, all structural decisions and the
+ * coarsest direct solve stay in double. */
+typedef enum { LAIR_FP64 = 0, LAIR_MIXED = 1 } lair_precision;
+
+/* Outer iteration: stationary (iterative refinement x += M^{-1}(b - A x)) or
+ * right-preconditioned flexible GMRES with restart (Sec. 4: V-cycles as a
+ * GMRES preconditioner). */
+typedef enum { LAIR_CYCLE_STATIONARY = 0, LAIR_CYCLE_FGMRES = 1 } lair_cycle;
+
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *row_ptr;   /* n+1 */
+    const int32_t *col;       /* nnz, ascending per row */
+    const double *val;        /* nnz */
+    int on_device;            /* 1: the three arrays are device pointers */
+} lair_csr;
+
+typedef struct {
+    int cf_mode;              /* lair_cf_mode (default AUTO) */
+    const int8_t *cf_user;    /* LAIR_CF_USER: host array of n entries, 1 = C, 0 = F */
+    int distance;             /* restriction/interpolation neighbourhood distance, 1 or 2 */
+    double theta;             /* strength threshold for the neighbourhoods (Sec. 4, N_i) */
+    double theta_cf;          /* strength threshold for the splitting */
+    int strength_abs;         /* 1: compare |a_ij| instead of -a_ij */
+    int interp;               /* lair_interp */
+    int relax;                /* lair_relax */
+    double lump_tol;          /* lumping threshold theta_D on coarse levels (Sec. 3.3), 0 = off */
+    int lump_level0;          /* 1: lump the finest operator as well */
+    int precision;            /* lair_precision */
+    int coarse_max;           /* direct solve once a level has <= coarse_max unknowns */
+    int max_levels;
+    int block_size;           /* > 1: scale A and b by the inverse block diagonal first (DG, Sec. 4.2.1) */
+    int rs_max_n;             /* AUTO: largest level split by the first pass (<= 32768) */
+    uint64_t pmis_seed;
+    int fgmres_restart;
+    void *stream;             /* cudaStream_t, or NULL (see above); never the legacy default stream itself */
+} lair_options;
+
+typedef struct {
+    int iters;                /* preconditioner applications (V-cycles) */
+    double final_rel;         /* ||b - A x|| / ||b|| of the system solved (scaled one with block_size) */
+    double setup_ms;          /* of the handle (filled by every call that reports) */
+    double solve_ms;
+    int nlevels;
+    int64_t singular_R;       /* local systems that took the least-squares branch */
+    int64_t singular_P;
+    double op_complexity;     /* sum nnz(A_l) / nnz(A_0) */
+    double cycle_complexity;  /* nonzeros touched per cycle / nnz(A_0) */
+    double *hist;             /* optional, caller-owned: residual history */
+    int hist_cap;
+    int hist_len;
+} lair_report;
+
+typedef struct {
+    int64_t n, nnz, nc, nnz_R, nnz_P;
+    int is_coarsest;
+} lair_level_info;
+
+typedef struct lair_handle lair_handle;
+
+/* Fill *o with the defaults (AUTO splitting, distance 1, theta 0.25, lAIP, F-F-C,
+ * lumping 1e-3 on coarse levels, FP64, coarse_max 256, 25 levels, rs_max_n 8192,
+ * FGMRES restart 30). */
+lair_status lair_options_default(lair_options *o);
+
+/* Build the hierarchy for A (Sec. 2.1 set-up: strength, splitting, lAIR
+ * restriction by the local systems of Eq. (3.2), interpolation, Galerkin
+ * product R A P, lumping; recursively). A is copied; *h receives a new handle
+ * that the caller releases with lair_free(). On failure *h may still hold a
+ * handle (for lair_last_error) that must be freed. */
+lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **h);
+
+/* Solve A x = b to ||b - A x||/||b|| <= tol. x holds the initial guess on entry
+ * (host or device, n doubles) and the result on return. cycle is a lair_cycle;
+ * max_iter bounds the V-cycles. rep may be NULL. Returns LAIR_ERR_NOT_CONVERGED
+ * if max_iter is reached first. */
+lair_status lair_solve(lair_handle *h, const double *b, double *x, double tol, int cycle,
+                       int max_iter, lair_report *rep);
+
+/* x = M^{-1} b: one V-cycle with zero initial guess (Sec. 4 cycle), in the
+ * handle's precision. b, x: n doubles, host or device. */
+lair_status lair_precond_apply(lair_handle *h, const double *b, double *x);
+
+/* Adjoint solve A^T lambda = g (for gradients). The first call builds a second
+ * hierarchy on A^T with the same options (C/F splitting of A^T is computed,
+ * never taken from cf_user) and keeps it in the handle. */
+lair_status lair_adjoint(lair_handle *h, const double *g, double *lambda, double tol, int cycle,
+                         int max_iter, lair_report *rep);
+
+/* grad_vals[k] = -lambda[i] * x[j] for every stored entry k = (i, j) of A:
+ * the gradient of a scalar loss through x = A^{-1} b with respect to the
+ * nonzeros of A, given lambda = A^{-T} dL/dx. All three pointers are of the same
+ * kind (host or device); grad_vals has nnz entries. With block scaling the
+ * gradient is with respect to the unscaled A. */
+lair_status lair_grad_A(lair_handle *h, const double *lambda, const double *x, double *grad_vals);
+
+/* Level sizes. out may hold max_levels entries; *nlevels receives the count. */
+lair_status lair_hierarchy_info(const lair_handle *h, lair_level_info *out, int max_levels, int *nlevels);
+
+/* Host copies of one level's CSR (which: 0 = A_l, 1 = R_l, 2 = P_l). Sizes from
+ * lair_hierarchy_info (rows + 1, nnz). Any of the three pointers may be NULL. */
+lair_status lair_export_csr(const lair_handle *h, int level, int which, int64_t *row_ptr,
+                            int32_t *col, double *val);
+
+/* Host copies of one level's splitting (n entries, 1 = C, 0 = F), strength mask
+ * over A_l's pattern (nnz entries), and the per-C-point least-squares flags of
+ * the restriction and interpolation solves (nc entries each). NULL skips. */
+lair_status lair_export_cf(const lair_handle *h, int level, int8_t *cf, uint8_t *strong,
+                           uint8_t *ls_R, uint8_t *ls_P);
+
+/* Number of device kernels the library has launched since the handle was created. */
+int64_t lair_kernel_launches(const lair_handle *h);
+
+void lair_free(lair_handle *h);
+const char *lair_status_string(lair_status s);
+const char *lair_last_error(const lair_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAIR_H */

@@ -1,0 +1,1184 @@
+// lair_api.cu -- host orchestration and the C ABI declared in include/lair.h.
+//
+// Set-up runs level by level on the handle's stream; the host reads back only a few
+// sizes per level (coarse count, pattern sizes, bin counts) to size the next
+// allocations. The V-cycle of each hierarchy is captured once into a CUDA graph and
+// replayed for every preconditioner application; the outer FP64 loop synchronises
+// once per iteration (to read a norm or one Hessenberg column).
+#include <cub/device/device_scan.cuh>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "setup_kernels.cuh"
+
+namespace lair {
+
+void plus_one(int n, const int *a, int *b, cudaStream_t s);
+void count_flags(int n, const uint8_t *f, int *out, cudaStream_t s);
+void normalize_cf(int n, int8_t *cf, cudaStream_t s);
+
+static thread_local long long *g_launches = nullptr;
+void count_launch(int k) {
+    if (g_launches) *g_launches += k;
+}
+
+// ---------------------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------------------
+struct Level {
+    DCsr A;
+    int8_t *cf = nullptr;
+    uint8_t *strong = nullptr;
+    int nc = 0;
+    int *cidx = nullptr;
+    DCsr R, P;
+    uint8_t *lsR = nullptr, *lsP = nullptr;
+    double *dinv = nullptr;
+    float *dinv32 = nullptr;
+    double *b64 = nullptr, *x64[2] = {nullptr, nullptr};
+    float *b32 = nullptr, *x32[2] = {nullptr, nullptr};
+    int xfinal = 0;         // which x buffer holds the cycle's result on this level
+    bool coarsest = false;
+    double *Ainv = nullptr;
+};
+
+struct Hier {
+    std::vector<Level> lev;
+    int bs = 0;
+    double *blk_inv = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_nodes = 0;
+    long long singular_R = 0, singular_P = 0;
+    double setup_ms = 0.0;
+};
+
+}  // namespace lair
+
+struct lair_handle {
+    lair_options o;
+    cudaStream_t s = nullptr;
+    cudaStream_t own = nullptr;   // created when the caller gives no stream
+    lair::DCsr A_in;              // the caller's matrix on the device (unscaled, unlumped)
+    lair::Hier H;
+    lair::Hier *HT = nullptr;     // adjoint hierarchy, built on demand
+    int *status = nullptr;        // device status word
+    int *h_int = nullptr;         // pinned host scratch
+    double *h_dbl = nullptr;
+    void *scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    std::vector<void *> allocs;   // everything owned by the handle
+    // outer-iteration work (FP64)
+    double *wb = nullptr, *wx = nullptr, *wr = nullptr, *part = nullptr, *dsc = nullptr;
+    double *V = nullptr, *Z = nullptr;
+    int fg_m = 0;
+    std::string err;
+    long long launches = 0;
+    int in_setup = 0;
+};
+
+namespace lair {
+
+static lair_status fail(lair_handle *h, lair_status st, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+#define CU(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            if (e_ == cudaErrorMemoryAllocation) return fail(h, LAIR_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return fail(h, LAIR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                   \
+        }                                                                                              \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        lair_status st_ = (expr);          \
+        if (st_ != LAIR_OK) return st_;    \
+    } while (0)
+
+template <class T>
+static lair_status dalloc(lair_handle *h, T **p, size_t n, bool keep = true) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMallocAsync((void **)p, n * sizeof(T), h->s);
+    if (e != cudaSuccess) return fail(h, LAIR_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
+    if (keep) h->allocs.push_back(*p);
+    return LAIR_OK;
+}
+
+static void dfree(lair_handle *h, void *p) {
+    if (p) cudaFreeAsync(p, h->s);
+}
+
+// temporaries of one set-up step
+struct Temps {
+    lair_handle *h;
+    std::vector<void *> ptrs;
+    explicit Temps(lair_handle *hh) : h(hh) {}
+    template <class T> lair_status get(T **p, size_t n) {
+        TRY(dalloc(h, p, n, false));
+        ptrs.push_back(*p);
+        return LAIR_OK;
+    }
+    ~Temps() {
+        for (void *p : ptrs) dfree(h, p);
+    }
+};
+
+static lair_status sync_status(lair_handle *h) {
+    CU(cudaMemcpyAsync(h->h_int, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    int st = h->h_int[0];
+    if (st != 0) {
+        CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
+        return fail(h, (lair_status)st, "device reported %s", lair_status_string((lair_status)st));
+    }
+    return LAIR_OK;
+}
+
+static lair_status read_ints(lair_handle *h, const int *d, int n, int *out) {
+    CU(cudaMemcpyAsync(h->h_int + 1, d, sizeof(int) * n, cudaMemcpyDeviceToHost, h->s));
+    TRY(sync_status(h));
+    memcpy(out, h->h_int + 1, sizeof(int) * n);
+    return LAIR_OK;
+}
+
+// exclusive scan of cnt[0..n) into out[0..n] (out[n] = total); returns the total
+static lair_status scan(lair_handle *h, const int *cnt, int *out, int n, int *total) {
+    // cnt must have n+1 entries with cnt[n] = 0
+    size_t need = 0;
+    CU(cub::DeviceScan::ExclusiveSum(nullptr, need, cnt, out, n + 1, h->s));
+    if (need > h->scan_tmp_bytes) {
+        if (h->scan_tmp) CU(cudaFreeAsync(h->scan_tmp, h->s));
+        CU(cudaMallocAsync(&h->scan_tmp, need, h->s));
+        h->scan_tmp_bytes = need;
+    }
+    CU(cub::DeviceScan::ExclusiveSum(h->scan_tmp, need, cnt, out, n + 1, h->s));
+    count_launch(2);
+    if (total) TRY(read_ints(h, out + n, 1, total));
+    return LAIR_OK;
+}
+
+static lair_status new_counts(lair_handle *h, Temps &t, int **p, int n) {
+    TRY(t.get(p, (size_t)n + 1));
+    CU(cudaMemsetAsync(*p, 0, sizeof(int) * ((size_t)n + 1), h->s));
+    return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// graphs and transposes
+// ---------------------------------------------------------------------------------------
+static lair_status build_strength_graph(lair_handle *h, Temps &t, const DCsr &A, double theta, uint8_t *mask, Graph &G) {
+    int *cnt;
+    TRY(new_counts(h, t, &cnt, A.nr));
+    launch_strength(A, theta, h->o.strength_abs, mask, cnt, h->s);
+    G.n = A.nr;
+    TRY(t.get(&G.rp, (size_t)A.nr + 1));
+    TRY(scan(h, cnt, G.rp, A.nr, &G.nnz));
+    TRY(t.get(&G.col, (size_t)G.nnz));
+    launch_graph_fill(A, mask, G, h->s);
+    return LAIR_OK;
+}
+
+// transpose of an nr x nc CSR (values optional); output rows sorted by column
+static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, const int *rp, const int *col,
+                             const double *val, int **trp, int **tcol, double **tval, bool keep) {
+    int *cnt;
+    TRY(new_counts(h, t, &cnt, nc));
+    launch_col_count(nr, rp, col, cnt, h->s);
+    if (keep) TRY(dalloc(h, trp, (size_t)nc + 1));
+    else TRY(t.get(trp, (size_t)nc + 1));
+    int total = 0;
+    TRY(scan(h, cnt, *trp, nc, nullptr));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)nc + 1), h->s));
+    if (keep) {
+        TRY(dalloc(h, tcol, (size_t)nnz));
+        if (val) TRY(dalloc(h, tval, (size_t)nnz));
+    } else {
+        TRY(t.get(tcol, (size_t)nnz));
+        if (val) TRY(t.get(tval, (size_t)nnz));
+    }
+    launch_transpose_scatter(nr, rp, col, val, *trp, cnt, *tcol, val ? *tval : nullptr, h->s);
+    launch_sort_rows(nc, *trp, *tcol, val ? *tval : nullptr, h->s);
+    (void)total;
+    return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// local solves: neighbourhoods of C points in graph G, systems of matrix B, rows into out
+// ---------------------------------------------------------------------------------------
+static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
+                              const int *brp, const int *bcol, const double *bval, int **out_rp, int **out_col,
+                              double **out_val, float **out_val32, uint8_t *lsflag, long long *singular, bool keep) {
+    const int distance = h->o.distance;
+    int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
+    TRY(new_counts(h, t, &ub, nc));
+    launch_nb_bound(nc, cpts, G, cf, distance, ub, h->s);
+    TRY(t.get(&off, (size_t)nc + 1));
+    int total = 0;
+    TRY(scan(h, ub, off, nc, &total));
+    TRY(t.get(&tmp, (size_t)total));
+    TRY(new_counts(h, t, &cnt, nc));
+    launch_nb_fill(nc, cpts, G, cf, distance, off, tmp, cnt, h->s);
+    TRY(t.get(&nb_rp, (size_t)nc + 1));
+    int nnb = 0;
+    TRY(scan(h, cnt, nb_rp, nc, &nnb));
+    TRY(t.get(&nb_col, (size_t)nnb));
+    launch_nb_compact(nc, off, tmp, nb_rp, nb_col, h->s);
+
+    // output row pointers: nb_rp[c] + c
+    const int nout = nnb + nc;
+    int *orp;
+    if (keep) TRY(dalloc(h, &orp, (size_t)nc + 1)); else TRY(t.get(&orp, (size_t)nc + 1));
+    {
+        int *c2;   // c2[c] = s_c + 1
+        TRY(new_counts(h, t, &c2, nc));
+        plus_one(nc, cnt, c2, h->s);
+        TRY(scan(h, c2, orp, nc, nullptr));
+    }
+    int *ocol;
+    double *oval;
+    float *oval32 = nullptr;
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    if (keep) {
+        TRY(dalloc(h, &ocol, (size_t)nout));
+        TRY(dalloc(h, &oval, (size_t)nout));
+        if (fp32 && out_val32) TRY(dalloc(h, &oval32, (size_t)nout));
+    } else {
+        TRY(t.get(&ocol, (size_t)nout));
+        TRY(t.get(&oval, (size_t)nout));
+    }
+    int *lists, *bcounts, *smax;
+    TRY(t.get(&lists, (size_t)3 * nc + 1));
+    TRY(new_counts(h, t, &bcounts, 4));
+    smax = bcounts + 3;
+    launch_local_bin(nc, nb_rp, lists, bcounts, smax, h->s);
+    int hc[4];
+    TRY(read_ints(h, bcounts, 4, hc));
+    void *scratch = nullptr;
+    if (hc[2] > 0) {
+        unsigned char *sp;
+        TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
+        scratch = sp;
+    }
+    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag};
+    CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
+    if (singular && lsflag) {
+        // count least-squares rows
+        int *c1;
+        TRY(new_counts(h, t, &c1, 1));
+        count_flags(nc, lsflag, c1, h->s);
+        int v = 0;
+        TRY(read_ints(h, c1, 1, &v));
+        *singular += v;
+    }
+    *out_rp = orp;
+    *out_col = ocol;
+    *out_val = oval;
+    if (out_val32) *out_val32 = oval32;
+    return LAIR_OK;
+}
+
+// Z = X Y, canonical accumulation order (see setup_rap.cu)
+static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep) {
+    const int nr = X.nr;
+    int *ub, *off;
+    TRY(new_counts(h, t, &ub, nr));
+    launch_spgemm_ub(nr, X.rp, X.col, Y.rp, ub, h->s);
+    TRY(t.get(&off, (size_t)nr + 1));
+    int total = 0;
+    TRY(scan(h, ub, off, nr, &total));
+    int *tcol, *cnt, *lists, *bc;
+    double *tval;
+    TRY(t.get(&tcol, (size_t)total));
+    TRY(t.get(&tval, (size_t)total));
+    TRY(new_counts(h, t, &cnt, nr));
+    TRY(t.get(&lists, (size_t)2 * nr + 1));
+    TRY(new_counts(h, t, &bc, 3));
+    launch_spgemm_classify(nr, off, lists, bc, bc + 2, h->s);
+    int hc[3];
+    TRY(read_ints(h, bc, 3, hc));
+    int *skeys = nullptr;
+    double *svals = nullptr;
+    if (hc[1] > 0) {
+        size_t cap = spgemm_big_cap(hc[2]);
+        size_t slots = 2 * cap * (size_t)(hc[1] < SPGEMM_CTA_GRID ? hc[1] : SPGEMM_CTA_GRID);
+        TRY(t.get(&skeys, slots));
+        TRY(t.get(&svals, slots));
+    }
+    SpgemmArgs g{X.rp, X.col, X.val, Y.rp, Y.col, Y.val, off, tcol, tval, cnt};
+    CU(launch_spgemm_rows(g, nr, lists, bc, hc, hc[2], skeys, svals, h->s));
+    Z.nr = nr;
+    Z.nc = Y.nc;
+    if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
+    TRY(scan(h, cnt, Z.rp, nr, &Z.nnz));
+    if (keep) {
+        TRY(dalloc(h, &Z.col, (size_t)Z.nnz));
+        TRY(dalloc(h, &Z.val, (size_t)Z.nnz));
+    } else {
+        TRY(t.get(&Z.col, (size_t)Z.nnz));
+        TRY(t.get(&Z.val, (size_t)Z.nnz));
+    }
+    launch_copy_rows(nr, off, tcol, tval, Z, h->s);
+    return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// one coarsening step: level l -> level l+1
+// ---------------------------------------------------------------------------------------
+static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user, bool *last) {
+    Temps t(h);
+    Level &L = H.lev[l];
+    const DCsr &A = L.A;
+    const lair_options &o = h->o;
+    const int n = A.nr;
+    const bool fp32 = o.precision == LAIR_MIXED;
+
+    TRY(dalloc(h, &L.strong, (size_t)A.nnz));
+    Graph S, ST, Scf, STcf;
+    TRY(build_strength_graph(h, t, A, o.theta, L.strong, S));
+    TRY(transpose(h, t, n, n, S.nnz, S.rp, S.col, nullptr, &ST.rp, &ST.col, nullptr, false));
+    ST.n = n;
+    ST.nnz = S.nnz;
+    if (o.theta_cf != o.theta) {
+        uint8_t *m2;
+        TRY(t.get(&m2, (size_t)A.nnz));
+        TRY(build_strength_graph(h, t, A, o.theta_cf, m2, Scf));
+        TRY(transpose(h, t, n, n, Scf.nnz, Scf.rp, Scf.col, nullptr, &STcf.rp, &STcf.col, nullptr, false));
+        STcf.n = n;
+        STcf.nnz = Scf.nnz;
+    } else {
+        Scf = S;
+        STcf = ST;
+    }
+
+    // ---- C/F splitting
+    TRY(dalloc(h, &L.cf, (size_t)n));
+    if (cf_user) {
+        CU(cudaMemcpyAsync(L.cf, cf_user, (size_t)n, cudaMemcpyHostToDevice, h->s));
+        normalize_cf(n, L.cf, h->s);
+    } else {
+        bool use_rs = o.cf_mode == LAIR_CF_RS || (o.cf_mode != LAIR_CF_PMIS && n <= o.rs_max_n);
+        if (use_rs) {
+            if (n > RS_MAX_N)
+                return fail(h, LAIR_ERR_UNSUPPORTED, "first-pass splitting is limited to %d points (level %d has %d)",
+                            RS_MAX_N, l, n);
+            CU(launch_rs(n, Scf, STcf, L.cf, h->status, h->s));
+        } else {
+            double *w;
+            int8_t *newc;
+            int *und;
+            TRY(t.get(&w, (size_t)n));
+            TRY(t.get(&newc, (size_t)n));
+            TRY(new_counts(h, t, &und, 1));
+            launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, L.cf, h->s);
+            for (int round = 0; round <= n; ++round) {
+                CU(cudaMemsetAsync(und, 0, sizeof(int), h->s));
+                launch_pmis_round(n, Scf, STcf, w, L.cf, newc, und, h->s);
+                int u = 0;
+                TRY(read_ints(h, und, 1, &u));
+                if (u == 0) break;
+            }
+        }
+    }
+    TRY(sync_status(h));
+
+    // ---- coarse numbering
+    int *flag, *scanv, *cpts;
+    TRY(new_counts(h, t, &flag, n));
+    launch_cidx(n, L.cf, flag, nullptr, nullptr, 0, h->s);
+    TRY(t.get(&scanv, (size_t)n + 1));
+    int nc = 0;
+    TRY(scan(h, flag, scanv, n, &nc));
+    L.nc = nc;
+    if (nc == 0 || nc == n) {
+        *last = true;
+        return LAIR_OK;
+    }
+    TRY(dalloc(h, &L.cidx, (size_t)n));
+    TRY(t.get(&cpts, (size_t)nc));
+    launch_cidx(n, L.cf, scanv, L.cidx, cpts, 1, h->s);
+
+    // ---- restriction (lAIR): local systems of A on the neighbourhoods in S
+    TRY(dalloc(h, &L.lsR, (size_t)nc));
+    L.R.nr = nc;
+    L.R.nc = n;
+    TRY(local_rows(h, t, nc, cpts, S, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
+                   fp32 ? &L.R.val32 : nullptr, L.lsR, &H.singular_R, true));
+    TRY(read_ints(h, L.R.rp + nc, 1, &L.R.nnz));
+
+    // ---- interpolation
+    L.P.nr = n;
+    L.P.nc = nc;
+    if (o.interp == LAIR_P_ONEPOINT) {
+        int *choice, *cnt;
+        TRY(t.get(&choice, (size_t)n));
+        TRY(new_counts(h, t, &cnt, n));
+        launch_onepoint(0, A, L.strong, L.cf, L.cidx, o.strength_abs, choice, cnt, nullptr, h->s);
+        TRY(dalloc(h, &L.P.rp, (size_t)n + 1));
+        TRY(scan(h, cnt, L.P.rp, n, &L.P.nnz));
+        TRY(dalloc(h, &L.P.col, (size_t)L.P.nnz));
+        TRY(dalloc(h, &L.P.val, (size_t)L.P.nnz));
+        if (fp32) TRY(dalloc(h, &L.P.val32, (size_t)L.P.nnz));
+        launch_onepoint(1, A, L.strong, L.cf, L.cidx, o.strength_abs, choice, cnt, &L.P, h->s);
+    } else {
+        // approximate ideal interpolation = lAIR applied to A^T on the transposed graph, transposed back
+        int *atrp, *atcol;
+        double *atval;
+        TRY(transpose(h, t, n, n, A.nnz, A.rp, A.col, A.val, &atrp, &atcol, &atval, false));
+        TRY(dalloc(h, &L.lsP, (size_t)nc));
+        int *wrp, *wcol;
+        double *wval;
+        TRY(local_rows(h, t, nc, cpts, ST, L.cf, atrp, atcol, atval, &wrp, &wcol, &wval, nullptr, L.lsP,
+                       &H.singular_P, false));
+        int wnnz = 0;
+        TRY(read_ints(h, wrp + nc, 1, &wnnz));
+        TRY(transpose(h, t, nc, n, wnnz, wrp, wcol, wval, &L.P.rp, &L.P.col, &L.P.val, true));
+        L.P.nnz = wnnz;
+        if (fp32) {
+            TRY(dalloc(h, &L.P.val32, (size_t)wnnz));
+            launch_to_f32(wnnz, L.P.val, L.P.val32, h->s);
+        }
+    }
+
+    // ---- Galerkin product and lumping
+    DCsr RA, K;
+    TRY(spgemm(h, t, L.R, A, RA, false));
+    const bool lump = o.lump_tol > 0.0;
+    TRY(spgemm(h, t, RA, L.P, K, !lump));
+    Level next;
+    if (lump) {
+        int *cnt;
+        double *nd;
+        TRY(new_counts(h, t, &cnt, K.nr));
+        TRY(t.get(&nd, (size_t)K.nr));
+        launch_lump(0, K, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
+        DCsr Kl;
+        Kl.nr = Kl.nc = K.nr;
+        TRY(dalloc(h, &Kl.rp, (size_t)K.nr + 1));
+        TRY(scan(h, cnt, Kl.rp, K.nr, &Kl.nnz));
+        TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
+        TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
+        launch_lump(1, K, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
+        next.A = Kl;
+    } else {
+        next.A = K;
+    }
+    TRY(sync_status(h));
+    H.lev.push_back(next);
+    *last = false;
+    return LAIR_OK;
+}
+
+static lair_status finish_level(lair_handle *h, Hier &H, int l) {
+    Level &L = H.lev[l];
+    const int n = L.A.nr;
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    TRY(dalloc(h, &L.dinv, (size_t)n));
+    if (fp32) TRY(dalloc(h, &L.dinv32, (size_t)n));
+    launch_dinv(L.A, L.dinv, L.dinv32, h->status, h->s);
+    if (fp32) {
+        TRY(dalloc(h, &L.A.val32, (size_t)L.A.nnz));
+        launch_to_f32(L.A.nnz, L.A.val, L.A.val32, h->s);
+        TRY(dalloc(h, &L.b32, (size_t)n));
+        TRY(dalloc(h, &L.x32[0], (size_t)n));
+        TRY(dalloc(h, &L.x32[1], (size_t)n));
+    } else {
+        TRY(dalloc(h, &L.b64, (size_t)n));
+        TRY(dalloc(h, &L.x64[0], (size_t)n));
+        TRY(dalloc(h, &L.x64[1], (size_t)n));
+    }
+    return LAIR_OK;
+}
+
+static const int relax_seq[3][3] = {{CF_F, CF_F, CF_C}, {CF_F, CF_C, CF_F}, {CF_F, CF_F, -1}};
+
+template <class T>
+static void record_cycle(lair_handle *h, Hier &H, int l);
+
+template <>
+void record_cycle<double>(lair_handle *h, Hier &H, int l) {
+    Level &L = H.lev[l];
+    if (L.coarsest) {
+        dense_apply<double>(L.A.nr, L.Ainv, L.b64, L.x64[0], h->s);
+        L.xfinal = 0;
+        return;
+    }
+    Level &C = H.lev[l + 1];
+    spmv<double>(L.R, L.b64, C.b64, h->s);
+    record_cycle<double>(h, H, l + 1);
+    spmv<double>(L.P, C.x64[C.xfinal], L.x64[0], h->s);
+    int cur = 0;
+    for (int k = 0; k < 3; ++k) {
+        int tg = relax_seq[h->o.relax][k];
+        if (tg < 0) break;
+        sweep<double>(L.A, L.cf, tg, L.dinv, L.b64, L.x64[cur], L.x64[1 - cur], h->s);
+        cur ^= 1;
+    }
+    L.xfinal = cur;
+}
+
+template <>
+void record_cycle<float>(lair_handle *h, Hier &H, int l) {
+    Level &L = H.lev[l];
+    if (L.coarsest) {
+        dense_apply<float>(L.A.nr, L.Ainv, L.b32, L.x32[0], h->s);
+        L.xfinal = 0;
+        return;
+    }
+    Level &C = H.lev[l + 1];
+    spmv<float>(L.R, L.b32, C.b32, h->s);
+    record_cycle<float>(h, H, l + 1);
+    spmv<float>(L.P, C.x32[C.xfinal], L.x32[0], h->s);
+    int cur = 0;
+    for (int k = 0; k < 3; ++k) {
+        int tg = relax_seq[h->o.relax][k];
+        if (tg < 0) break;
+        sweep<float>(L.A, L.cf, tg, L.dinv32, L.b32, L.x32[cur], L.x32[1 - cur], h->s);
+        cur ^= 1;
+    }
+    L.xfinal = cur;
+}
+
+static lair_status capture_cycle(lair_handle *h, Hier &H) {
+    long long dummy = 0;
+    long long *saved = g_launches;
+    g_launches = &dummy;
+    cudaGraph_t g;
+    CU(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    if (h->o.precision == LAIR_MIXED) record_cycle<float>(h, H, 0);
+    else record_cycle<double>(h, H, 0);
+    cudaError_t e = cudaStreamEndCapture(h->s, &g);
+    g_launches = saved;
+    CU(e);
+    CU(cudaGraphInstantiate(&H.graph, g, 0));
+    size_t nn = 0;
+    CU(cudaGraphGetNodes(g, nullptr, &nn));
+    H.graph_nodes = (int)nn;
+    CU(cudaGraphDestroy(g));
+    return LAIR_OK;
+}
+
+static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, const int8_t *cf_user) {
+    auto t0 = std::chrono::steady_clock::now();
+    const lair_options &o = h->o;
+    H.lev.clear();
+    Level L0;
+    {
+        Temps t(h);
+        DCsr A = A0;
+        if (o.block_size > 1) {
+            const int bs = o.block_size, nblk = A.nr / bs;
+            int *rowcnt;
+            TRY(new_counts(h, t, &rowcnt, A.nr));
+            launch_block_count(nblk, bs, A, rowcnt, h->status, h->s);
+            DCsr B;
+            B.nr = B.nc = A.nr;
+            TRY(dalloc(h, &B.rp, (size_t)A.nr + 1));
+            TRY(scan(h, rowcnt, B.rp, A.nr, &B.nnz));
+            TRY(dalloc(h, &B.col, (size_t)B.nnz));
+            TRY(dalloc(h, &B.val, (size_t)B.nnz));
+            H.bs = bs;
+            TRY(dalloc(h, &H.blk_inv, (size_t)A.nr * bs));
+            launch_block_fill(nblk, bs, A, B, H.blk_inv, h->status, h->s);
+            TRY(sync_status(h));
+            A = B;
+        }
+        if (o.lump_level0 && o.lump_tol > 0.0) {
+            int *cnt;
+            double *nd;
+            TRY(new_counts(h, t, &cnt, A.nr));
+            TRY(t.get(&nd, (size_t)A.nr));
+            launch_lump(0, A, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
+            DCsr Kl;
+            Kl.nr = Kl.nc = A.nr;
+            TRY(dalloc(h, &Kl.rp, (size_t)A.nr + 1));
+            TRY(scan(h, cnt, Kl.rp, A.nr, &Kl.nnz));
+            TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
+            TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
+            launch_lump(1, A, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
+            TRY(sync_status(h));
+            A = Kl;
+        }
+        L0.A = A;
+    }
+    H.lev.push_back(L0);
+    for (int l = 0;; ++l) {
+        const int n = H.lev[l].A.nr;
+        bool last = n <= o.coarse_max || l + 1 >= o.max_levels;
+        if (!last) TRY(coarsen(h, H, l, l == 0 ? cf_user : nullptr, &last));
+        TRY(finish_level(h, H, l));
+        if (last) {
+            Level &L = H.lev[l];
+            L.coarsest = true;
+            if (n > 4096)
+                return fail(h, LAIR_ERR_COARSENING_STALLED, "coarsening stopped at level %d with %d unknowns", l, n);
+            Temps t(h);
+            double *D;
+            int *perm;
+            TRY(t.get(&D, (size_t)n * n));
+            TRY(t.get(&perm, (size_t)n));
+            TRY(dalloc(h, &L.Ainv, (size_t)n * n));
+            launch_dense_setup(L.A, D, perm, L.Ainv, h->status, h->s);
+            TRY(sync_status(h));
+            break;
+        }
+    }
+    TRY(sync_status(h));
+    TRY(capture_cycle(h, H));
+    CU(cudaStreamSynchronize(h->s));
+    H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------------------
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// z = M^{-1} v (one cycle, zero initial guess); v, z: FP64 device vectors of length n0
+static lair_status precond(lair_handle *h, Hier &H, const double *v, double *z) {
+    Level &L = H.lev[0];
+    const int n = L.A.nr;
+    if (h->o.precision == LAIR_MIXED) {
+        d2f(n, v, L.b32, h->s);
+        CU(cudaGraphLaunch(H.graph, h->s));
+        count_launch(H.graph_nodes);
+        f2d(n, L.x32[L.xfinal], z, h->s);
+    } else {
+        CU(cudaMemcpyAsync(L.b64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+        CU(cudaGraphLaunch(H.graph, h->s));
+        count_launch(H.graph_nodes);
+        CU(cudaMemcpyAsync(z, L.x64[L.xfinal], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+    }
+    return LAIR_OK;
+}
+
+static lair_status ensure_work(lair_handle *h, int n, int m) {
+    if (!h->wb) {
+        TRY(dalloc(h, &h->wb, (size_t)n));
+        TRY(dalloc(h, &h->wx, (size_t)n));
+        TRY(dalloc(h, &h->wr, (size_t)n));
+        TRY(dalloc(h, &h->part, (size_t)RED_PARTS * 33));
+        TRY(dalloc(h, &h->dsc, (size_t)256));
+    }
+    if (m > 0 && h->fg_m < m) {
+        TRY(dalloc(h, &h->V, (size_t)n * (m + 1)));
+        TRY(dalloc(h, &h->Z, (size_t)n * m));
+        h->fg_m = m;
+    }
+    return LAIR_OK;
+}
+
+static lair_status norm2_dev(lair_handle *h, int n, const double *v, double *out_dev, double *out_host) {
+    multidot(n, 1, v, n, v, h->part, out_dev, nullptr, h->s);
+    if (out_host) {
+        CU(cudaMemcpyAsync(h->h_dbl, out_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        *out_host = h->h_dbl[0];
+    }
+    return LAIR_OK;
+}
+
+// solve A0 x = b on hierarchy H (device vectors b, x of length n; b already scaled)
+static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int cycle, int max_iter,
+                             lair_report *rep) {
+    Level &L0 = H.lev[0];
+    const DCsr &A = L0.A;
+    const int n = A.nr;
+    const int m = cycle == LAIR_CYCLE_FGMRES ? (h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30) : 0;
+    if (m > 31) return fail(h, LAIR_ERR_INVALID_ARG, "fgmres_restart must be <= 31");
+    TRY(ensure_work(h, n, m));
+    double bn2 = 0.0;
+    TRY(norm2_dev(h, n, b, h->dsc, &bn2));
+    double bn = std::sqrt(bn2);
+    if (bn == 0.0) bn = 1.0;
+    int it = 0, nh = 0;
+    auto hist = [&](double v) {
+        if (rep && rep->hist && nh < rep->hist_cap) rep->hist[nh] = v;
+        ++nh;
+    };
+    const bool mixed = h->o.precision == LAIR_MIXED;
+    double rel = 0.0;
+    lair_status st = LAIR_ERR_NOT_CONVERGED;
+    if (cycle == LAIR_CYCLE_STATIONARY) {
+        for (;;) {
+            // r = b - A x written straight into the cycle's input buffer
+            double *r = mixed ? h->wr : L0.b64;
+            residual(A, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
+            finish_partials(1, h->part, h->dsc, h->s);
+            CU(cudaMemcpyAsync(h->h_dbl, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+            CU(cudaStreamSynchronize(h->s));
+            rel = std::sqrt(h->h_dbl[0]) / bn;
+            hist(rel);
+            if (!std::isfinite(rel)) { st = LAIR_ERR_NAN; break; }
+            if (rel <= tol) { st = LAIR_OK; break; }
+            if (it >= max_iter) break;
+            CU(cudaGraphLaunch(H.graph, h->s));
+            count_launch(H.graph_nodes);
+            if (mixed) axpy_f(n, L0.x32[L0.xfinal], x, h->s);
+            else axpy_d(n, L0.x64[L0.xfinal], x, h->s);
+            ++it;
+        }
+    } else {
+        double *V = h->V, *Z = h->Z;
+        std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hc(m + 2), y(m + 1);
+        double *hsum = h->dsc + 8, *hbuf = h->dsc + 48, *nrm = h->dsc + 1, *ydev = h->dsc + 96;
+        residual(A, b, x, V, nullptr, h->part, h->s);
+        finish_partials(1, h->part, nrm, h->s);
+        CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        double beta = std::sqrt(h->h_dbl[0]);
+        rel = beta / bn;
+        hist(rel);
+        while (std::isfinite(rel) && rel > tol && it < max_iter) {
+            scale_by_norm(n, V, nrm, V, h->s);
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int jdone = 0;
+            for (int j = 0; j < m && it < max_iter; ++j) {
+                double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
+                TRY(precond(h, H, vj, zj));
+                ++it;
+                spmv<double>(A, zj, w, h->s);
+                CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (j + 1), h->s));
+                for (int pass = 0; pass < 2; ++pass) {
+                    multidot(n, j + 1, V, n, w, h->part, hbuf, hsum, h->s);
+                    sub_combo(n, j + 1, V, n, hbuf, w, h->s);
+                }
+                TRY(norm2_dev(h, n, w, nrm, nullptr));
+                scale_by_norm(n, w, nrm, w, h->s);
+                CU(cudaMemcpyAsync(h->h_dbl, hsum, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->s));
+                CU(cudaMemcpyAsync(h->h_dbl + 40, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+                CU(cudaStreamSynchronize(h->s));
+                for (int k = 0; k <= j; ++k) hc[k] = h->h_dbl[k];
+                double hn = std::sqrt(h->h_dbl[40]);
+                hc[j + 1] = hn;
+                for (int k = 0; k < j; ++k) {
+                    double t = cs[k] * hc[k] + sn[k] * hc[k + 1];
+                    hc[k + 1] = -sn[k] * hc[k] + cs[k] * hc[k + 1];
+                    hc[k] = t;
+                }
+                double den = std::sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
+                cs[j] = den > 0.0 ? hc[j] / den : 1.0;
+                sn[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
+                hc[j] = den;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hc[k];
+                double est = std::fabs(g[j + 1]) / bn;
+                hist(est);
+                jdone = j + 1;
+                if (est <= tol || hn == 0.0 || !std::isfinite(est)) break;
+            }
+            for (int k = jdone - 1; k >= 0; --k) {
+                double acc = g[k];
+                for (int c = k + 1; c < jdone; ++c) acc -= Hm[(size_t)k * m + c] * y[c];
+                y[k] = acc / Hm[(size_t)k * m + k];
+            }
+            CU(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->s));
+            add_combo(n, jdone, Z, n, ydev, x, h->s);
+            residual(A, b, x, V, nullptr, h->part, h->s);
+            finish_partials(1, h->part, nrm, h->s);
+            CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+            CU(cudaStreamSynchronize(h->s));
+            beta = std::sqrt(h->h_dbl[0]);
+            rel = beta / bn;
+        }
+        if (!std::isfinite(rel)) st = LAIR_ERR_NAN;
+        else if (rel <= tol) st = LAIR_OK;
+    }
+    CU(cudaStreamSynchronize(h->s));
+    if (rep) {
+        rep->iters = it;
+        rep->final_rel = rel;
+        rep->hist_len = nh < rep->hist_cap ? nh : rep->hist_cap;
+    }
+    if (st == LAIR_ERR_NOT_CONVERGED) fail(h, st, "not converged: relative residual %.3e after %d cycles", rel, it);
+    if (st == LAIR_ERR_NAN) fail(h, st, "residual became NaN/Inf after %d cycles", it);
+    return st;
+}
+
+static void fill_report(lair_handle *h, Hier &H, lair_report *rep) {
+    if (!rep) return;
+    rep->setup_ms = H.setup_ms;
+    rep->nlevels = (int)H.lev.size();
+    rep->singular_R = H.singular_R;
+    rep->singular_P = H.singular_P;
+    double nnz0 = (double)H.lev[0].A.nnz, tot = 0.0, cyc = 0.0;
+    for (auto &L : H.lev) {
+        tot += L.A.nnz;
+        if (!L.coarsest) cyc += 3.0 * L.A.nnz + L.R.nnz + L.P.nnz;
+        else cyc += (double)L.A.nr * L.A.nr;
+    }
+    rep->op_complexity = tot / nnz0;
+    rep->cycle_complexity = cyc / nnz0;
+}
+
+static lair_status run_solve(lair_handle *h, Hier &H, const double *b, double *x, double tol, int cycle, int max_iter,
+                             lair_report *rep, bool scale) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = H.lev[0].A.nr;
+    TRY(ensure_work(h, n, 0));
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    double *db = h->wb, *dx = h->wx;
+    if (bdev) CU(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+    else CU(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+    if (xdev) CU(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+    else CU(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+    if (scale && H.bs > 1) {
+        launch_block_apply(n / H.bs, H.bs, H.blk_inv, db, h->wr, h->s);
+        CU(cudaMemcpyAsync(db, h->wr, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+    }
+    lair_status st = solve_dev(h, H, db, dx, tol, cycle, max_iter, rep);
+    if (st != LAIR_OK && st != LAIR_ERR_NOT_CONVERGED) return st;
+    if (xdev) CU(cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
+    else CU(cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    fill_report(h, H, rep);
+    if (rep) rep->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+// ---------------------------------------------------------------------------------------
+// input: copy and check the caller's CSR
+// ---------------------------------------------------------------------------------------
+__global__ void k_check_csr(int n, long long nnz, const long long *rp64, int *rp, const int *col, const double *val,
+                            int *status, int need_diag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+        long long b = rp64[i];
+        rp[i] = (int)b;
+        if ((i == 0 && b != 0) || (i == n && b != nnz)) set_status(status, LAIR_ERR_NOT_SQUARE);
+        if (i == n || b < 0 || rp64[i + 1] > nnz) continue;
+        long long e = rp64[i + 1];
+        if (e < b) { set_status(status, LAIR_ERR_NOT_SQUARE); continue; }
+        bool diag = false;
+        for (long long k = b; k < e; ++k) {
+            int c = col[k];
+            if (c < 0 || c >= n) { set_status(status, LAIR_ERR_UNSORTED_CSR); break; }
+            if (k > b && col[k - 1] == c) { set_status(status, LAIR_ERR_DUPLICATE_ENTRY); break; }
+            if (k > b && col[k - 1] > c) { set_status(status, LAIR_ERR_UNSORTED_CSR); break; }
+            if (c == i && val[k] != 0.0) diag = true;
+        }
+        if (need_diag && !diag) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+    }
+}
+
+__global__ void k_plus_one(int n, const int *a, int *b) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = a[i] + 1;
+}
+void plus_one(int n, const int *a, int *b, cudaStream_t s) {
+    k_plus_one<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+    count_launch();
+}
+
+__global__ void k_count_flags(int n, const uint8_t *f, int *out) {
+    int c = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) c += f[i] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+void count_flags(int n, const uint8_t *f, int *out, cudaStream_t s) {
+    k_count_flags<<<grid_for(n, 256), 256, 0, s>>>(n, f, out);
+    count_launch();
+}
+
+__global__ void k_normalize_cf(int n, int8_t *cf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) cf[i] = cf[i] ? CF_C : CF_F;
+}
+void normalize_cf(int n, int8_t *cf, cudaStream_t s) {
+    k_normalize_cf<<<grid_for(n, 256), 256, 0, s>>>(n, cf);
+    count_launch();
+}
+
+static lair_status load_matrix(lair_handle *h, const lair_csr *A) {
+    if (A->n <= 0 || A->nnz < A->n || A->n > 0x7fffffff || A->nnz > 0x7fffffff)
+        return fail(h, LAIR_ERR_INVALID_ARG, "matrix sizes n=%lld nnz=%lld out of range", (long long)A->n,
+                    (long long)A->nnz);
+    if (!A->row_ptr || !A->col || !A->val) return fail(h, LAIR_ERR_INVALID_ARG, "NULL matrix array");
+    const int n = (int)A->n, nnz = (int)A->nnz;
+    DCsr &M = h->A_in;
+    M.nr = M.nc = n;
+    M.nnz = nnz;
+    TRY(dalloc(h, &M.rp, (size_t)n + 1));
+    TRY(dalloc(h, &M.col, (size_t)nnz));
+    TRY(dalloc(h, &M.val, (size_t)nnz));
+    long long *rp64;
+    TRY(dalloc(h, &rp64, (size_t)n + 1, false));
+    cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (!A->on_device) {
+        if (A->row_ptr[0] != 0 || A->row_ptr[n] != A->nnz) {
+            dfree(h, rp64);
+            return fail(h, LAIR_ERR_NOT_SQUARE, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+        }
+    }
+    CU(cudaMemcpyAsync(rp64, A->row_ptr, sizeof(long long) * ((size_t)n + 1), kind, h->s));
+    CU(cudaMemcpyAsync(M.col, A->col, sizeof(int) * (size_t)nnz, kind, h->s));
+    CU(cudaMemcpyAsync(M.val, A->val, sizeof(double) * (size_t)nnz, kind, h->s));
+    k_check_csr<<<grid_for((long long)n + 1, 256), 256, 0, h->s>>>(n, (long long)nnz, rp64, M.rp, M.col, M.val, h->status,
+                                                                    h->o.block_size > 1 ? 0 : 1);
+    count_launch();
+    dfree(h, rp64);
+    TRY(sync_status(h));
+    return LAIR_OK;
+}
+
+}  // namespace lair
+
+// =======================================================================================
+// C ABI
+// =======================================================================================
+using namespace lair;
+
+namespace {
+struct LaunchScope {
+    long long *saved;
+    explicit LaunchScope(lair_handle *h) : saved(g_launches) { g_launches = h ? &h->launches : nullptr; }
+    ~LaunchScope() { g_launches = saved; }
+};
+}  // namespace
+
+extern "C" {
+
+const char *lair_status_string(lair_status s) {
+    switch (s) {
+        case LAIR_OK: return "LAIR_OK";
+        case LAIR_ERR_INVALID_ARG: return "LAIR_ERR_INVALID_ARG";
+        case LAIR_ERR_NOT_SQUARE: return "LAIR_ERR_NOT_SQUARE";
+        case LAIR_ERR_UNSORTED_CSR: return "LAIR_ERR_UNSORTED_CSR";
+        case LAIR_ERR_DUPLICATE_ENTRY: return "LAIR_ERR_DUPLICATE_ENTRY";
+        case LAIR_ERR_ZERO_DIAGONAL: return "LAIR_ERR_ZERO_DIAGONAL";
+        case LAIR_ERR_COARSENING_STALLED: return "LAIR_ERR_COARSENING_STALLED";
+        case LAIR_ERR_NOT_CONVERGED: return "LAIR_ERR_NOT_CONVERGED";
+        case LAIR_ERR_NAN: return "LAIR_ERR_NAN";
+        case LAIR_ERR_OOM: return "LAIR_ERR_OOM";
+        case LAIR_ERR_ARENA_OVERFLOW: return "LAIR_ERR_ARENA_OVERFLOW";
+        case LAIR_ERR_DEVICE_TIMEOUT: return "LAIR_ERR_DEVICE_TIMEOUT";
+        case LAIR_ERR_CUDA: return "LAIR_ERR_CUDA";
+        case LAIR_ERR_UNSUPPORTED: return "LAIR_ERR_UNSUPPORTED";
+    }
+    return "LAIR_UNKNOWN_STATUS";
+}
+
+const char *lair_last_error(const lair_handle *h) { return h ? h->err.c_str() : "no handle"; }
+
+int64_t lair_kernel_launches(const lair_handle *h) { return h ? h->launches : 0; }
+
+lair_status lair_options_default(lair_options *o) {
+    if (!o) return LAIR_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->cf_mode = LAIR_CF_AUTO;
+    o->distance = 1;
+    o->theta = 0.25;
+    o->theta_cf = 0.25;
+    o->interp = LAIR_P_LAIP;
+    o->relax = LAIR_RELAX_FFC;
+    o->lump_tol = 1e-3;
+    o->precision = LAIR_FP64;
+    o->coarse_max = 256;
+    o->max_levels = 25;
+    o->rs_max_n = 8192;
+    o->pmis_seed = 0x5eedULL;
+    o->fgmres_restart = 30;
+    return LAIR_OK;
+}
+
+static lair_status check_options(lair_handle *h, const lair_options *o) {
+    if (o->cf_mode < 0 || o->cf_mode > 3) return fail(h, LAIR_ERR_INVALID_ARG, "cf_mode %d", o->cf_mode);
+    if (o->cf_mode == LAIR_CF_USER && !o->cf_user) return fail(h, LAIR_ERR_INVALID_ARG, "cf_user is NULL");
+    if (o->distance < 1 || o->distance > 2) return fail(h, LAIR_ERR_INVALID_ARG, "distance must be 1 or 2");
+    if (o->interp < 0 || o->interp > 1) return fail(h, LAIR_ERR_INVALID_ARG, "interp %d", o->interp);
+    if (o->relax < 0 || o->relax > 2) return fail(h, LAIR_ERR_INVALID_ARG, "relax %d", o->relax);
+    if (o->precision < 0 || o->precision > 1) return fail(h, LAIR_ERR_INVALID_ARG, "precision %d", o->precision);
+    if (o->coarse_max < 1 || o->coarse_max > 4096) return fail(h, LAIR_ERR_INVALID_ARG, "coarse_max in [1, 4096]");
+    if (o->max_levels < 1) return fail(h, LAIR_ERR_INVALID_ARG, "max_levels >= 1");
+    if (o->rs_max_n < 0 || o->rs_max_n > RS_MAX_N) return fail(h, LAIR_ERR_INVALID_ARG, "rs_max_n in [0, %d]", RS_MAX_N);
+    if (o->block_size > 8) return fail(h, LAIR_ERR_UNSUPPORTED, "block_size <= 8");
+    if (o->fgmres_restart < 0 || o->fgmres_restart > 31) return fail(h, LAIR_ERR_INVALID_ARG, "fgmres_restart in [1, 31]");
+    if (!(o->theta >= 0.0) || !(o->theta_cf >= 0.0) || !(o->lump_tol >= 0.0))
+        return fail(h, LAIR_ERR_INVALID_ARG, "thresholds must be >= 0");
+    return LAIR_OK;
+}
+
+lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **out) {
+    if (!A || !out) return LAIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    lair_handle *h = new lair_handle();
+    *out = h;
+    LaunchScope ls(h);
+    if (o) h->o = *o;
+    else lair_options_default(&h->o);
+    TRY(check_options(h, &h->o));
+    if (h->o.block_size > 1 && A->n % h->o.block_size)
+        return fail(h, LAIR_ERR_INVALID_ARG, "n is not a multiple of block_size");
+    h->s = (cudaStream_t)h->o.stream;
+    if (!h->s) {
+        // a blocking stream: ordered with the legacy default stream, and capturable into graphs
+        CU(cudaStreamCreate(&h->own));
+        h->s = h->own;
+    }
+    CU(cudaMallocHost(&h->h_int, 64 * sizeof(int)));
+    CU(cudaMallocHost(&h->h_dbl, 64 * sizeof(double)));
+    TRY(dalloc(h, &h->status, 1));
+    CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
+    TRY(load_matrix(h, A));
+    const int8_t *cfu = h->o.cf_mode == LAIR_CF_USER ? h->o.cf_user : nullptr;
+    TRY(build_hierarchy(h, h->H, h->A_in, cfu));
+    h->o.cf_user = nullptr;   // never retained
+    return LAIR_OK;
+}
+
+lair_status lair_solve(lair_handle *h, const double *b, double *x, double tol, int cycle, int max_iter,
+                       lair_report *rep) {
+    if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || cycle < 0 || cycle > 1) return LAIR_ERR_INVALID_ARG;
+    if (h->H.lev.empty()) return fail(h, LAIR_ERR_INVALID_ARG, "handle has no hierarchy");
+    LaunchScope ls(h);
+    return run_solve(h, h->H, b, x, tol, cycle, max_iter, rep, true);
+}
+
+lair_status lair_precond_apply(lair_handle *h, const double *b, double *x) {
+    if (!h || !b || !x) return LAIR_ERR_INVALID_ARG;
+    if (h->H.lev.empty()) return fail(h, LAIR_ERR_INVALID_ARG, "handle has no hierarchy");
+    LaunchScope ls(h);
+    const int n = h->H.lev[0].A.nr;
+    TRY(ensure_work(h, n, 0));
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    CU(cudaMemcpyAsync(h->wb, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    TRY(precond(h, h->H, h->wb, h->wx));
+    CU(cudaMemcpyAsync(x, h->wx, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return LAIR_OK;
+}
+
+lair_status lair_adjoint(lair_handle *h, const double *g, double *lambda, double tol, int cycle, int max_iter,
+                         lair_report *rep) {
+    if (!h || !g || !lambda || !(tol >= 0.0) || max_iter < 0 || cycle < 0 || cycle > 1) return LAIR_ERR_INVALID_ARG;
+    if (h->o.block_size > 1) return fail(h, LAIR_ERR_UNSUPPORTED, "adjoint with block scaling is not supported");
+    LaunchScope ls(h);
+    if (!h->HT) {
+        h->HT = new Hier();
+        Temps t(h);
+        DCsr AT;
+        AT.nr = AT.nc = h->A_in.nr;
+        AT.nnz = h->A_in.nnz;
+        TRY(transpose(h, t, AT.nr, AT.nc, AT.nnz, h->A_in.rp, h->A_in.col, h->A_in.val, &AT.rp, &AT.col, &AT.val, true));
+        lair_options save = h->o;
+        if (h->o.cf_mode == LAIR_CF_USER) h->o.cf_mode = LAIR_CF_AUTO;
+        lair_status st = build_hierarchy(h, *h->HT, AT, nullptr);
+        h->o = save;
+        if (st != LAIR_OK) {
+            delete h->HT;
+            h->HT = nullptr;
+            return st;
+        }
+    }
+    return run_solve(h, *h->HT, g, lambda, tol, cycle, max_iter, rep, false);
+}
+
+lair_status lair_grad_A(lair_handle *h, const double *lambda, const double *x, double *grad) {
+    if (!h || !lambda || !x || !grad) return LAIR_ERR_INVALID_ARG;
+    LaunchScope ls(h);
+    const DCsr &A = h->A_in;
+    const bool dev = is_device_ptr(grad);
+    if (dev) {
+        grad_A(A, lambda, x, grad, h->s);
+    } else {
+        TRY(ensure_work(h, A.nr, 0));
+        double *g;
+        TRY(dalloc(h, &g, (size_t)A.nnz, false));
+        CU(cudaMemcpyAsync(h->wb, lambda, sizeof(double) * A.nr, cudaMemcpyHostToDevice, h->s));
+        CU(cudaMemcpyAsync(h->wx, x, sizeof(double) * A.nr, cudaMemcpyHostToDevice, h->s));
+        grad_A(A, h->wb, h->wx, g, h->s);
+        CU(cudaMemcpyAsync(grad, g, sizeof(double) * A.nnz, cudaMemcpyDeviceToHost, h->s));
+        dfree(h, g);
+    }
+    CU(cudaStreamSynchronize(h->s));
+    return LAIR_OK;
+}
+
+lair_status lair_hierarchy_info(const lair_handle *h, lair_level_info *out, int max_levels, int *nlevels) {
+    if (!h || !nlevels) return LAIR_ERR_INVALID_ARG;
+    *nlevels = (int)h->H.lev.size();
+    for (int l = 0; l < *nlevels && l < max_levels && out; ++l) {
+        const Level &L = h->H.lev[l];
+        out[l].n = L.A.nr;
+        out[l].nnz = L.A.nnz;
+        out[l].nc = L.coarsest ? 0 : L.nc;
+        out[l].nnz_R = L.coarsest ? 0 : L.R.nnz;
+        out[l].nnz_P = L.coarsest ? 0 : L.P.nnz;
+        out[l].is_coarsest = L.coarsest ? 1 : 0;
+    }
+    return LAIR_OK;
+}
+
+lair_status lair_export_csr(const lair_handle *hc, int level, int which, int64_t *row_ptr, int32_t *col, double *val) {
+    lair_handle *h = const_cast<lair_handle *>(hc);
+    if (!h || level < 0 || level >= (int)h->H.lev.size() || which < 0 || which > 2) return LAIR_ERR_INVALID_ARG;
+    const Level &L = h->H.lev[level];
+    const DCsr &M = which == 0 ? L.A : (which == 1 ? L.R : L.P);
+    if (which > 0 && L.coarsest) return fail(h, LAIR_ERR_INVALID_ARG, "coarsest level has no transfer operators");
+    if (row_ptr) {
+        std::vector<int> rp(M.nr + 1);
+        CU(cudaMemcpyAsync(rp.data(), M.rp, sizeof(int) * (M.nr + 1), cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        for (int i = 0; i <= M.nr; ++i) row_ptr[i] = rp[i];
+    }
+    if (col) CU(cudaMemcpyAsync(col, M.col, sizeof(int) * M.nnz, cudaMemcpyDeviceToHost, h->s));
+    if (val) CU(cudaMemcpyAsync(val, M.val, sizeof(double) * M.nnz, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return LAIR_OK;
+}
+
+lair_status lair_export_cf(const lair_handle *hc, int level, int8_t *cf, uint8_t *strong, uint8_t *ls_R, uint8_t *ls_P) {
+    lair_handle *h = const_cast<lair_handle *>(hc);
+    if (!h || level < 0 || level >= (int)h->H.lev.size()) return LAIR_ERR_INVALID_ARG;
+    const Level &L = h->H.lev[level];
+    if (L.coarsest) return fail(h, LAIR_ERR_INVALID_ARG, "coarsest level has no splitting");
+    if (cf) CU(cudaMemcpyAsync(cf, L.cf, L.A.nr, cudaMemcpyDeviceToHost, h->s));
+    if (strong) CU(cudaMemcpyAsync(strong, L.strong, L.A.nnz, cudaMemcpyDeviceToHost, h->s));
+    if (ls_R && L.lsR) CU(cudaMemcpyAsync(ls_R, L.lsR, L.nc, cudaMemcpyDeviceToHost, h->s));
+    if (ls_P && L.lsP) CU(cudaMemcpyAsync(ls_P, L.lsP, L.nc, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return LAIR_OK;
+}
+
+void lair_free(lair_handle *h) {
+    if (!h) return;
+    if (h->H.graph) cudaGraphExecDestroy(h->H.graph);
+    if (h->HT) {
+        if (h->HT->graph) cudaGraphExecDestroy(h->HT->graph);
+        delete h->HT;
+    }
+    for (void *p : h->allocs) cudaFreeAsync(p, h->s);
+    if (h->scan_tmp) cudaFreeAsync(h->scan_tmp, h->s);
+    cudaStreamSynchronize(h->s);
+    if (h->own) cudaStreamDestroy(h->own);
+    if (h->h_int) cudaFreeHost(h->h_int);
+    if (h->h_dbl) cudaFreeHost(h->h_dbl);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

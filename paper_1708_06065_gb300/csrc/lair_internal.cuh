@@ -1,0 +1,73 @@
+// lair_internal.cuh -- shared device/host definitions of the lAIR CUDA library.
+//
+// Conventions
+//  * Device CSR matrices use int32 row pointers and column indices (sizes are
+//    checked against 2^31 - 1 on the host) and keep an FP64 value array plus,
+//    in mixed precision, an FP32 copy used by the cycle.
+//  * Every floating-point operation whose result feeds a structural decision on
+//    a coarser level (strength, splitting, lumping) is written with explicit
+//    __fma_rn / __dmul_rn / __dadd_rn / IEEE division, in the order documented at
+//    each routine, so that the hierarchy is a deterministic function of A.
+//  * Kernels report failures through a device status word (atomicCAS of a
+//    lair_status code), read by the host at its synchronisation points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lair.h"
+
+namespace lair {
+
+constexpr int8_t CF_F = 0;
+constexpr int8_t CF_C = 1;
+constexpr int8_t CF_U = -1;
+
+struct DCsr {
+    int nr = 0, nc = 0, nnz = 0;
+    int *rp = nullptr;
+    int *col = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;
+};
+
+struct Graph {          // pattern-only CSR
+    int n = 0, nnz = 0;
+    int *rp = nullptr;
+    int *col = nullptr;
+};
+
+// -------------------------------------------------------------------------------------
+// error reporting from device code
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int *st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// -------------------------------------------------------------------------------------
+// warp helpers
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// -------------------------------------------------------------------------------------
+// host-side launch helpers (defined in lair_api.cu)
+// -------------------------------------------------------------------------------------
+void count_launch(int k = 1);
+inline int grid_for(long long work, int block, int max_blocks = 152 * 32) {
+    long long g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+// exclusive scan of n ints (out may alias in); returns the total through *total_dev (device int) if given
+cudaError_t scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s, void *&tmp,
+                           size_t &tmp_bytes);
+
+}  // namespace lair

@@ -1,0 +1,440 @@
+// setup_graph.cu -- strength of connection, strength graphs, C/F splitting,
+// coarse numbering and restriction neighbourhoods (the integer part of the
+// lAIR set-up, Sec. 3.1 and Sec. 4).
+#include "setup_kernels.cuh"
+
+namespace lair {
+
+// -------------------------------------------------------------------------------------
+// Strength of connection (Sec. 4): j in N_i iff j != i and
+//   -a_ij >= theta * m_i (signed) or |a_ij| >= theta * m_i (abs), m_i = max_{k!=i} |a_ik|.
+// m_i = 0 gives no strong connections; a stored zero is never strong. theta*m_i is one
+// rounded multiply. One thread per row (rows are short on every level we build).
+// -------------------------------------------------------------------------------------
+__global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                           const double *__restrict__ val, double theta, int absmode,
+                           uint8_t *__restrict__ mask, int *__restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int b = rp[i], e = rp[i + 1];
+        double m = 0.0;
+        for (int k = b; k < e; ++k)
+            if (col[k] != i && fabs(val[k]) > m) m = fabs(val[k]);
+        double thr = __dmul_rn(theta, m);
+        int c = 0;
+        for (int k = b; k < e; ++k) {
+            double a = val[k];
+            int s = 0;
+            if (col[k] != i && m > 0.0 && a != 0.0) s = absmode ? (fabs(a) >= thr) : (-a >= thr);
+            mask[k] = (uint8_t)s;
+            c += s;
+        }
+        cnt[i] = c;
+    }
+}
+
+__global__ void k_graph_fill(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                             const uint8_t *__restrict__ mask, const int *__restrict__ grp,
+                             int *__restrict__ gcol) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p = grp[i];
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (mask[k]) gcol[p++] = col[k];
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// Transposes (pattern, or pattern + values): count, scan, scatter with atomic cursors,
+// then an insertion sort per output row so that the result is deterministic.
+// -------------------------------------------------------------------------------------
+__global__ void k_col_count(int nr, const int *__restrict__ rp, const int *__restrict__ col, int *__restrict__ cnt) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(&cnt[col[k]], 1);
+}
+
+__global__ void k_transpose_scatter(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                    const double *__restrict__ val, const int *__restrict__ trp,
+                                    int *__restrict__ cursor, int *__restrict__ tcol, double *__restrict__ tval) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int j = col[k];
+            int d = trp[j] + atomicAdd(&cursor[j], 1);
+            tcol[d] = i;
+            if (val) tval[d] = val[k];
+        }
+}
+
+__global__ void k_sort_rows(int nr, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        int b = rp[i], e = rp[i + 1];
+        for (int k = b + 1; k < e; ++k) {
+            int c = col[k];
+            double v = val ? val[k] : 0.0;
+            int m = k - 1;
+            while (m >= b && col[m] > c) {
+                col[m + 1] = col[m];
+                if (val) val[m + 1] = val[m];
+                --m;
+            }
+            col[m + 1] = c;
+            if (val) val[m + 1] = v;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// PMIS: w_i = |ST_i| + u_i with u_i = (splitmix64((seed << 32) ^ i) >> 11) * 2^-53
+// (splitmix64 is Vigna's published mixer). |ST_i| = 0 -> F. Rounds: every undecided i
+// whose (w_i, -i) beats every undecided neighbour in S_i u ST_i becomes C; then the
+// undecided points of ST_i of each new C point i become F.
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_pmis_init(int n, const int *__restrict__ st_rp, uint64_t seed, double *__restrict__ w,
+                            int8_t *__restrict__ cf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int lam = st_rp[i + 1] - st_rp[i];
+        double u = __dmul_rn(__ull2double_rn(splitmix64((seed << 32) ^ (uint64_t)i) >> 11), 0x1.0p-53);
+        w[i] = __dadd_rn((double)lam, u);
+        cf[i] = lam == 0 ? CF_F : CF_U;
+    }
+}
+
+__device__ __forceinline__ bool beats(double wi, int i, double wj, int j) {
+    return (wi > wj) || (wi == wj && i < j);
+}
+
+__global__ void k_pmis_select(int n, Graph S, Graph ST, const double *__restrict__ w, const int8_t *__restrict__ cf,
+                              int8_t *__restrict__ newc, int *__restrict__ undecided) {
+    int local = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int8_t nc = 0;
+        if (cf[i] == CF_U) {
+            ++local;
+            double wi = w[i];
+            bool best = true;
+            for (int p = S.rp[i]; p < S.rp[i + 1] && best; ++p) {
+                int j = S.col[p];
+                if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
+            }
+            for (int p = ST.rp[i]; p < ST.rp[i + 1] && best; ++p) {
+                int j = ST.col[p];
+                if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
+            }
+            nc = best;
+        }
+        newc[i] = nc;
+    }
+    local = __reduce_add_sync(0xffffffffu, local);
+    if (lane_id() == 0 && local) atomicAdd(undecided, local);
+}
+
+// new C points never lie in ST of another new C point (they would beat each other), so
+// setting C and F in one pass is race-free.
+__global__ void k_pmis_mark(int n, Graph ST, const int8_t *__restrict__ newc, int8_t *__restrict__ cf) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!newc[i]) continue;
+        cf[i] = CF_C;
+        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) {
+            int j = ST.col[p];
+            if (cf[j] == CF_U) cf[j] = CF_F;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// Classical first pass (Sec. 4, no second pass), one warp, everything in shared memory.
+// lambda_i = |ST_i|; points with S_i and ST_i empty start as F. Each step takes the
+// undecided point with the largest lambda (ties: smallest index) as C; its undecided
+// dependants ST_i become F; each undecided k in S_j of a new F point j gets lambda += 1;
+// each undecided k in S_i gets lambda -= 1.
+// Keys pack (lambda + 1) << 16 | (0xFFFF - i) (0 = decided), so the largest key is the
+// point to take. A 32-ary max tree (leaves, level 1 = max of 32 leaves, level 2 = max of
+// 32 level-1 nodes, at most 32 of them) finds it in three warp reductions.
+// -------------------------------------------------------------------------------------
+constexpr int RS_LIST = 2048;
+constexpr int8_t CF_NEWF = 2;   // F point created in the current step
+
+__device__ __forceinline__ unsigned warp_max_u32(unsigned v) { return __reduce_max_sync(0xffffffffu, v); }
+
+__device__ void rs_rebuild(int n, int n1, const unsigned *key, unsigned *l1, unsigned *l2, unsigned lane) {
+    for (int g = lane; g < n1; g += 32) {
+        unsigned m = 0;
+        for (int t = 0; t < 32 && 32 * g + t < n; ++t) m = max(m, key[32 * g + t]);
+        l1[g] = m;
+    }
+    __syncwarp();
+    {
+        unsigned m = 0;
+        for (int t = 0; t < 32 && 32 * (int)lane + t < n1; ++t) m = max(m, l1[32 * lane + t]);
+        l2[lane] = m;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_rs_split(int n, Graph S, Graph ST, int8_t *__restrict__ cf_out, int *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned *key = reinterpret_cast<unsigned *>(smem);
+    const int n1 = (n + 31) / 32;
+    unsigned *l1 = key + n;
+    unsigned *l2 = l1 + n1;
+    int *list = reinterpret_cast<int *>(l2 + 32);      // leaves changed in the current step
+    int8_t *cf = reinterpret_cast<int8_t *>(list + RS_LIST);
+    __shared__ int nlist;
+    const unsigned lane = threadIdx.x;
+
+    for (int i = lane; i < n; i += 32) {
+        int lam = ST.rp[i + 1] - ST.rp[i];
+        bool iso = (S.rp[i + 1] == S.rp[i]) && lam == 0;
+        cf[i] = iso ? CF_F : CF_U;
+        key[i] = iso ? 0u : (((unsigned)(lam + 1)) << 16) | (0xFFFFu - (unsigned)i);
+    }
+    __syncwarp();
+    rs_rebuild(n, n1, key, l1, l2, lane);
+
+    for (long long step = 0; step <= (long long)n; ++step) {
+        unsigned v = l2[lane];
+        const unsigned best = warp_max_u32(v);
+        if (best == 0u) break;
+        const int h = __ffs(__ballot_sync(0xffffffffu, v == best)) - 1;
+        int g1 = 32 * h + (int)lane;
+        v = g1 < n1 ? l1[g1] : 0u;
+        const int g = 32 * h + __ffs(__ballot_sync(0xffffffffu, v == best)) - 1;
+        int leaf = 32 * g + (int)lane;
+        v = leaf < n ? key[leaf] : 0u;
+        const int i = 32 * g + __ffs(__ballot_sync(0xffffffffu, v == best)) - 1;
+        if (lane == 0) {
+            cf[i] = CF_C;
+            key[i] = 0u;
+            list[0] = i;
+            nlist = 1;
+        }
+        __syncwarp();
+        // undecided dependants of i become F (marked as new for this step)
+        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
+            int j = ST.col[p];
+            if (cf[j] == CF_U) {
+                cf[j] = CF_NEWF;
+                key[j] = 0u;
+                int t = atomicAdd(&nlist, 1);
+                if (t < RS_LIST) list[t] = j;
+            }
+        }
+        __syncwarp();
+        // lambda_k += 1 for undecided k in S_j of every new F point j
+        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
+            int j = ST.col[p];
+            if (cf[j] != CF_NEWF) continue;
+            for (int q = S.rp[j]; q < S.rp[j + 1]; ++q) {
+                int k = S.col[q];
+                if (cf[k] == CF_U) {
+                    atomicAdd(&key[k], 1u << 16);
+                    int t = atomicAdd(&nlist, 1);
+                    if (t < RS_LIST) list[t] = k;
+                }
+            }
+        }
+        // lambda_k -= 1 for undecided k in S_i
+        for (int q = S.rp[i] + lane; q < S.rp[i + 1]; q += 32) {
+            int k = S.col[q];
+            if (cf[k] == CF_U) {
+                atomicSub(&key[k], 1u << 16);
+                int t = atomicAdd(&nlist, 1);
+                if (t < RS_LIST) list[t] = k;
+            }
+        }
+        __syncwarp();
+        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
+            int j = ST.col[p];
+            if (cf[j] == CF_NEWF) cf[j] = CF_F;
+        }
+        const int nl = nlist;
+        __syncwarp();
+        if (nl > RS_LIST) {
+            rs_rebuild(n, n1, key, l1, l2, lane);
+            continue;
+        }
+        // recompute the level-1 nodes of changed leaves (duplicates write identical values)
+        for (int t = lane; t < nl; t += 32) {
+            int gg = list[t] >> 5;
+            unsigned m = 0;
+            for (int u = 0; u < 32 && 32 * gg + u < n; ++u) m = max(m, key[32 * gg + u]);
+            l1[gg] = m;
+        }
+        __syncwarp();
+        for (int t = lane; t < nl; t += 32) {
+            int hh = list[t] >> 10;
+            unsigned m = 0;
+            for (int u = 0; u < 32 && 32 * hh + u < n1; ++u) m = max(m, l1[32 * hh + u]);
+            l2[hh] = m;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) {
+        int8_t c = cf[i];
+        if (c != CF_C && c != CF_F) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+        cf_out[i] = c;
+    }
+}
+
+size_t rs_smem_bytes(int n) {
+    int n1 = (n + 31) / 32;
+    return sizeof(unsigned) * ((size_t)n + n1 + 32) + sizeof(int) * RS_LIST + (size_t)n + 16;
+}
+
+// -------------------------------------------------------------------------------------
+// coarse numbering
+// -------------------------------------------------------------------------------------
+__global__ void k_cflag(int n, const int8_t *__restrict__ cf, int *__restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flag[i] = cf[i] == CF_C;
+}
+
+__global__ void k_cidx(int n, const int8_t *__restrict__ cf, const int *__restrict__ scan, int *__restrict__ cidx,
+                       int *__restrict__ cpts) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (cf[i] == CF_C) {
+            cidx[i] = scan[i];
+            cpts[scan[i]] = i;
+        } else {
+            cidx[i] = -1;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// Neighbourhoods (Sec. 3.1; F-F-C only for distance two, Sec. 4). For C point i in graph G:
+// distance 1: G_i n F; distance 2 adds G_j n F for each j in G_i n F. Sorted, unique.
+// -------------------------------------------------------------------------------------
+__global__ void k_nb_bound(int nc, const int *__restrict__ cpts, Graph G, const int8_t *__restrict__ cf,
+                           int distance, int *__restrict__ ub) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int i = cpts[c];
+        int u = 0;
+        for (int p = G.rp[i]; p < G.rp[i + 1]; ++p) {
+            int j = G.col[p];
+            if (cf[j] != CF_F) continue;
+            u += 1;
+            if (distance >= 2) u += G.rp[j + 1] - G.rp[j];
+        }
+        ub[c] = u;
+    }
+}
+
+__global__ void k_nb_fill(int nc, const int *__restrict__ cpts, Graph G, const int8_t *__restrict__ cf,
+                          int distance, const int *__restrict__ off, int *__restrict__ tmp, int *__restrict__ cnt) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int i = cpts[c];
+        int *t = tmp + off[c];
+        int m = 0;
+        for (int p = G.rp[i]; p < G.rp[i + 1]; ++p) {
+            int j = G.col[p];
+            if (cf[j] != CF_F) continue;
+            t[m++] = j;
+            if (distance >= 2)
+                for (int q = G.rp[j]; q < G.rp[j + 1]; ++q) {
+                    int k = G.col[q];
+                    if (cf[k] == CF_F && k != i) t[m++] = k;
+                }
+        }
+        // insertion sort + unique
+        for (int a = 1; a < m; ++a) {
+            int v = t[a], b = a - 1;
+            while (b >= 0 && t[b] > v) { t[b + 1] = t[b]; --b; }
+            t[b + 1] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < m; ++a)
+            if (u == 0 || t[u - 1] != t[a]) t[u++] = t[a];
+        cnt[c] = u;
+    }
+}
+
+__global__ void k_nb_compact(int nc, const int *__restrict__ off, const int *__restrict__ tmp,
+                             const int *__restrict__ nb_rp, int *__restrict__ nb_col) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int b = nb_rp[c], e = nb_rp[c + 1];
+        const int *t = tmp + off[c];
+        for (int k = b; k < e; ++k) nb_col[k] = t[k - b];
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// host wrappers
+// -------------------------------------------------------------------------------------
+static const int TB = 256;
+
+void launch_strength(const DCsr &A, double theta, int absmode, uint8_t *mask, int *cnt, cudaStream_t s) {
+    k_strength<<<grid_for(A.nr, TB), TB, 0, s>>>(A.nr, A.rp, A.col, A.val, theta, absmode, mask, cnt);
+    count_launch();
+}
+
+void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaStream_t s) {
+    k_graph_fill<<<grid_for(A.nr, TB), TB, 0, s>>>(A.nr, A.rp, A.col, mask, G.rp, G.col);
+    count_launch();
+}
+
+void launch_col_count(int nr, const int *rp, const int *col, int *cnt, cudaStream_t s) {
+    k_col_count<<<grid_for(nr, TB), TB, 0, s>>>(nr, rp, col, cnt);
+    count_launch();
+}
+
+void launch_transpose_scatter(int nr, const int *rp, const int *col, const double *val, const int *trp,
+                              int *cursor, int *tcol, double *tval, cudaStream_t s) {
+    k_transpose_scatter<<<grid_for(nr, TB), TB, 0, s>>>(nr, rp, col, val, trp, cursor, tcol, tval);
+    count_launch();
+}
+
+void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s) {
+    k_sort_rows<<<grid_for(nr, 128), 128, 0, s>>>(nr, rp, col, val);
+    count_launch();
+}
+
+void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s) {
+    k_pmis_init<<<grid_for(n, TB), TB, 0, s>>>(n, ST.rp, seed, w, cf);
+    count_launch();
+}
+
+void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
+                       int *undecided, cudaStream_t s) {
+    k_pmis_select<<<grid_for(n, TB), TB, 0, s>>>(n, S, ST, w, cf, newc, undecided);
+    k_pmis_mark<<<grid_for(n, TB), TB, 0, s>>>(n, ST, newc, cf);
+    count_launch(2);
+}
+
+cudaError_t launch_rs(int n, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
+    size_t bytes = rs_smem_bytes(n);
+    cudaError_t e = cudaFuncSetAttribute(k_rs_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_rs_split<<<1, 32, bytes, s>>>(n, S, ST, cf, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+void launch_cidx(int n, const int8_t *cf, int *flag, int *cidx, int *cpts, int phase, cudaStream_t s) {
+    if (phase == 0) k_cflag<<<grid_for(n, TB), TB, 0, s>>>(n, cf, flag);
+    else k_cidx<<<grid_for(n, TB), TB, 0, s>>>(n, cf, flag, cidx, cpts);
+    count_launch();
+}
+
+void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, int *ub, cudaStream_t s) {
+    k_nb_bound<<<grid_for(nc, TB), TB, 0, s>>>(nc, cpts, G, cf, distance, ub);
+    count_launch();
+}
+
+void launch_nb_fill(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, const int *off, int *tmp,
+                    int *cnt, cudaStream_t s) {
+    k_nb_fill<<<grid_for(nc, 128), 128, 0, s>>>(nc, cpts, G, cf, distance, off, tmp, cnt);
+    count_launch();
+}
+
+void launch_nb_compact(int nc, const int *off, const int *tmp, const int *nb_rp, int *nb_col, cudaStream_t s) {
+    k_nb_compact<<<grid_for(nc, TB), TB, 0, s>>>(nc, off, tmp, nb_rp, nb_col);
+    count_launch();
+}
+
+}  // namespace lair

@@ -1,0 +1,94 @@
+// setup_kernels.cuh -- host-side entry points of the device kernels (internal).
+#pragma once
+
+#include "lair_internal.cuh"
+
+namespace lair {
+
+// ---- setup_graph.cu -------------------------------------------------------------------
+void launch_strength(const DCsr &A, double theta, int absmode, uint8_t *mask, int *cnt, cudaStream_t s);
+void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaStream_t s);
+void launch_col_count(int nr, const int *rp, const int *col, int *cnt, cudaStream_t s);
+void launch_transpose_scatter(int nr, const int *rp, const int *col, const double *val, const int *trp, int *cursor,
+                              int *tcol, double *tval, cudaStream_t s);
+void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s);
+void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
+void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
+                       int *undecided, cudaStream_t s);
+cudaError_t launch_rs(int n, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
+size_t rs_smem_bytes(int n);
+constexpr int RS_MAX_N = 32768;
+void launch_cidx(int n, const int8_t *cf, int *flag, int *cidx, int *cpts, int phase, cudaStream_t s);
+void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, int *ub, cudaStream_t s);
+void launch_nb_fill(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, const int *off, int *tmp,
+                    int *cnt, cudaStream_t s);
+void launch_nb_compact(int nc, const int *off, const int *tmp, const int *nb_rp, int *nb_col, cudaStream_t s);
+
+// ---- setup_local.cu -------------------------------------------------------------------
+struct LocalArgs {
+    const int *cpts;      // C point of each coarse row
+    const int *nb_rp;     // neighbourhoods, CSR over coarse rows
+    const int *nb_col;
+    const int *brp;       // the matrix B whose local systems are solved (A, or A^T for lAIP)
+    const int *bcol;
+    const double *bval;
+    int *out_col;         // output rows: row c at nb_rp[c] + c, nb_rp[c+1]-nb_rp[c] + 1 entries
+    double *out_val;
+    float *out_val32;     // optional
+    uint8_t *lsflag;      // optional, per coarse row
+};
+constexpr int LOCAL_CTA_GRID = 152 * 2;
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s);
+cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
+                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s);
+size_t local_cta_scratch_bytes(int smax, bool fp32);
+void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t *cf, const int *cidx, int absmode,
+                     int *choice, int *cnt, DCsr *P, cudaStream_t s);
+void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *status, cudaStream_t s);
+void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s);
+void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, double *out, cudaStream_t s);
+
+// ---- setup_rap.cu ---------------------------------------------------------------------
+struct SpgemmArgs {
+    const int *xrp, *xcol;
+    const double *xval;
+    const int *yrp, *ycol;
+    const double *yval;
+    const int *off;       // upper-bound offsets (exclusive scan of ub), nr + 1
+    int *tcol;            // staging, off[nr] entries
+    double *tval;
+    int *cnt;             // exact row lengths
+};
+constexpr int SPGEMM_CTA_GRID = 152;
+void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
+void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s);
+cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
+                               const int counts_host[2], int ubmax, int *skeys, double *svals, cudaStream_t s);
+unsigned spgemm_big_cap(int ubmax);
+void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tval, DCsr &Z, cudaStream_t s);
+void launch_lump(int phase, const DCsr &K, double tol, int *cnt, double *newdiag, const DCsr *out, int *status,
+                 cudaStream_t s);
+void launch_dinv(const DCsr &A, double *dinv, float *dinv32, int *status, cudaStream_t s);
+void launch_to_f32(long long n, const double *a, float *b, cudaStream_t s);
+void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s);
+
+// ---- solve_kernels.cu -----------------------------------------------------------------
+template <class T> void spmv(const DCsr &A, const T *x, T *y, cudaStream_t s);
+template <class T>
+void sweep(const DCsr &A, const int8_t *cf, int target, const T *dinv, const T *b, const T *x, T *xo, cudaStream_t s);
+template <class T> void dense_apply(int n, const double *Ainv, const T *b, T *y, cudaStream_t s);
+constexpr int RED_PARTS = 152 * 4;
+void residual(const DCsr &A, const double *b, const double *x, double *r, float *r32, double *part, cudaStream_t s);
+void multidot(int n, int m, const double *X, long long ldx, const double *y, double *part, double *out, double *acc,
+              cudaStream_t s);
+void finish_partials(int m, const double *part, double *out, cudaStream_t s);
+void sub_combo(int n, int m, const double *X, long long ldx, const double *h, double *w, cudaStream_t s);
+void add_combo(int n, int m, const double *Z, long long ldz, const double *y, double *x, cudaStream_t s);
+void scale_by_norm(int n, const double *v, const double *nrm2, double *out, cudaStream_t s);
+void d2f(int n, const double *a, float *b, cudaStream_t s);
+void f2d(int n, const float *a, double *b, cudaStream_t s);
+void axpy_f(int n, const float *e, double *x, cudaStream_t s);
+void axpy_d(int n, const double *e, double *x, cudaStream_t s);
+void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s);
+
+}  // namespace lair

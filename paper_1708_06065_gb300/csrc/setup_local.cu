@@ -1,0 +1,613 @@
+// setup_local.cu -- the local dense systems of lAIR (Sec. 3.1, Eq. (3.1)/(3.2)),
+// assembly of R = [Z I] and of the transposed interpolation rows, one-point
+// interpolation (Sec. 4), and the DG block-diagonal scaling (Sec. 4.2.1).
+//
+// One routine solves every local system, written over a "team" of cooperating
+// threads: a single thread (tiny systems, s <= 6), a warp (s <= 32, matrix in
+// shared memory) or a CTA (s > 32, matrix in global scratch). Whatever the team,
+// each matrix entry receives the same sequence of IEEE operations:
+//   LU with partial pivoting (pivot = largest |M[r][k]|, r >= k, ties -> smallest r),
+//   multipliers l_r = M[r][k] / M[k][k], updates M[r][c] = fma(-l_r, M[k][c], M[r][c]),
+//   column-oriented back substitution z[c] = rhs[c] / M[c][c], rhs[r] = fma(-M[r][c], z[c], rhs[r]);
+//   singular when a pivot |M[k][k]| <= (s * eps) * max|M|, then the minimum-norm
+//   least-squares solution by one-sided Jacobi (Hestenes) with canonical 32-way tree sums.
+// so the restriction does not depend on which bin a row fell into.
+#include "setup_kernels.cuh"
+
+namespace lair {
+
+// ---------------------------------------------------------------------------------------
+// correctly rounded scalar operations (no contraction)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+
+template <class T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 0x1.0p-52; };
+template <> struct Eps<float> { static constexpr float v = 0x1.0p-23f; };
+
+// ---------------------------------------------------------------------------------------
+// teams
+// ---------------------------------------------------------------------------------------
+struct ThreadTeam {
+    __device__ int rank() const { return 0; }
+    __device__ int size() const { return 1; }
+    __device__ void sync() const {}
+    template <class T> __device__ T max(T v) const { return v; }
+    // (value, index) argmax with ties -> smaller index; each member passes its local best
+    template <class T> __device__ void argmax(T &v, int &idx) const {}
+    __device__ int any(int p) const { return p; }
+};
+
+struct WarpTeam {
+    __device__ int rank() const { return threadIdx.x & 31; }
+    __device__ int size() const { return 32; }
+    __device__ void sync() const { __syncwarp(); }
+    template <class T> __device__ T max(T v) const {
+        for (int o = 16; o >= 1; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
+    template <class T> __device__ void argmax(T &v, int &idx) const {
+        for (int o = 16; o >= 1; o >>= 1) {
+            T ov = __shfl_xor_sync(0xffffffffu, v, o);
+            int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (oi >= 0 && (idx < 0 || ov > v || (ov == v && oi < idx))) { v = ov; idx = oi; }
+        }
+    }
+    __device__ int any(int p) const { return __any_sync(0xffffffffu, p); }
+};
+
+// CTA team: blockDim.x is a multiple of 32 (<= 1024); red is shared scratch of >= 2*32 words of 8 bytes
+struct CtaTeam {
+    double *red;
+    __device__ int rank() const { return threadIdx.x; }
+    __device__ int size() const { return blockDim.x; }
+    __device__ void sync() const { __syncthreads(); }
+    template <class T> __device__ T max(T v) const {
+        WarpTeam w;
+        v = w.max(v);
+        int nw = blockDim.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+        __syncthreads();
+        T r = (T)red[0];
+        for (int k = 1; k < nw; ++k) r = fmax(r, (T)red[k]);
+        __syncthreads();
+        return r;
+    }
+    template <class T> __device__ void argmax(T &v, int &idx) const {
+        WarpTeam w;
+        w.argmax(v, idx);
+        int nw = blockDim.x >> 5;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = (double)v;
+            reinterpret_cast<int *>(red + 32)[threadIdx.x >> 5] = idx;
+        }
+        __syncthreads();
+        T bv = (T)red[0];
+        int bi = reinterpret_cast<int *>(red + 32)[0];
+        for (int k = 1; k < nw; ++k) {
+            T ov = (T)red[k];
+            int oi = reinterpret_cast<int *>(red + 32)[k];
+            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+        }
+        __syncthreads();
+        v = bv;
+        idx = bi;
+    }
+    __device__ int any(int p) const { return __syncthreads_or(p); }
+};
+
+// ---------------------------------------------------------------------------------------
+// canonical 32-way tree sum of x[r] * y[r], r < s (strides sx, sy): partial l = fma-sum of
+// the terms r = l mod 32 in ascending r; then butterflies p_l = p_l + p_{l^o}, o = 16..1.
+// Every member of the team receives the result.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ T tree_dot(const ThreadTeam &, const T *x, int sx, const T *y, int sy, int s) {
+    T p[32];
+    for (int l = 0; l < 32; ++l) p[l] = T(0);
+    for (int r = 0; r < s; ++r) p[r & 31] = fma_rn(x[r * sx], y[r * sy], p[r & 31]);
+    for (int o = 16; o >= 1; o >>= 1) {
+        T q[32];
+        for (int l = 0; l < 32; ++l) q[l] = add_rn(p[l], p[l ^ o]);
+        for (int l = 0; l < 32; ++l) p[l] = q[l];
+    }
+    return p[0];
+}
+
+template <class T>
+__device__ T tree_dot(const WarpTeam &, const T *x, int sx, const T *y, int sy, int s) {
+    int l = threadIdx.x & 31;
+    T p = T(0);
+    for (int r = l; r < s; r += 32) p = fma_rn(x[r * sx], y[r * sy], p);
+    for (int o = 16; o >= 1; o >>= 1) p = add_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+    return p;
+}
+
+template <class T>
+__device__ T tree_dot(const CtaTeam &t, const T *x, int sx, const T *y, int sy, int s) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T p = tree_dot(WarpTeam(), x, sx, y, sy, s);
+        if (threadIdx.x == 0) t.red[0] = (double)p;
+    }
+    __syncthreads();
+    T r = (T)t.red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// local system gather: M[r][c] = B[l_c][l_r] and rhs[r] = -B[i][l_r] (Eq. (3.2))
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_pos(const int *list, int len, int key) {
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = list[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+template <class Team, class T>
+__device__ void gather_system(const Team &tm, const int *__restrict__ brp, const int *__restrict__ bcol,
+                              const double *__restrict__ bval, int i, const int *nb, int s, T *M, T *rhs) {
+    for (int e = tm.rank(); e < s * s; e += tm.size()) M[e] = T(0);
+    for (int e = tm.rank(); e < s; e += tm.size()) rhs[e] = T(0);
+    tm.sync();
+    for (int c = tm.rank(); c < s; c += tm.size()) {
+        int row = nb[c];
+        for (int k = brp[row]; k < brp[row + 1]; ++k) {
+            int r = find_pos(nb, s, bcol[k]);
+            if (r >= 0) M[r * s + c] = (T)bval[k];
+        }
+    }
+    for (int k = brp[i] + tm.rank(); k < brp[i + 1]; k += tm.size()) {
+        int r = find_pos(nb, s, bcol[k]);
+        if (r >= 0) rhs[r] = (T)(-bval[k]);
+    }
+    tm.sync();
+}
+
+// LU with partial pivoting and back substitution; returns 1 when singular (nothing solved)
+template <class Team, class T>
+__device__ int lu_solve(const Team &tm, int s, T *M, T *rhs, T *z, T *L) {
+    T mx = T(0);
+    for (int e = tm.rank(); e < s * s; e += tm.size()) mx = fmax(mx, fabs(M[e]));
+    mx = tm.max(mx);
+    if (mx == T(0)) return 1;
+    const T thr = mul_rn(mul_rn((T)s, Eps<T>::v), mx);
+    for (int k = 0; k < s; ++k) {
+        T best = T(-1);
+        int piv = -1;
+        for (int r = k + tm.rank(); r < s; r += tm.size()) {
+            T v = fabs(M[r * s + k]);
+            if (piv < 0 || v > best) { best = v; piv = r; }
+        }
+        tm.argmax(best, piv);
+        if (best <= thr) return 1;
+        if (piv != k) {
+            for (int c = tm.rank(); c < s; c += tm.size()) {
+                T t = M[k * s + c];
+                M[k * s + c] = M[piv * s + c];
+                M[piv * s + c] = t;
+            }
+            if (tm.rank() == 0) {
+                T t = rhs[k];
+                rhs[k] = rhs[piv];
+                rhs[piv] = t;
+            }
+        }
+        tm.sync();
+        for (int r = k + 1 + tm.rank(); r < s; r += tm.size()) L[r] = div_rn(M[r * s + k], M[k * s + k]);
+        tm.sync();
+        const int w = s - k;           // columns k+1 .. s-1 plus the right-hand side
+        const int cnt = (s - k - 1) * w;
+        for (int e = tm.rank(); e < cnt; e += tm.size()) {
+            int r = k + 1 + e / w;
+            int c = k + 1 + e % w;
+            if (c == s) rhs[r] = fma_rn(-L[r], rhs[k], rhs[r]);
+            else M[r * s + c] = fma_rn(-L[r], M[k * s + c], M[r * s + c]);
+        }
+        tm.sync();
+    }
+    for (int c = s - 1; c >= 0; --c) {
+        if (tm.rank() == 0) z[c] = div_rn(rhs[c], M[c * s + c]);
+        tm.sync();
+        const T zc = z[c];
+        for (int r = tm.rank(); r < c; r += tm.size()) rhs[r] = fma_rn(-M[r * s + c], zc, rhs[r]);
+        tm.sync();
+    }
+    return 0;
+}
+
+constexpr int LS_MAX_SWEEPS = 60;
+
+// minimum-norm least squares by one-sided Jacobi; B holds the original matrix (destroyed),
+// rhs the original right-hand side; V is s*s scratch; out z
+template <class Team, class T>
+__device__ void jacobi_ls(const Team &tm, int s, T *B, const T *rhs, T *V, T *z) {
+    for (int e = tm.rank(); e < s * s; e += tm.size()) V[e] = (e / s == e % s) ? T(1) : T(0);
+    tm.sync();
+    const T tol = mul_rn(Eps<T>::v, (T)s);
+    for (int sweep = 0; sweep < LS_MAX_SWEEPS; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < s - 1; ++p)
+            for (int q = p + 1; q < s; ++q) {
+                T alpha = tree_dot(tm, B + p, s, B + p, s, s);
+                T beta = tree_dot(tm, B + q, s, B + q, s, s);
+                T gamma = tree_dot(tm, B + p, s, B + q, s, s);
+                if (gamma == T(0) || fabs(gamma) <= mul_rn(tol, sqrt_rn(mul_rn(alpha, beta)))) continue;
+                rotated = 1;
+                T zeta = div_rn(sub_rn(beta, alpha), mul_rn(T(2), gamma));
+                T sg = zeta >= T(0) ? T(1) : T(-1);
+                T t = div_rn(sg, add_rn(fabs(zeta), sqrt_rn(fma_rn(zeta, zeta, T(1)))));
+                T c = div_rn(T(1), sqrt_rn(fma_rn(t, t, T(1))));
+                T sn = mul_rn(c, t);
+                for (int r = tm.rank(); r < s; r += tm.size()) {
+                    T bp = B[r * s + p], bq = B[r * s + q];
+                    B[r * s + p] = fma_rn(c, bp, -mul_rn(sn, bq));
+                    B[r * s + q] = fma_rn(sn, bp, mul_rn(c, bq));
+                    T vp = V[r * s + p], vq = V[r * s + q];
+                    V[r * s + p] = fma_rn(c, vp, -mul_rn(sn, vq));
+                    V[r * s + q] = fma_rn(sn, vp, mul_rn(c, vq));
+                }
+                tm.sync();
+            }
+        if (!rotated) break;
+    }
+    T smax = T(0);
+    for (int j = 0; j < s; ++j) {
+        T sig = sqrt_rn(tree_dot(tm, B + j, s, B + j, s, s));
+        if (sig > smax) smax = sig;
+    }
+    const T cut = mul_rn(mul_rn((T)s, Eps<T>::v), smax);
+    for (int r = tm.rank(); r < s; r += tm.size()) z[r] = T(0);
+    tm.sync();
+    for (int j = 0; j < s; ++j) {
+        T sig = sqrt_rn(tree_dot(tm, B + j, s, B + j, s, s));
+        if (!(sig > cut)) continue;
+        T coef = div_rn(div_rn(tree_dot(tm, B + j, s, rhs, 1, s), sig), sig);
+        for (int r = tm.rank(); r < s; r += tm.size()) z[r] = fma_rn(V[r * s + j], coef, z[r]);
+        tm.sync();
+    }
+}
+
+// one C point: gather, solve (LU or least squares), write its R row {nb, z} u {(i, 1)}
+template <class Team, class T>
+__device__ void solve_row(const Team &tm, const LocalArgs &a, int c, T *M, T *rhs, T *z, T *L, T *V) {
+    const int i = a.cpts[c];
+    const int *nb = a.nb_col + a.nb_rp[c];
+    const int s = a.nb_rp[c + 1] - a.nb_rp[c];
+    int singular = 0;
+    if (s > 0) {
+        gather_system(tm, a.brp, a.bcol, a.bval, i, nb, s, M, rhs);
+        singular = lu_solve(tm, s, M, rhs, z, L);
+        if (singular) {
+            gather_system(tm, a.brp, a.bcol, a.bval, i, nb, s, M, rhs);
+            jacobi_ls(tm, s, M, rhs, V, z);
+        }
+    }
+    tm.sync();
+    const int base = a.nb_rp[c] + c;
+    int before = 0;   // entries of nb left of i
+    for (int r = tm.rank(); r < s; r += tm.size()) {
+        int pos = r + (nb[r] > i ? 1 : 0);
+        a.out_col[base + pos] = nb[r];
+        double v = (double)z[r];
+        a.out_val[base + pos] = v;
+        if (a.out_val32) a.out_val32[base + pos] = (float)z[r];
+    }
+    if (tm.rank() == 0) {
+        int lo = 0, hi = s;
+        while (lo < hi) { int m = (lo + hi) >> 1; if (nb[m] < i) lo = m + 1; else hi = m; }
+        before = lo;
+        a.out_col[base + before] = i;
+        a.out_val[base + before] = 1.0;
+        if (a.out_val32) a.out_val32[base + before] = 1.0f;
+        if (a.lsflag) a.lsflag[c] = (uint8_t)singular;
+    }
+    tm.sync();
+}
+
+// ---------------------------------------------------------------------------------------
+// bin kernels
+// ---------------------------------------------------------------------------------------
+constexpr int THREAD_SMAX = 6;
+
+template <class T>
+__global__ void __launch_bounds__(128) k_local_thread(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count) {
+    const int n = *count;
+    T M[THREAD_SMAX * THREAD_SMAX], V[THREAD_SMAX * THREAD_SMAX], rhs[THREAD_SMAX], z[THREAD_SMAX], L[THREAD_SMAX];
+    ThreadTeam tm;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        solve_row(tm, a, list[t], M, rhs, z, L, V);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_local_warp(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = *count;
+    const int w = threadIdx.x >> 5;
+    T *base = reinterpret_cast<T *>(smem) + (size_t)w * (2 * 32 * 32 + 3 * 32);
+    T *M = base, *V = base + 32 * 32, *rhs = V + 32 * 32, *z = rhs + 32, *L = z + 32;
+    WarpTeam tm;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int t = blockIdx.x * (blockDim.x >> 5) + w; t < n; t += nwarps) solve_row(tm, a, list[t], M, rhs, z, L, V);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count,
+                                                   T *__restrict__ scratch, int smax) {
+    __shared__ double red[64];
+    const int n = *count;
+    const size_t per = (size_t)2 * smax * smax + 3 * (size_t)smax;
+    T *M = scratch + per * blockIdx.x;
+    T *V = M + (size_t)smax * smax, *rhs = V + (size_t)smax * smax, *z = rhs + smax, *L = z + smax;
+    CtaTeam tm{red};
+    for (int t = blockIdx.x; t < n; t += gridDim.x) solve_row(tm, a, list[t], M, rhs, z, L, V);
+}
+
+__global__ void k_local_bin(int nc, const int *__restrict__ nb_rp, int *__restrict__ lists, int *__restrict__ counts,
+                            int *__restrict__ smax) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        int s = nb_rp[c + 1] - nb_rp[c];
+        int b = s <= THREAD_SMAX ? 0 : (s <= 32 ? 1 : 2);
+        int p = atomicAdd(&counts[b], 1);
+        lists[(size_t)b * nc + p] = c;
+        atomicMax(smax, s);
+    }
+}
+
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s) {
+    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, nb_rp, lists, counts, smax);
+    count_launch();
+}
+
+cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
+                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (counts_host[0] > 0) {
+        int g = grid_for(counts_host[0], 128);
+        if (fp32) k_local_thread<float><<<g, 128, 0, s>>>(a, lists, counts_dev);
+        else k_local_thread<double><<<g, 128, 0, s>>>(a, lists, counts_dev);
+        count_launch();
+    }
+    if (counts_host[1] > 0) {
+        size_t el = fp32 ? sizeof(float) : sizeof(double);
+        size_t bytes = 4 * el * (2 * 32 * 32 + 3 * 32);
+        int g = grid_for(counts_host[1], 4, 152 * 8);
+        if (fp32) {
+            cudaFuncSetAttribute(k_local_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            k_local_warp<float><<<g, 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
+        } else {
+            cudaFuncSetAttribute(k_local_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            k_local_warp<double><<<g, 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
+        }
+        count_launch();
+    }
+    if (counts_host[2] > 0) {
+        int g = counts_host[2] < LOCAL_CTA_GRID ? counts_host[2] : LOCAL_CTA_GRID;
+        if (fp32) k_local_cta<float><<<g, 256, 0, s>>>(a, lists + 2 * (size_t)nc, counts_dev + 2, (float *)scratch, smax);
+        else k_local_cta<double><<<g, 256, 0, s>>>(a, lists + 2 * (size_t)nc, counts_dev + 2, (double *)scratch, smax);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    return e;
+}
+
+size_t local_cta_scratch_bytes(int smax, bool fp32) {
+    size_t el = fp32 ? sizeof(float) : sizeof(double);
+    return el * ((size_t)2 * smax * smax + 3 * (size_t)smax) * LOCAL_CTA_GRID;
+}
+
+// ---------------------------------------------------------------------------------------
+// one-point interpolation (Sec. 4): F row j -> 1 at its strongest C connection
+// (largest -a_jc, or |a_jc| in abs mode; ties -> smallest c); C rows -> identity.
+// ---------------------------------------------------------------------------------------
+__global__ void k_onepoint_choose(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                  const double *__restrict__ val, const uint8_t *__restrict__ mask,
+                                  const int8_t *__restrict__ cf, const int *__restrict__ cidx, int absmode,
+                                  int *__restrict__ choice, int *__restrict__ cnt) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        int ch = -1;
+        if (cf[j] == CF_C) {
+            ch = cidx[j];
+        } else {
+            double bk = 0.0;
+            int best = -1;
+            for (int k = rp[j]; k < rp[j + 1]; ++k) {
+                int c = col[k];
+                if (!mask[k] || cf[c] != CF_C) continue;
+                double key = absmode ? fabs(val[k]) : -val[k];
+                if (best < 0 || key > bk) { best = c; bk = key; }
+            }
+            if (best >= 0) ch = cidx[best];
+        }
+        choice[j] = ch;
+        cnt[j] = ch >= 0;
+    }
+}
+
+__global__ void k_onepoint_fill(int n, const int *__restrict__ choice, const int *__restrict__ prp,
+                                int *__restrict__ pcol, double *__restrict__ pval, float *__restrict__ pval32) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (choice[j] < 0) continue;
+        pcol[prp[j]] = choice[j];
+        pval[prp[j]] = 1.0;
+        if (pval32) pval32[prp[j]] = 1.0f;
+    }
+}
+
+void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t *cf, const int *cidx, int absmode,
+                     int *choice, int *cnt, DCsr *P, cudaStream_t s) {
+    if (phase == 0)
+        k_onepoint_choose<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, A.col, A.val, mask, cf, cidx, absmode, choice, cnt);
+    else
+        k_onepoint_fill<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, choice, P->rp, P->col, P->val, P->val32);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// DG block-diagonal scaling (Sec. 4.2.1): A -> D_B^{-1} A with bs x bs diagonal blocks.
+// D_B^{-1} from LU with partial pivoting (same rules as above, multipliers kept, rows of
+// L swapped with M) applied to unit vectors; row r of block K of the result is
+// sum_t Dinv[r][t] * A[K t, :] (fma, ascending t) on the union of the block rows'
+// off-block columns, and the diagonal block becomes the exact identity.
+// ---------------------------------------------------------------------------------------
+constexpr int BS_MAX = 8;
+constexpr int BS_UNION_MAX = 256;
+
+__device__ int block_union(const int *rp, const int *col, int r0, int bs, int *u) {
+    int nu = 0;
+    for (int r = 0; r < bs; ++r)
+        for (int k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k) {
+            int j = col[k];
+            if (j >= r0 && j < r0 + bs) continue;
+            // insert into sorted unique list
+            int lo = 0, hi = nu;
+            while (lo < hi) { int m = (lo + hi) >> 1; if (u[m] < j) lo = m + 1; else hi = m; }
+            if (lo < nu && u[lo] == j) continue;
+            if (nu >= BS_UNION_MAX) return -1;
+            for (int m = nu; m > lo; --m) u[m] = u[m - 1];
+            u[lo] = j;
+            ++nu;
+        }
+    return nu;
+}
+
+__global__ void k_block_count(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                              int *__restrict__ rowcnt, int *status) {
+    int u[BS_UNION_MAX];
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
+        int nu = block_union(rp, col, K * bs, bs, u);
+        if (nu < 0) { set_status(status, LAIR_ERR_UNSUPPORTED); nu = 0; }
+        for (int r = 0; r < bs; ++r) rowcnt[K * bs + r] = nu + 1;
+    }
+}
+
+__device__ double entry(const int *rp, const int *col, const double *val, int i, int j) {
+    int lo = rp[i], hi = rp[i + 1] - 1;
+    while (lo <= hi) {
+        int m = (lo + hi) >> 1;
+        int c = col[m];
+        if (c == j) return val[m];
+        if (c < j) lo = m + 1; else hi = m - 1;
+    }
+    return 0.0;
+}
+
+__global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ val, const int *__restrict__ orp, int *__restrict__ ocol,
+                             double *__restrict__ oval, double *__restrict__ dinv_out, int *status) {
+    int u[BS_UNION_MAX];
+    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], Di[BS_MAX * BS_MAX], rhs[BS_MAX];
+    int perm[BS_MAX];
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
+        const int r0 = K * bs;
+        for (int r = 0; r < bs; ++r) {
+            perm[r] = r;
+            for (int c = 0; c < bs; ++c) {
+                M[r * bs + c] = entry(rp, col, val, r0 + r, r0 + c);
+                Lm[r * bs + c] = 0.0;
+            }
+        }
+        double mx = 0.0;
+        for (int e = 0; e < bs * bs; ++e) mx = fmax(mx, fabs(M[e]));
+        const double thr = __dmul_rn(__dmul_rn((double)bs, 0x1.0p-52), mx);
+        bool bad = mx == 0.0;
+        for (int k = 0; k < bs && !bad; ++k) {
+            int piv = k;
+            double best = fabs(M[k * bs + k]);
+            for (int r = k + 1; r < bs; ++r)
+                if (fabs(M[r * bs + k]) > best) { best = fabs(M[r * bs + k]); piv = r; }
+            if (best <= thr) { bad = true; break; }
+            if (piv != k) {
+                for (int c = 0; c < bs; ++c) {
+                    double t = M[k * bs + c]; M[k * bs + c] = M[piv * bs + c]; M[piv * bs + c] = t;
+                    t = Lm[k * bs + c]; Lm[k * bs + c] = Lm[piv * bs + c]; Lm[piv * bs + c] = t;
+                }
+                int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+            }
+            for (int r = k + 1; r < bs; ++r) {
+                double l = __ddiv_rn(M[r * bs + k], M[k * bs + k]);
+                Lm[r * bs + k] = l;
+                for (int c = k + 1; c < bs; ++c) M[r * bs + c] = __fma_rn(-l, M[k * bs + c], M[r * bs + c]);
+            }
+        }
+        if (bad) { set_status(status, LAIR_ERR_ZERO_DIAGONAL); continue; }
+        for (int t = 0; t < bs; ++t) {
+            for (int r = 0; r < bs; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
+            for (int k = 0; k < bs; ++k)
+                for (int r = k + 1; r < bs; ++r) rhs[r] = __fma_rn(-Lm[r * bs + k], rhs[k], rhs[r]);
+            for (int c = bs - 1; c >= 0; --c) {
+                double zc = __ddiv_rn(rhs[c], M[c * bs + c]);
+                Di[c * bs + t] = zc;
+                for (int r = 0; r < c; ++r) rhs[r] = __fma_rn(-M[r * bs + c], zc, rhs[r]);
+            }
+        }
+        for (int e = 0; e < bs * bs; ++e) dinv_out[(size_t)K * bs * bs + e] = Di[e];
+        int nu = block_union(rp, col, r0, bs, u);
+        if (nu < 0) continue;
+        for (int r = 0; r < bs; ++r) {
+            int p = orp[r0 + r];
+            bool placed = false;
+            for (int a = 0; a <= nu; ++a) {
+                if (!placed && (a == nu || u[a] > r0 + r)) {
+                    ocol[p] = r0 + r;
+                    oval[p] = 1.0;
+                    ++p;
+                    placed = true;
+                }
+                if (a == nu) break;
+                int j = u[a];
+                double acc = 0.0;
+                for (int t = 0; t < bs; ++t) acc = __fma_rn(Di[r * bs + t], entry(rp, col, val, r0 + t, j), acc);
+                ocol[p] = j;
+                oval[p] = acc;
+                ++p;
+            }
+        }
+    }
+}
+
+__global__ void k_block_apply(int nblk, int bs, const double *__restrict__ dinv, const double *__restrict__ b,
+                              double *__restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nblk * bs; e += gridDim.x * blockDim.x) {
+        int K = e / bs, r = e % bs;
+        double acc = 0.0;
+        for (int t = 0; t < bs; ++t) acc = __fma_rn(dinv[(size_t)K * bs * bs + r * bs + t], b[K * bs + t], acc);
+        out[e] = acc;
+    }
+}
+
+void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *status, cudaStream_t s) {
+    k_block_count<<<grid_for(nblk, 64), 64, 0, s>>>(nblk, bs, A.rp, A.col, rowcnt, status);
+    count_launch();
+}
+
+void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
+    k_block_fill<<<grid_for(nblk, 64), 64, 0, s>>>(nblk, bs, A.rp, A.col, A.val, out.rp, out.col, out.val, dinv, status);
+    count_launch();
+}
+
+void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, double *out, cudaStream_t s) {
+    k_block_apply<<<grid_for((long long)nblk * bs, 256), 256, 0, s>>>(nblk, bs, dinv, b, out);
+    count_launch();
+}
+
+}  // namespace lair

@@ -1,0 +1,421 @@
+// setup_rap.cu -- Galerkin coarse operator K = R A P (Sec. 2.1), lumping of small
+// entries into the diagonal (Sec. 3.3), Jacobi diagonals, FP32 copies, and the
+// dense factorisation of the coarsest level.
+//
+// Products are formed row by row as Z = X Y (first R A, then (R A) P). Entry (a, l)
+// of a row starts at 0 and receives fma(x_ak, y_kl, .) for the k of row a of X in
+// ascending order, exactly one update per k; the pattern is the full symbolic
+// product (structural zeros kept). This fixed order makes K a deterministic function
+// of R, A and P, independent of the thread layout.
+#include "setup_kernels.cuh"
+
+namespace lair {
+
+constexpr int WARP_CAP = 2048;      // hash slots per warp (rows with ub <= WARP_CAP / 2)
+constexpr int SPGEMM_WARPS = 4;
+
+__global__ void k_spgemm_ub(int nr, const int *__restrict__ xrp, const int *__restrict__ xcol,
+                            const int *__restrict__ yrp, int *__restrict__ ub) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nr; a += gridDim.x * blockDim.x) {
+        int u = 0;
+        for (int p = xrp[a]; p < xrp[a + 1]; ++p) {
+            int k = xcol[p];
+            u += yrp[k + 1] - yrp[k];
+        }
+        ub[a] = u;
+    }
+}
+
+__global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__restrict__ lists,
+                                  int *__restrict__ counts, int *__restrict__ ubmax) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nr; a += gridDim.x * blockDim.x) {
+        int u = off[a + 1] - off[a];
+        int b = u <= WARP_CAP / 2 ? 0 : 1;
+        int p = atomicAdd(&counts[b], 1);
+        lists[(size_t)b * nr + p] = a;
+        if (b) atomicMax(ubmax, u);
+    }
+}
+
+__device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
+
+__global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
+                                                                const int *__restrict__ count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    double *vals = reinterpret_cast<double *>(smem) + (size_t)w * WARP_CAP;
+    int *keys = reinterpret_cast<int *>(reinterpret_cast<double *>(smem) + (size_t)SPGEMM_WARPS * WARP_CAP) + (size_t)w * WARP_CAP;
+    const int n = *count;
+    const int nwarps = gridDim.x * SPGEMM_WARPS;
+    for (int t = blockIdx.x * SPGEMM_WARPS + w; t < n; t += nwarps) {
+        const int a = list[t];
+        const int ub = g.off[a + 1] - g.off[a];
+        unsigned cap = 32;
+        while ((int)cap < 2 * ub) cap <<= 1;
+        const unsigned mask = cap - 1;
+        for (unsigned e = lane; e < cap; e += 32) keys[e] = -1;
+        __syncwarp();
+        for (int p = g.xrp[a]; p < g.xrp[a + 1]; ++p) {
+            const int k = g.xcol[p];
+            const double x = g.xval[p];
+            for (int q = g.yrp[k] + lane; q < g.yrp[k + 1]; q += 32) {
+                const int l = g.ycol[q];
+                const double y = g.yval[q];
+                unsigned h = hash_slot(l, mask);
+                for (;;) {
+                    int prev = atomicCAS(&keys[h], -1, l);
+                    if (prev == -1) { vals[h] = __fma_rn(x, y, 0.0); break; }
+                    if (prev == l) { vals[h] = __fma_rn(x, y, vals[h]); break; }
+                    h = (h + 1) & mask;
+                }
+            }
+            __syncwarp();
+        }
+        // compact occupied slots to the front (in order of slot; positions never pass the read slot)
+        int cnt = 0;
+        for (unsigned base = 0; base < cap; base += 32) {
+            int key = keys[base + lane];
+            double v = vals[base + lane];
+            unsigned occ = __ballot_sync(0xffffffffu, key != -1);
+            __syncwarp();
+            if (key != -1) {
+                int pos = cnt + __popc(occ & ((1u << lane) - 1u));
+                keys[pos] = key;
+                vals[pos] = v;
+            }
+            cnt += __popc(occ);
+            __syncwarp();
+        }
+        unsigned np2 = 1;
+        while ((int)np2 < cnt) np2 <<= 1;
+        for (unsigned e = cnt + lane; e < np2; e += 32) keys[e] = 0x7fffffff;
+        __syncwarp();
+        // bitonic sort by column
+        for (unsigned kk = 2; kk <= np2; kk <<= 1)
+            for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+                for (unsigned i = lane; i < np2; i += 32) {
+                    unsigned ixj = i ^ j;
+                    if (ixj > i) {
+                        bool up = (i & kk) == 0;
+                        int ki = keys[i], kj = keys[ixj];
+                        if ((ki > kj) == up) {
+                            keys[i] = kj; keys[ixj] = ki;
+                            double tv = vals[i]; vals[i] = vals[ixj]; vals[ixj] = tv;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        const int o = g.off[a];
+        for (int e = lane; e < cnt; e += 32) {
+            g.tcol[o + e] = keys[e];
+            g.tval[o + e] = vals[e];
+        }
+        if (lane == 0) g.cnt[a] = cnt;
+        __syncwarp();
+    }
+}
+
+// long rows: one CTA per row, hash table and staging area in global scratch
+__global__ void __launch_bounds__(256) k_spgemm_cta(SpgemmArgs g, const int *__restrict__ list, const int *__restrict__ count,
+                                                   int *__restrict__ skeys, double *__restrict__ svals, unsigned cap) {
+    __shared__ int cnt;
+    const int n = *count;
+    int *keys = skeys + (size_t)2 * cap * blockIdx.x;
+    int *stk = keys + cap;
+    double *vals = svals + (size_t)2 * cap * blockIdx.x;
+    double *stv = vals + cap;
+    const unsigned mask = cap - 1;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int a = list[t];
+        for (unsigned e = threadIdx.x; e < cap; e += blockDim.x) keys[e] = -1;
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        for (int p = g.xrp[a]; p < g.xrp[a + 1]; ++p) {
+            const int k = g.xcol[p];
+            const double x = g.xval[p];
+            for (int q = g.yrp[k] + threadIdx.x; q < g.yrp[k + 1]; q += blockDim.x) {
+                const int l = g.ycol[q];
+                const double y = g.yval[q];
+                unsigned h = hash_slot(l, mask);
+                for (;;) {
+                    int prev = atomicCAS(&keys[h], -1, l);
+                    if (prev == -1) { vals[h] = __fma_rn(x, y, 0.0); break; }
+                    if (prev == l) { vals[h] = __fma_rn(x, y, vals[h]); break; }
+                    h = (h + 1) & mask;
+                }
+            }
+            __syncthreads();
+        }
+        for (unsigned e = threadIdx.x; e < cap; e += blockDim.x) {
+            int key = keys[e];
+            if (key != -1) {
+                int pos = atomicAdd(&cnt, 1);
+                stk[pos] = key;
+                stv[pos] = vals[e];
+            }
+        }
+        __syncthreads();
+        const int c = cnt;
+        unsigned np2 = 1;
+        while ((int)np2 < c) np2 <<= 1;
+        for (unsigned e = c + threadIdx.x; e < np2; e += blockDim.x) stk[e] = 0x7fffffff;
+        __syncthreads();
+        for (unsigned kk = 2; kk <= np2; kk <<= 1)
+            for (unsigned j = kk >> 1; j > 0; j >>= 1) {
+                for (unsigned i = threadIdx.x; i < np2; i += blockDim.x) {
+                    unsigned ixj = i ^ j;
+                    if (ixj > i) {
+                        bool up = (i & kk) == 0;
+                        int ki = stk[i], kj = stk[ixj];
+                        if ((ki > kj) == up) {
+                            stk[i] = kj; stk[ixj] = ki;
+                            double tv = stv[i]; stv[i] = stv[ixj]; stv[ixj] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        const int o = g.off[a];
+        for (int e = threadIdx.x; e < c; e += blockDim.x) {
+            g.tcol[o + e] = stk[e];
+            g.tval[o + e] = stv[e];
+        }
+        if (threadIdx.x == 0) g.cnt[a] = c;
+        __syncthreads();
+    }
+}
+
+__global__ void k_copy_rows(int nr, const int *__restrict__ off, const int *__restrict__ tcol, const double *__restrict__ tval,
+                            const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
+    // one warp per row
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int a = wid; a < nr; a += nw) {
+        int b = rp[a], e = rp[a + 1], o = off[a];
+        for (int k = b + lane; k < e; k += 32) {
+            col[k] = tcol[o + k - b];
+            val[k] = tval[o + k - b];
+        }
+    }
+}
+
+void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s) {
+    k_spgemm_ub<<<grid_for(nr, 256), 256, 0, s>>>(nr, xrp, xcol, yrp, ub);
+    count_launch();
+}
+
+void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s) {
+    k_spgemm_classify<<<grid_for(nr, 256), 256, 0, s>>>(nr, off, lists, counts, ubmax);
+    count_launch();
+}
+
+cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
+                               const int counts_host[2], int ubmax, int *skeys, double *svals, cudaStream_t s) {
+    if (counts_host[0] > 0) {
+        size_t bytes = (size_t)SPGEMM_WARPS * WARP_CAP * (sizeof(double) + sizeof(int));
+        cudaFuncSetAttribute(k_spgemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        int grid = grid_for(counts_host[0], SPGEMM_WARPS, 152 * 8);
+        k_spgemm_warp<<<grid, 32 * SPGEMM_WARPS, bytes, s>>>(g, lists, counts_dev);
+        count_launch();
+    }
+    if (counts_host[1] > 0) {
+        unsigned cap = spgemm_big_cap(ubmax);
+        int grid = counts_host[1] < SPGEMM_CTA_GRID ? counts_host[1] : SPGEMM_CTA_GRID;
+        k_spgemm_cta<<<grid, 256, 0, s>>>(g, lists + nr, counts_dev + 1, skeys, svals, cap);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+unsigned spgemm_big_cap(int ubmax) {
+    unsigned cap = 32;
+    while ((long long)cap < 2LL * ubmax) cap <<= 1;
+    return cap;
+}
+
+void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tval, DCsr &Z, cudaStream_t s) {
+    k_copy_rows<<<grid_for((long long)nr * 32, 256), 256, 0, s>>>(nr, off, tcol, tval, Z.rp, Z.col, Z.val);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// lumping (Sec. 3.3): in row i drop every off-diagonal with |k_ij| < theta_D * max_j |k_ij|
+// (max over the whole row) and add it to k_ii, in ascending j, starting from k_ii.
+// ---------------------------------------------------------------------------------------
+__global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+                             double tol, int *__restrict__ cnt, double *__restrict__ newdiag, int *status) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int b = rp[i], e = rp[i + 1];
+        double m = 0.0;
+        for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
+        double thr = __dmul_rn(tol, m);
+        double d = 0.0;
+        bool has = false;
+        for (int k = b; k < e; ++k)
+            if (col[k] == i) { d = val[k]; has = true; }
+        if (!has) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+        int c = 0;
+        for (int k = b; k < e; ++k) {
+            if (col[k] != i && fabs(val[k]) < thr) d = __dadd_rn(d, val[k]);
+            else ++c;
+        }
+        cnt[i] = c;
+        newdiag[i] = d;
+    }
+}
+
+__global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+                            double tol, const double *__restrict__ newdiag, const int *__restrict__ orp,
+                            int *__restrict__ ocol, double *__restrict__ oval) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int b = rp[i], e = rp[i + 1];
+        double m = 0.0;
+        for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
+        double thr = __dmul_rn(tol, m);
+        int p = orp[i];
+        for (int k = b; k < e; ++k) {
+            if (col[k] != i && fabs(val[k]) < thr) continue;
+            ocol[p] = col[k];
+            oval[p] = col[k] == i ? newdiag[i] : val[k];
+            ++p;
+        }
+    }
+}
+
+void launch_lump(int phase, const DCsr &K, double tol, int *cnt, double *newdiag, const DCsr *out, int *status,
+                 cudaStream_t s) {
+    if (phase == 0)
+        k_lump_count<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, K.col, K.val, tol, cnt, newdiag, status);
+    else
+        k_lump_fill<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, K.col, K.val, tol, newdiag, out->rp, out->col, out->val);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// Jacobi diagonal inverse (1 / a_ii, IEEE division) and FP32 copies
+// ---------------------------------------------------------------------------------------
+__global__ void k_dinv(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+                       double *__restrict__ dinv, float *__restrict__ dinv32, int *status) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] == i) d = val[k];
+        if (d == 0.0) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+        double r = __ddiv_rn(1.0, d);
+        dinv[i] = r;
+        if (dinv32) dinv32[i] = (float)r;
+    }
+}
+
+__global__ void k_to_f32(long long n, const double *__restrict__ a, float *__restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+void launch_dinv(const DCsr &A, double *dinv, float *dinv32, int *status, cudaStream_t s) {
+    k_dinv<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, A.col, A.val, dinv, dinv32, status);
+    count_launch();
+}
+
+void launch_to_f32(long long n, const double *a, float *b, cudaStream_t s) {
+    if (n <= 0) return;
+    k_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// coarsest level: dense LU with partial pivoting in one CTA, then the explicit inverse
+// (one thread per column), so that the per-cycle coarse solve is a dense product.
+// ---------------------------------------------------------------------------------------
+__global__ void k_dense_build(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+                              double *__restrict__ D) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x)
+        D[e] = 0.0;
+}
+
+__global__ void k_dense_scatter(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
+                                double *__restrict__ D) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = rp[i]; k < rp[i + 1]; ++k) D[(size_t)i * n + col[k]] = val[k];
+}
+
+__global__ void __launch_bounds__(1024) k_dense_lu(int n, double *__restrict__ D, int *__restrict__ perm, int *status) {
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int piv = -1;
+        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+            double v = fabs(D[(size_t)r * n + k]);
+            if (piv < 0 || v > best) { best = v; piv = r; }
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (oi >= 0 && (piv < 0 || ov > best || (ov == best && oi < piv))) { best = ov; piv = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = piv; }
+        __syncthreads();
+        best = bv[0];
+        piv = bi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (bi[w] >= 0 && (piv < 0 || bv[w] > best || (bv[w] == best && bi[w] < piv))) { best = bv[w]; piv = bi[w]; }
+        __syncthreads();
+        if (best == 0.0) {
+            if (threadIdx.x == 0) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+            return;
+        }
+        if (piv != k) {
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                double t = D[(size_t)k * n + c];
+                D[(size_t)k * n + c] = D[(size_t)piv * n + c];
+                D[(size_t)piv * n + c] = t;
+            }
+            if (threadIdx.x == 0) { int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t; }
+        }
+        __syncthreads();
+        const double pk = D[(size_t)k * n + k];
+        for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) D[(size_t)r * n + k] = D[(size_t)r * n + k] / pk;
+        __syncthreads();
+        const int w = n - k - 1;
+        for (long long e = threadIdx.x; e < (long long)w * w; e += blockDim.x) {
+            int r = k + 1 + (int)(e / w), c = k + 1 + (int)(e % w);
+            D[(size_t)r * n + c] = fma(-D[(size_t)r * n + k], D[(size_t)k * n + c], D[(size_t)r * n + c]);
+        }
+        __syncthreads();
+    }
+}
+
+// Ainv[:, t] = U^{-1} L^{-1} P e_t
+__global__ void k_dense_inverse(int n, const double *__restrict__ LU, const int *__restrict__ perm, double *__restrict__ Ainv) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        for (int r = 0; r < n; ++r) Ainv[(size_t)r * n + t] = perm[r] == t ? 1.0 : 0.0;
+        for (int k = 0; k < n; ++k) {
+            double xk = Ainv[(size_t)k * n + t];
+            if (xk == 0.0) continue;
+            for (int r = k + 1; r < n; ++r) Ainv[(size_t)r * n + t] = fma(-LU[(size_t)r * n + k], xk, Ainv[(size_t)r * n + t]);
+        }
+        for (int c = n - 1; c >= 0; --c) {
+            double xc = Ainv[(size_t)c * n + t] / LU[(size_t)c * n + c];
+            Ainv[(size_t)c * n + t] = xc;
+            for (int r = 0; r < c; ++r) Ainv[(size_t)r * n + t] = fma(-LU[(size_t)r * n + c], xc, Ainv[(size_t)r * n + t]);
+        }
+    }
+}
+
+void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s) {
+    int n = A.nr;
+    k_dense_build<<<grid_for((long long)n * n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
+    k_dense_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
+    k_dense_lu<<<1, 1024, 0, s>>>(n, D, perm, status);
+    k_dense_inverse<<<grid_for(n, 64), 64, 0, s>>>(n, D, perm, Ainv);
+    count_launch(4);
+}
+
+}  // namespace lair

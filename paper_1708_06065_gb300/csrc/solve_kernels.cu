@@ -1,0 +1,333 @@
+// solve_kernels.cu -- the cycle (Sec. 4): restriction b_c = R r, interpolation
+// x = P x_c, Jacobi F/C sweeps x_i <- x_i + d_i (b_i - A_i x) (Eq. (2.4)), the dense
+// coarsest solve, and the FP64 outer-iteration kernels (residual, norms, block dots
+// for classical Gram-Schmidt, updates).
+//
+// Sparse rows are processed by groups of G consecutive lanes (G = 1, 2, 4, 8, 16 or
+// 32, picked from the average row length); group lanes stride over the row so that
+// consecutive lanes load consecutive column indices and values, and the partial sums
+// are combined by xor-shuffles inside the group. All of these kernels are bound by
+// HBM bandwidth on the large levels.
+#include "setup_kernels.cuh"
+
+namespace lair {
+
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// y = A x  (also R b and P x_c)
+template <int G, class T>
+__global__ void __launch_bounds__(256) k_spmv(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                             const T *__restrict__ val, const T *__restrict__ x, T *__restrict__ y) {
+    const int gl = threadIdx.x & (G - 1);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long lane = threadIdx.x & 31;
+    for (long long base = tid; base - lane < (long long)nr * G; base += stride) {  // warp-uniform trip count
+        int i = (int)(base / G);
+        T acc = T(0);
+        if (i < nr) {
+            int b = __ldg(rp + i), e = __ldg(rp + i + 1);
+            for (int k = b + gl; k < e; k += G) acc = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), acc);
+        }
+        acc = group_sum<G>(acc);
+        if (i < nr && gl == 0) y[i] = acc;
+    }
+}
+
+// one Jacobi sweep over the points with cf == target; all other points are copied
+template <int G, class T>
+__global__ void __launch_bounds__(256) k_sweep(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                              const T *__restrict__ val, const int8_t *__restrict__ cf, int target,
+                                              const T *__restrict__ dinv, const T *__restrict__ b,
+                                              const T *__restrict__ x, T *__restrict__ xo) {
+    const int gl = threadIdx.x & (G - 1);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long lane = threadIdx.x & 31;
+    for (long long base = tid; base - lane < (long long)nr * G; base += stride) {  // warp-uniform trip count
+        int i = (int)(base / G);
+        bool act = i < nr && cf[i] == target;
+        T acc = T(0);
+        if (act) {
+            int bb = __ldg(rp + i), e = __ldg(rp + i + 1);
+            for (int k = bb + gl; k < e; k += G) acc = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), acc);
+        }
+        acc = group_sum<G>(acc);
+        if (i < nr && gl == 0) xo[i] = act ? fma(dinv[i], b[i] - acc, x[i]) : x[i];
+    }
+}
+
+template <class T>
+static int pick_group(const DCsr &A) {
+    double avg = A.nr > 0 ? (double)A.nnz / A.nr : 1.0;
+    if (avg <= 1.5) return 1;
+    if (avg <= 3.0) return 2;
+    if (avg <= 10.0) return 4;
+    if (avg <= 24.0) return 8;
+    if (avg <= 48.0) return 16;
+    return 32;
+}
+
+template <class T>
+static const T *vals_of(const DCsr &A);
+template <> const double *vals_of<double>(const DCsr &A) { return A.val; }
+template <> const float *vals_of<float>(const DCsr &A) { return A.val32; }
+
+template <class T>
+void spmv(const DCsr &A, const T *x, T *y, cudaStream_t s) {
+    if (A.nr == 0) return;
+    int G = pick_group<T>(A);
+    int grid = grid_for((long long)A.nr * G, 256, 152 * 16);
+    const T *v = vals_of<T>(A);
+    switch (G) {
+        case 1: k_spmv<1, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+        case 2: k_spmv<2, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+        case 4: k_spmv<4, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+        case 8: k_spmv<8, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+        case 16: k_spmv<16, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+        default: k_spmv<32, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
+    }
+    count_launch();
+}
+
+template <class T>
+void sweep(const DCsr &A, const int8_t *cf, int target, const T *dinv, const T *b, const T *x, T *xo, cudaStream_t s) {
+    if (A.nr == 0) return;
+    int G = pick_group<T>(A);
+    int grid = grid_for((long long)A.nr * G, 256, 152 * 16);
+    const T *v = vals_of<T>(A);
+    switch (G) {
+        case 1: k_sweep<1, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+        case 2: k_sweep<2, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+        case 4: k_sweep<4, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+        case 8: k_sweep<8, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+        case 16: k_sweep<16, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+        default: k_sweep<32, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
+    }
+    count_launch();
+}
+
+template void spmv<double>(const DCsr &, const double *, double *, cudaStream_t);
+template void spmv<float>(const DCsr &, const float *, float *, cudaStream_t);
+template void sweep<double>(const DCsr &, const int8_t *, int, const double *, const double *, const double *, double *,
+                            cudaStream_t);
+template void sweep<float>(const DCsr &, const int8_t *, int, const float *, const float *, const float *, float *,
+                           cudaStream_t);
+
+// coarsest level: y = Ainv b (dense, FP64), with the input/output in T
+template <class T>
+__global__ void k_dense_apply(int n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ y) {
+    int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int r = wid; r < n; r += nw) {
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc = fma(Ainv[(size_t)r * n + c], (double)b[c], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) y[r] = (T)acc;
+    }
+}
+
+template <class T>
+void dense_apply(int n, const double *Ainv, const T *b, T *y, cudaStream_t s) {
+    k_dense_apply<T><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(n, Ainv, b, y);
+    count_launch();
+}
+template void dense_apply<double>(int, const double *, const double *, double *, cudaStream_t);
+template void dense_apply<float>(int, const double *, const float *, float *, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// FP64 outer iteration
+// ---------------------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 152 * 4;
+constexpr int RED_THREADS = 256;
+
+// r = b - A x (FP64, one thread per row... group of G lanes), optional float copy, block partials of |r|^2
+template <int G>
+__global__ void __launch_bounds__(RED_THREADS) k_residual(int nr, const int *__restrict__ rp, const int *__restrict__ col,
+                                                          const double *__restrict__ val, const double *__restrict__ b,
+                                                          const double *__restrict__ x, double *__restrict__ r,
+                                                          float *__restrict__ r32, double *__restrict__ part) {
+    __shared__ double red[RED_THREADS / 32];
+    const int gl = threadIdx.x & (G - 1);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    double ss = 0.0;
+    const long long lane = threadIdx.x & 31;
+    for (long long base = tid; base - lane < (long long)nr * G; base += stride) {  // warp-uniform trip count
+        int i = (int)(base / G);
+        double acc = 0.0;
+        if (i < nr)
+            for (int k = __ldg(rp + i) + gl; k < __ldg(rp + i + 1); k += G) acc = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), acc);
+        acc = group_sum<G>(acc);
+        if (i < nr && gl == 0) {
+            double ri = b[i] - acc;
+            r[i] = ri;
+            if (r32) r32[i] = (float)ri;
+            ss = fma(ri, ri, ss);
+        }
+    }
+    ss = warp_sum(ss);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+void residual(const DCsr &A, const double *b, const double *x, double *r, float *r32, double *part, cudaStream_t s) {
+    int G = pick_group<double>(A);
+    switch (G) {
+        case 1: k_residual<1><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+        case 2: k_residual<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+        case 4: k_residual<4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+        case 8: k_residual<8><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+        case 16: k_residual<16><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+        default: k_residual<32><<<RED_BLOCKS, RED_THREADS, 0, s>>>(A.nr, A.rp, A.col, A.val, b, x, r, r32, part); break;
+    }
+    count_launch();
+}
+
+// block partials of sum_i x_i y_i for m vectors x_k (stride ldx) against y: part[k * RED_BLOCKS + block]
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(int n, int m, const double *__restrict__ X, long long ldx,
+                                                          const double *__restrict__ y, double *__restrict__ part) {
+    __shared__ double red[RED_THREADS / 32][32];
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double yi = y[i];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < m) acc[k] = fma(X[k * ldx + i], yi, acc[k]);
+    }
+    for (int k = 0; k < m; ++k) {
+        double v = warp_sum(acc[k]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double t = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        part[threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+    }
+}
+
+// out[k] = sum of the RED_BLOCKS partials of vector k (fixed order); if acc != NULL, acc[k] += out[k]
+__global__ void k_finish(int m, const double *__restrict__ part, double *__restrict__ out, double *__restrict__ acc) {
+    int k = blockIdx.x;
+    if (k >= m) return;
+    __shared__ double red[32];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) t += part[k * RED_BLOCKS + b];
+    t = warp_sum(t);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+        out[k] = u;
+        if (acc) acc[k] += u;
+    }
+}
+
+void multidot(int n, int m, const double *X, long long ldx, const double *y, double *part, double *out, double *acc,
+              cudaStream_t s) {
+    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m, X, ldx, y, part);
+    k_finish<<<m, 256, 0, s>>>(m, part, out, acc);
+    count_launch(2);
+}
+
+void finish_partials(int m, const double *part, double *out, cudaStream_t s) {
+    k_finish<<<m, 256, 0, s>>>(m, part, out, nullptr);
+    count_launch();
+}
+
+// w -= sum_k h_k X_k (h on the device)
+__global__ void k_sub_combo(int n, int m, const double *__restrict__ X, long long ldx, const double *__restrict__ h,
+                            double *__restrict__ w) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = w[i];
+        for (int k = 0; k < m; ++k) v = fma(-h[k], X[k * ldx + i], v);
+        w[i] = v;
+    }
+}
+
+void sub_combo(int n, int m, const double *X, long long ldx, const double *h, double *w, cudaStream_t s) {
+    k_sub_combo<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, m, X, ldx, h, w);
+    count_launch();
+}
+
+// x += sum_k y_k Z_k (y on the device)
+__global__ void k_add_combo(int n, int m, const double *__restrict__ Z, long long ldz, const double *__restrict__ y,
+                            double *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = x[i];
+        for (int k = 0; k < m; ++k) v = fma(y[k], Z[k * ldz + i], v);
+        x[i] = v;
+    }
+}
+
+void add_combo(int n, int m, const double *Z, long long ldz, const double *y, double *x, cudaStream_t s) {
+    k_add_combo<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, m, Z, ldz, y, x);
+    count_launch();
+}
+
+// v_out = v_in / *nrm (nrm = sqrt of a device scalar of squared norm)
+__global__ void k_scale_by_norm(int n, const double *__restrict__ v, const double *__restrict__ nrm2, double *__restrict__ out) {
+    const double n2 = *nrm2;
+    const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = v[i] * inv;
+}
+
+void scale_by_norm(int n, const double *v, const double *nrm2, double *out, cudaStream_t s) {
+    k_scale_by_norm<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, v, nrm2, out);
+    count_launch();
+}
+
+// precision conversions and plain vector updates
+__global__ void k_d2f(int n, const double *__restrict__ a, float *__restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+__global__ void k_f2d(int n, const float *__restrict__ a, double *__restrict__ b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+__global__ void k_axpy_f(int n, const float *__restrict__ e, double *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)e[i];
+}
+__global__ void k_axpy_d(int n, const double *__restrict__ e, double *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += e[i];
+}
+
+void d2f(int n, const double *a, float *b, cudaStream_t s) { k_d2f<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, a, b); count_launch(); }
+void f2d(int n, const float *a, double *b, cudaStream_t s) { k_f2d<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, a, b); count_launch(); }
+void axpy_f(int n, const float *e, double *x, cudaStream_t s) { k_axpy_f<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, e, x); count_launch(); }
+void axpy_d(int n, const double *e, double *x, cudaStream_t s) { k_axpy_d<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, e, x); count_launch(); }
+
+// adjoint gradient on the pattern of A: g[k] = -lambda_i x_j
+__global__ void k_grad_A(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ lam,
+                         const double *__restrict__ x, double *__restrict__ g) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double li = lam[i];
+        for (int k = rp[i]; k < rp[i + 1]; ++k) g[k] = -li * x[col[k]];
+    }
+}
+
+void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s) {
+    k_grad_A<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, A.col, lam, x, g);
+    count_launch();
+}
+
+}  // namespace lair

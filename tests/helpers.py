@@ -1,0 +1,60 @@
+"""Shared test helpers: comparing a GPU hierarchy with an oracle hierarchy."""
+import numpy as np
+
+
+def max_rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.size == 0:
+        return 0.0
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
+
+def row_rel(rp, a, b):
+    """max over rows of max|a - b| / max|b| within the row"""
+    worst = 0.0
+    d = np.abs(np.asarray(a) - np.asarray(b))
+    m = np.abs(np.asarray(b))
+    for i in range(len(rp) - 1):
+        s, e = rp[i], rp[i + 1]
+        if e > s:
+            sc = m[s:e].max()
+            if sc > 0:
+                worst = max(worst, d[s:e].max() / sc)
+            elif d[s:e].max() > 0:
+                worst = np.inf
+    return worst
+
+
+def compare_hierarchies(G, H, val_tol):
+    """Integer structure must match bit for bit; values within val_tol (row-relative).
+    Returns a dict of the largest value differences seen."""
+    ginfo = G.info()
+    glev = len(ginfo)
+    # the oracle reports a level whose splitting produced no coarse points as a level with cf but no R
+    olev = len(H.levels)
+    assert glev == olev, f"levels: gpu {glev} oracle {olev} ({[g['n'] for g in ginfo]} vs {[L.n for L in H.levels]})"
+    worst = {}
+    for l, (gi, L) in enumerate(zip(ginfo, H.levels)):
+        rp, col, val = G.export_csr(l, 0)
+        assert gi["n"] == L.n, f"level {l}: n {gi['n']} vs {L.n}"
+        assert np.array_equal(rp, L.A[0]), f"level {l}: A row pointers differ"
+        assert np.array_equal(col, L.A[1]), f"level {l}: A columns differ"
+        worst[f"A{l}"] = row_rel(rp, val, L.A[2])
+        assert worst[f"A{l}"] <= val_tol, f"level {l}: A values differ by {worst[f'A{l}']:.3e}"
+        if gi["coarsest"]:
+            break
+        cf, strong, lsr, lsp = G.export_cf(l)
+        assert np.array_equal(strong, L.strong), f"level {l}: strength masks differ ({(strong != L.strong).sum()})"
+        assert np.array_equal(cf, L.cf), f"level {l}: C/F splittings differ ({(cf != L.cf).sum()} points)"
+        assert np.array_equal(lsr, L.ls_R), f"level {l}: least-squares flags of R differ"
+        if L.ls_P is not None:
+            assert np.array_equal(lsp, L.ls_P), f"level {l}: least-squares flags of P differ"
+        for which, name, O in ((1, "R", L.R), (2, "P", L.P)):
+            rp, col, val = G.export_csr(l, which)
+            assert np.array_equal(rp, O[0]), f"level {l}: {name} row pointers differ"
+            assert np.array_equal(col, O[1]), f"level {l}: {name} columns differ"
+            worst[f"{name}{l}"] = row_rel(rp, val, O[2])
+            assert worst[f"{name}{l}"] <= val_tol, f"level {l}: {name} values differ by {worst[f'{name}{l}']:.3e}"
+    return worst

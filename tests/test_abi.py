@@ -1,0 +1,55 @@
+"""CPU-side checks of the C ABI: the library loads and exports every declared entry point."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "lair.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lair_[A-Za-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lair_setup", "lair_solve", "lair_adjoint", "lair_grad_A", "lair_precond_apply",
+                     "lair_options_default", "lair_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    lib = ctypes.CDLL(lair.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_options_defaults_and_status_strings():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    o = lair.options()
+    assert o.cf_mode == lair.CF_AUTO and o.distance == 1 and o.theta == 0.25 and o.lump_tol == 1e-3
+    assert o.coarse_max == 256 and o.max_levels == 25 and o.rs_max_n == 8192 and o.fgmres_restart == 30
+    assert lair.lib.lair_status_string(0) == b"LAIR_OK"
+    assert lair.lib.lair_status_string(13) == b"LAIR_ERR_UNSUPPORTED"
+
+
+def test_setup_rejects_bad_arguments_without_a_gpu():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    h = ctypes.c_void_p()
+    assert lair.lib.lair_setup(None, None, ctypes.byref(h)) == 1
+    o = lair.options(distance=3)
+    A = lair.lair_csr(4, 4, None, None, None, 0)
+    st = lair.lib.lair_setup(ctypes.byref(A), ctypes.byref(o), ctypes.byref(h))
+    assert st == 1
+    assert b"distance" in lair.lib.lair_last_error(h)
+    lair.lib.lair_free(h)

@@ -1,0 +1,229 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Integer structure (strength masks, C/F splittings, least-squares flags, patterns of
+R, P and every coarse operator) must be identical; FP64 values within 1e-12 and FP32
+(mixed precision) values within 1e-5 of the row's largest entry. The set-up follows
+the same operation order on both sides, so in practice the values agree bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import oracle as O
+from tests.helpers import compare_hierarchies, max_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-12, 1e-5
+
+
+@pytest.fixture(scope="module")
+def lair():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair as L
+    torch.cuda.init()
+    return L
+
+
+def oracle_kw(kw):
+    m = dict(cf_mode="cf_mode", distance="distance", theta="theta", theta_cf="theta_cf", strength_abs="strength_abs",
+             interp="interp", relax="relax", lump_tol="lump_tol", coarse_max="coarse_max", max_levels="max_levels",
+             block_size="block_size", rs_max_n="rs_max_n", precision="prec")
+    return {m[k]: v for k, v in kw.items()}
+
+
+CASES = {
+    "fd2d64_rs_d1": ("fd2d_64", None, dict(cf_mode=0, distance=1)),
+    "fd2d64_rs_d2": ("fd2d_64", None, dict(cf_mode=0, distance=2)),
+    "fd2d64_pmis_d1": ("fd2d_64", None, dict(cf_mode=1, distance=1)),
+    "fd2d64_auto_onepoint": ("fd2d_64", None, dict(distance=2, interp=1, rs_max_n=1000)),
+    "fd2d64_mixed": ("fd2d_64", None, dict(cf_mode=0, distance=2, precision=1)),
+    "fd2d_diffusive_d2": ("diffusive", None, dict(distance=2)),
+    "fd3d_20_d1": ("fd3d_192", 20, dict(distance=1)),
+    "fd3d_20_mixed": ("fd3d_192", 20, dict(distance=1, precision=1)),
+    "dg_p2_16": ("dg_p2_256", 16, dict(distance=2, interp=1, strength_abs=1, block_size=6, precision=1)),
+    "dg_p2_16_fp64_laip": ("dg_p2_256", 16, dict(distance=2, interp=0, strength_abs=1, block_size=6)),
+    "random_theta_cf": ("random", None, dict(distance=2, theta=0.1, theta_cf=0.3, lump_tol=0.01)),
+}
+
+
+def make(name, scale):
+    if name == "diffusive":
+        return W.fd_adr_2d(40, 1.1, 0.5, 0.3)
+    if name == "random":
+        return W.random_sparse(1500, 6, seed=5)
+    return W.config(name, scale=scale)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hierarchy_matches_oracle(lair, case):
+    name, scale, kw = CASES[case]
+    s = make(name, scale)
+    G = lair.Hierarchy.from_system(s, device=True, **kw)
+    H = O.Hierarchy(s, **oracle_kw(kw))
+    assert H.status == 0
+    tol = TOL32 if kw.get("precision") == 1 else TOL64
+    worst = compare_hierarchies(G, H, tol)
+    assert max(worst.values()) <= tol
+
+
+@pytest.mark.parametrize("case", ["fd2d64_rs_d1", "fd2d64_mixed", "fd3d_20_d1", "dg_p2_16", "fd2d_diffusive_d2"])
+def test_vcycle_matches_oracle(lair, case):
+    import torch
+    name, scale, kw = CASES[case]
+    s = make(name, scale)
+    G = lair.Hierarchy.from_system(s, device=True, **kw)
+    H = O.Hierarchy(s, **oracle_kw(kw))
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        v = rng.uniform(-1, 1, s.n)      # with block scaling the cycle acts on the scaled system on both sides
+        z = G.precond(torch.from_numpy(v).cuda()).cpu().numpy()
+        zo = H.precond(v)
+        tol = TOL32 if kw.get("precision") == 1 else TOL64
+        assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), np.linalg.norm(z - zo) / np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("cycle", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_fd2d_64(lair, cycle, precision):
+    import torch
+    s = W.config("fd2d_64")
+    G = lair.Hierarchy.from_system(s, device=True, cf_mode=0, precision=precision)
+    H = O.Hierarchy(s, cf_mode=O.CF_RS, prec=precision)
+    b = torch.from_numpy(s.b).cuda()
+    x, rep = G.solve(b, tol=1e-10, cycle=cycle)
+    xo, ro = H.solve(s.b, tol=1e-10, cycle=cycle)
+    assert rep.status == 0 and rep.final_rel <= 1e-10
+    A = s.to_scipy()
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(s.b - A @ xg) / np.linalg.norm(s.b) <= 1.5e-10
+    # same preconditioner, same iteration: counts agree and iterates are close
+    assert abs(rep.iters - ro["iters"]) <= 1
+    assert np.linalg.norm(xg - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_host_and_device_buffers_agree(lair):
+    import torch
+    s = W.config("fd2d_64", scale=40)
+    Gd = lair.Hierarchy.from_system(s, device=True)
+    Gh = lair.Hierarchy.from_system(s, device=False)
+    xd, rd = Gd.solve(torch.from_numpy(s.b).cuda(), tol=1e-10)
+    xh, rh = Gh.solve(s.b.copy(), tol=1e-10)
+    assert rd.iters == rh.iters
+    np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+
+
+def test_single_level_direct_solve(lair):
+    s = W.config("fd2d_64", scale=12)          # n = 144 <= coarse_max: the hierarchy is one dense level
+    G = lair.Hierarchy.from_system(s)
+    assert len(G.info()) == 1
+    x, rep = G.solve(s.b.copy(), tol=1e-12, cycle=0)
+    assert rep.iters == 1 and rep.final_rel <= 1e-12
+
+
+def test_least_squares_branch_matches_oracle(lair):
+    """A C point whose two F neighbours have proportional rows on the neighbourhood gives a
+    singular local system (Sec. 3.1 footnote): minimum-norm least squares on both sides."""
+    n = 9
+    A = np.eye(n) * 4.0
+    # C point 0 depends strongly on F points 1 and 2; rows 1 and 2 restricted to {1, 2} are equal
+    A[0, 1] = A[0, 2] = -1.0
+    A[1, 1], A[1, 2] = 2.0, 2.0
+    A[2, 1], A[2, 2] = 2.0, 2.0
+    A[1, 0], A[2, 0] = -0.5, -0.7          # rows differ outside the neighbourhood: A itself is nonsingular
+    for i in range(3, n):
+        A[i, i - 1] = -1.0
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    s = W.CsrSystem(n, M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.copy(), np.ones(n))
+    cf = np.array([1, 0, 0, 1, 0, 1, 0, 1, 0], np.int8)
+    kw = dict(distance=1, max_levels=2, coarse_max=2, lump_tol=0.0, theta=0.1, theta_cf=0.1)
+    G = lair.Hierarchy.from_system(s, cf_user=cf, **kw)
+    H = O.Hierarchy(s, cf_user=cf, **oracle_kw(kw))
+    assert H.levels[0].ls_R[0] == 1
+    compare_hierarchies(G, H, TOL64)
+
+
+@pytest.mark.parametrize("bad,code", [("unsorted", 3), ("duplicate", 4), ("zero_diag", 5), ("bad_rowptr", 2)])
+def test_invalid_input_reports_status(lair, bad, code):
+    s = W.config("fd2d_64", scale=8)
+    rp, col, val = s.row_ptr.copy(), s.col.copy(), s.val.copy()
+    if bad == "unsorted":
+        col[rp[5]], col[rp[5] + 1] = col[rp[5] + 1], col[rp[5]]
+    elif bad == "duplicate":
+        col[rp[5] + 1] = col[rp[5]]
+    elif bad == "zero_diag":
+        k = rp[5] + list(col[rp[5]:rp[6]]).index(5)
+        val[k] = 0.0
+    else:
+        rp[-1] += 1
+    with pytest.raises(lair.LairError) as e:
+        lair.Hierarchy(rp, col, val)
+    assert e.value.status == code
+
+
+def test_not_converged_status(lair):
+    s = W.config("fd2d_64")
+    G = lair.Hierarchy.from_system(s)
+    x, rep = G.solve(s.b.copy(), tol=1e-14, cycle=0, max_iter=2)
+    assert rep.status == 7 and rep.iters == 2
+    with pytest.raises(lair.LairError):
+        G.solve(s.b.copy(), tol=1e-14, cycle=0, max_iter=2, raise_on_nc=True)
+
+
+def test_adjoint_gradients(lair):
+    """grad_b = A^{-T} g and grad_A = -lambda x^T on the pattern, against dense FP64 algebra and
+    central finite differences of J(x) = 1/2 ||x - x*||^2."""
+    import torch
+    from paper_1708_06065_gb300 import autograd
+    s = W.config("adjoint_fd2d_512", scale=32)
+    xs = s.meta["x_star"]
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    col = torch.from_numpy(s.col).cuda()
+    vals = torch.from_numpy(s.val).cuda().requires_grad_(True)
+    b = torch.from_numpy(s.b).cuda().requires_grad_(True)
+    xstar = torch.from_numpy(xs).cuda()
+    x = autograd.solve(rp, col, vals, b, tol=1e-12)
+    J = 0.5 * ((x - xstar) ** 2).sum()
+    J.backward()
+    A = s.to_scipy().toarray()
+    xd = np.linalg.solve(A, s.b)
+    lam = np.linalg.solve(A.T, xd - xs)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), lam, rtol=0, atol=1e-8 * np.abs(lam).max())
+    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+    gA = -lam[rows] * xd[s.col]
+    np.testing.assert_allclose(vals.grad.cpu().numpy(), gA, rtol=0, atol=1e-8 * np.abs(gA).max())
+    # central differences along random directions of b and of the nonzeros of A
+    rng = np.random.default_rng(3)
+
+    def Jf(v, bb):
+        Ad = sp.csr_matrix((v, s.col, s.row_ptr), shape=(s.n, s.n)).toarray()
+        xx = np.linalg.solve(Ad, bb)
+        return 0.5 * np.sum((xx - xs) ** 2)
+
+    for _ in range(4):
+        db = rng.standard_normal(s.n)
+        dv = rng.standard_normal(len(s.val)) * np.abs(s.val)
+        h = 1e-6
+        fd_b = (Jf(s.val, s.b + h * db) - Jf(s.val, s.b - h * db)) / (2 * h)
+        fd_v = (Jf(s.val + h * dv, s.b) - Jf(s.val - h * dv, s.b)) / (2 * h)
+        assert fd_b == pytest.approx(float(b.grad.cpu().numpy() @ db), rel=1e-5)
+        assert fd_v == pytest.approx(float(vals.grad.cpu().numpy() @ dv), rel=1e-5)
+
+
+def test_adjoint_hierarchy_matches_oracle_on_transpose(lair):
+    s = W.config("fd2d_64", scale=40)
+    G = lair.Hierarchy.from_system(s)
+    g = np.random.default_rng(2).uniform(-1, 1, s.n)
+    lam, rep = G.adjoint(g, tol=1e-10)
+    trp, tcol, tval = O.transpose(s)
+    st = W.CsrSystem(s.n, trp, tcol, tval, g)
+    H = O.Hierarchy(st)
+    lo, ro = H.solve(g, tol=1e-10)
+    assert rep.status == 0 and abs(rep.iters - ro["iters"]) <= 1
+    assert np.linalg.norm(lam - lo) <= 1e-8 * np.linalg.norm(lo)
