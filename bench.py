@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the lAIR hot path on one GB300 (or N independent replicas).
+
+Workload (default): the 2D DG-P2 recirculating-advection system on a 256 x 256
+square mesh cut into triangles (786,432 unknowns, 6 per element), one backward-Euler
+step dt = h, block-diagonally scaled; lAIR distance 2 with one-point interpolation,
+abs-value strength theta 0.25; FP32 V-cycle inside FP64 FGMRES(30) to a relative
+residual of 1e-8. A step is set-up + solve of that system (the whole hot path).
+
+Metric: unknowns/s = n / (t_setup + t_solve), mixed precision, with the plain FP64
+path measured the same way beside it. `value` is timed with CUDA events on the
+library's stream with the matrix and right-hand side already in HBM; `e2e` goes
+through the same C ABI with pinned host buffers, copies included.
+
+--impl reference times the CPU oracle (plain single-threaded FP64 C) on a bounded
+sample of the same workload family (the 64 x 64 mesh of the same discretisation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns/s to 1e-8 rel. residual (setup+solve), mixed vs FP64; % HBM peak"
+WORKLOADS = {
+    "dg_p2_256": dict(
+        desc="2D upwind DG-P2, 256x256 squares x 2 triangles (n=786432), recirculating velocity, backward Euler dt=h, "
+             "block-diagonal scaling; lAIR distance 2, one-point P, |a| strength 0.25; FP32 cycle in FP64 FGMRES(30), tol 1e-8",
+        opts=dict(distance=2, interp=1, strength_abs=1, block_size=6), tol=1e-8, sample_scale=64),
+    "fd3d_192": dict(
+        desc="3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1; "
+             "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
+        opts=dict(distance=1), tol=1e-8, sample_scale=40),
+}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lair", choices=["lair", "reference"])
+    p.add_argument("--workload", default="dg_p2_256", choices=sorted(WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------------------
+# distributed plumbing (replicas: every rank solves its own copy; only timing is reduced)
+# ----------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([float(v)])
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6], swt=f[7],
+                                 swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("swp", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r["smax"] for r in rows), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
+    import workloads as W
+    from oracle import oracle as O
+    wl = WORKLOADS[workload]
+    s = W.config(workload, scale=wl["sample_scale"])
+    kw = dict(wl["opts"])
+    okw = dict(distance=kw["distance"], prec=1)
+    if "interp" in kw:
+        okw["interp"] = kw["interp"]
+    if "strength_abs" in kw:
+        okw["strength_abs"] = kw["strength_abs"]
+    if "block_size" in kw:
+        okw["block_size"] = kw["block_size"]
+    O.build()
+    reps, total, iters = 0, 0.0, 0
+    while reps < min_reps or (total < budget_s and reps < max_reps):
+        t0 = time.perf_counter()
+        H = O.Hierarchy(s, **okw)
+        x, rep = H.solve(s.b, tol=wl["tol"], cycle=1)
+        total += time.perf_counter() - t0
+        assert rep["status"] == 0, rep
+        iters = rep["iters"]
+        H.close()
+        reps += 1
+    return dict(n=s.n, reps=reps, seconds=total, value=s.n * reps / total, iters=iters,
+                sample=f"{workload} family at mesh side {wl['sample_scale']} (n={s.n}), set-up + solve, mixed mode, "
+                       f"{reps} repetitions, {total:.1f} s")
+
+
+def reference_arm(args, dist):
+    if dist.rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, budget_s=0.0)
+    times = []
+    n = None
+    for _ in range(args.steps):
+        r = oracle_sample(args.workload, budget_s=0.0)
+        times.append(r["seconds"])
+        n = r["n"]
+        sample = r["sample"]
+    t = sum(times) / len(times)
+    v = n / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 local solves and cycle)", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "reference_sample": sample},
+            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                             "sample": sample.rsplit(",", 2)[0]},
+            "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(kernel, workload):
+    """ncu dram bytes per launch from the committed profile summary, if one matches."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == workload:
+                return float(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        reference_arm(args, dist)
+        return
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import workloads as W
+    from paper_1708_06065_gb300 import lair
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    wl = WORKLOADS[args.workload]
+    s = W.config(args.workload)
+    n, nnz = s.n, s.nnz
+    stream = torch.cuda.Stream(device=dev)
+    rp = torch.from_numpy(s.row_ptr).to(dev)
+    col = torch.from_numpy(s.col).to(dev)
+    val = torch.from_numpy(s.val).to(dev)
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def run_steps(k, precision, timed, host=None):
+        """k set-up + solve steps; returns per-step ms (CUDA events on the library stream) and stats."""
+        times, its, rels, launches = [], [], [], 0
+        timers = {}
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))           # evict L2 between steps (not timed)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            if host is None:
+                G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
+                x.zero_() if False else None
+                xx = torch.zeros(n, dtype=torch.float64, device=dev) if False else x
+                with torch.cuda.stream(stream):
+                    xx.zero_()
+                _, rep = G.solve(b, xx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
+            else:
+                hrp, hcol, hval, hb, hx = host
+                hx.zero_()
+                G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=1, **wl["opts"])
+                _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
+            ev1.record(stream)
+            ev1.synchronize()
+            if rep.status != 0:
+                raise RuntimeError(f"solve did not converge: {rep}")
+            times.append(ev0.elapsed_time(ev1))
+            its.append(rep.iters)
+            rels.append(rep.final_rel)
+            launches += G.launches
+            for name, (cnt, ms, byt) in G.timers().items():
+                t = timers.setdefault(name, [0, 0.0, byt])
+                t[0] += cnt
+                t[1] += ms
+            G.close()
+        return times, its, rels, launches, timers
+
+    # ---- mixed precision (the headline), device-resident inputs
+    run_steps(args.warmup, lair.MIXED, False)
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_mixed, it_mixed, rel_mixed, launches, timers = run_steps(args.steps, lair.MIXED, True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist.barrier()
+    ms_mixed = dist.max(sum(t_mixed) / len(t_mixed))
+
+    # ---- plain FP64 path, same protocol
+    run_steps(1, lair.FP64, False)
+    t64, it64, rel64, _, _ = run_steps(args.steps, lair.FP64, True)
+    ms64 = dist.max(sum(t64) / len(t64))
+
+    # ---- end to end through host buffers (pinned), mixed
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        host = (pin(s.row_ptr), pin(s.col), pin(s.val), pin(s.b), torch.zeros(n, dtype=torch.float64).pin_memory())
+        run_steps(1, lair.MIXED, False, host=host)
+        te, _, _, _, _ = run_steps(args.steps, lair.MIXED, True, host=host)
+        mse = dist.max(sum(te) / len(te))
+        e2e = {"value": dist.world * n / (mse / 1e3), "unit": "unknowns/s",
+               "h2d_bytes_per_step": int((n + 1) * 8 + nnz * 4 + nnz * 8 + 2 * n * 8),
+               "d2h_bytes_per_step": int(n * 8), "ms_per_step": mse}
+
+    # ---- roofline of the dominant timed kernel (largest accumulated time)
+    peak, peak_src = load_peaks()
+    kern = [(v[1], k, v) for k, v in timers.items() if k != "vcycle" and v[0] > 0]
+    roof = None
+    if kern:
+        _, name, (cnt, ms, byt) = max(kern)
+        avg_ms = ms / cnt
+        achieved = byt / (avg_ms * 1e-3) / 1e9
+        traffic = load_traffic(name, args.workload)
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "bytes_per_launch": byt, "avg_launch_us": 1e3 * avg_ms,
+                "launches": cnt, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                "all_timed": {k: {"launches": v[0], "avg_us": 1e3 * v[1] / max(v[0], 1),
+                                  "GBps": (v[2] / (v[1] / max(v[0], 1) * 1e-3) / 1e9) if v[2] and v[1] else None}
+                              for k, v in timers.items()}}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and dist.rank == 0 and dist.world == 1:
+        r = oracle_sample(args.workload, budget_s=12.0)
+        cpu = {"value": r["value"], "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": r["sample"]}
+
+    value = dist.world * n / (ms_mixed / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "unknowns/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 cycle + f64 outer (mixed)", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "nnz": nnz, "parallelism": "replicas",
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB written before every step (untimed); matrix alone is "
+                         f"{(nnz * 12 + n * 8) / 1e6:.0f} MB > 129 MB L2"},
+        "mixed": {"value": value, "ms_per_step": ms_mixed, "iters": it_mixed, "final_rel": max(rel_mixed)},
+        "fp64": {"value": dist.world * n / (ms64 / 1e3), "ms_per_step": ms64, "iters": it64, "final_rel": max(rel64)},
+        "mixed_over_fp64": ms64 / ms_mixed,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

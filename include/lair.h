@@ -47,9 +47,11 @@ typedef enum {
     LAIR_ERR_UNSUPPORTED = 13       /* an input beyond a documented limit */
 } lair_status;
 
-/* C/F splitting: classical Ruge-Stueben first pass, no second pass (Sec. 4);
- * PMIS (hashed-weight parallel independent set); a user array on level 0;
- * AUTO = first pass when the level has at most rs_max_n points, PMIS above. */
+/* C/F splitting: classical Ruge-Stueben first pass, no second pass (Sec. 4), on the
+ * whole level (RS, at most 32768 points); PMIS (hashed-weight parallel independent
+ * set); a user array on level 0; AUTO = the first pass run independently on
+ * consecutive index blocks of rs_block points (exactly RS on levels that fit in one
+ * block), in parallel over blocks. */
 typedef enum { LAIR_CF_RS = 0, LAIR_CF_PMIS = 1, LAIR_CF_USER = 2, LAIR_CF_AUTO = 3 } lair_cf_mode;
 
 /* Interpolation P = [W; I] (Eq. (2.2)): approximate ideal interpolation
@@ -96,10 +98,11 @@ typedef struct {
     int coarse_max;           /* direct solve once a level has <= coarse_max unknowns */
     int max_levels;
     int block_size;           /* > 1: scale A and b by the inverse block diagonal first (DG, Sec. 4.2.1) */
-    int rs_max_n;             /* AUTO: largest level split by the first pass (<= 32768) */
+    int rs_block;             /* AUTO: index-block size of the blocked first pass (1..32768) */
     uint64_t pmis_seed;
     int fgmres_restart;
     void *stream;             /* cudaStream_t, or NULL (see above); never the legacy default stream itself */
+    int timing;               /* 1: record CUDA-event timings of the main kernels (lair_kernel_timers) */
 } lair_options;
 
 typedef struct {
@@ -125,7 +128,7 @@ typedef struct {
 typedef struct lair_handle lair_handle;
 
 /* Fill *o with the defaults (AUTO splitting, distance 1, theta 0.25, lAIP, F-F-C,
- * lumping 1e-3 on coarse levels, FP64, coarse_max 256, 25 levels, rs_max_n 8192,
+ * lumping 1e-3 on coarse levels, FP64, coarse_max 128, 25 levels, rs_block 4096,
  * FGMRES restart 30). */
 lair_status lair_options_default(lair_options *o);
 
@@ -173,6 +176,21 @@ lair_status lair_export_csr(const lair_handle *h, int level, int which, int64_t 
  * the restriction and interpolation solves (nc entries each). NULL skips. */
 lair_status lair_export_cf(const lair_handle *h, int level, int8_t *cf, uint8_t *strong,
                            uint8_t *ls_R, uint8_t *ls_P);
+
+/* Timing of one kind of kernel launch, accumulated since the handle was created:
+ * CUDA events recorded on the launching stream immediately before and after each
+ * launch (inside the captured cycle graph for cycle kernels). bytes_per_launch is
+ * the algorithmic byte count of one launch (matrix entries read once, vectors read
+ * or written once). Filled only when lair_options.timing was set at set-up. */
+typedef struct {
+    char name[40];
+    int64_t launches;
+    double total_ms;
+    double bytes_per_launch;
+} lair_kernel_timer;
+
+/* Copy up to cap timers into out; *count receives the number available. */
+lair_status lair_kernel_timers(const lair_handle *h, lair_kernel_timer *out, int cap, int *count);
 
 /* Number of device kernels the library has launched since the handle was created. */
 int64_t lair_kernel_launches(const lair_handle *h);

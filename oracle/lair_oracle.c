@@ -10,8 +10,8 @@
  * Everything is FP64 unless a function says otherwise. The steps follow the
  * paper's order and notation:
  *   strength of connection ........ Sec. 4, definition of N_i (hard minimum)
- *   C/F splitting .................. Sec. 4 (classical first pass, no second pass);
- *                                    PMIS as the parallel alternative
+ *   C/F splitting .................. Sec. 4 (classical first pass, no second pass),
+ *                                    also run independently in index blocks; PMIS
  *   restriction neighbourhoods ..... Sec. 3.1 (distance one/two, F-F-C only, Sec. 4)
  *   local systems .................. Sec. 3.1, Eq. (3.1) johnair and Eq. (3.2) system,
  *                                    least squares when singular (Sec. 3.1 footnote)
@@ -51,7 +51,7 @@
 /* options (mirrors the public option set; defined independently)            */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-    int cf_mode;           /* 0 RS, 1 PMIS, 2 USER (level 0 only), 3 AUTO (RS if n <= rs_max_n) */
+    int cf_mode;           /* 0 RS, 1 PMIS, 2 USER (level 0 only), 3 AUTO (first pass in blocks of rs_block) */
     const int8_t *cf_user; /* level-0 splitting for USER mode (1 = C, 0 = F) */
     int distance;          /* 1 or 2 */
     double theta;          /* strength threshold for R/P neighbourhoods */
@@ -65,7 +65,7 @@ typedef struct {
     int coarse_max;        /* direct solve when n <= coarse_max */
     int max_levels;
     int block_size;        /* >1: scale by the inverse block diagonal first */
-    int rs_max_n;
+    int rs_block;          /* AUTO: index-block size of the blocked first pass */
     uint64_t pmis_seed;
 } ora_opts;
 
@@ -244,6 +244,49 @@ static heapent heap_pop(oheap *h) {
         i = m;
     }
     return top;
+}
+
+/* The first pass restricted to the index block [b0, b1): lambda and the updates only
+ * count strong connections with both ends in the block; points without any strong
+ * connection in the whole graph start as F. With one block covering all points this is
+ * the classical first pass above. */
+static void cf_rs_block(const ograph *S, const ograph *ST, int64_t b0, int64_t b1, int8_t *cf, int64_t *lam) {
+    oheap h = {0};
+    for (int64_t i = b0; i < b1; ++i) {
+        int64_t l = 0;
+        for (int64_t p = ST->rp[i]; p < ST->rp[i + 1]; ++p) l += (ST->col[p] >= b0 && ST->col[p] < b1);
+        lam[i] = l;
+        int isolated = (S->rp[i + 1] == S->rp[i]) && (ST->rp[i + 1] == ST->rp[i]);
+        cf[i] = isolated ? CF_F : CF_U;
+        if (!isolated) heap_push(&h, (heapent){lam[i], i});
+    }
+    while (h.len > 0) {
+        heapent e = heap_pop(&h);
+        int64_t i = e.idx;
+        if (cf[i] != CF_U || lam[i] != e.lam) continue;
+        cf[i] = CF_C;
+        for (int64_t p = ST->rp[i]; p < ST->rp[i + 1]; ++p) {
+            int64_t j = ST->col[p];
+            if (j < b0 || j >= b1 || cf[j] != CF_U) continue;
+            cf[j] = CF_F;
+            for (int64_t q = S->rp[j]; q < S->rp[j + 1]; ++q) {
+                int64_t k = S->col[q];
+                if (k >= b0 && k < b1 && cf[k] == CF_U) { lam[k] += 1; heap_push(&h, (heapent){lam[k], k}); }
+            }
+        }
+        for (int64_t p = S->rp[i]; p < S->rp[i + 1]; ++p) {
+            int64_t k = S->col[p];
+            if (k >= b0 && k < b1 && cf[k] == CF_U) { lam[k] -= 1; heap_push(&h, (heapent){lam[k], k}); }
+        }
+    }
+    free(h.a);
+}
+
+static void cf_rs_blocked(const ograph *S, const ograph *ST, int64_t B, int8_t *cf) {
+    int64_t n = S->n;
+    int64_t *lam = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t b0 = 0; b0 < n; b0 += B) cf_rs_block(S, ST, b0, b0 + B < n ? b0 + B : n, cf, lam);
+    free(lam);
 }
 
 static void cf_rs(const ograph *S, const ograph *ST, int8_t *cf) {
@@ -1065,10 +1108,10 @@ void ora_opts_default(ora_opts *o) {
     o->lump_tol = 1e-3;
     o->lump_level0 = 0;
     o->prec = 0;
-    o->coarse_max = 256;
+    o->coarse_max = 128;
     o->max_levels = 25;
     o->block_size = 0;
-    o->rs_max_n = 8192;
+    o->rs_block = 4096;
     o->pmis_seed = 0x5eedULL;
 }
 
@@ -1091,8 +1134,8 @@ static int coarsen_level(ohier *H, int l, int *is_last) {
     if (l == 0 && o->cf_mode == 2 && o->cf_user) {
         for (int64_t i = 0; i < n; ++i) L->cf[i] = o->cf_user[i] ? CF_C : CF_F;
     } else {
-        int use_rs = (o->cf_mode == 0) || (o->cf_mode != 1 && n <= o->rs_max_n);
-        if (use_rs) cf_rs(&Scf, &STcf, L->cf);
+        if (o->cf_mode == 0) cf_rs(&Scf, &STcf, L->cf);
+        else if (o->cf_mode != 1) cf_rs_blocked(&Scf, &STcf, o->rs_block, L->cf);
         else cf_pmis(&Scf, &STcf, o->pmis_seed + (uint64_t)l, L->cf);
     }
     L->cidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -1496,7 +1539,9 @@ void ora_cf_split(int64_t n, const int64_t *rp, const int32_t *col, const uint8_
     ograph S, ST;
     graph_from_mask(n, rp, col, mask, &S);
     graph_transpose(&S, &ST);
-    if (mode == 0) cf_rs(&S, &ST, cf); else cf_pmis(&S, &ST, seed, cf);
+    if (mode == 0) cf_rs(&S, &ST, cf);
+    else if (mode == 1) cf_pmis(&S, &ST, seed, cf);
+    else cf_rs_blocked(&S, &ST, (int64_t)seed, cf);   /* mode 3: blocked first pass, block size = seed */
     graph_free(&S); graph_free(&ST);
 }
 

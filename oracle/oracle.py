@@ -40,7 +40,7 @@ class Opts(C.Structure):
         ("theta", C.c_double), ("theta_cf", C.c_double), ("strength_abs", C.c_int),
         ("interp", C.c_int), ("relax", C.c_int), ("lump_tol", C.c_double), ("lump_level0", C.c_int),
         ("prec", C.c_int), ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
-        ("rs_max_n", C.c_int), ("pmis_seed", C.c_uint64),
+        ("rs_block", C.c_int), ("pmis_seed", C.c_uint64),
     ]
 
 
@@ -211,6 +211,7 @@ def strength(A, theta, absmode=False):
 
 
 def cf_split(A, mask, mode=CF_RS, seed=0x5EED):
+    """mode CF_RS, CF_PMIS (seed = hash seed) or CF_AUTO (blocked first pass, seed = block size)."""
     rp, col, _ = _csr_arrays(A)
     mask = np.ascontiguousarray(mask, np.uint8)
     cf = np.zeros(A.n, np.int8)

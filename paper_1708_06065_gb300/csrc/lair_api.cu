@@ -46,6 +46,7 @@ struct Level {
     int xfinal = 0;         // which x buffer holds the cycle's result on this level
     bool coarsest = false;
     double *Ainv = nullptr;
+    long long nF = 0, nnzF = 0, nC = 0, nnzC = 0;   // rows and entries by kind (for byte counts)
 };
 
 struct Hier {
@@ -79,7 +80,14 @@ struct lair_handle {
     int fg_m = 0;
     std::string err;
     long long launches = 0;
-    int in_setup = 0;
+    // kernel timing (options.timing)
+    struct Timer { std::string name; long long launches = 0; double ms = 0.0; double bytes = 0.0; };
+    struct Pending { int slot; cudaEvent_t a, b; };
+    std::vector<Timer> timers;
+    std::vector<Pending> pending;        // events recorded by direct launches, read at the next sync
+    std::vector<Pending> graph_events;   // events inside the captured cycle graph
+    std::vector<cudaEvent_t> ev_pool;
+    bool graph_pending = false;
 };
 
 namespace lair {
@@ -140,9 +148,12 @@ struct Temps {
     }
 };
 
+static void flush_timers(lair_handle *h);
+
 static lair_status sync_status(lair_handle *h) {
     CU(cudaMemcpyAsync(h->h_int, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CU(cudaStreamSynchronize(h->s));
+    flush_timers(h);
     int st = h->h_int[0];
     if (st != 0) {
         CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
@@ -156,6 +167,73 @@ static lair_status read_ints(lair_handle *h, const int *d, int n, int *out) {
     TRY(sync_status(h));
     memcpy(out, h->h_int + 1, sizeof(int) * n);
     return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// kernel timers: events around selected launches, read back at the next host sync
+// ---------------------------------------------------------------------------------------
+static int timer_slot(lair_handle *h, const std::string &name, double bytes) {
+    for (size_t i = 0; i < h->timers.size(); ++i)
+        if (h->timers[i].name == name) return (int)i;
+    lair_handle::Timer t;
+    t.name = name;
+    t.bytes = bytes;
+    h->timers.push_back(t);
+    return (int)h->timers.size() - 1;
+}
+
+static cudaEvent_t get_event(lair_handle *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// begin/end around one launch; in_graph: the events become nodes of the graph being captured
+static int tbegin(lair_handle *h, const std::string &name, double bytes, bool in_graph = false) {
+    if (!h->o.timing) return -1;
+    int slot = timer_slot(h, name, bytes);
+    lair_handle::Pending p{slot, get_event(h), get_event(h)};
+    cudaEventRecord(p.a, h->s);
+    if (in_graph) h->graph_events.push_back(p);
+    else h->pending.push_back(p);
+    return slot;
+}
+
+static void tend(lair_handle *h, int slot, bool in_graph = false) {
+    if (slot < 0) return;
+    auto &v = in_graph ? h->graph_events : h->pending;
+    cudaEventRecord(v.back().b, h->s);
+}
+
+// call only after the stream has been synchronised
+static void flush_timers(lair_handle *h) {
+    if (!h->o.timing) return;
+    for (auto &p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->timers[p.slot].ms += ms;
+            h->timers[p.slot].launches += 1;
+        }
+        h->ev_pool.push_back(p.a);
+        h->ev_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    if (h->graph_pending) {
+        for (auto &p : h->graph_events) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                h->timers[p.slot].ms += ms;
+                h->timers[p.slot].launches += 1;
+            }
+        }
+        h->graph_pending = false;
+    }
+    cudaGetLastError();
 }
 
 // exclusive scan of cnt[0..n) into out[0..n] (out[n] = total); returns the total
@@ -373,12 +451,13 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         CU(cudaMemcpyAsync(L.cf, cf_user, (size_t)n, cudaMemcpyHostToDevice, h->s));
         normalize_cf(n, L.cf, h->s);
     } else {
-        bool use_rs = o.cf_mode == LAIR_CF_RS || (o.cf_mode != LAIR_CF_PMIS && n <= o.rs_max_n);
-        if (use_rs) {
-            if (n > RS_MAX_N)
-                return fail(h, LAIR_ERR_UNSUPPORTED, "first-pass splitting is limited to %d points (level %d has %d)",
+        if (o.cf_mode != LAIR_CF_PMIS) {
+            // RS: the exact first pass (one block); AUTO: the first pass in blocks of rs_block points
+            int B = o.cf_mode == LAIR_CF_RS ? n : o.rs_block;
+            if (B > RS_MAX_N)
+                return fail(h, LAIR_ERR_UNSUPPORTED, "the first pass runs on at most %d points at once (level %d has %d)",
                             RS_MAX_N, l, n);
-            CU(launch_rs(n, Scf, STcf, L.cf, h->status, h->s));
+            CU(launch_rs(n, B, Scf, STcf, L.cf, h->status, h->s));
         } else {
             double *w;
             int8_t *newc;
@@ -492,6 +571,17 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
     TRY(dalloc(h, &L.dinv, (size_t)n));
     if (fp32) TRY(dalloc(h, &L.dinv32, (size_t)n));
     launch_dinv(L.A, L.dinv, L.dinv32, h->status, h->s);
+    if (h->o.timing && L.cf && l == 0) {
+        Temps t(h);
+        unsigned long long *st;
+        TRY(t.get(&st, 4));
+        CU(cudaMemsetAsync(st, 0, 4 * sizeof(unsigned long long), h->s));
+        cf_stats(L.A, L.cf, st, h->s);
+        unsigned long long hs[4];
+        CU(cudaMemcpyAsync(hs, st, sizeof hs, cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        L.nF = (long long)hs[0]; L.nnzF = (long long)hs[1]; L.nC = (long long)hs[2]; L.nnzC = (long long)hs[3];
+    }
     if (fp32) {
         TRY(dalloc(h, &L.A.val32, (size_t)L.A.nnz));
         launch_to_f32(L.A.nnz, L.A.val, L.A.val32, h->s);
@@ -508,48 +598,53 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
 
 static const int relax_seq[3][3] = {{CF_F, CF_F, CF_C}, {CF_F, CF_C, CF_F}, {CF_F, CF_F, -1}};
 
-template <class T>
-static void record_cycle(lair_handle *h, Hier &H, int l);
+template <class T> struct CycleBufs;
+template <> struct CycleBufs<double> {
+    static double *b(Level &L) { return L.b64; }
+    static double *x(Level &L, int k) { return L.x64[k]; }
+    static const double *dinv(Level &L) { return L.dinv; }
+};
+template <> struct CycleBufs<float> {
+    static float *b(Level &L) { return L.b32; }
+    static float *x(Level &L, int k) { return L.x32[k]; }
+    static const float *dinv(Level &L) { return L.dinv32; }
+};
 
-template <>
-void record_cycle<double>(lair_handle *h, Hier &H, int l) {
-    Level &L = H.lev[l];
-    if (L.coarsest) {
-        dense_apply<double>(L.A.nr, L.Ainv, L.b64, L.x64[0], h->s);
-        L.xfinal = 0;
-        return;
-    }
-    Level &C = H.lev[l + 1];
-    spmv<double>(L.R, L.b64, C.b64, h->s);
-    record_cycle<double>(h, H, l + 1);
-    spmv<double>(L.P, C.x64[C.xfinal], L.x64[0], h->s);
-    int cur = 0;
-    for (int k = 0; k < 3; ++k) {
-        int tg = relax_seq[h->o.relax][k];
-        if (tg < 0) break;
-        sweep<double>(L.A, L.cf, tg, L.dinv, L.b64, L.x64[cur], L.x64[1 - cur], h->s);
-        cur ^= 1;
-    }
-    L.xfinal = cur;
+// algorithmic bytes (matrix entries read once, vectors read or written once)
+static double bytes_sweep(const Level &L, int target, double sv) {
+    double nT = target == CF_F ? (double)L.nF : (double)L.nC, nnzT = target == CF_F ? (double)L.nnzF : (double)L.nnzC;
+    return nnzT * (sv + 4.0) + nT * (4.0 + 3.0 * sv) + (double)L.A.nr * sv;
+}
+static double bytes_spmv(const DCsr &M, double sv) {
+    return (double)M.nnz * (sv + 4.0) + (double)M.nr * (4.0 + sv) + (double)M.nc * sv;
 }
 
-template <>
-void record_cycle<float>(lair_handle *h, Hier &H, int l) {
+template <class T>
+static void record_cycle(lair_handle *h, Hier &H, int l) {
+    using B = CycleBufs<T>;
+    const double sv = sizeof(T);
     Level &L = H.lev[l];
+    const bool tm = l == 0;
     if (L.coarsest) {
-        dense_apply<float>(L.A.nr, L.Ainv, L.b32, L.x32[0], h->s);
+        dense_apply<T>(L.A.nr, L.Ainv, B::b(L), B::x(L, 0), h->s);
         L.xfinal = 0;
         return;
     }
     Level &C = H.lev[l + 1];
-    spmv<float>(L.R, L.b32, C.b32, h->s);
-    record_cycle<float>(h, H, l + 1);
-    spmv<float>(L.P, C.x32[C.xfinal], L.x32[0], h->s);
+    int t = tm ? tbegin(h, "L0_restrict", bytes_spmv(L.R, sv), true) : -1;
+    spmv<T>(L.R, B::b(L), B::b(C), h->s);
+    if (tm) tend(h, t, true);
+    record_cycle<T>(h, H, l + 1);
+    t = tm ? tbegin(h, "L0_interp", bytes_spmv(L.P, sv), true) : -1;
+    spmv<T>(L.P, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    if (tm) tend(h, t, true);
     int cur = 0;
     for (int k = 0; k < 3; ++k) {
         int tg = relax_seq[h->o.relax][k];
         if (tg < 0) break;
-        sweep<float>(L.A, L.cf, tg, L.dinv32, L.b32, L.x32[cur], L.x32[1 - cur], h->s);
+        t = tm ? tbegin(h, tg == CF_F ? "L0_sweep_F" : "L0_sweep_C", bytes_sweep(L, tg, sv), true) : -1;
+        sweep<T>(L.A, L.cf, tg, B::dinv(L), B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
+        if (tm) tend(h, t, true);
         cur ^= 1;
     }
     L.xfinal = cur;
@@ -561,8 +656,11 @@ static lair_status capture_cycle(lair_handle *h, Hier &H) {
     g_launches = &dummy;
     cudaGraph_t g;
     CU(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    h->graph_events.clear();
+    int tall = tbegin(h, "vcycle", 0.0, true);
     if (h->o.precision == LAIR_MIXED) record_cycle<float>(h, H, 0);
     else record_cycle<double>(h, H, 0);
+    tend(h, tall, true);
     cudaError_t e = cudaStreamEndCapture(h->s, &g);
     g_launches = saved;
     CU(e);
@@ -666,11 +764,13 @@ static lair_status precond(lair_handle *h, Hier &H, const double *v, double *z) 
         d2f(n, v, L.b32, h->s);
         CU(cudaGraphLaunch(H.graph, h->s));
         count_launch(H.graph_nodes);
+        h->graph_pending = h->o.timing;
         f2d(n, L.x32[L.xfinal], z, h->s);
     } else {
         CU(cudaMemcpyAsync(L.b64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
         CU(cudaGraphLaunch(H.graph, h->s));
         count_launch(H.graph_nodes);
+        h->graph_pending = h->o.timing;
         CU(cudaMemcpyAsync(z, L.x64[L.xfinal], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
     }
     return LAIR_OK;
@@ -697,6 +797,7 @@ static lair_status norm2_dev(lair_handle *h, int n, const double *v, double *out
     if (out_host) {
         CU(cudaMemcpyAsync(h->h_dbl, out_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
+        flush_timers(h);
         *out_host = h->h_dbl[0];
     }
     return LAIR_OK;
@@ -727,10 +828,14 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
         for (;;) {
             // r = b - A x written straight into the cycle's input buffer
             double *r = mixed ? h->wr : L0.b64;
+            int tr = tbegin(h, "outer_residual", (double)A.nnz * 12.0 + (double)n * (4.0 + 24.0 + (mixed ? 4.0 : 0.0)));
             residual(A, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
+            tend(h, tr);
             finish_partials(1, h->part, h->dsc, h->s);
             CU(cudaMemcpyAsync(h->h_dbl, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
             CU(cudaStreamSynchronize(h->s));
+
+            flush_timers(h);
             rel = std::sqrt(h->h_dbl[0]) / bn;
             hist(rel);
             if (!std::isfinite(rel)) { st = LAIR_ERR_NAN; break; }
@@ -738,6 +843,7 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
             if (it >= max_iter) break;
             CU(cudaGraphLaunch(H.graph, h->s));
             count_launch(H.graph_nodes);
+            h->graph_pending = h->o.timing;
             if (mixed) axpy_f(n, L0.x32[L0.xfinal], x, h->s);
             else axpy_d(n, L0.x64[L0.xfinal], x, h->s);
             ++it;
@@ -750,6 +856,8 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
         finish_partials(1, h->part, nrm, h->s);
         CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
+
+        flush_timers(h);
         double beta = std::sqrt(h->h_dbl[0]);
         rel = beta / bn;
         hist(rel);
@@ -762,7 +870,9 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
                 double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
                 TRY(precond(h, H, vj, zj));
                 ++it;
+                int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
                 spmv<double>(A, zj, w, h->s);
+                tend(h, ts);
                 CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (j + 1), h->s));
                 for (int pass = 0; pass < 2; ++pass) {
                     multidot(n, j + 1, V, n, w, h->part, hbuf, hsum, h->s);
@@ -773,6 +883,8 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
                 CU(cudaMemcpyAsync(h->h_dbl, hsum, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->s));
                 CU(cudaMemcpyAsync(h->h_dbl + 40, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
                 CU(cudaStreamSynchronize(h->s));
+
+                flush_timers(h);
                 for (int k = 0; k <= j; ++k) hc[k] = h->h_dbl[k];
                 double hn = std::sqrt(h->h_dbl[40]);
                 hc[j + 1] = hn;
@@ -804,6 +916,8 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
             finish_partials(1, h->part, nrm, h->s);
             CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
             CU(cudaStreamSynchronize(h->s));
+
+            flush_timers(h);
             beta = std::sqrt(h->h_dbl[0]);
             rel = beta / bn;
         }
@@ -986,6 +1100,20 @@ const char *lair_last_error(const lair_handle *h) { return h ? h->err.c_str() : 
 
 int64_t lair_kernel_launches(const lair_handle *h) { return h ? h->launches : 0; }
 
+lair_status lair_kernel_timers(const lair_handle *h, lair_kernel_timer *out, int cap, int *count) {
+    if (!h || !count) return LAIR_ERR_INVALID_ARG;
+    *count = (int)h->timers.size();
+    for (int i = 0; i < *count && i < cap && out; ++i) {
+        const auto &t = h->timers[i];
+        memset(out[i].name, 0, sizeof out[i].name);
+        strncpy(out[i].name, t.name.c_str(), sizeof out[i].name - 1);
+        out[i].launches = t.launches;
+        out[i].total_ms = t.ms;
+        out[i].bytes_per_launch = t.bytes;
+    }
+    return LAIR_OK;
+}
+
 lair_status lair_options_default(lair_options *o) {
     if (!o) return LAIR_ERR_INVALID_ARG;
     memset(o, 0, sizeof(*o));
@@ -997,9 +1125,9 @@ lair_status lair_options_default(lair_options *o) {
     o->relax = LAIR_RELAX_FFC;
     o->lump_tol = 1e-3;
     o->precision = LAIR_FP64;
-    o->coarse_max = 256;
+    o->coarse_max = 128;
     o->max_levels = 25;
-    o->rs_max_n = 8192;
+    o->rs_block = 4096;
     o->pmis_seed = 0x5eedULL;
     o->fgmres_restart = 30;
     return LAIR_OK;
@@ -1014,7 +1142,7 @@ static lair_status check_options(lair_handle *h, const lair_options *o) {
     if (o->precision < 0 || o->precision > 1) return fail(h, LAIR_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->coarse_max < 1 || o->coarse_max > 4096) return fail(h, LAIR_ERR_INVALID_ARG, "coarse_max in [1, 4096]");
     if (o->max_levels < 1) return fail(h, LAIR_ERR_INVALID_ARG, "max_levels >= 1");
-    if (o->rs_max_n < 0 || o->rs_max_n > RS_MAX_N) return fail(h, LAIR_ERR_INVALID_ARG, "rs_max_n in [0, %d]", RS_MAX_N);
+    if (o->rs_block < 1 || o->rs_block > RS_MAX_N) return fail(h, LAIR_ERR_INVALID_ARG, "rs_block in [1, %d]", RS_MAX_N);
     if (o->block_size > 8) return fail(h, LAIR_ERR_UNSUPPORTED, "block_size <= 8");
     if (o->fgmres_restart < 0 || o->fgmres_restart > 31) return fail(h, LAIR_ERR_INVALID_ARG, "fgmres_restart in [1, 31]");
     if (!(o->theta >= 0.0) || !(o->theta_cf >= 0.0) || !(o->lump_tol >= 0.0))
@@ -1174,6 +1302,9 @@ void lair_free(lair_handle *h) {
     for (void *p : h->allocs) cudaFreeAsync(p, h->s);
     if (h->scan_tmp) cudaFreeAsync(h->scan_tmp, h->s);
     cudaStreamSynchronize(h->s);
+    for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto &p : h->graph_events) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->own) cudaStreamDestroy(h->own);
     if (h->h_int) cudaFreeHost(h->h_int);
     if (h->h_dbl) cudaFreeHost(h->h_dbl);

@@ -147,17 +147,21 @@ __global__ void k_pmis_mark(int n, Graph ST, const int8_t *__restrict__ newc, in
 }
 
 // -------------------------------------------------------------------------------------
-// Classical first pass (Sec. 4, no second pass), one warp, everything in shared memory.
-// lambda_i = |ST_i|; points with S_i and ST_i empty start as F. Each step takes the
-// undecided point with the largest lambda (ties: smallest index) as C; its undecided
-// dependants ST_i become F; each undecided k in S_j of a new F point j gets lambda += 1;
-// each undecided k in S_i gets lambda -= 1.
-// Keys pack (lambda + 1) << 16 | (0xFFFF - i) (0 = decided), so the largest key is the
-// point to take. A 32-ary max tree (leaves, level 1 = max of 32 leaves, level 2 = max of
-// 32 level-1 nodes, at most 32 of them) finds it in three warp reductions.
+// Classical first pass (Sec. 4, no second pass), run independently on index blocks
+// [b0, b0 + B) of the level, one warp per block, everything of a block in shared memory.
+// Inside a block, lambda_i = |ST_i n block|; points without any strong connection in
+// the whole graph start as F. Each step takes the undecided point with the largest
+// lambda (ties: smallest index) as C; its undecided in-block dependants (ST_i) become F;
+// each undecided in-block k in S_j of a new F point j gets lambda += 1; each undecided
+// in-block k in S_i gets lambda -= 1. With one block covering the level this is exactly
+// the classical first pass.
+// Keys pack (lambda + 1) << 16 | (0xFFFF - local index) (0 = decided), so the largest key
+// is the point to take. A 32-ary max tree (leaves, level 1 = max of 32 leaves, level 2 =
+// max of 32 level-1 nodes, at most 32 of them) finds it in three warp reductions.
 // -------------------------------------------------------------------------------------
-constexpr int RS_LIST = 2048;
+constexpr int RS_LIST = 1024;
 constexpr int8_t CF_NEWF = 2;   // F point created in the current step
+constexpr int RS_SMEM_MAX = 200 * 1024;
 
 __device__ __forceinline__ unsigned warp_max_u32(unsigned v) { return __reduce_max_sync(0xffffffffu, v); }
 
@@ -176,26 +180,27 @@ __device__ void rs_rebuild(int n, int n1, const unsigned *key, unsigned *l1, uns
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(32) k_rs_split(int n, Graph S, Graph ST, int8_t *__restrict__ cf_out, int *status) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned *key = reinterpret_cast<unsigned *>(smem);
-    const int n1 = (n + 31) / 32;
-    unsigned *l1 = key + n;
-    unsigned *l2 = l1 + n1;
-    int *list = reinterpret_cast<int *>(l2 + 32);      // leaves changed in the current step
-    int8_t *cf = reinterpret_cast<int8_t *>(list + RS_LIST);
-    __shared__ int nlist;
+// in-block view of a strength graph: rows and neighbours as local indices 0..n-1
+struct StagedView {         // copied to shared memory, out-of-block entries removed
+    const int *rp;
+    const uint16_t *col;
+    __device__ int beg(int li) const { return rp[li]; }
+    __device__ int end(int li) const { return rp[li + 1]; }
+    __device__ int at(int p) const { return col[p]; }    // always in the block
+};
+struct GlobalView {         // read from global memory, out-of-block entries reported as -1
+    const int *rp, *col;
+    int b0, b1;
+    __device__ int beg(int li) const { return rp[b0 + li]; }
+    __device__ int end(int li) const { return rp[b0 + li + 1]; }
+    __device__ int at(int p) const { int j = col[p]; return (j >= b0 && j < b1) ? j - b0 : -1; }
+};
+
+template <class V>
+__device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned *l1, unsigned *l2, int *list,
+                         int8_t *cf, int *nlist_p) {
     const unsigned lane = threadIdx.x;
-
-    for (int i = lane; i < n; i += 32) {
-        int lam = ST.rp[i + 1] - ST.rp[i];
-        bool iso = (S.rp[i + 1] == S.rp[i]) && lam == 0;
-        cf[i] = iso ? CF_F : CF_U;
-        key[i] = iso ? 0u : (((unsigned)(lam + 1)) << 16) | (0xFFFFu - (unsigned)i);
-    }
-    __syncwarp();
-    rs_rebuild(n, n1, key, l1, l2, lane);
-
+    const int n1 = (n + 31) / 32;
     for (long long step = 0; step <= (long long)n; ++step) {
         unsigned v = l2[lane];
         const unsigned best = warp_max_u32(v);
@@ -211,48 +216,48 @@ __global__ void __launch_bounds__(32) k_rs_split(int n, Graph S, Graph ST, int8_
             cf[i] = CF_C;
             key[i] = 0u;
             list[0] = i;
-            nlist = 1;
+            *nlist_p = 1;
         }
         __syncwarp();
-        // undecided dependants of i become F (marked as new for this step)
-        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
-            int j = ST.col[p];
-            if (cf[j] == CF_U) {
+        // undecided in-block dependants of i become F (marked as new for this step)
+        for (int p = ST.beg(i) + lane; p < ST.end(i); p += 32) {
+            int j = ST.at(p);
+            if (j >= 0 && cf[j] == CF_U) {
                 cf[j] = CF_NEWF;
                 key[j] = 0u;
-                int t = atomicAdd(&nlist, 1);
+                int t = atomicAdd(nlist_p, 1);
                 if (t < RS_LIST) list[t] = j;
             }
         }
         __syncwarp();
-        // lambda_k += 1 for undecided k in S_j of every new F point j
-        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
-            int j = ST.col[p];
-            if (cf[j] != CF_NEWF) continue;
-            for (int q = S.rp[j]; q < S.rp[j + 1]; ++q) {
-                int k = S.col[q];
-                if (cf[k] == CF_U) {
+        // lambda_k += 1 for undecided in-block k in S_j of every new F point j
+        for (int p = ST.beg(i) + lane; p < ST.end(i); p += 32) {
+            int j = ST.at(p);
+            if (j < 0 || cf[j] != CF_NEWF) continue;
+            for (int q = S.beg(j); q < S.end(j); ++q) {
+                int k = S.at(q);
+                if (k >= 0 && cf[k] == CF_U) {
                     atomicAdd(&key[k], 1u << 16);
-                    int t = atomicAdd(&nlist, 1);
+                    int t = atomicAdd(nlist_p, 1);
                     if (t < RS_LIST) list[t] = k;
                 }
             }
         }
-        // lambda_k -= 1 for undecided k in S_i
-        for (int q = S.rp[i] + lane; q < S.rp[i + 1]; q += 32) {
-            int k = S.col[q];
-            if (cf[k] == CF_U) {
+        // lambda_k -= 1 for undecided in-block k in S_i
+        for (int q = S.beg(i) + lane; q < S.end(i); q += 32) {
+            int k = S.at(q);
+            if (k >= 0 && cf[k] == CF_U) {
                 atomicSub(&key[k], 1u << 16);
-                int t = atomicAdd(&nlist, 1);
+                int t = atomicAdd(nlist_p, 1);
                 if (t < RS_LIST) list[t] = k;
             }
         }
         __syncwarp();
-        for (int p = ST.rp[i] + lane; p < ST.rp[i + 1]; p += 32) {
-            int j = ST.col[p];
-            if (cf[j] == CF_NEWF) cf[j] = CF_F;
+        for (int p = ST.beg(i) + lane; p < ST.end(i); p += 32) {
+            int j = ST.at(p);
+            if (j >= 0 && cf[j] == CF_NEWF) cf[j] = CF_F;
         }
-        const int nl = nlist;
+        const int nl = *nlist_p;
         __syncwarp();
         if (nl > RS_LIST) {
             rs_rebuild(n, n1, key, l1, l2, lane);
@@ -274,16 +279,110 @@ __global__ void __launch_bounds__(32) k_rs_split(int n, Graph S, Graph ST, int8_
         }
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) {
-        int8_t c = cf[i];
+}
+
+// copy the in-block part of graph G (rows b0..b1-1) into shared memory; returns false if it
+// does not fit in cap bytes (nothing is used then)
+__device__ bool rs_stage(const Graph &G, int b0, int b1, int *rp, uint16_t *col, size_t cap_entries) {
+    const unsigned lane = threadIdx.x;
+    const int n = b1 - b0;
+    // counts, then an exclusive scan in lane-contiguous chunks
+    const int chunk = (n + 31) / 32;
+    const int r0 = min(n, (int)lane * chunk), r1 = min(n, r0 + chunk);
+    int mine = 0;
+    for (int li = r0; li < r1; ++li) {
+        int c = 0;
+        for (int p = G.rp[b0 + li]; p < G.rp[b0 + li + 1]; ++p) c += (G.col[p] >= b0 && G.col[p] < b1);
+        rp[li] = c;
+        mine += c;
+    }
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if ((size_t)total > cap_entries) return false;
+    int run = incl - mine;
+    for (int li = r0; li < r1; ++li) {
+        int c = rp[li];
+        rp[li] = run;
+        run += c;
+    }
+    if (lane == 31) rp[n] = total;
+    __syncwarp();
+    for (int li = r0; li < r1; ++li) {
+        int q = rp[li];
+        for (int p = G.rp[b0 + li]; p < G.rp[b0 + li + 1]; ++p) {
+            int j = G.col[p];
+            if (j >= b0 && j < b1) col[q++] = (uint16_t)(j - b0);
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(32) k_rs_split(int n_all, int B, Graph S, Graph ST, int8_t *__restrict__ cf_out,
+                                                 int *status, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b0 = blockIdx.x * B;
+    const int b1 = min(n_all, b0 + B);
+    const int n = b1 - b0;
+    const int n1 = (n + 31) / 32;
+    unsigned *key = reinterpret_cast<unsigned *>(smem);
+    unsigned *l1 = key + n;
+    unsigned *l2 = l1 + n1;
+    int *list = reinterpret_cast<int *>(l2 + 32);      // local indices of leaves changed in the current step
+    int *srp = list + RS_LIST;                         // staged graphs: row pointers of S and ST, then columns
+    int *strp = srp + (n + 1);
+    int8_t *cf = reinterpret_cast<int8_t *>(strp + (n + 1));
+    uint16_t *scol = reinterpret_cast<uint16_t *>(cf + ((n + 15) & ~15));
+    __shared__ int nlist;
+    const unsigned lane = threadIdx.x;
+
+    for (int li = lane; li < n; li += 32) {
+        const int i = b0 + li;
+        int lam = 0;
+        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) lam += (ST.col[p] >= b0 && ST.col[p] < b1);
+        bool iso = (S.rp[i + 1] == S.rp[i]) && (ST.rp[i + 1] == ST.rp[i]);
+        cf[li] = iso ? CF_F : CF_U;
+        key[li] = iso ? 0u : (((unsigned)(lam + 1)) << 16) | (0xFFFFu - (unsigned)li);
+    }
+    __syncwarp();
+    rs_rebuild(n, n1, key, l1, l2, lane);
+
+    // both in-block graphs have the same number of entries; stage them if they fit
+    const size_t used = (size_t)(reinterpret_cast<unsigned char *>(scol) - smem);
+    const size_t cap = used < (size_t)smem_bytes ? ((size_t)smem_bytes - used) / (2 * sizeof(uint16_t)) : 0;
+    bool staged = rs_stage(S, b0, b1, srp, scol, cap);
+    if (staged) {
+        const int e = srp[n];
+        staged = rs_stage(ST, b0, b1, strp, scol + e, cap);
+    }
+    if (staged) {
+        StagedView vs{srp, scol}, vt{strp, scol + srp[n]};
+        rs_steps(n, vs, vt, key, l1, l2, list, cf, &nlist);
+    } else {
+        GlobalView vs{S.rp, S.col, b0, b1}, vt{ST.rp, ST.col, b0, b1};
+        rs_steps(n, vs, vt, key, l1, l2, list, cf, &nlist);
+    }
+    for (int li = lane; li < n; li += 32) {
+        int8_t c = cf[li];
         if (c != CF_C && c != CF_F) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
-        cf_out[i] = c;
+        cf_out[b0 + li] = c;
     }
 }
 
-size_t rs_smem_bytes(int n) {
+// shared memory of one block: the fixed part (keys, tree, list, row pointers, splitting) plus room
+// for the staged in-block graphs, up to RS_SMEM_MAX bytes in all
+size_t rs_smem_bytes(int n, double avg_degree) {
     int n1 = (n + 31) / 32;
-    return sizeof(unsigned) * ((size_t)n + n1 + 32) + sizeof(int) * RS_LIST + (size_t)n + 16;
+    size_t fixed = sizeof(unsigned) * ((size_t)n + n1 + 32) + sizeof(int) * (RS_LIST + 2 * ((size_t)n + 1)) +
+                   (((size_t)n + 15) & ~(size_t)15);
+    double per_row = 1.25 * avg_degree + 2.0;            // room for the in-block entries of a typical block
+    if (per_row > 24.0) per_row = 24.0;
+    size_t want = fixed + (size_t)(2 * sizeof(uint16_t) * (double)n * per_row);
+    return want < RS_SMEM_MAX ? want : (fixed < RS_SMEM_MAX ? RS_SMEM_MAX : fixed);
 }
 
 // -------------------------------------------------------------------------------------
@@ -406,11 +505,12 @@ void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, 
     count_launch(2);
 }
 
-cudaError_t launch_rs(int n, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
-    size_t bytes = rs_smem_bytes(n);
+cudaError_t launch_rs(int n, int B, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
+    if (B > n) B = n;
+    size_t bytes = rs_smem_bytes(B, n > 0 ? (double)S.nnz / n : 0.0);
     cudaError_t e = cudaFuncSetAttribute(k_rs_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_rs_split<<<1, 32, bytes, s>>>(n, S, ST, cf, status);
+    k_rs_split<<<(n + B - 1) / B, 32, bytes, s>>>(n, B, S, ST, cf, status, (int)bytes);
     count_launch();
     return cudaGetLastError();
 }

@@ -15,8 +15,8 @@ void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
 void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
                        int *undecided, cudaStream_t s);
-cudaError_t launch_rs(int n, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
-size_t rs_smem_bytes(int n);
+cudaError_t launch_rs(int n, int B, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
+size_t rs_smem_bytes(int n, double avg_degree);
 constexpr int RS_MAX_N = 32768;
 void launch_cidx(int n, const int8_t *cf, int *flag, int *cidx, int *cpts, int phase, cudaStream_t s);
 void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, int *ub, cudaStream_t s);
@@ -90,5 +90,6 @@ void f2d(int n, const float *a, double *b, cudaStream_t s);
 void axpy_f(int n, const float *e, double *x, cudaStream_t s);
 void axpy_d(int n, const double *e, double *x, cudaStream_t s);
 void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s);
+void cf_stats(const DCsr &A, const int8_t *cf, unsigned long long *out4, cudaStream_t s);
 
 }  // namespace lair

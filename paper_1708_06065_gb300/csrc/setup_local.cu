@@ -470,32 +470,50 @@ void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t
 // off-block columns, and the diagonal block becomes the exact identity.
 // ---------------------------------------------------------------------------------------
 constexpr int BS_MAX = 8;
-constexpr int BS_UNION_MAX = 256;
 
-__device__ int block_union(const int *rp, const int *col, int r0, int bs, int *u) {
-    int nu = 0;
-    for (int r = 0; r < bs; ++r)
-        for (int k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k) {
-            int j = col[k];
-            if (j >= r0 && j < r0 + bs) continue;
-            // insert into sorted unique list
-            int lo = 0, hi = nu;
-            while (lo < hi) { int m = (lo + hi) >> 1; if (u[m] < j) lo = m + 1; else hi = m; }
-            if (lo < nu && u[lo] == j) continue;
-            if (nu >= BS_UNION_MAX) return -1;
-            for (int m = nu; m > lo; --m) u[m] = u[m - 1];
-            u[lo] = j;
-            ++nu;
+// Walk the bs rows of a block in merged column order, skipping the block's own columns.
+// For every column j of the union, vals[t] = A[r0 + t][j] (0 when not stored).
+struct BlockMerge {
+    const int *rp, *col;
+    const double *val;
+    int r0, bs;
+    int pos[BS_MAX], end[BS_MAX];
+    __device__ void init() {
+        for (int t = 0; t < bs; ++t) {
+            pos[t] = rp[r0 + t];
+            end[t] = rp[r0 + t + 1];
+            skip(t);
         }
-    return nu;
-}
+    }
+    __device__ void skip(int t) {
+        while (pos[t] < end[t] && col[pos[t]] >= r0 && col[pos[t]] < r0 + bs) ++pos[t];
+    }
+    // next union column (or -1); fills vals[t]
+    __device__ int next(double *vals) {
+        int j = 0x7fffffff;
+        for (int t = 0; t < bs; ++t)
+            if (pos[t] < end[t] && col[pos[t]] < j) j = col[pos[t]];
+        if (j == 0x7fffffff) return -1;
+        for (int t = 0; t < bs; ++t) {
+            if (pos[t] < end[t] && col[pos[t]] == j) {
+                if (vals) vals[t] = val[pos[t]];
+                ++pos[t];
+                skip(t);
+            } else if (vals) {
+                vals[t] = 0.0;
+            }
+        }
+        return j;
+    }
+};
 
 __global__ void k_block_count(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                               int *__restrict__ rowcnt, int *status) {
-    int u[BS_UNION_MAX];
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
-        int nu = block_union(rp, col, K * bs, bs, u);
-        if (nu < 0) { set_status(status, LAIR_ERR_UNSUPPORTED); nu = 0; }
+        BlockMerge m{rp, col, nullptr, K * bs, bs};
+        m.init();
+        int nu = 0;
+        while (m.next(nullptr) >= 0) ++nu;
         for (int r = 0; r < bs; ++r) rowcnt[K * bs + r] = nu + 1;
     }
 }
@@ -511,14 +529,15 @@ __device__ double entry(const int *rp, const int *col, const double *val, int i,
     return 0.0;
 }
 
+// one thread per row of the output: every thread of a block factors the same bs x bs block
+// (identical operations, so identical D_B^{-1}) and writes its own row
 __global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
                              const double *__restrict__ val, const int *__restrict__ orp, int *__restrict__ ocol,
                              double *__restrict__ oval, double *__restrict__ dinv_out, int *status) {
-    int u[BS_UNION_MAX];
-    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], Di[BS_MAX * BS_MAX], rhs[BS_MAX];
+    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], Di[BS_MAX], rhs[BS_MAX], a[BS_MAX];
     int perm[BS_MAX];
-    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
-        const int r0 = K * bs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nblk * bs; e += gridDim.x * blockDim.x) {
+        const int K = e / bs, rr = e % bs, r0 = K * bs;
         for (int r = 0; r < bs; ++r) {
             perm[r] = r;
             for (int c = 0; c < bs; ++c) {
@@ -527,7 +546,7 @@ __global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const
             }
         }
         double mx = 0.0;
-        for (int e = 0; e < bs * bs; ++e) mx = fmax(mx, fabs(M[e]));
+        for (int q = 0; q < bs * bs; ++q) mx = fmax(mx, fabs(M[q]));
         const double thr = __dmul_rn(__dmul_rn((double)bs, 0x1.0p-52), mx);
         bool bad = mx == 0.0;
         for (int k = 0; k < bs && !bad; ++k) {
@@ -550,37 +569,36 @@ __global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const
             }
         }
         if (bad) { set_status(status, LAIR_ERR_ZERO_DIAGONAL); continue; }
+        // row rr of D_B^{-1}: column t of the inverse is the solve with unit vector e_t
         for (int t = 0; t < bs; ++t) {
             for (int r = 0; r < bs; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
             for (int k = 0; k < bs; ++k)
                 for (int r = k + 1; r < bs; ++r) rhs[r] = __fma_rn(-Lm[r * bs + k], rhs[k], rhs[r]);
             for (int c = bs - 1; c >= 0; --c) {
                 double zc = __ddiv_rn(rhs[c], M[c * bs + c]);
-                Di[c * bs + t] = zc;
+                if (c == rr) Di[t] = zc;
                 for (int r = 0; r < c; ++r) rhs[r] = __fma_rn(-M[r * bs + c], zc, rhs[r]);
             }
         }
-        for (int e = 0; e < bs * bs; ++e) dinv_out[(size_t)K * bs * bs + e] = Di[e];
-        int nu = block_union(rp, col, r0, bs, u);
-        if (nu < 0) continue;
-        for (int r = 0; r < bs; ++r) {
-            int p = orp[r0 + r];
-            bool placed = false;
-            for (int a = 0; a <= nu; ++a) {
-                if (!placed && (a == nu || u[a] > r0 + r)) {
-                    ocol[p] = r0 + r;
-                    oval[p] = 1.0;
-                    ++p;
-                    placed = true;
-                }
-                if (a == nu) break;
-                int j = u[a];
-                double acc = 0.0;
-                for (int t = 0; t < bs; ++t) acc = __fma_rn(Di[r * bs + t], entry(rp, col, val, r0 + t, j), acc);
-                ocol[p] = j;
-                oval[p] = acc;
+        for (int t = 0; t < bs; ++t) dinv_out[(size_t)K * bs * bs + rr * bs + t] = Di[t];
+        BlockMerge m{rp, col, val, r0, bs};
+        m.init();
+        int p = orp[r0 + rr];
+        bool placed = false;
+        for (;;) {
+            int j = m.next(a);
+            if (!placed && (j < 0 || j > r0 + rr)) {
+                ocol[p] = r0 + rr;
+                oval[p] = 1.0;
                 ++p;
+                placed = true;
             }
+            if (j < 0) break;
+            double acc = 0.0;
+            for (int t = 0; t < bs; ++t) acc = __fma_rn(Di[t], a[t], acc);
+            ocol[p] = j;
+            oval[p] = acc;
+            ++p;
         }
     }
 }
@@ -596,12 +614,13 @@ __global__ void k_block_apply(int nblk, int bs, const double *__restrict__ dinv,
 }
 
 void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *status, cudaStream_t s) {
-    k_block_count<<<grid_for(nblk, 64), 64, 0, s>>>(nblk, bs, A.rp, A.col, rowcnt, status);
+    k_block_count<<<grid_for(nblk, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, rowcnt, status);
     count_launch();
 }
 
 void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
-    k_block_fill<<<grid_for(nblk, 64), 64, 0, s>>>(nblk, bs, A.rp, A.col, A.val, out.rp, out.col, out.val, dinv, status);
+    k_block_fill<<<grid_for((long long)nblk * bs, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, A.val, out.rp, out.col, out.val,
+                                                                     dinv, status);
     count_launch();
 }
 

@@ -39,6 +39,19 @@ __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__re
 
 __device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
 
+constexpr int XCHUNK = 128;   // entries of an X row staged at a time
+// per-warp staging area after the hash tables: x (XCHUNK doubles), px/py (2 x 32 doubles),
+// k (XCHUNK ints), offsets (XCHUNK + 1 ints); the stride is rounded up to 16 bytes so that
+// every warp's doubles stay aligned
+constexpr size_t SPGEMM_EXTRA =
+    ((XCHUNK * sizeof(double) + 64 * sizeof(double) + (2 * XCHUNK + 1) * sizeof(int)) + 15) & ~(size_t)15;
+
+// One warp per output row a. The products x_ak * y_kl of the row are laid out flat in
+// ascending (k, position in row k of Y) order and taken 32 at a time; lanes holding the
+// same column l are grouped with __match_any_sync and the lowest lane of a group (the
+// smallest k) applies the group's products in ascending k, so every entry receives its
+// fma updates in ascending k exactly as in a sequential loop. The unique columns are then
+// ordered by rank counting.
 __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
                                                                 const int *__restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -46,6 +59,14 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
     const unsigned lane = threadIdx.x & 31;
     double *vals = reinterpret_cast<double *>(smem) + (size_t)w * WARP_CAP;
     int *keys = reinterpret_cast<int *>(reinterpret_cast<double *>(smem) + (size_t)SPGEMM_WARPS * WARP_CAP) + (size_t)w * WARP_CAP;
+    unsigned char *extra = reinterpret_cast<unsigned char *>(reinterpret_cast<int *>(reinterpret_cast<double *>(smem) +
+                                                             (size_t)SPGEMM_WARPS * WARP_CAP) + (size_t)SPGEMM_WARPS * WARP_CAP);
+    extra += (size_t)w * SPGEMM_EXTRA;
+    double *sxv = reinterpret_cast<double *>(extra);          // x of the staged chunk of row a of X
+    double *px = sxv + XCHUNK;                               // products of one round: x and y per lane
+    double *py = px + 32;
+    int *sk = reinterpret_cast<int *>(py + 32);              // k of the staged chunk
+    int *soff = sk + XCHUNK;                                 // flat offsets, XCHUNK + 1
     const int n = *count;
     const int nwarps = gridDim.x * SPGEMM_WARPS;
     for (int t = blockIdx.x * SPGEMM_WARPS + w; t < n; t += nwarps) {
@@ -55,24 +76,72 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
         while ((int)cap < 2 * ub) cap <<= 1;
         const unsigned mask = cap - 1;
         for (unsigned e = lane; e < cap; e += 32) keys[e] = -1;
-        __syncwarp();
-        for (int p = g.xrp[a]; p < g.xrp[a + 1]; ++p) {
-            const int k = g.xcol[p];
-            const double x = g.xval[p];
-            for (int q = g.yrp[k] + lane; q < g.yrp[k + 1]; q += 32) {
-                const int l = g.ycol[q];
-                const double y = g.yval[q];
-                unsigned h = hash_slot(l, mask);
-                for (;;) {
-                    int prev = atomicCAS(&keys[h], -1, l);
-                    if (prev == -1) { vals[h] = __fma_rn(x, y, 0.0); break; }
-                    if (prev == l) { vals[h] = __fma_rn(x, y, vals[h]); break; }
-                    h = (h + 1) & mask;
-                }
-            }
+        const int xb = g.xrp[a], xe = g.xrp[a + 1];
+        for (int c0 = xb; c0 < xe; c0 += XCHUNK) {
+            const int cn = min(XCHUNK, xe - c0);
             __syncwarp();
+            // stage k, x and flat offsets of this chunk (warp scan of the row lengths of Y)
+            int carry = 0;
+            for (int b = 0; b < cn; b += 32) {
+                int len = 0;
+                if (b + (int)lane < cn) {
+                    int k = g.xcol[c0 + b + lane];
+                    sk[b + lane] = k;
+                    sxv[b + lane] = g.xval[c0 + b + lane];
+                    len = g.yrp[k + 1] - g.yrp[k];
+                }
+                int incl = len;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)lane >= o) incl += v;
+                }
+                if (b + (int)lane < cn) soff[b + lane] = carry + incl - len;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) soff[cn] = carry;
+            __syncwarp();
+            const int total = carry;
+            for (int base = 0; base < total; base += 32) {
+                const int p = base + (int)lane;
+                const bool act = p < total;
+                int l = -1;
+                if (act) {
+                    int lo = 0, hi = cn - 1;       // last chunk entry with soff <= p
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (soff[mid] <= p) lo = mid; else hi = mid - 1;
+                    }
+                    const int k = sk[lo];
+                    const int q = g.yrp[k] + (p - soff[lo]);
+                    l = g.ycol[q];
+                    px[lane] = sxv[lo];
+                    py[lane] = g.yval[q];
+                }
+                const unsigned am = __ballot_sync(0xffffffffu, act);
+                __syncwarp();
+                if (act) {
+                    const unsigned grp = __match_any_sync(am, l);
+                    if ((int)lane == __ffs(grp) - 1) {
+                        unsigned h = hash_slot(l, mask);
+                        double v;
+                        for (;;) {
+                            int prev = atomicCAS(&keys[h], -1, l);
+                            if (prev == -1) { v = 0.0; break; }
+                            if (prev == l) { v = vals[h]; break; }
+                            h = (h + 1) & mask;
+                        }
+                        for (unsigned m = grp; m; m &= m - 1) {
+                            int b = __ffs(m) - 1;
+                            v = __fma_rn(px[b], py[b], v);
+                        }
+                        vals[h] = v;
+                    }
+                }
+                __syncwarp();
+            }
         }
-        // compact occupied slots to the front (in order of slot; positions never pass the read slot)
+        __syncwarp();
+        // compact occupied slots to the front (positions never pass the slot being read)
         int cnt = 0;
         for (unsigned base = 0; base < cap; base += 32) {
             int key = keys[base + lane];
@@ -87,30 +156,14 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
             cnt += __popc(occ);
             __syncwarp();
         }
-        unsigned np2 = 1;
-        while ((int)np2 < cnt) np2 <<= 1;
-        for (unsigned e = cnt + lane; e < np2; e += 32) keys[e] = 0x7fffffff;
-        __syncwarp();
-        // bitonic sort by column
-        for (unsigned kk = 2; kk <= np2; kk <<= 1)
-            for (unsigned j = kk >> 1; j > 0; j >>= 1) {
-                for (unsigned i = lane; i < np2; i += 32) {
-                    unsigned ixj = i ^ j;
-                    if (ixj > i) {
-                        bool up = (i & kk) == 0;
-                        int ki = keys[i], kj = keys[ixj];
-                        if ((ki > kj) == up) {
-                            keys[i] = kj; keys[ixj] = ki;
-                            double tv = vals[i]; vals[i] = vals[ixj]; vals[ixj] = tv;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+        // rank counting: the position of a key is the number of smaller keys (keys are unique)
         const int o = g.off[a];
         for (int e = lane; e < cnt; e += 32) {
-            g.tcol[o + e] = keys[e];
-            g.tval[o + e] = vals[e];
+            const int key = keys[e];
+            int r = 0;
+            for (int f = 0; f < cnt; ++f) r += keys[f] < key;
+            g.tcol[o + r] = key;
+            g.tval[o + r] = vals[e];
         }
         if (lane == 0) g.cnt[a] = cnt;
         __syncwarp();
@@ -215,7 +268,7 @@ void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
                                const int counts_host[2], int ubmax, int *skeys, double *svals, cudaStream_t s) {
     if (counts_host[0] > 0) {
-        size_t bytes = (size_t)SPGEMM_WARPS * WARP_CAP * (sizeof(double) + sizeof(int));
+        size_t bytes = (size_t)SPGEMM_WARPS * (WARP_CAP * (sizeof(double) + sizeof(int)) + SPGEMM_EXTRA);
         cudaFuncSetAttribute(k_spgemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         int grid = grid_for(counts_host[0], SPGEMM_WARPS, 152 * 8);
         k_spgemm_warp<<<grid, 32 * SPGEMM_WARPS, bytes, s>>>(g, lists, counts_dev);
@@ -409,8 +462,104 @@ __global__ void k_dense_inverse(int n, const double *__restrict__ LU, const int 
     }
 }
 
+// small coarsest levels (n <= DENSE_SMEM_N): the LU and the inverse entirely in shared memory,
+// one CTA; each warp then forms columns of the inverse from the factors
+constexpr int DENSE_SMEM_N = 128;
+
+__global__ void __launch_bounds__(1024) k_dense_small(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                      const double *__restrict__ val, double *__restrict__ Ainv,
+                                                      int *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *D = reinterpret_cast<double *>(smem);            // n x n
+    double *X = D + (size_t)n * n;                           // 32 warps x n
+    int *perm = reinterpret_cast<int *>(X + (size_t)32 * n);
+    __shared__ double bv[32];
+    __shared__ int bi[32];
+    __shared__ int bad;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) D[e] = 0.0;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        perm[i] = i;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) D[i * n + col[k]] = val[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int piv = -1;
+        for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+            double v = fabs(D[r * n + k]);
+            if (piv < 0 || v > best) { best = v; piv = r; }
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (oi >= 0 && (piv < 0 || ov > best || (ov == best && oi < piv))) { best = ov; piv = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = piv; }
+        __syncthreads();
+        best = bv[0];
+        piv = bi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (bi[w] >= 0 && (piv < 0 || bv[w] > best || (bv[w] == best && bi[w] < piv))) { best = bv[w]; piv = bi[w]; }
+        if (best == 0.0) {
+            if (threadIdx.x == 0) { set_status(status, LAIR_ERR_ZERO_DIAGONAL); bad = 1; }
+            break;
+        }
+        if (piv != k) {
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                double t = D[k * n + c];
+                D[k * n + c] = D[piv * n + c];
+                D[piv * n + c] = t;
+            }
+            if (threadIdx.x == 0) { int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t; }
+        }
+        __syncthreads();
+        const double pk = D[k * n + k];
+        for (int r = k + 1 + threadIdx.x; r < n; r += blockDim.x) D[r * n + k] = D[r * n + k] / pk;
+        __syncthreads();
+        const int w = n - k - 1;
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            int r = k + 1 + e / w, c = k + 1 + e % w;
+            D[r * n + c] = fma(-D[r * n + k], D[k * n + c], D[r * n + c]);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (bad) return;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double *x = X + (size_t)wid * n;
+    for (int t = wid; t < n; t += nw) {
+        for (int r = lane; r < n; r += 32) x[r] = perm[r] == t ? 1.0 : 0.0;
+        __syncwarp();
+        for (int k = 0; k < n; ++k) {
+            const double xk = x[k];
+            for (int r = k + 1 + lane; r < n; r += 32) x[r] = fma(-D[r * n + k], xk, x[r]);
+            __syncwarp();
+        }
+        for (int c = n - 1; c >= 0; --c) {
+            if (lane == 0) x[c] = x[c] / D[c * n + c];
+            __syncwarp();
+            const double xc = x[c];
+            for (int r = lane; r < c; r += 32) x[r] = fma(-D[r * n + c], xc, x[r]);
+            __syncwarp();
+        }
+        for (int r = lane; r < n; r += 32) Ainv[(size_t)r * n + t] = x[r];
+        __syncwarp();
+    }
+}
+
+bool dense_small(int n) { return n <= DENSE_SMEM_N; }
+
 void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s) {
     int n = A.nr;
+    if (n <= DENSE_SMEM_N) {
+        size_t bytes = sizeof(double) * ((size_t)n * n + 32 * (size_t)n) + sizeof(int) * (size_t)n;
+        cudaFuncSetAttribute(k_dense_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        k_dense_small<<<1, 1024, bytes, s>>>(n, A.rp, A.col, A.val, Ainv, status);
+        count_launch();
+        return;
+    }
     k_dense_build<<<grid_for((long long)n * n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
     k_dense_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
     k_dense_lu<<<1, 1024, 0, s>>>(n, D, perm, status);

@@ -208,9 +208,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(int n, int m, const do
         for (int k = 0; k < 32; ++k)
             if (k < m) acc[k] = fma(X[k * ldx + i], yi, acc[k]);
     }
-    for (int k = 0; k < m; ++k) {
-        double v = warp_sum(acc[k]);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (k < m) {
+            double v = warp_sum(acc[k]);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x < m) {
@@ -327,6 +330,25 @@ __global__ void k_grad_A(int n, const int *__restrict__ rp, const int *__restric
 
 void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s) {
     k_grad_A<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, A.col, lam, x, g);
+    count_launch();
+}
+
+// rows and entries of F and C rows: out = {n_F, nnz_F, n_C, nnz_C}
+__global__ void k_cf_stats(int n, const int *__restrict__ rp, const int8_t *__restrict__ cf,
+                           unsigned long long *__restrict__ out) {
+    unsigned long long a = 0, b = 0, c = 0, d = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned long long len = (unsigned long long)(rp[i + 1] - rp[i]);
+        if (cf[i] == CF_F) { a += 1; b += len; } else { c += 1; d += len; }
+    }
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c); d = warp_sum(d);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, a); atomicAdd(out + 1, b); atomicAdd(out + 2, c); atomicAdd(out + 3, d);
+    }
+}
+
+void cf_stats(const DCsr &A, const int8_t *cf, unsigned long long *out4, cudaStream_t s) {
+    k_cf_stats<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, cf, out4);
     count_launch();
 }
 

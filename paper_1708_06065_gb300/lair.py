@@ -43,8 +43,8 @@ class lair_options(C.Structure):
                 ("theta_cf", C.c_double), ("strength_abs", C.c_int), ("interp", C.c_int), ("relax", C.c_int),
                 ("lump_tol", C.c_double), ("lump_level0", C.c_int), ("precision", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
-                ("rs_max_n", C.c_int), ("pmis_seed", C.c_uint64), ("fgmres_restart", C.c_int),
-                ("stream", C.c_void_p)]
+                ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("fgmres_restart", C.c_int),
+                ("stream", C.c_void_p), ("timing", C.c_int)]
 
 
 class lair_report(C.Structure):
@@ -52,6 +52,11 @@ class lair_report(C.Structure):
                 ("nlevels", C.c_int), ("singular_R", C.c_int64), ("singular_P", C.c_int64),
                 ("op_complexity", C.c_double), ("cycle_complexity", C.c_double), ("hist", C.c_void_p),
                 ("hist_cap", C.c_int), ("hist_len", C.c_int)]
+
+
+class lair_kernel_timer(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes_per_launch", C.c_double)]
 
 
 class lair_level_info(C.Structure):
@@ -75,6 +80,7 @@ def _load():
         "lair_export_csr": (C.c_int, [p, C.c_int, C.c_int, p, p, p]),
         "lair_export_cf": (C.c_int, [p, C.c_int, p, p, p, p]),
         "lair_kernel_launches": (C.c_int64, [p]),
+        "lair_kernel_timers": (C.c_int, [p, C.POINTER(lair_kernel_timer), C.c_int, C.POINTER(C.c_int)]),
         "lair_free": (None, [p]),
         "lair_status_string": (C.c_char_p, [C.c_int]),
         "lair_last_error": (C.c_char_p, [p]),
@@ -241,6 +247,14 @@ class Hierarchy:
             out = np.zeros(self.nnz) if isinstance(lam, np.ndarray) else lam.new_zeros(self.nnz)
         self._check(lib.lair_grad_A(self._h, _ptr(lam), _ptr(x), _ptr(out)))
         return out
+
+    def timers(self):
+        """{name: (launches, total_ms, bytes_per_launch)} of the kernels timed with options(timing=1)."""
+        cnt = C.c_int(0)
+        arr = (lair_kernel_timer * 64)()
+        self._check(lib.lair_kernel_timers(self._h, arr, 64, C.byref(cnt)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms), float(arr[i].bytes_per_launch))
+                for i in range(min(cnt.value, 64))}
 
     def info(self):
         nl = C.c_int(0)

@@ -36,7 +36,7 @@ def test_options_defaults_and_status_strings():
     from paper_1708_06065_gb300 import lair
     o = lair.options()
     assert o.cf_mode == lair.CF_AUTO and o.distance == 1 and o.theta == 0.25 and o.lump_tol == 1e-3
-    assert o.coarse_max == 256 and o.max_levels == 25 and o.rs_max_n == 8192 and o.fgmres_restart == 30
+    assert o.coarse_max == 128 and o.max_levels == 25 and o.rs_block == 4096 and o.fgmres_restart == 30
     assert lair.lib.lair_status_string(0) == b"LAIR_OK"
     assert lair.lib.lair_status_string(13) == b"LAIR_ERR_UNSUPPORTED"
 

@@ -33,7 +33,7 @@ def lair():
 def oracle_kw(kw):
     m = dict(cf_mode="cf_mode", distance="distance", theta="theta", theta_cf="theta_cf", strength_abs="strength_abs",
              interp="interp", relax="relax", lump_tol="lump_tol", coarse_max="coarse_max", max_levels="max_levels",
-             block_size="block_size", rs_max_n="rs_max_n", precision="prec")
+             block_size="block_size", rs_block="rs_block", precision="prec")
     return {m[k]: v for k, v in kw.items()}
 
 
@@ -41,7 +41,7 @@ CASES = {
     "fd2d64_rs_d1": ("fd2d_64", None, dict(cf_mode=0, distance=1)),
     "fd2d64_rs_d2": ("fd2d_64", None, dict(cf_mode=0, distance=2)),
     "fd2d64_pmis_d1": ("fd2d_64", None, dict(cf_mode=1, distance=1)),
-    "fd2d64_auto_onepoint": ("fd2d_64", None, dict(distance=2, interp=1, rs_max_n=1000)),
+    "fd2d64_auto_onepoint": ("fd2d_64", None, dict(distance=2, interp=1, rs_block=1000)),
     "fd2d64_mixed": ("fd2d_64", None, dict(cf_mode=0, distance=2, precision=1)),
     "fd2d_diffusive_d2": ("diffusive", None, dict(distance=2)),
     "fd3d_20_d1": ("fd3d_192", 20, dict(distance=1)),
@@ -49,6 +49,8 @@ CASES = {
     "dg_p2_16": ("dg_p2_256", 16, dict(distance=2, interp=1, strength_abs=1, block_size=6, precision=1)),
     "dg_p2_16_fp64_laip": ("dg_p2_256", 16, dict(distance=2, interp=0, strength_abs=1, block_size=6)),
     "random_theta_cf": ("random", None, dict(distance=2, theta=0.1, theta_cf=0.3, lump_tol=0.01)),
+    "fd2d512_auto_blocks": ("adjoint_fd2d_512", None, dict(distance=1)),
+    "fd3d_40_auto_blocks": ("fd3d_192", 40, dict(distance=1, rs_block=2048)),
 }
 
 
@@ -119,7 +121,7 @@ def test_host_and_device_buffers_agree(lair):
 
 
 def test_single_level_direct_solve(lair):
-    s = W.config("fd2d_64", scale=12)          # n = 144 <= coarse_max: the hierarchy is one dense level
+    s = W.config("fd2d_64", scale=10)          # n = 100 <= coarse_max: the hierarchy is one dense level
     G = lair.Hierarchy.from_system(s)
     assert len(G.info()) == 1
     x, rep = G.solve(s.b.copy(), tol=1e-12, cycle=0)

@@ -179,6 +179,42 @@ def test_rs_invariants_and_greedy_order(seed):
     assert [1 if v == "C" else 0 for v in st] == cf.tolist()
 
 
+@pytest.mark.parametrize("B", [7, 40, 1000])
+def test_blocked_first_pass_replay(B):
+    """The first pass run independently on index blocks: lambda and updates count only
+    in-block strong connections; one block covering every point is the classical pass."""
+    s = W.fd_adr_2d(14, 0.9, 1e-3, 0.1)
+    mask = O.strength(s, 0.25)
+    cf = O.cf_split(s, mask, O.CF_AUTO, seed=B)
+    if B >= s.n:
+        assert np.array_equal(cf, O.cf_split(s, mask, O.CF_RS))
+    S, ST = _graph(s, mask)
+    out = []
+    for b0 in range(0, s.n, B):
+        blk = range(b0, min(s.n, b0 + B))
+        inb = lambda j: b0 <= j < b0 + B
+        lam = {i: sum(1 for j in ST[i] if inb(j)) for i in blk}
+        st = {i: ("F" if not S[i] and not ST[i] else "U") for i in blk}
+        while "U" in st.values():
+            i = -max((lam[i], -i) for i in blk if st[i] == "U")[1]
+            st[i] = "C"
+            for j in sorted(ST[i]):
+                if inb(j) and st[j] == "U":
+                    st[j] = "F"
+                    for k in S[j]:
+                        if inb(k) and st[k] == "U":
+                            lam[k] += 1
+            for k in S[i]:
+                if inb(k) and st[k] == "U":
+                    lam[k] -= 1
+        out += [1 if st[i] == "C" else 0 for i in blk]
+    assert out == cf.tolist()
+    # every F point with connections depends on a C point
+    for i in range(s.n):
+        if cf[i] == 0 and (S[i] or ST[i]):
+            assert any(cf[j] == 1 for j in S[i])
+
+
 def test_pmis_weight_splitmix64_vector():
     # splitmix64 (Vigna): the first output of the generator seeded with 0 is 0xE220A8397B1DCDAF
     u = O.pmis_weight(0, 0, 0)
