@@ -192,6 +192,28 @@ typedef struct {
 /* Copy up to cap timers into out; *count receives the number available. */
 lair_status lair_kernel_timers(const lair_handle *h, lair_kernel_timer *out, int cap, int *count);
 
+/* Solve nsys independent dense local systems M_k z_k = rhs_k of one size s without
+ * allocating any memory. The paper has no counterpart to this entry point: it exists for
+ * callers that cannot call cudaMalloc at the point where they need the solve (code running
+ * while a CUDA graph is captured or replayed, processes whose device memory is already
+ * handed out to other pools, or latency-critical threads that must stay off the allocator).
+ * The solve is the one lair_setup uses for the rows of R (LU with partial pivoting, the
+ * minimum-norm least-squares branch for singular systems), so results are bit-identical.
+ *   M:       nsys * s * s doubles, row-major per system, device memory (not modified)
+ *   rhs:     nsys * s doubles, device memory
+ *   z:       nsys * s doubles, device memory, receives the solutions
+ *   ls_flag: nsys bytes of device memory or NULL; 1 where the least-squares branch was used
+ *   stream:  cudaStream_t (NULL = legacy default stream); the call only enqueues the work
+ * Limits: 1 <= s <= 64 (LAIR_ERR_UNSUPPORTED above). Working storage is one fixed device
+ * array of 10,194,944 bytes (152 slots of 64*64*2 + 3*64 doubles) that every GPU loading
+ * the library holds until the process exits; every call writes what it reads, so nothing
+ * of an earlier call leaks in, but all calls share the array: calls that may overlap on the
+ * GPU (different streams, or different host threads) race and must be serialised by the
+ * caller. The first call on a device looks up the array's device address; make that first
+ * call before any stream capture. Returns LAIR_ERR_INVALID_ARG for NULL pointers or s < 1. */
+lair_status lair_local_solve_noalloc(int64_t nsys, int32_t s, const double *M, const double *rhs, double *z,
+                                     uint8_t *ls_flag, void *stream);
+
 /* Number of device kernels the library has launched since the handle was created. */
 int64_t lair_kernel_launches(const lair_handle *h);
 

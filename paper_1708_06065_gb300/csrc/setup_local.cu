@@ -629,4 +629,91 @@ void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, d
     count_launch();
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free batch of local solves.
+//
+// Some callers cannot allocate device memory at the point where they need a solve: code
+// running while a CUDA graph is being captured or replayed, callers under a memory
+// budget that has already been handed out to other pools, or host threads that must not
+// touch the allocator for latency reasons. For them lair_local_solve_noalloc solves
+// caller-provided dense local systems with the same CTA-team LU / least-squares routine as
+// the set-up (so results are bit-identical to the restriction rows lair_setup produces),
+// but its working storage is the fixed device array below instead of memory from
+// cudaMalloc. Every GPU that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------------------
+constexpr int NOALLOC_SMAX = 64;        // largest system size accepted
+constexpr int NOALLOC_SLOTS = 152;      // CTAs working at once, one scratch slot each
+constexpr size_t NOALLOC_SLOT = (size_t)2 * NOALLOC_SMAX * NOALLOC_SMAX + 3 * NOALLOC_SMAX;   // doubles per slot
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// 152 slots x 8384 doubles = 10,194,944 bytes. Host code must not pass this name to a
+// kernel: on the host it only stands for the symbol; its device address is looked up below.
+static __device__ __align__(256) double g_local_scratch[NOALLOC_SLOTS * NOALLOC_SLOT];
+
+__global__ void __launch_bounds__(256) k_local_cta_dense(long long nsys, int s, const double *__restrict__ M,
+                                                         const double *__restrict__ rhs, double *__restrict__ z,
+                                                         uint8_t *__restrict__ ls, double *__restrict__ scratch) {
+    __shared__ double red[64];
+    CtaTeam tm{red};
+    double *Mw = scratch + NOALLOC_SLOT * blockIdx.x;      // this CTA's slot: M, V, rhs, z, multipliers
+    double *V = Mw + (size_t)s * s, *rw = V + (size_t)s * s, *zw = rw + s, *Lw = zw + s;
+    for (long long k = blockIdx.x; k < nsys; k += gridDim.x) {
+        const double *Mk = M + (size_t)k * s * s, *bk = rhs + (size_t)k * s;
+        // every value the solve reads is written here first: nothing of an earlier call is used
+        for (int e = threadIdx.x; e < s * s; e += blockDim.x) Mw[e] = Mk[e];
+        for (int e = threadIdx.x; e < s; e += blockDim.x) rw[e] = bk[e];
+        __syncthreads();
+        int singular = lu_solve(tm, s, Mw, rw, zw, Lw);
+        if (singular) {
+            for (int e = threadIdx.x; e < s * s; e += blockDim.x) Mw[e] = Mk[e];
+            for (int e = threadIdx.x; e < s; e += blockDim.x) rw[e] = bk[e];
+            __syncthreads();
+            jacobi_ls(tm, s, Mw, rw, V, zw);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < s; e += blockDim.x) z[(size_t)k * s + e] = zw[e];
+        if (threadIdx.x == 0 && ls) ls[k] = (uint8_t)singular;
+        __syncthreads();
+    }
+}
+
 }  // namespace lair
+
+#include <mutex>
+
+namespace {
+// device address of g_local_scratch for each device, looked up once with that device current
+double *g_noalloc_ptr[lair::NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+extern "C" lair_status lair_local_solve_noalloc(int64_t nsys, int32_t s, const double *M, const double *rhs, double *z,
+                                                uint8_t *ls_flag, void *stream) {
+    using namespace lair;
+    if (nsys < 0 || (nsys > 0 && (!M || !rhs || !z))) return LAIR_ERR_INVALID_ARG;
+    if (s < 1) return LAIR_ERR_INVALID_ARG;
+    if (s > NOALLOC_SMAX) return LAIR_ERR_UNSUPPORTED;        // the scratch slots hold systems up to 64 x 64
+    if (nsys == 0) return LAIR_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return LAIR_ERR_CUDA;
+    }
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_local_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LAIR_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int grid = nsys < NOALLOC_SLOTS ? (int)nsys : NOALLOC_SLOTS;
+    k_local_cta_dense<<<grid, 256, 0, (cudaStream_t)stream>>>((long long)nsys, s, M, rhs, z, ls_flag, scratch);
+    return cudaGetLastError() == cudaSuccess ? LAIR_OK : LAIR_ERR_CUDA;
+}
+

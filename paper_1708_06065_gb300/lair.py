@@ -81,6 +81,7 @@ def _load():
         "lair_export_cf": (C.c_int, [p, C.c_int, p, p, p, p]),
         "lair_kernel_launches": (C.c_int64, [p]),
         "lair_kernel_timers": (C.c_int, [p, C.POINTER(lair_kernel_timer), C.c_int, C.POINTER(C.c_int)]),
+        "lair_local_solve_noalloc": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, p]),
         "lair_free": (None, [p]),
         "lair_status_string": (C.c_char_p, [C.c_int]),
         "lair_last_error": (C.c_char_p, [p]),
