@@ -33,8 +33,9 @@ METRIC = "unknowns/s to 1e-8 rel. residual (setup+solve), mixed vs FP64; % HBM p
 WORKLOADS = {
     "dg_p2_256": dict(
         desc="2D upwind DG-P2, 256x256 squares x 2 triangles (n=786432), recirculating velocity, backward Euler dt=h, "
-             "block-diagonal scaling; lAIR distance 2, one-point P, |a| strength 0.25; FP32 cycle in FP64 FGMRES(30), tol 1e-8",
-        opts=dict(distance=2, interp=1, strength_abs=1, block_size=6), tol=1e-8, sample_scale=64),
+             "block-diagonal scaling; lAIR distance 2, one-point P, |a| strength 0.25, PMIS splitting; "
+             "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
+        opts=dict(distance=2, interp=1, strength_abs=1, block_size=6, cf_mode=1), tol=1e-8, sample_scale=64),
     "fd3d_192": dict(
         desc="3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1; "
              "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
@@ -150,6 +151,8 @@ def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
     s = W.config(workload, scale=wl["sample_scale"])
     kw = dict(wl["opts"])
     okw = dict(distance=kw["distance"], prec=1)
+    if "cf_mode" in kw:
+        okw["cf_mode"] = kw["cf_mode"]
     if "interp" in kw:
         okw["interp"] = kw["interp"]
     if "strength_abs" in kw:
@@ -261,11 +264,9 @@ def main():
             ev0.record(stream)
             if host is None:
                 G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
-                x.zero_() if False else None
-                xx = torch.zeros(n, dtype=torch.float64, device=dev) if False else x
                 with torch.cuda.stream(stream):
-                    xx.zero_()
-                _, rep = G.solve(b, xx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
+                    x.zero_()
+                _, rep = G.solve(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
             else:
                 hrp, hcol, hval, hb, hx = host
                 hx.zero_()

@@ -146,6 +146,33 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **h
 lair_status lair_solve(lair_handle *h, const double *b, double *x, double tol, int cycle,
                        int max_iter, lair_report *rep);
 
+/* Batched independent systems (spec pattern 2). A is the block-diagonal matrix of
+ * nsys systems; sys_offsets (host, nsys + 1 entries, from 0 to n) gives each system's first
+ * row. One hierarchy is built for the whole batch, so every set-up and cycle step is one
+ * launch over all systems of all sizes; nothing couples the systems (the C/F splitting
+ * blocks never span two systems), so each system gets the hierarchy it would get alone,
+ * apart from the common number of levels. User splittings and block scaling are not
+ * available here (LAIR_ERR_INVALID_ARG / LAIR_ERR_UNSUPPORTED). */
+lair_status lair_setup_batched(const lair_csr *A, int nsys, const int64_t *sys_offsets, const lair_options *o,
+                               lair_handle **h);
+
+/* Solve every system of a batched handle to its own relative residual
+ * ||b_q - A_q x_q|| / ||b_q|| <= tol. cycle: LAIR_CYCLE_STATIONARY (FP64 refinement; a system
+ * is no longer updated once it has converged) or LAIR_CYCLE_FGMRES (FGMRES per system, all
+ * systems stepping together, each with its own rotations, stopping test and restarts).
+ * b, x: n doubles (host or device; x holds the initial guess). iters and rel (host, nsys
+ * entries, may be NULL) receive per-system cycle counts and final relative residuals.
+ * Returns LAIR_ERR_NOT_CONVERGED if some system is still above tol after max_iter cycles. */
+lair_status lair_solve_batched(lair_handle *h, const double *b, double *x, double tol, int cycle, int max_iter,
+                               int *iters, double *rel);
+
+/* Convenience: set up and solve nsys separate systems in one batch. A[q] (host or device
+ * arrays, per A[q].on_device), b[q] and x[q] (host or device, x[q] holds the initial guess
+ * and receives the solution) describe system q. The systems are concatenated on the host,
+ * solved with lair_setup_batched + lair_solve_batched, and the handle is released. */
+lair_status lair_batch_setup_solve(int nsys, const lair_csr *A, const double *const *b, double *const *x,
+                                   const lair_options *o, double tol, int cycle, int max_iter, int *iters, double *rel);
+
 /* x = M^{-1} b: one V-cycle with zero initial guess (Sec. 4 cycle), in the
  * handle's precision. b, x: n doubles, host or device. */
 lair_status lair_precond_apply(lair_handle *h, const double *b, double *x);

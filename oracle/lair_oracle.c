@@ -67,6 +67,8 @@ typedef struct {
     int block_size;        /* >1: scale by the inverse block diagonal first */
     int rs_block;          /* AUTO: index-block size of the blocked first pass */
     uint64_t pmis_seed;
+    const int64_t *seg;    /* batched systems: nseg + 1 offsets of the independent systems on level 0 */
+    int nseg;
 } ora_opts;
 
 /* ------------------------------------------------------------------------- */
@@ -282,11 +284,22 @@ static void cf_rs_block(const ograph *S, const ograph *ST, int64_t b0, int64_t b
     free(h.a);
 }
 
-static void cf_rs_blocked(const ograph *S, const ograph *ST, int64_t B, int8_t *cf) {
+/* blocks of at most B points; with system offsets seg (nseg + 1 entries) no block spans two systems */
+static void cf_rs_blocked_seg(const ograph *S, const ograph *ST, int64_t B, const int64_t *seg, int nseg, int8_t *cf) {
     int64_t n = S->n;
     int64_t *lam = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    for (int64_t b0 = 0; b0 < n; b0 += B) cf_rs_block(S, ST, b0, b0 + B < n ? b0 + B : n, cf, lam);
+    if (!seg || nseg <= 0) {
+        for (int64_t b0 = 0; b0 < n; b0 += B) cf_rs_block(S, ST, b0, b0 + B < n ? b0 + B : n, cf, lam);
+    } else {
+        for (int q = 0; q < nseg; ++q)
+            for (int64_t b0 = seg[q]; b0 < seg[q + 1]; b0 += B)
+                cf_rs_block(S, ST, b0, b0 + B < seg[q + 1] ? b0 + B : seg[q + 1], cf, lam);
+    }
     free(lam);
+}
+
+static void cf_rs_blocked(const ograph *S, const ograph *ST, int64_t B, int8_t *cf) {
+    cf_rs_blocked_seg(S, ST, B, NULL, 0, cf);
 }
 
 static void cf_rs(const ograph *S, const ograph *ST, int8_t *cf) {
@@ -1080,6 +1093,7 @@ typedef struct {
     uint8_t *ls_R, *ls_P;
     double *dinv;
     float *A32, *R32, *P32, *dinv32;
+    int64_t *seg;      /* batched systems: offsets of the systems on this level (nseg + 1) */
 } olevel;
 
 typedef struct {
@@ -1135,7 +1149,7 @@ static int coarsen_level(ohier *H, int l, int *is_last) {
         for (int64_t i = 0; i < n; ++i) L->cf[i] = o->cf_user[i] ? CF_C : CF_F;
     } else {
         if (o->cf_mode == 0) cf_rs(&Scf, &STcf, L->cf);
-        else if (o->cf_mode != 1) cf_rs_blocked(&Scf, &STcf, o->rs_block, L->cf);
+        else if (o->cf_mode != 1) cf_rs_blocked_seg(&Scf, &STcf, o->rs_block, L->seg, o->nseg, L->cf);
         else cf_pmis(&Scf, &STcf, o->pmis_seed + (uint64_t)l, L->cf);
     }
     L->cidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -1146,6 +1160,16 @@ static int coarsen_level(ohier *H, int l, int *is_last) {
         graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
         *is_last = 1;
         return ORA_OK;
+    }
+    if (o->nseg > 0 && L->seg) {
+        /* the systems' offsets on the next level: C points before each system's first point */
+        olevel *Ln = &H->lev[l + 1];
+        Ln->seg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(o->nseg + 1));
+        int64_t c = 0, i = 0;
+        for (int q = 0; q <= o->nseg; ++q) {
+            for (; i < L->seg[q] && i < n; ++i) c += (L->cf[i] == CF_C);
+            Ln->seg[q] = c;
+        }
     }
     int64_t *cpts = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
     for (int64_t i = 0; i < n; ++i) if (L->cf[i] == CF_C) cpts[L->cidx[i]] = i;
@@ -1217,7 +1241,7 @@ void ora_free(ohier *H) {
         olevel *L = &H->lev[l];
         csr_free(&L->A); csr_free(&L->R); csr_free(&L->P);
         free(L->cf); free(L->cidx); free(L->strong); free(L->strong_cf); free(L->ls_R); free(L->ls_P);
-        free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32);
+        free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32); free(L->seg);
         for (int k = 0; k < 4; ++k) { free(H->w64[l][k]); free(H->w32[l][k]); }
     }
     free(H->coarse.LU); free(H->coarse.perm); free(H->blk_inv);
@@ -1243,6 +1267,11 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
         memcpy(A0->col, col, sizeof(int32_t) * (size_t)nnz);
         memcpy(A0->val, val, sizeof(double) * (size_t)nnz);
     }
+    if (opts->nseg > 0 && opts->seg) {
+        H->lev[0].seg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(opts->nseg + 1));
+        memcpy(H->lev[0].seg, opts->seg, sizeof(int64_t) * (size_t)(opts->nseg + 1));
+    }
+    H->o.seg = NULL;   /* not retained */
     if (opts->lump_level0 && opts->lump_tol > 0.0) {
         int st = lump(A0, opts->lump_tol);
         if (st) { *status = st; H->nlev = 1; return H; }
@@ -1495,6 +1524,84 @@ int ora_solve(ohier *H, const double *b_in, double *x, double tol, int cycle, in
 }
 
 /* ------------------------------------------------------------------------- */
+/* Batched systems (a block-diagonal matrix with nseg systems): stationary      */
+/* refinement x_q += (M^{-1} r)_q where every system q is tested on its own     */
+/* relative residual and stops being updated once it is <= tol.               */
+/* ------------------------------------------------------------------------- */
+int ora_solve_batched(ohier *H, const double *b, double *x, double tol, int max_iter, int *iters, double *rel) {
+    const ocsr *A = &H->lev[0].A;
+    int64_t n = A->nr;
+    int nseg = H->o.nseg;
+    const int64_t *seg = H->lev[0].seg;
+    if (nseg <= 0 || !seg) return ORA_ERR_ARG;
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *e = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *bn = (double *)malloc(sizeof(double) * (size_t)nseg);
+    int *active = (int *)malloc(sizeof(int) * (size_t)nseg);
+    for (int q = 0; q < nseg; ++q) {
+        double t = 0.0;
+        for (int64_t i = seg[q]; i < seg[q + 1]; ++i) t = fma(b[i], b[i], t);
+        bn[q] = t > 0.0 ? sqrt(t) : 1.0;
+        iters[q] = 0;
+        active[q] = 1;
+    }
+    int status = ORA_OK;
+    for (int it = 0;; ++it) {
+        residual(A, b, x, r);
+        int any = 0;
+        for (int q = 0; q < nseg; ++q) {
+            if (!active[q]) continue;
+            double t = 0.0;
+            for (int64_t i = seg[q]; i < seg[q + 1]; ++i) t = fma(r[i], r[i], t);
+            rel[q] = sqrt(t) / bn[q];
+            if (rel[q] != rel[q]) { status = ORA_ERR_NAN; active[q] = 0; continue; }
+            if (rel[q] <= tol || it >= max_iter) active[q] = 0;
+            else any = 1;
+        }
+        if (!any) break;
+        precond(H, r, e);
+        for (int q = 0; q < nseg; ++q) {
+            if (!active[q]) continue;
+            for (int64_t i = seg[q]; i < seg[q + 1]; ++i) x[i] += e[i];
+            iters[q] += 1;
+        }
+    }
+    for (int q = 0; q < nseg && status == ORA_OK; ++q)
+        if (!(rel[q] <= tol)) status = ORA_ERR_NOT_CONVERGED;
+    free(r); free(e); free(bn); free(active);
+    return status;
+}
+
+/* Batched systems with FGMRES: every system q is solved on its own (FGMRES with  */
+/* the block-diagonal hierarchy applied to vectors that vanish outside q, which   */
+/* keeps them inside q), with its own restarts and stopping test.               */
+int ora_solve_batched_fgmres(ohier *H, const double *b, double *x, double tol, int max_iter, int restart,
+                             int *iters, double *rel) {
+    const ocsr *A = &H->lev[0].A;
+    int64_t n = A->nr;
+    int nseg = H->o.nseg;
+    const int64_t *seg = H->lev[0].seg;
+    if (nseg <= 0 || !seg) return ORA_ERR_ARG;
+    double *bq = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *xq = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int status = ORA_OK;
+    for (int q = 0; q < nseg; ++q) {
+        memset(bq, 0, sizeof(double) * (size_t)n);
+        memset(xq, 0, sizeof(double) * (size_t)n);
+        for (int64_t i = seg[q]; i < seg[q + 1]; ++i) { bq[i] = b[i]; xq[i] = x[i]; }
+        int it = 0;
+        double r = 0.0;
+        int st = ora_solve(H, bq, xq, tol, 1, max_iter, restart, &it, &r, NULL, 0);
+        iters[q] = it;
+        rel[q] = r;
+        for (int64_t i = seg[q]; i < seg[q + 1]; ++i) x[i] = xq[i];
+        if (st != ORA_OK && status == ORA_OK) status = st;
+    }
+    free(bq); free(xq);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Export for tests                                                           */
 /* ------------------------------------------------------------------------- */
 int ora_nlevels(const ohier *H) { return H->nlev; }
@@ -1511,6 +1618,10 @@ void ora_level_info(const ohier *H, int l, int64_t *info) {
     info[5] = L->cf != NULL;
     info[6] = 0;
     info[7] = 0;
+}
+
+void ora_export_seg(const ohier *H, int l, int64_t *seg) {
+    if (H->lev[l].seg) memcpy(seg, H->lev[l].seg, sizeof(int64_t) * (size_t)(H->o.nseg + 1));
 }
 
 /* which: 0 A, 1 R, 2 P */

@@ -40,7 +40,7 @@ class Opts(C.Structure):
         ("theta", C.c_double), ("theta_cf", C.c_double), ("strength_abs", C.c_int),
         ("interp", C.c_int), ("relax", C.c_int), ("lump_tol", C.c_double), ("lump_level0", C.c_int),
         ("prec", C.c_int), ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
-        ("rs_block", C.c_int), ("pmis_seed", C.c_uint64),
+        ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("seg", C.c_void_p), ("nseg", C.c_int),
     ]
 
 
@@ -79,6 +79,11 @@ def lib():
         L.ora_block_scale_nnz.argtypes = [C.c_int64, p, p, C.c_int64]
         L.ora_block_scale.restype = C.c_int
         L.ora_block_scale.argtypes = [C.c_int64, p, p, p, C.c_int64, p, p, p, p]
+        L.ora_solve_batched.restype = C.c_int
+        L.ora_solve_batched.argtypes = [p, p, p, C.c_double, C.c_int, p, p]
+        L.ora_export_seg.argtypes = [p, C.c_int, p]
+        L.ora_solve_batched_fgmres.restype = C.c_int
+        L.ora_solve_batched_fgmres.argtypes = [p, p, p, C.c_double, C.c_int, C.c_int, p, p]
         L.ora_transpose.restype = C.c_int64
         L.ora_transpose.argtypes = [C.c_int64, p, p, p, p, p, p]
         _lib = L
@@ -125,10 +130,15 @@ class Level:
 class Hierarchy:
     """An oracle hierarchy: ``Hierarchy(A, **opts)``; ``levels`` holds host copies."""
 
-    def __init__(self, A, cf_user=None, **kw):
+    def __init__(self, A, cf_user=None, seg=None, **kw):
         L = lib()
         self.opts = default_opts(**kw)
         self._keep = []
+        if seg is not None:
+            sg = np.ascontiguousarray(seg, np.int64)
+            self._keep.append(sg)
+            self.opts.seg = sg.ctypes.data
+            self.opts.nseg = len(sg) - 1
         if cf_user is not None:
             cfu = np.ascontiguousarray(cf_user, np.int8)
             self._keep.append(cfu)
@@ -186,6 +196,25 @@ class Hierarchy:
                              C.byref(it), C.byref(rel), _ptr(hist), hist_cap)
         nh = min(hist_cap, it.value + 1 if cycle == 0 else hist_cap)
         return x, dict(status=st, iters=it.value, rel=rel.value, hist=hist[:nh])
+
+    def solve_batched(self, b, tol=1e-8, max_iter=500, cycle=0, restart=30):
+        """Per-system solves of a batch (systems given by seg at set-up): stationary refinement
+        (cycle 0) or FGMRES per system (cycle 1)."""
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros_like(b)
+        nseg = self.opts.nseg
+        its = np.zeros(nseg, np.int32)
+        rel = np.zeros(nseg)
+        if cycle == 0:
+            st = lib().ora_solve_batched(self.h, _ptr(b), _ptr(x), tol, max_iter, _ptr(its), _ptr(rel))
+        else:
+            st = lib().ora_solve_batched_fgmres(self.h, _ptr(b), _ptr(x), tol, max_iter, restart, _ptr(its), _ptr(rel))
+        return x, dict(status=st, iters=its, rel=rel)
+
+    def seg(self, level):
+        out = np.zeros(self.opts.nseg + 1, np.int64)
+        lib().ora_export_seg(self.h, level, _ptr(out))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

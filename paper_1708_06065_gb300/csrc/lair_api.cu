@@ -47,6 +47,12 @@ struct Level {
     bool coarsest = false;
     double *Ainv = nullptr;
     long long nF = 0, nnzF = 0, nC = 0, nnzC = 0;   // rows and entries by kind (for byte counts)
+    std::vector<int> seg_h;   // batched systems: first row of every system on this level, nseg + 1 entries
+    int *seg_d = nullptr;
+    // cycle storage: sliced-ELL views of the F rows and C rows of A, of R and of P (cycle precision)
+    int *frows = nullptr, *crows = nullptr;
+    SellView AF, AC, Rv, Pv;
+    SellView A64;             // level 0: all rows of A in FP64 for the outer iteration
 };
 
 struct Hier {
@@ -88,6 +94,15 @@ struct lair_handle {
     std::vector<Pending> graph_events;   // events inside the captured cycle graph
     std::vector<cudaEvent_t> ev_pool;
     bool graph_pending = false;
+    // batched systems (block-diagonal input)
+    int nseg = 0;
+    std::vector<int> seg0;
+    double *h_seg = nullptr;      // pinned, nseg doubles
+    uint8_t *h_act = nullptr;     // pinned, nseg bytes
+    double *h_bat = nullptr;      // pinned, nseg * 32 doubles (per-system Hessenberg columns)
+    double *d_bat = nullptr;      // device, nseg * (3 * 32 + 1) doubles: sums, pass values, y, norms
+    int *d_batcnt = nullptr;      // device, nseg ints
+    int *h_batcnt = nullptr;      // pinned, nseg ints
 };
 
 namespace lair {
@@ -194,20 +209,24 @@ static cudaEvent_t get_event(lair_handle *h) {
 }
 
 // begin/end around one launch; in_graph: the events become nodes of the graph being captured
+// returns the index of the event pair (for tend), or -1 when timing is off
 static int tbegin(lair_handle *h, const std::string &name, double bytes, bool in_graph = false) {
     if (!h->o.timing) return -1;
     int slot = timer_slot(h, name, bytes);
     lair_handle::Pending p{slot, get_event(h), get_event(h)};
-    cudaEventRecord(p.a, h->s);
-    if (in_graph) h->graph_events.push_back(p);
-    else h->pending.push_back(p);
-    return slot;
+    // inside stream capture only an external record becomes an event node of the graph
+    if (in_graph) cudaEventRecordWithFlags(p.a, h->s, cudaEventRecordExternal);
+    else cudaEventRecord(p.a, h->s);
+    auto &v = in_graph ? h->graph_events : h->pending;
+    v.push_back(p);
+    return (int)v.size() - 1;
 }
 
-static void tend(lair_handle *h, int slot, bool in_graph = false) {
-    if (slot < 0) return;
+static void tend(lair_handle *h, int pair, bool in_graph = false) {
+    if (pair < 0) return;
     auto &v = in_graph ? h->graph_events : h->pending;
-    cudaEventRecord(v.back().b, h->s);
+    if (in_graph) cudaEventRecordWithFlags(v[pair].b, h->s, cudaEventRecordExternal);
+    else cudaEventRecord(v[pair].b, h->s);
 }
 
 // call only after the stream has been synchronised
@@ -281,7 +300,6 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
     launch_col_count(nr, rp, col, cnt, h->s);
     if (keep) TRY(dalloc(h, trp, (size_t)nc + 1));
     else TRY(t.get(trp, (size_t)nc + 1));
-    int total = 0;
     TRY(scan(h, cnt, *trp, nc, nullptr));
     CU(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)nc + 1), h->s));
     if (keep) {
@@ -293,7 +311,6 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
     }
     launch_transpose_scatter(nr, rp, col, val, *trp, cnt, *tcol, val ? *tval : nullptr, h->s);
     launch_sort_rows(nc, *trp, *tcol, val ? *tval : nullptr, h->s);
-    (void)total;
     return LAIR_OK;
 }
 
@@ -386,21 +403,22 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(t.get(&tcol, (size_t)total));
     TRY(t.get(&tval, (size_t)total));
     TRY(new_counts(h, t, &cnt, nr));
-    TRY(t.get(&lists, (size_t)2 * nr + 1));
-    TRY(new_counts(h, t, &bc, 3));
-    launch_spgemm_classify(nr, off, lists, bc, bc + 2, h->s);
-    int hc[3];
-    TRY(read_ints(h, bc, 3, hc));
+    TRY(t.get(&lists, (size_t)SPGEMM_BINS * nr + 1));
+    TRY(new_counts(h, t, &bc, SPGEMM_BINS + 1));
+    launch_spgemm_classify(nr, off, lists, bc, bc + SPGEMM_BINS, h->s);
+    int hc[SPGEMM_BINS + 1];
+    TRY(read_ints(h, bc, SPGEMM_BINS + 1, hc));
     int *skeys = nullptr;
     double *svals = nullptr;
-    if (hc[1] > 0) {
-        size_t cap = spgemm_big_cap(hc[2]);
-        size_t slots = 2 * cap * (size_t)(hc[1] < SPGEMM_CTA_GRID ? hc[1] : SPGEMM_CTA_GRID);
+    const int nbig = hc[SPGEMM_BINS - 1], ubmax = hc[SPGEMM_BINS];
+    if (nbig > 0) {
+        size_t cap = spgemm_big_cap(ubmax);
+        size_t slots = 2 * cap * (size_t)(nbig < SPGEMM_CTA_GRID ? nbig : SPGEMM_CTA_GRID);
         TRY(t.get(&skeys, slots));
         TRY(t.get(&svals, slots));
     }
     SpgemmArgs g{X.rp, X.col, X.val, Y.rp, Y.col, Y.val, off, tcol, tval, cnt};
-    CU(launch_spgemm_rows(g, nr, lists, bc, hc, hc[2], skeys, svals, h->s));
+    CU(launch_spgemm_rows(g, nr, lists, bc, hc, ubmax, skeys, svals, h->s));
     Z.nr = nr;
     Z.nc = Y.nc;
     if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
@@ -452,12 +470,29 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         normalize_cf(n, L.cf, h->s);
     } else {
         if (o.cf_mode != LAIR_CF_PMIS) {
-            // RS: the exact first pass (one block); AUTO: the first pass in blocks of rs_block points
-            int B = o.cf_mode == LAIR_CF_RS ? n : o.rs_block;
-            if (B > RS_MAX_N)
-                return fail(h, LAIR_ERR_UNSUPPORTED, "the first pass runs on at most %d points at once (level %d has %d)",
-                            RS_MAX_N, l, n);
-            CU(launch_rs(n, B, Scf, STcf, L.cf, h->status, h->s));
+            // RS: the exact first pass (one block per system); AUTO: the first pass in blocks of rs_block points.
+            // Blocks never span two batched systems.
+            std::vector<int> cuts = L.seg_h;
+            if (cuts.empty()) cuts = {0, n};
+            std::vector<int2> blocks;
+            int Bmax = 1;
+            for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+                const int s0 = cuts[q], s1 = cuts[q + 1];
+                const int B = o.cf_mode == LAIR_CF_RS ? (s1 - s0) : o.rs_block;
+                if (B > RS_MAX_N)
+                    return fail(h, LAIR_ERR_UNSUPPORTED,
+                                "the first pass runs on at most %d points at once (level %d has %d)", RS_MAX_N, l, B);
+                for (int b0 = s0; b0 < s1; b0 += B) {
+                    int b1 = b0 + B < s1 ? b0 + B : s1;
+                    blocks.push_back(make_int2(b0, b1));
+                    if (b1 - b0 > Bmax) Bmax = b1 - b0;
+                }
+            }
+            int2 *bd;
+            TRY(t.get(&bd, blocks.size()));
+            CU(cudaMemcpyAsync(bd, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, h->s));
+            CU(launch_rs(n, bd, (int)blocks.size(), Bmax, Scf, STcf, L.cf, h->status, h->s));
+            CU(cudaStreamSynchronize(h->s));   // the host block list must outlive the copy
         } else {
             double *w;
             int8_t *newc;
@@ -466,9 +501,12 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
             TRY(t.get(&newc, (size_t)n));
             TRY(new_counts(h, t, &und, 1));
             launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, L.cf, h->s);
-            for (int round = 0; round <= n; ++round) {
+            // rounds after the last undecided point is gone change nothing, so the host looks
+            // at the count only every few rounds
+            const int every = 4;
+            for (int round = 0; round <= n; round += every) {
                 CU(cudaMemsetAsync(und, 0, sizeof(int), h->s));
-                launch_pmis_round(n, Scf, STcf, w, L.cf, newc, und, h->s);
+                for (int k = 0; k < every; ++k) launch_pmis_round(n, Scf, STcf, w, L.cf, newc, und, h->s);
                 int u = 0;
                 TRY(read_ints(h, und, 1, &u));
                 if (u == 0) break;
@@ -490,8 +528,24 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         return LAIR_OK;
     }
     TRY(dalloc(h, &L.cidx, (size_t)n));
-    TRY(t.get(&cpts, (size_t)nc));
+    TRY(dalloc(h, &cpts, (size_t)nc));
     launch_cidx(n, L.cf, scanv, L.cidx, cpts, 1, h->s);
+    L.crows = cpts;
+    if (n - nc > 0) {
+        TRY(dalloc(h, &L.frows, (size_t)(n - nc)));
+        launch_frows(n, L.cf, scanv, L.frows, h->s);
+    }
+    std::vector<int> next_seg;
+    if (!L.seg_h.empty()) {
+        // a system's first coarse point: number of C points before its first fine point
+        const int m = (int)L.seg_h.size();
+        int *g;
+        TRY(t.get(&g, (size_t)m));
+        gather_int(m, L.seg_d, scanv, g, h->s);
+        next_seg.resize(m);
+        CU(cudaMemcpyAsync(next_seg.data(), g, sizeof(int) * m, cudaMemcpyDeviceToHost, h->s));
+        TRY(sync_status(h));
+    }
 
     // ---- restriction (lAIR): local systems of A on the neighbourhoods in S
     TRY(dalloc(h, &L.lsR, (size_t)nc));
@@ -558,9 +612,65 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     } else {
         next.A = K;
     }
+    if (!next_seg.empty()) {
+        next.seg_h = next_seg;
+        TRY(dalloc(h, &next.seg_d, next_seg.size()));
+        CU(cudaMemcpyAsync(next.seg_d, next.seg_h.data(), sizeof(int) * next_seg.size(), cudaMemcpyHostToDevice, h->s));
+    }
     TRY(sync_status(h));
     H.lev.push_back(next);
     *last = false;
+    return LAIR_OK;
+}
+
+// build sliced-ELL views; all totals are read back with one synchronisation
+struct SellPlan {
+    SellView *v;
+    const DCsr *M;
+    const int *rows_in;   // NULL: all rows in order
+    int nrows;
+    const double *dinv;   // NULL: no diagonal
+    bool fp32;
+    int *cnt = nullptr;
+};
+
+static lair_status build_sells(lair_handle *h, std::vector<SellPlan> &plans) {
+    Temps t(h);
+    for (auto &p : plans) {
+        SellView &v = *p.v;
+        v.nrows = p.nrows;
+        if (p.nrows <= 0) continue;
+        const int nsl = (p.nrows + 31) / 32;
+        TRY(dalloc(h, &v.row, (size_t)p.nrows));
+        TRY(new_counts(h, t, &p.cnt, nsl));
+        launch_sell_prepare(p.nrows, p.rows_in, p.M->rp, v.row, p.cnt, h->s);
+        TRY(dalloc(h, &v.slice_ptr, (size_t)nsl + 1));
+        TRY(scan(h, p.cnt, v.slice_ptr, nsl, nullptr));
+    }
+    int k = 0;
+    for (auto &p : plans) {
+        if (p.nrows <= 0) continue;
+        const int nsl = (p.nrows + 31) / 32;
+        CU(cudaMemcpyAsync(h->h_int + 8 + k, p.v->slice_ptr + nsl, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        ++k;
+    }
+    TRY(sync_status(h));
+    k = 0;
+    for (auto &p : plans) {
+        if (p.nrows <= 0) continue;
+        const int total = h->h_int[8 + k++];
+        const size_t el = p.fp32 ? sizeof(float) : sizeof(double);
+        unsigned char *vv;
+        TRY(dalloc(h, &p.v->col, (size_t)total));
+        TRY(dalloc(h, &vv, el * (size_t)total));
+        p.v->val = vv;
+        if (p.dinv) {
+            unsigned char *dd;
+            TRY(dalloc(h, &dd, el * (size_t)p.nrows));
+            p.v->dinv = dd;
+        }
+        launch_sell_fill(*p.v, *p.M, p.dinv, p.fp32, h->s);
+    }
     return LAIR_OK;
 }
 
@@ -581,6 +691,18 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
         CU(cudaMemcpyAsync(hs, st, sizeof hs, cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
         L.nF = (long long)hs[0]; L.nnzF = (long long)hs[1]; L.nC = (long long)hs[2]; L.nnzC = (long long)hs[3];
+    }
+    if (!L.coarsest || l == 0) {
+        std::vector<SellPlan> plans;
+        if (!L.coarsest) {
+            const int n = L.A.nr, nc = L.nc;
+            plans.push_back(SellPlan{&L.AF, &L.A, L.frows, n - nc, L.dinv, fp32});
+            plans.push_back(SellPlan{&L.AC, &L.A, L.crows, nc, L.dinv, fp32});
+            plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
+            plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
+        }
+        if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
+        TRY(build_sells(h, plans));
     }
     if (fp32) {
         TRY(dalloc(h, &L.A.val32, (size_t)L.A.nnz));
@@ -632,18 +754,20 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     }
     Level &C = H.lev[l + 1];
     int t = tm ? tbegin(h, "L0_restrict", bytes_spmv(L.R, sv), true) : -1;
-    spmv<T>(L.R, B::b(L), B::b(C), h->s);
+    sell_spmv<T>(L.Rv, B::b(L), B::b(C), h->s);
     if (tm) tend(h, t, true);
     record_cycle<T>(h, H, l + 1);
     t = tm ? tbegin(h, "L0_interp", bytes_spmv(L.P, sv), true) : -1;
-    spmv<T>(L.P, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    sell_spmv<T>(L.Pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
     if (tm) tend(h, t, true);
     int cur = 0;
+    const int n = L.A.nr, nc = L.nc;
     for (int k = 0; k < 3; ++k) {
         int tg = relax_seq[h->o.relax][k];
         if (tg < 0) break;
         t = tm ? tbegin(h, tg == CF_F ? "L0_sweep_F" : "L0_sweep_C", bytes_sweep(L, tg, sv), true) : -1;
-        sweep<T>(L.A, L.cf, tg, B::dinv(L), B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
+        if (tg == CF_F) sell_sweep<T>(L.AF, L.crows, nc, B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
+        else sell_sweep<T>(L.AC, L.frows, n - nc, B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
         if (tm) tend(h, t, true);
         cur ^= 1;
     }
@@ -715,15 +839,21 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         }
         L0.A = A;
     }
+    if (!h->seg0.empty()) {
+        L0.seg_h = h->seg0;
+        TRY(dalloc(h, &L0.seg_d, L0.seg_h.size()));
+        CU(cudaMemcpyAsync(L0.seg_d, L0.seg_h.data(), sizeof(int) * L0.seg_h.size(), cudaMemcpyHostToDevice, h->s));
+        CU(cudaStreamSynchronize(h->s));
+    }
     H.lev.push_back(L0);
     for (int l = 0;; ++l) {
         const int n = H.lev[l].A.nr;
         bool last = n <= o.coarse_max || l + 1 >= o.max_levels;
         if (!last) TRY(coarsen(h, H, l, l == 0 ? cf_user : nullptr, &last));
+        if (last) H.lev[l].coarsest = true;
         TRY(finish_level(h, H, l));
         if (last) {
             Level &L = H.lev[l];
-            L.coarsest = true;
             if (n > 4096)
                 return fail(h, LAIR_ERR_COARSENING_STALLED, "coarsening stopped at level %d with %d unknowns", l, n);
             Temps t(h);
@@ -871,7 +1001,7 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
                 TRY(precond(h, H, vj, zj));
                 ++it;
                 int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
-                spmv<double>(A, zj, w, h->s);
+                sell_spmv<double>(L0.A64, zj, w, h->s);
                 tend(h, ts);
                 CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (j + 1), h->s));
                 for (int pass = 0; pass < 2; ++pass) {
@@ -932,6 +1062,190 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
     }
     if (st == LAIR_ERR_NOT_CONVERGED) fail(h, st, "not converged: relative residual %.3e after %d cycles", rel, it);
     if (st == LAIR_ERR_NAN) fail(h, st, "residual became NaN/Inf after %d cycles", it);
+    return st;
+}
+
+// batched systems: stationary refinement where every system is tested on its own relative
+// residual and stops being updated once it is <= tol (the cycle itself acts on all systems)
+static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
+                                     int *iters, double *rel) {
+    Level &L0 = H.lev[0];
+    const DCsr &A = L0.A;
+    const int n = A.nr, nseg = h->nseg;
+    const bool mixed = h->o.precision == LAIR_MIXED;
+    TRY(ensure_work(h, n, 0));
+    double *nrm;
+    uint8_t *act;
+    {
+        // device scratch for the per-system norms and flags lives in the handle's FP64 work area
+        nrm = h->part;                                  // RED_PARTS * 33 doubles >= nseg
+        act = reinterpret_cast<uint8_t *>(h->part + (size_t)RED_PARTS * 16);
+    }
+    if ((size_t)nseg > (size_t)RED_PARTS * 16) return fail(h, LAIR_ERR_UNSUPPORTED, "at most %d systems", RED_PARTS * 16);
+    std::vector<double> bn(nseg), rl(nseg, 0.0);
+    std::vector<int> its(nseg, 0);
+    std::vector<uint8_t> active(nseg, 1);
+    seg_norm2(nseg, L0.seg_d, b, nrm, h->s);
+    CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
+    lair_status st = LAIR_OK;
+    for (int it = 0;; ++it) {
+        double *r = mixed ? h->wr : L0.b64;
+        seg_residual(A, nseg, L0.seg_d, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
+        CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        flush_timers(h);
+        int any = 0;
+        for (int q = 0; q < nseg; ++q) {
+            if (!active[q]) continue;
+            rl[q] = std::sqrt(h->h_seg[q]) / bn[q];
+            if (!std::isfinite(rl[q])) { st = LAIR_ERR_NAN; active[q] = 0; continue; }
+            if (rl[q] <= tol || it >= max_iter) active[q] = 0;
+            else any = 1;
+        }
+        if (!any) break;
+        for (int q = 0; q < nseg; ++q) h->h_act[q] = active[q];
+        CU(cudaMemcpyAsync(act, h->h_act, nseg, cudaMemcpyHostToDevice, h->s));
+        CU(cudaGraphLaunch(H.graph, h->s));
+        count_launch(H.graph_nodes);
+        h->graph_pending = h->o.timing;
+        if (mixed) seg_axpy<float>(nseg, L0.seg_d, act, L0.x32[L0.xfinal], x, h->s);
+        else seg_axpy<double>(nseg, L0.seg_d, act, L0.x64[L0.xfinal], x, h->s);
+        for (int q = 0; q < nseg; ++q) its[q] += active[q];
+    }
+    CU(cudaStreamSynchronize(h->s));
+    int worst = 0;
+    for (int q = 0; q < nseg; ++q) {
+        if (iters) iters[q] = its[q];
+        if (rel) rel[q] = rl[q];
+        if (st == LAIR_OK && !(rl[q] <= tol)) { st = LAIR_ERR_NOT_CONVERGED; worst = q; }
+    }
+    if (st == LAIR_ERR_NOT_CONVERGED) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
+    return st;
+}
+
+// batched systems, right-preconditioned FGMRES(m) per system in lockstep: one Arnoldi step for
+// every running system per iteration (classical Gram-Schmidt twice on each system's rows), each
+// system with its own Givens rotations, stopping test and restarts
+static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
+                                        int *iters, double *rel) {
+    constexpr int HS = 32;
+    Level &L0 = H.lev[0];
+    const DCsr &A = L0.A;
+    const int n = A.nr, nseg = h->nseg;
+    const int m = h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30;
+    TRY(ensure_work(h, n, m));
+    if (!h->d_bat) {
+        TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
+        TRY(dalloc(h, &h->d_batcnt, (size_t)nseg));
+        CU(cudaMallocHost(&h->h_bat, sizeof(double) * nseg * HS));
+        CU(cudaMallocHost(&h->h_batcnt, sizeof(int) * nseg));
+    }
+    double *hsum = h->d_bat, *hbuf = hsum + (size_t)nseg * HS, *ydev = hbuf + (size_t)nseg * HS,
+           *nrm = ydev + (size_t)nseg * HS;
+    double *V = h->V, *Z = h->Z;
+    std::vector<double> bn(nseg), rl(nseg, 0.0), beta(nseg);
+    std::vector<int> its(nseg, 0), jd(nseg, 0);
+    std::vector<char> done(nseg, 0), running(nseg, 0);
+    std::vector<double> Hm((size_t)nseg * (m + 1) * m), cs((size_t)nseg * m), sn((size_t)nseg * m), g((size_t)nseg * (m + 1));
+    seg_norm2(nseg, L0.seg_d, b, nrm, h->s);
+    CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
+    lair_status st = LAIR_OK;
+    for (;;) {
+        seg_residual(A, nseg, L0.seg_d, b, x, V, nullptr, nrm, h->s);
+        CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        flush_timers(h);
+        int any = 0;
+        for (int q = 0; q < nseg; ++q) {
+            beta[q] = std::sqrt(h->h_seg[q]);
+            rl[q] = beta[q] / bn[q];
+            if (!std::isfinite(rl[q])) { st = LAIR_ERR_NAN; done[q] = 1; }
+            if (rl[q] <= tol || its[q] >= max_iter) done[q] = 1;
+            running[q] = !done[q];
+            jd[q] = 0;
+            any |= running[q];
+            if (running[q]) {
+                std::fill(&g[(size_t)q * (m + 1)], &g[(size_t)q * (m + 1)] + (m + 1), 0.0);
+                g[(size_t)q * (m + 1)] = beta[q];
+            }
+        }
+        if (!any) break;
+        seg_scale(nseg, L0.seg_d, V, nrm, V, h->s);
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
+            TRY(precond(h, H, vj, zj));
+            int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
+            sell_spmv<double>(L0.A64, zj, w, h->s);
+            tend(h, ts);
+            CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (size_t)nseg * HS, h->s));
+            for (int pass = 0; pass < 2; ++pass) {
+                seg_multidot(nseg, L0.seg_d, j + 1, V, n, w, HS, hbuf, hsum, h->s);
+                seg_sub_combo(nseg, L0.seg_d, j + 1, V, n, HS, hbuf, w, h->s);
+            }
+            seg_norm2(nseg, L0.seg_d, w, nrm, h->s);
+            seg_scale(nseg, L0.seg_d, w, nrm, w, h->s);
+            CU(cudaMemcpyAsync(h->h_bat, hsum, sizeof(double) * (size_t)nseg * HS, cudaMemcpyDeviceToHost, h->s));
+            CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+            CU(cudaStreamSynchronize(h->s));
+            flush_timers(h);
+            int still = 0;
+            for (int q = 0; q < nseg; ++q) {
+                if (!running[q]) continue;
+                double hc[HS + 1];
+                for (int k = 0; k <= j; ++k) hc[k] = h->h_bat[(size_t)q * HS + k];
+                const double hn = std::sqrt(h->h_seg[q]);
+                hc[j + 1] = hn;
+                double *csq = &cs[(size_t)q * m], *snq = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
+                for (int k = 0; k < j; ++k) {
+                    double t = csq[k] * hc[k] + snq[k] * hc[k + 1];
+                    hc[k + 1] = -snq[k] * hc[k] + csq[k] * hc[k + 1];
+                    hc[k] = t;
+                }
+                double den = std::sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
+                csq[j] = den > 0.0 ? hc[j] / den : 1.0;
+                snq[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
+                hc[j] = den;
+                gq[j + 1] = -snq[j] * gq[j];
+                gq[j] = csq[j] * gq[j];
+                for (int k = 0; k <= j; ++k) Hm[(size_t)q * (m + 1) * m + (size_t)k * m + j] = hc[k];
+                its[q] += 1;
+                const double est = std::fabs(gq[j + 1]) / bn[q];
+                if (est <= tol || hn == 0.0 || !std::isfinite(est) || its[q] >= max_iter || j == m - 1) {
+                    running[q] = 0;
+                    jd[q] = j + 1;
+                } else {
+                    still = 1;
+                }
+            }
+            if (!still) break;
+        }
+        // per-system least-squares solutions y and the update x += Z y
+        for (int q = 0; q < nseg; ++q) {
+            h->h_batcnt[q] = jd[q];
+            const double *Hq = &Hm[(size_t)q * (m + 1) * m], *gq = &g[(size_t)q * (m + 1)];
+            double *yq = h->h_bat + (size_t)q * HS;
+            for (int k = jd[q] - 1; k >= 0; --k) {
+                double acc = gq[k];
+                for (int c = k + 1; c < jd[q]; ++c) acc -= Hq[(size_t)k * m + c] * yq[c];
+                yq[k] = acc / Hq[(size_t)k * m + k];
+            }
+        }
+        CU(cudaMemcpyAsync(ydev, h->h_bat, sizeof(double) * (size_t)nseg * HS, cudaMemcpyHostToDevice, h->s));
+        CU(cudaMemcpyAsync(h->d_batcnt, h->h_batcnt, sizeof(int) * nseg, cudaMemcpyHostToDevice, h->s));
+        seg_add_combo(nseg, L0.seg_d, h->d_batcnt, Z, n, HS, ydev, x, h->s);
+    }
+    CU(cudaStreamSynchronize(h->s));
+    int worst = -1;
+    for (int q = 0; q < nseg; ++q) {
+        if (iters) iters[q] = its[q];
+        if (rel) rel[q] = rl[q];
+        if (st == LAIR_OK && !(rl[q] <= tol)) { st = LAIR_ERR_NOT_CONVERGED; worst = q; }
+    }
+    if (worst >= 0) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
     return st;
 }
 
@@ -1178,6 +1492,107 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **o
     return LAIR_OK;
 }
 
+lair_status lair_setup_batched(const lair_csr *A, int nsys, const int64_t *sys_offsets, const lair_options *o,
+                               lair_handle **out) {
+    if (!A || !out || nsys < 1 || !sys_offsets) return LAIR_ERR_INVALID_ARG;
+    *out = nullptr;
+    lair_handle *h = new lair_handle();
+    *out = h;
+    LaunchScope ls(h);
+    if (o) h->o = *o;
+    else lair_options_default(&h->o);
+    TRY(check_options(h, &h->o));
+    if (h->o.cf_mode == LAIR_CF_USER) return fail(h, LAIR_ERR_INVALID_ARG, "user splitting is not available for batches");
+    if (h->o.block_size > 1) return fail(h, LAIR_ERR_UNSUPPORTED, "block scaling is not available for batches");
+    if (sys_offsets[0] != 0 || sys_offsets[nsys] != A->n)
+        return fail(h, LAIR_ERR_INVALID_ARG, "system offsets must run from 0 to n");
+    h->seg0.resize(nsys + 1);
+    for (int q = 0; q <= nsys; ++q) {
+        if (q > 0 && sys_offsets[q] < sys_offsets[q - 1]) return fail(h, LAIR_ERR_INVALID_ARG, "offsets must not decrease");
+        h->seg0[q] = (int)sys_offsets[q];
+    }
+    h->nseg = nsys;
+    h->s = (cudaStream_t)h->o.stream;
+    if (!h->s) {
+        CU(cudaStreamCreate(&h->own));
+        h->s = h->own;
+    }
+    CU(cudaMallocHost(&h->h_int, 64 * sizeof(int)));
+    CU(cudaMallocHost(&h->h_dbl, 64 * sizeof(double)));
+    CU(cudaMallocHost(&h->h_seg, sizeof(double) * nsys));
+    CU(cudaMallocHost(&h->h_act, nsys));
+    TRY(dalloc(h, &h->status, 1));
+    CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
+    TRY(load_matrix(h, A));
+    TRY(build_hierarchy(h, h->H, h->A_in, nullptr));
+    return LAIR_OK;
+}
+
+lair_status lair_solve_batched(lair_handle *h, const double *b, double *x, double tol, int cycle, int max_iter,
+                               int *iters, double *rel) {
+    if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || cycle < 0 || cycle > 1) return LAIR_ERR_INVALID_ARG;
+    if (h->nseg < 1 || h->H.lev.empty()) return fail(h, LAIR_ERR_INVALID_ARG, "handle was not set up with lair_setup_batched");
+    LaunchScope ls(h);
+    const int n = h->H.lev[0].A.nr;
+    TRY(ensure_work(h, n, 0));
+    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    CU(cudaMemcpyAsync(h->wb, b, sizeof(double) * n, bdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    CU(cudaMemcpyAsync(h->wx, x, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    lair_status st = cycle == LAIR_CYCLE_FGMRES ? solve_batched_fgmres(h, h->H, h->wb, h->wx, tol, max_iter, iters, rel)
+                                                : solve_batched_dev(h, h->H, h->wb, h->wx, tol, max_iter, iters, rel);
+    if (st != LAIR_OK && st != LAIR_ERR_NOT_CONVERGED) return st;
+    CU(cudaMemcpyAsync(x, h->wx, sizeof(double) * n, xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    return st;
+}
+
+lair_status lair_batch_setup_solve(int nsys, const lair_csr *A, const double *const *b, double *const *x,
+                                   const lair_options *o, double tol, int cycle, int max_iter, int *iters, double *rel) {
+    if (nsys < 1 || !A || !b || !x) return LAIR_ERR_INVALID_ARG;
+    // concatenate on the host (the systems may live on the host or on the device)
+    std::vector<int64_t> off(nsys + 1, 0), noff(nsys + 1, 0);
+    for (int q = 0; q < nsys; ++q) {
+        if (A[q].n < 1 || A[q].nnz < 0 || !A[q].row_ptr || !A[q].col || !A[q].val || !b[q] || !x[q])
+            return LAIR_ERR_INVALID_ARG;
+        off[q + 1] = off[q] + A[q].n;
+        noff[q + 1] = noff[q] + A[q].nnz;
+    }
+    if (off[nsys] > 0x7fffffff || noff[nsys] > 0x7fffffff) return LAIR_ERR_UNSUPPORTED;
+    const int64_t n = off[nsys], nnz = noff[nsys];
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col(nnz);
+    std::vector<double> val(nnz), bb(n), xx(n);
+    for (int q = 0; q < nsys; ++q) {
+        const int64_t nq = A[q].n, zq = A[q].nnz;
+        std::vector<int64_t> rq(nq + 1);
+        cudaMemcpyKind k = A[q].on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+        if (cudaMemcpy(rq.data(), A[q].row_ptr, sizeof(int64_t) * (nq + 1), k) != cudaSuccess ||
+            cudaMemcpy(col.data() + noff[q], A[q].col, sizeof(int32_t) * zq, k) != cudaSuccess ||
+            cudaMemcpy(val.data() + noff[q], A[q].val, sizeof(double) * zq, k) != cudaSuccess ||
+            cudaMemcpy(bb.data() + off[q], b[q], sizeof(double) * nq, cudaMemcpyDefault) != cudaSuccess ||
+            cudaMemcpy(xx.data() + off[q], x[q], sizeof(double) * nq, cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return LAIR_ERR_CUDA;
+        }
+        if (rq[0] != 0 || rq[nq] != zq) return LAIR_ERR_NOT_SQUARE;
+        for (int64_t i = 0; i <= nq; ++i) rp[off[q] + i] = rq[i] + noff[q];
+        for (int64_t k2 = noff[q]; k2 < noff[q + 1]; ++k2) col[k2] += (int32_t)off[q];
+    }
+    lair_csr M{n, nnz, rp.data(), col.data(), val.data(), 0};
+    lair_handle *h = nullptr;
+    lair_status st = lair_setup_batched(&M, nsys, off.data(), o, &h);
+    if (st == LAIR_OK) st = lair_solve_batched(h, bb.data(), xx.data(), tol, cycle, max_iter, iters, rel);
+    if (st == LAIR_OK || st == LAIR_ERR_NOT_CONVERGED)
+        for (int q = 0; q < nsys; ++q)
+            if (cudaMemcpy(x[q], xx.data() + off[q], sizeof(double) * A[q].n, cudaMemcpyDefault) != cudaSuccess) {
+                cudaGetLastError();
+                st = LAIR_ERR_CUDA;
+                break;
+            }
+    lair_free(h);
+    return st;
+}
+
 lair_status lair_solve(lair_handle *h, const double *b, double *x, double tol, int cycle, int max_iter,
                        lair_report *rep) {
     if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || cycle < 0 || cycle > 1) return LAIR_ERR_INVALID_ARG;
@@ -1306,6 +1721,10 @@ void lair_free(lair_handle *h) {
     for (auto &p : h->graph_events) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->own) cudaStreamDestroy(h->own);
+    if (h->h_bat) cudaFreeHost(h->h_bat);
+    if (h->h_batcnt) cudaFreeHost(h->h_batcnt);
+    if (h->h_seg) cudaFreeHost(h->h_seg);
+    if (h->h_act) cudaFreeHost(h->h_act);
     if (h->h_int) cudaFreeHost(h->h_int);
     if (h->h_dbl) cudaFreeHost(h->h_dbl);
     cudaGetLastError();

@@ -322,11 +322,11 @@ __device__ bool rs_stage(const Graph &G, int b0, int b1, int *rp, uint16_t *col,
     return true;
 }
 
-__global__ void __launch_bounds__(32) k_rs_split(int n_all, int B, Graph S, Graph ST, int8_t *__restrict__ cf_out,
-                                                 int *status, int smem_bytes) {
+__global__ void __launch_bounds__(32) k_rs_split(int n_all, const int2 *__restrict__ blocks, Graph S, Graph ST,
+                                                 int8_t *__restrict__ cf_out, int *status, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int b0 = blockIdx.x * B;
-    const int b1 = min(n_all, b0 + B);
+    const int b0 = blocks[blockIdx.x].x;          // this warp's index block [b0, b1)
+    const int b1 = blocks[blockIdx.x].y;
     const int n = b1 - b0;
     const int n1 = (n + 31) / 32;
     unsigned *key = reinterpret_cast<unsigned *>(smem);
@@ -505,12 +505,13 @@ void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, 
     count_launch(2);
 }
 
-cudaError_t launch_rs(int n, int B, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
-    if (B > n) B = n;
-    size_t bytes = rs_smem_bytes(B, n > 0 ? (double)S.nnz / n : 0.0);
+// blocks: nblocks (b0, b1) pairs on the device, every block at most Bmax points
+cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, const Graph &S, const Graph &ST, int8_t *cf,
+                      int *status, cudaStream_t s) {
+    size_t bytes = rs_smem_bytes(Bmax, n > 0 ? (double)S.nnz / n : 0.0);
     cudaError_t e = cudaFuncSetAttribute(k_rs_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_rs_split<<<(n + B - 1) / B, 32, bytes, s>>>(n, B, S, ST, cf, status, (int)bytes);
+    k_rs_split<<<nblocks, 32, bytes, s>>>(n, blocks, S, ST, cf, status, (int)bytes);
     count_launch();
     return cudaGetLastError();
 }

@@ -5,6 +5,16 @@
 
 namespace lair {
 
+// sliced-ELL view of a subset of a matrix's rows (sell.cu)
+struct SellView {
+    int nrows = 0;
+    int *slice_ptr = nullptr;   // nslices + 1 offsets, in entries
+    int *col = nullptr;
+    void *val = nullptr;        // float or double
+    int *row = nullptr;         // view row -> matrix row
+    void *dinv = nullptr;       // Jacobi diagonal per view row (sweep views), same type as val
+};
+
 // ---- setup_graph.cu -------------------------------------------------------------------
 void launch_strength(const DCsr &A, double theta, int absmode, uint8_t *mask, int *cnt, cudaStream_t s);
 void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaStream_t s);
@@ -15,7 +25,8 @@ void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
 void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
                        int *undecided, cudaStream_t s);
-cudaError_t launch_rs(int n, int B, const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
+cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, const Graph &S, const Graph &ST, int8_t *cf,
+                      int *status, cudaStream_t s);
 size_t rs_smem_bytes(int n, double avg_degree);
 constexpr int RS_MAX_N = 32768;
 void launch_cidx(int n, const int8_t *cf, int *flag, int *cidx, int *cpts, int phase, cudaStream_t s);
@@ -60,10 +71,11 @@ struct SpgemmArgs {
     int *cnt;             // exact row lengths
 };
 constexpr int SPGEMM_CTA_GRID = 152;
+constexpr int SPGEMM_BINS = 4;   // three warp bins by row bound, then the CTA bin
 void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
 void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
-                               const int counts_host[2], int ubmax, int *skeys, double *svals, cudaStream_t s);
+                               const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s);
 unsigned spgemm_big_cap(int ubmax);
 void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tval, DCsr &Z, cudaStream_t s);
 void launch_lump(int phase, const DCsr &K, double tol, int *cnt, double *newdiag, const DCsr *out, int *status,
@@ -91,5 +103,27 @@ void axpy_f(int n, const float *e, double *x, cudaStream_t s);
 void axpy_d(int n, const double *e, double *x, cudaStream_t s);
 void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s);
 void cf_stats(const DCsr &A, const int8_t *cf, unsigned long long *out4, cudaStream_t s);
+
+// ---- sell.cu --------------------------------------------------------------------------
+void launch_frows(int n, const int8_t *cf, const int *cscan, int *frows, cudaStream_t s);
+void launch_sell_prepare(int nrows, const int *rows_in, const int *rp, int *rows_sorted, int *cnt, cudaStream_t s);
+void launch_sell_fill(const SellView &v, const DCsr &M, const double *dinv, bool fp32, cudaStream_t s);
+template <class T> void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s);
+template <class T>
+void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);
+// batched systems: per-system residual r = b - A x (rows seg[q]..seg[q+1]), its squared norm, optional FP32 copy
+void seg_residual(const DCsr &A, int nseg, const int *seg, const double *b, const double *x, double *r, float *r32,
+                  double *norm2, cudaStream_t s);
+void seg_norm2(int nseg, const int *seg, const double *v, double *norm2, cudaStream_t s);
+template <class T>
+void seg_axpy(int nseg, const int *seg, const uint8_t *active, const T *e, double *x, cudaStream_t s);
+void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s);
+void seg_multidot(int nseg, const int *seg, int m, const double *X, long long ldx, const double *w, int hs,
+                  double *out, double *acc, cudaStream_t s);
+void seg_sub_combo(int nseg, const int *seg, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+                   cudaStream_t s);
+void seg_add_combo(int nseg, const int *seg, const int *cnt, const double *Z, long long ldz, int hs, const double *y,
+                   double *x, cudaStream_t s);
+void seg_scale(int nseg, const int *seg, const double *v, const double *nrm2, double *out, cudaStream_t s);
 
 }  // namespace lair

@@ -364,13 +364,26 @@ __global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__res
 
 __global__ void k_local_bin(int nc, const int *__restrict__ nb_rp, int *__restrict__ lists, int *__restrict__ counts,
                             int *__restrict__ smax) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
-        int s = nb_rp[c + 1] - nb_rp[c];
-        int b = s <= THREAD_SMAX ? 0 : (s <= 32 ? 1 : 2);
-        int p = atomicAdd(&counts[b], 1);
-        lists[(size_t)b * nc + p] = c;
-        atomicMax(smax, s);
+    const unsigned lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int local_max = 0;
+    for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; base < nc; base += stride) {
+        const int c = (int)(base + lane);
+        const bool act = c < nc;
+        const int s = act ? nb_rp[c + 1] - nb_rp[c] : 0;
+        const int b = s <= THREAD_SMAX ? 0 : (s <= 32 ? 1 : 2);
+        local_max = max(local_max, s);
+        for (int bb = 0; bb < 3; ++bb) {       // one atomic per warp and bin
+            const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
+            if (!m) continue;
+            int p0 = 0;
+            if (lane == __ffs(m) - 1) p0 = atomicAdd(&counts[bb], __popc(m));
+            p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
+            if (act && b == bb) lists[(size_t)bb * nc + p0 + __popc(m & ((1u << lane) - 1u))] = c;
+        }
     }
+    local_max = __reduce_max_sync(0xffffffffu, local_max);
+    if (lane == 0 && local_max > 0) atomicMax(smax, local_max);
 }
 
 void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s) {
@@ -529,21 +542,29 @@ __device__ double entry(const int *rp, const int *col, const double *val, int i,
     return 0.0;
 }
 
-// one thread per row of the output: every thread of a block factors the same bs x bs block
-// (identical operations, so identical D_B^{-1}) and writes its own row
-__global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
-                             const double *__restrict__ val, const int *__restrict__ orp, int *__restrict__ ocol,
-                             double *__restrict__ oval, double *__restrict__ dinv_out, int *status) {
-    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], Di[BS_MAX], rhs[BS_MAX], a[BS_MAX];
+// the diagonal block of K read by a linear walk of each block row (columns are sorted)
+__device__ void load_diag_block(const int *rp, const int *col, const double *val, int r0, int bs, double *M) {
+    for (int r = 0; r < bs; ++r) {
+        for (int c = 0; c < bs; ++c) M[r * bs + c] = 0.0;
+        for (int k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k) {
+            int j = col[k];
+            if (j >= r0 + bs) break;
+            if (j >= r0) M[r * bs + (j - r0)] = val[k];
+        }
+    }
+}
+
+// one thread per block: D_B^{-1} of the block by the LU above applied to unit vectors
+__global__ void k_block_inverse(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                                const double *__restrict__ val, double *__restrict__ dinv_out, int *status) {
+    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], rhs[BS_MAX];
     int perm[BS_MAX];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nblk * bs; e += gridDim.x * blockDim.x) {
-        const int K = e / bs, rr = e % bs, r0 = K * bs;
+    for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
+        const int r0 = K * bs;
+        load_diag_block(rp, col, val, r0, bs, M);
         for (int r = 0; r < bs; ++r) {
             perm[r] = r;
-            for (int c = 0; c < bs; ++c) {
-                M[r * bs + c] = entry(rp, col, val, r0 + r, r0 + c);
-                Lm[r * bs + c] = 0.0;
-            }
+            for (int c = 0; c < bs; ++c) Lm[r * bs + c] = 0.0;
         }
         double mx = 0.0;
         for (int q = 0; q < bs * bs; ++q) mx = fmax(mx, fabs(M[q]));
@@ -569,18 +590,28 @@ __global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const
             }
         }
         if (bad) { set_status(status, LAIR_ERR_ZERO_DIAGONAL); continue; }
-        // row rr of D_B^{-1}: column t of the inverse is the solve with unit vector e_t
+        double *Di = dinv_out + (size_t)K * bs * bs;
         for (int t = 0; t < bs; ++t) {
             for (int r = 0; r < bs; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
             for (int k = 0; k < bs; ++k)
                 for (int r = k + 1; r < bs; ++r) rhs[r] = __fma_rn(-Lm[r * bs + k], rhs[k], rhs[r]);
             for (int c = bs - 1; c >= 0; --c) {
                 double zc = __ddiv_rn(rhs[c], M[c * bs + c]);
-                if (c == rr) Di[t] = zc;
+                Di[c * bs + t] = zc;
                 for (int r = 0; r < c; ++r) rhs[r] = __fma_rn(-M[r * bs + c], zc, rhs[r]);
             }
         }
-        for (int t = 0; t < bs; ++t) dinv_out[(size_t)K * bs * bs + rr * bs + t] = Di[t];
+    }
+}
+
+// one thread per row of the output: merge the block rows, scale by the row of D_B^{-1}
+__global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
+                             const double *__restrict__ val, const int *__restrict__ orp, int *__restrict__ ocol,
+                             double *__restrict__ oval, const double *__restrict__ dinv, int *status) {
+    double Di[BS_MAX], a[BS_MAX];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nblk * bs; e += gridDim.x * blockDim.x) {
+        const int K = e / bs, rr = e % bs, r0 = K * bs;
+        for (int t = 0; t < bs; ++t) Di[t] = dinv[(size_t)K * bs * bs + rr * bs + t];
         BlockMerge m{rp, col, val, r0, bs};
         m.init();
         int p = orp[r0 + rr];
@@ -619,9 +650,10 @@ void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *statu
 }
 
 void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
+    k_block_inverse<<<grid_for(nblk, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, A.val, dinv, status);
     k_block_fill<<<grid_for((long long)nblk * bs, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, A.val, out.rp, out.col, out.val,
                                                                      dinv, status);
-    count_launch();
+    count_launch(2);
 }
 
 void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, double *out, cudaStream_t s) {

@@ -11,8 +11,7 @@
 
 namespace lair {
 
-constexpr int WARP_CAP = 2048;      // hash slots per warp (rows with ub <= WARP_CAP / 2)
-constexpr int SPGEMM_WARPS = 4;
+constexpr int WARP_CAP = 2048;      // largest hash table of the warp kernels (rows with ub <= WARP_CAP / 2)
 
 __global__ void k_spgemm_ub(int nr, const int *__restrict__ xrp, const int *__restrict__ xcol,
                             const int *__restrict__ yrp, int *__restrict__ ub) {
@@ -26,50 +25,68 @@ __global__ void k_spgemm_ub(int nr, const int *__restrict__ xrp, const int *__re
     }
 }
 
+// bins by the row's upper bound: 0: ub <= 128 (256 slots), 1: ub <= 512 (1024), 2: ub <= 1024 (2048), 3: larger
+__device__ __forceinline__ int spgemm_bin(int u) { return u <= 128 ? 0 : (u <= 512 ? 1 : (u <= WARP_CAP / 2 ? 2 : 3)); }
+
 __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__restrict__ lists,
                                   int *__restrict__ counts, int *__restrict__ ubmax) {
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nr; a += gridDim.x * blockDim.x) {
-        int u = off[a + 1] - off[a];
-        int b = u <= WARP_CAP / 2 ? 0 : 1;
-        int p = atomicAdd(&counts[b], 1);
-        lists[(size_t)b * nr + p] = a;
-        if (b) atomicMax(ubmax, u);
+    const unsigned lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; base < nr; base += stride) {
+        const int a = (int)(base + lane);
+        const bool act = a < nr;
+        const int u = act ? off[a + 1] - off[a] : 0;
+        const int b = spgemm_bin(u);
+        for (int bb = 0; bb < SPGEMM_BINS; ++bb) {       // one atomic per warp and bin
+            const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
+            if (!m) continue;
+            int p0 = 0;
+            if (lane == __ffs(m) - 1) p0 = atomicAdd(&counts[bb], __popc(m));
+            p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
+            if (act && b == bb) lists[(size_t)bb * nr + p0 + __popc(m & ((1u << lane) - 1u))] = a;
+        }
+        if (act && b == SPGEMM_BINS - 1) atomicMax(ubmax, u);
     }
 }
 
 __device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
 
-constexpr int XCHUNK = 128;   // entries of an X row staged at a time
-// per-warp staging area after the hash tables: x (XCHUNK doubles), px/py (2 x 32 doubles),
-// k (XCHUNK ints), offsets (XCHUNK + 1 ints); the stride is rounded up to 16 bytes so that
-// every warp's doubles stay aligned
-constexpr size_t SPGEMM_EXTRA =
-    ((XCHUNK * sizeof(double) + 64 * sizeof(double) + (2 * XCHUNK + 1) * sizeof(int)) + 15) & ~(size_t)15;
+constexpr int XCHUNK = 64;            // entries of an X row staged at a time
+constexpr int BM_WORDS = 512;         // column bitmap of a row: spans up to 16384 columns
+// per-warp staging after the hash table: x (XCHUNK doubles), px/py (2 x 32 doubles), k (XCHUNK ints),
+// offsets (XCHUNK + 1 ints), bitmap (BM_WORDS words), word prefix counts (BM_WORDS ushort); 16-byte aligned
+constexpr size_t SPGEMM_EXTRA = ((XCHUNK * sizeof(double) + 64 * sizeof(double) + (2 * XCHUNK + 1) * sizeof(int) +
+                                  BM_WORDS * sizeof(unsigned) + BM_WORDS * sizeof(unsigned short)) + 15) & ~(size_t)15;
 
-// One warp per output row a. The products x_ak * y_kl of the row are laid out flat in
-// ascending (k, position in row k of Y) order and taken 32 at a time; lanes holding the
-// same column l are grouped with __match_any_sync and the lowest lane of a group (the
-// smallest k) applies the group's products in ascending k, so every entry receives its
-// fma updates in ascending k exactly as in a sequential loop. The unique columns are then
-// ordered by rank counting.
-__global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
-                                                                const int *__restrict__ count) {
+template <int CAP>
+__host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * (sizeof(double) + sizeof(int)) + SPGEMM_EXTRA; }
+
+// One warp per output row a with a hash table of CAP slots (rows with ub <= CAP / 2). The products
+// x_ak * y_kl of the row are laid out flat in ascending (k, position in row k of Y) order and taken
+// 32 at a time; lanes holding the same column l are grouped with __match_any_sync and the lowest lane
+// of a group (the smallest k) applies the group's products in ascending k, so every entry receives its
+// fma updates in ascending k exactly as in a sequential loop. Columns are ordered through a bitmap of
+// the row's column span (position = set bits before the column) or, for wide rows, by rank counting.
+template <int CAP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
+                                                           const int *__restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31;
-    double *vals = reinterpret_cast<double *>(smem) + (size_t)w * WARP_CAP;
-    int *keys = reinterpret_cast<int *>(reinterpret_cast<double *>(smem) + (size_t)SPGEMM_WARPS * WARP_CAP) + (size_t)w * WARP_CAP;
-    unsigned char *extra = reinterpret_cast<unsigned char *>(reinterpret_cast<int *>(reinterpret_cast<double *>(smem) +
-                                                             (size_t)SPGEMM_WARPS * WARP_CAP) + (size_t)SPGEMM_WARPS * WARP_CAP);
-    extra += (size_t)w * SPGEMM_EXTRA;
-    double *sxv = reinterpret_cast<double *>(extra);          // x of the staged chunk of row a of X
-    double *px = sxv + XCHUNK;                               // products of one round: x and y per lane
+    unsigned char *mine = smem + (size_t)w * spgemm_warp_bytes<CAP>();
+    double *vals = reinterpret_cast<double *>(mine);
+    int *keys = reinterpret_cast<int *>(vals + CAP);
+    double *sxv = reinterpret_cast<double *>(keys + CAP);      // CAP * 12 bytes: 16-aligned for CAP >= 4
+    double *px = sxv + XCHUNK;
     double *py = px + 32;
-    int *sk = reinterpret_cast<int *>(py + 32);              // k of the staged chunk
-    int *soff = sk + XCHUNK;                                 // flat offsets, XCHUNK + 1
+    int *sk = reinterpret_cast<int *>(py + 32);
+    int *soff = sk + XCHUNK;
+    unsigned *bm = reinterpret_cast<unsigned *>(soff + XCHUNK + 1);
+    unsigned short *pre = reinterpret_cast<unsigned short *>(bm + BM_WORDS);
     const int n = *count;
-    const int nwarps = gridDim.x * SPGEMM_WARPS;
-    for (int t = blockIdx.x * SPGEMM_WARPS + w; t < n; t += nwarps) {
+    const int nwarps = gridDim.x * WARPS;
+    for (unsigned e = lane; e < BM_WORDS; e += 32) bm[e] = 0u;
+    for (int t = blockIdx.x * WARPS + w; t < n; t += nwarps) {
         const int a = list[t];
         const int ub = g.off[a + 1] - g.off[a];
         unsigned cap = 32;
@@ -77,6 +94,19 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
         const unsigned mask = cap - 1;
         for (unsigned e = lane; e < cap; e += 32) keys[e] = -1;
         const int xb = g.xrp[a], xe = g.xrp[a + 1];
+        // column span of the row: rows of Y are sorted, so their first and last columns bound it
+        int cmin = 0x7fffffff, cmax = -1;
+        for (int p = xb + (int)lane; p < xe; p += 32) {
+            const int k = g.xcol[p];
+            const int yb = g.yrp[k], ye = g.yrp[k + 1];
+            if (ye > yb) {
+                cmin = min(cmin, g.ycol[yb]);
+                cmax = max(cmax, g.ycol[ye - 1]);
+            }
+        }
+        cmin = __reduce_min_sync(0xffffffffu, cmin);
+        cmax = __reduce_max_sync(0xffffffffu, cmax);
+        const bool use_bm = cmax >= cmin && cmax - cmin < BM_WORDS * 32;
         for (int c0 = xb; c0 < xe; c0 += XCHUNK) {
             const int cn = min(XCHUNK, xe - c0);
             __syncwarp();
@@ -126,7 +156,11 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
                         double v;
                         for (;;) {
                             int prev = atomicCAS(&keys[h], -1, l);
-                            if (prev == -1) { v = 0.0; break; }
+                            if (prev == -1) {
+                                v = 0.0;
+                                if (use_bm) atomicOr(&bm[(l - cmin) >> 5], 1u << ((l - cmin) & 31));
+                                break;
+                            }
                             if (prev == l) { v = vals[h]; break; }
                             h = (h + 1) & mask;
                         }
@@ -141,29 +175,60 @@ __global__ void __launch_bounds__(32 * SPGEMM_WARPS) k_spgemm_warp(SpgemmArgs g,
             }
         }
         __syncwarp();
-        // compact occupied slots to the front (positions never pass the slot being read)
-        int cnt = 0;
-        for (unsigned base = 0; base < cap; base += 32) {
-            int key = keys[base + lane];
-            double v = vals[base + lane];
-            unsigned occ = __ballot_sync(0xffffffffu, key != -1);
-            __syncwarp();
-            if (key != -1) {
-                int pos = cnt + __popc(occ & ((1u << lane) - 1u));
-                keys[pos] = key;
-                vals[pos] = v;
-            }
-            cnt += __popc(occ);
-            __syncwarp();
-        }
-        // rank counting: the position of a key is the number of smaller keys (keys are unique)
         const int o = g.off[a];
-        for (int e = lane; e < cnt; e += 32) {
-            const int key = keys[e];
-            int r = 0;
-            for (int f = 0; f < cnt; ++f) r += keys[f] < key;
-            g.tcol[o + r] = key;
-            g.tval[o + r] = vals[e];
+        int cnt;
+        if (use_bm) {
+            // prefix counts of the bitmap words (lane owns 16 consecutive words), then each
+            // occupied slot goes straight to its sorted position
+            const int wpl = BM_WORDS / 32;
+            int c = 0;
+            for (int j = 0; j < wpl; ++j) c += __popc(bm[lane * wpl + j]);
+            int incl = c;
+            for (int d = 1; d < 32; d <<= 1) {
+                int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if ((int)lane >= d) incl += v;
+            }
+            cnt = __shfl_sync(0xffffffffu, incl, 31);
+            int run = incl - c;
+            for (int j = 0; j < wpl; ++j) {
+                pre[lane * wpl + j] = (unsigned short)run;
+                run += __popc(bm[lane * wpl + j]);
+            }
+            __syncwarp();
+            for (unsigned e = lane; e < cap; e += 32) {
+                const int key = keys[e];
+                if (key == -1) continue;
+                const int d = key - cmin;
+                const int r = pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+                g.tcol[o + r] = key;
+                g.tval[o + r] = vals[e];
+            }
+            __syncwarp();
+            for (int j = 0; j < wpl; ++j) bm[lane * wpl + j] = 0u;
+        } else {
+            // compact occupied slots to the front (positions never pass the slot being read)
+            cnt = 0;
+            for (unsigned base = 0; base < cap; base += 32) {
+                int key = keys[base + lane];
+                double v = vals[base + lane];
+                unsigned occ = __ballot_sync(0xffffffffu, key != -1);
+                __syncwarp();
+                if (key != -1) {
+                    int pos = cnt + __popc(occ & ((1u << lane) - 1u));
+                    keys[pos] = key;
+                    vals[pos] = v;
+                }
+                cnt += __popc(occ);
+                __syncwarp();
+            }
+            // rank counting: the position of a key is the number of smaller keys (keys are unique)
+            for (int e = lane; e < cnt; e += 32) {
+                const int key = keys[e];
+                int r = 0;
+                for (int f = 0; f < cnt; ++f) r += keys[f] < key;
+                g.tcol[o + r] = key;
+                g.tval[o + r] = vals[e];
+            }
         }
         if (lane == 0) g.cnt[a] = cnt;
         __syncwarp();
@@ -265,19 +330,24 @@ void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int
     count_launch();
 }
 
+template <int CAP, int WARPS>
+static void launch_spgemm_bin(const SpgemmArgs &g, const int *list, const int *count_dev, int count, cudaStream_t s) {
+    const size_t bytes = (size_t)WARPS * spgemm_warp_bytes<CAP>();
+    cudaFuncSetAttribute(k_spgemm_warp<CAP, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int grid = grid_for(count, WARPS, 152 * 16);
+    k_spgemm_warp<CAP, WARPS><<<grid, 32 * WARPS, bytes, s>>>(g, list, count_dev);
+    count_launch();
+}
+
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
-                               const int counts_host[2], int ubmax, int *skeys, double *svals, cudaStream_t s) {
-    if (counts_host[0] > 0) {
-        size_t bytes = (size_t)SPGEMM_WARPS * (WARP_CAP * (sizeof(double) + sizeof(int)) + SPGEMM_EXTRA);
-        cudaFuncSetAttribute(k_spgemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        int grid = grid_for(counts_host[0], SPGEMM_WARPS, 152 * 8);
-        k_spgemm_warp<<<grid, 32 * SPGEMM_WARPS, bytes, s>>>(g, lists, counts_dev);
-        count_launch();
-    }
-    if (counts_host[1] > 0) {
+                               const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s) {
+    if (counts_host[0] > 0) launch_spgemm_bin<256, 8>(g, lists, counts_dev, counts_host[0], s);
+    if (counts_host[1] > 0) launch_spgemm_bin<1024, 4>(g, lists + nr, counts_dev + 1, counts_host[1], s);
+    if (counts_host[2] > 0) launch_spgemm_bin<2048, 2>(g, lists + 2 * (size_t)nr, counts_dev + 2, counts_host[2], s);
+    if (counts_host[3] > 0) {
         unsigned cap = spgemm_big_cap(ubmax);
-        int grid = counts_host[1] < SPGEMM_CTA_GRID ? counts_host[1] : SPGEMM_CTA_GRID;
-        k_spgemm_cta<<<grid, 256, 0, s>>>(g, lists + nr, counts_dev + 1, skeys, svals, cap);
+        int grid = counts_host[3] < SPGEMM_CTA_GRID ? counts_host[3] : SPGEMM_CTA_GRID;
+        k_spgemm_cta<<<grid, 256, 0, s>>>(g, lists + 3 * (size_t)nr, counts_dev + 3, skeys, svals, cap);
         count_launch();
     }
     return cudaGetLastError();

@@ -195,21 +195,24 @@ void residual(const DCsr &A, const double *b, const double *x, double *r, float 
     count_launch();
 }
 
-// block partials of sum_i x_i y_i for m vectors x_k (stride ldx) against y: part[k * RED_BLOCKS + block]
-__global__ void __launch_bounds__(RED_THREADS) k_multidot(int n, int m, const double *__restrict__ X, long long ldx,
+// block partials of sum_i x_i y_i for vectors x_k (stride ldx) against y, MD vectors per launch:
+// part[k * RED_BLOCKS + block] for k = k0 .. k0 + m - 1
+constexpr int MD = 8;
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(int n, int k0, int m, const double *__restrict__ X, long long ldx,
                                                           const double *__restrict__ y, double *__restrict__ part) {
-    __shared__ double red[RED_THREADS / 32][32];
-    double acc[32];
+    __shared__ double red[RED_THREADS / 32][MD];
+    double acc[MD];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] = 0.0;
+    for (int k = 0; k < MD; ++k) acc[k] = 0.0;
+    const double *Xk = X + (long long)k0 * ldx;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         double yi = y[i];
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (k < m) acc[k] = fma(X[k * ldx + i], yi, acc[k]);
+        for (int k = 0; k < MD; ++k)
+            if (k < m) acc[k] = fma(Xk[k * ldx + i], yi, acc[k]);
     }
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < MD; ++k) {
         if (k < m) {
             double v = warp_sum(acc[k]);
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(int n, int m, const do
     if (threadIdx.x < m) {
         double t = 0.0;
         for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
-        part[threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+        part[(k0 + threadIdx.x) * RED_BLOCKS + blockIdx.x] = t;
     }
 }
 
@@ -243,9 +246,13 @@ __global__ void k_finish(int m, const double *__restrict__ part, double *__restr
 
 void multidot(int n, int m, const double *X, long long ldx, const double *y, double *part, double *out, double *acc,
               cudaStream_t s) {
-    k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m, X, ldx, y, part);
+    for (int k0 = 0; k0 < m; k0 += MD) {
+        int mm = m - k0 < MD ? m - k0 : MD;
+        k_multidot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, k0, mm, X, ldx, y, part);
+        count_launch();
+    }
     k_finish<<<m, 256, 0, s>>>(m, part, out, acc);
-    count_launch(2);
+    count_launch();
 }
 
 void finish_partials(int m, const double *part, double *out, cudaStream_t s) {
@@ -330,6 +337,183 @@ __global__ void k_grad_A(int n, const int *__restrict__ rp, const int *__restric
 
 void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaStream_t s) {
     k_grad_A<<<grid_for(A.nr, 256), 256, 0, s>>>(A.nr, A.rp, A.col, lam, x, g);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// batched systems: one CTA per system for the residual, norms and masked updates
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_seg_residual(int nseg, const int *__restrict__ seg, const int *__restrict__ rp,
+                                                      const int *__restrict__ col, const double *__restrict__ val,
+                                                      const double *__restrict__ b, const double *__restrict__ x,
+                                                      double *__restrict__ r, float *__restrict__ r32,
+                                                      double *__restrict__ norm2) {
+    __shared__ double red[8];
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        double ss = 0.0;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+            double acc = 0.0;
+            for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(val[k], x[col[k]], acc);
+            double ri = b[i] - acc;
+            r[i] = ri;
+            if (r32) r32[i] = (float)ri;
+            ss = fma(ri, ri, ss);
+        }
+        double t = block_sum(ss, red);
+        if (threadIdx.x == 0) norm2[q] = t;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_seg_norm2(int nseg, const int *__restrict__ seg, const double *__restrict__ v,
+                                                   double *__restrict__ norm2) {
+    __shared__ double red[8];
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        double ss = 0.0;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) ss = fma(v[i], v[i], ss);
+        double t = block_sum(ss, red);
+        if (threadIdx.x == 0) norm2[q] = t;
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_seg_axpy(int nseg, const int *__restrict__ seg, const uint8_t *__restrict__ active,
+                                                  const T *__restrict__ e, double *__restrict__ x) {
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        if (!active[q]) continue;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) x[i] += (double)e[i];
+    }
+}
+
+// per system q: out[q * HS + k0 + k] = sum over the system's rows of X_{k0+k}[i] w[i], k < m (m <= MD)
+constexpr int SEG_MD = 8;
+__global__ void __launch_bounds__(256) k_seg_multidot(int nseg, const int *__restrict__ seg, int k0, int m,
+                                                      const double *__restrict__ X, long long ldx,
+                                                      const double *__restrict__ w, int hs, double *__restrict__ out,
+                                                      double *__restrict__ acc_out) {
+    __shared__ double red[8][SEG_MD];
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        double acc[SEG_MD];
+#pragma unroll
+        for (int k = 0; k < SEG_MD; ++k) acc[k] = 0.0;
+        const double *Xk = X + (long long)k0 * ldx;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+            const double wi = w[i];
+#pragma unroll
+            for (int k = 0; k < SEG_MD; ++k)
+                if (k < m) acc[k] = fma(Xk[k * ldx + i], wi, acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < SEG_MD; ++k) {
+            if (k < m) {
+                double v = warp_sum(acc[k]);
+                if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < m) {
+            double t = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+            out[q * hs + k0 + threadIdx.x] = t;
+            if (acc_out) acc_out[q * hs + k0 + threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// w_i -= sum_{k < m} h[q * hs + k] X_k[i] for the rows of system q
+__global__ void __launch_bounds__(256) k_seg_sub_combo(int nseg, const int *__restrict__ seg, int m,
+                                                       const double *__restrict__ X, long long ldx, int hs,
+                                                       const double *__restrict__ h, double *__restrict__ w) {
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x)
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+            double v = w[i];
+            for (int k = 0; k < m; ++k) v = fma(-h[q * hs + k], X[k * ldx + i], v);
+            w[i] = v;
+        }
+}
+
+// x_i += sum_{k < cnt[q]} y[q * hs + k] Z_k[i] for the rows of system q
+__global__ void __launch_bounds__(256) k_seg_add_combo(int nseg, const int *__restrict__ seg, const int *__restrict__ cnt,
+                                                       const double *__restrict__ Z, long long ldz, int hs,
+                                                       const double *__restrict__ y, double *__restrict__ x) {
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        const int m = cnt[q];
+        if (m == 0) continue;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+            double v = x[i];
+            for (int k = 0; k < m; ++k) v = fma(y[q * hs + k], Z[k * ldz + i], v);
+            x[i] = v;
+        }
+    }
+}
+
+// out_i = v_i / sqrt(nrm2[q]) (0 when the norm is 0) for the rows of system q
+__global__ void __launch_bounds__(256) k_seg_scale(int nseg, const int *__restrict__ seg, const double *__restrict__ v,
+                                                   const double *__restrict__ nrm2, double *__restrict__ out) {
+    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+        const double n2 = nrm2[q];
+        const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) out[i] = v[i] * inv;
+    }
+}
+
+void seg_multidot(int nseg, const int *seg, int m, const double *X, long long ldx, const double *w, int hs,
+                  double *out, double *acc, cudaStream_t s) {
+    for (int k0 = 0; k0 < m; k0 += SEG_MD) {
+        int mm = m - k0 < SEG_MD ? m - k0 : SEG_MD;
+        k_seg_multidot<<<nseg, 256, 0, s>>>(nseg, seg, k0, mm, X, ldx, w, hs, out, acc);
+        count_launch();
+    }
+}
+void seg_sub_combo(int nseg, const int *seg, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+                   cudaStream_t s) {
+    k_seg_sub_combo<<<nseg, 256, 0, s>>>(nseg, seg, m, X, ldx, hs, h, w);
+    count_launch();
+}
+void seg_add_combo(int nseg, const int *seg, const int *cnt, const double *Z, long long ldz, int hs, const double *y,
+                   double *x, cudaStream_t s) {
+    k_seg_add_combo<<<nseg, 256, 0, s>>>(nseg, seg, cnt, Z, ldz, hs, y, x);
+    count_launch();
+}
+void seg_scale(int nseg, const int *seg, const double *v, const double *nrm2, double *out, cudaStream_t s) {
+    k_seg_scale<<<nseg, 256, 0, s>>>(nseg, seg, v, nrm2, out);
+    count_launch();
+}
+
+__global__ void k_gather_int(int m, const int *__restrict__ idx, const int *__restrict__ src, int *__restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) out[t] = src[idx[t]];
+}
+
+void seg_residual(const DCsr &A, int nseg, const int *seg, const double *b, const double *x, double *r, float *r32,
+                  double *norm2, cudaStream_t s) {
+    k_seg_residual<<<nseg, 256, 0, s>>>(nseg, seg, A.rp, A.col, A.val, b, x, r, r32, norm2);
+    count_launch();
+}
+void seg_norm2(int nseg, const int *seg, const double *v, double *norm2, cudaStream_t s) {
+    k_seg_norm2<<<nseg, 256, 0, s>>>(nseg, seg, v, norm2);
+    count_launch();
+}
+template <class T>
+void seg_axpy(int nseg, const int *seg, const uint8_t *active, const T *e, double *x, cudaStream_t s) {
+    k_seg_axpy<T><<<nseg, 256, 0, s>>>(nseg, seg, active, e, x);
+    count_launch();
+}
+template void seg_axpy<float>(int, const int *, const uint8_t *, const float *, double *, cudaStream_t);
+template void seg_axpy<double>(int, const int *, const uint8_t *, const double *, double *, cudaStream_t);
+void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s) {
+    k_gather_int<<<grid_for(m, 256), 256, 0, s>>>(m, idx, src, out);
     count_launch();
 }
 

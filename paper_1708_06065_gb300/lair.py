@@ -82,6 +82,10 @@ def _load():
         "lair_kernel_launches": (C.c_int64, [p]),
         "lair_kernel_timers": (C.c_int, [p, C.POINTER(lair_kernel_timer), C.c_int, C.POINTER(C.c_int)]),
         "lair_local_solve_noalloc": (C.c_int, [C.c_int64, C.c_int32, p, p, p, p, p]),
+        "lair_setup_batched": (C.c_int, [C.POINTER(lair_csr), C.c_int, p, C.POINTER(lair_options), C.POINTER(p)]),
+        "lair_solve_batched": (C.c_int, [p, p, p, C.c_double, C.c_int, C.c_int, p, p]),
+        "lair_batch_setup_solve": (C.c_int, [C.c_int, C.POINTER(lair_csr), p, p, C.POINTER(lair_options), C.c_double,
+                                             C.c_int, C.c_int, p, p]),
         "lair_free": (None, [p]),
         "lair_status_string": (C.c_char_p, [C.c_int]),
         "lair_last_error": (C.c_char_p, [p]),
@@ -171,6 +175,36 @@ class Hierarchy:
             msg = self.last_error()
             self.close()
             raise LairError(st, msg)
+
+    @classmethod
+    def batched(cls, row_ptr, col, val, sys_offsets, **kw):
+        """One hierarchy for independent systems stored as one block-diagonal CSR."""
+        self = cls.__new__(cls)
+        self._h = C.c_void_p()
+        self.n, self.nnz = len(row_ptr) - 1, len(col)
+        on_dev = not isinstance(row_ptr, np.ndarray)
+        A = lair_csr(self.n, self.nnz, _ptr(row_ptr), _ptr(col), _ptr(val), int(on_dev))
+        offs = np.ascontiguousarray(sys_offsets, np.int64)
+        self.nsys = len(offs) - 1
+        self.opts = options(**kw)
+        st = lib.lair_setup_batched(C.byref(A), self.nsys, offs.ctypes.data, C.byref(self.opts), C.byref(self._h))
+        if st != LAIR_OK:
+            msg = self.last_error()
+            self.close()
+            raise LairError(st, msg)
+        return self
+
+    def solve_batched(self, b, x=None, tol=1e-8, max_iter=500, cycle=STATIONARY, raise_on_nc=False):
+        """Per-system solves (stationary refinement or FGMRES); returns (x, iters[nsys], rel[nsys], status)."""
+        b = _vec(b, self.n)
+        if x is None:
+            x = np.zeros(self.n) if isinstance(b, np.ndarray) else b.new_zeros(self.n)
+        x = _vec(x, self.n)
+        its = np.zeros(self.nsys, np.int32)
+        rel = np.zeros(self.nsys)
+        st = lib.lair_solve_batched(self._h, _ptr(b), _ptr(x), tol, cycle, max_iter, its.ctypes.data, rel.ctypes.data)
+        self._check(st, (LAIR_OK,) if raise_on_nc else (LAIR_OK, 7))
+        return x, its, rel, st
 
     @classmethod
     def from_system(cls, sys_, device=False, **kw):

@@ -74,6 +74,22 @@ def test_hierarchy_matches_oracle(lair, case):
     assert max(worst.values()) <= tol
 
 
+@pytest.mark.parametrize("M", [24, 32, 40])
+def test_vcycle_dg_sizes_match_oracle(lair, M):
+    """The cycle on several DG meshes (coarsest levels of different sizes, interpolation rows
+    without entries): finite and equal to the oracle's."""
+    import torch
+    s = W.config("dg_p2_256", scale=M)
+    kw = dict(distance=2, interp=1, strength_abs=1, block_size=6, cf_mode=1, precision=1)
+    G = lair.Hierarchy.from_system(s, device=True, **kw)
+    H = O.Hierarchy(s, **oracle_kw(kw))
+    v = np.random.default_rng(M).uniform(-1, 1, s.n)
+    z = G.precond(torch.from_numpy(v).cuda()).cpu().numpy()
+    zo = H.precond(v)
+    assert np.isfinite(z).all()
+    assert np.linalg.norm(z - zo) <= TOL32 * np.linalg.norm(zo)
+
+
 @pytest.mark.parametrize("case", ["fd2d64_rs_d1", "fd2d64_mixed", "fd3d_20_d1", "dg_p2_16", "fd2d_diffusive_d2"])
 def test_vcycle_matches_oracle(lair, case):
     import torch

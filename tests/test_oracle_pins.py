@@ -633,3 +633,22 @@ def test_dg_generator_consistency():
     assert (A @ np.ones(s.n)).sum() == pytest.approx(1.0, rel=1e-12)
     # the neighbour blocks couple only elements sharing an edge
     assert s.n == 6 * 2 * 16
+
+
+def test_batched_splitting_is_per_system():
+    """Batched systems (block diagonal): the splitting of every system equals the one it gets alone."""
+    systems = W.batched_fd(count=5, side_lo=8, side_hi=20)
+    A, offs = W.block_diagonal(systems)
+    for mode in (O.CF_RS, O.CF_AUTO):
+        H = O.Hierarchy(A, seg=offs, cf_mode=mode, rs_block=150, max_levels=2, coarse_max=4)
+        cf = H.levels[0].cf
+        for k, s in enumerate(systems):
+            seg_cf = cf[offs[k]:offs[k + 1]]
+            if mode == O.CF_RS:
+                alone = O.cf_split(s, O.strength(s, 0.25), O.CF_RS)
+            else:
+                alone = O.cf_split(s, O.strength(s, 0.25), O.CF_AUTO, seed=150)
+            assert np.array_equal(seg_cf, alone)
+        # coarse offsets count the C points of the systems before
+        c = np.concatenate([[0], np.cumsum([int((cf[offs[k]:offs[k + 1]] == 1).sum()) for k in range(len(systems))])])
+        assert np.array_equal(H.seg(1), c)

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = [
-    "CsrSystem", "fd_adr", "fd_adr_2d", "fd_adr_3d", "batched_fd", "dg_p2_advection",
+    "CsrSystem", "fd_adr", "fd_adr_2d", "fd_adr_3d", "batched_fd", "block_diagonal", "dg_p2_advection",
     "config", "CONFIG_NAMES", "upwind_chain", "random_sparse", "triangle_rule",
 ]
 
@@ -148,6 +148,26 @@ def batched_fd(count=512, side_lo=32, side_hi=256, seed=2):
         s.meta.update(angle=angle)
         out.append(s)
     return out
+
+
+def block_diagonal(systems):
+    """Concatenate independent systems into one block-diagonal CSR; returns (CsrSystem, offsets)."""
+    offs = np.zeros(len(systems) + 1, np.int64)
+    for k, s_ in enumerate(systems):
+        offs[k + 1] = offs[k] + s_.n
+    nnzs = np.array([s_.nnz for s_ in systems], np.int64)
+    noff = np.concatenate([[0], np.cumsum(nnzs)])
+    n = int(offs[-1])
+    row_ptr = np.zeros(n + 1, np.int64)
+    col = np.empty(int(noff[-1]), np.int32)
+    val = np.empty(int(noff[-1]))
+    b = np.empty(n)
+    for k, s_ in enumerate(systems):
+        row_ptr[offs[k] + 1:offs[k + 1] + 1] = s_.row_ptr[1:] + noff[k]
+        col[noff[k]:noff[k + 1]] = s_.col + offs[k]
+        val[noff[k]:noff[k + 1]] = s_.val
+        b[offs[k]:offs[k + 1]] = s_.b
+    return CsrSystem(n, row_ptr, col, val, b, dict(kind="batch", nsys=len(systems))), offs
 
 
 # --------------------------------------------------------------------------------------
