@@ -36,6 +36,11 @@ WORKLOADS = {
              "block-diagonal scaling; lAIR distance 2, one-point P, |a| strength 0.25, PMIS splitting; "
              "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
         opts=dict(distance=2, interp=1, strength_abs=1, block_size=6, cf_mode=1), tol=1e-8, sample_scale=64),
+    "batched_512": dict(
+        desc="512 independent 2D upwind FD systems, side U{32..256}, angle U(0,2pi), log10 eps U(-6,0), c U(0,1), "
+             "seed 2 (n~12.8M in all); one block-diagonal lAIR hierarchy (distance 1), per-system FGMRES(30) "
+             "with FP32 cycle, per-system tol 1e-8",
+        opts=dict(distance=1), tol=1e-8, sample_scale=8, batched=True),
     "fd3d_192": dict(
         desc="3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1; "
              "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
@@ -145,10 +150,14 @@ class ClockSampler:
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------------
 def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
+    import numpy as np
     import workloads as W
     from oracle import oracle as O
     wl = WORKLOADS[workload]
     s = W.config(workload, scale=wl["sample_scale"])
+    offs = None
+    if wl.get("batched"):
+        s, offs = W.block_diagonal(s)
     kw = dict(wl["opts"])
     okw = dict(distance=kw["distance"], prec=1)
     if "cf_mode" in kw:
@@ -163,11 +172,15 @@ def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
     reps, total, iters = 0, 0.0, 0
     while reps < min_reps or (total < budget_s and reps < max_reps):
         t0 = time.perf_counter()
-        H = O.Hierarchy(s, **okw)
-        x, rep = H.solve(s.b, tol=wl["tol"], cycle=1)
+        if offs is None:
+            H = O.Hierarchy(s, **okw)
+            x, rep = H.solve(s.b, tol=wl["tol"], cycle=1)
+        else:
+            H = O.Hierarchy(s, seg=offs, **okw)
+            x, rep = H.solve_batched(s.b, tol=wl["tol"], cycle=1)
         total += time.perf_counter() - t0
         assert rep["status"] == 0, rep
-        iters = rep["iters"]
+        iters = rep["iters"] if offs is None else int(np.max(rep["iters"]))
         H.close()
         reps += 1
     return dict(n=s.n, reps=reps, seconds=total, value=s.n * reps / total, iters=iters,
@@ -242,6 +255,9 @@ def main():
     dev = torch.device("cuda", dist.local)
     wl = WORKLOADS[args.workload]
     s = W.config(args.workload)
+    offs = None
+    if wl.get("batched"):
+        s, offs = W.block_diagonal(s)
     n, nnz = s.n, s.nnz
     stream = torch.cuda.Stream(device=dev)
     rp = torch.from_numpy(s.row_ptr).to(dev)
@@ -262,7 +278,21 @@ def main():
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            if host is None:
+            if offs is not None:
+                if host is None:
+                    G = lair.Hierarchy.batched(rp, col, val, offs, precision=precision, stream=stream, timing=1,
+                                               **wl["opts"])
+                    with torch.cuda.stream(stream):
+                        x.zero_()
+                    _, sys_its, rls, st = G.solve_batched(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
+                else:
+                    hrp, hcol, hval, hb, hx = host
+                    hx.zero_()
+                    G = lair.Hierarchy.batched(hrp, hcol, hval, offs, precision=precision, stream=stream, timing=1,
+                                               **wl["opts"])
+                    _, sys_its, rls, st = G.solve_batched(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
+                rep = lair.Report(st, int(sys_its.max()), float(rls.max()), 0.0, 0.0, 0, 0, 0, 0.0, 0.0)
+            elif host is None:
                 G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
                 with torch.cuda.stream(stream):
                     x.zero_()

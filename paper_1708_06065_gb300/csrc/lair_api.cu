@@ -258,6 +258,11 @@ static void flush_timers(lair_handle *h) {
 // exclusive scan of cnt[0..n) into out[0..n] (out[n] = total); returns the total
 static lair_status scan(lair_handle *h, const int *cnt, int *out, int n, int *total) {
     // cnt must have n+1 entries with cnt[n] = 0
+    if (n + 1 <= SMALL_SCAN_MAX) {
+        small_scan(n + 1, cnt, out, h->s);
+        if (total) TRY(read_ints(h, out + n, 1, total));
+        return LAIR_OK;
+    }
     size_t need = 0;
     CU(cub::DeviceScan::ExclusiveSum(nullptr, need, cnt, out, n + 1, h->s));
     if (need > h->scan_tmp_bytes) {
@@ -319,7 +324,7 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
 // ---------------------------------------------------------------------------------------
 static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
                               const int *brp, const int *bcol, const double *bval, int **out_rp, int **out_col,
-                              double **out_val, float **out_val32, uint8_t *lsflag, long long *singular, bool keep) {
+                              double **out_val, float **out_val32, uint8_t *lsflag, int *out_nnz, bool keep) {
     const int distance = h->o.distance;
     int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
     TRY(new_counts(h, t, &ub, nc));
@@ -373,15 +378,7 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
     }
     LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag};
     CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
-    if (singular && lsflag) {
-        // count least-squares rows
-        int *c1;
-        TRY(new_counts(h, t, &c1, 1));
-        count_flags(nc, lsflag, c1, h->s);
-        int v = 0;
-        TRY(read_ints(h, c1, 1, &v));
-        *singular += v;
-    }
+    *out_nnz = nout;
     *out_rp = orp;
     *out_col = ocol;
     *out_val = oval;
@@ -396,18 +393,20 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(new_counts(h, t, &ub, nr));
     launch_spgemm_ub(nr, X.rp, X.col, Y.rp, ub, h->s);
     TRY(t.get(&off, (size_t)nr + 1));
-    int total = 0;
-    TRY(scan(h, ub, off, nr, &total));
+    TRY(scan(h, ub, off, nr, nullptr));
     int *tcol, *cnt, *lists, *bc;
     double *tval;
-    TRY(t.get(&tcol, (size_t)total));
-    TRY(t.get(&tval, (size_t)total));
     TRY(new_counts(h, t, &cnt, nr));
     TRY(t.get(&lists, (size_t)SPGEMM_BINS * nr + 1));
-    TRY(new_counts(h, t, &bc, SPGEMM_BINS + 1));
+    TRY(new_counts(h, t, &bc, SPGEMM_BINS + 2));
     launch_spgemm_classify(nr, off, lists, bc, bc + SPGEMM_BINS, h->s);
-    int hc[SPGEMM_BINS + 1];
-    TRY(read_ints(h, bc, SPGEMM_BINS + 1, hc));
+    // one read-back: bin counts, largest bound, and the total bound (staging size)
+    CU(cudaMemcpyAsync(bc + SPGEMM_BINS + 1, off + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
+    int hc[SPGEMM_BINS + 2];
+    TRY(read_ints(h, bc, SPGEMM_BINS + 2, hc));
+    const int total = hc[SPGEMM_BINS + 1];
+    TRY(t.get(&tcol, (size_t)total));
+    TRY(t.get(&tval, (size_t)total));
     int *skeys = nullptr;
     double *svals = nullptr;
     const int nbig = hc[SPGEMM_BINS - 1], ubmax = hc[SPGEMM_BINS];
@@ -491,8 +490,11 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
             int2 *bd;
             TRY(t.get(&bd, blocks.size()));
             CU(cudaMemcpyAsync(bd, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, h->s));
-            CU(launch_rs(n, bd, (int)blocks.size(), Bmax, Scf, STcf, L.cf, h->status, h->s));
-            CU(cudaStreamSynchronize(h->s));   // the host block list must outlive the copy
+            int *mx, maxin = 0;
+            TRY(new_counts(h, t, &mx, 1));
+            launch_rs_count(bd, (int)blocks.size(), Scf, mx, h->s);
+            TRY(read_ints(h, mx, 1, &maxin));   // also keeps the host block list alive until its copy is done
+            CU(launch_rs(n, bd, (int)blocks.size(), Bmax, maxin, Scf, STcf, L.cf, h->status, h->s));
         } else {
             double *w;
             int8_t *newc;
@@ -513,7 +515,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
             }
         }
     }
-    TRY(sync_status(h));
+    // the status word (first-pass errors) is checked with the next read-back
 
     // ---- coarse numbering
     int *flag, *scanv, *cpts;
@@ -552,8 +554,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     L.R.nr = nc;
     L.R.nc = n;
     TRY(local_rows(h, t, nc, cpts, S, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
-                   fp32 ? &L.R.val32 : nullptr, L.lsR, &H.singular_R, true));
-    TRY(read_ints(h, L.R.rp + nc, 1, &L.R.nnz));
+                   fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true));
 
     // ---- interpolation
     L.P.nr = n;
@@ -577,10 +578,9 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         TRY(dalloc(h, &L.lsP, (size_t)nc));
         int *wrp, *wcol;
         double *wval;
-        TRY(local_rows(h, t, nc, cpts, ST, L.cf, atrp, atcol, atval, &wrp, &wcol, &wval, nullptr, L.lsP,
-                       &H.singular_P, false));
         int wnnz = 0;
-        TRY(read_ints(h, wrp + nc, 1, &wnnz));
+        TRY(local_rows(h, t, nc, cpts, ST, L.cf, atrp, atcol, atval, &wrp, &wcol, &wval, nullptr, L.lsP, &wnnz,
+                       false));
         TRY(transpose(h, t, nc, n, wnnz, wrp, wcol, wval, &L.P.rp, &L.P.col, &L.P.val, true));
         L.P.nnz = wnnz;
         if (fp32) {
@@ -616,8 +616,8 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         next.seg_h = next_seg;
         TRY(dalloc(h, &next.seg_d, next_seg.size()));
         CU(cudaMemcpyAsync(next.seg_d, next.seg_h.data(), sizeof(int) * next_seg.size(), cudaMemcpyHostToDevice, h->s));
+        CU(cudaStreamSynchronize(h->s));   // the host vector is copied from pageable memory
     }
-    TRY(sync_status(h));
     H.lev.push_back(next);
     *last = false;
     return LAIR_OK;
@@ -867,7 +867,21 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             break;
         }
     }
-    TRY(sync_status(h));
+    {
+        // least-squares rows of all levels, counted with one read-back
+        Temps t(h);
+        int *c2;
+        TRY(new_counts(h, t, &c2, 2));
+        for (auto &L : H.lev) {
+            if (L.coarsest) continue;
+            if (L.lsR) count_flags(L.nc, L.lsR, c2, h->s);
+            if (L.lsP) count_flags(L.nc, L.lsP, c2 + 1, h->s);
+        }
+        int hc[2];
+        TRY(read_ints(h, c2, 2, hc));
+        H.singular_R = hc[0];
+        H.singular_P = hc[1];
+    }
     TRY(capture_cycle(h, H));
     CU(cudaStreamSynchronize(h->s));
     H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

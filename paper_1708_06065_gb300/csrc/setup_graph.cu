@@ -63,9 +63,37 @@ __global__ void k_transpose_scatter(int nr, const int *__restrict__ rp, const in
         }
 }
 
+constexpr int SORT_REG = 8;   // rows up to this length are sorted in registers
+
 __global__ void k_sort_rows(int nr, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         int b = rp[i], e = rp[i + 1];
+        if (e - b <= SORT_REG) {
+            int c[SORT_REG];
+            double v[SORT_REG];
+            const int len = e - b;
+#pragma unroll
+            for (int k = 0; k < SORT_REG; ++k) {
+                c[k] = k < len ? col[b + k] : 0x7fffffff;
+                v[k] = (k < len && val) ? val[b + k] : 0.0;
+            }
+            // odd-even transposition network (the columns of a row are distinct)
+#pragma unroll
+            for (int pass = 0; pass < SORT_REG; ++pass)
+#pragma unroll
+                for (int k = pass & 1; k + 1 < SORT_REG; k += 2)
+                    if (c[k] > c[k + 1]) {
+                        int tc = c[k]; c[k] = c[k + 1]; c[k + 1] = tc;
+                        double tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
+                    }
+#pragma unroll
+            for (int k = 0; k < SORT_REG; ++k)
+                if (k < len) {
+                    col[b + k] = c[k];
+                    if (val) val[b + k] = v[k];
+                }
+            continue;
+        }
         for (int k = b + 1; k < e; ++k) {
             int c = col[k];
             double v = val ? val[k] : 0.0;
@@ -159,7 +187,6 @@ __global__ void k_pmis_mark(int n, Graph ST, const int8_t *__restrict__ newc, in
 // is the point to take. A 32-ary max tree (leaves, level 1 = max of 32 leaves, level 2 =
 // max of 32 level-1 nodes, at most 32 of them) finds it in three warp reductions.
 // -------------------------------------------------------------------------------------
-constexpr int RS_LIST = 1024;
 constexpr int8_t CF_NEWF = 2;   // F point created in the current step
 constexpr int RS_SMEM_MAX = 200 * 1024;
 
@@ -182,7 +209,7 @@ __device__ void rs_rebuild(int n, int n1, const unsigned *key, unsigned *l1, uns
 
 // in-block view of a strength graph: rows and neighbours as local indices 0..n-1
 struct StagedView {         // copied to shared memory, out-of-block entries removed
-    const int *rp;
+    const uint16_t *rp;       // row offsets (the staged area holds fewer than 65536 entries per graph)
     const uint16_t *col;
     __device__ int beg(int li) const { return rp[li]; }
     __device__ int end(int li) const { return rp[li + 1]; }
@@ -196,9 +223,12 @@ struct GlobalView {         // read from global memory, out-of-block entries rep
     __device__ int at(int p) const { int j = col[p]; return (j >= b0 && j < b1) ? j - b0 : -1; }
 };
 
+// marks the level-1 node of leaf k as changed: bit (k / 32) % 32 of word k / 1024
+__device__ __forceinline__ void rs_mark(unsigned *gmask, int k) { atomicOr(&gmask[k >> 10], 1u << ((k >> 5) & 31)); }
+
 template <class V>
-__device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned *l1, unsigned *l2, int *list,
-                         int8_t *cf, int *nlist_p) {
+__device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned *l1, unsigned *l2, unsigned *gmask,
+                         int8_t *cf) {
     const unsigned lane = threadIdx.x;
     const int n1 = (n + 31) / 32;
     for (long long step = 0; step <= (long long)n; ++step) {
@@ -215,8 +245,7 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
         if (lane == 0) {
             cf[i] = CF_C;
             key[i] = 0u;
-            list[0] = i;
-            *nlist_p = 1;
+            rs_mark(gmask, i);
         }
         __syncwarp();
         // undecided in-block dependants of i become F (marked as new for this step)
@@ -225,8 +254,7 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
             if (j >= 0 && cf[j] == CF_U) {
                 cf[j] = CF_NEWF;
                 key[j] = 0u;
-                int t = atomicAdd(nlist_p, 1);
-                if (t < RS_LIST) list[t] = j;
+                rs_mark(gmask, j);
             }
         }
         __syncwarp();
@@ -238,8 +266,7 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
                 int k = S.at(q);
                 if (k >= 0 && cf[k] == CF_U) {
                     atomicAdd(&key[k], 1u << 16);
-                    int t = atomicAdd(nlist_p, 1);
-                    if (t < RS_LIST) list[t] = k;
+                    rs_mark(gmask, k);
                 }
             }
         }
@@ -248,8 +275,7 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
             int k = S.at(q);
             if (k >= 0 && cf[k] == CF_U) {
                 atomicSub(&key[k], 1u << 16);
-                int t = atomicAdd(nlist_p, 1);
-                if (t < RS_LIST) list[t] = k;
+                rs_mark(gmask, k);
             }
         }
         __syncwarp();
@@ -257,25 +283,26 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
             int j = ST.at(p);
             if (j >= 0 && cf[j] == CF_NEWF) cf[j] = CF_F;
         }
-        const int nl = *nlist_p;
+        // recompute the changed level-1 nodes (one warp reduction each), then their level-2 nodes
+        const unsigned word = gmask[lane];
         __syncwarp();
-        if (nl > RS_LIST) {
-            rs_rebuild(n, n1, key, l1, l2, lane);
-            continue;
-        }
-        // recompute the level-1 nodes of changed leaves (duplicates write identical values)
-        for (int t = lane; t < nl; t += 32) {
-            int gg = list[t] >> 5;
-            unsigned m = 0;
-            for (int u = 0; u < 32 && 32 * gg + u < n; ++u) m = max(m, key[32 * gg + u]);
-            l1[gg] = m;
-        }
-        __syncwarp();
-        for (int t = lane; t < nl; t += 32) {
-            int hh = list[t] >> 10;
-            unsigned m = 0;
-            for (int u = 0; u < 32 && 32 * hh + u < n1; ++u) m = max(m, l1[32 * hh + u]);
-            l2[hh] = m;
+        gmask[lane] = 0u;
+        unsigned hs = __ballot_sync(0xffffffffu, word != 0u);
+        while (hs) {
+            const int hh = __ffs(hs) - 1;
+            hs &= hs - 1;
+            unsigned bits = __shfl_sync(0xffffffffu, word, hh);
+            while (bits) {
+                const int gg = 32 * hh + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int lf = 32 * gg + (int)lane;
+                const unsigned m = warp_max_u32(lf < n ? key[lf] : 0u);
+                if (lane == 0) l1[gg] = m;
+            }
+            __syncwarp();
+            const int gq = 32 * hh + (int)lane;
+            const unsigned m = warp_max_u32(gq < n1 ? l1[gq] : 0u);
+            if (lane == 0) l2[hh] = m;
         }
         __syncwarp();
     }
@@ -283,7 +310,7 @@ __device__ void rs_steps(int n, const V &S, const V &ST, unsigned *key, unsigned
 
 // copy the in-block part of graph G (rows b0..b1-1) into shared memory; returns false if it
 // does not fit in cap bytes (nothing is used then)
-__device__ bool rs_stage(const Graph &G, int b0, int b1, int *rp, uint16_t *col, size_t cap_entries) {
+__device__ bool rs_stage(const Graph &G, int b0, int b1, uint16_t *rp, uint16_t *col, size_t cap_entries) {
     const unsigned lane = threadIdx.x;
     const int n = b1 - b0;
     // counts, then an exclusive scan in lane-contiguous chunks
@@ -302,14 +329,14 @@ __device__ bool rs_stage(const Graph &G, int b0, int b1, int *rp, uint16_t *col,
         if ((int)lane >= o) incl += t;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if ((size_t)total > cap_entries) return false;
+    if ((size_t)total > cap_entries || total > 65535) return false;
     int run = incl - mine;
     for (int li = r0; li < r1; ++li) {
         int c = rp[li];
-        rp[li] = run;
+        rp[li] = (uint16_t)run;
         run += c;
     }
-    if (lane == 31) rp[n] = total;
+    if (lane == 31) rp[n] = (uint16_t)total;
     __syncwarp();
     for (int li = r0; li < r1; ++li) {
         int q = rp[li];
@@ -332,13 +359,13 @@ __global__ void __launch_bounds__(32) k_rs_split(int n_all, const int2 *__restri
     unsigned *key = reinterpret_cast<unsigned *>(smem);
     unsigned *l1 = key + n;
     unsigned *l2 = l1 + n1;
-    int *list = reinterpret_cast<int *>(l2 + 32);      // local indices of leaves changed in the current step
-    int *srp = list + RS_LIST;                         // staged graphs: row pointers of S and ST, then columns
-    int *strp = srp + (n + 1);
-    int8_t *cf = reinterpret_cast<int8_t *>(strp + (n + 1));
-    uint16_t *scol = reinterpret_cast<uint16_t *>(cf + ((n + 15) & ~15));
-    __shared__ int nlist;
+    int8_t *cf = reinterpret_cast<int8_t *>(l2 + 32);
+    uint16_t *srp = reinterpret_cast<uint16_t *>(cf + ((n + 15) & ~15));   // staged graphs: row offsets of S, ST
+    uint16_t *strp = srp + (n + 1);
+    uint16_t *scol = strp + (n + 1);                   // then the columns of S and of ST
+    __shared__ unsigned gmask[32];                     // changed level-1 nodes of the current step
     const unsigned lane = threadIdx.x;
+    gmask[lane] = 0u;
 
     for (int li = lane; li < n; li += 32) {
         const int i = b0 + li;
@@ -361,10 +388,10 @@ __global__ void __launch_bounds__(32) k_rs_split(int n_all, const int2 *__restri
     }
     if (staged) {
         StagedView vs{srp, scol}, vt{strp, scol + srp[n]};
-        rs_steps(n, vs, vt, key, l1, l2, list, cf, &nlist);
+        rs_steps(n, vs, vt, key, l1, l2, gmask, cf);
     } else {
         GlobalView vs{S.rp, S.col, b0, b1}, vt{ST.rp, ST.col, b0, b1};
-        rs_steps(n, vs, vt, key, l1, l2, list, cf, &nlist);
+        rs_steps(n, vs, vt, key, l1, l2, gmask, cf);
     }
     for (int li = lane; li < n; li += 32) {
         int8_t c = cf[li];
@@ -373,15 +400,24 @@ __global__ void __launch_bounds__(32) k_rs_split(int n_all, const int2 *__restri
     }
 }
 
-// shared memory of one block: the fixed part (keys, tree, list, row pointers, splitting) plus room
-// for the staged in-block graphs, up to RS_SMEM_MAX bytes in all
-size_t rs_smem_bytes(int n, double avg_degree) {
+// the largest number of in-block entries of S over the blocks (S and ST have the same count)
+__global__ void __launch_bounds__(32) k_rs_count(const int2 *__restrict__ blocks, Graph S, int *__restrict__ maxcnt) {
+    const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
+    int c = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += 32)
+        for (int p = S.rp[i]; p < S.rp[i + 1]; ++p) c += (S.col[p] >= b0 && S.col[p] < b1);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (threadIdx.x == 0) atomicMax(maxcnt, c);
+}
+
+// shared memory of one block: the fixed part (keys, tree, splitting, row offsets) plus room for
+// both staged in-block graphs of the fullest block, up to RS_SMEM_MAX bytes in all (blocks that
+// do not fit then read their graphs from global memory)
+size_t rs_smem_bytes(int n, int max_inblock) {
     int n1 = (n + 31) / 32;
-    size_t fixed = sizeof(unsigned) * ((size_t)n + n1 + 32) + sizeof(int) * (RS_LIST + 2 * ((size_t)n + 1)) +
-                   (((size_t)n + 15) & ~(size_t)15);
-    double per_row = 1.25 * avg_degree + 2.0;            // room for the in-block entries of a typical block
-    if (per_row > 24.0) per_row = 24.0;
-    size_t want = fixed + (size_t)(2 * sizeof(uint16_t) * (double)n * per_row);
+    size_t fixed = sizeof(unsigned) * ((size_t)n + n1 + 32) + (((size_t)n + 15) & ~(size_t)15) +
+                   sizeof(uint16_t) * 2 * ((size_t)n + 1);
+    size_t want = fixed + 2 * sizeof(uint16_t) * (size_t)max_inblock + 16;
     return want < RS_SMEM_MAX ? want : (fixed < RS_SMEM_MAX ? RS_SMEM_MAX : fixed);
 }
 
@@ -463,6 +499,46 @@ __global__ void k_nb_compact(int nc, const int *__restrict__ off, const int *__r
 }
 
 // -------------------------------------------------------------------------------------
+// exclusive scan of m <= SMALL_SCAN_MAX ints in one CTA: every thread owns a contiguous chunk
+// -------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_small_scan(int m, const int *__restrict__ in, int *__restrict__ out) {
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int chunk = (m + 1023) / 1024;
+    const int b = min(m, t * chunk), e = min(m, b + chunk);
+    int mine = 0;
+    for (int i = b; i < e; ++i) mine += in[i];
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        int iv = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += u;
+        }
+        wsum[lane] = iv - v;
+    }
+    __syncthreads();
+    int run = wsum[w] + incl - mine;
+    for (int i = b; i < e; ++i) {
+        int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+}
+
+void small_scan(int m, const int *in, int *out, cudaStream_t s) {
+    k_small_scan<<<1, 1024, 0, s>>>(m, in, out);
+    count_launch();
+}
+
+// -------------------------------------------------------------------------------------
 // host wrappers
 // -------------------------------------------------------------------------------------
 static const int TB = 256;
@@ -506,9 +582,14 @@ void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, 
 }
 
 // blocks: nblocks (b0, b1) pairs on the device, every block at most Bmax points
-cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, const Graph &S, const Graph &ST, int8_t *cf,
-                      int *status, cudaStream_t s) {
-    size_t bytes = rs_smem_bytes(Bmax, n > 0 ? (double)S.nnz / n : 0.0);
+void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s) {
+    k_rs_count<<<nblocks, 32, 0, s>>>(blocks, S, maxcnt);
+    count_launch();
+}
+
+cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
+                      int8_t *cf, int *status, cudaStream_t s) {
+    size_t bytes = rs_smem_bytes(Bmax, max_inblock);
     cudaError_t e = cudaFuncSetAttribute(k_rs_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_rs_split<<<nblocks, 32, bytes, s>>>(n, blocks, S, ST, cf, status, (int)bytes);

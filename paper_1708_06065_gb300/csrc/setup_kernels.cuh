@@ -16,6 +16,8 @@ struct SellView {
 };
 
 // ---- setup_graph.cu -------------------------------------------------------------------
+constexpr int SMALL_SCAN_MAX = 65536;   // exclusive scans up to this length run in one CTA
+void small_scan(int m, const int *in, int *out, cudaStream_t s);
 void launch_strength(const DCsr &A, double theta, int absmode, uint8_t *mask, int *cnt, cudaStream_t s);
 void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaStream_t s);
 void launch_col_count(int nr, const int *rp, const int *col, int *cnt, cudaStream_t s);
@@ -25,9 +27,10 @@ void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
 void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
                        int *undecided, cudaStream_t s);
-cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, const Graph &S, const Graph &ST, int8_t *cf,
-                      int *status, cudaStream_t s);
-size_t rs_smem_bytes(int n, double avg_degree);
+void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s);
+cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
+                      int8_t *cf, int *status, cudaStream_t s);
+size_t rs_smem_bytes(int n, int max_inblock);
 constexpr int RS_MAX_N = 32768;
 void launch_cidx(int n, const int8_t *cf, int *flag, int *cidx, int *cpts, int phase, cudaStream_t s);
 void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, int *ub, cudaStream_t s);
