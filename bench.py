@@ -271,17 +271,20 @@ def main():
     def run_steps(k, precision, timed, host=None):
         """k set-up + solve steps; returns per-step ms (CUDA events on the library stream) and stats."""
         times, its, rels, launches = [], [], [], 0
+        setup_ms = []
         timers = {}
         for i in range(k):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))           # evict L2 between steps (not timed)
             ev0 = torch.cuda.Event(enable_timing=True)
+            evm = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             if offs is not None:
                 if host is None:
                     G = lair.Hierarchy.batched(rp, col, val, offs, precision=precision, stream=stream, timing=1,
                                                **wl["opts"])
+                    evm.record(stream)
                     with torch.cuda.stream(stream):
                         x.zero_()
                     _, sys_its, rls, st = G.solve_batched(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
@@ -290,10 +293,12 @@ def main():
                     hx.zero_()
                     G = lair.Hierarchy.batched(hrp, hcol, hval, offs, precision=precision, stream=stream, timing=1,
                                                **wl["opts"])
+                    evm.record(stream)
                     _, sys_its, rls, st = G.solve_batched(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
                 rep = lair.Report(st, int(sys_its.max()), float(rls.max()), 0.0, 0.0, 0, 0, 0, 0.0, 0.0)
             elif host is None:
                 G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
+                evm.record(stream)
                 with torch.cuda.stream(stream):
                     x.zero_()
                 _, rep = G.solve(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
@@ -301,12 +306,14 @@ def main():
                 hrp, hcol, hval, hb, hx = host
                 hx.zero_()
                 G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=1, **wl["opts"])
+                evm.record(stream)
                 _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
             ev1.record(stream)
             ev1.synchronize()
             if rep.status != 0:
                 raise RuntimeError(f"solve did not converge: {rep}")
             times.append(ev0.elapsed_time(ev1))
+            setup_ms.append(ev0.elapsed_time(evm))
             its.append(rep.iters)
             rels.append(rep.final_rel)
             launches += G.launches
@@ -315,7 +322,7 @@ def main():
                 t[0] += cnt
                 t[1] += ms
             G.close()
-        return times, its, rels, launches, timers
+        return times, its, rels, launches, timers, setup_ms
 
     # ---- mixed precision (the headline), device-resident inputs
     run_steps(args.warmup, lair.MIXED, False)
@@ -323,7 +330,7 @@ def main():
     dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    t_mixed, it_mixed, rel_mixed, launches, timers = run_steps(args.steps, lair.MIXED, True)
+    t_mixed, it_mixed, rel_mixed, launches, timers, su_mixed = run_steps(args.steps, lair.MIXED, True)
     torch.cuda.synchronize()
     clk = clocks.stop()
     dist.barrier()
@@ -331,7 +338,7 @@ def main():
 
     # ---- plain FP64 path, same protocol
     run_steps(1, lair.FP64, False)
-    t64, it64, rel64, _, _ = run_steps(args.steps, lair.FP64, True)
+    t64, it64, rel64, _, _, su64 = run_steps(args.steps, lair.FP64, True)
     ms64 = dist.max(sum(t64) / len(t64))
 
     # ---- end to end through host buffers (pinned), mixed
@@ -340,7 +347,7 @@ def main():
         pin = lambda a: torch.from_numpy(a).pin_memory()
         host = (pin(s.row_ptr), pin(s.col), pin(s.val), pin(s.b), torch.zeros(n, dtype=torch.float64).pin_memory())
         run_steps(1, lair.MIXED, False, host=host)
-        te, _, _, _, _ = run_steps(args.steps, lair.MIXED, True, host=host)
+        te, _, _, _, _, _ = run_steps(args.steps, lair.MIXED, True, host=host)
         mse = dist.max(sum(te) / len(te))
         e2e = {"value": dist.world * n / (mse / 1e3), "unit": "unknowns/s",
                "h2d_bytes_per_step": int((n + 1) * 8 + nnz * 4 + nnz * 8 + 2 * n * 8),
@@ -376,8 +383,10 @@ def main():
         "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "nnz": nnz, "parallelism": "replicas",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB written before every step (untimed); matrix alone is "
                          f"{(nnz * 12 + n * 8) / 1e6:.0f} MB > 129 MB L2"},
-        "mixed": {"value": value, "ms_per_step": ms_mixed, "iters": it_mixed, "final_rel": max(rel_mixed)},
-        "fp64": {"value": dist.world * n / (ms64 / 1e3), "ms_per_step": ms64, "iters": it64, "final_rel": max(rel64)},
+        "mixed": {"value": value, "ms_per_step": ms_mixed, "setup_ms": dist.max(sum(su_mixed) / len(su_mixed)),
+                  "iters": it_mixed, "final_rel": max(rel_mixed)},
+        "fp64": {"value": dist.world * n / (ms64 / 1e3), "ms_per_step": ms64, "setup_ms": dist.max(sum(su64) / len(su64)),
+                 "iters": it64, "final_rel": max(rel64)},
         "mixed_over_fp64": ms64 / ms_mixed,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,

@@ -501,18 +501,9 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
             int *und;
             TRY(t.get(&w, (size_t)n));
             TRY(t.get(&newc, (size_t)n));
-            TRY(new_counts(h, t, &und, 1));
+            TRY(new_counts(h, t, &und, 4));
             launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, L.cf, h->s);
-            // rounds after the last undecided point is gone change nothing, so the host looks
-            // at the count only every few rounds
-            const int every = 4;
-            for (int round = 0; round <= n; round += every) {
-                CU(cudaMemsetAsync(und, 0, sizeof(int), h->s));
-                for (int k = 0; k < every; ++k) launch_pmis_round(n, Scf, STcf, w, L.cf, newc, und, h->s);
-                int u = 0;
-                TRY(read_ints(h, und, 1, &u));
-                if (u == 0) break;
-            }
+            CU(launch_pmis_all(n, Scf, STcf, w, L.cf, newc, und, h->status, h->s));
         }
     }
     // the status word (first-pass errors) is checked with the next read-back
@@ -808,7 +799,8 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             const int bs = o.block_size, nblk = A.nr / bs;
             int *rowcnt;
             TRY(new_counts(h, t, &rowcnt, A.nr));
-            launch_block_count(nblk, bs, A, rowcnt, h->status, h->s);
+            if (!launch_block_count(nblk, bs, A, rowcnt, h->s))
+                return fail(h, LAIR_ERR_UNSUPPORTED, "block_size %d", bs);
             DCsr B;
             B.nr = B.nc = A.nr;
             TRY(dalloc(h, &B.rp, (size_t)A.nr + 1));
@@ -817,7 +809,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             TRY(dalloc(h, &B.val, (size_t)B.nnz));
             H.bs = bs;
             TRY(dalloc(h, &H.blk_inv, (size_t)A.nr * bs));
-            launch_block_fill(nblk, bs, A, B, H.blk_inv, h->status, h->s);
+            launch_block_fill(nblk, bs, A, B, H.blk_inv, h->status, h->s);   // block size checked above
             TRY(sync_status(h));
             A = B;
         }
@@ -995,7 +987,8 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
     } else {
         double *V = h->V, *Z = h->Z;
         std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hc(m + 2), y(m + 1);
-        double *hsum = h->dsc + 8, *hbuf = h->dsc + 48, *nrm = h->dsc + 1, *ydev = h->dsc + 96;
+        // device scalars: |r|^2 at 1, Hessenberg column at 8 (32), the two CGS2 projections at 48 (64), y at 112 (32)
+        double *hsum = h->dsc + 8, *hbuf = h->dsc + 48, *nrm = h->dsc + 1, *ydev = h->dsc + 112;
         residual(A, b, x, V, nullptr, h->part, h->s);
         finish_partials(1, h->part, nrm, h->s);
         CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -1018,12 +1011,15 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
                 sell_spmv<double>(L0.A64, zj, w, h->s);
                 tend(h, ts);
                 CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (j + 1), h->s));
-                for (int pass = 0; pass < 2; ++pass) {
-                    multidot(n, j + 1, V, n, w, h->part, hbuf, hsum, h->s);
-                    sub_combo(n, j + 1, V, n, hbuf, w, h->s);
-                }
-                TRY(norm2_dev(h, n, w, nrm, nullptr));
+                int to = tbegin(h, "outer_cgs2", 8.0 * n * (3.0 * (j + 2) + 4.0));
+                cgs_pass(1, n, j + 1, V, n, nullptr, w, h->part, h->s);
+                finish_partials_acc(j + 1, h->part, hbuf, hsum, h->s);
+                cgs_pass(2, n, j + 1, V, n, hbuf, w, h->part, h->s);
+                finish_partials_acc(j + 1, h->part, hbuf + 32, hsum, h->s);
+                cgs_pass(3, n, j + 1, V, n, hbuf + 32, w, h->part, h->s);
+                finish_partials(1, h->part, nrm, h->s);
                 scale_by_norm(n, w, nrm, w, h->s);
+                tend(h, to);
                 CU(cudaMemcpyAsync(h->h_dbl, hsum, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->s));
                 CU(cudaMemcpyAsync(h->h_dbl + 40, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
                 CU(cudaStreamSynchronize(h->s));

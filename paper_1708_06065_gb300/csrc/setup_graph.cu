@@ -136,41 +136,87 @@ __device__ __forceinline__ bool beats(double wi, int i, double wj, int j) {
     return (wi > wj) || (wi == wj && i < j);
 }
 
-__global__ void k_pmis_select(int n, Graph S, Graph ST, const double *__restrict__ w, const int8_t *__restrict__ cf,
-                              int8_t *__restrict__ newc, int *__restrict__ undecided) {
-    int local = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int8_t nc = 0;
-        if (cf[i] == CF_U) {
-            ++local;
-            double wi = w[i];
-            bool best = true;
-            for (int p = S.rp[i]; p < S.rp[i + 1] && best; ++p) {
-                int j = S.col[p];
-                if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
+// -------------------------------------------------------------------------------------
+// All PMIS rounds of a level in one cooperative launch. A round: every undecided point whose
+// weight beats those of all undecided points in S_i and ST_i is selected; grid barrier; stop
+// when the select pass saw no undecided point; selected points become C and their undecided
+// dependants (ST_i) F; grid barrier. Two selected points never lie in each other's ST (they
+// would beat each other), so marking C and F in one pass is race-free.
+// ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2 + r % 2] undecided count of round r
+// (zero on entry). Every barrier wait is bounded; a wait that gives up sets
+// LAIR_ERR_DEVICE_TIMEOUT and the block returns.
+// -------------------------------------------------------------------------------------
+constexpr long long GRID_SPIN_LIMIT = 1ll << 22;
+
+__device__ bool grid_barrier(int *ctl, int *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile int *gen = ctl + 1;
+        const int g = *gen;
+        __threadfence();
+        if (atomicAdd(ctl, 1) == (int)gridDim.x - 1) {
+            atomicExch(ctl, 0);
+            __threadfence();
+            atomicAdd(ctl + 1, 1);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > GRID_SPIN_LIMIT) {
+                    set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
             }
-            for (int p = ST.rp[i]; p < ST.rp[i + 1] && best; ++p) {
-                int j = ST.col[p];
-                if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
-            }
-            nc = best;
         }
-        newc[i] = nc;
+        __threadfence();
     }
-    local = __reduce_add_sync(0xffffffffu, local);
-    if (lane_id() == 0 && local) atomicAdd(undecided, local);
+    __syncthreads();
+    return ok != 0;
 }
 
-// new C points never lie in ST of another new C point (they would beat each other), so
-// setting C and F in one pass is race-free.
-__global__ void k_pmis_mark(int n, Graph ST, const int8_t *__restrict__ newc, int8_t *__restrict__ cf) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (!newc[i]) continue;
-        cf[i] = CF_C;
-        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) {
-            int j = ST.col[p];
-            if (cf[j] == CF_U) cf[j] = CF_F;
+__global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, const double *__restrict__ w,
+                                                   int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
+                                                   int *status) {
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int round = 0; round <= n; ++round) {
+        int local = 0;
+        for (int i = t0; i < n; i += stride) {
+            int8_t nc = 0;
+            if (cf[i] == CF_U) {
+                ++local;
+                const double wi = w[i];
+                bool best = true;
+                for (int p = S.rp[i]; p < S.rp[i + 1] && best; ++p) {
+                    const int j = S.col[p];
+                    if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
+                }
+                for (int p = ST.rp[i]; p < ST.rp[i + 1] && best; ++p) {
+                    const int j = ST.col[p];
+                    if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
+                }
+                nc = best;
+            }
+            newc[i] = nc;
         }
+        local = __reduce_add_sync(0xffffffffu, local);
+        if (lane_id() == 0 && local) atomicAdd(ctl + 2 + (round & 1), local);
+        if (!grid_barrier(ctl, status)) return;
+        const int und = *(volatile int *)(ctl + 2 + (round & 1));
+        if (und == 0) return;
+        if (t0 == 0) ctl[2 + ((round + 1) & 1)] = 0;   // nobody adds to it before the next barrier
+        for (int i = t0; i < n; i += stride) {
+            if (!newc[i]) continue;
+            cf[i] = CF_C;
+            for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) {
+                const int j = ST.col[p];
+                if (cf[j] == CF_U) cf[j] = CF_F;
+            }
+        }
+        if (!grid_barrier(ctl, status)) return;
     }
 }
 
@@ -499,37 +545,54 @@ __global__ void k_nb_compact(int nc, const int *__restrict__ off, const int *__r
 }
 
 // -------------------------------------------------------------------------------------
-// exclusive scan of m <= SMALL_SCAN_MAX ints in one CTA: every thread owns a contiguous chunk
+// exclusive scan of m <= SMALL_SCAN_MAX ints in one CTA, in tiles of 16384: warp w scans the
+// 512 entries [512 w, 512 w + 512) of a tile as 16 coalesced strips of 32 held in registers
 // -------------------------------------------------------------------------------------
+constexpr int SCAN_STRIPS = 16;
+constexpr int SCAN_TILE = 1024 * SCAN_STRIPS;
+
 __global__ void __launch_bounds__(1024) k_small_scan(int m, const int *__restrict__ in, int *__restrict__ out) {
     __shared__ int wsum[32];
+    __shared__ int tile_total;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int chunk = (m + 1023) / 1024;
-    const int b = min(m, t * chunk), e = min(m, b + chunk);
-    int mine = 0;
-    for (int i = b; i < e; ++i) mine += in[i];
-    int incl = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int v = wsum[lane];
-        int iv = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, iv, o);
-            if (lane >= o) iv += u;
+    int carry = 0;
+    for (int base = 0; base < m; base += SCAN_TILE) {
+        const int seg = base + w * 32 * SCAN_STRIPS + lane;
+        int v[SCAN_STRIPS];
+#pragma unroll
+        for (int k = 0; k < SCAN_STRIPS; ++k) v[k] = seg + 32 * k < m ? in[seg + 32 * k] : 0;
+        int run = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_STRIPS; ++k) {
+            int x = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            v[k] = run + x - v[k];
+            run += __shfl_sync(0xffffffffu, x, 31);
         }
-        wsum[lane] = iv - v;
-    }
-    __syncthreads();
-    int run = wsum[w] + incl - mine;
-    for (int i = b; i < e; ++i) {
-        int v = in[i];
-        out[i] = run;
-        run += v;
+        if (lane == 0) wsum[w] = run;
+        __syncthreads();
+        if (w == 0) {
+            const int sv = wsum[lane];
+            int x = sv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            wsum[lane] = x - sv;
+            if (lane == 31) tile_total = x;
+        }
+        __syncthreads();
+        const int off = carry + wsum[w];
+#pragma unroll
+        for (int k = 0; k < SCAN_STRIPS; ++k)
+            if (seg + 32 * k < m) out[seg + 32 * k] = off + v[k];
+        carry += tile_total;
+        __syncthreads();
     }
 }
 
@@ -574,12 +637,23 @@ void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *
     count_launch();
 }
 
-void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
-                       int *undecided, cudaStream_t s) {
-    k_pmis_select<<<grid_for(n, TB), TB, 0, s>>>(n, S, ST, w, cf, newc, undecided);
-    k_pmis_mark<<<grid_for(n, TB), TB, 0, s>>>(n, ST, newc, cf);
-    count_launch(2);
+// ctl: 4 ints, zero
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc, int *ctl,
+                            int *status, cudaStream_t s) {
+    int dev = 0, per_sm = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pmis_coop, 256, 0);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int grid = (per_sm > 0 ? per_sm : 1) * sms;
+    const int need = (n + 255) / 256;
+    if (grid > need) grid = need > 0 ? need : 1;
+    void *args[] = {(void *)&n, (void *)&S, (void *)&ST, (void *)&w, (void *)&cf, (void *)&newc, (void *)&ctl, (void *)&status};
+    e = cudaLaunchCooperativeKernel((const void *)k_pmis_coop, dim3(grid), dim3(256), args, 0, s);
+    count_launch();
+    return e;
 }
+
 
 // blocks: nblocks (b0, b1) pairs on the device, every block at most Bmax points
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s) {

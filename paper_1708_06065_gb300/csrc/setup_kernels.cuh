@@ -25,8 +25,8 @@ void launch_transpose_scatter(int nr, const int *rp, const int *col, const doubl
                               int *tcol, double *tval, cudaStream_t s);
 void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s);
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
-void launch_pmis_round(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc,
-                       int *undecided, cudaStream_t s);
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc, int *ctl,
+                            int *status, cudaStream_t s);
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
                       int8_t *cf, int *status, cudaStream_t s);
@@ -58,8 +58,9 @@ cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, co
 size_t local_cta_scratch_bytes(int smax, bool fp32);
 void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t *cf, const int *cidx, int absmode,
                      int *choice, int *cnt, DCsr *P, cudaStream_t s);
-void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *status, cudaStream_t s);
-void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s);
+// block sizes 2..8 (false for any other)
+bool launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, cudaStream_t s);
+bool launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s);
 void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, double *out, cudaStream_t s);
 
 // ---- setup_rap.cu ---------------------------------------------------------------------
@@ -97,6 +98,10 @@ void residual(const DCsr &A, const double *b, const double *x, double *r, float 
 void multidot(int n, int m, const double *X, long long ldx, const double *y, double *part, double *out, double *acc,
               cudaStream_t s);
 void finish_partials(int m, const double *part, double *out, cudaStream_t s);
+void finish_partials_acc(int m, const double *part, double *out, double *acc, cudaStream_t s);
+// one pass (1, 2 or 3) of CGS2 of w against the m <= 32 columns of X; block partials in part
+void cgs_pass(int pass, int n, int m, const double *X, long long ldx, const double *h, double *w, double *part,
+              cudaStream_t s);
 void sub_combo(int n, int m, const double *X, long long ldx, const double *h, double *w, cudaStream_t s);
 void add_combo(int n, int m, const double *Z, long long ldz, const double *y, double *x, cudaStream_t s);
 void scale_by_norm(int n, const double *v, const double *nrm2, double *out, cudaStream_t s);

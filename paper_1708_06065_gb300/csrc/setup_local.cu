@@ -482,33 +482,39 @@ void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t
 // sum_t Dinv[r][t] * A[K t, :] (fma, ascending t) on the union of the block rows'
 // off-block columns, and the diagonal block becomes the exact identity.
 // ---------------------------------------------------------------------------------------
-constexpr int BS_MAX = 8;
-
-// Walk the bs rows of a block in merged column order, skipping the block's own columns.
-// For every column j of the union, vals[t] = A[r0 + t][j] (0 when not stored).
+// Walk the BS rows of a block in merged column order, skipping the block's own columns.
+// For every column j of the union, vals[t] = A[r0 + t][j] (0 when not stored). BS is a
+// compile-time constant so that the cursors stay in registers.
+template <int BS>
 struct BlockMerge {
     const int *rp, *col;
     const double *val;
-    int r0, bs;
-    int pos[BS_MAX], end[BS_MAX];
-    __device__ void init() {
-        for (int t = 0; t < bs; ++t) {
+    int r0;
+    int pos[BS], end[BS];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
             pos[t] = rp[r0 + t];
             end[t] = rp[r0 + t + 1];
             skip(t);
         }
     }
-    __device__ void skip(int t) {
-        while (pos[t] < end[t] && col[pos[t]] >= r0 && col[pos[t]] < r0 + bs) ++pos[t];
+    __device__ __forceinline__ void skip(int t) {
+        while (pos[t] < end[t] && col[pos[t]] >= r0 && col[pos[t]] < r0 + BS) ++pos[t];
     }
     // next union column (or -1); fills vals[t]
-    __device__ int next(double *vals) {
+    __device__ __forceinline__ int next(double *vals) {
+        int c[BS];
         int j = 0x7fffffff;
-        for (int t = 0; t < bs; ++t)
-            if (pos[t] < end[t] && col[pos[t]] < j) j = col[pos[t]];
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+            c[t] = pos[t] < end[t] ? col[pos[t]] : 0x7fffffff;
+            j = min(j, c[t]);
+        }
         if (j == 0x7fffffff) return -1;
-        for (int t = 0; t < bs; ++t) {
-            if (pos[t] < end[t] && col[pos[t]] == j) {
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+            if (c[t] == j) {
                 if (vals) vals[t] = val[pos[t]];
                 ++pos[t];
                 skip(t);
@@ -520,116 +526,140 @@ struct BlockMerge {
     }
 };
 
-__global__ void k_block_count(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
-                              int *__restrict__ rowcnt, int *status) {
+template <int BS>
+__global__ void k_block_count(int nblk, const int *__restrict__ rp, const int *__restrict__ col, int *__restrict__ rowcnt) {
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
-        BlockMerge m{rp, col, nullptr, K * bs, bs};
+        BlockMerge<BS> m{rp, col, nullptr, K * BS};
         m.init();
         int nu = 0;
         while (m.next(nullptr) >= 0) ++nu;
-        for (int r = 0; r < bs; ++r) rowcnt[K * bs + r] = nu + 1;
+#pragma unroll
+        for (int r = 0; r < BS; ++r) rowcnt[K * BS + r] = nu + 1;
     }
 }
 
-__device__ double entry(const int *rp, const int *col, const double *val, int i, int j) {
-    int lo = rp[i], hi = rp[i + 1] - 1;
-    while (lo <= hi) {
-        int m = (lo + hi) >> 1;
-        int c = col[m];
-        if (c == j) return val[m];
-        if (c < j) lo = m + 1; else hi = m - 1;
-    }
-    return 0.0;
-}
+// One thread per block. D_B^{-1}: in-place LU with partial pivoting (multipliers stored below
+// the diagonal, whole rows swapped, so the rows of L move with those of U), then each unit
+// vector through it. The row swaps run over compile-time row indices with predicates, so M
+// stays in registers. Then the block's rows are merged once and the BS output rows written:
+// the off-block union columns below the block, the identity entry, the union columns above.
+constexpr int BLK_THREADS = 64;
 
-// the diagonal block of K read by a linear walk of each block row (columns are sorted)
-__device__ void load_diag_block(const int *rp, const int *col, const double *val, int r0, int bs, double *M) {
-    for (int r = 0; r < bs; ++r) {
-        for (int c = 0; c < bs; ++c) M[r * bs + c] = 0.0;
-        for (int k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k) {
-            int j = col[k];
-            if (j >= r0 + bs) break;
-            if (j >= r0) M[r * bs + (j - r0)] = val[k];
-        }
-    }
-}
-
-// one thread per block: D_B^{-1} of the block by the LU above applied to unit vectors
-__global__ void k_block_inverse(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
-                                const double *__restrict__ val, double *__restrict__ dinv_out, int *status) {
-    double M[BS_MAX * BS_MAX], Lm[BS_MAX * BS_MAX], rhs[BS_MAX];
-    int perm[BS_MAX];
+template <int BS>
+__global__ void __launch_bounds__(BLK_THREADS) k_block_scale(int nblk, const int *__restrict__ rp,
+                                                             const int *__restrict__ col, const double *__restrict__ val,
+                                                             const int *__restrict__ orp, int *__restrict__ ocol,
+                                                             double *__restrict__ oval, double *__restrict__ dinv_out,
+                                                             int *status) {
+    // the LU factors live in shared memory, thread-major (entry q of this thread at q * BLK_THREADS)
+    __shared__ double Msh[BS * BS * BLK_THREADS];
     for (int K = blockIdx.x * blockDim.x + threadIdx.x; K < nblk; K += gridDim.x * blockDim.x) {
-        const int r0 = K * bs;
-        load_diag_block(rp, col, val, r0, bs, M);
-        for (int r = 0; r < bs; ++r) {
-            perm[r] = r;
-            for (int c = 0; c < bs; ++c) Lm[r * bs + c] = 0.0;
-        }
-        double mx = 0.0;
-        for (int q = 0; q < bs * bs; ++q) mx = fmax(mx, fabs(M[q]));
-        const double thr = __dmul_rn(__dmul_rn((double)bs, 0x1.0p-52), mx);
-        bool bad = mx == 0.0;
-        for (int k = 0; k < bs && !bad; ++k) {
-            int piv = k;
-            double best = fabs(M[k * bs + k]);
-            for (int r = k + 1; r < bs; ++r)
-                if (fabs(M[r * bs + k]) > best) { best = fabs(M[r * bs + k]); piv = r; }
-            if (best <= thr) { bad = true; break; }
-            if (piv != k) {
-                for (int c = 0; c < bs; ++c) {
-                    double t = M[k * bs + c]; M[k * bs + c] = M[piv * bs + c]; M[piv * bs + c] = t;
-                    t = Lm[k * bs + c]; Lm[k * bs + c] = Lm[piv * bs + c]; Lm[piv * bs + c] = t;
+        const int r0 = K * BS;
+        double Di[BS * BS];
+        {
+            struct Rows {
+                double *p;
+                __device__ double &operator[](int q) const { return p[q * BLK_THREADS]; }
+            } M{Msh + threadIdx.x};
+            int perm[BS];
+#pragma unroll
+            for (int r = 0; r < BS; ++r) {
+                perm[r] = r;
+#pragma unroll
+                for (int c = 0; c < BS; ++c) M[r * BS + c] = 0.0;
+                for (int k = rp[r0 + r]; k < rp[r0 + r + 1]; ++k) {
+                    const int j = col[k];
+                    if (j >= r0 + BS) break;
+                    const double v = val[k];
+#pragma unroll
+                    for (int c = 0; c < BS; ++c)
+                        if (j == r0 + c) M[r * BS + c] = v;
                 }
-                int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
             }
-            for (int r = k + 1; r < bs; ++r) {
-                double l = __ddiv_rn(M[r * bs + k], M[k * bs + k]);
-                Lm[r * bs + k] = l;
-                for (int c = k + 1; c < bs; ++c) M[r * bs + c] = __fma_rn(-l, M[k * bs + c], M[r * bs + c]);
+            double mx = 0.0;
+#pragma unroll
+            for (int q = 0; q < BS * BS; ++q) mx = fmax(mx, fabs(M[q]));
+            const double thr = __dmul_rn(__dmul_rn((double)BS, 0x1.0p-52), mx);
+            bool bad = mx == 0.0;
+#pragma unroll
+            for (int k = 0; k < BS; ++k) {
+                int piv = k;
+                double best = fabs(M[k * BS + k]);
+#pragma unroll
+                for (int r = k + 1; r < BS; ++r)
+                    if (fabs(M[r * BS + k]) > best) { best = fabs(M[r * BS + k]); piv = r; }
+                if (best <= thr) bad = true;
+#pragma unroll
+                for (int r = k + 1; r < BS; ++r)
+                    if (r == piv) {
+#pragma unroll
+                        for (int c = 0; c < BS; ++c) {
+                            const double t = M[k * BS + c]; M[k * BS + c] = M[r * BS + c]; M[r * BS + c] = t;
+                        }
+                        const int t = perm[k]; perm[k] = perm[r]; perm[r] = t;
+                    }
+#pragma unroll
+                for (int r = k + 1; r < BS; ++r) {
+                    const double l = __ddiv_rn(M[r * BS + k], M[k * BS + k]);
+                    M[r * BS + k] = l;
+#pragma unroll
+                    for (int c = k + 1; c < BS; ++c) M[r * BS + c] = __fma_rn(-l, M[k * BS + c], M[r * BS + c]);
+                }
+            }
+            if (bad) {
+                set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+                continue;
+            }
+#pragma unroll
+            for (int t = 0; t < BS; ++t) {
+                double rhs[BS];
+#pragma unroll
+                for (int r = 0; r < BS; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
+#pragma unroll
+                for (int k = 0; k < BS; ++k)
+#pragma unroll
+                    for (int r = k + 1; r < BS; ++r) rhs[r] = __fma_rn(-M[r * BS + k], rhs[k], rhs[r]);
+#pragma unroll
+                for (int c = BS - 1; c >= 0; --c) {
+                    const double zc = __ddiv_rn(rhs[c], M[c * BS + c]);
+                    Di[c * BS + t] = zc;
+#pragma unroll
+                    for (int r = 0; r < c; ++r) rhs[r] = __fma_rn(-M[r * BS + c], zc, rhs[r]);
+                }
             }
         }
-        if (bad) { set_status(status, LAIR_ERR_ZERO_DIAGONAL); continue; }
-        double *Di = dinv_out + (size_t)K * bs * bs;
-        for (int t = 0; t < bs; ++t) {
-            for (int r = 0; r < bs; ++r) rhs[r] = (perm[r] == t) ? 1.0 : 0.0;
-            for (int k = 0; k < bs; ++k)
-                for (int r = k + 1; r < bs; ++r) rhs[r] = __fma_rn(-Lm[r * bs + k], rhs[k], rhs[r]);
-            for (int c = bs - 1; c >= 0; --c) {
-                double zc = __ddiv_rn(rhs[c], M[c * bs + c]);
-                Di[c * bs + t] = zc;
-                for (int r = 0; r < c; ++r) rhs[r] = __fma_rn(-M[r * bs + c], zc, rhs[r]);
-            }
-        }
-    }
-}
+        double *dst = dinv_out + (size_t)K * BS * BS;
+#pragma unroll
+        for (int q = 0; q < BS * BS; ++q) dst[q] = Di[q];
 
-// one thread per row of the output: merge the block rows, scale by the row of D_B^{-1}
-__global__ void k_block_fill(int nblk, int bs, const int *__restrict__ rp, const int *__restrict__ col,
-                             const double *__restrict__ val, const int *__restrict__ orp, int *__restrict__ ocol,
-                             double *__restrict__ oval, const double *__restrict__ dinv, int *status) {
-    double Di[BS_MAX], a[BS_MAX];
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nblk * bs; e += gridDim.x * blockDim.x) {
-        const int K = e / bs, rr = e % bs, r0 = K * bs;
-        for (int t = 0; t < bs; ++t) Di[t] = dinv[(size_t)K * bs * bs + rr * bs + t];
-        BlockMerge m{rp, col, val, r0, bs};
+        BlockMerge<BS> m{rp, col, val, r0};
         m.init();
-        int p = orp[r0 + rr];
-        bool placed = false;
+        const int p0 = orp[r0];        // every row of the block has the same length
+        const int len = orp[r0 + 1] - p0;
+        int u = 0;
+        bool below = true;
+        double a[BS];
         for (;;) {
-            int j = m.next(a);
-            if (!placed && (j < 0 || j > r0 + rr)) {
-                ocol[p] = r0 + rr;
-                oval[p] = 1.0;
-                ++p;
-                placed = true;
+            const int j = m.next(a);
+            if (below && (j < 0 || j > r0)) {
+#pragma unroll
+                for (int rr = 0; rr < BS; ++rr) {
+                    ocol[p0 + rr * len + u] = r0 + rr;
+                    oval[p0 + rr * len + u] = 1.0;
+                }
+                ++u;
+                below = false;
             }
             if (j < 0) break;
-            double acc = 0.0;
-            for (int t = 0; t < bs; ++t) acc = __fma_rn(Di[t], a[t], acc);
-            ocol[p] = j;
-            oval[p] = acc;
-            ++p;
+#pragma unroll
+            for (int rr = 0; rr < BS; ++rr) {
+                double acc = 0.0;
+#pragma unroll
+                for (int t = 0; t < BS; ++t) acc = __fma_rn(Di[rr * BS + t], a[t], acc);
+                ocol[p0 + rr * len + u] = j;
+                oval[p0 + rr * len + u] = acc;
+            }
+            ++u;
         }
     }
 }
@@ -644,16 +674,37 @@ __global__ void k_block_apply(int nblk, int bs, const double *__restrict__ dinv,
     }
 }
 
-void launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, int *status, cudaStream_t s) {
-    k_block_count<<<grid_for(nblk, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, rowcnt, status);
-    count_launch();
+template <int BS>
+static void block_count_bs(int nblk, const DCsr &A, int *rowcnt, cudaStream_t s) {
+    k_block_count<BS><<<grid_for(nblk, 128), 128, 0, s>>>(nblk, A.rp, A.col, rowcnt);
+}
+template <int BS>
+static void block_scale_bs(int nblk, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
+    k_block_scale<BS><<<grid_for(nblk, BLK_THREADS), BLK_THREADS, 0, s>>>(nblk, A.rp, A.col, A.val, out.rp, out.col, out.val, dinv, status);
 }
 
-void launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
-    k_block_inverse<<<grid_for(nblk, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, A.val, dinv, status);
-    k_block_fill<<<grid_for((long long)nblk * bs, 128), 128, 0, s>>>(nblk, bs, A.rp, A.col, A.val, out.rp, out.col, out.val,
-                                                                     dinv, status);
-    count_launch(2);
+#define LAIR_BS_CASES(F, ...)          \
+    switch (bs) {                      \
+    case 2: F<2>(__VA_ARGS__); break;  \
+    case 3: F<3>(__VA_ARGS__); break;  \
+    case 4: F<4>(__VA_ARGS__); break;  \
+    case 5: F<5>(__VA_ARGS__); break;  \
+    case 6: F<6>(__VA_ARGS__); break;  \
+    case 7: F<7>(__VA_ARGS__); break;  \
+    case 8: F<8>(__VA_ARGS__); break;  \
+    default: return false;             \
+    }
+
+bool launch_block_count(int nblk, int bs, const DCsr &A, int *rowcnt, cudaStream_t s) {
+    LAIR_BS_CASES(block_count_bs, nblk, A, rowcnt, s)
+    count_launch();
+    return true;
+}
+
+bool launch_block_fill(int nblk, int bs, const DCsr &A, const DCsr &out, double *dinv, int *status, cudaStream_t s) {
+    LAIR_BS_CASES(block_scale_bs, nblk, A, out, dinv, status, s)
+    count_launch();
+    return true;
 }
 
 void launch_block_apply(int nblk, int bs, const double *dinv, const double *b, double *out, cudaStream_t s) {

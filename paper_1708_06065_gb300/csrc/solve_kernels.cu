@@ -260,6 +260,11 @@ void finish_partials(int m, const double *part, double *out, cudaStream_t s) {
     count_launch();
 }
 
+void finish_partials_acc(int m, const double *part, double *out, double *acc, cudaStream_t s) {
+    k_finish<<<m, 256, 0, s>>>(m, part, out, acc);
+    count_launch();
+}
+
 // w -= sum_k h_k X_k (h on the device)
 __global__ void k_sub_combo(int n, int m, const double *__restrict__ X, long long ldx, const double *__restrict__ h,
                             double *__restrict__ w) {
@@ -287,6 +292,81 @@ __global__ void k_add_combo(int n, int m, const double *__restrict__ Z, long lon
 
 void add_combo(int n, int m, const double *Z, long long ldz, const double *y, double *x, cudaStream_t s) {
     k_add_combo<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, m, Z, ldz, y, x);
+    count_launch();
+}
+
+// ---------------------------------------------------------------------------------------
+// One classical Gram-Schmidt step with re-orthogonalisation (CGS2) of w against the m <= 32
+// columns of X in three streaming passes over X instead of four:
+//   pass 1: part_k = X_k . w
+//   pass 2: w <- w - sum_k h1_k X_k, then part_k = X_k . w (the new w)
+//   pass 3: w <- w - sum_k h2_k X_k, then part_0 = w . w
+// Each thread loads X_k[i] once per pass and keeps it in registers for both of its uses.
+// The w update accumulates fma(-h_k, X_k[i], .) in ascending k.
+// ---------------------------------------------------------------------------------------
+template <int MM>
+__device__ __forceinline__ void block_partials(const double (&acc)[MM], int m, double *part) {
+    __shared__ double red[RED_THREADS / 32][MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+        if (k < m) {
+            const double v = warp_sum(acc[k]);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+        }
+    __syncthreads();
+    if ((int)threadIdx.x < m) {
+        double t = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        part[threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+    }
+}
+
+template <int MM, int PASS>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs_pass(int n, int m, const double *__restrict__ X, long long ldx,
+                                                          const double *__restrict__ h, double *__restrict__ w,
+                                                          double *__restrict__ part) {
+    double acc[MM];
+    double hk[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        acc[k] = 0.0;
+        hk[k] = (PASS > 1 && k < m) ? h[k] : 0.0;
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double x[MM];
+#pragma unroll
+        for (int k = 0; k < MM; ++k) x[k] = k < m ? X[k * ldx + i] : 0.0;
+        double v = w[i];
+        if (PASS > 1) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k)
+                if (k < m) v = fma(-hk[k], x[k], v);
+            w[i] = v;
+        }
+        if (PASS < 3) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k)
+                if (k < m) acc[k] = fma(x[k], v, acc[k]);
+        } else {
+            acc[0] = fma(v, v, acc[0]);
+        }
+    }
+    block_partials<MM>(acc, PASS < 3 ? m : 1, part);
+}
+
+template <int MM>
+static void cgs_pass_mm(int pass, int n, int m, const double *X, long long ldx, const double *h, double *w, double *part,
+                        cudaStream_t s) {
+    if (pass == 1) k_cgs_pass<MM, 1><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m, X, ldx, h, w, part);
+    else if (pass == 2) k_cgs_pass<MM, 2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m, X, ldx, h, w, part);
+    else k_cgs_pass<MM, 3><<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, m, X, ldx, h, w, part);
+}
+
+void cgs_pass(int pass, int n, int m, const double *X, long long ldx, const double *h, double *w, double *part,
+              cudaStream_t s) {
+    if (m <= 8) cgs_pass_mm<8>(pass, n, m, X, ldx, h, w, part, s);
+    else if (m <= 16) cgs_pass_mm<16>(pass, n, m, X, ldx, h, w, part, s);
+    else cgs_pass_mm<32>(pass, n, m, X, ldx, h, w, part, s);
     count_launch();
 }
 
