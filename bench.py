@@ -355,7 +355,7 @@ def main():
 
     # ---- roofline of the dominant timed kernel (largest accumulated time)
     peak, peak_src = load_peaks()
-    kern = [(v[1], k, v) for k, v in timers.items() if k != "vcycle" and v[0] > 0]
+    kern = [(v[1], k, v) for k, v in timers.items() if k != "vcycle" and not k.startswith("setup_") and v[0] > 0]
     roof = None
     if kern:
         _, name, (cnt, ms, byt) = max(kern)
@@ -367,7 +367,7 @@ def main():
                 "launches": cnt, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
                 "all_timed": {k: {"launches": v[0], "avg_us": 1e3 * v[1] / max(v[0], 1),
                                   "GBps": (v[2] / (v[1] / max(v[0], 1) * 1e-3) / 1e9) if v[2] and v[1] else None}
-                              for k, v in timers.items()}}
+                              for k, v in timers.items() if not k.startswith("setup_")}}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -388,6 +388,7 @@ def main():
         "fp64": {"value": dist.world * n / (ms64 / 1e3), "ms_per_step": ms64, "setup_ms": dist.max(sum(su64) / len(su64)),
                  "iters": it64, "final_rel": max(rel64)},
         "mixed_over_fp64": ms64 / ms_mixed,
+        "setup_phases_ms": {k[len("setup_"):]: v[1] / args.steps for k, v in timers.items() if k.startswith("setup_")},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -80,6 +81,12 @@ struct lair_handle {
     void *scan_tmp = nullptr;
     size_t scan_tmp_bytes = 0;
     std::vector<void *> allocs;   // everything owned by the handle
+    // bump arenas over large device chunks (owned through allocs): set-up temporaries (stack
+    // discipline, see Temps) and small long-lived arrays; each allocation is 256-byte aligned
+    struct Chunk { char *p; size_t size; size_t used; };
+    std::vector<Chunk> tmp_chunks;
+    int tmp_cur = -1, tmp_depth = 0;
+    Chunk keep_chunk{nullptr, 0, 0};
     // outer-iteration work (FP64)
     double *wb = nullptr, *wx = nullptr, *wr = nullptr, *part = nullptr, *dsc = nullptr;
     double *V = nullptr, *Z = nullptr;
@@ -88,7 +95,8 @@ struct lair_handle {
     long long launches = 0;
     // kernel timing (options.timing)
     struct Timer { std::string name; long long launches = 0; double ms = 0.0; double bytes = 0.0; };
-    struct Pending { int slot; cudaEvent_t a, b; };
+    struct Pending { int slot; cudaEvent_t a, b; bool closed; int id; };
+    int next_timer_id = 0;
     std::vector<Timer> timers;
     std::vector<Pending> pending;        // events recorded by direct launches, read at the next sync
     std::vector<Pending> graph_events;   // events inside the captured cycle graph
@@ -134,13 +142,101 @@ static lair_status fail(lair_handle *h, lair_status st, const char *fmt, ...) {
         if (st_ != LAIR_OK) return st_;    \
     } while (0)
 
+constexpr size_t ARENA_ALIGN = 256;
+constexpr size_t KEEP_CHUNK = (size_t)32 << 20;      // long-lived arrays up to KEEP_CHUNK / 8 share chunks
+constexpr size_t TMP_CHUNK_MIN = (size_t)64 << 20;
+
+static size_t arena_round(size_t bytes) { return (bytes + ARENA_ALIGN - 1) & ~(ARENA_ALIGN - 1); }
+
+// The library's own stream-ordered pool per device: memory freed by one handle stays reserved
+// (up to POOL_KEEP bytes) for the next one instead of going back to the driver at every
+// synchronisation, and the device's default pool is left as the caller configured it.
+constexpr unsigned long long POOL_KEEP = 16ull << 30;
+constexpr int POOL_DEVICES = 64;
+
+static cudaError_t lair_pool(cudaMemPool_t *out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[POOL_DEVICES] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= POOL_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = POOL_KEEP;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+// pinned host scratch of HOST_BLOCK bytes per handle, recycled between handles
+constexpr size_t HOST_BLOCK = 1024;
+static std::mutex g_host_mu;
+static std::vector<void *> g_host_free;
+
+static cudaError_t host_block_get(void **p) {
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        if (!g_host_free.empty()) {
+            *p = g_host_free.back();
+            g_host_free.pop_back();
+            return cudaSuccess;
+        }
+    }
+    return cudaMallocHost(p, HOST_BLOCK);
+}
+
+static void host_block_put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    g_host_free.push_back(p);
+}
+
+static lair_status raw_alloc(lair_handle *h, void **p, size_t bytes) {
+    cudaMemPool_t pool;
+    cudaError_t e = lair_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, h->s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LAIR_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+    }
+    return LAIR_OK;
+}
+
+// keep = true: owned by the handle until lair_free (small arrays share chunks);
+// keep = false: plain stream-ordered allocation, released with dfree
 template <class T>
 static lair_status dalloc(lair_handle *h, T **p, size_t n, bool keep = true) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMallocAsync((void **)p, n * sizeof(T), h->s);
-    if (e != cudaSuccess) return fail(h, LAIR_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
-    if (keep) h->allocs.push_back(*p);
+    const size_t bytes = arena_round(n * sizeof(T));
+    void *q = nullptr;
+    if (keep && bytes <= KEEP_CHUNK / 8) {
+        auto &c = h->keep_chunk;
+        if (!c.p || c.used + bytes > c.size) {
+            void *np = nullptr;
+            TRY(raw_alloc(h, &np, KEEP_CHUNK));
+            h->allocs.push_back(np);
+            c = lair_handle::Chunk{static_cast<char *>(np), KEEP_CHUNK, 0};
+        }
+        q = c.p + c.used;
+        c.used += bytes;
+    } else {
+        TRY(raw_alloc(h, &q, bytes));
+        if (keep) h->allocs.push_back(q);
+    }
+    *p = static_cast<T *>(q);
     return LAIR_OK;
 }
 
@@ -148,18 +244,58 @@ static void dfree(lair_handle *h, void *p) {
     if (p) cudaFreeAsync(p, h->s);
 }
 
-// temporaries of one set-up step
+// Set-up temporaries. The innermost live Temps bumps through the handle's temporary chunks and
+// gives everything back at once when it goes out of scope; memory is reused only by work issued
+// later on the same stream. A Temps that is not the innermost one allocates plainly instead.
 struct Temps {
     lair_handle *h;
-    std::vector<void *> ptrs;
-    explicit Temps(lair_handle *hh) : h(hh) {}
+    int depth, mark_cur;
+    size_t mark_used;
+    std::vector<void *> raw;
+    explicit Temps(lair_handle *hh) : h(hh) {
+        depth = ++h->tmp_depth;
+        mark_cur = h->tmp_cur;
+        mark_used = h->tmp_cur >= 0 ? h->tmp_chunks[h->tmp_cur].used : 0;
+    }
     template <class T> lair_status get(T **p, size_t n) {
-        TRY(dalloc(h, p, n, false));
-        ptrs.push_back(*p);
+        if (n == 0) n = 1;
+        const size_t bytes = arena_round(n * sizeof(T));
+        if (depth != h->tmp_depth) {
+            void *q = nullptr;
+            TRY(raw_alloc(h, &q, bytes));
+            raw.push_back(q);
+            *p = static_cast<T *>(q);
+            return LAIR_OK;
+        }
+        auto &ch = h->tmp_chunks;
+        if (h->tmp_cur < 0 || ch[h->tmp_cur].used + bytes > ch[h->tmp_cur].size) {
+            // the next chunk if it is large enough, else a new one in its place
+            const int nx = h->tmp_cur + 1;
+            if (nx < (int)ch.size() && ch[nx].size >= bytes) {
+                ch[nx].used = 0;
+            } else {
+                size_t sz = TMP_CHUNK_MIN;
+                if (!ch.empty() && 2 * ch.back().size > sz) sz = 2 * ch.back().size;
+                if (bytes > sz) sz = bytes;
+                void *np = nullptr;
+                TRY(raw_alloc(h, &np, sz));
+                h->allocs.push_back(np);
+                ch.insert(ch.begin() + nx, lair_handle::Chunk{static_cast<char *>(np), sz, 0});
+            }
+            h->tmp_cur = nx;
+        }
+        auto &c = ch[h->tmp_cur];
+        *p = reinterpret_cast<T *>(c.p + c.used);
+        c.used += bytes;
         return LAIR_OK;
     }
     ~Temps() {
-        for (void *p : ptrs) dfree(h, p);
+        for (void *q : raw) dfree(h, q);
+        if (depth == h->tmp_depth) {
+            h->tmp_cur = mark_cur;
+            if (mark_cur >= 0) h->tmp_chunks[mark_cur].used = mark_used;
+        }
+        --h->tmp_depth;
     }
 };
 
@@ -175,6 +311,12 @@ static lair_status sync_status(lair_handle *h) {
         return fail(h, (lair_status)st, "device reported %s", lair_status_string((lair_status)st));
     }
     return LAIR_OK;
+}
+
+// read n device ints into pageable host memory (any n)
+static lair_status read_ints_big(lair_handle *h, const int *d, int n, int *out) {
+    CU(cudaMemcpyAsync(out, d, sizeof(int) * n, cudaMemcpyDeviceToHost, h->s));
+    return sync_status(h);
 }
 
 static lair_status read_ints(lair_handle *h, const int *d, int n, int *out) {
@@ -213,26 +355,37 @@ static cudaEvent_t get_event(lair_handle *h) {
 static int tbegin(lair_handle *h, const std::string &name, double bytes, bool in_graph = false) {
     if (!h->o.timing) return -1;
     int slot = timer_slot(h, name, bytes);
-    lair_handle::Pending p{slot, get_event(h), get_event(h)};
+    lair_handle::Pending p{slot, get_event(h), get_event(h), false, h->next_timer_id++};
     // inside stream capture only an external record becomes an event node of the graph
     if (in_graph) cudaEventRecordWithFlags(p.a, h->s, cudaEventRecordExternal);
     else cudaEventRecord(p.a, h->s);
     auto &v = in_graph ? h->graph_events : h->pending;
     v.push_back(p);
-    return (int)v.size() - 1;
+    return p.id;
 }
 
-static void tend(lair_handle *h, int pair, bool in_graph = false) {
-    if (pair < 0) return;
+static void tend(lair_handle *h, int id, bool in_graph = false) {
+    if (id < 0) return;
     auto &v = in_graph ? h->graph_events : h->pending;
-    if (in_graph) cudaEventRecordWithFlags(v[pair].b, h->s, cudaEventRecordExternal);
-    else cudaEventRecord(v[pair].b, h->s);
+    for (size_t q = v.size(); q-- > 0;) {
+        if (v[q].id != id) continue;
+        if (in_graph) cudaEventRecordWithFlags(v[q].b, h->s, cudaEventRecordExternal);
+        else cudaEventRecord(v[q].b, h->s);
+        v[q].closed = true;
+        return;
+    }
 }
 
 // call only after the stream has been synchronised
 static void flush_timers(lair_handle *h) {
     if (!h->o.timing) return;
+    // pairs still open (a region spanning this synchronisation) stay pending
+    std::vector<lair_handle::Pending> open;
     for (auto &p : h->pending) {
+        if (!p.closed) {
+            open.push_back(p);
+            continue;
+        }
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             h->timers[p.slot].ms += ms;
@@ -241,7 +394,7 @@ static void flush_timers(lair_handle *h) {
         h->ev_pool.push_back(p.a);
         h->ev_pool.push_back(p.b);
     }
-    h->pending.clear();
+    h->pending.swap(open);
     if (h->graph_pending) {
         for (auto &p : h->graph_events) {
             float ms = 0.f;
@@ -291,7 +444,9 @@ static lair_status build_strength_graph(lair_handle *h, Temps &t, const DCsr &A,
     launch_strength(A, theta, h->o.strength_abs, mask, cnt, h->s);
     G.n = A.nr;
     TRY(t.get(&G.rp, (size_t)A.nr + 1));
-    TRY(scan(h, cnt, G.rp, A.nr, &G.nnz));
+    // S is a subset of the pattern of A, so A's entry count bounds it and no read-back is needed
+    TRY(scan(h, cnt, G.rp, A.nr, nullptr));
+    G.nnz = A.nnz;
     TRY(t.get(&G.col, (size_t)G.nnz));
     launch_graph_fill(A, mask, G, h->s);
     return LAIR_OK;
@@ -336,8 +491,17 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
     TRY(new_counts(h, t, &cnt, nc));
     launch_nb_fill(nc, cpts, G, cf, distance, off, tmp, cnt, h->s);
     TRY(t.get(&nb_rp, (size_t)nc + 1));
-    int nnb = 0;
-    TRY(scan(h, cnt, nb_rp, nc, &nnb));
+    TRY(scan(h, cnt, nb_rp, nc, nullptr));
+    // size bins of the local systems; one read-back for the bins and the neighbourhood total
+    int *lists, *bcounts, *smax;
+    TRY(t.get(&lists, (size_t)3 * nc + 1));
+    TRY(new_counts(h, t, &bcounts, 5));
+    smax = bcounts + 3;
+    launch_local_bin(nc, nb_rp, lists, bcounts, smax, h->s);
+    CU(cudaMemcpyAsync(bcounts + 4, nb_rp + nc, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
+    int hc[5];
+    TRY(read_ints(h, bcounts, 5, hc));
+    const int nnb = hc[4];
     TRY(t.get(&nb_col, (size_t)nnb));
     launch_nb_compact(nc, off, tmp, nb_rp, nb_col, h->s);
 
@@ -363,13 +527,6 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
         TRY(t.get(&ocol, (size_t)nout));
         TRY(t.get(&oval, (size_t)nout));
     }
-    int *lists, *bcounts, *smax;
-    TRY(t.get(&lists, (size_t)3 * nc + 1));
-    TRY(new_counts(h, t, &bcounts, 4));
-    smax = bcounts + 3;
-    launch_local_bin(nc, nb_rp, lists, bcounts, smax, h->s);
-    int hc[4];
-    TRY(read_ints(h, bcounts, 4, hc));
     void *scratch = nullptr;
     if (hc[2] > 0) {
         unsigned char *sp;
@@ -421,7 +578,13 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     Z.nr = nr;
     Z.nc = Y.nc;
     if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
-    TRY(scan(h, cnt, Z.rp, nr, &Z.nnz));
+    // a kept product is stored at its exact size; a temporary one at the bound (its entry count
+    // is then only a capacity and is not read back)
+    if (keep) TRY(scan(h, cnt, Z.rp, nr, &Z.nnz));
+    else {
+        TRY(scan(h, cnt, Z.rp, nr, nullptr));
+        Z.nnz = total;
+    }
     if (keep) {
         TRY(dalloc(h, &Z.col, (size_t)Z.nnz));
         TRY(dalloc(h, &Z.val, (size_t)Z.nnz));
@@ -444,6 +607,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     const int n = A.nr;
     const bool fp32 = o.precision == LAIR_MIXED;
 
+    int tp = tbegin(h, "setup_strength", 0.0);
     TRY(dalloc(h, &L.strong, (size_t)A.nnz));
     Graph S, ST, Scf, STcf;
     TRY(build_strength_graph(h, t, A, o.theta, L.strong, S));
@@ -463,6 +627,8 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     }
 
     // ---- C/F splitting
+    tend(h, tp);
+    tp = tbegin(h, "setup_split", 0.0);
     TRY(dalloc(h, &L.cf, (size_t)n));
     if (cf_user) {
         CU(cudaMemcpyAsync(L.cf, cf_user, (size_t)n, cudaMemcpyHostToDevice, h->s));
@@ -517,6 +683,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     TRY(scan(h, flag, scanv, n, &nc));
     L.nc = nc;
     if (nc == 0 || nc == n) {
+        tend(h, tp);
         *last = true;
         return LAIR_OK;
     }
@@ -541,6 +708,8 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     }
 
     // ---- restriction (lAIR): local systems of A on the neighbourhoods in S
+    tend(h, tp);
+    tp = tbegin(h, "setup_R", 0.0);
     TRY(dalloc(h, &L.lsR, (size_t)nc));
     L.R.nr = nc;
     L.R.nc = n;
@@ -548,6 +717,8 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
                    fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true));
 
     // ---- interpolation
+    tend(h, tp);
+    tp = tbegin(h, "setup_P", 0.0);
     L.P.nr = n;
     L.P.nc = nc;
     if (o.interp == LAIR_P_ONEPOINT) {
@@ -556,10 +727,13 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         TRY(new_counts(h, t, &cnt, n));
         launch_onepoint(0, A, L.strong, L.cf, L.cidx, o.strength_abs, choice, cnt, nullptr, h->s);
         TRY(dalloc(h, &L.P.rp, (size_t)n + 1));
-        TRY(scan(h, cnt, L.P.rp, n, &L.P.nnz));
-        TRY(dalloc(h, &L.P.col, (size_t)L.P.nnz));
-        TRY(dalloc(h, &L.P.val, (size_t)L.P.nnz));
-        if (fp32) TRY(dalloc(h, &L.P.val32, (size_t)L.P.nnz));
+        // at most one entry per row: stored with room for n, exact count read back with the
+        // other hierarchy totals once the hierarchy is built
+        TRY(scan(h, cnt, L.P.rp, n, nullptr));
+        L.P.nnz = n;
+        TRY(dalloc(h, &L.P.col, (size_t)n));
+        TRY(dalloc(h, &L.P.val, (size_t)n));
+        if (fp32) TRY(dalloc(h, &L.P.val32, (size_t)n));
         launch_onepoint(1, A, L.strong, L.cf, L.cidx, o.strength_abs, choice, cnt, &L.P, h->s);
     } else {
         // approximate ideal interpolation = lAIR applied to A^T on the transposed graph, transposed back
@@ -581,6 +755,8 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     }
 
     // ---- Galerkin product and lumping
+    tend(h, tp);
+    tp = tbegin(h, "setup_RAP", 0.0);
     DCsr RA, K;
     TRY(spgemm(h, t, L.R, A, RA, false));
     const bool lump = o.lump_tol > 0.0;
@@ -610,11 +786,14 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         CU(cudaStreamSynchronize(h->s));   // the host vector is copied from pageable memory
     }
     H.lev.push_back(next);
+    tend(h, tp);
     *last = false;
     return LAIR_OK;
 }
 
-// build sliced-ELL views; all totals are read back with one synchronisation
+// build sliced-ELL views, all of them with a handful of launches and one synchronisation:
+// views are grouped by element type (FP32, FP64); each group gets one slice-offset scan and
+// one column and one value array, which its views index with group-wide offsets
 struct SellPlan {
     SellView *v;
     const DCsr *M;
@@ -622,50 +801,122 @@ struct SellPlan {
     int nrows;
     const double *dinv;   // NULL: no diagonal
     bool fp32;
-    int *cnt = nullptr;
 };
 
 static lair_status build_sells(lair_handle *h, std::vector<SellPlan> &plans) {
     Temps t(h);
-    for (auto &p : plans) {
-        SellView &v = *p.v;
-        v.nrows = p.nrows;
-        if (p.nrows <= 0) continue;
-        const int nsl = (p.nrows + 31) / 32;
-        TRY(dalloc(h, &v.row, (size_t)p.nrows));
-        TRY(new_counts(h, t, &p.cnt, nsl));
-        launch_sell_prepare(p.nrows, p.rows_in, p.M->rp, v.row, p.cnt, h->s);
-        TRY(dalloc(h, &v.slice_ptr, (size_t)nsl + 1));
-        TRY(scan(h, p.cnt, v.slice_ptr, nsl, nullptr));
-    }
-    int k = 0;
-    for (auto &p : plans) {
-        if (p.nrows <= 0) continue;
-        const int nsl = (p.nrows + 31) / 32;
-        CU(cudaMemcpyAsync(h->h_int + 8 + k, p.v->slice_ptr + nsl, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-        ++k;
-    }
-    TRY(sync_status(h));
-    k = 0;
-    for (auto &p : plans) {
-        if (p.nrows <= 0) continue;
-        const int total = h->h_int[8 + k++];
-        const size_t el = p.fp32 ? sizeof(float) : sizeof(double);
-        unsigned char *vv;
-        TRY(dalloc(h, &p.v->col, (size_t)total));
-        TRY(dalloc(h, &vv, el * (size_t)total));
-        p.v->val = vv;
-        if (p.dinv) {
-            unsigned char *dd;
-            TRY(dalloc(h, &dd, el * (size_t)p.nrows));
-            p.v->dinv = dd;
+    std::vector<SellDesc> hd;
+    std::vector<SellPlan *> hp;
+    int win = 0, lin = 0, sl = 0;
+    int gp[3] = {0, 0, 0}, glin[3] = {0, 0, 0}, gsl0[2] = {0, 0}, gsl1[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+        gp[g] = (int)hd.size();
+        glin[g] = lin;
+        gsl0[g] = sl;
+        for (auto &p : plans) {
+            if (p.nrows <= 0 || (p.fp32 ? 0 : 1) != g) continue;
+            SellView &v = *p.v;
+            v.nrows = p.nrows;
+            TRY(dalloc(h, &v.row, (size_t)p.nrows));
+            const int nsl = (p.nrows + 31) / 32;
+            SellDesc d{};
+            d.rows_in = p.rows_in;
+            d.rp = p.M->rp;
+            d.col = p.M->col;
+            d.val = p.M->val;
+            d.dinv = p.dinv;
+            d.row_out = v.row;
+            d.nrows = p.nrows;
+            d.win0 = win;
+            d.lin0 = lin;
+            d.sl0 = sl;
+            d.group = g;
+            hd.push_back(d);
+            hp.push_back(&p);
+            win += (p.nrows + 255) / 256;
+            lin += nsl;
+            sl += nsl;
         }
-        launch_sell_fill(*p.v, *p.M, p.dinv, p.fp32, h->s);
+        gsl1[g] = sl;
+        sl += 1;   // the group's end offset
     }
+    gp[2] = (int)hd.size();
+    glin[2] = lin;
+    const int nd = (int)hd.size();
+    if (nd == 0) return LAIR_OK;
+    for (auto &p : plans)
+        if (p.nrows <= 0) p.v->nrows = 0;
+
+    SellDesc *dd;
+    int *cnt, *sp, *tot;
+    unsigned long long *gsum;
+    TRY(t.get(&dd, (size_t)nd));
+    TRY(new_counts(h, t, &cnt, sl));
+    TRY(t.get(&gsum, 2));
+    TRY(t.get(&tot, 6));
+    TRY(dalloc(h, &sp, (size_t)sl + 1));
+    CU(cudaMemsetAsync(gsum, 0, 2 * sizeof(unsigned long long), h->s));
+    CU(cudaMemcpyAsync(dd, hd.data(), sizeof(SellDesc) * nd, cudaMemcpyHostToDevice, h->s));
+    launch_sell_prepare_multi(dd, nd, win, lin, cnt, gsum, h->s);
+    for (int g = 0; g < 2; ++g) {
+        if (gsl1[g] > gsl0[g]) TRY(scan(h, cnt + gsl0[g], sp + gsl0[g], gsl1[g] - gsl0[g], nullptr));
+        CU(cudaMemcpyAsync(tot + g, sp + gsl1[g], sizeof(int), cudaMemcpyDeviceToDevice, h->s));
+    }
+    CU(cudaMemcpyAsync(tot + 2, gsum, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->s));
+    int ht[6];
+    TRY(read_ints(h, tot, 6, ht));
+    unsigned long long hs[2];
+    memcpy(hs, ht + 2, sizeof hs);
+    for (int g = 0; g < 2; ++g) {
+        if (gp[g + 1] == gp[g]) continue;
+        if (hs[g] > 0x7fffffffull)
+            return fail(h, LAIR_ERR_UNSUPPORTED, "sliced-ELL copies of %llu entries exceed 32-bit offsets", hs[g]);
+        const size_t el = g == 0 ? sizeof(float) : sizeof(double);
+        int *gcol;
+        unsigned char *gval, *gdinv = nullptr;
+        TRY(dalloc(h, &gcol, (size_t)ht[g]));
+        TRY(dalloc(h, &gval, el * (size_t)ht[g]));
+        size_t drows = 0;
+        for (int q = gp[g]; q < gp[g + 1]; ++q)
+            if (hd[q].dinv) drows += (size_t)hd[q].nrows;
+        if (drows) TRY(dalloc(h, &gdinv, el * drows));
+        size_t doff = 0;
+        for (int q = gp[g]; q < gp[g + 1]; ++q) {
+            SellDesc &d = hd[q];
+            SellView &v = *hp[q]->v;
+            d.slice_ptr = sp + d.sl0;
+            d.scol = gcol;
+            d.sval = gval;
+            d.sdinv = d.dinv ? gdinv + el * doff : nullptr;
+            if (d.dinv) doff += (size_t)d.nrows;
+            v.slice_ptr = sp + d.sl0;
+            v.col = gcol;
+            v.val = gval;
+            v.dinv = d.sdinv;
+        }
+    }
+    CU(cudaMemcpyAsync(dd, hd.data(), sizeof(SellDesc) * nd, cudaMemcpyHostToDevice, h->s));
+    // (a copy from pageable memory is staged before cudaMemcpyAsync returns, so hd may go)
+    for (int g = 0; g < 2; ++g) launch_sell_fill_multi(dd, gp[g], gp[g + 1], glin[g], glin[g + 1], g == 0, h->s);
     return LAIR_OK;
 }
 
+// the sliced-ELL views of level l (built for all levels at once when the hierarchy is complete)
+static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan> &plans) {
+    Level &L = H.lev[l];
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    if (!L.coarsest) {
+        const int n = L.A.nr, nc = L.nc;
+        plans.push_back(SellPlan{&L.AF, &L.A, L.frows, n - nc, L.dinv, fp32});
+        plans.push_back(SellPlan{&L.AC, &L.A, L.crows, nc, L.dinv, fp32});
+        plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
+        plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
+    }
+    if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
+}
+
 static lair_status finish_level(lair_handle *h, Hier &H, int l) {
+    const int tp = tbegin(h, "setup_finish", 0.0);
     Level &L = H.lev[l];
     const int n = L.A.nr;
     const bool fp32 = h->o.precision == LAIR_MIXED;
@@ -683,18 +934,6 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
         CU(cudaStreamSynchronize(h->s));
         L.nF = (long long)hs[0]; L.nnzF = (long long)hs[1]; L.nC = (long long)hs[2]; L.nnzC = (long long)hs[3];
     }
-    if (!L.coarsest || l == 0) {
-        std::vector<SellPlan> plans;
-        if (!L.coarsest) {
-            const int n = L.A.nr, nc = L.nc;
-            plans.push_back(SellPlan{&L.AF, &L.A, L.frows, n - nc, L.dinv, fp32});
-            plans.push_back(SellPlan{&L.AC, &L.A, L.crows, nc, L.dinv, fp32});
-            plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
-            plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
-        }
-        if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
-        TRY(build_sells(h, plans));
-    }
     if (fp32) {
         TRY(dalloc(h, &L.A.val32, (size_t)L.A.nnz));
         launch_to_f32(L.A.nnz, L.A.val, L.A.val32, h->s);
@@ -706,6 +945,7 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
         TRY(dalloc(h, &L.x64[0], (size_t)n));
         TRY(dalloc(h, &L.x64[1], (size_t)n));
     }
+    tend(h, tp);
     return LAIR_OK;
 }
 
@@ -792,6 +1032,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
     const lair_options &o = h->o;
     H.lev.clear();
     Level L0;
+    int tp = tbegin(h, "setup_level0", 0.0);
     {
         Temps t(h);
         DCsr A = A0;
@@ -838,6 +1079,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         CU(cudaStreamSynchronize(h->s));
     }
     H.lev.push_back(L0);
+    tend(h, tp);
     for (int l = 0;; ++l) {
         const int n = H.lev[l].A.nr;
         bool last = n <= o.coarse_max || l + 1 >= o.max_levels;
@@ -848,6 +1090,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             Level &L = H.lev[l];
             if (n > 4096)
                 return fail(h, LAIR_ERR_COARSENING_STALLED, "coarsening stopped at level %d with %d unknowns", l, n);
+            tp = tbegin(h, "setup_coarsest", 0.0);
             Temps t(h);
             double *D;
             int *perm;
@@ -855,27 +1098,45 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             TRY(t.get(&perm, (size_t)n));
             TRY(dalloc(h, &L.Ainv, (size_t)n * n));
             launch_dense_setup(L.A, D, perm, L.Ainv, h->status, h->s);
+            tend(h, tp);
             TRY(sync_status(h));
             break;
         }
     }
     {
-        // least-squares rows of all levels, counted with one read-back
+        // least-squares rows of all levels and the exact entry counts of the one-point P,
+        // with one read-back
         Temps t(h);
+        const int nl = (int)H.lev.size();
         int *c2;
-        TRY(new_counts(h, t, &c2, 2));
-        for (auto &L : H.lev) {
+        TRY(new_counts(h, t, &c2, 2 + nl));
+        for (int l = 0; l < nl; ++l) {
+            Level &L = H.lev[l];
             if (L.coarsest) continue;
             if (L.lsR) count_flags(L.nc, L.lsR, c2, h->s);
             if (L.lsP) count_flags(L.nc, L.lsP, c2 + 1, h->s);
+            if (o.interp == LAIR_P_ONEPOINT && L.P.rp)
+                CU(cudaMemcpyAsync(c2 + 2 + l, L.P.rp + L.P.nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
         }
-        int hc[2];
-        TRY(read_ints(h, c2, 2, hc));
+        std::vector<int> hc(2 + nl);
+        TRY(read_ints_big(h, c2, 2 + nl, hc.data()));
         H.singular_R = hc[0];
         H.singular_P = hc[1];
+        for (int l = 0; l < nl; ++l)
+            if (o.interp == LAIR_P_ONEPOINT && H.lev[l].P.rp && !H.lev[l].coarsest) H.lev[l].P.nnz = hc[2 + l];
     }
+    {
+        int tv = tbegin(h, "setup_views", 0.0);
+        std::vector<SellPlan> plans;
+        for (int l = 0; l < (int)H.lev.size(); ++l) add_view_plans(h, H, l, plans);
+        TRY(build_sells(h, plans));
+        tend(h, tv);
+    }
+    tp = tbegin(h, "setup_graph", 0.0);
     TRY(capture_cycle(h, H));
+    tend(h, tp);
     CU(cudaStreamSynchronize(h->s));
+    flush_timers(h);
     H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return LAIR_OK;
 }
@@ -1351,6 +1612,15 @@ void normalize_cf(int n, int8_t *cf, cudaStream_t s) {
     count_launch();
 }
 
+// h_int: 64 ints, h_dbl: 64 doubles, in one recycled pinned block
+static lair_status host_scratch(lair_handle *h) {
+    void *blk = nullptr;
+    CU(host_block_get(&blk));
+    h->h_int = static_cast<int *>(blk);
+    h->h_dbl = reinterpret_cast<double *>(static_cast<char *>(blk) + 512);
+    return LAIR_OK;
+}
+
 static lair_status load_matrix(lair_handle *h, const lair_csr *A) {
     if (A->n <= 0 || A->nnz < A->n || A->n > 0x7fffffff || A->nnz > 0x7fffffff)
         return fail(h, LAIR_ERR_INVALID_ARG, "matrix sizes n=%lld nnz=%lld out of range", (long long)A->n,
@@ -1491,8 +1761,7 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **o
         CU(cudaStreamCreate(&h->own));
         h->s = h->own;
     }
-    CU(cudaMallocHost(&h->h_int, 64 * sizeof(int)));
-    CU(cudaMallocHost(&h->h_dbl, 64 * sizeof(double)));
+    TRY(host_scratch(h));
     TRY(dalloc(h, &h->status, 1));
     CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
     TRY(load_matrix(h, A));
@@ -1527,8 +1796,7 @@ lair_status lair_setup_batched(const lair_csr *A, int nsys, const int64_t *sys_o
         CU(cudaStreamCreate(&h->own));
         h->s = h->own;
     }
-    CU(cudaMallocHost(&h->h_int, 64 * sizeof(int)));
-    CU(cudaMallocHost(&h->h_dbl, 64 * sizeof(double)));
+    TRY(host_scratch(h));
     CU(cudaMallocHost(&h->h_seg, sizeof(double) * nsys));
     CU(cudaMallocHost(&h->h_act, nsys));
     TRY(dalloc(h, &h->status, 1));
@@ -1735,8 +2003,7 @@ void lair_free(lair_handle *h) {
     if (h->h_batcnt) cudaFreeHost(h->h_batcnt);
     if (h->h_seg) cudaFreeHost(h->h_seg);
     if (h->h_act) cudaFreeHost(h->h_act);
-    if (h->h_int) cudaFreeHost(h->h_int);
-    if (h->h_dbl) cudaFreeHost(h->h_dbl);
+    host_block_put(h->h_int);   // h_dbl lives in the same block
     cudaGetLastError();
     delete h;
 }

@@ -32,7 +32,7 @@ struct DCsr {
 };
 
 struct Graph {          // pattern-only CSR
-    int n = 0, nnz = 0;
+    int n = 0, nnz = 0;     // nnz: capacity of col (at least rp[n])
     int *rp = nullptr;
     int *col = nullptr;
 };

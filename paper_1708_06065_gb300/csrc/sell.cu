@@ -19,66 +19,97 @@ __global__ void k_frows(int n, const int8_t *__restrict__ cf, const int *__restr
         if (cf[i] != CF_C) frows[i - cscan[i]] = i;
 }
 
+// ---------------------------------------------------------------------------------------
+// Building many views at once. Views are described by SellDesc entries; view p owns windows
+// [win0, win0 + its windows), linear slices [lin0, lin0 + its slices) and, in the slice-length
+// array cnt, positions [sl0, sl0 + its slices). Every kernel finds the view of its window or
+// slice by binary search over the descriptors.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_desc(const SellDesc *__restrict__ d, int nd, int key, int which) {
+    int lo = 0, hi = nd - 1;     // last descriptor whose start <= key
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int st = which == 0 ? d[mid].win0 : d[mid].lin0;
+        if (st <= key) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // one CTA per window: order the window's rows by decreasing length (stable)
-__global__ void __launch_bounds__(SELL_WINDOW) k_sell_sort(int nrows, const int *__restrict__ rows_in,
-                                                          const int *__restrict__ rp, int *__restrict__ rows_out) {
+__global__ void __launch_bounds__(SELL_WINDOW) k_sell_sort_multi(const SellDesc *__restrict__ d, int nd) {
     __shared__ int len[SELL_WINDOW];
     __shared__ int rid[SELL_WINDOW];
-    const int w0 = blockIdx.x * SELL_WINDOW;
+    const int p = find_desc(d, nd, blockIdx.x, 0);
+    const SellDesc v = d[p];
+    const int w0 = (blockIdx.x - v.win0) * SELL_WINDOW;
     const int t = threadIdx.x;
-    const int cnt = min(SELL_WINDOW, nrows - w0);
+    const int cnt = min(SELL_WINDOW, v.nrows - w0);
     if (t < cnt) {
-        const int i = rows_in ? rows_in[w0 + t] : w0 + t;
+        const int i = v.rows_in ? v.rows_in[w0 + t] : w0 + t;
         rid[t] = i;
-        len[t] = rp[i + 1] - rp[i];
+        len[t] = v.rp[i + 1] - v.rp[i];
     }
     __syncthreads();
     if (t < cnt) {
         const int lt = len[t];
         int r = 0;
         for (int u = 0; u < cnt; ++u) r += (len[u] > lt) || (len[u] == lt && u < t);
-        rows_out[w0 + r] = rid[t];
+        v.row_out[w0 + r] = rid[t];
     }
 }
 
-// slice lengths (in entries: 32 x longest row of the slice); cnt has nslices + 1 entries
-__global__ void k_sell_len(int nrows, const int *__restrict__ rows, const int *__restrict__ rp, int *__restrict__ cnt) {
+// slice lengths in entries (32 x longest row of the slice), one warp per slice; also their
+// 64-bit sum per group, so that an int overflow of the offsets is caught on the host
+__global__ void k_sell_len_multi(const SellDesc *__restrict__ d, int nd, int nlin, int *__restrict__ cnt,
+                                 unsigned long long *__restrict__ gsum) {
     const int lane = threadIdx.x & 31;
-    const int nsl = (nrows + 31) / 32;
-    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsl; s += (gridDim.x * blockDim.x) >> 5) {
-        const int r = s * 32 + lane;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nlin; q += (gridDim.x * blockDim.x) >> 5) {
+        const int p = find_desc(d, nd, q, 1);
+        const SellDesc &v = d[p];
+        const int sl = q - v.lin0;
+        const int r = sl * 32 + lane;
         int l = 0;
-        if (r < nrows) {
-            const int i = rows[r];
-            l = rp[i + 1] - rp[i];
+        if (r < v.nrows) {
+            const int i = v.row_out[r];
+            l = v.rp[i + 1] - v.rp[i];
         }
         l = __reduce_max_sync(0xffffffffu, l);
-        if (lane == 0) cnt[s] = 32 * l;
+        if (lane == 0) {
+            cnt[v.sl0 + sl] = 32 * l;
+            atomicAdd(&gsum[v.group], 32ull * (unsigned long long)l);
+        }
     }
 }
 
+// entries of the views [p0, p1) (one element type), one thread per row slot of a slice
 template <class T>
-__global__ void k_sell_fill(int nrows, const int *__restrict__ rows, const int *__restrict__ rp, const int *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ dinv, const int *__restrict__ sptr,
-                            int *__restrict__ scol, T *__restrict__ sval, T *__restrict__ sdinv) {
-    const int nsl = (nrows + 31) / 32;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nsl * 32; r += gridDim.x * blockDim.x) {
-        const int s = r >> 5, lane = r & 31;
-        const int base = sptr[s] + lane, len = (sptr[s + 1] - sptr[s]) >> 5;
+__global__ void k_sell_fill_multi(const SellDesc *__restrict__ d, int p0, int p1, int lin_end) {
+    const int lin_beg = d[p0].lin0;
+    const long long nslot = 32ll * (lin_end - lin_beg);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nslot; e += (long long)gridDim.x * blockDim.x) {
+        const int q = lin_beg + (int)(e >> 5), lane = (int)(e & 31);
+        const int p = p0 + find_desc(d + p0, p1 - p0, q, 1);
+        const SellDesc &v = d[p];
+        const int sl = q - v.lin0;
+        const int *sptr = v.slice_ptr;
+        const int base = sptr[sl] + lane, len = (sptr[sl + 1] - sptr[sl]) >> 5;
+        const int r = sl * 32 + lane;
         // padding entries carry value 0 and a column that is valid for x: the row's last column
         // (a row index is not one when the matrix is rectangular, as P and R are)
-        int b = 0, e = 0, pad = 0;
-        if (r < nrows) {
-            const int i = rows[r];
-            b = rp[i];
-            e = rp[i + 1];
-            pad = e > b ? col[e - 1] : 0;
-            if (sdinv) sdinv[r] = (T)dinv[i];
+        int b = 0, en = 0, pad = 0;
+        if (r < v.nrows) {
+            const int i = v.row_out[r];
+            b = v.rp[i];
+            en = v.rp[i + 1];
+            pad = en > b ? v.col[en - 1] : 0;
+            if (v.sdinv) static_cast<T *>(v.sdinv)[r] = (T)v.dinv[i];
         }
+        int *scol = v.scol;
+        T *sval = static_cast<T *>(v.sval);
         for (int j = 0; j < len; ++j) {
-            const bool in = b + j < e;
-            scol[base + 32 * j] = in ? col[b + j] : pad;
-            sval[base + 32 * j] = in ? (T)val[b + j] : T(0);
+            const bool in = b + j < en;
+            scol[base + 32 * j] = in ? v.col[b + j] : pad;
+            sval[base + 32 * j] = in ? (T)v.val[b + j] : T(0);
         }
     }
 }
@@ -135,24 +166,19 @@ void launch_frows(int n, const int8_t *cf, const int *cscan, int *frows, cudaStr
     count_launch();
 }
 
-void launch_sell_prepare(int nrows, const int *rows_in, const int *rp, int *rows_sorted, int *cnt, cudaStream_t s) {
-    if (nrows <= 0) return;
-    k_sell_sort<<<(nrows + SELL_WINDOW - 1) / SELL_WINDOW, SELL_WINDOW, 0, s>>>(nrows, rows_in, rp, rows_sorted);
-    const int nsl = (nrows + 31) / 32;
-    k_sell_len<<<grid_for((long long)nsl * 32, 256), 256, 0, s>>>(nrows, rows_sorted, rp, cnt);
+void launch_sell_prepare_multi(const SellDesc *d, int nd, int nwin, int nlin, int *cnt, unsigned long long *gsum,
+                               cudaStream_t s) {
+    if (nwin <= 0) return;
+    k_sell_sort_multi<<<nwin, SELL_WINDOW, 0, s>>>(d, nd);
+    k_sell_len_multi<<<grid_for((long long)nlin * 32, 256), 256, 0, s>>>(d, nd, nlin, cnt, gsum);
     count_launch(2);
 }
 
-void launch_sell_fill(const SellView &v, const DCsr &M, const double *dinv, bool fp32, cudaStream_t s) {
-    if (v.nrows <= 0) return;
-    const int nsl = (v.nrows + 31) / 32;
-    const int grid = grid_for((long long)nsl * 32, 256);
-    if (fp32)
-        k_sell_fill<float><<<grid, 256, 0, s>>>(v.nrows, v.row, M.rp, M.col, M.val, dinv, v.slice_ptr, v.col,
-                                                static_cast<float *>(v.val), static_cast<float *>(v.dinv));
-    else
-        k_sell_fill<double><<<grid, 256, 0, s>>>(v.nrows, v.row, M.rp, M.col, M.val, dinv, v.slice_ptr, v.col,
-                                                 static_cast<double *>(v.val), static_cast<double *>(v.dinv));
+void launch_sell_fill_multi(const SellDesc *d, int p0, int p1, int lin_beg, int lin_end, bool fp32, cudaStream_t s) {
+    if (p1 <= p0 || lin_end <= lin_beg) return;
+    const int grid = grid_for(32ll * (lin_end - lin_beg), 256);
+    if (fp32) k_sell_fill_multi<float><<<grid, 256, 0, s>>>(d, p0, p1, lin_end);
+    else k_sell_fill_multi<double><<<grid, 256, 0, s>>>(d, p0, p1, lin_end);
     count_launch();
 }
 

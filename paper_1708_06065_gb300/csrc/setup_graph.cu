@@ -127,7 +127,7 @@ __global__ void k_pmis_init(int n, const int *__restrict__ st_rp, uint64_t seed,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int lam = st_rp[i + 1] - st_rp[i];
         double u = __dmul_rn(__ull2double_rn(splitmix64((seed << 32) ^ (uint64_t)i) >> 11), 0x1.0p-53);
-        w[i] = __dadd_rn((double)lam, u);
+        w[i] = lam == 0 ? -1.0 : __dadd_rn((double)lam, u);    // -1: decided
         cf[i] = lam == 0 ? CF_F : CF_U;
     }
 }
@@ -141,7 +141,8 @@ __device__ __forceinline__ bool beats(double wi, int i, double wj, int j) {
 // weight beats those of all undecided points in S_i and ST_i is selected; grid barrier; stop
 // when the select pass saw no undecided point; selected points become C and their undecided
 // dependants (ST_i) F; grid barrier. Two selected points never lie in each other's ST (they
-// would beat each other), so marking C and F in one pass is race-free.
+// would beat each other), so marking C and F in one pass is race-free. A decided point's
+// weight is set to -1, so the select pass reads one array per neighbour.
 // ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2 + r % 2] undecided count of round r
 // (zero on entry). Every barrier wait is bounded; a wait that gives up sets
 // LAIR_ERR_DEVICE_TIMEOUT and the block returns.
@@ -177,7 +178,25 @@ __device__ bool grid_barrier(int *ctl, int *status) {
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, const double *__restrict__ w,
+// true if w_i beats the weight of every undecided j among col[b..e) (decided points carry
+// weight -1); the neighbours are read four at a time so that their loads overlap
+__device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, const int *__restrict__ col,
+                                               const double *w) {
+    for (int p = b; p < e; p += 4) {
+        int j[4];
+        double wj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = p + u < e ? col[p + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wj[u] = j[u] >= 0 ? w[j[u]] : -1.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (wj[u] >= 0.0 && !beats(wi, i, wj[u], j[u])) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, double *w,
                                                    int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
                                                    int *status) {
     const int stride = gridDim.x * blockDim.x;
@@ -186,19 +205,11 @@ __global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, con
         int local = 0;
         for (int i = t0; i < n; i += stride) {
             int8_t nc = 0;
-            if (cf[i] == CF_U) {
+            const double wi = w[i];
+            if (wi >= 0.0) {
                 ++local;
-                const double wi = w[i];
-                bool best = true;
-                for (int p = S.rp[i]; p < S.rp[i + 1] && best; ++p) {
-                    const int j = S.col[p];
-                    if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
-                }
-                for (int p = ST.rp[i]; p < ST.rp[i + 1] && best; ++p) {
-                    const int j = ST.col[p];
-                    if (cf[j] == CF_U && !beats(wi, i, w[j], j)) best = false;
-                }
-                nc = best;
+                nc = pmis_beats_all(wi, i, S.rp[i], S.rp[i + 1], S.col, w) &&
+                     pmis_beats_all(wi, i, ST.rp[i], ST.rp[i + 1], ST.col, w);
             }
             newc[i] = nc;
         }
@@ -211,9 +222,13 @@ __global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, con
         for (int i = t0; i < n; i += stride) {
             if (!newc[i]) continue;
             cf[i] = CF_C;
+            w[i] = -1.0;
             for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) {
                 const int j = ST.col[p];
-                if (cf[j] == CF_U) cf[j] = CF_F;
+                if (cf[j] == CF_U) {
+                    cf[j] = CF_F;
+                    w[j] = -1.0;
+                }
             }
         }
         if (!grid_barrier(ctl, status)) return;
@@ -638,7 +653,7 @@ void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *
 }
 
 // ctl: 4 ints, zero
-cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc, int *ctl,
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
                             int *status, cudaStream_t s) {
     int dev = 0, per_sm = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -25,7 +25,7 @@ void launch_transpose_scatter(int nr, const int *rp, const int *col, const doubl
                               int *tcol, double *tval, cudaStream_t s);
 void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s);
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
-cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, const double *w, int8_t *cf, int8_t *newc, int *ctl,
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
                             int *status, cudaStream_t s);
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
@@ -114,8 +114,20 @@ void cf_stats(const DCsr &A, const int8_t *cf, unsigned long long *out4, cudaStr
 
 // ---- sell.cu --------------------------------------------------------------------------
 void launch_frows(int n, const int8_t *cf, const int *cscan, int *frows, cudaStream_t s);
-void launch_sell_prepare(int nrows, const int *rows_in, const int *rp, int *rows_sorted, int *cnt, cudaStream_t s);
-void launch_sell_fill(const SellView &v, const DCsr &M, const double *dinv, bool fp32, cudaStream_t s);
+// one view of a batch built together (see sell.cu)
+struct SellDesc {
+    const int *rows_in;      // matrix rows of the view in order (NULL: all rows)
+    const int *rp, *col;     // the matrix
+    const double *val, *dinv;
+    int *row_out;            // view row -> matrix row (rows sorted by length inside windows)
+    int nrows, win0, lin0, sl0, group;
+    const int *slice_ptr;    // filled in before the fill pass
+    int *scol;
+    void *sval, *sdinv;
+};
+void launch_sell_prepare_multi(const SellDesc *d, int nd, int nwin, int nlin, int *cnt, unsigned long long *gsum,
+                               cudaStream_t s);
+void launch_sell_fill_multi(const SellDesc *d, int p0, int p1, int lin_beg, int lin_end, bool fp32, cudaStream_t s);
 template <class T> void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s);
 template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);

@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
     double *sxv = reinterpret_cast<double *>(keys + CAP);      // CAP * 12 bytes: 16-aligned for CAP >= 4
     double *px = sxv + XCHUNK;
     double *py = px + 32;
-    int *sk = reinterpret_cast<int *>(py + 32);
-    int *soff = sk + XCHUNK;
+    int *sy = reinterpret_cast<int *>(py + 32);                // first entry of row k of Y per staged k
+    int *soff = sy + XCHUNK;
     unsigned *bm = reinterpret_cast<unsigned *>(soff + XCHUNK + 1);
     unsigned short *pre = reinterpret_cast<unsigned short *>(bm + BM_WORDS);
     const int n = *count;
@@ -115,10 +115,11 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
             for (int b = 0; b < cn; b += 32) {
                 int len = 0;
                 if (b + (int)lane < cn) {
-                    int k = g.xcol[c0 + b + lane];
-                    sk[b + lane] = k;
+                    const int k = g.xcol[c0 + b + lane];
+                    const int y0 = g.yrp[k];
+                    sy[b + lane] = y0;
                     sxv[b + lane] = g.xval[c0 + b + lane];
-                    len = g.yrp[k + 1] - g.yrp[k];
+                    len = g.yrp[k + 1] - y0;
                 }
                 int incl = len;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -131,21 +132,30 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
             if (lane == 0) soff[cn] = carry;
             __syncwarp();
             const int total = carry;
+            // product p of the chunk: column, x and y value (the y loads of the next 32 products are
+            // issued before the current ones are accumulated)
+            auto fetch = [&](int p, int &l, double &xv, double &yv) {
+                int lo = 0, hi = cn - 1;       // last chunk entry with soff <= p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (soff[mid] <= p) lo = mid; else hi = mid - 1;
+                }
+                const int q = sy[lo] + (p - soff[lo]);
+                xv = sxv[lo];
+                l = g.ycol[q];
+                yv = g.yval[q];
+            };
+            int l = -1;
+            double xv = 0.0, yv = 0.0;
+            if ((int)lane < total) fetch((int)lane, l, xv, yv);
             for (int base = 0; base < total; base += 32) {
-                const int p = base + (int)lane;
-                const bool act = p < total;
-                int l = -1;
+                const bool act = base + (int)lane < total;
+                int ln = -1;
+                double xn = 0.0, yn = 0.0;
+                if (base + 32 + (int)lane < total) fetch(base + 32 + (int)lane, ln, xn, yn);
                 if (act) {
-                    int lo = 0, hi = cn - 1;       // last chunk entry with soff <= p
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (soff[mid] <= p) lo = mid; else hi = mid - 1;
-                    }
-                    const int k = sk[lo];
-                    const int q = g.yrp[k] + (p - soff[lo]);
-                    l = g.ycol[q];
-                    px[lane] = sxv[lo];
-                    py[lane] = g.yval[q];
+                    px[lane] = xv;
+                    py[lane] = yv;
                 }
                 const unsigned am = __ballot_sync(0xffffffffu, act);
                 __syncwarp();
@@ -172,6 +182,9 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
                     }
                 }
                 __syncwarp();
+                l = ln;
+                xv = xn;
+                yv = yn;
             }
         }
         __syncwarp();
