@@ -275,8 +275,7 @@ struct Temps {
                 ch[nx].used = 0;
             } else {
                 size_t sz = TMP_CHUNK_MIN;
-                if (!ch.empty() && 2 * ch.back().size > sz) sz = 2 * ch.back().size;
-                if (bytes > sz) sz = bytes;
+                if (2 * bytes > sz) sz = 2 * bytes;
                 void *np = nullptr;
                 TRY(raw_alloc(h, &np, sz));
                 h->allocs.push_back(np);
@@ -470,7 +469,10 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
         if (val) TRY(t.get(tval, (size_t)nnz));
     }
     launch_transpose_scatter(nr, rp, col, val, *trp, cnt, *tcol, val ? *tval : nullptr, h->s);
-    launch_sort_rows(nc, *trp, *tcol, val ? *tval : nullptr, h->s);
+    int *lists;
+    TRY(t.get(&lists, 2 * (size_t)nc + 2));
+    CU(cudaMemsetAsync(lists, 0, 2 * sizeof(int), h->s));
+    launch_sort_rows(nc, *trp, *tcol, val ? *tval : nullptr, lists, h->s);
     return LAIR_OK;
 }
 

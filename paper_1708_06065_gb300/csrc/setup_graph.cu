@@ -63,49 +63,181 @@ __global__ void k_transpose_scatter(int nr, const int *__restrict__ rp, const in
         }
 }
 
-constexpr int SORT_REG = 8;   // rows up to this length are sorted in registers
+// Row sort after a transpose, by row length: up to SORT_REG entries in one thread's registers;
+// up to SORT_WARP by a warp (32 R entries in registers, R = 1, 2, 4 or 8, bitonic network with
+// shuffles across lanes and register exchanges within a lane); up to SORT_CTA by a CTA in
+// shared memory (bitonic); longer rows by insertion. The columns of a row are distinct. The
+// short-row pass appends the other rows to two lists (counts in lists[0], lists[1]) with one
+// atomic per warp and list.
+constexpr int SORT_REG = 8;
+constexpr int SORT_WARP = 256;
+constexpr int SORT_CTA = 4096;
+constexpr int SORT_CTA_THREADS = 256;
 
-__global__ void k_sort_rows(int nr, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val) {
+__device__ void insertion_sort_row(int b, int e, int *col, double *val) {
+    for (int k = b + 1; k < e; ++k) {
+        const int c = col[k];
+        const double v = val ? val[k] : 0.0;
+        int m = k - 1;
+        while (m >= b && col[m] > c) {
+            col[m + 1] = col[m];
+            if (val) val[m + 1] = val[m];
+            --m;
+        }
+        col[m + 1] = c;
+        if (val) val[m + 1] = v;
+    }
+}
+
+// appends row i to list l (0 or 1) if want; all active lanes call it together
+__device__ __forceinline__ void list_append(int *lists, int nr, int l, bool want, int i) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    int base = 0;
+    if (lane == lead) base = atomicAdd(&lists[l], __popc(m));
+    base = __shfl_sync(act, base, lead);
+    if (want) lists[2 + l * nr + base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+// lists: [0] warp-list count, [1] CTA-list count, then nr entries of each list
+__global__ void k_sort_rows(int nr, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val,
+                            int *__restrict__ lists) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
-        int b = rp[i], e = rp[i + 1];
-        if (e - b <= SORT_REG) {
-            int c[SORT_REG];
-            double v[SORT_REG];
-            const int len = e - b;
+        const int b = rp[i], e = rp[i + 1];
+        const int len = e - b;
+        list_append(lists, nr, 0, len > SORT_REG && len <= SORT_WARP, i);
+        list_append(lists, nr, 1, len > SORT_WARP && len <= SORT_CTA, i);
+        if (len > SORT_CTA) insertion_sort_row(b, e, col, val);
+        if (len > SORT_REG) continue;
+        int c[SORT_REG];
+        double v[SORT_REG];
 #pragma unroll
-            for (int k = 0; k < SORT_REG; ++k) {
-                c[k] = k < len ? col[b + k] : 0x7fffffff;
-                v[k] = (k < len && val) ? val[b + k] : 0.0;
-            }
-            // odd-even transposition network (the columns of a row are distinct)
+        for (int k = 0; k < SORT_REG; ++k) {
+            c[k] = k < len ? col[b + k] : 0x7fffffff;
+            v[k] = (k < len && val) ? val[b + k] : 0.0;
+        }
+        // odd-even transposition network
 #pragma unroll
-            for (int pass = 0; pass < SORT_REG; ++pass)
+        for (int pass = 0; pass < SORT_REG; ++pass)
 #pragma unroll
-                for (int k = pass & 1; k + 1 < SORT_REG; k += 2)
-                    if (c[k] > c[k + 1]) {
-                        int tc = c[k]; c[k] = c[k + 1]; c[k + 1] = tc;
-                        double tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
-                    }
-#pragma unroll
-            for (int k = 0; k < SORT_REG; ++k)
-                if (k < len) {
-                    col[b + k] = c[k];
-                    if (val) val[b + k] = v[k];
+            for (int k = pass & 1; k + 1 < SORT_REG; k += 2)
+                if (c[k] > c[k + 1]) {
+                    int tc = c[k]; c[k] = c[k + 1]; c[k + 1] = tc;
+                    double tv = v[k]; v[k] = v[k + 1]; v[k + 1] = tv;
                 }
-            continue;
-        }
-        for (int k = b + 1; k < e; ++k) {
-            int c = col[k];
-            double v = val ? val[k] : 0.0;
-            int m = k - 1;
-            while (m >= b && col[m] > c) {
-                col[m + 1] = col[m];
-                if (val) val[m + 1] = val[m];
-                --m;
+#pragma unroll
+        for (int k = 0; k < SORT_REG; ++k)
+            if (k < len) {
+                col[b + k] = c[k];
+                if (val) val[b + k] = v[k];
             }
-            col[m + 1] = c;
-            if (val) val[m + 1] = v;
+    }
+}
+
+// bitonic sort of 32 R (key, value) pairs held by a warp: element e = 32 r + lane
+template <int R>
+__device__ __forceinline__ void warp_sort_row(int b, int len, int *col, double *val, int lane) {
+    int key[R];
+    double v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        key[r] = e < len ? col[b + e] : 0x7fffffff;
+        v[r] = (e < len && val) ? val[b + e] : 0.0;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int r2 = r ^ (j >> 5);
+                    if (r2 > r) {
+                        const bool up = ((32 * r + lane) & k) == 0;
+                        if (up ? key[r] > key[r2] : key[r] < key[r2]) {
+                            const int tk = key[r]; key[r] = key[r2]; key[r2] = tk;
+                            const double tv = v[r]; v[r] = v[r2]; v[r2] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int pk = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const double pv = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    const bool up = ((32 * r + lane) & k) == 0, lower = (lane & j) == 0;
+                    if (lower == up ? pk < key[r] : pk > key[r]) {
+                        key[r] = pk;
+                        v[r] = pv;
+                    }
+                }
+            }
         }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        if (e < len) {
+            col[b + e] = key[r];
+            if (val) val[b + e] = v[r];
+        }
+    }
+}
+
+// one warp per row of the warp list
+__global__ void k_sort_rows_warp(int nr, const int *__restrict__ rp, int *__restrict__ col, double *__restrict__ val,
+                                 const int *__restrict__ lists) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = lists[0];
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < cnt; t += (gridDim.x * blockDim.x) >> 5) {
+        const int i = lists[2 + t];
+        const int b = rp[i], len = rp[i + 1] - b;
+        if (len <= 32) warp_sort_row<1>(b, len, col, val, lane);
+        else if (len <= 64) warp_sort_row<2>(b, len, col, val, lane);
+        else if (len <= 128) warp_sort_row<4>(b, len, col, val, lane);
+        else warp_sort_row<8>(b, len, col, val, lane);
+    }
+}
+
+// one CTA per row of the CTA list: bitonic sort in shared memory
+__global__ void __launch_bounds__(SORT_CTA_THREADS) k_sort_rows_cta(int nr, const int *__restrict__ rp,
+                                                                     int *__restrict__ col, double *__restrict__ val,
+                                                                     const int *__restrict__ lists) {
+    __shared__ int sk[SORT_CTA];
+    __shared__ double sv[SORT_CTA];
+    const int cnt = lists[1];
+    for (int t = blockIdx.x; t < cnt; t += gridDim.x) {
+        const int i = lists[2 + nr + t];
+        const int b = rp[i], len = rp[i + 1] - b;
+        int P = 2 * SORT_WARP;
+        while (P < len) P <<= 1;
+        for (int q = threadIdx.x; q < P; q += blockDim.x) {
+            sk[q] = q < len ? col[b + q] : 0x7fffffff;
+            sv[q] = (q < len && val) ? val[b + q] : 0.0;
+        }
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = threadIdx.x; q < P; q += blockDim.x) {
+                    const int o = q ^ j;
+                    if (o > q) {
+                        const bool up = (q & k) == 0;
+                        if (up ? sk[q] > sk[o] : sk[q] < sk[o]) {
+                            const int tk = sk[q]; sk[q] = sk[o]; sk[o] = tk;
+                            const double tv = sv[q]; sv[q] = sv[o]; sv[o] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int q = threadIdx.x; q < len; q += blockDim.x) {
+            col[b + q] = sk[q];
+            if (val) val[b + q] = sv[q];
+        }
+        __syncthreads();
     }
 }
 
@@ -196,7 +328,9 @@ __device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, c
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_pmis_coop(int n, Graph S, Graph ST, double *w,
+constexpr int PMIS_THREADS = 1024;   // one CTA per SM keeps the grid barrier short
+
+__global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Graph ST, double *w,
                                                    int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
                                                    int *status) {
     const int stride = gridDim.x * blockDim.x;
@@ -642,9 +776,13 @@ void launch_transpose_scatter(int nr, const int *rp, const int *col, const doubl
     count_launch();
 }
 
-void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s) {
-    k_sort_rows<<<grid_for(nr, 128), 128, 0, s>>>(nr, rp, col, val);
-    count_launch();
+// lists: 2 * nr + 2 ints of scratch, the first two zero
+void launch_sort_rows(int nr, const int *rp, int *col, double *val, int *lists, cudaStream_t s) {
+    if (nr <= 0) return;
+    k_sort_rows<<<grid_for(nr, 128), 128, 0, s>>>(nr, rp, col, val, lists);
+    k_sort_rows_warp<<<152 * 8, 256, 0, s>>>(nr, rp, col, val, lists);
+    k_sort_rows_cta<<<152 * 2, SORT_CTA_THREADS, 0, s>>>(nr, rp, col, val, lists);
+    count_launch(3);
 }
 
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s) {
@@ -657,14 +795,15 @@ cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, i
                             int *status, cudaStream_t s) {
     int dev = 0, per_sm = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pmis_coop, 256, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pmis_coop, PMIS_THREADS, 0);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    int grid = (per_sm > 0 ? per_sm : 1) * sms;
-    const int need = (n + 255) / 256;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    int grid = sms;
+    const int need = (n + PMIS_THREADS - 1) / PMIS_THREADS;
     if (grid > need) grid = need > 0 ? need : 1;
     void *args[] = {(void *)&n, (void *)&S, (void *)&ST, (void *)&w, (void *)&cf, (void *)&newc, (void *)&ctl, (void *)&status};
-    e = cudaLaunchCooperativeKernel((const void *)k_pmis_coop, dim3(grid), dim3(256), args, 0, s);
+    e = cudaLaunchCooperativeKernel((const void *)k_pmis_coop, dim3(grid), dim3(PMIS_THREADS), args, 0, s);
     count_launch();
     return e;
 }

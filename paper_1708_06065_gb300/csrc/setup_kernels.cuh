@@ -23,7 +23,7 @@ void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaS
 void launch_col_count(int nr, const int *rp, const int *col, int *cnt, cudaStream_t s);
 void launch_transpose_scatter(int nr, const int *rp, const int *col, const double *val, const int *trp, int *cursor,
                               int *tcol, double *tval, cudaStream_t s);
-void launch_sort_rows(int nr, const int *rp, int *col, double *val, cudaStream_t s);
+void launch_sort_rows(int nr, const int *rp, int *col, double *val, int *lists, cudaStream_t s);
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
 cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
                             int *status, cudaStream_t s);
