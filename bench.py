@@ -355,7 +355,9 @@ def main():
 
     # ---- roofline of the dominant timed kernel (largest accumulated time)
     peak, peak_src = load_peaks()
-    kern = [(v[1], k, v) for k, v in timers.items() if k != "vcycle" and not k.startswith("setup_") and v[0] > 0]
+    # single-kernel timers only (the V-cycle, CGS2 and residual regions span several kernels)
+    multi = ("vcycle", "outer_cgs2", "outer_residual")
+    kern = [(v[1], k, v) for k, v in timers.items() if k not in multi and not k.startswith("setup_") and v[0] > 0]
     roof = None
     if kern:
         _, name, (cnt, ms, byt) = max(kern)

@@ -81,6 +81,8 @@ struct lair_handle {
     void *scan_tmp = nullptr;
     size_t scan_tmp_bytes = 0;
     std::vector<void *> allocs;   // everything owned by the handle
+    int *prod_nnz = nullptr;      // device: entry counts of the timed level-0 products (timing only)
+    double prod_in_bytes[2] = {0.0, 0.0};
     // bump arenas over large device chunks (owned through allocs): set-up temporaries (stack
     // discipline, see Temps) and small long-lived arrays; each allocation is 256-byte aligned
     struct Chunk { char *p; size_t size; size_t used; };
@@ -546,7 +548,8 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
 }
 
 // Z = X Y, canonical accumulation order (see setup_rap.cu)
-static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep) {
+// timed (0 or 1): the product's row pass is timed as "L0_RA" / "L0_RAP" and its entry count kept
+static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep, int timed = -1) {
     const int nr = X.nr;
     int *ub, *off;
     TRY(new_counts(h, t, &ub, nr));
@@ -576,7 +579,14 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
         TRY(t.get(&svals, slots));
     }
     SpgemmArgs g{X.rp, X.col, X.val, Y.rp, Y.col, Y.val, off, tcol, tval, cnt};
+    int tp = -1;
+    if (timed >= 0 && h->o.timing) {
+        // algorithmic bytes: X and Y read once, the product written once (its size is added later)
+        h->prod_in_bytes[timed] = 12.0 * ((double)X.nnz + (double)Y.nnz) + 4.0 * ((double)X.nr + Y.nr + 2);
+        tp = tbegin(h, timed == 0 ? "L0_RA" : "L0_RAP", 0.0);
+    }
     CU(launch_spgemm_rows(g, nr, lists, bc, hc, ubmax, skeys, svals, h->s));
+    tend(h, tp);
     Z.nr = nr;
     Z.nc = Y.nc;
     if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
@@ -595,6 +605,10 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
         TRY(t.get(&Z.val, (size_t)Z.nnz));
     }
     launch_copy_rows(nr, off, tcol, tval, Z, h->s);
+    if (timed >= 0 && h->o.timing) {
+        if (!h->prod_nnz) TRY(dalloc(h, &h->prod_nnz, 2));
+        CU(cudaMemcpyAsync(h->prod_nnz + timed, Z.rp + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
+    }
     return LAIR_OK;
 }
 
@@ -760,9 +774,9 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     tend(h, tp);
     tp = tbegin(h, "setup_RAP", 0.0);
     DCsr RA, K;
-    TRY(spgemm(h, t, L.R, A, RA, false));
+    TRY(spgemm(h, t, L.R, A, RA, false, l == 0 ? 0 : -1));
     const bool lump = o.lump_tol > 0.0;
-    TRY(spgemm(h, t, RA, L.P, K, !lump));
+    TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1));
     Level next;
     if (lump) {
         int *cnt;
@@ -1126,6 +1140,16 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         H.singular_P = hc[1];
         for (int l = 0; l < nl; ++l)
             if (o.interp == LAIR_P_ONEPOINT && H.lev[l].P.rp && !H.lev[l].coarsest) H.lev[l].P.nnz = hc[2 + l];
+        if (h->prod_nnz) {
+            int pn[2];
+            TRY(read_ints(h, h->prod_nnz, 2, pn));
+            // R A: R, A read, RA written. (R A) P: RA (its exact size is known only now), P read, K written
+            const Level &L0r = H.lev[0];
+            const double in0 = h->prod_in_bytes[0];
+            const double in1 = 12.0 * ((double)pn[0] + (double)L0r.P.nnz) + 4.0 * ((double)L0r.nc + L0r.A.nr + 2);
+            h->timers[timer_slot(h, "L0_RA", 0.0)].bytes = in0 + 12.0 * pn[0];
+            h->timers[timer_slot(h, "L0_RAP", 0.0)].bytes = in1 + 12.0 * pn[1];
+        }
     }
     {
         int tv = tbegin(h, "setup_views", 0.0);

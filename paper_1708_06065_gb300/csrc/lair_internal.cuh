@@ -55,6 +55,44 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Ascending bitonic sort of 32 R (key, value) pairs held by a warp, element e = 32 r + lane
+// in key[r], val[r]. Exchanges at distance < 32 go through shuffles, the others stay inside a
+// lane's registers; every index is a compile-time constant. Keys are distinct apart from
+// padding (INT_MAX), which ends up last.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(int (&key)[R], double (&val)[R], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int r2 = r ^ (j >> 5);
+                    if (r2 > r) {
+                        const bool up = ((32 * r + lane) & k) == 0;
+                        if (up ? key[r] > key[r2] : key[r] < key[r2]) {
+                            const int tk = key[r]; key[r] = key[r2]; key[r2] = tk;
+                            const double tv = val[r]; val[r] = val[r2]; val[r2] = tv;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int pk = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const double pv = __shfl_xor_sync(0xffffffffu, val[r], j);
+                    const bool up = ((32 * r + lane) & k) == 0, lower = (lane & j) == 0;
+                    if (lower == up ? pk < key[r] : pk > key[r]) {
+                        key[r] = pk;
+                        val[r] = pv;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // -------------------------------------------------------------------------------------
 // host-side launch helpers (defined in lair_api.cu)
 // -------------------------------------------------------------------------------------

@@ -136,7 +136,7 @@ __global__ void k_sort_rows(int nr, const int *__restrict__ rp, int *__restrict_
     }
 }
 
-// bitonic sort of 32 R (key, value) pairs held by a warp: element e = 32 r + lane
+// one row of at most 32 R entries sorted by a warp
 template <int R>
 __device__ __forceinline__ void warp_sort_row(int b, int len, int *col, double *val, int lane) {
     int key[R];
@@ -147,36 +147,7 @@ __device__ __forceinline__ void warp_sort_row(int b, int len, int *col, double *
         key[r] = e < len ? col[b + e] : 0x7fffffff;
         v[r] = (e < len && val) ? val[b + e] : 0.0;
     }
-#pragma unroll
-    for (int k = 2; k <= 32 * R; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int r2 = r ^ (j >> 5);
-                    if (r2 > r) {
-                        const bool up = ((32 * r + lane) & k) == 0;
-                        if (up ? key[r] > key[r2] : key[r] < key[r2]) {
-                            const int tk = key[r]; key[r] = key[r2]; key[r2] = tk;
-                            const double tv = v[r]; v[r] = v[r2]; v[r2] = tv;
-                        }
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int pk = __shfl_xor_sync(0xffffffffu, key[r], j);
-                    const double pv = __shfl_xor_sync(0xffffffffu, v[r], j);
-                    const bool up = ((32 * r + lane) & k) == 0, lower = (lane & j) == 0;
-                    if (lower == up ? pk < key[r] : pk > key[r]) {
-                        key[r] = pk;
-                        v[r] = pv;
-                    }
-                }
-            }
-        }
-    }
+    warp_bitonic<R>(key, v, lane);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int e = 32 * r + lane;

@@ -52,11 +52,32 @@ __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__re
 __device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
 
 constexpr int XCHUNK = 64;            // entries of an X row staged at a time
-constexpr int BM_WORDS = 512;         // column bitmap of a row: spans up to 16384 columns
-// per-warp staging after the hash table: x (XCHUNK doubles), px/py (2 x 32 doubles), k (XCHUNK ints),
-// offsets (XCHUNK + 1 ints), bitmap (BM_WORDS words), word prefix counts (BM_WORDS ushort); 16-byte aligned
-constexpr size_t SPGEMM_EXTRA = ((XCHUNK * sizeof(double) + 64 * sizeof(double) + (2 * XCHUNK + 1) * sizeof(int) +
-                                  BM_WORDS * sizeof(unsigned) + BM_WORDS * sizeof(unsigned short)) + 15) & ~(size_t)15;
+// per-warp staging after the hash table: x (XCHUNK doubles), px/py (2 x 32 doubles), Y row starts
+// (XCHUNK ints), offsets (XCHUNK + 1 ints); 16-byte aligned
+constexpr size_t SPGEMM_EXTRA = ((XCHUNK * sizeof(double) + 64 * sizeof(double) + (2 * XCHUNK + 1) * sizeof(int)) + 15) &
+                                ~(size_t)15;
+
+// the cnt compacted (column, value) pairs of a row, sorted by column, written to col/val
+template <int R>
+__device__ __forceinline__ void sorted_out(const int *keys, const double *vals, int cnt, int *col, double *val, int lane) {
+    int k[R];
+    double v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        k[r] = e < cnt ? keys[e] : 0x7fffffff;
+        v[r] = e < cnt ? vals[e] : 0.0;
+    }
+    warp_bitonic<R>(k, v, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        if (e < cnt) {
+            col[e] = k[r];
+            val[e] = v[r];
+        }
+    }
+}
 
 template <int CAP>
 __host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * (sizeof(double) + sizeof(int)) + SPGEMM_EXTRA; }
@@ -65,8 +86,8 @@ __host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * 
 // x_ak * y_kl of the row are laid out flat in ascending (k, position in row k of Y) order and taken
 // 32 at a time; lanes holding the same column l are grouped with __match_any_sync and the lowest lane
 // of a group (the smallest k) applies the group's products in ascending k, so every entry receives its
-// fma updates in ascending k exactly as in a sequential loop. Columns are ordered through a bitmap of
-// the row's column span (position = set bits before the column) or, for wide rows, by rank counting.
+// fma updates in ascending k exactly as in a sequential loop. The occupied slots are then compacted
+// and ordered by column with a register bitonic network (rank counting for the largest rows).
 template <int CAP, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
                                                            const int *__restrict__ count) {
@@ -81,11 +102,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
     double *py = px + 32;
     int *sy = reinterpret_cast<int *>(py + 32);                // first entry of row k of Y per staged k
     int *soff = sy + XCHUNK;
-    unsigned *bm = reinterpret_cast<unsigned *>(soff + XCHUNK + 1);
-    unsigned short *pre = reinterpret_cast<unsigned short *>(bm + BM_WORDS);
     const int n = *count;
     const int nwarps = gridDim.x * WARPS;
-    for (unsigned e = lane; e < BM_WORDS; e += 32) bm[e] = 0u;
     for (int t = blockIdx.x * WARPS + w; t < n; t += nwarps) {
         const int a = list[t];
         const int ub = g.off[a + 1] - g.off[a];
@@ -94,19 +112,6 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
         const unsigned mask = cap - 1;
         for (unsigned e = lane; e < cap; e += 32) keys[e] = -1;
         const int xb = g.xrp[a], xe = g.xrp[a + 1];
-        // column span of the row: rows of Y are sorted, so their first and last columns bound it
-        int cmin = 0x7fffffff, cmax = -1;
-        for (int p = xb + (int)lane; p < xe; p += 32) {
-            const int k = g.xcol[p];
-            const int yb = g.yrp[k], ye = g.yrp[k + 1];
-            if (ye > yb) {
-                cmin = min(cmin, g.ycol[yb]);
-                cmax = max(cmax, g.ycol[ye - 1]);
-            }
-        }
-        cmin = __reduce_min_sync(0xffffffffu, cmin);
-        cmax = __reduce_max_sync(0xffffffffu, cmax);
-        const bool use_bm = cmax >= cmin && cmax - cmin < BM_WORDS * 32;
         for (int c0 = xb; c0 < xe; c0 += XCHUNK) {
             const int cn = min(XCHUNK, xe - c0);
             __syncwarp();
@@ -168,7 +173,6 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
                             int prev = atomicCAS(&keys[h], -1, l);
                             if (prev == -1) {
                                 v = 0.0;
-                                if (use_bm) atomicOr(&bm[(l - cmin) >> 5], 1u << ((l - cmin) & 31));
                                 break;
                             }
                             if (prev == l) { v = vals[h]; break; }
@@ -190,50 +194,27 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
         __syncwarp();
         const int o = g.off[a];
         int cnt;
-        if (use_bm) {
-            // prefix counts of the bitmap words (lane owns 16 consecutive words), then each
-            // occupied slot goes straight to its sorted position
-            const int wpl = BM_WORDS / 32;
-            int c = 0;
-            for (int j = 0; j < wpl; ++j) c += __popc(bm[lane * wpl + j]);
-            int incl = c;
-            for (int d = 1; d < 32; d <<= 1) {
-                int v = __shfl_up_sync(0xffffffffu, incl, d);
-                if ((int)lane >= d) incl += v;
-            }
-            cnt = __shfl_sync(0xffffffffu, incl, 31);
-            int run = incl - c;
-            for (int j = 0; j < wpl; ++j) {
-                pre[lane * wpl + j] = (unsigned short)run;
-                run += __popc(bm[lane * wpl + j]);
-            }
+        // compact occupied slots to the front (positions never pass the slot being read)
+        cnt = 0;
+        for (unsigned base = 0; base < cap; base += 32) {
+            int key = keys[base + lane];
+            double v = vals[base + lane];
+            unsigned occ = __ballot_sync(0xffffffffu, key != -1);
             __syncwarp();
-            for (unsigned e = lane; e < cap; e += 32) {
-                const int key = keys[e];
-                if (key == -1) continue;
-                const int d = key - cmin;
-                const int r = pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
-                g.tcol[o + r] = key;
-                g.tval[o + r] = vals[e];
+            if (key != -1) {
+                int pos = cnt + __popc(occ & ((1u << lane) - 1u));
+                keys[pos] = key;
+                vals[pos] = v;
             }
+            cnt += __popc(occ);
             __syncwarp();
-            for (int j = 0; j < wpl; ++j) bm[lane * wpl + j] = 0u;
-        } else {
-            // compact occupied slots to the front (positions never pass the slot being read)
-            cnt = 0;
-            for (unsigned base = 0; base < cap; base += 32) {
-                int key = keys[base + lane];
-                double v = vals[base + lane];
-                unsigned occ = __ballot_sync(0xffffffffu, key != -1);
-                __syncwarp();
-                if (key != -1) {
-                    int pos = cnt + __popc(occ & ((1u << lane) - 1u));
-                    keys[pos] = key;
-                    vals[pos] = v;
-                }
-                cnt += __popc(occ);
-                __syncwarp();
-            }
+        }
+        if (cnt <= 32) sorted_out<1>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        else if (cnt <= 64) sorted_out<2>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        else if (CAP >= 256 && cnt <= 128) sorted_out<(CAP >= 256 ? 4 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        else if (CAP >= 512 && cnt <= 256) sorted_out<(CAP >= 512 ? 8 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        else if (CAP >= 1024 && cnt <= 512) sorted_out<(CAP >= 1024 ? 16 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        else {
             // rank counting: the position of a key is the number of smaller keys (keys are unique)
             for (int e = lane; e < cnt; e += 32) {
                 const int key = keys[e];
