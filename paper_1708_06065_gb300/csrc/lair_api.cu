@@ -82,7 +82,7 @@ struct lair_handle {
     size_t scan_tmp_bytes = 0;
     std::vector<void *> allocs;   // everything owned by the handle
     int *prod_nnz = nullptr;      // device: entry counts of the timed level-0 products (timing only)
-    double prod_in_bytes[2] = {0.0, 0.0};
+    bool prod_fused = false;      // level 0 formed R A P in one pass
     // bump arenas over large device chunks (owned through allocs): set-up temporaries (stack
     // discipline, see Temps) and small long-lived arrays; each allocation is 256-byte aligned
     struct Chunk { char *p; size_t size; size_t used; };
@@ -548,8 +548,11 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
 }
 
 // Z = X Y, canonical accumulation order (see setup_rap.cu)
+// Z = X Y, or Z = X Y P when P (one-point: at most one entry per row) is given; the triple product is
+// formed in one pass when every row of X Y fits the short-row kernels, else as (X Y) P.
 // timed (0 or 1): the product's row pass is timed as "L0_RA" / "L0_RAP" and its entry count kept
-static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep, int timed = -1) {
+static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep, int timed = -1,
+                          const DCsr *P = nullptr) {
     const int nr = X.nr;
     int *ub, *off;
     TRY(new_counts(h, t, &ub, nr));
@@ -567,6 +570,11 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     int hc[SPGEMM_BINS + 2];
     TRY(read_ints(h, bc, SPGEMM_BINS + 2, hc));
     const int total = hc[SPGEMM_BINS + 1];
+    if (P && !spgemm_can_fuse(hc)) {
+        DCsr XY;
+        TRY(spgemm(h, t, X, Y, XY, false, timed >= 0 ? 0 : -1));
+        return spgemm(h, t, XY, *P, Z, keep, timed >= 0 ? 1 : -1);
+    }
     TRY(t.get(&tcol, (size_t)total));
     TRY(t.get(&tval, (size_t)total));
     int *skeys = nullptr;
@@ -579,16 +587,18 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
         TRY(t.get(&svals, slots));
     }
     SpgemmArgs g{X.rp, X.col, X.val, Y.rp, Y.col, Y.val, off, tcol, tval, cnt};
-    int tp = -1;
-    if (timed >= 0 && h->o.timing) {
-        // algorithmic bytes: X and Y read once, the product written once (its size is added later)
-        h->prod_in_bytes[timed] = 12.0 * ((double)X.nnz + (double)Y.nnz) + 4.0 * ((double)X.nr + Y.nr + 2);
-        tp = tbegin(h, timed == 0 ? "L0_RA" : "L0_RAP", 0.0);
+    if (P) {
+        g.prp = P->rp;
+        g.pcol = P->col;
+        g.pval = P->val;
+        if (timed >= 0) h->prod_fused = true;
     }
+    int tp = -1;
+    if (timed >= 0 && h->o.timing) tp = tbegin(h, timed == 0 ? "L0_RA" : "L0_RAP", 0.0);
     CU(launch_spgemm_rows(g, nr, lists, bc, hc, ubmax, skeys, svals, h->s));
     tend(h, tp);
     Z.nr = nr;
-    Z.nc = Y.nc;
+    Z.nc = P ? P->nc : Y.nc;
     if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
     // a kept product is stored at its exact size; a temporary one at the bound (its entry count
     // is then only a capacity and is not read back)
@@ -774,9 +784,13 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     tend(h, tp);
     tp = tbegin(h, "setup_RAP", 0.0);
     DCsr RA, K;
-    TRY(spgemm(h, t, L.R, A, RA, false, l == 0 ? 0 : -1));
     const bool lump = o.lump_tol > 0.0;
-    TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1));
+    if (o.interp == LAIR_P_ONEPOINT) {
+        TRY(spgemm(h, t, L.R, A, K, !lump, l == 0 ? 1 : -1, &L.P));
+    } else {
+        TRY(spgemm(h, t, L.R, A, RA, false, l == 0 ? 0 : -1));
+        TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1));
+    }
     Level next;
     if (lump) {
         int *cnt;
@@ -1143,12 +1157,18 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         if (h->prod_nnz) {
             int pn[2];
             TRY(read_ints(h, h->prod_nnz, 2, pn));
-            // R A: R, A read, RA written. (R A) P: RA (its exact size is known only now), P read, K written
+            // algorithmic bytes: every factor read once, the product written once.
+            // R A: R, A -> RA. (R A) P: RA, P -> K. Fused: R, A, P -> K.
             const Level &L0r = H.lev[0];
-            const double in0 = h->prod_in_bytes[0];
-            const double in1 = 12.0 * ((double)pn[0] + (double)L0r.P.nnz) + 4.0 * ((double)L0r.nc + L0r.A.nr + 2);
-            h->timers[timer_slot(h, "L0_RA", 0.0)].bytes = in0 + 12.0 * pn[0];
-            h->timers[timer_slot(h, "L0_RAP", 0.0)].bytes = in1 + 12.0 * pn[1];
+            const double n0 = L0r.A.nr, nc0 = L0r.nc;
+            const double rd_R = 12.0 * L0r.R.nnz + 4.0 * (nc0 + 1), rd_A = 12.0 * L0r.A.nnz + 4.0 * (n0 + 1);
+            const double rd_P = 12.0 * L0r.P.nnz + 4.0 * (n0 + 1);
+            if (h->prod_fused) {
+                h->timers[timer_slot(h, "L0_RAP", 0.0)].bytes = rd_R + rd_A + rd_P + 12.0 * pn[1];
+            } else {
+                h->timers[timer_slot(h, "L0_RA", 0.0)].bytes = rd_R + rd_A + 12.0 * pn[0];
+                h->timers[timer_slot(h, "L0_RAP", 0.0)].bytes = 12.0 * pn[0] + 4.0 * (nc0 + 1) + rd_P + 12.0 * pn[1];
+            }
         }
     }
     {

@@ -73,11 +73,16 @@ struct SpgemmArgs {
     int *tcol;            // staging, off[nr] entries
     double *tval;
     int *cnt;             // exact row lengths
+    // fused third factor (one-point P: at most one entry per row); NULL for a plain product
+    const int *prp = nullptr, *pcol = nullptr;
+    const double *pval = nullptr;
 };
 constexpr int SPGEMM_CTA_GRID = 152;
 constexpr int SPGEMM_BINS = 4;   // three warp bins by row bound, then the CTA bin
 void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
 void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s);
+// true if every row of the product fits the fused one-point-P kernels (bins 0 and 1)
+bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s);
 unsigned spgemm_big_cap(int ubmax);

@@ -79,6 +79,117 @@ __device__ __forceinline__ void sorted_out(const int *keys, const double *vals, 
     }
 }
 
+// the leader of group grp (lanes holding column l) adds the group's products px[b] * py[b] to
+// the table entry of l, in ascending lane order
+__device__ __forceinline__ void hash_group_fma(int *keys, double *vals, unsigned mask, int l, unsigned grp,
+                                               const double *px, const double *py) {
+    unsigned h = hash_slot(l, mask);
+    double v;
+    for (;;) {
+        const int prev = atomicCAS(&keys[h], -1, l);
+        if (prev == -1) {
+            v = 0.0;
+            break;
+        }
+        if (prev == l) {
+            v = vals[h];
+            break;
+        }
+        h = (h + 1) & mask;
+    }
+    for (unsigned m = grp; m; m &= m - 1) {
+        const int b = __ffs(m) - 1;
+        v = __fma_rn(px[b], py[b], v);
+    }
+    vals[h] = v;
+}
+
+// compact the occupied slots of a table of cap slots to [0, cnt); returns cnt
+__device__ __forceinline__ int compact_table(int *keys, double *vals, unsigned cap, unsigned lane) {
+    int cnt = 0;
+    for (unsigned base = 0; base < cap; base += 32) {
+        const int key = keys[base + lane];
+        const double v = vals[base + lane];
+        const unsigned occ = __ballot_sync(0xffffffffu, key != -1);
+        __syncwarp();
+        if (key != -1) {
+            const int pos = cnt + __popc(occ & ((1u << lane) - 1u));
+            keys[pos] = key;
+            vals[pos] = v;
+        }
+        cnt += __popc(occ);
+        __syncwarp();
+    }
+    return cnt;
+}
+
+template <int R>
+__device__ __forceinline__ void sorted_out(const int *keys, const double *vals, int cnt, int *col, double *val, int lane);
+
+// write the compacted table [0, cnt) sorted by column (cnt <= 32 * RMAX)
+template <int RMAX>
+__device__ __forceinline__ void write_sorted(const int *keys, const double *vals, int cnt, int *col, double *val, int lane) {
+    if (cnt <= 32) sorted_out<1>(keys, vals, cnt, col, val, lane);
+    else if (RMAX >= 2 && cnt <= 64) sorted_out<(RMAX >= 2 ? 2 : 1)>(keys, vals, cnt, col, val, lane);
+    else if (RMAX >= 4 && cnt <= 128) sorted_out<(RMAX >= 4 ? 4 : 1)>(keys, vals, cnt, col, val, lane);
+    else if (RMAX >= 8 && cnt <= 256) sorted_out<(RMAX >= 8 ? 8 : 1)>(keys, vals, cnt, col, val, lane);
+    else if (RMAX >= 16) sorted_out<(RMAX >= 16 ? 16 : 1)>(keys, vals, cnt, col, val, lane);
+}
+
+// Fused (X Y) P for a one-point P. The cnt entries of row (X Y)_a, compacted in [0, cnt), are sorted
+// by column j in registers; the table is cleared and entry (j, z) adds fma(z, p_j, .) to column
+// P(j) in ascending j, 32 entries at a time, grouped by target column as in the product pass: the
+// same sequence of fma as forming X Y and then (X Y) P. Returns the entry count of the result row,
+// written sorted to col/val.
+template <int R>
+__device__ int fused_p_tail(const SpgemmArgs &g, int *keys, double *vals, unsigned cap, int cnt, double *px, double *py,
+                            int *col, double *val, unsigned lane) {
+    int k[R], lk[R];
+    double v[R], pv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + (int)lane;
+        k[r] = e < cnt ? keys[e] : 0x7fffffff;
+        v[r] = e < cnt ? vals[e] : 0.0;
+    }
+    warp_bitonic<R>(k, v, (int)lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        lk[r] = -1;
+        pv[r] = 0.0;
+        if (32 * r + (int)lane < cnt) {
+            const int pb = g.prp[k[r]], pe = g.prp[k[r] + 1];
+            if (pe > pb) {
+                lk[r] = g.pcol[pb];
+                pv[r] = g.pval[pb];
+            }
+        }
+    }
+    __syncwarp();
+    for (unsigned e = lane; e < cap; e += 32) keys[e] = -1;
+    __syncwarp();
+    const unsigned mask = cap - 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (32 * r >= cnt) break;
+        const bool act = lk[r] >= 0;
+        if (act) {
+            px[lane] = v[r];
+            py[lane] = pv[r];
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        __syncwarp();
+        if (act) {
+            const unsigned grp = __match_any_sync(am, lk[r]);
+            if ((int)lane == __ffs(grp) - 1) hash_group_fma(keys, vals, mask, lk[r], grp, px, py);
+        }
+        __syncwarp();
+    }
+    const int cntk = compact_table(keys, vals, cap, lane);
+    write_sorted<R>(keys, vals, cntk, col, val, (int)lane);
+    return cntk;
+}
+
 template <int CAP>
 __host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * (sizeof(double) + sizeof(int)) + SPGEMM_EXTRA; }
 
@@ -88,7 +199,7 @@ __host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * 
 // of a group (the smallest k) applies the group's products in ascending k, so every entry receives its
 // fma updates in ascending k exactly as in a sequential loop. The occupied slots are then compacted
 // and ordered by column with a register bitonic network (rank counting for the largest rows).
-template <int CAP, int WARPS>
+template <int CAP, int WARPS, bool FUSE>
 __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
                                                            const int *__restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -166,24 +277,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
                 __syncwarp();
                 if (act) {
                     const unsigned grp = __match_any_sync(am, l);
-                    if ((int)lane == __ffs(grp) - 1) {
-                        unsigned h = hash_slot(l, mask);
-                        double v;
-                        for (;;) {
-                            int prev = atomicCAS(&keys[h], -1, l);
-                            if (prev == -1) {
-                                v = 0.0;
-                                break;
-                            }
-                            if (prev == l) { v = vals[h]; break; }
-                            h = (h + 1) & mask;
-                        }
-                        for (unsigned m = grp; m; m &= m - 1) {
-                            int b = __ffs(m) - 1;
-                            v = __fma_rn(px[b], py[b], v);
-                        }
-                        vals[h] = v;
-                    }
+                    if ((int)lane == __ffs(grp) - 1) hash_group_fma(keys, vals, mask, l, grp, px, py);
                 }
                 __syncwarp();
                 l = ln;
@@ -193,28 +287,18 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
         }
         __syncwarp();
         const int o = g.off[a];
-        int cnt;
-        // compact occupied slots to the front (positions never pass the slot being read)
-        cnt = 0;
-        for (unsigned base = 0; base < cap; base += 32) {
-            int key = keys[base + lane];
-            double v = vals[base + lane];
-            unsigned occ = __ballot_sync(0xffffffffu, key != -1);
-            __syncwarp();
-            if (key != -1) {
-                int pos = cnt + __popc(occ & ((1u << lane) - 1u));
-                keys[pos] = key;
-                vals[pos] = v;
-            }
-            cnt += __popc(occ);
-            __syncwarp();
-        }
-        if (cnt <= 32) sorted_out<1>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
-        else if (cnt <= 64) sorted_out<2>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
-        else if (CAP >= 256 && cnt <= 128) sorted_out<(CAP >= 256 ? 4 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
-        else if (CAP >= 512 && cnt <= 256) sorted_out<(CAP >= 512 ? 8 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
-        else if (CAP >= 1024 && cnt <= 512) sorted_out<(CAP >= 1024 ? 16 : 1)>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
-        else {
+        int cnt = compact_table(keys, vals, cap, lane);
+        constexpr int RMAX = CAP >= 1024 ? 16 : CAP / 64;
+        if (FUSE) {
+            // rows reach this kernel with cnt <= CAP / 2 <= 32 * RMAX only (the host fuses when every row does)
+            if (cnt <= 32) cnt = fused_p_tail<1>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
+            else if (cnt <= 64) cnt = fused_p_tail<(RMAX >= 2 ? 2 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
+            else if (cnt <= 128) cnt = fused_p_tail<(RMAX >= 4 ? 4 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
+            else if (cnt <= 256) cnt = fused_p_tail<(RMAX >= 8 ? 8 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
+            else cnt = fused_p_tail<(RMAX >= 16 ? 16 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
+        } else if (cnt <= 32 * RMAX) {
+            write_sorted<RMAX>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+        } else {
             // rank counting: the position of a key is the number of smaller keys (keys are unique)
             for (int e = lane; e < cnt; e += 32) {
                 const int key = keys[e];
@@ -324,20 +408,29 @@ void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int
     count_launch();
 }
 
-template <int CAP, int WARPS>
+template <int CAP, int WARPS, bool FUSE>
 static void launch_spgemm_bin(const SpgemmArgs &g, const int *list, const int *count_dev, int count, cudaStream_t s) {
     const size_t bytes = (size_t)WARPS * spgemm_warp_bytes<CAP>();
-    cudaFuncSetAttribute(k_spgemm_warp<CAP, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_spgemm_warp<CAP, WARPS, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     int grid = grid_for(count, WARPS, 152 * 16);
-    k_spgemm_warp<CAP, WARPS><<<grid, 32 * WARPS, bytes, s>>>(g, list, count_dev);
+    k_spgemm_warp<CAP, WARPS, FUSE><<<grid, 32 * WARPS, bytes, s>>>(g, list, count_dev);
     count_launch();
 }
 
+bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]) { return counts_host[2] == 0 && counts_host[3] == 0; }
+
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s) {
-    if (counts_host[0] > 0) launch_spgemm_bin<256, 8>(g, lists, counts_dev, counts_host[0], s);
-    if (counts_host[1] > 0) launch_spgemm_bin<1024, 4>(g, lists + nr, counts_dev + 1, counts_host[1], s);
-    if (counts_host[2] > 0) launch_spgemm_bin<2048, 2>(g, lists + 2 * (size_t)nr, counts_dev + 2, counts_host[2], s);
+    if (g.prp) {
+        // fused one-point P: rows of the two short bins only (checked by spgemm_can_fuse)
+        if (!spgemm_can_fuse(counts_host)) return cudaErrorInvalidValue;
+        if (counts_host[0] > 0) launch_spgemm_bin<256, 8, true>(g, lists, counts_dev, counts_host[0], s);
+        if (counts_host[1] > 0) launch_spgemm_bin<1024, 4, true>(g, lists + nr, counts_dev + 1, counts_host[1], s);
+        return cudaGetLastError();
+    }
+    if (counts_host[0] > 0) launch_spgemm_bin<256, 8, false>(g, lists, counts_dev, counts_host[0], s);
+    if (counts_host[1] > 0) launch_spgemm_bin<1024, 4, false>(g, lists + nr, counts_dev + 1, counts_host[1], s);
+    if (counts_host[2] > 0) launch_spgemm_bin<2048, 2, false>(g, lists + 2 * (size_t)nr, counts_dev + 2, counts_host[2], s);
     if (counts_host[3] > 0) {
         unsigned cap = spgemm_big_cap(ubmax);
         int grid = counts_host[3] < SPGEMM_CTA_GRID ? counts_host[3] : SPGEMM_CTA_GRID;

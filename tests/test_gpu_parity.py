@@ -51,6 +51,9 @@ CASES = {
     "random_theta_cf": ("random", None, dict(distance=2, theta=0.1, theta_cf=0.3, lump_tol=0.01)),
     "fd2d512_auto_blocks": ("adjoint_fd2d_512", None, dict(distance=1)),
     "fd3d_40_auto_blocks": ("fd3d_192", 40, dict(distance=1, rs_block=2048)),
+    # one-point P with dense coarse operators: some R A rows exceed the fused triple-product kernels
+    "fd3d_16_onepoint_d2_nolump": ("fd3d_192", 16, dict(distance=2, interp=1, lump_tol=0.0)),
+    "diffusive_onepoint_d2": ("diffusive", None, dict(distance=2, interp=1, lump_tol=0.0)),
 }
 
 
