@@ -43,8 +43,8 @@ WORKLOADS = {
         opts=dict(distance=1), tol=1e-8, sample_scale=8, batched=True),
     "fd3d_192": dict(
         desc="3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1; "
-             "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
-        opts=dict(distance=1), tol=1e-8, sample_scale=40),
+             "FP32 cycle in FP64 stationary refinement, tol 1e-8",
+        opts=dict(distance=1), tol=1e-8, sample_scale=40, cycle="stationary"),
 }
 L2_FLUSH_BYTES = 512 << 20
 
@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lair", choices=["lair", "reference"])
     p.add_argument("--workload", default="dg_p2_256", choices=sorted(WORKLOADS))
+    p.add_argument("--cycle", default=None, choices=["fgmres", "stationary"],
+                   help="outer iteration (default: the workload's, FGMRES(30))")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -174,7 +176,7 @@ def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
         t0 = time.perf_counter()
         if offs is None:
             H = O.Hierarchy(s, **okw)
-            x, rep = H.solve(s.b, tol=wl["tol"], cycle=1)
+            x, rep = H.solve(s.b, tol=wl["tol"], cycle=0 if wl.get("cycle") == "stationary" else 1)
         else:
             H = O.Hierarchy(s, seg=offs, **okw)
             x, rep = H.solve_batched(s.b, tol=wl["tol"], cycle=1)
@@ -268,6 +270,11 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
+    cycle = lair.FGMRES if (args.cycle or wl.get("cycle", "fgmres")) == "fgmres" else lair.STATIONARY
+    if args.cycle:
+        other = "FP64 stationary refinement" if args.cycle == "stationary" else "FP64 FGMRES(30)"
+        wl = dict(wl, desc=wl["desc"].replace("FP64 FGMRES(30)", other).replace("FP64 stationary refinement", other))
+
     def run_steps(k, precision, timed, host=None):
         """k set-up + solve steps; returns per-step ms (CUDA events on the library stream) and stats."""
         times, its, rels, launches = [], [], [], 0
@@ -287,27 +294,27 @@ def main():
                     evm.record(stream)
                     with torch.cuda.stream(stream):
                         x.zero_()
-                    _, sys_its, rls, st = G.solve_batched(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
+                    _, sys_its, rls, st = G.solve_batched(b, x, tol=wl["tol"], cycle=cycle, max_iter=2000)
                 else:
                     hrp, hcol, hval, hb, hx = host
                     hx.zero_()
                     G = lair.Hierarchy.batched(hrp, hcol, hval, offs, precision=precision, stream=stream, timing=1,
                                                **wl["opts"])
                     evm.record(stream)
-                    _, sys_its, rls, st = G.solve_batched(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=2000)
+                    _, sys_its, rls, st = G.solve_batched(hb, hx, tol=wl["tol"], cycle=cycle, max_iter=2000)
                 rep = lair.Report(st, int(sys_its.max()), float(rls.max()), 0.0, 0.0, 0, 0, 0, 0.0, 0.0)
             elif host is None:
                 G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
                 evm.record(stream)
                 with torch.cuda.stream(stream):
                     x.zero_()
-                _, rep = G.solve(b, x, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
+                _, rep = G.solve(b, x, tol=wl["tol"], cycle=cycle, max_iter=500)
             else:
                 hrp, hcol, hval, hb, hx = host
                 hx.zero_()
                 G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=1, **wl["opts"])
                 evm.record(stream)
-                _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=lair.FGMRES, max_iter=500)
+                _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=cycle, max_iter=500)
             ev1.record(stream)
             ev1.synchronize()
             if rep.status != 0:

@@ -1272,7 +1272,7 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
             // r = b - A x written straight into the cycle's input buffer
             double *r = mixed ? h->wr : L0.b64;
             int tr = tbegin(h, "outer_residual", (double)A.nnz * 12.0 + (double)n * (4.0 + 24.0 + (mixed ? 4.0 : 0.0)));
-            residual(A, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
+            sell_residual(L0.A64, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
             tend(h, tr);
             finish_partials(1, h->part, h->dsc, h->s);
             CU(cudaMemcpyAsync(h->h_dbl, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -1296,7 +1296,7 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
         std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hc(m + 2), y(m + 1);
         // device scalars: |r|^2 at 1, Hessenberg column at 8 (32), the two CGS2 projections at 48 (64), y at 112 (32)
         double *hsum = h->dsc + 8, *hbuf = h->dsc + 48, *nrm = h->dsc + 1, *ydev = h->dsc + 112;
-        residual(A, b, x, V, nullptr, h->part, h->s);
+        sell_residual(L0.A64, b, x, V, nullptr, h->part, h->s);
         finish_partials(1, h->part, nrm, h->s);
         CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
@@ -1359,7 +1359,7 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
             }
             CU(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->s));
             add_combo(n, jdone, Z, n, ydev, x, h->s);
-            residual(A, b, x, V, nullptr, h->part, h->s);
+            sell_residual(L0.A64, b, x, V, nullptr, h->part, h->s);
             finish_partials(1, h->part, nrm, h->s);
             CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
             CU(cudaStreamSynchronize(h->s));

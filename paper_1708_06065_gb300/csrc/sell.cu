@@ -158,6 +158,47 @@ __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__res
     }
 }
 
+// r = b - A x over all rows of an FP64 view of A (optional FP32 copy of r), and the block partial
+// of |r|^2 in part[blockIdx.x] (gridDim.x = RED_PARTS blocks, summed by finish_partials)
+constexpr int RES_THREADS = 512;
+
+__global__ void __launch_bounds__(RES_THREADS) k_sell_residual(SellView v, const double *__restrict__ b,
+                                                               const double *__restrict__ x, double *__restrict__ r,
+                                                               float *__restrict__ r32, double *__restrict__ part) {
+    __shared__ double red[RES_THREADS / 32];
+    const int *__restrict__ sptr = v.slice_ptr;
+    const int *__restrict__ scol = v.col;
+    const double *__restrict__ sval = static_cast<const double *>(v.val);
+    double ss = 0.0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < v.nrows; q += gridDim.x * blockDim.x) {
+        const int sl = q >> 5;
+        const int base = __ldg(sptr + sl) + (q & 31);
+        const int len = (__ldg(sptr + sl + 1) - __ldg(sptr + sl)) >> 5;
+        double acc = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), __ldg(x + __ldg(scol + base + 32 * j)), acc);
+        const int i = v.row[q];
+        const double ri = b[i] - acc;
+        r[i] = ri;
+        if (r32) r32[i] = (float)ri;
+        ss = fma(ri, ri, ss);
+    }
+    for (int o = 16; o >= 1; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RES_THREADS / 32; ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+void sell_residual(const SellView &v, const double *b, const double *x, double *r, float *r32, double *part,
+                   cudaStream_t s) {
+    k_sell_residual<<<RED_PARTS, RES_THREADS, 0, s>>>(v, b, x, r, r32, part);
+    count_launch();
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------

@@ -100,6 +100,9 @@ void sweep(const DCsr &A, const int8_t *cf, int target, const T *dinv, const T *
 template <class T> void dense_apply(int n, const double *Ainv, const T *b, T *y, cudaStream_t s);
 constexpr int RED_PARTS = 152 * 4;
 void residual(const DCsr &A, const double *b, const double *x, double *r, float *r32, double *part, cudaStream_t s);
+// the same over an FP64 sliced-ELL view of all rows (RED_PARTS block partials)
+void sell_residual(const SellView &v, const double *b, const double *x, double *r, float *r32, double *part,
+                   cudaStream_t s);
 void multidot(int n, int m, const double *X, long long ldx, const double *y, double *part, double *out, double *acc,
               cudaStream_t s);
 void finish_partials(int m, const double *part, double *out, cudaStream_t s);

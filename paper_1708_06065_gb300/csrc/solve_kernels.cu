@@ -322,7 +322,7 @@ __device__ __forceinline__ void block_partials(const double (&acc)[MM], int m, d
 }
 
 template <int MM, int PASS>
-__global__ void __launch_bounds__(RED_THREADS) k_cgs_pass(int n, int m, const double *__restrict__ X, long long ldx,
+__global__ void __launch_bounds__(RED_THREADS, MM <= 8 ? RED_BLOCKS / 152 : 1) k_cgs_pass(int n, int m, const double *__restrict__ X, long long ldx,
                                                           const double *__restrict__ h, double *__restrict__ w,
                                                           double *__restrict__ part) {
     double acc[MM];
