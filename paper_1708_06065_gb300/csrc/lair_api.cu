@@ -564,7 +564,9 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(new_counts(h, t, &cnt, nr));
     TRY(t.get(&lists, (size_t)SPGEMM_BINS * nr + 1));
     TRY(new_counts(h, t, &bc, SPGEMM_BINS + 2));
-    launch_spgemm_classify(nr, off, lists, bc, bc + SPGEMM_BINS, h->s);
+    // thread-per-row merging needs many rows to keep the GPU busy; short products stay on warps
+    const bool merge = P == nullptr && nr >= SPGEMM_MERGE_MIN_ROWS;
+    launch_spgemm_classify(nr, off, X.rp, merge, lists, bc, bc + SPGEMM_BINS, h->s);
     // one read-back: bin counts, largest bound, and the total bound (staging size)
     CU(cudaMemcpyAsync(bc + SPGEMM_BINS + 1, off + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
     int hc[SPGEMM_BINS + 2];
@@ -579,7 +581,7 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(t.get(&tval, (size_t)total));
     int *skeys = nullptr;
     double *svals = nullptr;
-    const int nbig = hc[SPGEMM_BINS - 1], ubmax = hc[SPGEMM_BINS];
+    const int nbig = hc[SPGEMM_BIN_CTA], ubmax = hc[SPGEMM_BINS];
     if (nbig > 0) {
         size_t cap = spgemm_big_cap(ubmax);
         size_t slots = 2 * cap * (size_t)(nbig < SPGEMM_CTA_GRID ? nbig : SPGEMM_CTA_GRID);

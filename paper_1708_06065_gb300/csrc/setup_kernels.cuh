@@ -78,9 +78,16 @@ struct SpgemmArgs {
     const double *pval = nullptr;
 };
 constexpr int SPGEMM_CTA_GRID = 152;
-constexpr int SPGEMM_BINS = 4;   // three warp bins by row bound, then the CTA bin
+constexpr int SPGEMM_BINS = 6;      // three warp bins by row bound, the CTA bin, two merge bins
+constexpr int SPGEMM_BIN_CTA = 3;   // rows with a bound beyond the warp kernels
+constexpr int SPGEMM_BIN_MERGE = 4; // rows of X with at most SPGEMM_MERGE_K entries (thread per row)
+constexpr int SPGEMM_BIN_MERGE2 = 5; // rows of X with at most SPGEMM_MERGE_K2 entries (thread per row)
+constexpr int SPGEMM_MERGE_K = 8;
+constexpr int SPGEMM_MERGE_K2 = 32;
+constexpr int SPGEMM_MERGE_MIN_ROWS = 65536;   // products with fewer rows use the warp kernels only
 void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
-void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s);
+void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, int *lists, int *counts, int *ubmax,
+                            cudaStream_t s);
 // true if every row of the product fits the fused one-point-P kernels (bins 0 and 1)
 bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,

@@ -25,18 +25,21 @@ __global__ void k_spgemm_ub(int nr, const int *__restrict__ xrp, const int *__re
     }
 }
 
-// bins by the row's upper bound: 0: ub <= 128 (256 slots), 1: ub <= 512 (1024), 2: ub <= 1024 (2048), 3: larger
+// bins by the row's upper bound: 0: ub <= 128 (256 slots), 1: ub <= 512 (1024), 2: ub <= 1024 (2048), 3: larger;
+// with merge, rows of X with at most SPGEMM_MERGE_K entries go to the merge bin whatever their bound
 __device__ __forceinline__ int spgemm_bin(int u) { return u <= 128 ? 0 : (u <= 512 ? 1 : (u <= WARP_CAP / 2 ? 2 : 3)); }
 
-__global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__restrict__ lists,
-                                  int *__restrict__ counts, int *__restrict__ ubmax) {
+__global__ void k_spgemm_classify(int nr, const int *__restrict__ off, const int *__restrict__ xrp, bool merge,
+                                  int *__restrict__ lists, int *__restrict__ counts, int *__restrict__ ubmax) {
     const unsigned lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; base < nr; base += stride) {
         const int a = (int)(base + lane);
         const bool act = a < nr;
         const int u = act ? off[a + 1] - off[a] : 0;
-        const int b = spgemm_bin(u);
+        const int xl = act ? xrp[a + 1] - xrp[a] : 0;
+        const int b = (merge && xl <= SPGEMM_MERGE_K) ? SPGEMM_BIN_MERGE
+                    : (merge && xl <= SPGEMM_MERGE_K2) ? SPGEMM_BIN_MERGE2 : spgemm_bin(u);
         for (int bb = 0; bb < SPGEMM_BINS; ++bb) {       // one atomic per warp and bin
             const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
             if (!m) continue;
@@ -45,7 +48,56 @@ __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, int *__re
             p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
             if (act && b == bb) lists[(size_t)bb * nr + p0 + __popc(m & ((1u << lane) - 1u))] = a;
         }
-        if (act && b == SPGEMM_BINS - 1) atomicMax(ubmax, u);
+        if (act && b == SPGEMM_BIN_CTA) atomicMax(ubmax, u);
+    }
+}
+
+// One thread per row a of a merge bin: the rows of Y named by the (at most K) entries
+// of row a of X are merged in column order; column j receives fma(x_ak, y_kj, .) for those k in
+// ascending order, starting from 0 -- the same updates in the same order as the hashed kernels,
+// written directly in column order.
+template <int K>
+__global__ void __launch_bounds__(K <= 8 ? 256 : 128) k_spgemm_merge(SpgemmArgs g, const int *__restrict__ list,
+                                                                     const int *__restrict__ count) {
+    const int n = *count;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int a = list[t];
+        const int xb = g.xrp[a], nk = g.xrp[a + 1] - xb;
+        int pos[K], end[K], cj[K];
+        double xv[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            pos[u] = 0;
+            end[u] = 0;
+            xv[u] = 0.0;
+            if (u < nk) {
+                const int k = g.xcol[xb + u];
+                pos[u] = g.yrp[k];
+                end[u] = g.yrp[k + 1];
+                xv[u] = g.xval[xb + u];
+            }
+            cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
+        }
+        const int o = g.off[a];
+        int c = 0;
+        for (;;) {
+            int j = 0x7fffffff;
+#pragma unroll
+            for (int u = 0; u < K; ++u) j = min(j, cj[u]);
+            if (j == 0x7fffffff) break;
+            double v = 0.0;
+#pragma unroll
+            for (int u = 0; u < K; ++u)
+                if (cj[u] == j) {
+                    v = __fma_rn(xv[u], g.yval[pos[u]], v);
+                    ++pos[u];
+                    cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
+                }
+            g.tcol[o + c] = j;
+            g.tval[o + c] = v;
+            ++c;
+        }
+        g.cnt[a] = c;
     }
 }
 
@@ -403,8 +455,9 @@ void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, i
     count_launch();
 }
 
-void launch_spgemm_classify(int nr, const int *off, int *lists, int *counts, int *ubmax, cudaStream_t s) {
-    k_spgemm_classify<<<grid_for(nr, 256), 256, 0, s>>>(nr, off, lists, counts, ubmax);
+void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, int *lists, int *counts, int *ubmax,
+                            cudaStream_t s) {
+    k_spgemm_classify<<<grid_for(nr, 256), 256, 0, s>>>(nr, off, xrp, merge, lists, counts, ubmax);
     count_launch();
 }
 
@@ -417,7 +470,10 @@ static void launch_spgemm_bin(const SpgemmArgs &g, const int *list, const int *c
     count_launch();
 }
 
-bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]) { return counts_host[2] == 0 && counts_host[3] == 0; }
+bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]) {
+    return counts_host[2] == 0 && counts_host[SPGEMM_BIN_CTA] == 0 && counts_host[SPGEMM_BIN_MERGE] == 0 &&
+           counts_host[SPGEMM_BIN_MERGE2] == 0;
+}
 
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s) {
@@ -431,10 +487,21 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
     if (counts_host[0] > 0) launch_spgemm_bin<256, 8, false>(g, lists, counts_dev, counts_host[0], s);
     if (counts_host[1] > 0) launch_spgemm_bin<1024, 4, false>(g, lists + nr, counts_dev + 1, counts_host[1], s);
     if (counts_host[2] > 0) launch_spgemm_bin<2048, 2, false>(g, lists + 2 * (size_t)nr, counts_dev + 2, counts_host[2], s);
-    if (counts_host[3] > 0) {
+    if (counts_host[SPGEMM_BIN_CTA] > 0) {
         unsigned cap = spgemm_big_cap(ubmax);
-        int grid = counts_host[3] < SPGEMM_CTA_GRID ? counts_host[3] : SPGEMM_CTA_GRID;
-        k_spgemm_cta<<<grid, 256, 0, s>>>(g, lists + 3 * (size_t)nr, counts_dev + 3, skeys, svals, cap);
+        int grid = counts_host[SPGEMM_BIN_CTA] < SPGEMM_CTA_GRID ? counts_host[SPGEMM_BIN_CTA] : SPGEMM_CTA_GRID;
+        k_spgemm_cta<<<grid, 256, 0, s>>>(g, lists + SPGEMM_BIN_CTA * (size_t)nr, counts_dev + SPGEMM_BIN_CTA, skeys,
+                                          svals, cap);
+        count_launch();
+    }
+    if (counts_host[SPGEMM_BIN_MERGE] > 0) {
+        k_spgemm_merge<SPGEMM_MERGE_K><<<grid_for(counts_host[SPGEMM_BIN_MERGE], 256, 152 * 16), 256, 0, s>>>(
+            g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE);
+        count_launch();
+    }
+    if (counts_host[SPGEMM_BIN_MERGE2] > 0) {
+        k_spgemm_merge<SPGEMM_MERGE_K2><<<grid_for(counts_host[SPGEMM_BIN_MERGE2], 128, 152 * 32), 128, 0, s>>>(
+            g, lists + SPGEMM_BIN_MERGE2 * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE2);
         count_launch();
     }
     return cudaGetLastError();
