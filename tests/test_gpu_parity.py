@@ -237,6 +237,62 @@ def test_adjoint_gradients(lair):
         assert fd_v == pytest.approx(float(vals.grad.cpu().numpy() @ dv), rel=1e-5)
 
 
+def test_adjoint_gradients_full_size(lair):
+    """The adjoint workload at full size (512 x 512 upwind FD, n = 262,144): grad_b and grad_A
+    against an FP64 sparse LU of A, and central finite differences of J along 64 random
+    directions of b and 64 random directions of the nonzeros of A."""
+    import torch
+    import scipy.sparse.linalg as spla
+    from paper_1708_06065_gb300 import autograd
+    s = W.config("adjoint_fd2d_512")
+    assert s.n == 262144
+    xs = s.meta["x_star"]
+    rp = torch.from_numpy(s.row_ptr).cuda()
+    col = torch.from_numpy(s.col).cuda()
+    vals = torch.from_numpy(s.val).cuda().requires_grad_(True)
+    b = torch.from_numpy(s.b).cuda().requires_grad_(True)
+    x = autograd.solve(rp, col, vals, b, tol=1e-12)
+    J = 0.5 * ((x - torch.from_numpy(xs).cuda()) ** 2).sum()
+    J.backward()
+    A = s.to_scipy().tocsc()
+    lu = spla.splu(A)
+    xd = lu.solve(s.b)
+    lam = lu.solve(xd - xs, trans="T")
+    gb = b.grad.cpu().numpy()
+    gv = vals.grad.cpu().numpy()
+    np.testing.assert_allclose(gb, lam, rtol=0, atol=1e-8 * np.abs(lam).max())
+    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+    gA = -lam[rows] * xd[s.col]
+    np.testing.assert_allclose(gv, gA, rtol=0, atol=1e-8 * np.abs(gA).max())
+    rng = np.random.default_rng(64)
+    # J is quadratic in b, so a central difference in b is exact for any step (h_b = 1 keeps the
+    # cancellation small); in the nonzeros of A, h_v = 1e-5 balances truncation against rounding
+    h_b, h_v = 1.0, 1e-5
+
+    def Jb(bb):
+        return 0.5 * np.sum((lu.solve(bb) - xs) ** 2)
+
+    for _ in range(64):
+        db = rng.standard_normal(s.n)
+        fd = (Jb(s.b + h_b * db) - Jb(s.b - h_b * db)) / (2 * h_b)
+        assert fd == pytest.approx(float(gb @ db), rel=1e-5)
+
+    def Jv(v):
+        # (A + h dA) x = b by refinement on the LU of A: the perturbation is O(h), so a few steps
+        # reach rounding level
+        Ad = sp.csr_matrix((v, s.col, s.row_ptr), shape=(s.n, s.n))
+        xx = xd.copy()
+        for _ in range(6):
+            xx += lu.solve(s.b - Ad @ xx)
+        assert np.linalg.norm(s.b - Ad @ xx) <= 1e-13 * np.linalg.norm(s.b)
+        return 0.5 * np.sum((xx - xs) ** 2)
+
+    for _ in range(64):
+        dv = rng.standard_normal(len(s.val)) * np.abs(s.val)
+        fd = (Jv(s.val + h_v * dv) - Jv(s.val - h_v * dv)) / (2 * h_v)
+        assert fd == pytest.approx(float(gv @ dv), rel=1e-5)
+
+
 def test_adjoint_hierarchy_matches_oracle_on_transpose(lair):
     s = W.config("fd2d_64", scale=40)
     G = lair.Hierarchy.from_system(s)
