@@ -227,6 +227,27 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def hierarchy_stats(last):
+    """Level sizes, coarsening factors, operator and cycle complexity, the mean convergence factor
+    and the work per digit (cycle complexity / -log10 of the convergence factor) of one step."""
+    import math
+    info, rep = last.get("info") or [], last.get("rep")
+    if not info:
+        return None
+    n = [lv["n"] for lv in info]
+    out = {"levels": len(info), "n": n, "nnz": [lv["nnz"] for lv in info],
+           "coarsening": [round(n[l] / n[l + 1], 3) for l in range(len(n) - 1)],
+           "op_complexity": round(sum(lv["nnz"] for lv in info) / info[0]["nnz"], 4)}
+    if rep is not None and rep.cycle_complexity > 0:
+        out["cycle_complexity"] = round(rep.cycle_complexity, 4)
+    if rep is not None and rep.iters > 0 and rep.final_rel > 0:
+        rho = rep.final_rel ** (1.0 / rep.iters)
+        out["conv_factor"] = round(rho, 5)
+        if rho < 1 and "cycle_complexity" in out:
+            out["work_per_digit"] = round(out["cycle_complexity"] / -math.log10(rho), 4)
+    return out
+
+
 def load_traffic(kernel, workload):
     """ncu dram bytes per launch from the committed profile summary, if one matches."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
@@ -279,6 +300,7 @@ def main():
         """k set-up + solve steps; returns per-step ms (CUDA events on the library stream) and stats."""
         times, its, rels, launches = [], [], [], 0
         setup_ms = []
+        last = {}
         timers = {}
         for i in range(k):
             with torch.cuda.stream(stream):
@@ -324,11 +346,13 @@ def main():
             its.append(rep.iters)
             rels.append(rep.final_rel)
             launches += G.launches
+            last = dict(rep=rep, info=G.info())
             for name, (cnt, ms, byt) in G.timers().items():
                 t = timers.setdefault(name, [0, 0.0, byt])
                 t[0] += cnt
                 t[1] += ms
             G.close()
+        run_steps.last = last
         return times, its, rels, launches, timers, setup_ms
 
     # ---- mixed precision (the headline), device-resident inputs
@@ -338,6 +362,7 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     t_mixed, it_mixed, rel_mixed, launches, timers, su_mixed = run_steps(args.steps, lair.MIXED, True)
+    hier = hierarchy_stats(run_steps.last)
     torch.cuda.synchronize()
     clk = clocks.stop()
     dist.barrier()
@@ -397,6 +422,7 @@ def main():
         "fp64": {"value": dist.world * n / (ms64 / 1e3), "ms_per_step": ms64, "setup_ms": dist.max(sum(su64) / len(su64)),
                  "iters": it64, "final_rel": max(rel64)},
         "mixed_over_fp64": ms64 / ms_mixed,
+        "hierarchy": hier,
         "setup_phases_ms": {k[len("setup_"):]: v[1] / args.steps for k, v in timers.items() if k.startswith("setup_")},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,

@@ -188,6 +188,95 @@ __device__ __forceinline__ void write_sorted(const int *keys, const double *vals
     else if (RMAX >= 16) sorted_out<(RMAX >= 16 ? 16 : 1)>(keys, vals, cnt, col, val, lane);
 }
 
+// Loads the compacted entries [0, cnt) of a row table of cap slots into registers (entry
+// e = 32 r + lane in kk[r], vv[r]; padding INT_MAX / 0) and finds each entry's rank by column
+// through a bitmap of the row's column span kept in the free upper half of the table
+// (cnt <= cap / 2): bitmap words in vals[cap/2, cap), word prefix counts in keys[cap/2, cap).
+// Lane l owns words l, l + 32, ..., so neither pass has bank conflicts. Returns false (ranks not
+// set, registers loaded) when the span exceeds 32 cap columns.
+template <int R>
+__device__ __forceinline__ bool bitmap_ranks(int *keys, double *vals, int cnt, unsigned cap, int lane, int (&kk)[R],
+                                             double (&vv)[R], int (&pos)[R]) {
+    int mn = 0x7fffffff, mx = -1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        kk[r] = e < cnt ? keys[e] : 0x7fffffff;
+        vv[r] = e < cnt ? vals[e] : 0.0;
+        if (e < cnt) {
+            mn = min(mn, kk[r]);
+            mx = max(mx, kk[r]);
+        }
+    }
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (cnt == 0) return true;
+    if ((long long)mx - mn >= 32ll * cap) return false;
+    const int used = ((mx - mn) >> 5) + 1;
+    unsigned *bm = reinterpret_cast<unsigned *>(vals + cap / 2);
+    unsigned short *pre = reinterpret_cast<unsigned short *>(keys + cap / 2);
+    __syncwarp();
+    for (int w = lane; w < used; w += 32) bm[w] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (32 * r + lane < cnt) {
+            const int d = kk[r] - mn;
+            atomicOr(&bm[d >> 5], 1u << (d & 31));
+        }
+    __syncwarp();
+    int carry = 0;
+    for (int base = 0; base < used; base += 32) {
+        const int w = base + lane;
+        const int c = w < used ? __popc(bm[w]) : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (w < used) pre[w] = (unsigned short)(carry + incl - c);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        pos[r] = 0;
+        if (32 * r + lane < cnt) {
+            const int d = kk[r] - mn;
+            pos[r] = pre[d >> 5] + __popc(bm[d >> 5] & ((1u << (d & 31)) - 1u));
+        }
+    }
+    return true;
+}
+
+// write the compacted table [0, cnt) ordered by column: bitmap ranks for rows of up to 128 entries
+// whose column span allows it, the bitonic network otherwise
+template <int RMAX>
+__device__ __forceinline__ void write_ordered(int *keys, double *vals, int cnt, unsigned cap, int *col, double *val,
+                                              int lane) {
+    if (cnt <= 128) {
+        bool done = false;
+        if (cnt <= 32) {
+            int kk[1], pos[1];
+            double vv[1];
+            if ((done = bitmap_ranks<1>(keys, vals, cnt, cap, lane, kk, vv, pos)))
+                if (lane < cnt) { col[pos[0]] = kk[0]; val[pos[0]] = vv[0]; }
+        } else {
+            int kk[4], pos[4];
+            double vv[4];
+            if ((done = bitmap_ranks<4>(keys, vals, cnt, cap, lane, kk, vv, pos))) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (32 * r + lane < cnt) { col[pos[r]] = kk[r]; val[pos[r]] = vv[r]; }
+            }
+        }
+        if (done) return;
+        __syncwarp();
+    }
+    write_sorted<RMAX>(keys, vals, cnt, col, val, lane);
+}
+
 // Fused (X Y) P for a one-point P. The cnt entries of row (X Y)_a, compacted in [0, cnt), are sorted
 // by column j in registers; the table is cleared and entry (j, z) adds fma(z, p_j, .) to column
 // P(j) in ascending j, 32 entries at a time, grouped by target column as in the product pass: the
@@ -198,13 +287,36 @@ __device__ int fused_p_tail(const SpgemmArgs &g, int *keys, double *vals, unsign
                             int *col, double *val, unsigned lane) {
     int k[R], lk[R];
     double v[R], pv[R];
+    bool ranked = false;
+    if (R <= 4) {
+        int pos[R];
+        ranked = bitmap_ranks<R>(keys, vals, cnt, cap, (int)lane, k, v, pos);
+        if (ranked) {
+            // permute in place through the registers, then read back in column order
+            __syncwarp();
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = 32 * r + (int)lane;
-        k[r] = e < cnt ? keys[e] : 0x7fffffff;
-        v[r] = e < cnt ? vals[e] : 0.0;
+            for (int r = 0; r < R; ++r)
+                if (32 * r + (int)lane < cnt) {
+                    keys[pos[r]] = k[r];
+                    vals[pos[r]] = v[r];
+                }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = 32 * r + (int)lane;
+                k[r] = e < cnt ? keys[e] : 0x7fffffff;
+                v[r] = e < cnt ? vals[e] : 0.0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = 32 * r + (int)lane;
+            k[r] = e < cnt ? keys[e] : 0x7fffffff;
+            v[r] = e < cnt ? vals[e] : 0.0;
+        }
     }
-    warp_bitonic<R>(k, v, (int)lane);
+    if (!ranked) warp_bitonic<R>(k, v, (int)lane);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         lk[r] = -1;
@@ -238,7 +350,7 @@ __device__ int fused_p_tail(const SpgemmArgs &g, int *keys, double *vals, unsign
         __syncwarp();
     }
     const int cntk = compact_table(keys, vals, cap, lane);
-    write_sorted<R>(keys, vals, cntk, col, val, (int)lane);
+    write_ordered<R>(keys, vals, cntk, cap, col, val, (int)lane);
     return cntk;
 }
 
@@ -252,7 +364,7 @@ __host__ __device__ constexpr size_t spgemm_warp_bytes() { return (size_t)CAP * 
 // fma updates in ascending k exactly as in a sequential loop. The occupied slots are then compacted
 // and ordered by column with a register bitonic network (rank counting for the largest rows).
 template <int CAP, int WARPS, bool FUSE>
-__global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
+__global__ void __launch_bounds__(32 * WARPS, CAP == 256 ? 6 : 1) k_spgemm_warp(SpgemmArgs g, const int *__restrict__ list,
                                                            const int *__restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5;
@@ -349,7 +461,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_spgemm_warp(SpgemmArgs g, const 
             else if (cnt <= 256) cnt = fused_p_tail<(RMAX >= 8 ? 8 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
             else cnt = fused_p_tail<(RMAX >= 16 ? 16 : 1)>(g, keys, vals, cap, cnt, px, py, g.tcol + o, g.tval + o, lane);
         } else if (cnt <= 32 * RMAX) {
-            write_sorted<RMAX>(keys, vals, cnt, g.tcol + o, g.tval + o, lane);
+            write_ordered<RMAX>(keys, vals, cnt, cap, g.tcol + o, g.tval + o, lane);
         } else {
             // rank counting: the position of a key is the number of smaller keys (keys are unique)
             for (int e = lane; e < cnt; e += 32) {
