@@ -1,6 +1,8 @@
 // setup_graph.cu -- strength of connection, strength graphs, C/F splitting,
 // coarse numbering and restriction neighbourhoods (the integer part of the
 // lAIR set-up, Sec. 3.1 and Sec. 4).
+#include <cooperative_groups.h>
+
 #include "setup_kernels.cuh"
 
 namespace lair {
@@ -283,6 +285,8 @@ __device__ bool grid_barrier(int *ctl, int *status) {
 
 // true if w_i beats the weight of every undecided j among col[b..e) (decided points carry
 // weight -1); the neighbours are read four at a time so that their loads overlap
+// (L2: the weights are read from L2, past this SM's L1, as other CTAs update them between rounds)
+template <bool L2 = false>
 __device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, const int *__restrict__ col,
                                                const double *w) {
     for (int p = b; p < e; p += 4) {
@@ -291,7 +295,7 @@ __device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, c
 #pragma unroll
         for (int u = 0; u < 4; ++u) j[u] = p + u < e ? col[p + u] : -1;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) wj[u] = j[u] >= 0 ? w[j[u]] : -1.0;
+        for (int u = 0; u < 4; ++u) wj[u] = j[u] >= 0 ? (L2 ? __ldcg(w + j[u]) : w[j[u]]) : -1.0;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (wj[u] >= 0.0 && !beats(wi, i, wj[u], j[u])) return false;
@@ -300,6 +304,51 @@ __device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, c
 }
 
 constexpr int PMIS_THREADS = 1024;   // one CTA per SM keeps the grid barrier short
+constexpr int PMIS_CLUSTER = 8;      // levels of at most 8 * 1024 points: one cluster, one point per thread
+
+// The PMIS rounds of a small level in one thread-block cluster: the same rounds as k_pmis_coop,
+// with the hardware cluster barrier between the passes. Counts of undecided points are summed
+// through distributed shared memory; weights and markers written by other CTAs are read from L2.
+__global__ void __launch_bounds__(PMIS_THREADS) k_pmis_cluster(int n, Graph S, Graph ST, double *w,
+                                                      int8_t *__restrict__ cf, int8_t *__restrict__ newc) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ int cnt_sh;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned ncta = cluster.num_blocks();
+    for (int round = 0; round <= n; ++round) {
+        int und = 0;
+        int8_t nc = 0;
+        if (i < n) {
+            const double wi = __ldcg(w + i);
+            if (wi >= 0.0) {
+                und = 1;
+                nc = pmis_beats_all<true>(wi, i, S.rp[i], S.rp[i + 1], S.col, w) &&
+                     pmis_beats_all<true>(wi, i, ST.rp[i], ST.rp[i + 1], ST.col, w);
+            }
+        }
+        und = __syncthreads_count(und);
+        if (threadIdx.x == 0) cnt_sh = und;
+        cluster.sync();
+        int total = 0;
+        for (unsigned r = 0; r < ncta; ++r) total += *cluster.map_shared_rank(&cnt_sh, r);
+        if (total == 0) break;
+        if (nc) {
+            cf[i] = CF_C;
+            w[i] = -1.0;
+            for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) {
+                const int j = ST.col[p];
+                if (__ldcg(cf + j) == CF_U) {
+                    cf[j] = CF_F;
+                    w[j] = -1.0;
+                }
+            }
+        }
+        __threadfence();
+        cluster.sync();
+    }
+    cluster.sync();   // no CTA leaves while another may still read its counter
+}
 
 __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Graph ST, double *w,
                                                    int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
@@ -313,8 +362,8 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Grap
             const double wi = w[i];
             if (wi >= 0.0) {
                 ++local;
-                nc = pmis_beats_all(wi, i, S.rp[i], S.rp[i + 1], S.col, w) &&
-                     pmis_beats_all(wi, i, ST.rp[i], ST.rp[i + 1], ST.col, w);
+                nc = pmis_beats_all<false>(wi, i, S.rp[i], S.rp[i + 1], S.col, w) &&
+                     pmis_beats_all<false>(wi, i, ST.rp[i], ST.rp[i + 1], ST.col, w);
             }
             newc[i] = nc;
         }
@@ -764,6 +813,25 @@ void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *
 // ctl: 4 ints, zero
 cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
                             int *status, cudaStream_t s) {
+    if (n <= PMIS_CLUSTER * PMIS_THREADS) {
+        const int c = n > 0 ? (n + PMIS_THREADS - 1) / PMIS_THREADS : 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(PMIS_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_pmis_cluster, n, S, ST, w, cf, newc) == cudaSuccess) {
+            count_launch();
+            return cudaSuccess;
+        }
+        cudaGetLastError();   // not launchable here: use the grid-wide version
+    }
     int dev = 0, per_sm = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pmis_coop, PMIS_THREADS, 0);
