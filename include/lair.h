@@ -102,7 +102,8 @@ typedef struct {
     uint64_t pmis_seed;
     int fgmres_restart;
     void *stream;             /* cudaStream_t, or NULL (see above); never the legacy default stream itself */
-    int timing;               /* 1: record CUDA-event timings of the main kernels (lair_kernel_timers) */
+    int timing;               /* 1: record CUDA-event timings of the main kernels and set-up phases
+                                 (lair_kernel_timers); 2: also one timer per set-up phase and level */
 } lair_options;
 
 typedef struct {

@@ -353,6 +353,13 @@ static cudaEvent_t get_event(lair_handle *h) {
 
 // begin/end around one launch; in_graph: the events become nodes of the graph being captured
 // returns the index of the event pair (for tend), or -1 when timing is off
+// set-up phase timer name; with timing >= 2 every level gets its own timer
+static std::string phase_name(const lair_handle *h, const char *phase, int level) {
+    std::string s = std::string("setup_") + phase;
+    if (h->o.timing >= 2 && level >= 0) s += "_L" + std::to_string(level);
+    return s;
+}
+
 static int tbegin(lair_handle *h, const std::string &name, double bytes, bool in_graph = false) {
     if (!h->o.timing) return -1;
     int slot = timer_slot(h, name, bytes);
@@ -551,8 +558,10 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
 // Z = X Y, or Z = X Y P when P (one-point: at most one entry per row) is given; the triple product is
 // formed in one pass when every row of X Y fits the short-row kernels, else as (X Y) P.
 // timed (0 or 1): the product's row pass is timed as "L0_RA" / "L0_RAP" and its entry count kept
+// With stage_len, Z is left in the staging area (not compacted): row a is Z.col/Z.val[Z.rp[a],
+// Z.rp[a] + (*stage_len)[a]); Z.nnz is then only the capacity.
 static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y, DCsr &Z, bool keep, int timed = -1,
-                          const DCsr *P = nullptr) {
+                          const DCsr *P = nullptr, int **stage_len = nullptr) {
     const int nr = X.nr;
     int *ub, *off;
     TRY(new_counts(h, t, &ub, nr));
@@ -575,7 +584,7 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     if (P && !spgemm_can_fuse(hc)) {
         DCsr XY;
         TRY(spgemm(h, t, X, Y, XY, false, timed >= 0 ? 0 : -1));
-        return spgemm(h, t, XY, *P, Z, keep, timed >= 0 ? 1 : -1);
+        return spgemm(h, t, XY, *P, Z, keep, timed >= 0 ? 1 : -1, nullptr, stage_len);
     }
     TRY(t.get(&tcol, (size_t)total));
     TRY(t.get(&tval, (size_t)total));
@@ -601,6 +610,22 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     tend(h, tp);
     Z.nr = nr;
     Z.nc = P ? P->nc : Y.nc;
+    if (stage_len && !keep) {
+        Z.rp = off;
+        Z.col = tcol;
+        Z.val = tval;
+        Z.nnz = total;
+        *stage_len = cnt;
+        if (timed >= 0 && h->o.timing) {
+            // the exact entry count, for the byte model
+            int *cs;
+            TRY(t.get(&cs, (size_t)nr + 1));
+            TRY(scan(h, cnt, cs, nr, nullptr));
+            if (!h->prod_nnz) TRY(dalloc(h, &h->prod_nnz, 2));
+            CU(cudaMemcpyAsync(h->prod_nnz + timed, cs + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
+        }
+        return LAIR_OK;
+    }
     if (keep) TRY(dalloc(h, &Z.rp, (size_t)nr + 1)); else TRY(t.get(&Z.rp, (size_t)nr + 1));
     // a kept product is stored at its exact size; a temporary one at the bound (its entry count
     // is then only a capacity and is not read back)
@@ -635,7 +660,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     const int n = A.nr;
     const bool fp32 = o.precision == LAIR_MIXED;
 
-    int tp = tbegin(h, "setup_strength", 0.0);
+    int tp = tbegin(h, phase_name(h, "strength", l), 0.0);
     TRY(dalloc(h, &L.strong, (size_t)A.nnz));
     Graph S, ST, Scf, STcf;
     TRY(build_strength_graph(h, t, A, o.theta, L.strong, S));
@@ -656,7 +681,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
 
     // ---- C/F splitting
     tend(h, tp);
-    tp = tbegin(h, "setup_split", 0.0);
+    tp = tbegin(h, phase_name(h, "split", l), 0.0);
     TRY(dalloc(h, &L.cf, (size_t)n));
     if (cf_user) {
         CU(cudaMemcpyAsync(L.cf, cf_user, (size_t)n, cudaMemcpyHostToDevice, h->s));
@@ -737,7 +762,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
 
     // ---- restriction (lAIR): local systems of A on the neighbourhoods in S
     tend(h, tp);
-    tp = tbegin(h, "setup_R", 0.0);
+    tp = tbegin(h, phase_name(h, "R", l), 0.0);
     TRY(dalloc(h, &L.lsR, (size_t)nc));
     L.R.nr = nc;
     L.R.nc = n;
@@ -746,7 +771,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
 
     // ---- interpolation
     tend(h, tp);
-    tp = tbegin(h, "setup_P", 0.0);
+    tp = tbegin(h, phase_name(h, "P", l), 0.0);
     L.P.nr = n;
     L.P.nc = nc;
     if (o.interp == LAIR_P_ONEPOINT) {
@@ -784,14 +809,15 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
 
     // ---- Galerkin product and lumping
     tend(h, tp);
-    tp = tbegin(h, "setup_RAP", 0.0);
+    tp = tbegin(h, phase_name(h, "RAP", l), 0.0);
     DCsr RA, K;
     const bool lump = o.lump_tol > 0.0;
+    int *klen = nullptr;   // with lumping, K stays in the product's staging area (rows of length klen)
     if (o.interp == LAIR_P_ONEPOINT) {
-        TRY(spgemm(h, t, L.R, A, K, !lump, l == 0 ? 1 : -1, &L.P));
+        TRY(spgemm(h, t, L.R, A, K, !lump, l == 0 ? 1 : -1, &L.P, lump ? &klen : nullptr));
     } else {
         TRY(spgemm(h, t, L.R, A, RA, false, l == 0 ? 0 : -1));
-        TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1));
+        TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1, nullptr, lump ? &klen : nullptr));
     }
     Level next;
     if (lump) {
@@ -799,14 +825,14 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         double *nd;
         TRY(new_counts(h, t, &cnt, K.nr));
         TRY(t.get(&nd, (size_t)K.nr));
-        launch_lump(0, K, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
+        launch_lump(0, K, klen, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
         DCsr Kl;
         Kl.nr = Kl.nc = K.nr;
         TRY(dalloc(h, &Kl.rp, (size_t)K.nr + 1));
         TRY(scan(h, cnt, Kl.rp, K.nr, &Kl.nnz));
         TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
         TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
-        launch_lump(1, K, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
+        launch_lump(1, K, klen, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
         next.A = Kl;
     } else {
         next.A = K;
@@ -948,7 +974,7 @@ static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan>
 }
 
 static lair_status finish_level(lair_handle *h, Hier &H, int l) {
-    const int tp = tbegin(h, "setup_finish", 0.0);
+    const int tp = tbegin(h, phase_name(h, "finish", l), 0.0);
     Level &L = H.lev[l];
     const int n = L.A.nr;
     const bool fp32 = h->o.precision == LAIR_MIXED;
@@ -1091,14 +1117,14 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             double *nd;
             TRY(new_counts(h, t, &cnt, A.nr));
             TRY(t.get(&nd, (size_t)A.nr));
-            launch_lump(0, A, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
+            launch_lump(0, A, nullptr, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
             DCsr Kl;
             Kl.nr = Kl.nc = A.nr;
             TRY(dalloc(h, &Kl.rp, (size_t)A.nr + 1));
             TRY(scan(h, cnt, Kl.rp, A.nr, &Kl.nnz));
             TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
             TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
-            launch_lump(1, A, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
+            launch_lump(1, A, nullptr, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
             TRY(sync_status(h));
             A = Kl;
         }

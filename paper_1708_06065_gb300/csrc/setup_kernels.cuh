@@ -94,8 +94,9 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s);
 unsigned spgemm_big_cap(int ubmax);
 void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tval, DCsr &Z, cudaStream_t s);
-void launch_lump(int phase, const DCsr &K, double tol, int *cnt, double *newdiag, const DCsr *out, int *status,
-                 cudaStream_t s);
+// K's rows: rp[i] .. rp[i + 1], or rp[i] .. rp[i] + len[i] when len is given
+void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
+                 int *status, cudaStream_t s);
 void launch_dinv(const DCsr &A, double *dinv, float *dinv32, int *status, cudaStream_t s);
 void launch_to_f32(long long n, const double *a, float *b, cudaStream_t s);
 void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s);

@@ -634,10 +634,13 @@ void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tva
 // lumping (Sec. 3.3): in row i drop every off-diagonal with |k_ij| < theta_D * max_j |k_ij|
 // (max over the whole row) and add it to k_ii, in ascending j, starting from k_ii.
 // ---------------------------------------------------------------------------------------
-__global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
-                             double tol, int *__restrict__ cnt, double *__restrict__ newdiag, int *status) {
+// Row i of K is col/val[rp[i], rp[i + 1]) or, when len is given, col/val[rp[i], rp[i] + len[i]) (the
+// staging area of a product that was not compacted).
+__global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__restrict__ len, const int *__restrict__ col,
+                             const double *__restrict__ val, double tol, int *__restrict__ cnt,
+                             double *__restrict__ newdiag, int *status) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int b = rp[i], e = rp[i + 1];
+        int b = rp[i], e = len ? b + len[i] : rp[i + 1];
         double m = 0.0;
         for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
         double thr = __dmul_rn(tol, m);
@@ -656,11 +659,11 @@ __global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__res
     }
 }
 
-__global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ val,
-                            double tol, const double *__restrict__ newdiag, const int *__restrict__ orp,
-                            int *__restrict__ ocol, double *__restrict__ oval) {
+__global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__restrict__ len, const int *__restrict__ col,
+                            const double *__restrict__ val, double tol, const double *__restrict__ newdiag,
+                            const int *__restrict__ orp, int *__restrict__ ocol, double *__restrict__ oval) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int b = rp[i], e = rp[i + 1];
+        int b = rp[i], e = len ? b + len[i] : rp[i + 1];
         double m = 0.0;
         for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
         double thr = __dmul_rn(tol, m);
@@ -674,12 +677,13 @@ __global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__rest
     }
 }
 
-void launch_lump(int phase, const DCsr &K, double tol, int *cnt, double *newdiag, const DCsr *out, int *status,
-                 cudaStream_t s) {
+void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
+                 int *status, cudaStream_t s) {
     if (phase == 0)
-        k_lump_count<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, K.col, K.val, tol, cnt, newdiag, status);
+        k_lump_count<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, tol, cnt, newdiag, status);
     else
-        k_lump_fill<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, K.col, K.val, tol, newdiag, out->rp, out->col, out->val);
+        k_lump_fill<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, tol, newdiag, out->rp, out->col,
+                                                         out->val);
     count_launch();
 }
 
