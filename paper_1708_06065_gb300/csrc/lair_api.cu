@@ -113,6 +113,7 @@ struct lair_handle {
     double *d_bat = nullptr;      // device, nseg * (3 * 32 + 1) doubles: sums, pass values, y, norms
     int *d_batcnt = nullptr;      // device, nseg ints
     int *h_batcnt = nullptr;      // pinned, nseg ints
+    lair::SegTiles segt;          // row tiles of the systems (level 0), built at the first batched solve
 };
 
 namespace lair {
@@ -1410,6 +1411,36 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
     return st;
 }
 
+// row tiles of the batch's systems at level 0 (SEG_TILE rows at most, never across systems)
+static lair_status ensure_tiles(lair_handle *h, const Level &L0) {
+    if (h->segt.tile) return LAIR_OK;
+    const std::vector<int> &seg = L0.seg_h;
+    const int nseg = (int)seg.size() - 1;
+    std::vector<int4> tiles;
+    std::vector<int> first(nseg + 1);
+    for (int q = 0; q < nseg; ++q) {
+        first[q] = (int)tiles.size();
+        for (int b0 = seg[q]; b0 < seg[q + 1]; b0 += SEG_TILE)
+            tiles.push_back(make_int4(q, b0, b0 + SEG_TILE < seg[q + 1] ? b0 + SEG_TILE : seg[q + 1], 0));
+    }
+    first[nseg] = (int)tiles.size();
+    int4 *dt;
+    int *df;
+    double *dp;
+    TRY(dalloc(h, &dt, tiles.size() + 1));
+    TRY(dalloc(h, &df, (size_t)nseg + 1));
+    TRY(dalloc(h, &dp, (tiles.size() + 1) * (size_t)SEG_TILE_PARTS));
+    if (!tiles.empty()) CU(cudaMemcpyAsync(dt, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, h->s));
+    CU(cudaMemcpyAsync(df, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, h->s));
+    CU(cudaStreamSynchronize(h->s));   // the host vectors are copied from pageable memory
+    h->segt.tile = dt;
+    h->segt.ntiles = (int)tiles.size();
+    h->segt.first = df;
+    h->segt.nseg = nseg;
+    h->segt.part = dp;
+    return LAIR_OK;
+}
+
 // batched systems: stationary refinement where every system is tested on its own relative
 // residual and stops being updated once it is <= tol (the cycle itself acts on all systems)
 static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
@@ -1419,6 +1450,7 @@ static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, d
     const int n = A.nr, nseg = h->nseg;
     const bool mixed = h->o.precision == LAIR_MIXED;
     TRY(ensure_work(h, n, 0));
+    TRY(ensure_tiles(h, L0));
     double *nrm;
     uint8_t *act;
     {
@@ -1430,14 +1462,14 @@ static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, d
     std::vector<double> bn(nseg), rl(nseg, 0.0);
     std::vector<int> its(nseg, 0);
     std::vector<uint8_t> active(nseg, 1);
-    seg_norm2(nseg, L0.seg_d, b, nrm, h->s);
+    seg_norm2(h->segt, b, nrm, h->s);
     CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
     CU(cudaStreamSynchronize(h->s));
     for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
     lair_status st = LAIR_OK;
     for (int it = 0;; ++it) {
         double *r = mixed ? h->wr : L0.b64;
-        seg_residual(A, nseg, L0.seg_d, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
+        seg_residual(A, h->segt, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
         CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
         flush_timers(h);
@@ -1455,8 +1487,8 @@ static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, d
         CU(cudaGraphLaunch(H.graph, h->s));
         count_launch(H.graph_nodes);
         h->graph_pending = h->o.timing;
-        if (mixed) seg_axpy<float>(nseg, L0.seg_d, act, L0.x32[L0.xfinal], x, h->s);
-        else seg_axpy<double>(nseg, L0.seg_d, act, L0.x64[L0.xfinal], x, h->s);
+        if (mixed) seg_axpy<float>(h->segt, act, L0.x32[L0.xfinal], x, h->s);
+        else seg_axpy<double>(h->segt, act, L0.x64[L0.xfinal], x, h->s);
         for (int q = 0; q < nseg; ++q) its[q] += active[q];
     }
     CU(cudaStreamSynchronize(h->s));
@@ -1481,6 +1513,7 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
     const int n = A.nr, nseg = h->nseg;
     const int m = h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30;
     TRY(ensure_work(h, n, m));
+    TRY(ensure_tiles(h, L0));
     if (!h->d_bat) {
         TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
         TRY(dalloc(h, &h->d_batcnt, (size_t)nseg));
@@ -1490,17 +1523,28 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
     double *hsum = h->d_bat, *hbuf = hsum + (size_t)nseg * HS, *ydev = hbuf + (size_t)nseg * HS,
            *nrm = ydev + (size_t)nseg * HS;
     double *V = h->V, *Z = h->Z;
+    // the Arnoldi kernels skip the tiles of systems that are not running
+    uint8_t *dact;
+    TRY(dalloc(h, &dact, (size_t)nseg));
+    SegTiles sta = h->segt;
+    sta.active = dact;
+    auto upload_running = [&](const std::vector<char> &run) -> lair_status {
+        CU(cudaStreamSynchronize(h->s));   // h_act may still feed the previous copy
+        for (int q = 0; q < nseg; ++q) h->h_act[q] = run[q] ? 1 : 0;
+        CU(cudaMemcpyAsync(dact, h->h_act, (size_t)nseg, cudaMemcpyHostToDevice, h->s));
+        return LAIR_OK;
+    };
     std::vector<double> bn(nseg), rl(nseg, 0.0), beta(nseg);
     std::vector<int> its(nseg, 0), jd(nseg, 0);
     std::vector<char> done(nseg, 0), running(nseg, 0);
     std::vector<double> Hm((size_t)nseg * (m + 1) * m), cs((size_t)nseg * m), sn((size_t)nseg * m), g((size_t)nseg * (m + 1));
-    seg_norm2(nseg, L0.seg_d, b, nrm, h->s);
+    seg_norm2(h->segt, b, nrm, h->s);
     CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
     CU(cudaStreamSynchronize(h->s));
     for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
     lair_status st = LAIR_OK;
     for (;;) {
-        seg_residual(A, nseg, L0.seg_d, b, x, V, nullptr, nrm, h->s);
+        seg_residual(A, h->segt, b, x, V, nullptr, nrm, h->s);
         CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
         flush_timers(h);
@@ -1519,7 +1563,8 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
             }
         }
         if (!any) break;
-        seg_scale(nseg, L0.seg_d, V, nrm, V, h->s);
+        TRY(upload_running(running));
+        seg_scale(sta, V, nrm, V, h->s);
         for (int j = 0; j < m; ++j) {
             double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
             TRY(precond(h, H, vj, zj));
@@ -1528,11 +1573,11 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
             tend(h, ts);
             CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (size_t)nseg * HS, h->s));
             for (int pass = 0; pass < 2; ++pass) {
-                seg_multidot(nseg, L0.seg_d, j + 1, V, n, w, HS, hbuf, hsum, h->s);
-                seg_sub_combo(nseg, L0.seg_d, j + 1, V, n, HS, hbuf, w, h->s);
+                seg_multidot(sta, j + 1, V, n, w, HS, hbuf, hsum, h->s);
+                seg_sub_combo(sta, j + 1, V, n, HS, hbuf, w, h->s);
             }
-            seg_norm2(nseg, L0.seg_d, w, nrm, h->s);
-            seg_scale(nseg, L0.seg_d, w, nrm, w, h->s);
+            seg_norm2(sta, w, nrm, h->s);
+            seg_scale(sta, w, nrm, w, h->s);
             CU(cudaMemcpyAsync(h->h_bat, hsum, sizeof(double) * (size_t)nseg * HS, cudaMemcpyDeviceToHost, h->s));
             CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
             CU(cudaStreamSynchronize(h->s));
@@ -1567,6 +1612,7 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
                 }
             }
             if (!still) break;
+            TRY(upload_running(running));
         }
         // per-system least-squares solutions y and the update x += Z y
         for (int q = 0; q < nseg; ++q) {
@@ -1581,7 +1627,7 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
         }
         CU(cudaMemcpyAsync(ydev, h->h_bat, sizeof(double) * (size_t)nseg * HS, cudaMemcpyHostToDevice, h->s));
         CU(cudaMemcpyAsync(h->d_batcnt, h->h_batcnt, sizeof(int) * nseg, cudaMemcpyHostToDevice, h->s));
-        seg_add_combo(nseg, L0.seg_d, h->d_batcnt, Z, n, HS, ydev, x, h->s);
+        seg_add_combo(h->segt, h->d_batcnt, Z, n, HS, ydev, x, h->s);
     }
     CU(cudaStreamSynchronize(h->s));
     int worst = -1;

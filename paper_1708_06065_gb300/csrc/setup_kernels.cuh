@@ -148,18 +148,30 @@ template <class T> void sell_spmv(const SellView &v, const T *x, T *y, cudaStrea
 template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);
 // batched systems: per-system residual r = b - A x (rows seg[q]..seg[q+1]), its squared norm, optional FP32 copy
-void seg_residual(const DCsr &A, int nseg, const int *seg, const double *b, const double *x, double *r, float *r32,
+// Row tiles of a batch of systems: tile t is system tile[t].x, rows [tile[t].y, tile[t].z);
+// the tiles of system q are first[q] .. first[q + 1] - 1; part holds SEG_TILE_PARTS doubles per tile.
+struct SegTiles {
+    const int4 *tile = nullptr;
+    int ntiles = 0;
+    const int *first = nullptr;
+    int nseg = 0;
+    double *part = nullptr;
+    const uint8_t *active = nullptr;   // if set, tiles of systems with active[q] == 0 are skipped
+};
+constexpr int SEG_TILE = 4096;
+constexpr int SEG_TILE_PARTS = 8;
+void seg_residual(const DCsr &A, const SegTiles &st, const double *b, const double *x, double *r, float *r32,
                   double *norm2, cudaStream_t s);
-void seg_norm2(int nseg, const int *seg, const double *v, double *norm2, cudaStream_t s);
+void seg_norm2(const SegTiles &st, const double *v, double *norm2, cudaStream_t s);
 template <class T>
-void seg_axpy(int nseg, const int *seg, const uint8_t *active, const T *e, double *x, cudaStream_t s);
-void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s);
-void seg_multidot(int nseg, const int *seg, int m, const double *X, long long ldx, const double *w, int hs,
-                  double *out, double *acc, cudaStream_t s);
-void seg_sub_combo(int nseg, const int *seg, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+void seg_axpy(const SegTiles &st, const uint8_t *active, const T *e, double *x, cudaStream_t s);
+void seg_multidot(const SegTiles &st, int m, const double *X, long long ldx, const double *w, int hs, double *out,
+                  double *acc, cudaStream_t s);
+void seg_sub_combo(const SegTiles &st, int m, const double *X, long long ldx, int hs, const double *h, double *w,
                    cudaStream_t s);
-void seg_add_combo(int nseg, const int *seg, const int *cnt, const double *Z, long long ldz, int hs, const double *y,
-                   double *x, cudaStream_t s);
-void seg_scale(int nseg, const int *seg, const double *v, const double *nrm2, double *out, cudaStream_t s);
+void seg_add_combo(const SegTiles &st, const int *cnt, const double *Z, long long ldz, int hs, const double *y, double *x,
+                   cudaStream_t s);
+void seg_scale(const SegTiles &st, const double *v, const double *nrm2, double *out, cudaStream_t s);
+void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s);
 
 }  // namespace lair

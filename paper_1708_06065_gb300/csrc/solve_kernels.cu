@@ -421,8 +421,15 @@ void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaSt
 }
 
 // ---------------------------------------------------------------------------------------
-// batched systems: one CTA per system for the residual, norms and masked updates
+// batched systems: per-system residuals, norms, dots and updates over row tiles. The rows of
+// every system are cut into tiles of at most SEG_TILE rows (tile t: system tile[t].x, rows
+// [tile[t].y, tile[t].z)); a CTA works on one tile at a time, so a large system is spread over
+// many SMs. Reductions write one partial per tile; seg_reduce then sums the partials of each
+// system in tile order (one warp per system), so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------------------
+constexpr int SEG_MD = SEG_TILE_PARTS;   // columns per multidot launch
+constexpr int SEG_GRID = 152 * 8;
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
     v = warp_sum(v);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -430,168 +437,205 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     double t = 0.0;
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
     return t;
 }
 
-__global__ void __launch_bounds__(256) k_seg_residual(int nseg, const int *__restrict__ seg, const int *__restrict__ rp,
-                                                      const int *__restrict__ col, const double *__restrict__ val,
-                                                      const double *__restrict__ b, const double *__restrict__ x,
-                                                      double *__restrict__ r, float *__restrict__ r32,
-                                                      double *__restrict__ norm2) {
+__global__ void __launch_bounds__(256) k_tile_residual(SegTiles st, const int *__restrict__ rp, const int *__restrict__ col,
+                                                       const double *__restrict__ val, const double *__restrict__ b,
+                                                       const double *__restrict__ x, double *__restrict__ r,
+                                                       float *__restrict__ r32) {
     __shared__ double red[8];
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
         double ss = 0.0;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
             double acc = 0.0;
             for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(val[k], x[col[k]], acc);
-            double ri = b[i] - acc;
+            const double ri = b[i] - acc;
             r[i] = ri;
             if (r32) r32[i] = (float)ri;
             ss = fma(ri, ri, ss);
         }
-        double t = block_sum(ss, red);
-        if (threadIdx.x == 0) norm2[q] = t;
-        __syncthreads();
+        const double tsum = block_sum(ss, red);
+        if (threadIdx.x == 0) st.part[t] = tsum;
     }
 }
 
-__global__ void __launch_bounds__(256) k_seg_norm2(int nseg, const int *__restrict__ seg, const double *__restrict__ v,
-                                                   double *__restrict__ norm2) {
+__global__ void __launch_bounds__(256) k_tile_norm2(SegTiles st, const double *__restrict__ v) {
     __shared__ double red[8];
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
         double ss = 0.0;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) ss = fma(v[i], v[i], ss);
-        double t = block_sum(ss, red);
-        if (threadIdx.x == 0) norm2[q] = t;
-        __syncthreads();
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) ss = fma(v[i], v[i], ss);
+        const double tsum = block_sum(ss, red);
+        if (threadIdx.x == 0) st.part[t] = tsum;
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_seg_axpy(int nseg, const int *__restrict__ seg, const uint8_t *__restrict__ active,
-                                                  const T *__restrict__ e, double *__restrict__ x) {
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
-        if (!active[q]) continue;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) x[i] += (double)e[i];
-    }
-}
-
-// per system q: out[q * HS + k0 + k] = sum over the system's rows of X_{k0+k}[i] w[i], k < m (m <= MD)
-constexpr int SEG_MD = 8;
-__global__ void __launch_bounds__(256) k_seg_multidot(int nseg, const int *__restrict__ seg, int k0, int m,
-                                                      const double *__restrict__ X, long long ldx,
-                                                      const double *__restrict__ w, int hs, double *__restrict__ out,
-                                                      double *__restrict__ acc_out) {
+// part[t * SEG_MD + k] = sum over the tile's rows of X_{k0+k}[i] w[i], k < m (m <= SEG_MD)
+__global__ void __launch_bounds__(256) k_tile_multidot(SegTiles st, int k0, int m, const double *__restrict__ X,
+                                                       long long ldx, const double *__restrict__ w) {
     __shared__ double red[8][SEG_MD];
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+    const double *Xk = X + (long long)k0 * ldx;
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
         double acc[SEG_MD];
 #pragma unroll
         for (int k = 0; k < SEG_MD; ++k) acc[k] = 0.0;
-        const double *Xk = X + (long long)k0 * ldx;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
             const double wi = w[i];
 #pragma unroll
             for (int k = 0; k < SEG_MD; ++k)
                 if (k < m) acc[k] = fma(Xk[k * ldx + i], wi, acc[k]);
         }
 #pragma unroll
-        for (int k = 0; k < SEG_MD; ++k) {
+        for (int k = 0; k < SEG_MD; ++k)
             if (k < m) {
-                double v = warp_sum(acc[k]);
+                const double v = warp_sum(acc[k]);
                 if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
             }
-        }
         __syncthreads();
-        if (threadIdx.x < m) {
-            double t = 0.0;
-            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
-            out[q * hs + k0 + threadIdx.x] = t;
-            if (acc_out) acc_out[q * hs + k0 + threadIdx.x] += t;
+        if ((int)threadIdx.x < m) {
+            double s2 = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s2 += red[ww][threadIdx.x];
+            st.part[(size_t)t * SEG_MD + threadIdx.x] = s2;
         }
         __syncthreads();
     }
 }
 
+// out[q * hs + k0 + k] = sum of the system's tile partials part[t * pw + k] in tile order (k < m);
+// acc_out[...] += the same when given. One warp per system.
+__global__ void __launch_bounds__(256) k_seg_reduce(SegTiles st, int pw, int m, int hs, int k0, double *__restrict__ out,
+                                                    double *__restrict__ acc_out) {
+    const int lane = threadIdx.x & 31;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < st.nseg; q += (gridDim.x * blockDim.x) >> 5) {
+        if (st.active && !st.active[q]) continue;
+        const int t0 = st.first[q], t1 = st.first[q + 1];
+        for (int k = 0; k < m; ++k) {
+            double v = 0.0;
+            for (int t = t0 + lane; t < t1; t += 32) v += st.part[(size_t)t * pw + k];
+            v = warp_sum(v);
+            if (lane == 0) {
+                out[(size_t)q * hs + k0 + k] = v;
+                if (acc_out) acc_out[(size_t)q * hs + k0 + k] += v;
+            }
+        }
+    }
+}
+
 // w_i -= sum_{k < m} h[q * hs + k] X_k[i] for the rows of system q
-__global__ void __launch_bounds__(256) k_seg_sub_combo(int nseg, const int *__restrict__ seg, int m,
-                                                       const double *__restrict__ X, long long ldx, int hs,
-                                                       const double *__restrict__ h, double *__restrict__ w) {
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x)
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+__global__ void __launch_bounds__(256) k_tile_sub_combo(SegTiles st, int m, const double *__restrict__ X, long long ldx,
+                                                        int hs, const double *__restrict__ h, double *__restrict__ w) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
+        const double *hq = h + (size_t)tl.x * hs;
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
             double v = w[i];
-            for (int k = 0; k < m; ++k) v = fma(-h[q * hs + k], X[k * ldx + i], v);
+            for (int k = 0; k < m; ++k) v = fma(-hq[k], X[k * ldx + i], v);
             w[i] = v;
         }
+    }
 }
 
 // x_i += sum_{k < cnt[q]} y[q * hs + k] Z_k[i] for the rows of system q
-__global__ void __launch_bounds__(256) k_seg_add_combo(int nseg, const int *__restrict__ seg, const int *__restrict__ cnt,
-                                                       const double *__restrict__ Z, long long ldz, int hs,
-                                                       const double *__restrict__ y, double *__restrict__ x) {
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
-        const int m = cnt[q];
+__global__ void __launch_bounds__(256) k_tile_add_combo(SegTiles st, const int *__restrict__ cnt, const double *__restrict__ Z,
+                                                        long long ldz, int hs, const double *__restrict__ y,
+                                                        double *__restrict__ x) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
+        const int m = cnt[tl.x];
         if (m == 0) continue;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) {
+        const double *yq = y + (size_t)tl.x * hs;
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
             double v = x[i];
-            for (int k = 0; k < m; ++k) v = fma(y[q * hs + k], Z[k * ldz + i], v);
+            for (int k = 0; k < m; ++k) v = fma(yq[k], Z[k * ldz + i], v);
             x[i] = v;
         }
     }
 }
 
-// out_i = v_i / sqrt(nrm2[q]) (0 when the norm is 0) for the rows of system q
-__global__ void __launch_bounds__(256) k_seg_scale(int nseg, const int *__restrict__ seg, const double *__restrict__ v,
-                                                   const double *__restrict__ nrm2, double *__restrict__ out) {
-    for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
-        const double n2 = nrm2[q];
+__global__ void __launch_bounds__(256) k_tile_scale(SegTiles st, const double *__restrict__ v,
+                                                    const double *__restrict__ nrm2, double *__restrict__ out) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
+        const double n2 = nrm2[tl.x];
         const double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-        for (int i = seg[q] + threadIdx.x; i < seg[q + 1]; i += blockDim.x) out[i] = v[i] * inv;
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) out[i] = v[i] * inv;
     }
 }
 
-void seg_multidot(int nseg, const int *seg, int m, const double *X, long long ldx, const double *w, int hs,
-                  double *out, double *acc, cudaStream_t s) {
-    for (int k0 = 0; k0 < m; k0 += SEG_MD) {
-        int mm = m - k0 < SEG_MD ? m - k0 : SEG_MD;
-        k_seg_multidot<<<nseg, 256, 0, s>>>(nseg, seg, k0, mm, X, ldx, w, hs, out, acc);
-        count_launch();
+template <class T>
+__global__ void __launch_bounds__(256) k_tile_axpy(SegTiles st, const uint8_t *__restrict__ active, const T *__restrict__ e,
+                                                   double *__restrict__ x) {
+    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
+        const int4 tl = st.tile[t];
+        if (st.active && !st.active[tl.x]) continue;
+        if (!active[tl.x]) continue;
+        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) x[i] += (double)e[i];
     }
 }
-void seg_sub_combo(int nseg, const int *seg, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+
+static int seg_grid(const SegTiles &st) { return st.ntiles < SEG_GRID ? (st.ntiles > 0 ? st.ntiles : 1) : SEG_GRID; }
+
+static void seg_reduce(const SegTiles &st, int pw, int m, int hs, int k0, double *out, double *acc, cudaStream_t s) {
+    k_seg_reduce<<<(st.nseg + 7) / 8, 256, 0, s>>>(st, pw, m, hs, k0, out, acc);
+    count_launch();
+}
+
+void seg_multidot(const SegTiles &st, int m, const double *X, long long ldx, const double *w, int hs, double *out,
+                  double *acc, cudaStream_t s) {
+    for (int k0 = 0; k0 < m; k0 += SEG_MD) {
+        const int mm = m - k0 < SEG_MD ? m - k0 : SEG_MD;
+        k_tile_multidot<<<seg_grid(st), 256, 0, s>>>(st, k0, mm, X, ldx, w);
+        count_launch();
+        seg_reduce(st, SEG_MD, mm, hs, k0, out, acc, s);
+    }
+}
+void seg_sub_combo(const SegTiles &st, int m, const double *X, long long ldx, int hs, const double *h, double *w,
                    cudaStream_t s) {
-    k_seg_sub_combo<<<nseg, 256, 0, s>>>(nseg, seg, m, X, ldx, hs, h, w);
+    k_tile_sub_combo<<<seg_grid(st), 256, 0, s>>>(st, m, X, ldx, hs, h, w);
     count_launch();
 }
-void seg_add_combo(int nseg, const int *seg, const int *cnt, const double *Z, long long ldz, int hs, const double *y,
-                   double *x, cudaStream_t s) {
-    k_seg_add_combo<<<nseg, 256, 0, s>>>(nseg, seg, cnt, Z, ldz, hs, y, x);
+void seg_add_combo(const SegTiles &st, const int *cnt, const double *Z, long long ldz, int hs, const double *y, double *x,
+                   cudaStream_t s) {
+    k_tile_add_combo<<<seg_grid(st), 256, 0, s>>>(st, cnt, Z, ldz, hs, y, x);
     count_launch();
 }
-void seg_scale(int nseg, const int *seg, const double *v, const double *nrm2, double *out, cudaStream_t s) {
-    k_seg_scale<<<nseg, 256, 0, s>>>(nseg, seg, v, nrm2, out);
+void seg_scale(const SegTiles &st, const double *v, const double *nrm2, double *out, cudaStream_t s) {
+    k_tile_scale<<<seg_grid(st), 256, 0, s>>>(st, v, nrm2, out);
     count_launch();
 }
+void seg_residual(const DCsr &A, const SegTiles &st, const double *b, const double *x, double *r, float *r32,
+                  double *norm2, cudaStream_t s) {
+    k_tile_residual<<<seg_grid(st), 256, 0, s>>>(st, A.rp, A.col, A.val, b, x, r, r32);
+    count_launch();
+    seg_reduce(st, 1, 1, 1, 0, norm2, nullptr, s);
+}
+void seg_norm2(const SegTiles &st, const double *v, double *norm2, cudaStream_t s) {
+    k_tile_norm2<<<seg_grid(st), 256, 0, s>>>(st, v);
+    count_launch();
+    seg_reduce(st, 1, 1, 1, 0, norm2, nullptr, s);
+}
+template <class T>
+void seg_axpy(const SegTiles &st, const uint8_t *active, const T *e, double *x, cudaStream_t s) {
+    k_tile_axpy<T><<<seg_grid(st), 256, 0, s>>>(st, active, e, x);
+    count_launch();
+}
+template void seg_axpy<float>(const SegTiles &, const uint8_t *, const float *, double *, cudaStream_t);
+template void seg_axpy<double>(const SegTiles &, const uint8_t *, const double *, double *, cudaStream_t);
 
 __global__ void k_gather_int(int m, const int *__restrict__ idx, const int *__restrict__ src, int *__restrict__ out) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) out[t] = src[idx[t]];
 }
 
-void seg_residual(const DCsr &A, int nseg, const int *seg, const double *b, const double *x, double *r, float *r32,
-                  double *norm2, cudaStream_t s) {
-    k_seg_residual<<<nseg, 256, 0, s>>>(nseg, seg, A.rp, A.col, A.val, b, x, r, r32, norm2);
-    count_launch();
-}
-void seg_norm2(int nseg, const int *seg, const double *v, double *norm2, cudaStream_t s) {
-    k_seg_norm2<<<nseg, 256, 0, s>>>(nseg, seg, v, norm2);
-    count_launch();
-}
-template <class T>
-void seg_axpy(int nseg, const int *seg, const uint8_t *active, const T *e, double *x, cudaStream_t s) {
-    k_seg_axpy<T><<<nseg, 256, 0, s>>>(nseg, seg, active, e, x);
-    count_launch();
-}
-template void seg_axpy<float>(int, const int *, const uint8_t *, const float *, double *, cudaStream_t);
-template void seg_axpy<double>(int, const int *, const uint8_t *, const double *, double *, cudaStream_t);
 void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s) {
     k_gather_int<<<grid_for(m, 256), 256, 0, s>>>(m, idx, src, out);
     count_launch();
