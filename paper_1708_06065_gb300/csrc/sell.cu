@@ -37,25 +37,34 @@ __device__ __forceinline__ int find_desc(const SellDesc *__restrict__ d, int nd,
 
 // one CTA per window: order the window's rows by decreasing length (stable)
 __global__ void __launch_bounds__(SELL_WINDOW) k_sell_sort_multi(const SellDesc *__restrict__ d, int nd) {
-    __shared__ int len[SELL_WINDOW];
+    // keys (INT_MAX - length, position) in a bitonic network: decreasing length, ties by position
+    __shared__ unsigned long long key[SELL_WINDOW];
     __shared__ int rid[SELL_WINDOW];
     const int p = find_desc(d, nd, blockIdx.x, 0);
     const SellDesc v = d[p];
     const int w0 = (blockIdx.x - v.win0) * SELL_WINDOW;
     const int t = threadIdx.x;
     const int cnt = min(SELL_WINDOW, v.nrows - w0);
+    key[t] = ~0ull;
     if (t < cnt) {
         const int i = v.rows_in ? v.rows_in[w0 + t] : w0 + t;
         rid[t] = i;
-        len[t] = v.rp[i + 1] - v.rp[i];
+        key[t] = ((unsigned long long)(0x7fffffff - (v.rp[i + 1] - v.rp[i])) << 32) | (unsigned)t;
     }
     __syncthreads();
-    if (t < cnt) {
-        const int lt = len[t];
-        int r = 0;
-        for (int u = 0; u < cnt; ++u) r += (len[u] > lt) || (len[u] == lt && u < t);
-        v.row_out[w0 + r] = rid[t];
-    }
+    for (int k = 2; k <= SELL_WINDOW; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int o = t ^ j;
+            if (o > t) {
+                const unsigned long long a = key[t], b = key[o];
+                if (((t & k) == 0) ? a > b : a < b) {
+                    key[t] = b;
+                    key[o] = a;
+                }
+            }
+            __syncthreads();
+        }
+    if (t < cnt) v.row_out[w0 + t] = rid[(int)(key[t] & 0xffffffffu)];
 }
 
 // slice lengths in entries (32 x longest row of the slice), one warp per slice; also their
