@@ -12,7 +12,7 @@
  *   strength of connection ........ Sec. 4, definition of N_i (hard minimum)
  *   C/F splitting .................. Sec. 4 (classical first pass, no second pass),
  *                                    also run independently in index blocks; PMIS
- *   restriction neighbourhoods ..... Sec. 3.1 (distance one/two, F-F-C only, Sec. 4)
+ *   restriction neighbourhoods ..... Sec. 3.1 (distance one to four, F-F-C only, Sec. 4)
  *   local systems .................. Sec. 3.1, Eq. (3.1) johnair and Eq. (3.2) system,
  *                                    least squares when singular (Sec. 3.1 footnote)
  *   R = [Z I], P = [W; I] .......... Sec. 2.1, Eq. (2.2)
@@ -53,7 +53,7 @@
 typedef struct {
     int cf_mode;           /* 0 RS, 1 PMIS, 2 USER (level 0 only), 3 AUTO (first pass in blocks of rs_block) */
     const int8_t *cf_user; /* level-0 splitting for USER mode (1 = C, 0 = F) */
-    int distance;          /* 1 or 2 */
+    int distance;          /* 1 to 4 */
     double theta;          /* strength threshold for R/P neighbourhoods */
     double theta_cf;       /* strength threshold for the C/F splitting */
     int strength_abs;      /* 1: |a_ij| >= theta max|a_ik| instead of -a_ij >= ... */
@@ -402,49 +402,63 @@ static void cf_pmis(const ograph *S, const ograph *ST, uint64_t seed, int8_t *cf
 /* ------------------------------------------------------------------------- */
 /* Neighbourhoods (Sec. 3.1, Sec. 4). For C-point i and graph G:              */
 /*   distance 1: G_i restricted to F points;                                  */
-/*   distance 2: adds G_j restricted to F for every j in that set (F-F-C).    */
+/*   distance d > 1: the distance d-1 set plus G_j restricted to F for every   */
+/*   j in that set (strong paths i -> F -> ... -> F, F-F-C only).             */
 /* Result sorted ascending, no duplicates. Output as CSR over C points.        */
 /* ------------------------------------------------------------------------- */
+static int64_t sort_unique(int32_t *t, int64_t m) {
+    qsort(t, (size_t)m, sizeof(int32_t), cmp_i32);
+    int64_t u = 0;
+    for (int64_t a = 0; a < m; ++a)
+        if (u == 0 || t[u - 1] != t[a]) t[u++] = t[a];
+    return u;
+}
+
 static int build_neighbourhoods(const ograph *G, const int8_t *cf, int distance,
                                 int64_t nc, const int64_t *cpts, int64_t **out_rp, int32_t **out_col) {
     int64_t *rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
     int64_t cap = 1024, len = 0;
     int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
-    int32_t *tmp = NULL;
-    int64_t tcap = 0;
+    int32_t *tmp = NULL, *nxt = NULL;
+    int64_t tcap = 0, ncap = 0;
     for (int64_t c = 0; c < nc; ++c) {
         int64_t i = cpts[c];
-        int64_t t = 0;
-        int64_t need = 0;
-        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p) {
-            int64_t j = G->col[p];
-            need += 1;
-            if (distance >= 2 && cf[j] == CF_F) need += G->rp[j + 1] - G->rp[j];
-        }
+        /* distance 1 */
+        int64_t need = G->rp[i + 1] - G->rp[i];
         if (need > tcap) { tcap = need + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
-        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p) {
-            int64_t j = G->col[p];
-            if (cf[j] != CF_F) continue;
-            tmp[t++] = (int32_t)j;
-            if (distance >= 2)
+        int64_t t = 0;
+        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p)
+            if (cf[G->col[p]] == CF_F) tmp[t++] = G->col[p];
+        t = sort_unique(tmp, t);
+        /* each further distance: the set and the F points of G_j for every j in it */
+        for (int d = 2; d <= distance; ++d) {
+            need = t;
+            for (int64_t a = 0; a < t; ++a) need += G->rp[tmp[a] + 1] - G->rp[tmp[a]];
+            if (need > ncap) { ncap = need + 16; nxt = (int32_t *)realloc(nxt, sizeof(int32_t) * (size_t)ncap); }
+            int64_t m = 0;
+            for (int64_t a = 0; a < t; ++a) {
+                int64_t j = tmp[a];
+                nxt[m++] = (int32_t)j;
                 for (int64_t q = G->rp[j]; q < G->rp[j + 1]; ++q) {
                     int64_t k = G->col[q];
-                    if (cf[k] == CF_F && k != i) tmp[t++] = (int32_t)k;
+                    if (cf[k] == CF_F && k != i) nxt[m++] = (int32_t)k;
                 }
+            }
+            m = sort_unique(nxt, m);
+            if (m > tcap) { tcap = m + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
+            memcpy(tmp, nxt, sizeof(int32_t) * (size_t)m);
+            t = m;
         }
-        qsort(tmp, (size_t)t, sizeof(int32_t), cmp_i32);
-        int64_t u = 0;
-        for (int64_t a = 0; a < t; ++a)
-            if (u == 0 || tmp[u - 1] != tmp[a]) tmp[u++] = tmp[a];
-        if (len + u > cap) {
-            while (len + u > cap) cap *= 2;
+        if (len + t > cap) {
+            while (len + t > cap) cap *= 2;
             col = (int32_t *)realloc(col, sizeof(int32_t) * (size_t)cap);
         }
-        memcpy(col + len, tmp, sizeof(int32_t) * (size_t)u);
-        len += u;
+        memcpy(col + len, tmp, sizeof(int32_t) * (size_t)t);
+        len += t;
         rp[c + 1] = len;
     }
     free(tmp);
+    free(nxt);
     *out_rp = rp;
     *out_col = col;
     return ORA_OK;

@@ -389,6 +389,8 @@ def test_one_point_interpolation_strongest_c():
     ("fd2d_64", dict(distance=1)),
     ("fd2d_64", dict(distance=2)),
     ("fd2d_64", dict(distance=2, cf_mode=O.CF_PMIS)),
+    ("fd2d_64", dict(distance=3)),
+    ("fd2d_64", dict(distance=4, cf_mode=O.CF_PMIS)),
 ])
 def test_RA_zero_on_pattern_every_level(cfg, kw):
     s = W.config(cfg, scale=32)
@@ -415,7 +417,7 @@ def test_larger_neighbourhood_is_more_accurate():
     errs = []
     A = s.to_scipy().toarray()
     cf = None
-    for k in (1, 2):
+    for k in (1, 2, 3, 4):
         H = O.Hierarchy(s, distance=k, cf_mode=O.CF_PMIS, max_levels=2, coarse_max=4, lump_tol=0.0)
         L = H.levels[0]
         cf = L.cf if cf is None else cf
@@ -424,7 +426,34 @@ def test_larger_neighbourhood_is_more_accurate():
         Zi = -A[np.ix_(Ci, Fi)] @ np.linalg.inv(A[np.ix_(Fi, Fi)])
         Z = csr_to_scipy(L.R, (len(Ci), s.n)).toarray()[:, Fi]
         errs.append(np.linalg.norm(Z - Zi) / np.linalg.norm(Zi))
-    assert errs[1] < errs[0] < 1.0
+    assert errs[3] < errs[2] < errs[1] < errs[0] < 1.0
+
+
+@pytest.mark.parametrize("distance", [1, 2, 3, 4])
+def test_neighbourhoods_are_strong_F_paths(distance):
+    """Sec. 3.1 / Sec. 4: the neighbourhood of C point i is every F point reachable from i by a path
+    of at most `distance` strong edges whose points after i are all F -- checked by enumerating the
+    paths directly on a small random graph (R's pattern is the neighbourhood plus i itself)."""
+    s = W.random_sparse(300, 5, seed=11)
+    H = O.Hierarchy(s, distance=distance, cf_mode=O.CF_PMIS, max_levels=2, coarse_max=4, lump_tol=0.0)
+    L = H.levels[0]
+    rp, col, _ = L.A
+    strong = np.asarray(L.strong).astype(bool)
+    nbrs = [col[rp[i]:rp[i + 1]][strong[rp[i]:rp[i + 1]]] for i in range(L.n)]
+    Cpts = np.nonzero(L.cf == 1)[0]
+    for c, i in enumerate(Cpts):
+        reach, frontier = set(), [i]
+        for _ in range(distance):
+            nxt = []
+            for j in frontier:
+                for k in nbrs[j]:
+                    k = int(k)
+                    if L.cf[k] == 0 and k not in reach:
+                        reach.add(k)
+                        nxt.append(k)
+            frontier = nxt
+        got = set(int(j) for j in L.R[1][L.R[0][c]:L.R[0][c + 1]]) - {int(i)}
+        assert got == reach
 
 
 # --------------------------------------------------------------------------------------
