@@ -86,7 +86,8 @@ typedef struct {
 typedef struct {
     int cf_mode;              /* lair_cf_mode (default AUTO) */
     const int8_t *cf_user;    /* LAIR_CF_USER: host array of n entries, 1 = C, 0 = F */
-    int distance;             /* restriction/interpolation neighbourhood distance, 1 or 2 */
+    int distance;             /* restriction/interpolation neighbourhood distance, 1 to 4 (Sec. 3.1, Sec. 4:
+                                 each step adds the strong F neighbours of the previous set) */
     double theta;             /* strength threshold for the neighbourhoods (Sec. 4, N_i) */
     double theta_cf;          /* strength threshold for the splitting */
     int strength_abs;         /* 1: compare |a_ij| instead of -a_ij */

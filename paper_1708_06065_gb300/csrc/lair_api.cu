@@ -492,18 +492,39 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
 static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
                               const int *brp, const int *bcol, const double *bval, int **out_rp, int **out_col,
                               double **out_val, float **out_val32, uint8_t *lsflag, int *out_nnz, bool keep) {
-    const int distance = h->o.distance;
+    const int distance = h->o.distance, d0 = distance < 2 ? distance : 2;
     int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
     TRY(new_counts(h, t, &ub, nc));
-    launch_nb_bound(nc, cpts, G, cf, distance, ub, h->s);
+    launch_nb_bound(nc, cpts, G, cf, d0, ub, h->s);
     TRY(t.get(&off, (size_t)nc + 1));
     int total = 0;
     TRY(scan(h, ub, off, nc, &total));
     TRY(t.get(&tmp, (size_t)total));
     TRY(new_counts(h, t, &cnt, nc));
-    launch_nb_fill(nc, cpts, G, cf, distance, off, tmp, cnt, h->s);
+    launch_nb_fill(nc, cpts, G, cf, d0, off, tmp, cnt, h->s);
     TRY(t.get(&nb_rp, (size_t)nc + 1));
     TRY(scan(h, cnt, nb_rp, nc, nullptr));
+    // distances beyond two: expand the sets one distance at a time
+    for (int d = 3; d <= distance; ++d) {
+        int nn = 0, tot = 0;
+        TRY(read_ints(h, nb_rp + nc, 1, &nn));
+        int *cur, *ub2, *off2, *tmp2, *cnt2, *rp2;
+        TRY(t.get(&cur, (size_t)nn));
+        launch_nb_compact(nc, off, tmp, nb_rp, cur, h->s);
+        TRY(new_counts(h, t, &ub2, nc));
+        launch_nb_expand(0, nc, cpts, G, cf, nb_rp, cur, nullptr, nullptr, ub2, h->s);
+        TRY(t.get(&off2, (size_t)nc + 1));
+        TRY(scan(h, ub2, off2, nc, &tot));
+        TRY(t.get(&tmp2, (size_t)tot));
+        TRY(new_counts(h, t, &cnt2, nc));
+        launch_nb_expand(1, nc, cpts, G, cf, nb_rp, cur, off2, tmp2, cnt2, h->s);
+        TRY(t.get(&rp2, (size_t)nc + 1));
+        TRY(scan(h, cnt2, rp2, nc, nullptr));
+        off = off2;
+        tmp = tmp2;
+        cnt = cnt2;
+        nb_rp = rp2;
+    }
     // size bins of the local systems; one read-back for the bins and the neighbourhood total
     int *lists, *bcounts, *smax;
     TRY(t.get(&lists, (size_t)3 * nc + 1));
@@ -1850,7 +1871,7 @@ lair_status lair_options_default(lair_options *o) {
 static lair_status check_options(lair_handle *h, const lair_options *o) {
     if (o->cf_mode < 0 || o->cf_mode > 3) return fail(h, LAIR_ERR_INVALID_ARG, "cf_mode %d", o->cf_mode);
     if (o->cf_mode == LAIR_CF_USER && !o->cf_user) return fail(h, LAIR_ERR_INVALID_ARG, "cf_user is NULL");
-    if (o->distance < 1 || o->distance > 2) return fail(h, LAIR_ERR_INVALID_ARG, "distance must be 1 or 2");
+    if (o->distance < 1 || o->distance > 4) return fail(h, LAIR_ERR_INVALID_ARG, "distance must be 1 to 4");
     if (o->interp < 0 || o->interp > 1) return fail(h, LAIR_ERR_INVALID_ARG, "interp %d", o->interp);
     if (o->relax < 0 || o->relax > 2) return fail(h, LAIR_ERR_INVALID_ARG, "relax %d", o->relax);
     if (o->precision < 0 || o->precision > 1) return fail(h, LAIR_ERR_INVALID_ARG, "precision %d", o->precision);

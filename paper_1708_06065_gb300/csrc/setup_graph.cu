@@ -657,8 +657,9 @@ __global__ void k_cidx(int n, const int8_t *__restrict__ cf, const int *__restri
 }
 
 // -------------------------------------------------------------------------------------
-// Neighbourhoods (Sec. 3.1; F-F-C only for distance two, Sec. 4). For C point i in graph G:
-// distance 1: G_i n F; distance 2 adds G_j n F for each j in G_i n F. Sorted, unique.
+// Neighbourhoods (Sec. 3.1; F-F-C only, Sec. 4). For C point i in graph G:
+// distance 1: G_i n F; distance 2 adds G_j n F for each j in G_i n F; each further distance
+// (k_nb_expand) adds G_j n F for each j of the previous set. Sorted, unique.
 // -------------------------------------------------------------------------------------
 __global__ void k_nb_bound(int nc, const int *__restrict__ cpts, Graph G, const int8_t *__restrict__ cf,
                            int distance, int *__restrict__ ub) {
@@ -696,6 +697,43 @@ __global__ void k_nb_fill(int nc, const int *__restrict__ cpts, Graph G, const i
             int v = t[a], b = a - 1;
             while (b >= 0 && t[b] > v) { t[b + 1] = t[b]; --b; }
             t[b + 1] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < m; ++a)
+            if (u == 0 || t[u - 1] != t[a]) t[u++] = t[a];
+        cnt[c] = u;
+    }
+}
+
+// One more distance (distances beyond two): the current set of C point c (nb_rp / nb_col) plus
+// G_j n F for every j in it. phase 0: the bound |set| + sum |G_j|; phase 1: the sorted, unique set
+// written at off[c] with its size in cnt[c].
+__global__ void k_nb_expand(int phase, int nc, const int *__restrict__ cpts, Graph G, const int8_t *__restrict__ cf,
+                            const int *__restrict__ nb_rp, const int *__restrict__ nb_col, const int *__restrict__ off,
+                            int *__restrict__ tmp, int *__restrict__ cnt) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int i = cpts[c];
+        const int b = nb_rp[c], e = nb_rp[c + 1];
+        if (phase == 0) {
+            int u = e - b;
+            for (int a = b; a < e; ++a) u += G.rp[nb_col[a] + 1] - G.rp[nb_col[a]];
+            cnt[c] = u;
+            continue;
+        }
+        int *t = tmp + off[c];
+        int m = 0;
+        for (int a = b; a < e; ++a) {
+            const int j = nb_col[a];
+            t[m++] = j;
+            for (int q = G.rp[j]; q < G.rp[j + 1]; ++q) {
+                const int k = G.col[q];
+                if (cf[k] == CF_F && k != i) t[m++] = k;
+            }
+        }
+        for (int a = 1; a < m; ++a) {
+            int v = t[a], bb = a - 1;
+            while (bb >= 0 && t[bb] > v) { t[bb + 1] = t[bb]; --bb; }
+            t[bb + 1] = v;
         }
         int u = 0;
         for (int a = 0; a < m; ++a)
@@ -878,6 +916,12 @@ void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, 
 void launch_nb_fill(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, const int *off, int *tmp,
                     int *cnt, cudaStream_t s) {
     k_nb_fill<<<grid_for(nc, 128), 128, 0, s>>>(nc, cpts, G, cf, distance, off, tmp, cnt);
+    count_launch();
+}
+
+void launch_nb_expand(int phase, int nc, const int *cpts, const Graph &G, const int8_t *cf, const int *nb_rp,
+                      const int *nb_col, const int *off, int *tmp, int *cnt, cudaStream_t s) {
+    k_nb_expand<<<grid_for(nc, TB), TB, 0, s>>>(phase, nc, cpts, G, cf, nb_rp, nb_col, off, tmp, cnt);
     count_launch();
 }
 

@@ -37,6 +37,9 @@ void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, 
 void launch_nb_fill(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, const int *off, int *tmp,
                     int *cnt, cudaStream_t s);
 void launch_nb_compact(int nc, const int *off, const int *tmp, const int *nb_rp, int *nb_col, cudaStream_t s);
+// one more distance: phase 0 writes the bound to cnt, phase 1 the sets at off (sizes in cnt)
+void launch_nb_expand(int phase, int nc, const int *cpts, const Graph &G, const int8_t *cf, const int *nb_rp,
+                      const int *nb_col, const int *off, int *tmp, int *cnt, cudaStream_t s);
 
 // ---- setup_local.cu -------------------------------------------------------------------
 struct LocalArgs {

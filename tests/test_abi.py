@@ -47,7 +47,7 @@ def test_setup_rejects_bad_arguments_without_a_gpu():
     from paper_1708_06065_gb300 import lair
     h = ctypes.c_void_p()
     assert lair.lib.lair_setup(None, None, ctypes.byref(h)) == 1
-    o = lair.options(distance=3)
+    o = lair.options(distance=5)
     A = lair.lair_csr(4, 4, None, None, None, 0)
     st = lair.lib.lair_setup(ctypes.byref(A), ctypes.byref(o), ctypes.byref(h))
     assert st == 1

@@ -54,6 +54,10 @@ CASES = {
     # one-point P with dense coarse operators: some R A rows exceed the fused triple-product kernels
     "fd3d_16_onepoint_d2_nolump": ("fd3d_192", 16, dict(distance=2, interp=1, lump_tol=0.0)),
     "diffusive_onepoint_d2": ("diffusive", None, dict(distance=2, interp=1, lump_tol=0.0)),
+    # neighbourhoods beyond distance two (Sec. 4, pure advection)
+    "fd2d64_d3": ("fd2d_64", None, dict(distance=3)),
+    "fd2d64_pmis_d4_mixed": ("fd2d_64", None, dict(distance=4, cf_mode=1, precision=1)),
+    "dg_p2_12_d3": ("dg_p2_256", 12, dict(distance=3, interp=1, strength_abs=1, block_size=6, cf_mode=1)),
 }
 
 
