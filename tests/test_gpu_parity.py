@@ -308,3 +308,34 @@ def test_adjoint_hierarchy_matches_oracle_on_transpose(lair):
     lo, ro = H.solve(g, tol=1e-10)
     assert rep.status == 0 and abs(rep.iters - ro["iters"]) <= 1
     assert np.linalg.norm(lam - lo) <= 1e-8 * np.linalg.norm(lo)
+
+
+def _diag_system(n, rng):
+    return W.CsrSystem(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), rng.uniform(1, 2, n),
+                       rng.uniform(-1, 1, n))
+
+
+def _dense_system(n, rng):
+    A = rng.uniform(-1, 1, (n, n)) + n * np.eye(n)
+    return W.CsrSystem(n, np.arange(0, n * n + 1, n, dtype=np.int64), np.tile(np.arange(n, dtype=np.int32), n),
+                       A.ravel(), rng.uniform(-1, 1, n))
+
+
+@pytest.mark.parametrize("kind", ["diagonal_1000", "n_1", "dense_3", "dense_200"])
+def test_degenerate_systems(lair, kind):
+    """Degenerate inputs: no strong connection at all (every point F, no coarse level: the whole
+    matrix goes to the dense solve), a single unknown, and dense systems small enough that the
+    finest level is the coarsest or nearly so. Hierarchy as the oracle's, solution as a dense solve."""
+    rng = np.random.default_rng(7)
+    s = {"diagonal_1000": lambda: _diag_system(1000, rng), "n_1": lambda: _diag_system(1, rng),
+         "dense_3": lambda: _dense_system(3, rng), "dense_200": lambda: _dense_system(200, rng)}[kind]()
+    G = lair.Hierarchy.from_system(s)
+    H = O.Hierarchy(s)
+    assert H.status == 0
+    assert len(G.info()) == len(H.levels)
+    worst = compare_hierarchies(G, H, TOL64)
+    assert max(worst.values(), default=0.0) <= TOL64
+    x, rep = G.solve(s.b, tol=1e-12)
+    xr = np.linalg.solve(s.to_scipy().toarray(), s.b)
+    assert rep.status == 0
+    assert np.abs(x - xr).max() <= 1e-10 * max(1.0, np.abs(xr).max())
