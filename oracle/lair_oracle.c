@@ -22,6 +22,8 @@
  *   lumping ........................ Sec. 3.3
  *   V-cycle with post F-F-C Jacobi . Sec. 4, Eq. (2.4)
  *   GMRES acceleration ............. Sec. 4 (here flexible GMRES, FP64)
+ *   refresh for new values ......... backward Euler steps I + dt S (Sec. 4.1.1):
+ *                                    structure kept, every value recomputed
  *
  * Points the paper leaves open are fixed here in one documented way (tie rules,
  * singular threshold, arithmetic order). Floating-point operations that decide
@@ -784,13 +786,10 @@ static int cmp_coo(const void *a, const void *b) {
     return (x->col > y->col) - (x->col < y->col);
 }
 
-static int build_P_laip(const ocsr *A, const ograph *S, const ograph *ST, const int8_t *cf,
-                        const int64_t *cidx, int64_t nc, const int64_t *cpts, int distance, int prec,
-                        ocsr *P, uint8_t *lsflag) {
+/* the local systems of lAIP on given sets Q_c (ascending fine indices, c's own point excluded) */
+static int build_P_laip_on(const ocsr *A, int64_t nc, const int64_t *cpts, const int64_t *q_rp,
+                           const int32_t *q_col, int prec, ocsr *P, uint8_t *lsflag) {
     int64_t n = A->nr;
-    /* neighbourhoods Q_c are the distance-k neighbourhoods of c in the transposed graph */
-    int64_t *q_rp; int32_t *q_col;
-    build_neighbourhoods(ST, cf, distance, nc, cpts, &q_rp, &q_col);
     int64_t total = q_rp[nc] + nc;
     coo_ent *ent = (coo_ent *)malloc(sizeof(coo_ent) * (size_t)(total > 0 ? total : 1));
     int64_t smax = 0;
@@ -802,7 +801,6 @@ static int build_P_laip(const ocsr *A, const ograph *S, const ograph *ST, const 
     float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
     float *wf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
     int64_t e = 0;
-    (void)S;
     for (int64_t c = 0; c < nc; ++c) {
         int64_t ci = cpts[c];
         const int32_t *Q = q_col + q_rp[c];
@@ -839,9 +837,18 @@ static int build_P_laip(const ocsr *A, const ograph *S, const ograph *ST, const 
         P->val[k] = ent[k].val;
     }
     for (int64_t i = 0; i < n; ++i) P->rp[i + 1] += P->rp[i];
-    (void)cidx;
-    free(ent); free(q_rp); free(q_col); free(M); free(rhs); free(w); free(Mf); free(rf); free(wf);
+    free(ent); free(M); free(rhs); free(w); free(Mf); free(rf); free(wf);
     return ORA_OK;
+}
+
+static int build_P_laip(const ocsr *A, const ograph *ST, const int8_t *cf, int64_t nc, const int64_t *cpts,
+                        int distance, int prec, ocsr *P, uint8_t *lsflag) {
+    /* neighbourhoods Q_c are the distance-k neighbourhoods of c in the transposed graph */
+    int64_t *q_rp; int32_t *q_col;
+    build_neighbourhoods(ST, cf, distance, nc, cpts, &q_rp, &q_col);
+    int st = build_P_laip_on(A, nc, cpts, q_rp, q_col, prec, P, lsflag);
+    free(q_rp); free(q_col);
+    return st;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -914,6 +921,34 @@ static int lump(ocsr *K, double tol) {
         }
         start = end;
         K->rp[i + 1] = p;
+    }
+    return ORA_OK;
+}
+
+/* Lumping on a kept pattern (hierarchy refresh): row i of T keeps exactly    */
+/* the columns it already has; every other entry of row i of K (the full      */
+/* product) is added to the diagonal, in ascending j order starting from      */
+/* k_ii, as in lump() when the dropped set is the same. T's pattern must be a  */
+/* subset of K's and both rows must hold the diagonal.                         */
+static int lump_on_pattern(const ocsr *K, ocsr *T) {
+    for (int64_t i = 0; i < K->nr; ++i) {
+        int64_t k0 = K->rp[i], k1 = K->rp[i + 1], t0 = T->rp[i], t1 = T->rp[i + 1];
+        double d;
+        if (!find_entry(K, i, i, &d)) return ORA_ERR_ZERO_DIAG;
+        int64_t t = t0;
+        for (int64_t k = k0; k < k1; ++k) {
+            int64_t j = K->col[k];
+            while (t < t1 && T->col[t] < j) ++t;
+            int kept = t < t1 && T->col[t] == j;
+            if (j != i && !kept) d = d + K->val[k];
+        }
+        t = t0;
+        for (int64_t k = k0; k < k1 && t < t1; ++k) {
+            if (K->col[k] != T->col[t]) continue;
+            T->val[t] = (T->col[t] == i) ? d : K->val[k];
+            ++t;
+        }
+        if (t != t1) return ORA_ERR_ARG;   /* an entry of T that K does not have */
     }
     return ORA_OK;
 }
@@ -1197,7 +1232,7 @@ static int coarsen_level(ohier *H, int l, int *is_last) {
         st = build_P_onepoint(A, &S, L->cf, L->cidx, nc, o->strength_abs, &L->P);
     } else {
         L->ls_P = (uint8_t *)calloc((size_t)nc, 1);
-        st = build_P_laip(A, &S, &ST, L->cf, L->cidx, nc, cpts, o->distance, o->prec, &L->P, L->ls_P);
+        st = build_P_laip(A, &ST, L->cf, nc, cpts, o->distance, o->prec, &L->P, L->ls_P);
     }
     free(cpts);
     graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
@@ -1309,6 +1344,142 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
         }
         ++l;
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Refresh: the same matrix pattern with new values, as for the backward      */
+/* Euler step I + dt S of Sec. 4.1.1 when dt or the coefficients change        */
+/* between steps. The splittings, strength masks, neighbourhoods of the local  */
+/* systems and the patterns of R, P and every coarse operator stay as set-up   */
+/* left them; every value is recomputed from the new matrix in set-up's order: */
+/* block scaling (Sec. 4.2.1), lumping of level 0 when asked, then per level   */
+/* R by the local solves of Sec. 3.1 on the neighbourhood read off R's pattern */
+/* (row c without c itself), lAIP by its local solves on the sets Q_c read off */
+/* P's pattern (column c without c's own point), one-point P unchanged (all    */
+/* its values are 1), K = (RA)P, lumping onto the kept pattern of the next     */
+/* level (Sec. 3.3), then D^{-1}, the FP32 copies and the dense factorisation  */
+/* of the coarsest operator. rp and col must be the set-up's.                 */
+/* ------------------------------------------------------------------------- */
+static void unfinish_level(ohier *H, int l) {
+    olevel *L = &H->lev[l];
+    free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32);
+    L->dinv = NULL; L->A32 = L->R32 = L->P32 = L->dinv32 = NULL;
+    for (int k = 0; k < 4; ++k) {
+        free(H->w64[l][k]); free(H->w32[l][k]);
+        H->w64[l][k] = NULL; H->w32[l][k] = NULL;
+    }
+}
+
+static int same_pattern(const ocsr *X, const ocsr *Y) {
+    if (X->nr != Y->nr || X->rp[X->nr] != Y->rp[Y->nr]) return 0;
+    if (memcmp(X->rp, Y->rp, sizeof(int64_t) * (size_t)(X->nr + 1))) return 0;
+    return memcmp(X->col, Y->col, sizeof(int32_t) * (size_t)X->rp[X->nr]) == 0;
+}
+
+static int refresh_level(ohier *H, int l) {
+    olevel *L = &H->lev[l];
+    const ora_opts *o = &H->o;
+    const ocsr *A = &L->A;
+    int64_t n = A->nr, nc = L->nc;
+    int st;
+    int64_t *cpts = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    for (int64_t i = 0; i < n; ++i) if (L->cf[i] == CF_C) cpts[L->cidx[i]] = i;
+    /* R: neighbourhoods from the kept pattern */
+    int64_t *nb_rp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+    int32_t *nb_col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(L->R.rp[nc] + 1));
+    int64_t q = 0;
+    nb_rp[0] = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int64_t k = L->R.rp[c]; k < L->R.rp[c + 1]; ++k)
+            if (L->R.col[k] != cpts[c]) nb_col[q++] = L->R.col[k];
+        nb_rp[c + 1] = q;
+    }
+    ocsr R2;
+    memset(&R2, 0, sizeof R2);
+    st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &R2, L->ls_R);
+    free(nb_rp); free(nb_col);
+    if (st || !same_pattern(&R2, &L->R)) { csr_free(&R2); free(cpts); return st ? st : ORA_ERR_ARG; }
+    csr_free(&L->R);
+    L->R = R2;
+    if (o->interp != 1) {
+        /* lAIP: Q_c = the fine rows of column c of P, without c's own point */
+        ocsr PT;
+        csr_transpose(&L->P, &PT);
+        int64_t *q_rp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+        int32_t *q_col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(PT.rp[nc] + 1));
+        q = 0;
+        q_rp[0] = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            for (int64_t k = PT.rp[c]; k < PT.rp[c + 1]; ++k)
+                if (PT.col[k] != cpts[c]) q_col[q++] = PT.col[k];
+            q_rp[c + 1] = q;
+        }
+        csr_free(&PT);
+        ocsr P2;
+        memset(&P2, 0, sizeof P2);
+        st = build_P_laip_on(A, nc, cpts, q_rp, q_col, o->prec, &P2, L->ls_P);
+        free(q_rp); free(q_col);
+        if (st || !same_pattern(&P2, &L->P)) { csr_free(&P2); free(cpts); return st ? st : ORA_ERR_ARG; }
+        csr_free(&L->P);
+        L->P = P2;
+    }
+    free(cpts);
+    for (int64_t c = 0; c < nc; ++c) {
+        H->singular_R += L->ls_R[c];
+        if (L->ls_P) H->singular_P += L->ls_P[c];
+    }
+    ocsr RA, K;
+    spgemm(&L->R, A, &RA);
+    spgemm(&RA, &L->P, &K);
+    csr_free(&RA);
+    ocsr *An = &H->lev[l + 1].A;
+    if (o->lump_tol > 0.0) {
+        st = lump_on_pattern(&K, An);
+    } else if (same_pattern(&K, An)) {
+        memcpy(An->val, K.val, sizeof(double) * (size_t)K.rp[K.nr]);
+        st = ORA_OK;
+    } else {
+        st = ORA_ERR_ARG;
+    }
+    csr_free(&K);
+    return st;
+}
+
+int ora_refresh(ohier *H, int64_t n, const int64_t *rp, const int32_t *col, const double *val) {
+    const ora_opts *o = &H->o;
+    ocsr *A0 = &H->lev[0].A;
+    if (n != A0->nr) return ORA_ERR_ARG;
+    ocsr T;
+    int64_t nnz = o->block_size > 1 ? ora_block_scale_nnz(n, rp, col, o->block_size) : rp[n];
+    if (csr_alloc(&T, n, n, nnz)) return ORA_ERR_OOM;
+    int st = ORA_OK;
+    if (o->block_size > 1) {
+        st = ora_block_scale(n, rp, col, val, H->bs, T.rp, T.col, T.val, H->blk_inv);
+    } else {
+        memcpy(T.rp, rp, sizeof(int64_t) * (size_t)(n + 1));
+        memcpy(T.col, col, sizeof(int32_t) * (size_t)nnz);
+        memcpy(T.val, val, sizeof(double) * (size_t)nnz);
+    }
+    if (!st) {
+        if (o->lump_level0 && o->lump_tol > 0.0) st = lump_on_pattern(&T, A0);
+        else if (same_pattern(&T, A0)) memcpy(A0->val, T.val, sizeof(double) * (size_t)nnz);
+        else st = ORA_ERR_ARG;
+    }
+    csr_free(&T);
+    if (st) return st;
+    H->singular_R = H->singular_P = 0;
+    for (int l = 0; l < H->nlev; ++l) {
+        if (l + 1 < H->nlev) {
+            st = refresh_level(H, l);
+            if (st) return st;
+        }
+        unfinish_level(H, l);
+        st = finish_level(H, l);
+        if (st) return st;
+    }
+    free(H->coarse.LU); free(H->coarse.perm);
+    memset(&H->coarse, 0, sizeof H->coarse);
+    return dense_factor(&H->lev[H->nlev - 1].A, &H->coarse);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -85,6 +85,8 @@ def lib():
         L.ora_solve_batched_fgmres.restype = C.c_int
         L.ora_solve_batched_fgmres.argtypes = [p, p, p, C.c_double, C.c_int, C.c_int, p, p]
         L.ora_transpose.restype = C.c_int64
+        L.ora_refresh.restype = C.c_int
+        L.ora_refresh.argtypes = [p, C.c_int64, p, p, p]
         L.ora_transpose.argtypes = [C.c_int64, p, p, p, p, p, p]
         _lib = L
     return _lib
@@ -176,6 +178,16 @@ class Hierarchy:
                     L.ora_export_csr(self.h, l, 1, *(_ptr(a) for a in R))
                     L.ora_export_csr(self.h, l, 2, *(_ptr(a) for a in P))
             self.levels.append(Level(n, A, cf, strong, R, P, lsr, lsp))
+
+    def refresh(self, A):
+        """New values of the set-up matrix's pattern: every value of the hierarchy is recomputed with
+        the splittings, neighbourhoods and patterns kept. Returns the oracle status."""
+        rp, col, val = _csr_arrays(A)
+        self.status = lib().ora_refresh(self.h, A.n, _ptr(rp), _ptr(col), _ptr(val))
+        self.levels = []
+        if self.status == 0:
+            self._export()
+        return self.status
 
     def singular_count(self, which=0):
         return int(lib().ora_singular_count(self.h, which))
