@@ -60,6 +60,7 @@ def parse():
                    help="outer iteration (default: the workload's, FGMRES(30))")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-refresh", action="store_true", help="skip the time-stepping (refresh + solve) measurement")
     return p.parse_args()
 
 
@@ -385,6 +386,49 @@ def main():
                "h2d_bytes_per_step": int((n + 1) * 8 + nnz * 4 + nnz * 8 + 2 * n * 8),
                "d2h_bytes_per_step": int(n * 8), "ms_per_step": mse}
 
+    # ---- reuse across time steps (backward Euler, I + dt S with a changing dt): one hierarchy, refreshed with
+    # new values on the same pattern before every solve; alternates between the workload's matrix and one with
+    # its diagonal scaled by 1.25. Not part of the headline: set-up + solve from scratch is.
+    tstep = None
+    if not args.no_refresh:
+        rows = torch.repeat_interleave(torch.arange(n, device=dev), rp[1:] - rp[:-1])
+        val2 = torch.where(rows == col.long(), 1.25 * val, val)
+        if offs is not None:
+            G = lair.Hierarchy.batched(rp, col, val, offs, precision=lair.MIXED, stream=stream, **wl["opts"])
+        else:
+            G = lair.Hierarchy(rp, col, val, precision=lair.MIXED, stream=stream, **wl["opts"])
+        ref_ms, sol_ms, ts_its = [], [], []
+        nts = min(args.steps, 5)
+        for i in range(2 + nts):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            evm = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            G.refresh(val2 if i % 2 == 0 else val)
+            evm.record(stream)
+            with torch.cuda.stream(stream):
+                x.zero_()
+            if offs is not None:
+                _, sys_its, _, st = G.solve_batched(b, x, tol=wl["tol"], cycle=cycle, max_iter=2000)
+                it = int(sys_its.max())
+            else:
+                _, rep = G.solve(b, x, tol=wl["tol"], cycle=cycle, max_iter=500)
+                st, it = rep.status, rep.iters
+            ev1.record(stream)
+            ev1.synchronize()
+            if st != 0:
+                raise RuntimeError(f"time step {i}: solve after refresh did not converge (status {st})")
+            if i >= 2:
+                ref_ms.append(ev0.elapsed_time(evm))
+                sol_ms.append(evm.elapsed_time(ev1))
+                ts_its.append(it)
+        G.close()
+        tstep = {"refresh_ms": dist.max(sum(ref_ms) / len(ref_ms)), "solve_ms": dist.max(sum(sol_ms) / len(sol_ms)),
+                 "iters": ts_its, "steps": nts, "fresh_setup_ms": dist.max(sum(su_mixed) / len(su_mixed)),
+                 "matrices": "the workload's and its diagonal x 1.25, alternating; refresh + solve per step"}
+
     # ---- roofline of the dominant timed kernel (largest accumulated time)
     peak, peak_src = load_peaks()
     # single-kernel timers only (the V-cycle, CGS2 and residual regions span several kernels)
@@ -424,6 +468,7 @@ def main():
         "mixed_over_fp64": ms64 / ms_mixed,
         "hierarchy": hier,
         "setup_phases_ms": {k[len("setup_"):]: v[1] / args.steps for k, v in timers.items() if k.startswith("setup_")},
+        "time_step_reuse": tstep,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }

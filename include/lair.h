@@ -141,6 +141,22 @@ lair_status lair_options_default(lair_options *o);
  * handle (for lair_last_error) that must be freed. */
 lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **h);
 
+/* New values for the matrix the hierarchy was built for, on the same pattern: the
+ * backward Euler matrix I + dt S of Sec. 4.1.1 when dt or the coefficients change
+ * between time steps. val holds A's nnz values in the order of the set-up's CSR (host
+ * or device; read before the call returns). The C/F splittings, the neighbourhoods of
+ * the local systems (Sec. 3.1), the patterns of R, P and every coarse operator (after
+ * lumping, Sec. 3.3), every allocation and the captured cycle are kept; every value is
+ * recomputed in the set-up's arithmetic: block scaling, R and lAIP by their local
+ * systems on the kept sets, one-point P unchanged (all ones), R A P, the entries of the
+ * product outside the kept coarse pattern lumped to the diagonal in ascending column
+ * order, Jacobi diagonals, FP32 copies, the coarsest factorisation. An adjoint
+ * hierarchy, if built, is refreshed too. With the set-up's own values the result is
+ * the set-up's, bit for bit. Errors: LAIR_ERR_INVALID_ARG (NULL arguments, a handle
+ * without a complete hierarchy), LAIR_ERR_ZERO_DIAGONAL (a zero pivot on some level);
+ * after an error the hierarchy's values are unspecified until a successful refresh. */
+lair_status lair_refresh(lair_handle *h, const double *val);
+
 /* Solve A x = b to ||b - A x||/||b|| <= tol. x holds the initial guess on entry
  * (host or device, n doubles) and the result on return. cycle is a lair_cycle;
  * max_iter bounds the V-cycles. rep may be NULL. Returns LAIR_ERR_NOT_CONVERGED

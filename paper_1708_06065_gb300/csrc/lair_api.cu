@@ -64,6 +64,9 @@ struct Hier {
     int graph_nodes = 0;
     long long singular_R = 0, singular_P = 0;
     double setup_ms = 0.0;
+    // the sliced-ELL fill descriptors of all views (device), kept so that a refresh refills the views in place
+    SellDesc *sell_desc = nullptr;
+    int sell_gp[3] = {0, 0, 0}, sell_glin[3] = {0, 0, 0};
 };
 
 }  // namespace lair
@@ -883,7 +886,7 @@ struct SellPlan {
     bool fp32;
 };
 
-static lair_status build_sells(lair_handle *h, std::vector<SellPlan> &plans) {
+static lair_status build_sells(lair_handle *h, Hier &H, std::vector<SellPlan> &plans) {
     Temps t(h);
     std::vector<SellDesc> hd;
     std::vector<SellPlan *> hp;
@@ -930,7 +933,7 @@ static lair_status build_sells(lair_handle *h, std::vector<SellPlan> &plans) {
     SellDesc *dd;
     int *cnt, *sp, *tot;
     unsigned long long *gsum;
-    TRY(t.get(&dd, (size_t)nd));
+    TRY(dalloc(h, &dd, (size_t)nd));
     TRY(new_counts(h, t, &cnt, sl));
     TRY(t.get(&gsum, 2));
     TRY(t.get(&tot, 6));
@@ -978,7 +981,20 @@ static lair_status build_sells(lair_handle *h, std::vector<SellPlan> &plans) {
     CU(cudaMemcpyAsync(dd, hd.data(), sizeof(SellDesc) * nd, cudaMemcpyHostToDevice, h->s));
     // (a copy from pageable memory is staged before cudaMemcpyAsync returns, so hd may go)
     for (int g = 0; g < 2; ++g) launch_sell_fill_multi(dd, gp[g], gp[g + 1], glin[g], glin[g + 1], g == 0, h->s);
+    H.sell_desc = dd;
+    for (int g = 0; g < 3; ++g) {
+        H.sell_gp[g] = gp[g];
+        H.sell_glin[g] = glin[g];
+    }
     return LAIR_OK;
+}
+
+// refill every view's values (and Jacobi diagonals) from the matrices they were built from
+static void refill_sells(lair_handle *h, Hier &H) {
+    if (!H.sell_desc) return;
+    for (int g = 0; g < 2; ++g)
+        launch_sell_fill_multi(H.sell_desc, H.sell_gp[g], H.sell_gp[g + 1], H.sell_glin[g], H.sell_glin[g + 1], g == 0,
+                               h->s);
 }
 
 // the sliced-ELL views of level l (built for all levels at once when the hierarchy is complete)
@@ -1225,11 +1241,145 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         int tv = tbegin(h, "setup_views", 0.0);
         std::vector<SellPlan> plans;
         for (int l = 0; l < (int)H.lev.size(); ++l) add_view_plans(h, H, l, plans);
-        TRY(build_sells(h, plans));
+        TRY(build_sells(h, H, plans));
         tend(h, tv);
     }
     tp = tbegin(h, "setup_graph", 0.0);
     TRY(capture_cycle(h, H));
+    tend(h, tp);
+    CU(cudaStreamSynchronize(h->s));
+    flush_timers(h);
+    H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return LAIR_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// refresh: new values on the set-up matrix's pattern (backward Euler steps I + dt S, Sec. 4.1.1,
+// with a new dt or new coefficients). The splittings, neighbourhoods and the patterns of R, P and
+// every coarse operator are kept, so is every allocation, view and the captured cycle graph; every
+// value is recomputed in the set-up's arithmetic.
+// ---------------------------------------------------------------------------------------
+
+// local solves on kept sets: set c is row c of (rp, col) without cpts[c] (nnz entries in all); the
+// solution row is written at rp[c] in the layout local_rows writes it
+static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
+                                 int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
+                                 float *oval32, uint8_t *lsflag) {
+    if (nc <= 0) return LAIR_OK;
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    int *nb_rp, *nb_col, *lists, *bcounts;
+    TRY(t.get(&nb_rp, (size_t)nc + 1));
+    TRY(t.get(&nb_col, (size_t)(nnz - nc) + 1));
+    launch_nb_from_rows(nc, rp, col, cpts, nb_rp, nb_col, h->s);
+    TRY(t.get(&lists, (size_t)3 * nc + 1));
+    TRY(new_counts(h, t, &bcounts, 5));
+    launch_local_bin(nc, nb_rp, lists, bcounts, bcounts + 3, h->s);
+    int hc[4];
+    TRY(read_ints(h, bcounts, 4, hc));
+    void *scratch = nullptr;
+    if (hc[2] > 0) {
+        unsigned char *sp;
+        TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
+        scratch = sp;
+    }
+    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag};
+    CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
+    return LAIR_OK;
+}
+
+static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
+    Temps t(h);
+    Level &L = H.lev[l];
+    const DCsr &A = L.A;
+    const int n = A.nr, nc = L.nc;
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    TRY(local_rows_on(h, t, nc, L.crows, L.R.rp, L.R.col, L.R.nnz, A.rp, A.col, A.val, L.R.col, L.R.val,
+                      fp32 ? L.R.val32 : nullptr, L.lsR));
+    if (h->o.interp != LAIR_P_ONEPOINT) {
+        // lAIP: the sets are the columns of P without their C point; the local systems are those of A^T,
+        // solved into W = P^T by rows and transposed back onto P's pattern
+        int *ptrp, *ptcol, *atrp, *atcol, *wcol, *prp, *pcol;
+        double *atval, *wval, *pval;
+        TRY(transpose(h, t, n, nc, L.P.nnz, L.P.rp, L.P.col, nullptr, &ptrp, &ptcol, nullptr, false));
+        TRY(transpose(h, t, n, n, A.nnz, A.rp, A.col, A.val, &atrp, &atcol, &atval, false));
+        TRY(t.get(&wcol, (size_t)L.P.nnz));
+        TRY(t.get(&wval, (size_t)L.P.nnz));
+        TRY(local_rows_on(h, t, nc, L.crows, ptrp, ptcol, L.P.nnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP));
+        TRY(transpose(h, t, nc, n, L.P.nnz, ptrp, wcol, wval, &prp, &pcol, &pval, false));
+        CU(cudaMemcpyAsync(L.P.val, pval, sizeof(double) * (size_t)L.P.nnz, cudaMemcpyDeviceToDevice, h->s));
+        if (fp32) launch_to_f32(L.P.nnz, L.P.val, L.P.val32, h->s);
+    }
+    // one-point P keeps its values (all 1)
+    DCsr RA, K;
+    int *klen = nullptr;
+    if (h->o.interp == LAIR_P_ONEPOINT) {
+        TRY(spgemm(h, t, L.R, A, K, false, -1, &L.P, &klen));
+    } else {
+        TRY(spgemm(h, t, L.R, A, RA, false));
+        TRY(spgemm(h, t, RA, L.P, K, false, -1, nullptr, &klen));
+    }
+    // without lumping the kept pattern is the whole product and nothing is added to the diagonal
+    launch_lump_kept(K, klen, H.lev[l + 1].A, h->status, h->s);
+    return LAIR_OK;
+}
+
+static lair_status refresh_hierarchy(lair_handle *h, Hier &H, const DCsr &Ain) {
+    auto t0 = std::chrono::steady_clock::now();
+    const lair_options &o = h->o;
+    const bool fp32 = o.precision == LAIR_MIXED;
+    int tp = tbegin(h, "refresh", 0.0);
+    {
+        Temps t(h);
+        Level &L0 = H.lev[0];
+        const bool lump0 = o.lump_level0 && o.lump_tol > 0.0;
+        DCsr A = Ain;
+        if (H.bs > 1) {
+            const int bs = H.bs, nblk = A.nr / bs;
+            DCsr B = L0.A;
+            if (lump0) {
+                int *rowcnt;
+                TRY(new_counts(h, t, &rowcnt, A.nr));
+                launch_block_count(nblk, bs, A, rowcnt, h->s);
+                TRY(t.get(&B.rp, (size_t)A.nr + 1));
+                TRY(scan(h, rowcnt, B.rp, A.nr, &B.nnz));
+                TRY(t.get(&B.col, (size_t)B.nnz));
+                TRY(t.get(&B.val, (size_t)B.nnz));
+            }
+            launch_block_fill(nblk, bs, A, B, H.blk_inv, h->status, h->s);
+            A = B;
+        }
+        if (lump0) launch_lump_kept(A, nullptr, L0.A, h->status, h->s);
+        else if (A.val != L0.A.val)
+            CU(cudaMemcpyAsync(L0.A.val, A.val, sizeof(double) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, h->s));
+    }
+    const int nl = (int)H.lev.size();
+    for (int l = 0; l + 1 < nl; ++l) TRY(refresh_level(h, H, l));
+    {
+        Temps t(h);
+        int *c2;
+        TRY(new_counts(h, t, &c2, 2));
+        for (int l = 0; l < nl; ++l) {
+            Level &L = H.lev[l];
+            launch_dinv(L.A, L.dinv, L.dinv32, h->status, h->s);
+            if (fp32) launch_to_f32(L.A.nnz, L.A.val, L.A.val32, h->s);
+            if (L.coarsest) {
+                const int n = L.A.nr;
+                double *D;
+                int *perm;
+                TRY(t.get(&D, (size_t)n * n));
+                TRY(t.get(&perm, (size_t)n));
+                launch_dense_setup(L.A, D, perm, L.Ainv, h->status, h->s);
+            } else {
+                if (L.lsR) count_flags(L.nc, L.lsR, c2, h->s);
+                if (L.lsP) count_flags(L.nc, L.lsP, c2 + 1, h->s);
+            }
+        }
+        refill_sells(h, H);
+        int hc[2];
+        TRY(read_ints(h, c2, 2, hc));   // also checks the status word
+        H.singular_R = hc[0];
+        H.singular_P = hc[1];
+    }
     tend(h, tp);
     CU(cudaStreamSynchronize(h->s));
     flush_timers(h);
@@ -1909,6 +2059,25 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **o
     const int8_t *cfu = h->o.cf_mode == LAIR_CF_USER ? h->o.cf_user : nullptr;
     TRY(build_hierarchy(h, h->H, h->A_in, cfu));
     h->o.cf_user = nullptr;   // never retained
+    return LAIR_OK;
+}
+
+lair_status lair_refresh(lair_handle *h, const double *val) {
+    if (!h || !val) return LAIR_ERR_INVALID_ARG;
+    if (h->H.lev.empty() || !h->H.lev.back().Ainv) return fail(h, LAIR_ERR_INVALID_ARG, "no hierarchy to refresh");
+    LaunchScope ls(h);
+    const DCsr &A = h->A_in;
+    CU(cudaMemcpyAsync(A.val, val, sizeof(double) * (size_t)A.nnz,
+                       is_device_ptr(val) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    TRY(refresh_hierarchy(h, h->H, A));
+    if (h->HT) {
+        Temps t(h);
+        DCsr AT;
+        AT.nr = AT.nc = A.nr;
+        AT.nnz = A.nnz;
+        TRY(transpose(h, t, A.nr, A.nr, A.nnz, A.rp, A.col, A.val, &AT.rp, &AT.col, &AT.val, false));
+        TRY(refresh_hierarchy(h, *h->HT, AT));
+    }
     return LAIR_OK;
 }
 

@@ -930,4 +930,25 @@ void launch_nb_compact(int nc, const int *off, const int *tmp, const int *nb_rp,
     count_launch();
 }
 
+// neighbourhoods read off a kept operator (hierarchy refresh): row c of (rp, col) is the neighbourhood of C point
+// cpts[c] plus that point itself (R = [Z I] by rows, P^T by rows), so set c is the row without cpts[c]
+__global__ void k_nb_from_rows(int nc, const int *__restrict__ rp, const int *__restrict__ col,
+                               const int *__restrict__ cpts, int *__restrict__ nb_rp, int *__restrict__ nb_col) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+        const int b = rp[c], e = rp[c + 1], self = cpts[c];
+        int q = b - c;
+        nb_rp[c] = q;
+        if (c == nc - 1) nb_rp[nc] = e - nc;
+        for (int k = b; k < e; ++k)
+            if (col[k] != self) nb_col[q++] = col[k];
+    }
+}
+
+void launch_nb_from_rows(int nc, const int *rp, const int *col, const int *cpts, int *nb_rp, int *nb_col,
+                         cudaStream_t s) {
+    if (nc <= 0) return;
+    k_nb_from_rows<<<grid_for(nc, TB), TB, 0, s>>>(nc, rp, col, cpts, nb_rp, nb_col);
+    count_launch();
+}
+
 }  // namespace lair

@@ -37,6 +37,9 @@ void launch_nb_bound(int nc, const int *cpts, const Graph &G, const int8_t *cf, 
 void launch_nb_fill(int nc, const int *cpts, const Graph &G, const int8_t *cf, int distance, const int *off, int *tmp,
                     int *cnt, cudaStream_t s);
 void launch_nb_compact(int nc, const int *off, const int *tmp, const int *nb_rp, int *nb_col, cudaStream_t s);
+// the sets of kept rows that hold their C point once each: row c of (rp, col) without cpts[c]
+void launch_nb_from_rows(int nc, const int *rp, const int *col, const int *cpts, int *nb_rp, int *nb_col,
+                         cudaStream_t s);
 // one more distance: phase 0 writes the bound to cnt, phase 1 the sets at off (sizes in cnt)
 void launch_nb_expand(int phase, int nc, const int *cpts, const Graph &G, const int8_t *cf, const int *nb_rp,
                       const int *nb_col, const int *off, int *tmp, int *cnt, cudaStream_t s);
@@ -100,6 +103,8 @@ void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tva
 // K's rows: rp[i] .. rp[i + 1], or rp[i] .. rp[i] + len[i] when len is given
 void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
                  int *status, cudaStream_t s);
+// the values of out (a kept pattern inside K's) from K: entries of K outside it are lumped to the diagonal
+void launch_lump_kept(const DCsr &K, const int *len, const DCsr &out, int *status, cudaStream_t s);
 void launch_dinv(const DCsr &A, double *dinv, float *dinv32, int *status, cudaStream_t s);
 void launch_to_f32(long long n, const double *a, float *b, cudaStream_t s);
 void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s);

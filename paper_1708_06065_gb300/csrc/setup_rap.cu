@@ -687,6 +687,42 @@ void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt,
     count_launch();
 }
 
+// Lumping onto a kept pattern (hierarchy refresh, Sec. 3.3): row i of the output keeps exactly its
+// columns; every other entry of row i of K is added to the diagonal in ascending column order from
+// k_ii (the order of k_lump_count when the dropped set is the same); kept entries take K's value.
+// Both rows ascending; the kept row must be a subset of K's row that holds the diagonal.
+__global__ void k_lump_kept(int n, const int *__restrict__ rp, const int *__restrict__ len, const int *__restrict__ col,
+                            const double *__restrict__ val, const int *__restrict__ orp, const int *__restrict__ ocol,
+                            double *__restrict__ oval, int *status) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = rp[i], e = len ? b + len[i] : rp[i + 1];
+        const int t0 = orp[i], t1 = orp[i + 1];
+        double d = 0.0;
+        for (int k = b; k < e; ++k)
+            if (col[k] == i) d = val[k];
+        int t = t0, dpos = -1;
+        for (int k = b; k < e; ++k) {
+            const int j = col[k];
+            const bool kept = t < t1 && ocol[t] == j;
+            if (kept) {
+                if (j == i) dpos = t;
+                else oval[t] = val[k];
+                ++t;
+            } else if (j != i) {
+                d = __dadd_rn(d, val[k]);
+            }
+        }
+        if (t != t1 || dpos < 0) set_status(status, t != t1 ? LAIR_ERR_INVALID_ARG : LAIR_ERR_ZERO_DIAGONAL);
+        else oval[dpos] = d;
+    }
+}
+
+void launch_lump_kept(const DCsr &K, const int *len, const DCsr &out, int *status, cudaStream_t s) {
+    if (K.nr <= 0) return;
+    k_lump_kept<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, out.rp, out.col, out.val, status);
+    count_launch();
+}
+
 // ---------------------------------------------------------------------------------------
 // Jacobi diagonal inverse (1 / a_ii, IEEE division) and FP32 copies
 // ---------------------------------------------------------------------------------------

@@ -73,6 +73,7 @@ def _load():
         "lair_options_default": (C.c_int, [C.POINTER(lair_options)]),
         "lair_setup": (C.c_int, [C.POINTER(lair_csr), C.POINTER(lair_options), C.POINTER(p)]),
         "lair_solve": (C.c_int, [p, p, p, C.c_double, C.c_int, C.c_int, C.POINTER(lair_report)]),
+        "lair_refresh": (C.c_int, [p, p]),
         "lair_precond_apply": (C.c_int, [p, p, p]),
         "lair_adjoint": (C.c_int, [p, p, p, C.c_double, C.c_int, C.c_int, C.POINTER(lair_report)]),
         "lair_grad_A": (C.c_int, [p, p, p, p]),
@@ -252,6 +253,18 @@ class Hierarchy:
         self._check(st, ok)
         return Report(st, rep.iters, rep.final_rel, rep.setup_ms, rep.solve_ms, rep.nlevels, rep.singular_R,
                       rep.singular_P, rep.op_complexity, rep.cycle_complexity, hist[:rep.hist_len].copy())
+
+    def refresh(self, val):
+        """New values (numpy or torch float64, nnz entries in the set-up's CSR order) on the set-up's
+        pattern: every value of the hierarchy is recomputed, its structure is kept."""
+        if isinstance(val, np.ndarray):
+            if val.dtype != np.float64 or not val.flags.c_contiguous or val.shape != (self.nnz,):
+                raise ValueError("val must be contiguous float64 with nnz entries")
+        else:
+            import torch
+            if val.dtype != torch.float64 or not val.is_contiguous() or val.numel() != self.nnz:
+                raise ValueError("val must be contiguous float64 with nnz entries")
+        self._check(lib.lair_refresh(self._h, _ptr(val)))
 
     def solve(self, b, x=None, tol=1e-8, cycle=FGMRES, max_iter=500, hist_cap=4096, raise_on_nc=False):
         """Solve in place into x (numpy or torch, float64); returns (x, Report)."""

@@ -1,5 +1,19 @@
-"""Shared test helpers: comparing a GPU hierarchy with an oracle hierarchy."""
+"""Shared test helpers: comparing a GPU hierarchy with an oracle hierarchy; new values on a pattern."""
 import numpy as np
+
+import workloads as W
+
+
+def with_values(s, val, b=None):
+    """The system s with new values on its pattern (and optionally a new right-hand side)."""
+    return W.CsrSystem(s.n, s.row_ptr.copy(), s.col.copy(), np.asarray(val, np.float64).copy(),
+                       s.b.copy() if b is None else b)
+
+
+def backward_euler(s, dt):
+    """I + dt S on S's pattern (S has an explicit diagonal): the time step of Sec. 4.1.1."""
+    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+    return with_values(s, dt * s.val + (rows == s.col))
 
 
 def max_rel(a, b):

@@ -24,23 +24,12 @@ import scipy.sparse.linalg as spla
 
 import workloads as W
 from oracle import oracle as O
+from tests.helpers import backward_euler, with_values
 
 
 def csr_to_scipy(t, shape):
     rp, col, val = t
     return sp.csr_matrix((val, col.astype(np.int64), rp), shape=shape)
-
-
-def with_values(s, val, b=None):
-    return W.CsrSystem(s.n, s.row_ptr.copy(), s.col.copy(), np.asarray(val, np.float64).copy(),
-                       s.b.copy() if b is None else b)
-
-
-def backward_euler(s, dt):
-    """I + dt S on S's pattern (S has an explicit diagonal)."""
-    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
-    val = dt * s.val + (rows == s.col)
-    return with_values(s, val)
 
 
 def assert_same_hierarchy(H1, H2):
