@@ -22,6 +22,7 @@
  *   lumping ........................ Sec. 3.3
  *   V-cycle with post F-F-C Jacobi . Sec. 4, Eq. (2.4)
  *   GMRES acceleration ............. Sec. 4 (here flexible GMRES, FP64)
+ *   Neumann restriction (nAIR) ..... Sec. 3.2, truncated Neumann series of A_ff^{-1}
  *   refresh for new values ......... backward Euler steps I + dt S (Sec. 4.1.1):
  *                                    structure kept, every value recomputed
  *
@@ -71,6 +72,7 @@ typedef struct {
     uint64_t pmis_seed;
     const int64_t *seg;    /* batched systems: nseg + 1 offsets of the independent systems on level 0 */
     int nseg;
+    int restriction;       /* 0 lAIR (Sec. 3.1), 1 Neumann nAIR of degree distance - 1 (Sec. 3.2) */
 } ora_opts;
 
 /* ------------------------------------------------------------------------- */
@@ -743,6 +745,91 @@ static int build_lair_R(const ocsr *A, const int8_t *cf, const int64_t *cidx, in
 }
 
 /* ------------------------------------------------------------------------- */
+/* Neumann restriction, nAIR (Sec. 3.2). For A with unit diagonal and         */
+/* A_ff = I - L_ff the paper takes Z = -A_cf sum_{m=0}^{k} L_ff^m. A general A */
+/* is brought to unit diagonal by D^{-1} A and the result scaled back          */
+/* (Z = D_c Z^ D_f^{-1}), which gives                                          */
+/*     Z = -A_cf sum_{m=0}^{k} (D_ff^{-1} E_ff)^m D_ff^{-1},  E_ff = D_ff - A_ff,  */
+/* and keeps the row-scaling invariance of Sec. 3.1. Row i of Z as a row      */
+/* vector over all F points: y_0 = -a_{i,F} D_ff^{-1}, y_{m+1} = y_m E_ff       */
+/* D_ff^{-1}, that is y_{m+1}[l] = -(sum_{j in F, j != l} y_m[j] a_{j,l}) / a_ll */
+/* (fma from 0 in ascending j), and z = y_0 + y_1 + ... + y_k in that order.    */
+/* Every nonzero of A counts (no strength filter): z is supported on the F     */
+/* points joined to i by a path of at most k + 1 edges whose points after i    */
+/* are all F, the neighbourhood of distance k + 1 in the graph of A; R's row   */
+/* holds that whole set (structural zeros kept) and (i, 1). In FP32 mode the    */
+/* values are rounded to float and the series summed in float.                */
+/* ------------------------------------------------------------------------- */
+static int build_R_neumann(const ocsr *A, const int8_t *cf, int64_t nc, const int64_t *cpts, const int64_t *nb_rp,
+                           const int32_t *nb_col, int k, int prec, ocsr *R) {
+    int64_t n = A->nr;
+    int64_t nnz = nb_rp[nc] + nc;
+    if (csr_alloc(R, nc, n, nnz)) return ORA_ERR_OOM;
+    ocsr AT;
+    csr_transpose(A, &AT);   /* row l of A^T: the entries a_{j,l}, ascending j */
+    double *diag = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t l = 0; l < n; ++l) find_entry(A, l, l, &diag[l]);
+    double *y = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *yn = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *z = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    float *yf = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
+    float *ynf = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
+    float *zf = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
+    int st = ORA_OK;
+    int64_t p = 0;
+    for (int64_t c = 0; c < nc && st == ORA_OK; ++c) {
+        int64_t i = cpts[c];
+        for (int64_t l = 0; l < n; ++l) { y[l] = yn[l] = z[l] = 0.0; yf[l] = ynf[l] = zf[l] = 0.0f; }
+        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
+            int64_t l = A->col[q];
+            if (l == i || cf[l] != CF_F) continue;
+            if (prec == 0) { y[l] = -A->val[q] / diag[l]; z[l] = y[l]; }
+            else { yf[l] = -(float)A->val[q] / (float)diag[l]; zf[l] = yf[l]; }
+        }
+        for (int m = 1; m <= k; ++m) {
+            for (int64_t l = 0; l < n; ++l) {
+                if (cf[l] != CF_F) continue;
+                double acc = 0.0;
+                float accf = 0.0f;
+                for (int64_t q = AT.rp[l]; q < AT.rp[l + 1]; ++q) {
+                    int64_t j = AT.col[q];
+                    if (j == l || cf[j] != CF_F) continue;
+                    if (prec == 0) acc = fma(y[j], AT.val[q], acc);
+                    else accf = fmaf(yf[j], (float)AT.val[q], accf);
+                }
+                if (prec == 0) yn[l] = -acc / diag[l];
+                else ynf[l] = -accf / (float)diag[l];
+            }
+            for (int64_t l = 0; l < n; ++l) {
+                if (cf[l] != CF_F) continue;
+                if (prec == 0) { y[l] = yn[l]; z[l] = z[l] + y[l]; }
+                else { yf[l] = ynf[l]; zf[l] = zf[l] + yf[l]; }
+            }
+        }
+        /* the row: the neighbourhood (ascending) merged with (i, 1); nothing may lie outside it */
+        const int32_t *nb = nb_col + nb_rp[c];
+        int64_t s = nb_rp[c + 1] - nb_rp[c], inside = 0;
+        int placed = 0;
+        for (int64_t r = 0; r < s; ++r) {
+            if (!placed && i < nb[r]) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; placed = 1; }
+            R->col[p] = nb[r];
+            R->val[p] = prec == 0 ? z[nb[r]] : (double)zf[nb[r]];
+            p++;
+        }
+        if (!placed) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; }
+        R->rp[c + 1] = p;
+        for (int64_t l = 0; l < n; ++l)
+            if ((prec == 0 ? z[l] != 0.0 : zf[l] != 0.0f)) inside++;
+        for (int64_t r = 0; r < s; ++r)
+            if ((prec == 0 ? z[nb[r]] != 0.0 : zf[nb[r]] != 0.0f)) inside--;
+        if (inside != 0) st = ORA_ERR_ARG;   /* a value outside the neighbourhood: the sets are wrong */
+    }
+    csr_free(&AT);
+    free(diag); free(y); free(yn); free(z); free(yf); free(ynf); free(zf);
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Interpolation P = [W; I] (Eq. (2.2)).                                      */
 /* One-point (Sec. 4): F row j takes value 1 at its strongest C connection     */
 /* c in N_j (largest -a_jc, abs mode |a_jc|; ties -> smallest c), none -> an   */
@@ -1223,9 +1310,21 @@ static int coarsen_level(ohier *H, int l, int *is_last) {
     int64_t *cpts = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
     for (int64_t i = 0; i < n; ++i) if (L->cf[i] == CF_C) cpts[L->cidx[i]] = i;
     int64_t *nb_rp; int32_t *nb_col;
-    build_neighbourhoods(&S, L->cf, o->distance, nc, cpts, &nb_rp, &nb_col);
     L->ls_R = (uint8_t *)calloc((size_t)nc, 1);
-    st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &L->R, L->ls_R);
+    if (o->restriction == 1) {
+        /* nAIR: the sets come from the graph of every nonzero off-diagonal of A */
+        uint8_t *all = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+        ora_strength(n, A->rp, A->col, A->val, 0.0, 1, all);
+        ograph G;
+        graph_from_mask(n, A->rp, A->col, all, &G);
+        free(all);
+        build_neighbourhoods(&G, L->cf, o->distance, nc, cpts, &nb_rp, &nb_col);
+        graph_free(&G);
+        st = build_R_neumann(A, L->cf, nc, cpts, nb_rp, nb_col, o->distance - 1, o->prec, &L->R);
+    } else {
+        build_neighbourhoods(&S, L->cf, o->distance, nc, cpts, &nb_rp, &nb_col);
+        st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &L->R, L->ls_R);
+    }
     free(nb_rp); free(nb_col);
     if (st) return st;
     if (o->interp == 1) {
@@ -1396,7 +1495,8 @@ static int refresh_level(ohier *H, int l) {
     }
     ocsr R2;
     memset(&R2, 0, sizeof R2);
-    st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &R2, L->ls_R);
+    if (o->restriction == 1) st = build_R_neumann(A, L->cf, nc, cpts, nb_rp, nb_col, o->distance - 1, o->prec, &R2);
+    else st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &R2, L->ls_R);
     free(nb_rp); free(nb_col);
     if (st || !same_pattern(&R2, &L->R)) { csr_free(&R2); free(cpts); return st ? st : ORA_ERR_ARG; }
     csr_free(&L->R);

@@ -22,6 +22,7 @@ LIB = os.path.join(HERE, "liblair_oracle.so")
 CF_F, CF_C = 0, 1
 CF_RS, CF_PMIS, CF_USER, CF_AUTO = 0, 1, 2, 3
 P_LAIP, P_ONEPOINT = 0, 1
+R_LAIR, R_NEUMANN = 0, 1
 RELAX_FFC, RELAX_FCF, RELAX_FF = 0, 1, 2
 STATUS = {0: "OK", 1: "ARG", 5: "ZERO_DIAG", 6: "STALLED", 7: "NOT_CONVERGED", 8: "NAN", 9: "OOM"}
 
@@ -41,6 +42,7 @@ class Opts(C.Structure):
         ("interp", C.c_int), ("relax", C.c_int), ("lump_tol", C.c_double), ("lump_level0", C.c_int),
         ("prec", C.c_int), ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
         ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("seg", C.c_void_p), ("nseg", C.c_int),
+        ("restriction", C.c_int),
     ]
 
 
