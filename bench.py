@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-refresh", action="store_true", help="skip the time-stepping (refresh + solve) measurement")
+    p.add_argument("--restriction", default="lair", choices=["lair", "neumann"],
+                   help="R from the local systems (lAIR, the default) or the Neumann series (nAIR, Sec. 3.2)")
     return p.parse_args()
 
 
@@ -293,6 +295,8 @@ def main():
     torch.cuda.synchronize()
 
     cycle = lair.FGMRES if (args.cycle or wl.get("cycle", "fgmres")) == "fgmres" else lair.STATIONARY
+    if args.restriction == "neumann":
+        wl = dict(wl, opts=dict(wl["opts"], restriction=lair.R_NEUMANN), desc=wl["desc"] + ", Neumann restriction (nAIR)")
     if args.cycle:
         other = "FP64 stationary refinement" if args.cycle == "stationary" else "FP64 FGMRES(30)"
         wl = dict(wl, desc=wl["desc"].replace("FP64 FGMRES(30)", other).replace("FP64 stationary refinement", other))

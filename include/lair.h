@@ -59,6 +59,14 @@ typedef enum { LAIR_CF_RS = 0, LAIR_CF_PMIS = 1, LAIR_CF_USER = 2, LAIR_CF_AUTO 
  * neighbourhoods) or one-point interpolation (Sec. 4). */
 typedef enum { LAIR_P_LAIP = 0, LAIR_P_ONEPOINT = 1 } lair_interp;
 
+/* Restriction R = [Z I]: lAIR (Sec. 3.1: Z from the local systems of Eq. (3.2) on the
+ * strong F-neighbourhoods) or the Neumann approximation nAIR (Sec. 3.2) that the paper
+ * compares it with: Z = -A_cf sum_{m=0}^{k} (D_ff^{-1} E_ff)^m D_ff^{-1} with E_ff = D_ff - A_ff
+ * and degree k = distance - 1 (the printed -A_cf sum L_ff^m once A has a unit diagonal),
+ * supported on the F points within `distance` edges of the C point in the graph of all
+ * nonzeros of A. */
+typedef enum { LAIR_R_LAIR = 0, LAIR_R_NEUMANN = 1 } lair_restriction;
+
 /* Post-relaxation after coarse-grid correction (Sec. 4): Jacobi sweeps over
  * F, F, C points (the paper's choice), F, C, F, or F, F only. */
 typedef enum { LAIR_RELAX_FFC = 0, LAIR_RELAX_FCF = 1, LAIR_RELAX_FF = 2 } lair_relax;
@@ -105,6 +113,7 @@ typedef struct {
     void *stream;             /* cudaStream_t, or NULL (see above); never the legacy default stream itself */
     int timing;               /* 1: record CUDA-event timings of the main kernels and set-up phases
                                  (lair_kernel_timers); 2: also one timer per set-up phase and level */
+    int restriction;          /* lair_restriction (default lAIR) */
 } lair_options;
 
 typedef struct {

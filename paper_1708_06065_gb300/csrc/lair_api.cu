@@ -450,10 +450,11 @@ static lair_status new_counts(lair_handle *h, Temps &t, int **p, int n) {
 // ---------------------------------------------------------------------------------------
 // graphs and transposes
 // ---------------------------------------------------------------------------------------
-static lair_status build_strength_graph(lair_handle *h, Temps &t, const DCsr &A, double theta, uint8_t *mask, Graph &G) {
+static lair_status build_strength_graph(lair_handle *h, Temps &t, const DCsr &A, double theta, uint8_t *mask, Graph &G,
+                                        int absmode) {
     int *cnt;
     TRY(new_counts(h, t, &cnt, A.nr));
-    launch_strength(A, theta, h->o.strength_abs, mask, cnt, h->s);
+    launch_strength(A, theta, absmode, mask, cnt, h->s);
     G.n = A.nr;
     TRY(t.get(&G.rp, (size_t)A.nr + 1));
     // S is a subset of the pattern of A, so A's entry count bounds it and no read-back is needed
@@ -494,7 +495,8 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
 // ---------------------------------------------------------------------------------------
 static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
                               const int *brp, const int *bcol, const double *bval, int **out_rp, int **out_col,
-                              double **out_val, float **out_val32, uint8_t *lsflag, int *out_nnz, bool keep) {
+                              double **out_val, float **out_val32, uint8_t *lsflag, int *out_nnz, bool keep,
+                              int neumann_deg = -1) {
     const int distance = h->o.distance, d0 = distance < 2 ? distance : 2;
     int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
     TRY(new_counts(h, t, &ub, nc));
@@ -569,7 +571,7 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
         TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
         scratch = sp;
     }
-    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag};
+    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg};
     CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
     *out_nnz = nout;
     *out_rp = orp;
@@ -688,14 +690,14 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     int tp = tbegin(h, phase_name(h, "strength", l), 0.0);
     TRY(dalloc(h, &L.strong, (size_t)A.nnz));
     Graph S, ST, Scf, STcf;
-    TRY(build_strength_graph(h, t, A, o.theta, L.strong, S));
+    TRY(build_strength_graph(h, t, A, o.theta, L.strong, S, o.strength_abs));
     TRY(transpose(h, t, n, n, S.nnz, S.rp, S.col, nullptr, &ST.rp, &ST.col, nullptr, false));
     ST.n = n;
     ST.nnz = S.nnz;
     if (o.theta_cf != o.theta) {
         uint8_t *m2;
         TRY(t.get(&m2, (size_t)A.nnz));
-        TRY(build_strength_graph(h, t, A, o.theta_cf, m2, Scf));
+        TRY(build_strength_graph(h, t, A, o.theta_cf, m2, Scf, o.strength_abs));
         TRY(transpose(h, t, n, n, Scf.nnz, Scf.rp, Scf.col, nullptr, &STcf.rp, &STcf.col, nullptr, false));
         STcf.n = n;
         STcf.nnz = Scf.nnz;
@@ -791,8 +793,18 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
     TRY(dalloc(h, &L.lsR, (size_t)nc));
     L.R.nr = nc;
     L.R.nc = n;
-    TRY(local_rows(h, t, nc, cpts, S, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
-                   fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true));
+    if (o.restriction == LAIR_R_NEUMANN) {
+        // nAIR: sets from the graph of every nonzero off-diagonal (theta 0 in abs mode), series of degree distance - 1
+        Graph GA;
+        uint8_t *all;
+        TRY(t.get(&all, (size_t)A.nnz));
+        TRY(build_strength_graph(h, t, A, 0.0, all, GA, 1));
+        TRY(local_rows(h, t, nc, cpts, GA, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
+                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true, o.distance - 1));
+    } else {
+        TRY(local_rows(h, t, nc, cpts, S, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
+                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true));
+    }
 
     // ---- interpolation
     tend(h, tp);
@@ -1264,7 +1276,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
 // solution row is written at rp[c] in the layout local_rows writes it
 static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
                                  int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
-                                 float *oval32, uint8_t *lsflag) {
+                                 float *oval32, uint8_t *lsflag, int neumann_deg = -1) {
     if (nc <= 0) return LAIR_OK;
     const bool fp32 = h->o.precision == LAIR_MIXED;
     int *nb_rp, *nb_col, *lists, *bcounts;
@@ -1282,7 +1294,7 @@ static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cp
         TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
         scratch = sp;
     }
-    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag};
+    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg};
     CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
     return LAIR_OK;
 }
@@ -1294,7 +1306,8 @@ static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
     const int n = A.nr, nc = L.nc;
     const bool fp32 = h->o.precision == LAIR_MIXED;
     TRY(local_rows_on(h, t, nc, L.crows, L.R.rp, L.R.col, L.R.nnz, A.rp, A.col, A.val, L.R.col, L.R.val,
-                      fp32 ? L.R.val32 : nullptr, L.lsR));
+                      fp32 ? L.R.val32 : nullptr, L.lsR,
+                      h->o.restriction == LAIR_R_NEUMANN ? h->o.distance - 1 : -1));
     if (h->o.interp != LAIR_P_ONEPOINT) {
         // lAIP: the sets are the columns of P without their C point; the local systems are those of A^T,
         // solved into W = P^T by rows and transposed back onto P's pattern
@@ -2023,6 +2036,8 @@ static lair_status check_options(lair_handle *h, const lair_options *o) {
     if (o->cf_mode == LAIR_CF_USER && !o->cf_user) return fail(h, LAIR_ERR_INVALID_ARG, "cf_user is NULL");
     if (o->distance < 1 || o->distance > 4) return fail(h, LAIR_ERR_INVALID_ARG, "distance must be 1 to 4");
     if (o->interp < 0 || o->interp > 1) return fail(h, LAIR_ERR_INVALID_ARG, "interp %d", o->interp);
+    if (o->restriction < 0 || o->restriction > 1)
+        return fail(h, LAIR_ERR_INVALID_ARG, "restriction %d", o->restriction);
     if (o->relax < 0 || o->relax > 2) return fail(h, LAIR_ERR_INVALID_ARG, "relax %d", o->relax);
     if (o->precision < 0 || o->precision > 1) return fail(h, LAIR_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->coarse_max < 1 || o->coarse_max > 4096) return fail(h, LAIR_ERR_INVALID_ARG, "coarse_max in [1, 4096]");

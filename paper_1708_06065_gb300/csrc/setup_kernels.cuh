@@ -56,6 +56,7 @@ struct LocalArgs {
     double *out_val;
     float *out_val32;     // optional
     uint8_t *lsflag;      // optional, per coarse row
+    int neumann_deg = -1; // >= 0: the Neumann series of that degree instead of the solve (nAIR, Sec. 3.2)
 };
 constexpr int LOCAL_CTA_GRID = 152 * 2;
 void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s);

@@ -287,7 +287,34 @@ __device__ void jacobi_ls(const Team &tm, int s, T *B, const T *rhs, T *V, T *z)
     }
 }
 
-// one C point: gather, solve (LU or least squares), write its R row {nb, z} u {(i, 1)}
+// nAIR (Sec. 3.2): the Neumann series of M = D - (D - M) from its diagonal D, truncated at degree k:
+// z = y_0 + ... + y_k, y_0 = D^{-1} rhs, y_{m+1}[r] = -(sum_{c != r} M[r][c] y_m[c]) / M[r][r] (fma from 0 in
+// ascending c). With M = A_NN^T and rhs = -a_{i,N} this is row i of -A_cf sum (D^{-1}E)^m D^{-1} on the set N,
+// which holds every point the series reaches. y and yn are s-entry scratch.
+template <class Team, class T>
+__device__ void neumann_sum(const Team &tm, int s, const T *M, const T *rhs, T *z, T *y, T *yn, int k) {
+    for (int r = tm.rank(); r < s; r += tm.size()) {
+        y[r] = div_rn(rhs[r], M[r * s + r]);
+        z[r] = y[r];
+    }
+    tm.sync();
+    for (int m = 1; m <= k; ++m) {
+        for (int r = tm.rank(); r < s; r += tm.size()) {
+            T acc = T(0);
+            for (int c = 0; c < s; ++c)
+                if (c != r) acc = fma_rn(M[r * s + c], y[c], acc);
+            yn[r] = div_rn(-acc, M[r * s + r]);
+        }
+        tm.sync();
+        for (int r = tm.rank(); r < s; r += tm.size()) {
+            y[r] = yn[r];
+            z[r] = add_rn(z[r], yn[r]);
+        }
+        tm.sync();
+    }
+}
+
+// one C point: gather, solve (LU or least squares) or sum the Neumann series, write its R row {nb, z} u {(i, 1)}
 template <class Team, class T>
 __device__ void solve_row(const Team &tm, const LocalArgs &a, int c, T *M, T *rhs, T *z, T *L, T *V) {
     const int i = a.cpts[c];
@@ -296,7 +323,8 @@ __device__ void solve_row(const Team &tm, const LocalArgs &a, int c, T *M, T *rh
     int singular = 0;
     if (s > 0) {
         gather_system(tm, a.brp, a.bcol, a.bval, i, nb, s, M, rhs);
-        singular = lu_solve(tm, s, M, rhs, z, L);
+        if (a.neumann_deg >= 0) neumann_sum(tm, s, M, rhs, z, L, V, a.neumann_deg);
+        else singular = lu_solve(tm, s, M, rhs, z, L);
         if (singular) {
             gather_system(tm, a.brp, a.bcol, a.bval, i, nb, s, M, rhs);
             jacobi_ls(tm, s, M, rhs, V, z);

@@ -22,6 +22,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "NOT_SQUARE", "UNSORTED_CSR", "DUPLICATE_EN
                 "UNSUPPORTED"]
 CF_RS, CF_PMIS, CF_USER, CF_AUTO = 0, 1, 2, 3
 P_LAIP, P_ONEPOINT = 0, 1
+R_LAIR, R_NEUMANN = 0, 1
 RELAX_FFC, RELAX_FCF, RELAX_FF = 0, 1, 2
 FP64, MIXED = 0, 1
 STATIONARY, FGMRES = 0, 1
@@ -44,7 +45,7 @@ class lair_options(C.Structure):
                 ("lump_tol", C.c_double), ("lump_level0", C.c_int), ("precision", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
                 ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("fgmres_restart", C.c_int),
-                ("stream", C.c_void_p), ("timing", C.c_int)]
+                ("stream", C.c_void_p), ("timing", C.c_int), ("restriction", C.c_int)]
 
 
 class lair_report(C.Structure):
