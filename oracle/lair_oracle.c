@@ -23,6 +23,8 @@
  *   V-cycle with post F-F-C Jacobi . Sec. 4, Eq. (2.4)
  *   GMRES acceleration ............. Sec. 4 (here flexible GMRES, FP64)
  *   Neumann restriction (nAIR) ..... Sec. 3.2, truncated Neumann series of A_ff^{-1}
+ *   nodal (block) hierarchy ........ Sec. 3.1 (k x k blocks), Sec. 4.2.1 approach (iii):
+ *                                    strength, splitting, R and P by block; block Jacobi
  *   refresh for new values ......... backward Euler steps I + dt S (Sec. 4.1.1):
  *                                    structure kept, every value recomputed
  *
@@ -73,6 +75,7 @@ typedef struct {
     const int64_t *seg;    /* batched systems: nseg + 1 offsets of the independent systems on level 0 */
     int nseg;
     int restriction;       /* 0 lAIR (Sec. 3.1), 1 Neumann nAIR of degree distance - 1 (Sec. 3.2) */
+    int nodal;             /* > 1: nodal hierarchy on k x k blocks of that size (Sec. 3.1, Sec. 4.2.1 (iii)) */
 } ora_opts;
 
 /* ------------------------------------------------------------------------- */
@@ -1214,6 +1217,146 @@ static void dense_solve(const odense *d, const double *b, double *x) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Nodal (block) hierarchy: Sec. 3.1 forms the local system with k x k blocks  */
+/* (the block system solved for k right-hand sides), and Sec. 4.2.1 names      */
+/* approach (iii): strength, C/F splitting and transfer operators by block.    */
+/* Node I holds the k consecutive unknowns kI .. kI + k - 1.                   */
+/* Node matrix: b_IJ = ||A_IJ||_F over the stored entries of block (I, J),     */
+/* summed as fma(a, a, .) from 0 in ascending row, then ascending column, then */
+/* one square root. Strength, splitting, neighbourhoods and the one-point      */
+/* choice are those of the scalar method applied to this matrix (abs mode: the */
+/* entries are norms); a node's unknowns all take the node's C/F label; the   */
+/* local-solve set of every unknown of a C node is every unknown of the node's */
+/* F-node neighbourhood, so its k rows of R are the block system of Sec. 3.1;  */
+/* one-point P puts the k x k identity at the strongest C node.                */
+/* ------------------------------------------------------------------------- */
+static int node_matrix(const ocsr *A, int64_t k, ocsr *B) {
+    int64_t N = A->nr / k;
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(A->rp[A->nr] + 1));
+    int64_t cap = A->rp[A->nr] + 1, len = 0;
+    B->nr = B->nc = N;
+    B->rp = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    B->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
+    B->val = (double *)malloc(sizeof(double) * (size_t)cap);
+    for (int64_t I = 0; I < N; ++I) {
+        int64_t m = 0;
+        for (int64_t q = A->rp[k * I]; q < A->rp[k * I + k]; ++q) cols[m++] = (int32_t)(A->col[q] / k);
+        m = sort_unique(cols, m);
+        for (int64_t a = 0; a < m; ++a) {
+            int64_t J = cols[a];
+            double acc = 0.0;
+            for (int64_t t = 0; t < k; ++t)
+                for (int64_t q = A->rp[k * I + t]; q < A->rp[k * I + t + 1]; ++q)
+                    if (A->col[q] / k == J) acc = fma(A->val[q], A->val[q], acc);
+            B->col[len] = (int32_t)J;
+            B->val[len] = sqrt(acc);
+            len++;
+        }
+        B->rp[I + 1] = len;
+    }
+    free(cols);
+    return ORA_OK;
+}
+
+/* sets of nodes -> sets of unknowns: set q of nodes gives k rows (one per unknown of coarse node q) */
+static void expand_sets(int64_t k, int64_t NC, const int64_t *brp, const int32_t *bcol, int64_t **rp, int32_t **col) {
+    int64_t nc = NC * k;
+    *rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(brp[NC] * k * k + 1));
+    int64_t p = 0;
+    for (int64_t q = 0; q < NC; ++q)
+        for (int64_t t = 0; t < k; ++t) {
+            for (int64_t a = brp[q]; a < brp[q + 1]; ++a)
+                for (int64_t u = 0; u < k; ++u) (*col)[p++] = (int32_t)(bcol[a] * k + u);
+            (*rp)[q * k + t + 1] = p;
+        }
+}
+
+/* Lumping by block (Sec. 3.3 with k x k blocks): in node row I, every block  */
+/* K_IJ (J != I) with ||K_IJ||_F < theta_D max_J ||K_IJ||_F (diagonal block    */
+/* included) is removed and added entrywise to the diagonal block:            */
+/* k_{i, kI+u} += k_{i, kJ+u}, in ascending column order starting from         */
+/* k_{i, kI+u}. Every scalar row sum is kept. With keep != NULL the kept       */
+/* blocks are those of the pattern keep (hierarchy refresh) and K's values are */
+/* written into keep; otherwise K is compacted in place.                       */
+static int lump_nodal(ocsr *K, int64_t k, double tol, ocsr *keep) {
+    int64_t n = K->nr, p = 0, start = 0;
+    ocsr BK;
+    node_matrix(K, k, &BK);
+    double *d = (double *)malloc(sizeof(double) * (size_t)k);
+    int8_t *has = (int8_t *)malloc((size_t)k);
+    int st = ORA_OK;
+    for (int64_t i = 0; i < n && st == ORA_OK; ++i) {
+        int64_t I = i / k, end = K->rp[i + 1];
+        double m = 0.0;
+        for (int64_t a = BK.rp[I]; a < BK.rp[I + 1]; ++a) if (BK.val[a] > m) m = BK.val[a];
+        double thr = tol * m;
+        for (int64_t u = 0; u < k; ++u) { d[u] = 0.0; has[u] = 0; }
+        for (int64_t q = start; q < end; ++q)
+            if (K->col[q] / k == I) { d[K->col[q] % k] = K->val[q]; has[K->col[q] % k] = 1; }
+        int64_t t0 = keep ? keep->rp[i] : 0, t1 = keep ? keep->rp[i + 1] : 0, t = t0;
+        for (int64_t q = start; q < end; ++q) {
+            int64_t J = K->col[q] / k;
+            int dropped;
+            if (keep) {
+                while (t < t1 && keep->col[t] < K->col[q]) ++t;
+                dropped = J != I && !(t < t1 && keep->col[t] == K->col[q]);
+            } else {
+                double bn = 0.0;
+                find_entry(&BK, I, J, &bn);
+                dropped = J != I && bn < thr;
+            }
+            if (!dropped) continue;
+            int64_t u = K->col[q] % k;
+            if (!has[u]) { st = ORA_ERR_ARG; break; }   /* no diagonal-block entry to take it */
+            d[u] = d[u] + K->val[q];
+        }
+        if (keep) {
+            t = t0;
+            for (int64_t q = start; q < end && t < t1; ++q) {
+                if (K->col[q] != keep->col[t]) continue;
+                keep->val[t] = (K->col[q] / k == I) ? d[K->col[q] % k] : K->val[q];
+                ++t;
+            }
+            if (t != t1) st = ORA_ERR_ARG;
+        } else {
+            for (int64_t q = start; q < end; ++q) {
+                int64_t J = K->col[q] / k;
+                double bn = 0.0;
+                find_entry(&BK, I, J, &bn);
+                if (J != I && bn < thr) continue;
+                K->col[p] = K->col[q];
+                K->val[p] = (J == I) ? d[K->col[q] % k] : K->val[q];
+                p++;
+            }
+            K->rp[i + 1] = p;
+        }
+        start = end;
+    }
+    csr_free(&BK);
+    free(d); free(has);
+    return st;
+}
+
+/* inverse diagonal blocks (block Jacobi) by the LU of block_inverse; a missing entry counts as 0 */
+static int node_block_inverses(const ocsr *A, int64_t k, double **out) {
+    int64_t N = A->nr / k;
+    double *binv = (double *)malloc(sizeof(double) * (size_t)(N * k * k > 0 ? N * k * k : 1));
+    double *D = (double *)malloc(sizeof(double) * (size_t)(k * k));
+    int st = ORA_OK;
+    for (int64_t I = 0; I < N && st == ORA_OK; ++I) {
+        for (int64_t e = 0; e < k * k; ++e) D[e] = 0.0;
+        for (int64_t t = 0; t < k; ++t)
+            for (int64_t q = A->rp[k * I + t]; q < A->rp[k * I + t + 1]; ++q)
+                if (A->col[q] / k == I) D[t * k + A->col[q] % k] = A->val[q];
+        st = block_inverse(k, D, binv + I * k * k);
+    }
+    free(D);
+    *out = binv;
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Hierarchy                                                                  */
 /* ------------------------------------------------------------------------- */
 #define ORA_MAX_LEVELS 64
@@ -1229,6 +1372,8 @@ typedef struct {
     uint8_t *ls_R, *ls_P;
     double *dinv;
     float *A32, *R32, *P32, *dinv32;
+    double *binv;      /* nodal: inverse diagonal blocks, k*k per node (block Jacobi) */
+    float *binv32;
     int64_t *seg;      /* batched systems: offsets of the systems on this level (nseg + 1) */
 } olevel;
 
@@ -1263,6 +1408,120 @@ void ora_opts_default(ora_opts *o) {
     o->block_size = 0;
     o->rs_block = 4096;
     o->pmis_seed = 0x5eedULL;
+}
+
+static int coarsen_level_nodal(ohier *H, int l, int *is_last) {
+    olevel *L = &H->lev[l];
+    const ora_opts *o = &H->o;
+    ocsr *A = &L->A;
+    const int64_t k = o->nodal;
+    int64_t n = A->nr, nnz = A->rp[n], N = n / k;
+    int st;
+    if (n % k) return ORA_ERR_ARG;
+    ocsr B;
+    node_matrix(A, k, &B);
+    int64_t bnnz = B.rp[N];
+    uint8_t *sB = (uint8_t *)malloc((size_t)(bnnz > 0 ? bnnz : 1));
+    uint8_t *sBcf = (uint8_t *)malloc((size_t)(bnnz > 0 ? bnnz : 1));
+    ora_strength(N, B.rp, B.col, B.val, o->theta, 1, sB);
+    ora_strength(N, B.rp, B.col, B.val, o->theta_cf, 1, sBcf);
+    /* the scalar masks: an entry is strong when its block is */
+    L->strong = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    L->strong_cf = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) {
+            int64_t pos = B.rp[i / k] + find_pos(B.col + B.rp[i / k], B.rp[i / k + 1] - B.rp[i / k], A->col[q] / k);
+            L->strong[q] = sB[pos];
+            L->strong_cf[q] = sBcf[pos];
+        }
+    ograph S, ST, Scf, STcf;
+    graph_from_mask(N, B.rp, B.col, sB, &S);
+    graph_transpose(&S, &ST);
+    graph_from_mask(N, B.rp, B.col, sBcf, &Scf);
+    graph_transpose(&Scf, &STcf);
+    int8_t *cfB = (int8_t *)malloc((size_t)(N > 0 ? N : 1));
+    if (l == 0 && o->cf_mode == 2 && o->cf_user) {
+        for (int64_t I = 0; I < N; ++I) cfB[I] = o->cf_user[I * k] ? CF_C : CF_F;
+    } else {
+        if (o->cf_mode == 0) cf_rs(&Scf, &STcf, cfB);
+        else if (o->cf_mode != 1) cf_rs_blocked(&Scf, &STcf, o->rs_block, cfB);
+        else cf_pmis(&Scf, &STcf, o->pmis_seed + (uint64_t)l, cfB);
+    }
+    L->cf = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) L->cf[i] = cfB[i / k];
+    L->cidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nc = 0;
+    for (int64_t i = 0; i < n; ++i) L->cidx[i] = (L->cf[i] == CF_C) ? nc++ : -1;
+    L->nc = nc;
+    int64_t NC = nc / k;
+    if (nc == 0 || nc == n) {
+        graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
+        csr_free(&B); free(sB); free(sBcf); free(cfB);
+        *is_last = 1;
+        return ORA_OK;
+    }
+    int64_t *cptsB = (int64_t *)malloc(sizeof(int64_t) * (size_t)NC);
+    int64_t *cidxB = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t I = 0, q = 0; I < N; ++I) {
+        cidxB[I] = cfB[I] == CF_C ? q : -1;
+        if (cfB[I] == CF_C) cptsB[q++] = I;
+    }
+    int64_t *cpts = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    for (int64_t i = 0; i < n; ++i) if (L->cf[i] == CF_C) cpts[L->cidx[i]] = i;
+    /* R: block local systems on the expanded node neighbourhoods */
+    int64_t *nbB_rp, *nb_rp;
+    int32_t *nbB_col, *nb_col;
+    build_neighbourhoods(&S, cfB, o->distance, NC, cptsB, &nbB_rp, &nbB_col);
+    expand_sets(k, NC, nbB_rp, nbB_col, &nb_rp, &nb_col);
+    L->ls_R = (uint8_t *)calloc((size_t)nc, 1);
+    st = build_lair_R(A, L->cf, L->cidx, nc, cpts, nb_rp, nb_col, o->prec, &L->R, L->ls_R);
+    free(nbB_rp); free(nbB_col); free(nb_rp); free(nb_col);
+    if (!st) {
+        if (o->interp == 1) {
+            /* block one-point: the node-level choice, as the k x k identity */
+            ocsr PB;
+            st = build_P_onepoint(&B, &S, cfB, cidxB, NC, 1, &PB);
+            if (!st && !(st = csr_alloc(&L->P, n, nc, PB.rp[N] * k))) {
+                int64_t p = 0;
+                for (int64_t i = 0; i < n; ++i) {
+                    for (int64_t a = PB.rp[i / k]; a < PB.rp[i / k + 1]; ++a) {
+                        L->P.col[p] = (int32_t)(PB.col[a] * k + i % k);
+                        L->P.val[p] = 1.0;
+                        p++;
+                    }
+                    L->P.rp[i + 1] = p;
+                }
+            }
+            csr_free(&PB);
+        } else {
+            int64_t *qB_rp, *q_rp;
+            int32_t *qB_col, *q_col;
+            build_neighbourhoods(&ST, cfB, o->distance, NC, cptsB, &qB_rp, &qB_col);
+            expand_sets(k, NC, qB_rp, qB_col, &q_rp, &q_col);
+            L->ls_P = (uint8_t *)calloc((size_t)nc, 1);
+            st = build_P_laip_on(A, nc, cpts, q_rp, q_col, o->prec, &L->P, L->ls_P);
+            free(qB_rp); free(qB_col); free(q_rp); free(q_col);
+        }
+    }
+    free(cpts); free(cptsB); free(cidxB); free(cfB); free(sB); free(sBcf);
+    csr_free(&B);
+    graph_free(&S); graph_free(&ST); graph_free(&Scf); graph_free(&STcf);
+    if (st) return st;
+    for (int64_t c = 0; c < nc; ++c) {
+        H->singular_R += L->ls_R[c];
+        if (L->ls_P) H->singular_P += L->ls_P[c];
+    }
+    ocsr RA, K;
+    spgemm(&L->R, A, &RA);
+    spgemm(&RA, &L->P, &K);
+    csr_free(&RA);
+    if (o->lump_tol > 0.0) {
+        st = lump_nodal(&K, k, o->lump_tol, NULL);
+        if (st) { csr_free(&K); return st; }
+    }
+    H->lev[l + 1].A = K;
+    *is_last = 0;
+    return ORA_OK;
 }
 
 static int coarsen_level(ohier *H, int l, int *is_last) {
@@ -1362,6 +1621,13 @@ static int finish_level(ohier *H, int l) {
         if (!find_entry(&L->A, i, i, &d) || d == 0.0) return ORA_ERR_ZERO_DIAG;
         L->dinv[i] = 1.0 / d;
     }
+    if (H->o.nodal > 1 && L->R.rp) {
+        int64_t k = H->o.nodal, N = n / k;
+        int st = node_block_inverses(&L->A, k, &L->binv);
+        if (st) return st;
+        L->binv32 = (float *)malloc(sizeof(float) * (size_t)(N * k * k > 0 ? N * k * k : 1));
+        for (int64_t e = 0; e < N * k * k; ++e) L->binv32[e] = (float)L->binv[e];
+    }
     for (int k = 0; k < 4; ++k) {
         H->w64[l][k] = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
         H->w32[l][k] = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
@@ -1390,6 +1656,7 @@ void ora_free(ohier *H) {
         csr_free(&L->A); csr_free(&L->R); csr_free(&L->P);
         free(L->cf); free(L->cidx); free(L->strong); free(L->strong_cf); free(L->ls_R); free(L->ls_P);
         free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32); free(L->seg);
+        free(L->binv); free(L->binv32);
         for (int k = 0; k < 4; ++k) { free(H->w64[l][k]); free(H->w32[l][k]); }
     }
     free(H->coarse.LU); free(H->coarse.perm); free(H->blk_inv);
@@ -1403,6 +1670,11 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
     int64_t nnz = rp[n];
     ocsr *A0 = &H->lev[0].A;
     if (opts->block_size > 1 && n % opts->block_size) { *status = ORA_ERR_ARG; return H; }
+    if (opts->nodal > 1 && (opts->nodal > 8 || n % opts->nodal || opts->block_size > 1 || opts->restriction != 0 ||
+                            opts->nseg > 0)) {
+        *status = ORA_ERR_ARG;
+        return H;
+    }
     if (opts->block_size > 1) nnz = ora_block_scale_nnz(n, rp, col, opts->block_size);
     if (csr_alloc(A0, n, n, nnz)) { *status = ORA_ERR_OOM; return H; }
     if (opts->block_size > 1) {
@@ -1421,7 +1693,7 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
     }
     H->o.seg = NULL;   /* not retained */
     if (opts->lump_level0 && opts->lump_tol > 0.0) {
-        int st = lump(A0, opts->lump_tol);
+        int st = opts->nodal > 1 ? lump_nodal(A0, opts->nodal, opts->lump_tol, NULL) : lump(A0, opts->lump_tol);
         if (st) { *status = st; H->nlev = 1; return H; }
     }
     int l = 0;
@@ -1430,7 +1702,7 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
         int64_t nl = H->lev[l].A.nr;
         int last = (nl <= opts->coarse_max) || (l + 1 >= opts->max_levels) || (l + 1 >= ORA_MAX_LEVELS);
         if (!last) {
-            int st = coarsen_level(H, l, &last);
+            int st = opts->nodal > 1 ? coarsen_level_nodal(H, l, &last) : coarsen_level(H, l, &last);
             if (st) { *status = st; return H; }
         }
         int st = finish_level(H, l);
@@ -1461,8 +1733,9 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
 /* ------------------------------------------------------------------------- */
 static void unfinish_level(ohier *H, int l) {
     olevel *L = &H->lev[l];
-    free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32);
+    free(L->dinv); free(L->A32); free(L->R32); free(L->P32); free(L->dinv32); free(L->binv); free(L->binv32);
     L->dinv = NULL; L->A32 = L->R32 = L->P32 = L->dinv32 = NULL;
+    L->binv = NULL; L->binv32 = NULL;
     for (int k = 0; k < 4; ++k) {
         free(H->w64[l][k]); free(H->w32[l][k]);
         H->w64[l][k] = NULL; H->w32[l][k] = NULL;
@@ -1534,7 +1807,7 @@ static int refresh_level(ohier *H, int l) {
     csr_free(&RA);
     ocsr *An = &H->lev[l + 1].A;
     if (o->lump_tol > 0.0) {
-        st = lump_on_pattern(&K, An);
+        st = o->nodal > 1 ? lump_nodal(&K, o->nodal, o->lump_tol, An) : lump_on_pattern(&K, An);
     } else if (same_pattern(&K, An)) {
         memcpy(An->val, K.val, sizeof(double) * (size_t)K.rp[K.nr]);
         st = ORA_OK;
@@ -1561,7 +1834,8 @@ int ora_refresh(ohier *H, int64_t n, const int64_t *rp, const int32_t *col, cons
         memcpy(T.val, val, sizeof(double) * (size_t)nnz);
     }
     if (!st) {
-        if (o->lump_level0 && o->lump_tol > 0.0) st = lump_on_pattern(&T, A0);
+        if (o->lump_level0 && o->lump_tol > 0.0)
+            st = o->nodal > 1 ? lump_nodal(&T, o->nodal, o->lump_tol, A0) : lump_on_pattern(&T, A0);
         else if (same_pattern(&T, A0)) memcpy(A0->val, T.val, sizeof(double) * (size_t)nnz);
         else st = ORA_ERR_ARG;
     }
@@ -1597,6 +1871,52 @@ static void spmv64(const ocsr *A, const double *x, double *y) {
     }
 }
 
+/* block Jacobi on a nodal level: x_I <- x_I + D_I^{-1} (b - A x)_I for the nodes of the target set; the
+   residual rows by fma from 0 in ascending column, the block product by fma from 0 in ascending u */
+static void sweep64_nodal(const olevel *L, int64_t k, int target, const double *b, const double *x, double *xo) {
+    const ocsr *A = &L->A;
+    double r[64];
+    for (int64_t I = 0; I < A->nr / k; ++I) {
+        if (L->cf[I * k] != target) {
+            for (int64_t t = 0; t < k; ++t) xo[I * k + t] = x[I * k + t];
+            continue;
+        }
+        for (int64_t t = 0; t < k; ++t) {
+            int64_t i = I * k + t;
+            double acc = 0.0;
+            for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) acc = fma(A->val[q], x[A->col[q]], acc);
+            r[t] = b[i] - acc;
+        }
+        for (int64_t t = 0; t < k; ++t) {
+            double acc = 0.0;
+            for (int64_t u = 0; u < k; ++u) acc = fma(L->binv[(I * k + t) * k + u], r[u], acc);
+            xo[I * k + t] = x[I * k + t] + acc;
+        }
+    }
+}
+
+static void sweep32_nodal(const olevel *L, int64_t k, int target, const float *b, const float *x, float *xo) {
+    const ocsr *A = &L->A;
+    float r[64];
+    for (int64_t I = 0; I < A->nr / k; ++I) {
+        if (L->cf[I * k] != target) {
+            for (int64_t t = 0; t < k; ++t) xo[I * k + t] = x[I * k + t];
+            continue;
+        }
+        for (int64_t t = 0; t < k; ++t) {
+            int64_t i = I * k + t;
+            float acc = 0.0f;
+            for (int64_t q = A->rp[i]; q < A->rp[i + 1]; ++q) acc = fmaf(L->A32[q], x[A->col[q]], acc);
+            r[t] = b[i] - acc;
+        }
+        for (int64_t t = 0; t < k; ++t) {
+            float acc = 0.0f;
+            for (int64_t u = 0; u < k; ++u) acc = fmaf(L->binv32[(I * k + t) * k + u], r[u], acc);
+            xo[I * k + t] = x[I * k + t] + acc;
+        }
+    }
+}
+
 static void sweep64(const olevel *L, int target, const double *b, const double *x, double *xo) {
     const ocsr *A = &L->A;
     for (int64_t i = 0; i < A->nr; ++i) {
@@ -1621,7 +1941,8 @@ static void cycle64(ohier *H, int l, const double *b, double *x) {
     for (int s = 0; s < 3; ++s) {
         int tgt = relax_seq[H->o.relax][s];
         if (tgt == -9) break;
-        sweep64(L, tgt, b, x, t);
+        if (H->o.nodal > 1) sweep64_nodal(L, H->o.nodal, tgt, b, x, t);
+        else sweep64(L, tgt, b, x, t);
         memcpy(x, t, sizeof(double) * (size_t)n);
     }
 }
@@ -1652,6 +1973,11 @@ static void cycle32(ohier *H, int l, const float *b, float *x) {
     for (int s = 0; s < 3; ++s) {
         int tgt = relax_seq[H->o.relax][s];
         if (tgt == -9) break;
+        if (H->o.nodal > 1) {
+            sweep32_nodal(L, H->o.nodal, tgt, b, x, t);
+            memcpy(x, t, sizeof(float) * (size_t)n);
+            continue;
+        }
         for (int64_t i = 0; i < n; ++i) {
             if (L->cf[i] != tgt) { t[i] = x[i]; continue; }
             float acc = 0.0f;

@@ -42,7 +42,7 @@ class Opts(C.Structure):
         ("interp", C.c_int), ("relax", C.c_int), ("lump_tol", C.c_double), ("lump_level0", C.c_int),
         ("prec", C.c_int), ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
         ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("seg", C.c_void_p), ("nseg", C.c_int),
-        ("restriction", C.c_int),
+        ("restriction", C.c_int), ("nodal", C.c_int),
     ]
 
 
