@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-refresh", action="store_true", help="skip the time-stepping (refresh + solve) measurement")
+    p.add_argument("--nodal", action="store_true",
+                   help="dg_p2_256: the nodal hierarchy on the 6-unknown elements (block strength, splitting, R and "
+                        "P by block, block Jacobi) instead of block-diagonal scaling")
     p.add_argument("--restriction", default="lair", choices=["lair", "neumann"],
                    help="R from the local systems (lAIR, the default) or the Neumann series (nAIR, Sec. 3.2)")
     return p.parse_args()
@@ -295,6 +298,13 @@ def main():
     torch.cuda.synchronize()
 
     cycle = lair.FGMRES if (args.cycle or wl.get("cycle", "fgmres")) == "fgmres" else lair.STATIONARY
+    if args.nodal:
+        if "block_size" not in wl["opts"]:
+            raise SystemExit("--nodal applies to the block-structured workload dg_p2_256")
+        opts = {k: v for k, v in wl["opts"].items() if k not in ("block_size", "strength_abs")}
+        wl = dict(wl, opts=dict(opts, nodal=wl["opts"]["block_size"]),
+                  desc=wl["desc"].replace("block-diagonal scaling", "nodal hierarchy on the 6-unknown elements "
+                                                                    "(block Jacobi)"))
     if args.restriction == "neumann":
         wl = dict(wl, opts=dict(wl["opts"], restriction=lair.R_NEUMANN), desc=wl["desc"] + ", Neumann restriction (nAIR)")
     if args.cycle:

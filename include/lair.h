@@ -114,6 +114,13 @@ typedef struct {
     int timing;               /* 1: record CUDA-event timings of the main kernels and set-up phases
                                  (lair_kernel_timers); 2: also one timer per set-up phase and level */
     int restriction;          /* lair_restriction (default lAIR) */
+    int nodal;                /* 2..8: nodal (block) hierarchy on nodes of that many consecutive unknowns
+                                 (Sec. 3.1 with k x k blocks; Sec. 4.2.1, approach (iii)): strength of
+                                 connection on the block Frobenius norms, C/F splitting by node, R from the
+                                 block local systems of the node neighbourhoods, one-point P as k x k
+                                 identity blocks, lumping by whole blocks, block Jacobi relaxation.
+                                 n must be a multiple of it; not with block_size, the Neumann restriction or
+                                 batched systems. 0 or 1: off (default). */
 } lair_options;
 
 typedef struct {

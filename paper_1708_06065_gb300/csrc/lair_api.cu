@@ -54,6 +54,11 @@ struct Level {
     int *frows = nullptr, *crows = nullptr;
     SellView AF, AC, Rv, Pv;
     SellView A64;             // level 0: all rows of A in FP64 for the outer iteration
+    // nodal hierarchy (k x k blocks): block Jacobi as point Jacobi on Ahat = D^{-1} A (diagonal blocks
+    // inverted, diagonal exactly 1) with right-hand side D^{-1} b; binv holds the k x k inverses
+    DCsr Ahat;
+    double *binv = nullptr, *dinv_hat = nullptr, *bh64 = nullptr;
+    float *binv32 = nullptr, *dinv_hat32 = nullptr, *bh32 = nullptr;
 };
 
 struct Hier {
@@ -676,6 +681,52 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     return LAIR_OK;
 }
 
+// C/F splitting of the n points of the graphs (Scf, STcf) into cf (level l): RS, the exact first pass (one
+// block per system); AUTO, the first pass in blocks of rs_block points, never spanning two batched systems;
+// or PMIS
+static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Graph &Scf, const Graph &STcf,
+                                const std::vector<int> &seg_h, int8_t *cf) {
+    const lair_options &o = h->o;
+    if (o.cf_mode != LAIR_CF_PMIS) {
+        // RS: the exact first pass (one block per system); AUTO: the first pass in blocks of rs_block points.
+        // Blocks never span two batched systems.
+        std::vector<int> cuts = seg_h;
+        if (cuts.empty()) cuts = {0, n};
+        std::vector<int2> blocks;
+        int Bmax = 1;
+        for (size_t q = 0; q + 1 < cuts.size(); ++q) {
+            const int s0 = cuts[q], s1 = cuts[q + 1];
+            const int B = o.cf_mode == LAIR_CF_RS ? (s1 - s0) : o.rs_block;
+            if (B > RS_MAX_N)
+                return fail(h, LAIR_ERR_UNSUPPORTED,
+                            "the first pass runs on at most %d points at once (level %d has %d)", RS_MAX_N, l, B);
+            for (int b0 = s0; b0 < s1; b0 += B) {
+                int b1 = b0 + B < s1 ? b0 + B : s1;
+                blocks.push_back(make_int2(b0, b1));
+                if (b1 - b0 > Bmax) Bmax = b1 - b0;
+            }
+        }
+        int2 *bd;
+        TRY(t.get(&bd, blocks.size()));
+        CU(cudaMemcpyAsync(bd, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, h->s));
+        int *mx, maxin = 0;
+        TRY(new_counts(h, t, &mx, 1));
+        launch_rs_count(bd, (int)blocks.size(), Scf, mx, h->s);
+        TRY(read_ints(h, mx, 1, &maxin));   // also keeps the host block list alive until its copy is done
+        CU(launch_rs(n, bd, (int)blocks.size(), Bmax, maxin, Scf, STcf, cf, h->status, h->s));
+    } else {
+        double *w;
+        int8_t *newc;
+        int *und;
+        TRY(t.get(&w, (size_t)n));
+        TRY(t.get(&newc, (size_t)n));
+        TRY(new_counts(h, t, &und, 4));
+        launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, cf, h->s);
+        CU(launch_pmis_all(n, Scf, STcf, w, cf, newc, und, h->status, h->s));
+    }
+    return LAIR_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // one coarsening step: level l -> level l+1
 // ---------------------------------------------------------------------------------------
@@ -714,43 +765,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         CU(cudaMemcpyAsync(L.cf, cf_user, (size_t)n, cudaMemcpyHostToDevice, h->s));
         normalize_cf(n, L.cf, h->s);
     } else {
-        if (o.cf_mode != LAIR_CF_PMIS) {
-            // RS: the exact first pass (one block per system); AUTO: the first pass in blocks of rs_block points.
-            // Blocks never span two batched systems.
-            std::vector<int> cuts = L.seg_h;
-            if (cuts.empty()) cuts = {0, n};
-            std::vector<int2> blocks;
-            int Bmax = 1;
-            for (size_t q = 0; q + 1 < cuts.size(); ++q) {
-                const int s0 = cuts[q], s1 = cuts[q + 1];
-                const int B = o.cf_mode == LAIR_CF_RS ? (s1 - s0) : o.rs_block;
-                if (B > RS_MAX_N)
-                    return fail(h, LAIR_ERR_UNSUPPORTED,
-                                "the first pass runs on at most %d points at once (level %d has %d)", RS_MAX_N, l, B);
-                for (int b0 = s0; b0 < s1; b0 += B) {
-                    int b1 = b0 + B < s1 ? b0 + B : s1;
-                    blocks.push_back(make_int2(b0, b1));
-                    if (b1 - b0 > Bmax) Bmax = b1 - b0;
-                }
-            }
-            int2 *bd;
-            TRY(t.get(&bd, blocks.size()));
-            CU(cudaMemcpyAsync(bd, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, h->s));
-            int *mx, maxin = 0;
-            TRY(new_counts(h, t, &mx, 1));
-            launch_rs_count(bd, (int)blocks.size(), Scf, mx, h->s);
-            TRY(read_ints(h, mx, 1, &maxin));   // also keeps the host block list alive until its copy is done
-            CU(launch_rs(n, bd, (int)blocks.size(), Bmax, maxin, Scf, STcf, L.cf, h->status, h->s));
-        } else {
-            double *w;
-            int8_t *newc;
-            int *und;
-            TRY(t.get(&w, (size_t)n));
-            TRY(t.get(&newc, (size_t)n));
-            TRY(new_counts(h, t, &und, 4));
-            launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, L.cf, h->s);
-            CU(launch_pmis_all(n, Scf, STcf, w, L.cf, newc, und, h->status, h->s));
-        }
+        TRY(split_points(h, t, l, n, Scf, STcf, L.seg_h, L.cf));
     }
     // the status word (first-pass errors) is checked with the next read-back
 
@@ -879,6 +894,242 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         TRY(dalloc(h, &next.seg_d, next_seg.size()));
         CU(cudaMemcpyAsync(next.seg_d, next.seg_h.data(), sizeof(int) * next_seg.size(), cudaMemcpyHostToDevice, h->s));
         CU(cudaStreamSynchronize(h->s));   // the host vector is copied from pageable memory
+    }
+    H.lev.push_back(next);
+    tend(h, tp);
+    *last = false;
+    return LAIR_OK;
+}
+
+// local solves on kept sets (defined with the hierarchy refresh below)
+static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
+                                 int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
+                                 float *oval32, uint8_t *lsflag, int neumann_deg = -1);
+
+// the neighbourhoods (distance o.distance) of the nc points cpts in graph G with labels cf, compacted:
+// set c is (*out_col)[(*out_rp)[c] .. (*out_rp)[c + 1]); *out_total entries in all
+static lair_status build_sets(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
+                              int **out_rp, int **out_col, int *out_total) {
+    const int distance = h->o.distance, d0 = distance < 2 ? distance : 2;
+    int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
+    TRY(new_counts(h, t, &ub, nc));
+    launch_nb_bound(nc, cpts, G, cf, d0, ub, h->s);
+    TRY(t.get(&off, (size_t)nc + 1));
+    int total = 0;
+    TRY(scan(h, ub, off, nc, &total));
+    TRY(t.get(&tmp, (size_t)total + 1));
+    TRY(new_counts(h, t, &cnt, nc));
+    launch_nb_fill(nc, cpts, G, cf, d0, off, tmp, cnt, h->s);
+    TRY(t.get(&nb_rp, (size_t)nc + 1));
+    TRY(scan(h, cnt, nb_rp, nc, nullptr));
+    for (int d = 3; d <= distance; ++d) {
+        int nn = 0, tot = 0;
+        TRY(read_ints(h, nb_rp + nc, 1, &nn));
+        int *cur, *ub2, *off2, *tmp2, *cnt2, *rp2;
+        TRY(t.get(&cur, (size_t)nn + 1));
+        launch_nb_compact(nc, off, tmp, nb_rp, cur, h->s);
+        TRY(new_counts(h, t, &ub2, nc));
+        launch_nb_expand(0, nc, cpts, G, cf, nb_rp, cur, nullptr, nullptr, ub2, h->s);
+        TRY(t.get(&off2, (size_t)nc + 1));
+        TRY(scan(h, ub2, off2, nc, &tot));
+        TRY(t.get(&tmp2, (size_t)tot + 1));
+        TRY(new_counts(h, t, &cnt2, nc));
+        launch_nb_expand(1, nc, cpts, G, cf, nb_rp, cur, off2, tmp2, cnt2, h->s);
+        TRY(t.get(&rp2, (size_t)nc + 1));
+        TRY(scan(h, cnt2, rp2, nc, nullptr));
+        off = off2;
+        tmp = tmp2;
+        nb_rp = rp2;
+    }
+    int nnb = 0;
+    TRY(read_ints(h, nb_rp + nc, 1, &nnb));
+    TRY(t.get(&nb_col, (size_t)nnb + 1));
+    launch_nb_compact(nc, off, tmp, nb_rp, nb_col, h->s);
+    *out_rp = nb_rp;
+    *out_col = nb_col;
+    *out_total = nnb;
+    return LAIR_OK;
+}
+
+// one coarsening step of the nodal hierarchy (nodes of k = o.nodal consecutive unknowns): strength,
+// splitting, neighbourhoods and the one-point choice on the matrix of block norms, then R, P and R A P on
+// the unknowns, lumping by block
+static lair_status coarsen_nodal(lair_handle *h, Hier &H, int l, const int8_t *cf_user, bool *last) {
+    Temps t(h);
+    Level &L = H.lev[l];
+    const DCsr &A = L.A;
+    const lair_options &o = h->o;
+    const int n = A.nr, k = o.nodal, N = n / k;
+    const bool fp32 = o.precision == LAIR_MIXED;
+
+    int tp = tbegin(h, phase_name(h, "strength", l), 0.0);
+    DCsr B;
+    B.nr = B.nc = N;
+    int *bcnt;
+    TRY(new_counts(h, t, &bcnt, N));
+    launch_node_matrix(0, N, k, A, bcnt, nullptr, h->s);
+    TRY(t.get(&B.rp, (size_t)N + 1));
+    TRY(scan(h, bcnt, B.rp, N, &B.nnz));
+    TRY(t.get(&B.col, (size_t)B.nnz + 1));
+    TRY(t.get(&B.val, (size_t)B.nnz + 1));
+    launch_node_matrix(1, N, k, A, nullptr, &B, h->s);
+    uint8_t *smask;
+    TRY(t.get(&smask, (size_t)B.nnz + 1));
+    Graph S, ST, Scf, STcf;
+    TRY(build_strength_graph(h, t, B, o.theta, smask, S, 1));   // abs mode: the entries are norms
+    TRY(transpose(h, t, N, N, S.nnz, S.rp, S.col, nullptr, &ST.rp, &ST.col, nullptr, false));
+    ST.n = N;
+    ST.nnz = S.nnz;
+    if (o.theta_cf != o.theta) {
+        uint8_t *m2;
+        TRY(t.get(&m2, (size_t)B.nnz + 1));
+        TRY(build_strength_graph(h, t, B, o.theta_cf, m2, Scf, 1));
+        TRY(transpose(h, t, N, N, Scf.nnz, Scf.rp, Scf.col, nullptr, &STcf.rp, &STcf.col, nullptr, false));
+        STcf.n = N;
+        STcf.nnz = Scf.nnz;
+    } else {
+        Scf = S;
+        STcf = ST;
+    }
+
+    tend(h, tp);
+    tp = tbegin(h, phase_name(h, "split", l), 0.0);
+    int8_t *cfB;
+    TRY(t.get(&cfB, (size_t)N));
+    if (cf_user) {
+        std::vector<int8_t> hb((size_t)N);
+        for (int I = 0; I < N; ++I) hb[I] = cf_user[(size_t)I * k];
+        CU(cudaMemcpyAsync(cfB, hb.data(), (size_t)N, cudaMemcpyHostToDevice, h->s));
+        CU(cudaStreamSynchronize(h->s));
+        normalize_cf(N, cfB, h->s);
+    } else {
+        TRY(split_points(h, t, l, N, Scf, STcf, std::vector<int>(), cfB));
+    }
+    TRY(dalloc(h, &L.strong, (size_t)A.nnz));
+    TRY(dalloc(h, &L.cf, (size_t)n));
+    launch_node_expand(n, k, A, B, smask, L.strong, cfB, L.cf, h->s);
+
+    // coarse numbering of the unknowns and of the nodes
+    int *flag, *scanv, *cpts;
+    TRY(new_counts(h, t, &flag, n));
+    launch_cidx(n, L.cf, flag, nullptr, nullptr, 0, h->s);
+    TRY(t.get(&scanv, (size_t)n + 1));
+    int nc = 0;
+    TRY(scan(h, flag, scanv, n, &nc));
+    L.nc = nc;
+    if (nc == 0 || nc == n) {
+        tend(h, tp);
+        *last = true;
+        return LAIR_OK;
+    }
+    TRY(dalloc(h, &L.cidx, (size_t)n));
+    TRY(dalloc(h, &cpts, (size_t)nc));
+    launch_cidx(n, L.cf, scanv, L.cidx, cpts, 1, h->s);
+    L.crows = cpts;
+    if (n - nc > 0) {
+        TRY(dalloc(h, &L.frows, (size_t)(n - nc)));
+        launch_frows(n, L.cf, scanv, L.frows, h->s);
+    }
+    const int NC = nc / k;
+    int *flagB, *scanB, *cidxB, *cptsB;
+    TRY(new_counts(h, t, &flagB, N));
+    launch_cidx(N, cfB, flagB, nullptr, nullptr, 0, h->s);
+    TRY(t.get(&scanB, (size_t)N + 1));
+    TRY(scan(h, flagB, scanB, N, nullptr));
+    TRY(t.get(&cidxB, (size_t)N));
+    TRY(t.get(&cptsB, (size_t)NC));
+    launch_cidx(N, cfB, scanB, cidxB, cptsB, 1, h->s);
+
+    // restriction: for each unknown of a C node, the local system on every unknown of the node's
+    // F-node neighbourhood (together, the block system of Sec. 3.1 for k right-hand sides)
+    tend(h, tp);
+    tp = tbegin(h, phase_name(h, "R", l), 0.0);
+    int *nrp, *ncol, nn = 0, *len;
+    TRY(build_sets(h, t, NC, cptsB, S, cfB, &nrp, &ncol, &nn));
+    TRY(new_counts(h, t, &len, nc));
+    launch_node_rows(0, NC, k, nrp, ncol, cptsB, len, nullptr, nullptr, h->s);
+    L.R.nr = nc;
+    L.R.nc = n;
+    TRY(dalloc(h, &L.R.rp, (size_t)nc + 1));
+    TRY(scan(h, len, L.R.rp, nc, &L.R.nnz));
+    TRY(dalloc(h, &L.R.col, (size_t)L.R.nnz));
+    TRY(dalloc(h, &L.R.val, (size_t)L.R.nnz));
+    if (fp32) TRY(dalloc(h, &L.R.val32, (size_t)L.R.nnz));
+    launch_node_rows(1, NC, k, nrp, ncol, cptsB, nullptr, L.R.rp, L.R.col, h->s);
+    TRY(dalloc(h, &L.lsR, (size_t)nc));
+    TRY(local_rows_on(h, t, nc, cpts, L.R.rp, L.R.col, L.R.nnz, A.rp, A.col, A.val, L.R.col, L.R.val,
+                      fp32 ? L.R.val32 : nullptr, L.lsR));
+
+    // interpolation
+    tend(h, tp);
+    tp = tbegin(h, phase_name(h, "P", l), 0.0);
+    L.P.nr = n;
+    L.P.nc = nc;
+    if (o.interp == LAIR_P_ONEPOINT) {
+        int *choiceB, *cntB, *cnt;
+        TRY(t.get(&choiceB, (size_t)N));
+        TRY(new_counts(h, t, &cntB, N));
+        launch_onepoint(0, B, smask, cfB, cidxB, 1, choiceB, cntB, nullptr, h->s);
+        TRY(new_counts(h, t, &cnt, n));
+        launch_onepoint_nodal(0, n, k, choiceB, cnt, nullptr, h->s);
+        TRY(dalloc(h, &L.P.rp, (size_t)n + 1));
+        TRY(scan(h, cnt, L.P.rp, n, nullptr));
+        L.P.nnz = n;   // at most one entry per row; the exact count is read with the hierarchy totals
+        TRY(dalloc(h, &L.P.col, (size_t)n));
+        TRY(dalloc(h, &L.P.val, (size_t)n));
+        if (fp32) TRY(dalloc(h, &L.P.val32, (size_t)n));
+        launch_onepoint_nodal(1, n, k, choiceB, nullptr, &L.P, h->s);
+    } else {
+        // approximate ideal interpolation by block: the sets of the transposed node graph, the local
+        // systems of A^T, transposed back
+        int *qrp, *qcol, qn = 0, *wlen, *wrp, *wcol, wnnz = 0, *atrp, *atcol;
+        double *wval, *atval;
+        TRY(build_sets(h, t, NC, cptsB, ST, cfB, &qrp, &qcol, &qn));
+        TRY(new_counts(h, t, &wlen, nc));
+        launch_node_rows(0, NC, k, qrp, qcol, cptsB, wlen, nullptr, nullptr, h->s);
+        TRY(t.get(&wrp, (size_t)nc + 1));
+        TRY(scan(h, wlen, wrp, nc, &wnnz));
+        TRY(t.get(&wcol, (size_t)wnnz));
+        TRY(t.get(&wval, (size_t)wnnz));
+        launch_node_rows(1, NC, k, qrp, qcol, cptsB, nullptr, wrp, wcol, h->s);
+        TRY(transpose(h, t, n, n, A.nnz, A.rp, A.col, A.val, &atrp, &atcol, &atval, false));
+        TRY(dalloc(h, &L.lsP, (size_t)nc));
+        TRY(local_rows_on(h, t, nc, cpts, wrp, wcol, wnnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP));
+        TRY(transpose(h, t, nc, n, wnnz, wrp, wcol, wval, &L.P.rp, &L.P.col, &L.P.val, true));
+        L.P.nnz = wnnz;
+        if (fp32) {
+            TRY(dalloc(h, &L.P.val32, (size_t)wnnz));
+            launch_to_f32(wnnz, L.P.val, L.P.val32, h->s);
+        }
+    }
+
+    // Galerkin product and lumping by block
+    tend(h, tp);
+    tp = tbegin(h, phase_name(h, "RAP", l), 0.0);
+    DCsr RA, K;
+    const bool lump = o.lump_tol > 0.0;
+    int *klen = nullptr;
+    if (o.interp == LAIR_P_ONEPOINT) {
+        TRY(spgemm(h, t, L.R, A, K, !lump, l == 0 ? 1 : -1, &L.P, lump ? &klen : nullptr));
+    } else {
+        TRY(spgemm(h, t, L.R, A, RA, false, l == 0 ? 0 : -1));
+        TRY(spgemm(h, t, RA, L.P, K, !lump, l == 0 ? 1 : -1, nullptr, lump ? &klen : nullptr));
+    }
+    Level next;
+    if (lump) {
+        int *cnt;
+        TRY(new_counts(h, t, &cnt, K.nr));
+        launch_lump_nodal(0, k, K, klen, o.lump_tol, cnt, nullptr, h->status, h->s);
+        DCsr Kl;
+        Kl.nr = Kl.nc = K.nr;
+        TRY(dalloc(h, &Kl.rp, (size_t)K.nr + 1));
+        TRY(scan(h, cnt, Kl.rp, K.nr, &Kl.nnz));
+        TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
+        TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
+        launch_lump_nodal(1, k, K, klen, o.lump_tol, nullptr, &Kl, h->status, h->s);
+        next.A = Kl;
+    } else {
+        next.A = K;
     }
     H.lev.push_back(next);
     tend(h, tp);
@@ -1015,8 +1266,12 @@ static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan>
     const bool fp32 = h->o.precision == LAIR_MIXED;
     if (!L.coarsest) {
         const int n = L.A.nr, nc = L.nc;
-        plans.push_back(SellPlan{&L.AF, &L.A, L.frows, n - nc, L.dinv, fp32});
-        plans.push_back(SellPlan{&L.AC, &L.A, L.crows, nc, L.dinv, fp32});
+        // the relaxation's matrix: A (point Jacobi) or D^{-1} A (block Jacobi, nodal hierarchy)
+        const bool nodal = h->o.nodal > 1;
+        const DCsr *Ar = nodal ? &L.Ahat : &L.A;
+        const double *dv = nodal ? L.dinv_hat : L.dinv;
+        plans.push_back(SellPlan{&L.AF, Ar, L.frows, n - nc, dv, fp32});
+        plans.push_back(SellPlan{&L.AC, Ar, L.crows, nc, dv, fp32});
         plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
         plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
     }
@@ -1031,12 +1286,38 @@ static lair_status finish_level(lair_handle *h, Hier &H, int l) {
     TRY(dalloc(h, &L.dinv, (size_t)n));
     if (fp32) TRY(dalloc(h, &L.dinv32, (size_t)n));
     launch_dinv(L.A, L.dinv, L.dinv32, h->status, h->s);
+    const bool nodal = h->o.nodal > 1 && !L.coarsest;
+    if (nodal) {
+        // block Jacobi: Ahat = D^{-1} A (the scaling kernels of the DG option) and its unit diagonal
+        const int k = h->o.nodal, N = n / k;
+        Temps t(h);
+        int *rowcnt;
+        TRY(new_counts(h, t, &rowcnt, n));
+        launch_block_count(N, k, L.A, rowcnt, h->s);
+        L.Ahat.nr = L.Ahat.nc = n;
+        TRY(dalloc(h, &L.Ahat.rp, (size_t)n + 1));
+        TRY(scan(h, rowcnt, L.Ahat.rp, n, &L.Ahat.nnz));
+        TRY(dalloc(h, &L.Ahat.col, (size_t)L.Ahat.nnz));
+        TRY(dalloc(h, &L.Ahat.val, (size_t)L.Ahat.nnz));
+        TRY(dalloc(h, &L.binv, (size_t)n * k));
+        launch_block_fill(N, k, L.A, L.Ahat, L.binv, h->status, h->s);
+        TRY(dalloc(h, &L.dinv_hat, (size_t)n));
+        if (fp32) {
+            TRY(dalloc(h, &L.dinv_hat32, (size_t)n));
+            TRY(dalloc(h, &L.binv32, (size_t)n * k));
+            launch_to_f32((long long)n * k, L.binv, L.binv32, h->s);
+            TRY(dalloc(h, &L.bh32, (size_t)n));
+        } else {
+            TRY(dalloc(h, &L.bh64, (size_t)n));
+        }
+        launch_dinv(L.Ahat, L.dinv_hat, L.dinv_hat32, h->status, h->s);
+    }
     if (h->o.timing && L.cf && l == 0) {
         Temps t(h);
         unsigned long long *st;
         TRY(t.get(&st, 4));
         CU(cudaMemsetAsync(st, 0, 4 * sizeof(unsigned long long), h->s));
-        cf_stats(L.A, L.cf, st, h->s);
+        cf_stats(nodal ? L.Ahat : L.A, L.cf, st, h->s);
         unsigned long long hs[4];
         CU(cudaMemcpyAsync(hs, st, sizeof hs, cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
@@ -1061,11 +1342,15 @@ static const int relax_seq[3][3] = {{CF_F, CF_F, CF_C}, {CF_F, CF_C, CF_F}, {CF_
 
 template <class T> struct CycleBufs;
 template <> struct CycleBufs<double> {
+    static double *bh(Level &L) { return L.bh64; }
+    static const double *binv(Level &L) { return L.binv; }
     static double *b(Level &L) { return L.b64; }
     static double *x(Level &L, int k) { return L.x64[k]; }
     static const double *dinv(Level &L) { return L.dinv; }
 };
 template <> struct CycleBufs<float> {
+    static float *bh(Level &L) { return L.bh32; }
+    static const float *binv(Level &L) { return L.binv32; }
     static float *b(Level &L) { return L.b32; }
     static float *x(Level &L, int k) { return L.x32[k]; }
     static const float *dinv(Level &L) { return L.dinv32; }
@@ -1101,12 +1386,18 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     if (tm) tend(h, t, true);
     int cur = 0;
     const int n = L.A.nr, nc = L.nc;
+    T *rb = B::b(L);
+    if (h->o.nodal > 1) {
+        // block Jacobi: x += D^{-1} b - (D^{-1} A) x
+        block_apply_t<T>(n, h->o.nodal, B::binv(L), B::b(L), B::bh(L), h->s);
+        rb = B::bh(L);
+    }
     for (int k = 0; k < 3; ++k) {
         int tg = relax_seq[h->o.relax][k];
         if (tg < 0) break;
         t = tm ? tbegin(h, tg == CF_F ? "L0_sweep_F" : "L0_sweep_C", bytes_sweep(L, tg, sv), true) : -1;
-        if (tg == CF_F) sell_sweep<T>(L.AF, L.crows, nc, B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
-        else sell_sweep<T>(L.AC, L.frows, n - nc, B::b(L), B::x(L, cur), B::x(L, 1 - cur), h->s);
+        if (tg == CF_F) sell_sweep<T>(L.AF, L.crows, nc, rb, B::x(L, cur), B::x(L, 1 - cur), h->s);
+        else sell_sweep<T>(L.AC, L.frows, n - nc, rb, B::x(L, cur), B::x(L, 1 - cur), h->s);
         if (tm) tend(h, t, true);
         cur ^= 1;
     }
@@ -1167,14 +1458,16 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             double *nd;
             TRY(new_counts(h, t, &cnt, A.nr));
             TRY(t.get(&nd, (size_t)A.nr));
-            launch_lump(0, A, nullptr, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
+            if (o.nodal > 1) launch_lump_nodal(0, o.nodal, A, nullptr, o.lump_tol, cnt, nullptr, h->status, h->s);
+            else launch_lump(0, A, nullptr, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
             DCsr Kl;
             Kl.nr = Kl.nc = A.nr;
             TRY(dalloc(h, &Kl.rp, (size_t)A.nr + 1));
             TRY(scan(h, cnt, Kl.rp, A.nr, &Kl.nnz));
             TRY(dalloc(h, &Kl.col, (size_t)Kl.nnz));
             TRY(dalloc(h, &Kl.val, (size_t)Kl.nnz));
-            launch_lump(1, A, nullptr, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
+            if (o.nodal > 1) launch_lump_nodal(1, o.nodal, A, nullptr, o.lump_tol, nullptr, &Kl, h->status, h->s);
+            else launch_lump(1, A, nullptr, o.lump_tol, cnt, nd, &Kl, h->status, h->s);
             TRY(sync_status(h));
             A = Kl;
         }
@@ -1191,7 +1484,10 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
     for (int l = 0;; ++l) {
         const int n = H.lev[l].A.nr;
         bool last = n <= o.coarse_max || l + 1 >= o.max_levels;
-        if (!last) TRY(coarsen(h, H, l, l == 0 ? cf_user : nullptr, &last));
+        if (!last) {
+            if (o.nodal > 1) TRY(coarsen_nodal(h, H, l, l == 0 ? cf_user : nullptr, &last));
+            else TRY(coarsen(h, H, l, l == 0 ? cf_user : nullptr, &last));
+        }
         if (last) H.lev[l].coarsest = true;
         TRY(finish_level(h, H, l));
         if (last) {
@@ -1276,7 +1572,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
 // solution row is written at rp[c] in the layout local_rows writes it
 static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
                                  int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
-                                 float *oval32, uint8_t *lsflag, int neumann_deg = -1) {
+                                 float *oval32, uint8_t *lsflag, int neumann_deg) {
     if (nc <= 0) return LAIR_OK;
     const bool fp32 = h->o.precision == LAIR_MIXED;
     int *nb_rp, *nb_col, *lists, *bcounts;
@@ -1332,7 +1628,8 @@ static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
         TRY(spgemm(h, t, RA, L.P, K, false, -1, nullptr, &klen));
     }
     // without lumping the kept pattern is the whole product and nothing is added to the diagonal
-    launch_lump_kept(K, klen, H.lev[l + 1].A, h->status, h->s);
+    if (h->o.nodal > 1 && h->o.lump_tol > 0.0) launch_lump_nodal_kept(h->o.nodal, K, klen, H.lev[l + 1].A, h->status, h->s);
+    else launch_lump_kept(K, klen, H.lev[l + 1].A, h->status, h->s);
     return LAIR_OK;
 }
 
@@ -1361,7 +1658,8 @@ static lair_status refresh_hierarchy(lair_handle *h, Hier &H, const DCsr &Ain) {
             launch_block_fill(nblk, bs, A, B, H.blk_inv, h->status, h->s);
             A = B;
         }
-        if (lump0) launch_lump_kept(A, nullptr, L0.A, h->status, h->s);
+        if (lump0 && o.nodal > 1) launch_lump_nodal_kept(o.nodal, A, nullptr, L0.A, h->status, h->s);
+        else if (lump0) launch_lump_kept(A, nullptr, L0.A, h->status, h->s);
         else if (A.val != L0.A.val)
             CU(cudaMemcpyAsync(L0.A.val, A.val, sizeof(double) * (size_t)A.nnz, cudaMemcpyDeviceToDevice, h->s));
     }
@@ -1375,6 +1673,12 @@ static lair_status refresh_hierarchy(lair_handle *h, Hier &H, const DCsr &Ain) {
             Level &L = H.lev[l];
             launch_dinv(L.A, L.dinv, L.dinv32, h->status, h->s);
             if (fp32) launch_to_f32(L.A.nnz, L.A.val, L.A.val32, h->s);
+            if (o.nodal > 1 && !L.coarsest) {
+                const int k = o.nodal;
+                launch_block_fill(L.A.nr / k, k, L.A, L.Ahat, L.binv, h->status, h->s);
+                launch_dinv(L.Ahat, L.dinv_hat, L.dinv_hat32, h->status, h->s);
+                if (fp32) launch_to_f32((long long)L.A.nr * k, L.binv, L.binv32, h->s);
+            }
             if (L.coarsest) {
                 const int n = L.A.nr;
                 double *D;
@@ -2038,6 +2342,12 @@ static lair_status check_options(lair_handle *h, const lair_options *o) {
     if (o->interp < 0 || o->interp > 1) return fail(h, LAIR_ERR_INVALID_ARG, "interp %d", o->interp);
     if (o->restriction < 0 || o->restriction > 1)
         return fail(h, LAIR_ERR_INVALID_ARG, "restriction %d", o->restriction);
+    if (o->nodal < 0) return fail(h, LAIR_ERR_INVALID_ARG, "nodal %d", o->nodal);
+    if (o->nodal > NODAL_MAX) return fail(h, LAIR_ERR_UNSUPPORTED, "nodal <= %d", NODAL_MAX);
+    if (o->nodal > 1 && o->block_size > 1)
+        return fail(h, LAIR_ERR_INVALID_ARG, "nodal and block_size exclude each other");
+    if (o->nodal > 1 && o->restriction != LAIR_R_LAIR)
+        return fail(h, LAIR_ERR_UNSUPPORTED, "the nodal hierarchy builds R by lAIR only");
     if (o->relax < 0 || o->relax > 2) return fail(h, LAIR_ERR_INVALID_ARG, "relax %d", o->relax);
     if (o->precision < 0 || o->precision > 1) return fail(h, LAIR_ERR_INVALID_ARG, "precision %d", o->precision);
     if (o->coarse_max < 1 || o->coarse_max > 4096) return fail(h, LAIR_ERR_INVALID_ARG, "coarse_max in [1, 4096]");
@@ -2061,6 +2371,7 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **o
     TRY(check_options(h, &h->o));
     if (h->o.block_size > 1 && A->n % h->o.block_size)
         return fail(h, LAIR_ERR_INVALID_ARG, "n is not a multiple of block_size");
+    if (h->o.nodal > 1 && A->n % h->o.nodal) return fail(h, LAIR_ERR_INVALID_ARG, "n is not a multiple of nodal");
     h->s = (cudaStream_t)h->o.stream;
     if (!h->s) {
         // a blocking stream: ordered with the legacy default stream, and capturable into graphs
@@ -2108,6 +2419,7 @@ lair_status lair_setup_batched(const lair_csr *A, int nsys, const int64_t *sys_o
     TRY(check_options(h, &h->o));
     if (h->o.cf_mode == LAIR_CF_USER) return fail(h, LAIR_ERR_INVALID_ARG, "user splitting is not available for batches");
     if (h->o.block_size > 1) return fail(h, LAIR_ERR_UNSUPPORTED, "block scaling is not available for batches");
+    if (h->o.nodal > 1) return fail(h, LAIR_ERR_UNSUPPORTED, "the nodal hierarchy is not available for batches");
     if (sys_offsets[0] != 0 || sys_offsets[nsys] != A->n)
         return fail(h, LAIR_ERR_INVALID_ARG, "system offsets must run from 0 to n");
     h->seg0.resize(nsys + 1);

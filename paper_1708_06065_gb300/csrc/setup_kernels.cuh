@@ -104,6 +104,26 @@ void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tva
 // K's rows: rp[i] .. rp[i + 1], or rp[i] .. rp[i] + len[i] when len is given
 void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
                  int *status, cudaStream_t s);
+// ---- setup_nodal.cu: the nodal (block) hierarchy, nodes of k <= NODAL_MAX consecutive unknowns -------------
+constexpr int NODAL_MAX = 8;
+// phase 0: block columns per node into cnt; phase 1: B = the block Frobenius norms at B->rp
+void launch_node_matrix(int phase, int N, int k, const DCsr &A, int *cnt, const DCsr *B, cudaStream_t s);
+// per unknown: cf[i] = cfB[i / k] (cf may be NULL); per entry of A: mask = bmask of its block (mask may be NULL)
+void launch_node_expand(int n, int k, const DCsr &A, const DCsr &B, const uint8_t *bmask, uint8_t *mask,
+                        const int8_t *cfB, int8_t *cf, cudaStream_t s);
+// node sets (NC coarse nodes) to rows of unknowns with the C unknown itself: phase 0 lengths, phase 1 rows
+void launch_node_rows(int phase, int NC, int k, const int *nrp, const int *ncol, const int *cptsB, int *len,
+                      const int *orp, int *ocol, cudaStream_t s);
+// block one-point P from the node choice (coarse node or -1): phase 0 counts, phase 1 entries
+void launch_onepoint_nodal(int phase, int n, int k, const int *choiceB, int *cnt, const DCsr *P, cudaStream_t s);
+// lumping by block: phase 0 kept counts per row, phase 1 the rows of out
+void launch_lump_nodal(int phase, int k, const DCsr &K, const int *len, double tol, int *cnt, const DCsr *out,
+                       int *status, cudaStream_t s);
+// lumping onto a kept block pattern (refresh)
+void launch_lump_nodal_kept(int k, const DCsr &K, const int *len, const DCsr &out, int *status, cudaStream_t s);
+// out = D^{-1} b with the k x k inverse diagonal blocks inv (row-major per node)
+template <class T> void block_apply_t(int n, int k, const T *inv, const T *b, T *out, cudaStream_t s);
+
 // the values of out (a kept pattern inside K's) from K: entries of K outside it are lumped to the diagonal
 void launch_lump_kept(const DCsr &K, const int *len, const DCsr &out, int *status, cudaStream_t s);
 void launch_dinv(const DCsr &A, double *dinv, float *dinv32, int *status, cudaStream_t s);
