@@ -3,7 +3,7 @@
 nAIR of distance d (degree k = d - 1): Z = -A_cf sum_{m=0}^{k} (D_ff^{-1} E_ff)^m D_ff^{-1}, E_ff = D_ff - A_ff,
 the paper's -A_cf sum L_ff^m for a unit-diagonal matrix. Expected values come from dense numpy products of
 that formula, from the exact inverse where the series is finite (triangular A_ff), from exact power-of-two row
-scaling, from ℓAIR on a chain (where the paper states the two coincide), and from the paper's Table 2 finding
+scaling, from ℓAIR on a chain (where the paper states the two coincide), and from the paper's Table 1 finding
 that Neumann barely improves on Z = 0 for a recirculating flow while ℓAIR does.
 """
 import numpy as np
@@ -143,7 +143,7 @@ def _ideal_error(s, d, restriction, **kw):
 
 
 def test_recirculating_flow_neumann_is_no_better_than_zero():
-    """Table 2 (Sec. 3.2): on a recirculating flow the Neumann approximation is hardly closer to ideal
+    """Table 1 (Sec. 3.2): on a recirculating flow the Neumann approximation is hardly closer to ideal
     restriction than Z = 0 (relative error about 1), while ℓAIR is, and improves with distance."""
     s = W.dg_p2_advection(10)
     kw = dict(strength_abs=1)
