@@ -53,3 +53,43 @@ def test_setup_rejects_bad_arguments_without_a_gpu():
     assert st == 1
     assert b"distance" in lair.lib.lair_last_error(h)
     lair.lib.lair_free(h)
+
+
+@pytest.mark.parametrize("kw,code,word", [
+    (dict(restriction=2), 1, b"restriction"),
+    (dict(nodal=-1), 1, b"nodal"),
+    (dict(nodal=9), 13, b"nodal"),
+    (dict(nodal=6, block_size=6), 1, b"block_size"),
+    (dict(nodal=2, restriction=1), 13, b"lAIR"),
+    (dict(nodal=3), 1, b"multiple of nodal"),      # n = 4 is not a multiple of 3
+])
+def test_setup_rejects_option_combinations_without_a_gpu(kw, code, word):
+    """Option checks run before any device call: unknown values, nodal with block scaling or the Neumann
+    restriction, and a size that is not a multiple of the node size."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    h = ctypes.c_void_p()
+    o = lair.options(**kw)
+    A = lair.lair_csr(4, 4, None, None, None, 0)
+    st = lair.lib.lair_setup(ctypes.byref(A), ctypes.byref(o), ctypes.byref(h))
+    assert st == code
+    assert word in lair.lib.lair_last_error(h)
+    lair.lib.lair_free(h)
+
+
+def test_refresh_rejects_a_handle_without_a_hierarchy():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    lair.lib.lair_refresh.restype = ctypes.c_int
+    lair.lib.lair_refresh.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lair.lib.lair_refresh(None, None) == 1
+    h = ctypes.c_void_p()
+    o = lair.options(distance=5)
+    A = lair.lair_csr(4, 4, None, None, None, 0)
+    assert lair.lib.lair_setup(ctypes.byref(A), ctypes.byref(o), ctypes.byref(h)) == 1
+    val = (ctypes.c_double * 4)()
+    assert lair.lib.lair_refresh(h, val) == 1
+    assert b"no hierarchy" in lair.lib.lair_last_error(h)
+    lair.lib.lair_free(h)
