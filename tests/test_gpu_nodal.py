@@ -116,3 +116,30 @@ def test_nodal_rejected_combinations(lair, kw, code):
     with pytest.raises(lair.LairError) as e:
         lair.Hierarchy.from_system(s, **kw)
     assert e.value.status == code
+
+
+def test_nodal_adjoint_matches_oracle_on_the_transpose(lair):
+    s = W.dg_p2_advection(10)
+    kw = dict(nodal=6, distance=2, interp=1)
+    G = lair.Hierarchy.from_system(s, **kw)
+    g = np.random.default_rng(3).uniform(-1, 1, s.n)
+    lam, rep = G.adjoint(g, tol=1e-10)
+    assert rep.status == 0
+    AT = s.to_scipy().T.tocsr()
+    assert np.linalg.norm(g - AT @ lam) <= 2e-10 * np.linalg.norm(g)
+    H = O.Hierarchy(W.CsrSystem(s.n, *O.transpose(s), g), **okw(kw))
+    lo, ro = H.solve(g, tol=1e-10)
+    assert abs(rep.iters - ro["iters"]) <= 1
+    assert np.linalg.norm(lam - lo) <= 1e-8 * np.linalg.norm(lo)
+
+
+def test_nodal_user_splitting_matches_oracle(lair):
+    s = W.dg_p2_advection(10)
+    N = s.n // 6
+    cfB = (np.random.default_rng(8).uniform(size=N) < 0.4).astype(np.int8)
+    cf = np.repeat(cfB, 6)
+    kw = dict(nodal=6, distance=2, interp=1)
+    G = lair.Hierarchy.from_system(s, device=True, cf_user=cf, **kw)
+    H = O.Hierarchy(s, cf_user=cf, **okw(kw))
+    assert H.status == 0
+    compare_hierarchies(G, H, TOL64)
