@@ -904,7 +904,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
 // local solves on kept sets (defined with the hierarchy refresh below)
 static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
                                  int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
-                                 float *oval32, uint8_t *lsflag, int neumann_deg = -1);
+                                 float *oval32, uint8_t *lsflag, int neumann_deg = -1, int rows_per = 1);
 
 // the neighbourhoods (distance o.distance) of the nc points cpts in graph G with labels cf, compacted:
 // set c is (*out_col)[(*out_rp)[c] .. (*out_rp)[c + 1]); *out_total entries in all
@@ -1058,7 +1058,7 @@ static lair_status coarsen_nodal(lair_handle *h, Hier &H, int l, const int8_t *c
     launch_node_rows(1, NC, k, nrp, ncol, cptsB, nullptr, L.R.rp, L.R.col, h->s);
     TRY(dalloc(h, &L.lsR, (size_t)nc));
     TRY(local_rows_on(h, t, nc, cpts, L.R.rp, L.R.col, L.R.nnz, A.rp, A.col, A.val, L.R.col, L.R.val,
-                      fp32 ? L.R.val32 : nullptr, L.lsR));
+                      fp32 ? L.R.val32 : nullptr, L.lsR, -1, k));
 
     // interpolation
     tend(h, tp);
@@ -1094,7 +1094,7 @@ static lair_status coarsen_nodal(lair_handle *h, Hier &H, int l, const int8_t *c
         launch_node_rows(1, NC, k, qrp, qcol, cptsB, nullptr, wrp, wcol, h->s);
         TRY(transpose(h, t, n, n, A.nnz, A.rp, A.col, A.val, &atrp, &atcol, &atval, false));
         TRY(dalloc(h, &L.lsP, (size_t)nc));
-        TRY(local_rows_on(h, t, nc, cpts, wrp, wcol, wnnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP));
+        TRY(local_rows_on(h, t, nc, cpts, wrp, wcol, wnnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP, -1, k));
         TRY(transpose(h, t, nc, n, wnnz, wrp, wcol, wval, &L.P.rp, &L.P.col, &L.P.val, true));
         L.P.nnz = wnnz;
         if (fp32) {
@@ -1572,16 +1572,18 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
 // solution row is written at rp[c] in the layout local_rows writes it
 static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cpts, const int *rp, const int *col,
                                  int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
-                                 float *oval32, uint8_t *lsflag, int neumann_deg) {
+                                 float *oval32, uint8_t *lsflag, int neumann_deg, int rows_per) {
     if (nc <= 0) return LAIR_OK;
     const bool fp32 = h->o.precision == LAIR_MIXED;
     int *nb_rp, *nb_col, *lists, *bcounts;
     TRY(t.get(&nb_rp, (size_t)nc + 1));
     TRY(t.get(&nb_col, (size_t)(nnz - nc) + 1));
     launch_nb_from_rows(nc, rp, col, cpts, nb_rp, nb_col, h->s);
-    TRY(t.get(&lists, (size_t)3 * nc + 1));
+    // with rows_per > 1 (nodal hierarchy) consecutive groups of rows share one set and one factorisation
+    const int ng = nc / rows_per;
+    TRY(t.get(&lists, (size_t)3 * ng + 1));
     TRY(new_counts(h, t, &bcounts, 5));
-    launch_local_bin(nc, nb_rp, lists, bcounts, bcounts + 3, h->s);
+    launch_local_bin(ng, nb_rp, lists, bcounts, bcounts + 3, h->s, rows_per);
     int hc[4];
     TRY(read_ints(h, bcounts, 4, hc));
     void *scratch = nullptr;
@@ -1590,8 +1592,8 @@ static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cp
         TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
         scratch = sp;
     }
-    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg};
-    CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
+    LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg, rows_per};
+    CU(launch_local_solves(a, ng, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
     return LAIR_OK;
 }
 
@@ -1601,9 +1603,10 @@ static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
     const DCsr &A = L.A;
     const int n = A.nr, nc = L.nc;
     const bool fp32 = h->o.precision == LAIR_MIXED;
+    const int rows_per = h->o.nodal > 1 ? h->o.nodal : 1;
     TRY(local_rows_on(h, t, nc, L.crows, L.R.rp, L.R.col, L.R.nnz, A.rp, A.col, A.val, L.R.col, L.R.val,
                       fp32 ? L.R.val32 : nullptr, L.lsR,
-                      h->o.restriction == LAIR_R_NEUMANN ? h->o.distance - 1 : -1));
+                      h->o.restriction == LAIR_R_NEUMANN ? h->o.distance - 1 : -1, rows_per));
     if (h->o.interp != LAIR_P_ONEPOINT) {
         // lAIP: the sets are the columns of P without their C point; the local systems are those of A^T,
         // solved into W = P^T by rows and transposed back onto P's pattern
@@ -1613,7 +1616,8 @@ static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
         TRY(transpose(h, t, n, n, A.nnz, A.rp, A.col, A.val, &atrp, &atcol, &atval, false));
         TRY(t.get(&wcol, (size_t)L.P.nnz));
         TRY(t.get(&wval, (size_t)L.P.nnz));
-        TRY(local_rows_on(h, t, nc, L.crows, ptrp, ptcol, L.P.nnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP));
+        TRY(local_rows_on(h, t, nc, L.crows, ptrp, ptcol, L.P.nnz, atrp, atcol, atval, wcol, wval, nullptr, L.lsP, -1,
+                          rows_per));
         TRY(transpose(h, t, nc, n, L.P.nnz, ptrp, wcol, wval, &prp, &pcol, &pval, false));
         CU(cudaMemcpyAsync(L.P.val, pval, sizeof(double) * (size_t)L.P.nnz, cudaMemcpyDeviceToDevice, h->s));
         if (fp32) launch_to_f32(L.P.nnz, L.P.val, L.P.val32, h->s);

@@ -57,9 +57,12 @@ struct LocalArgs {
     float *out_val32;     // optional
     uint8_t *lsflag;      // optional, per coarse row
     int neumann_deg = -1; // >= 0: the Neumann series of that degree instead of the solve (nAIR, Sec. 3.2)
+    int rows_per = 1;     // > 1: rows c = q * rows_per + t (t < rows_per) share one set; the lists hold q
 };
 constexpr int LOCAL_CTA_GRID = 152 * 2;
-void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s);
+// bins of the local systems by size (s <= 6, <= 32, larger); with stride > 1 entry c of the lists is the group
+// of rows c * stride .. c * stride + stride - 1 (one set), sized by its first row
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride = 1);
 cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
                                 const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s);
 size_t local_cta_scratch_bytes(int smax, bool fp32);

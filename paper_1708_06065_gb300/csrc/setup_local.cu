@@ -235,6 +235,70 @@ __device__ int lu_solve(const Team &tm, int s, T *M, T *rhs, T *z, T *L) {
     return 0;
 }
 
+// The same elimination as lu_solve without a right-hand side, for systems solved for several right-hand
+// sides: the multiplier of row r at step k is kept in M[r][k] and the pivot row in piv[k]; only columns
+// >= k take part in a row swap, so the kept multipliers stay where step k left them. lu_apply then runs
+// lu_solve's right-hand-side operations in lu_solve's order: the same results, bit for bit.
+template <class Team, class T>
+__device__ int lu_factor(const Team &tm, int s, T *M, T *L, int *piv) {
+    T mx = T(0);
+    for (int e = tm.rank(); e < s * s; e += tm.size()) mx = fmax(mx, fabs(M[e]));
+    mx = tm.max(mx);
+    if (mx == T(0)) return 1;
+    const T thr = mul_rn(mul_rn((T)s, Eps<T>::v), mx);
+    for (int k = 0; k < s; ++k) {
+        T best = T(-1);
+        int p = -1;
+        for (int r = k + tm.rank(); r < s; r += tm.size()) {
+            T v = fabs(M[r * s + k]);
+            if (p < 0 || v > best) { best = v; p = r; }
+        }
+        tm.argmax(best, p);
+        if (best <= thr) return 1;
+        if (p != k)
+            for (int c = k + tm.rank(); c < s; c += tm.size()) {
+                T t = M[k * s + c];
+                M[k * s + c] = M[p * s + c];
+                M[p * s + c] = t;
+            }
+        if (tm.rank() == 0) piv[k] = p;
+        tm.sync();
+        for (int r = k + 1 + tm.rank(); r < s; r += tm.size()) L[r] = div_rn(M[r * s + k], M[k * s + k]);
+        tm.sync();
+        const int w = s - k - 1;
+        for (int e = tm.rank(); e < w * w; e += tm.size()) {
+            int r = k + 1 + e / w;
+            int c = k + 1 + e % w;
+            M[r * s + c] = fma_rn(-L[r], M[k * s + c], M[r * s + c]);
+        }
+        for (int r = k + 1 + tm.rank(); r < s; r += tm.size()) M[r * s + k] = L[r];
+        tm.sync();
+    }
+    return 0;
+}
+
+template <class Team, class T>
+__device__ void lu_apply(const Team &tm, int s, const T *M, const int *piv, T *rhs, T *z) {
+    for (int k = 0; k < s; ++k) {
+        if (tm.rank() == 0 && piv[k] != k) {
+            T t = rhs[k];
+            rhs[k] = rhs[piv[k]];
+            rhs[piv[k]] = t;
+        }
+        tm.sync();
+        const T rk = rhs[k];
+        for (int r = k + 1 + tm.rank(); r < s; r += tm.size()) rhs[r] = fma_rn(-M[r * s + k], rk, rhs[r]);
+        tm.sync();
+    }
+    for (int c = s - 1; c >= 0; --c) {
+        if (tm.rank() == 0) z[c] = div_rn(rhs[c], M[c * s + c]);
+        tm.sync();
+        const T zc = z[c];
+        for (int r = tm.rank(); r < c; r += tm.size()) rhs[r] = fma_rn(-M[r * s + c], zc, rhs[r]);
+        tm.sync();
+    }
+}
+
 constexpr int LS_MAX_SWEEPS = 60;
 
 // minimum-norm least squares by one-sided Jacobi; B holds the original matrix (destroyed),
@@ -287,6 +351,42 @@ __device__ void jacobi_ls(const Team &tm, int s, T *B, const T *rhs, T *V, T *z)
     }
 }
 
+// row c of the output: {nb, z} u {(i, 1)} at nb_rp[c] + c, ascending; the least-squares flag
+template <class Team, class T>
+__device__ void write_row(const Team &tm, const LocalArgs &a, int c, int i, const int *nb, int s, const T *z,
+                          int singular) {
+    const int base = a.nb_rp[c] + c;
+    for (int r = tm.rank(); r < s; r += tm.size()) {
+        int pos = r + (nb[r] > i ? 1 : 0);
+        a.out_col[base + pos] = nb[r];
+        double v = (double)z[r];
+        a.out_val[base + pos] = v;
+        if (a.out_val32) a.out_val32[base + pos] = (float)z[r];
+    }
+    if (tm.rank() == 0) {
+        int lo = 0, hi = s;
+        while (lo < hi) { int m = (lo + hi) >> 1; if (nb[m] < i) lo = m + 1; else hi = m; }
+        a.out_col[base + lo] = i;
+        a.out_val[base + lo] = 1.0;
+        if (a.out_val32) a.out_val32[base + lo] = 1.0f;
+        if (a.lsflag) a.lsflag[c] = (uint8_t)singular;
+    }
+    tm.sync();
+}
+
+// the right-hand side alone: rhs[r] = -B[i][l_r]
+template <class Team, class T>
+__device__ void gather_rhs(const Team &tm, const int *__restrict__ brp, const int *__restrict__ bcol,
+                           const double *__restrict__ bval, int i, const int *nb, int s, T *rhs) {
+    for (int e = tm.rank(); e < s; e += tm.size()) rhs[e] = T(0);
+    tm.sync();
+    for (int k = brp[i] + tm.rank(); k < brp[i + 1]; k += tm.size()) {
+        int r = find_pos(nb, s, bcol[k]);
+        if (r >= 0) rhs[r] = (T)(-bval[k]);
+    }
+    tm.sync();
+}
+
 // nAIR (Sec. 3.2): the Neumann series of M = D - (D - M) from its diagonal D, truncated at degree k:
 // z = y_0 + ... + y_k, y_0 = D^{-1} rhs, y_{m+1}[r] = -(sum_{c != r} M[r][c] y_m[c]) / M[r][r] (fma from 0 in
 // ascending c). With M = A_NN^T and rhs = -a_{i,N} this is row i of -A_cf sum (D^{-1}E)^m D^{-1} on the set N,
@@ -331,25 +431,36 @@ __device__ void solve_row(const Team &tm, const LocalArgs &a, int c, T *M, T *rh
         }
     }
     tm.sync();
-    const int base = a.nb_rp[c] + c;
-    int before = 0;   // entries of nb left of i
-    for (int r = tm.rank(); r < s; r += tm.size()) {
-        int pos = r + (nb[r] > i ? 1 : 0);
-        a.out_col[base + pos] = nb[r];
-        double v = (double)z[r];
-        a.out_val[base + pos] = v;
-        if (a.out_val32) a.out_val32[base + pos] = (float)z[r];
+    write_row(tm, a, c, i, nb, s, z, singular);
+}
+
+// the C points c0 .. c0 + rows_per - 1 share one set (the unknowns of a C node, nodal hierarchy): the
+// system matrix is gathered and factored once and applied to each row's right-hand side
+template <class Team, class T>
+__device__ void solve_rows_shared(const Team &tm, const LocalArgs &a, int q, T *M, T *rhs, T *z, T *L, T *V) {
+    const int c0 = q * a.rows_per;
+    const int *nb = a.nb_col + a.nb_rp[c0];
+    const int s = a.nb_rp[c0 + 1] - a.nb_rp[c0];
+    int *piv = reinterpret_cast<int *>(V);   // V is only needed by the least-squares branch
+    int singular = 0;
+    if (s > 0) {
+        gather_system(tm, a.brp, a.bcol, a.bval, a.cpts[c0], nb, s, M, rhs);
+        singular = lu_factor(tm, s, M, L, piv);
     }
-    if (tm.rank() == 0) {
-        int lo = 0, hi = s;
-        while (lo < hi) { int m = (lo + hi) >> 1; if (nb[m] < i) lo = m + 1; else hi = m; }
-        before = lo;
-        a.out_col[base + before] = i;
-        a.out_val[base + before] = 1.0;
-        if (a.out_val32) a.out_val32[base + before] = 1.0f;
-        if (a.lsflag) a.lsflag[c] = (uint8_t)singular;
+    for (int t = 0; t < a.rows_per; ++t) {
+        const int c = c0 + t, i = a.cpts[c];
+        if (s > 0) {
+            if (!singular) {
+                gather_rhs(tm, a.brp, a.bcol, a.bval, i, nb, s, rhs);
+                lu_apply(tm, s, M, piv, rhs, z);
+            } else {
+                gather_system(tm, a.brp, a.bcol, a.bval, i, nb, s, M, rhs);
+                jacobi_ls(tm, s, M, rhs, V, z);
+            }
+        }
+        tm.sync();
+        write_row(tm, a, c, i, nb, s, z, singular);
     }
-    tm.sync();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -357,16 +468,19 @@ __device__ void solve_row(const Team &tm, const LocalArgs &a, int c, T *M, T *rh
 // ---------------------------------------------------------------------------------------
 constexpr int THREAD_SMAX = 6;
 
-template <class T>
+// SHARED: the lists hold groups of rows that share one set (solve_rows_shared); a separate instantiation,
+// so that the one-row kernels keep their register budget
+template <class T, bool SHARED>
 __global__ void __launch_bounds__(128) k_local_thread(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count) {
     const int n = *count;
     T M[THREAD_SMAX * THREAD_SMAX], V[THREAD_SMAX * THREAD_SMAX], rhs[THREAD_SMAX], z[THREAD_SMAX], L[THREAD_SMAX];
     ThreadTeam tm;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        solve_row(tm, a, list[t], M, rhs, z, L, V);
+        if (SHARED) solve_rows_shared(tm, a, list[t], M, rhs, z, L, V);
+        else solve_row(tm, a, list[t], M, rhs, z, L, V);
 }
 
-template <class T>
+template <class T, bool SHARED>
 __global__ void __launch_bounds__(128) k_local_warp(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = *count;
@@ -375,10 +489,13 @@ __global__ void __launch_bounds__(128) k_local_warp(LocalArgs a, const int *__re
     T *M = base, *V = base + 32 * 32, *rhs = V + 32 * 32, *z = rhs + 32, *L = z + 32;
     WarpTeam tm;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int t = blockIdx.x * (blockDim.x >> 5) + w; t < n; t += nwarps) solve_row(tm, a, list[t], M, rhs, z, L, V);
+    for (int t = blockIdx.x * (blockDim.x >> 5) + w; t < n; t += nwarps) {
+        if (SHARED) solve_rows_shared(tm, a, list[t], M, rhs, z, L, V);
+        else solve_row(tm, a, list[t], M, rhs, z, L, V);
+    }
 }
 
-template <class T>
+template <class T, bool SHARED>
 __global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__restrict__ list, const int *__restrict__ count,
                                                    T *__restrict__ scratch, int smax) {
     __shared__ double red[64];
@@ -387,18 +504,21 @@ __global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__res
     T *M = scratch + per * blockIdx.x;
     T *V = M + (size_t)smax * smax, *rhs = V + (size_t)smax * smax, *z = rhs + smax, *L = z + smax;
     CtaTeam tm{red};
-    for (int t = blockIdx.x; t < n; t += gridDim.x) solve_row(tm, a, list[t], M, rhs, z, L, V);
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        if (SHARED) solve_rows_shared(tm, a, list[t], M, rhs, z, L, V);
+        else solve_row(tm, a, list[t], M, rhs, z, L, V);
+    }
 }
 
-__global__ void k_local_bin(int nc, const int *__restrict__ nb_rp, int *__restrict__ lists, int *__restrict__ counts,
-                            int *__restrict__ smax) {
+__global__ void k_local_bin(int nc, int group, const int *__restrict__ nb_rp, int *__restrict__ lists,
+                            int *__restrict__ counts, int *__restrict__ smax) {
     const unsigned lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     int local_max = 0;
     for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; base < nc; base += stride) {
         const int c = (int)(base + lane);
         const bool act = c < nc;
-        const int s = act ? nb_rp[c + 1] - nb_rp[c] : 0;
+        const int s = act ? nb_rp[(long long)c * group + 1] - nb_rp[(long long)c * group] : 0;
         const int b = s <= THREAD_SMAX ? 0 : (s <= 32 ? 1 : 2);
         local_max = max(local_max, s);
         for (int bb = 0; bb < 3; ++bb) {       // one atomic per warp and bin
@@ -414,41 +534,42 @@ __global__ void k_local_bin(int nc, const int *__restrict__ nb_rp, int *__restri
     if (lane == 0 && local_max > 0) atomicMax(smax, local_max);
 }
 
-void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s) {
-    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, nb_rp, lists, counts, smax);
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride) {
+    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, stride, nb_rp, lists, counts, smax);
     count_launch();
+}
+
+template <class T, bool SHARED>
+static void local_solves_t(const LocalArgs &a, int nc, const int *lists, const int *counts_dev, const int counts_host[3],
+                           int smax, void *scratch, cudaStream_t s) {
+    if (counts_host[0] > 0) {
+        k_local_thread<T, SHARED><<<grid_for(counts_host[0], 128), 128, 0, s>>>(a, lists, counts_dev);
+        count_launch();
+    }
+    if (counts_host[1] > 0) {
+        const size_t bytes = 4 * sizeof(T) * (2 * 32 * 32 + 3 * 32);
+        cudaFuncSetAttribute(k_local_warp<T, SHARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        k_local_warp<T, SHARED><<<grid_for(counts_host[1], 4, 152 * 8), 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
+        count_launch();
+    }
+    if (counts_host[2] > 0) {
+        const int g = counts_host[2] < LOCAL_CTA_GRID ? counts_host[2] : LOCAL_CTA_GRID;
+        k_local_cta<T, SHARED><<<g, 256, 0, s>>>(a, lists + 2 * (size_t)nc, counts_dev + 2, (T *)scratch, smax);
+        count_launch();
+    }
 }
 
 cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
                                 const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s) {
-    cudaError_t e = cudaSuccess;
-    if (counts_host[0] > 0) {
-        int g = grid_for(counts_host[0], 128);
-        if (fp32) k_local_thread<float><<<g, 128, 0, s>>>(a, lists, counts_dev);
-        else k_local_thread<double><<<g, 128, 0, s>>>(a, lists, counts_dev);
-        count_launch();
+    const bool shared = a.rows_per > 1;
+    if (fp32) {
+        if (shared) local_solves_t<float, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
+        else local_solves_t<float, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
+    } else {
+        if (shared) local_solves_t<double, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
+        else local_solves_t<double, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
     }
-    if (counts_host[1] > 0) {
-        size_t el = fp32 ? sizeof(float) : sizeof(double);
-        size_t bytes = 4 * el * (2 * 32 * 32 + 3 * 32);
-        int g = grid_for(counts_host[1], 4, 152 * 8);
-        if (fp32) {
-            cudaFuncSetAttribute(k_local_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-            k_local_warp<float><<<g, 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
-        } else {
-            cudaFuncSetAttribute(k_local_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-            k_local_warp<double><<<g, 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
-        }
-        count_launch();
-    }
-    if (counts_host[2] > 0) {
-        int g = counts_host[2] < LOCAL_CTA_GRID ? counts_host[2] : LOCAL_CTA_GRID;
-        if (fp32) k_local_cta<float><<<g, 256, 0, s>>>(a, lists + 2 * (size_t)nc, counts_dev + 2, (float *)scratch, smax);
-        else k_local_cta<double><<<g, 256, 0, s>>>(a, lists + 2 * (size_t)nc, counts_dev + 2, (double *)scratch, smax);
-        count_launch();
-    }
-    e = cudaGetLastError();
-    return e;
+    return cudaGetLastError();
 }
 
 size_t local_cta_scratch_bytes(int smax, bool fp32) {
