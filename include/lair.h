@@ -121,6 +121,12 @@ typedef struct {
                                  identity blocks, lumping by whole blocks, block Jacobi relaxation.
                                  n must be a multiple of it; not with block_size, the Neumann restriction or
                                  batched systems. 0 or 1: off (default). */
+    int autotune;             /* 1 (default): before the cycle is captured, time the launch schedules (threads
+                                 per block, grid cap) of the restriction, interpolation and sweep views of at
+                                 least 65,536 rows and keep the fastest when it beats the default by 5 %;
+                                 choices are cached for the process by view shape, so later hierarchies of
+                                 similar levels reuse them. Results do not depend on it. 0: the fixed default
+                                 schedule everywhere. */
 } lair_options;
 
 typedef struct {

@@ -12,7 +12,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -1404,6 +1407,118 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     L.xfinal = cur;
 }
 
+// ---------------------------------------------------------------------------------------
+// launch-schedule autotuner for the cycle's sliced-ELL kernels (restriction, interpolation, F and C
+// sweeps): every candidate (threads per block, grid cap) is timed with CUDA events on the level's own
+// buffers (best of five), a candidate replaces the default schedule only when it is more than 5 % faster,
+// views of fewer than TUNE_MIN_ROWS rows keep the default (their few-microsecond timings alone did not carry
+// over into the captured cycle),
+// and the choice is cached for the process by view shape (kind, precision, rows in quarter octaves, mean
+// row length), so later hierarchies with similar levels take it without timing. One thread owns each row
+// in these kernels, so the schedule never changes a result.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int TUNE_MIN_ROWS = 65536;
+struct TuneKey {
+    int dev, kind, fp32, rows, len;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, kind, fp32, rows, len) < std::tie(o.dev, o.kind, o.fp32, o.rows, o.len);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int2> g_tune;
+const int2 kTuneCandidates[] = {{256, 152 * 16}, {256, 152 * 4}, {256, 152 * 8},  {256, 152 * 32},
+                                {128, 152 * 8},  {128, 152 * 16}, {128, 152 * 32}, {128, 152 * 64}};
+}  // namespace
+
+template <class T>
+static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0, cudaEvent_t e1) {
+    using B = CycleBufs<T>;
+    Level &L = H.lev[l];
+    if (L.coarsest) return LAIR_OK;
+    Level &C = H.lev[l + 1];
+    const int n = L.A.nr, nc = L.nc;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    bool cleared = false;
+    const double lenA = n ? (double)L.A.nnz / n : 0.0;
+    struct Job { SellView *v; double len; };
+    const Job jobs[4] = {{&L.Rv, L.R.nr ? (double)L.R.nnz / L.R.nr : 0.0},
+                         {&L.Pv, L.P.nr ? (double)L.P.nnz / L.P.nr : 0.0}, {&L.AF, lenA}, {&L.AC, lenA}};
+    auto run = [&](int kind) {
+        switch (kind) {
+            case 0: sell_spmv<T>(L.Rv, B::b(L), B::b(C), h->s); break;
+            case 1: sell_spmv<T>(L.Pv, B::x(C, 0), B::x(L, 0), h->s); break;
+            case 2: sell_sweep<T>(L.AF, L.crows, nc, B::b(L), B::x(L, 0), B::x(L, 1), h->s); break;
+            default: sell_sweep<T>(L.AC, L.frows, n - nc, B::b(L), B::x(L, 0), B::x(L, 1), h->s); break;
+        }
+    };
+    for (int kind = 0; kind < 4; ++kind) {
+        SellView &v = *jobs[kind].v;
+        if (v.nrows < TUNE_MIN_ROWS) continue;
+        const TuneKey key{dev, kind, (int)sizeof(T), (int)std::floor(4.0 * std::log2((double)v.nrows)),
+                          (int)std::lround(jobs[kind].len)};
+        {
+            std::lock_guard<std::mutex> g(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                v.tb = it->second.x;
+                v.grid = it->second.y;
+                continue;
+            }
+        }
+        if (!cleared) {
+            // the buffers the timing runs read: zeros, so no candidate meets stray values
+            CU(cudaMemsetAsync(B::b(L), 0, sizeof(T) * (size_t)n, h->s));
+            CU(cudaMemsetAsync(B::x(L, 0), 0, sizeof(T) * (size_t)n, h->s));
+            CU(cudaMemsetAsync(B::b(C), 0, sizeof(T) * (size_t)C.A.nr, h->s));
+            CU(cudaMemsetAsync(B::x(C, 0), 0, sizeof(T) * (size_t)C.A.nr, h->s));
+            cleared = true;
+        }
+        float best = 3.4e38f, base = 3.4e38f;
+        int2 pick = kTuneCandidates[0];
+        for (const int2 &cand : kTuneCandidates) {
+            v.tb = cand.x;
+            v.grid = cand.y;
+            run(kind);   // warm
+            float tmin = 3.4e38f;
+            for (int rep = 0; rep < 5; ++rep) {
+                CU(cudaEventRecord(e0, h->s));
+                run(kind);
+                CU(cudaEventRecord(e1, h->s));
+                CU(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                tmin = std::min(tmin, ms);
+            }
+            if (&cand == kTuneCandidates) base = tmin;   // the default schedule
+            if (tmin < best) {
+                best = tmin;
+                pick = cand;
+            }
+        }
+        if (!(best < 0.95f * base)) pick = kTuneCandidates[0];
+        v.tb = pick.x;
+        v.grid = pick.y;
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune[key] = pick;
+    }
+    return LAIR_OK;
+}
+
+static lair_status autotune_views(lair_handle *h, Hier &H) {
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    lair_status st = LAIR_OK;
+    for (int l = 0; l < (int)H.lev.size() && st == LAIR_OK; ++l)
+        st = h->o.precision == LAIR_MIXED ? autotune_level<float>(h, H, l, e0, e1)
+                                          : autotune_level<double>(h, H, l, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 static lair_status capture_cycle(lair_handle *h, Hier &H) {
     long long dummy = 0;
     long long *saved = g_launches;
@@ -1551,6 +1666,11 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
         for (int l = 0; l < (int)H.lev.size(); ++l) add_view_plans(h, H, l, plans);
         TRY(build_sells(h, H, plans));
         tend(h, tv);
+    }
+    if (o.autotune) {
+        tp = tbegin(h, "setup_autotune", 0.0);
+        TRY(autotune_views(h, H));
+        tend(h, tp);
     }
     tp = tbegin(h, "setup_graph", 0.0);
     TRY(capture_cycle(h, H));
@@ -2336,6 +2456,7 @@ lair_status lair_options_default(lair_options *o) {
     o->rs_block = 4096;
     o->pmis_seed = 0x5eedULL;
     o->fgmres_restart = 30;
+    o->autotune = 1;
     return LAIR_OK;
 }
 
@@ -2347,6 +2468,7 @@ static lair_status check_options(lair_handle *h, const lair_options *o) {
     if (o->restriction < 0 || o->restriction > 1)
         return fail(h, LAIR_ERR_INVALID_ARG, "restriction %d", o->restriction);
     if (o->nodal < 0) return fail(h, LAIR_ERR_INVALID_ARG, "nodal %d", o->nodal);
+    if (o->autotune < 0 || o->autotune > 1) return fail(h, LAIR_ERR_INVALID_ARG, "autotune %d", o->autotune);
     if (o->nodal > NODAL_MAX) return fail(h, LAIR_ERR_UNSUPPORTED, "nodal <= %d", NODAL_MAX);
     if (o->nodal > 1 && o->block_size > 1)
         return fail(h, LAIR_ERR_INVALID_ARG, "nodal and block_size exclude each other");

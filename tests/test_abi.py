@@ -37,6 +37,7 @@ def test_options_defaults_and_status_strings():
     o = lair.options()
     assert o.cf_mode == lair.CF_AUTO and o.distance == 1 and o.theta == 0.25 and o.lump_tol == 1e-3
     assert o.coarse_max == 128 and o.max_levels == 25 and o.rs_block == 4096 and o.fgmres_restart == 30
+    assert o.autotune == 1 and o.nodal == 0 and o.restriction == lair.R_LAIR
     assert lair.lib.lair_status_string(0) == b"LAIR_OK"
     assert lair.lib.lair_status_string(13) == b"LAIR_ERR_UNSUPPORTED"
 
@@ -62,6 +63,7 @@ def test_setup_rejects_bad_arguments_without_a_gpu():
     (dict(nodal=6, block_size=6), 1, b"block_size"),
     (dict(nodal=2, restriction=1), 13, b"lAIR"),
     (dict(nodal=3), 1, b"multiple of nodal"),      # n = 4 is not a multiple of 3
+    (dict(autotune=2), 1, b"autotune"),
 ])
 def test_setup_rejects_option_combinations_without_a_gpu(kw, code, word):
     """Option checks run before any device call: unknown values, nodal with block scaling or the Neumann
