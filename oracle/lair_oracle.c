@@ -1994,8 +1994,8 @@ static void precond(ohier *H, const double *b, double *x) {
     if (H->o.prec == 0) {
         cycle64(H, 0, b, x);
     } else {
-        float *b32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
-        float *x32 = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+        float *b32 = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
+        float *x32 = (float *)calloc((size_t)(n > 0 ? n : 1), sizeof(float));
         for (int64_t i = 0; i < n; ++i) b32[i] = (float)b[i];
         cycle32(H, 0, b32, x32);
         for (int64_t i = 0; i < n; ++i) x[i] = (double)x32[i];
