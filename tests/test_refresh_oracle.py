@@ -176,3 +176,16 @@ def test_refresh_rejects_another_size():
     H = O.Hierarchy(s)
     t = W.config("fd2d_64", scale=20)
     assert H.refresh(t) != 0
+
+
+def test_refresh_rejects_another_pattern():
+    """Same size, different pattern: the kept structure does not apply, the refresh says so."""
+    s = W.fd_adr_2d(16, 3 * math.pi / 16, 1e-3, 0.5)
+    t = W.fd_adr_2d(16, 3 * math.pi / 16, 1e-3, 0.5)
+    A = t.to_scipy().tolil()
+    A[0, 17] = -0.01                  # one more entry in row 0
+    t2 = W.CsrSystem(s.n, *(lambda M: (M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data))(
+        A.tocsr()), s.b)
+    H = O.Hierarchy(s)
+    assert H.status == 0
+    assert H.refresh(t2) != 0
