@@ -13,7 +13,7 @@ c u = f, in synthetic stand-ins for the paper's Dolfin discretisations):
                     fastest, mesh width h = 1/(N+1).
 * ``dg_p2_advection`` upwind discontinuous Galerkin, nodal P2 on a structured
                     triangulated square, recirculating velocity, backward Euler
-                    mass shift (the implicit time step of Sec. 4.1.2, Eq. (4.3)).
+                    mass shift (the implicit time step of Sec. 4.1.1, Eq. (4.3)).
 * ``batched_fd``    many independent ``fd_adr`` systems with drawn parameters.
 
 Every matrix is CSR with int64 row pointers, int32 sorted column indices,
