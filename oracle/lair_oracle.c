@@ -472,32 +472,19 @@ static int build_neighbourhoods(const ograph *G, const int8_t *cf, int distance,
 }
 
 /* ------------------------------------------------------------------------- */
-/* Canonical 32-way tree sum used by the least-squares branch: partial l sums  */
-/* the terms with index = l (mod 32) in ascending order with fma; then pairs   */
-/* are added butterfly-wise with offsets 16, 8, 4, 2, 1 (p_l = p_l + p_{l^o}).  */
+/* Plain dot product of two strided vectors: terms added in ascending index    */
+/* with fma, starting from 0. Used by the least-squares branch.                */
 /* ------------------------------------------------------------------------- */
-static double tree_dot(const double *x, int64_t sx, const double *y, int64_t sy, int64_t s) {
-    double p[32];
-    for (int l = 0; l < 32; ++l) p[l] = 0.0;
-    for (int64_t r = 0; r < s; ++r) p[r & 31] = fma(x[r * sx], y[r * sy], p[r & 31]);
-    for (int o = 16; o >= 1; o >>= 1) {
-        double q[32];
-        for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
-        for (int l = 0; l < 32; ++l) p[l] = q[l];
-    }
-    return p[0];
+static double sdot(const double *x, int64_t sx, const double *y, int64_t sy, int64_t s) {
+    double acc = 0.0;
+    for (int64_t r = 0; r < s; ++r) acc = fma(x[r * sx], y[r * sy], acc);
+    return acc;
 }
 
-static float tree_dotf(const float *x, int64_t sx, const float *y, int64_t sy, int64_t s) {
-    float p[32];
-    for (int l = 0; l < 32; ++l) p[l] = 0.0f;
-    for (int64_t r = 0; r < s; ++r) p[r & 31] = fmaf(x[r * sx], y[r * sy], p[r & 31]);
-    for (int o = 16; o >= 1; o >>= 1) {
-        float q[32];
-        for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
-        for (int l = 0; l < 32; ++l) p[l] = q[l];
-    }
-    return p[0];
+static float sdotf(const float *x, int64_t sx, const float *y, int64_t sy, int64_t s) {
+    float acc = 0.0f;
+    for (int64_t r = 0; r < s; ++r) acc = fmaf(x[r * sx], y[r * sy], acc);
+    return acc;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -525,9 +512,9 @@ static void jacobi_ls(int64_t s, const double *M0, const double *rhs0, double *z
         int rotated = 0;
         for (int64_t p = 0; p < s - 1; ++p)
             for (int64_t q = p + 1; q < s; ++q) {
-                double alpha = tree_dot(B + p, s, B + p, s, s);
-                double beta = tree_dot(B + q, s, B + q, s, s);
-                double gamma = tree_dot(B + p, s, B + q, s, s);
+                double alpha = sdot(B + p, s, B + p, s, s);
+                double beta = sdot(B + q, s, B + q, s, s);
+                double gamma = sdot(B + p, s, B + q, s, s);
                 if (gamma == 0.0 || fabs(gamma) <= tol * sqrt(alpha * beta)) continue;
                 rotated = 1;
                 double zeta = (beta - alpha) / (2.0 * gamma);
@@ -547,14 +534,14 @@ static void jacobi_ls(int64_t s, const double *M0, const double *rhs0, double *z
     }
     double smax = 0.0;
     for (int64_t j = 0; j < s; ++j) {
-        sig[j] = sqrt(tree_dot(B + j, s, B + j, s, s));
+        sig[j] = sqrt(sdot(B + j, s, B + j, s, s));
         if (sig[j] > smax) smax = sig[j];
     }
     double cut = ((double)s * DBL_EPSILON) * smax;
     for (int64_t r = 0; r < s; ++r) z[r] = 0.0;
     for (int64_t j = 0; j < s; ++j) {
         if (!(sig[j] > cut)) continue;
-        double coef = (tree_dot(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
+        double coef = (sdot(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
         for (int64_t r = 0; r < s; ++r) z[r] = fma(V[r * s + j], coef, z[r]);
     }
     free(B); free(V); free(sig);
@@ -611,9 +598,9 @@ static void jacobi_lsf(int64_t s, const float *M0, const float *rhs0, float *z) 
         int rotated = 0;
         for (int64_t p = 0; p < s - 1; ++p)
             for (int64_t q = p + 1; q < s; ++q) {
-                float alpha = tree_dotf(B + p, s, B + p, s, s);
-                float beta = tree_dotf(B + q, s, B + q, s, s);
-                float gamma = tree_dotf(B + p, s, B + q, s, s);
+                float alpha = sdotf(B + p, s, B + p, s, s);
+                float beta = sdotf(B + q, s, B + q, s, s);
+                float gamma = sdotf(B + p, s, B + q, s, s);
                 if (gamma == 0.0f || fabsf(gamma) <= tol * sqrtf(alpha * beta)) continue;
                 rotated = 1;
                 float zeta = (beta - alpha) / (2.0f * gamma);
@@ -633,14 +620,14 @@ static void jacobi_lsf(int64_t s, const float *M0, const float *rhs0, float *z) 
     }
     float smax = 0.0f;
     for (int64_t j = 0; j < s; ++j) {
-        sig[j] = sqrtf(tree_dotf(B + j, s, B + j, s, s));
+        sig[j] = sqrtf(sdotf(B + j, s, B + j, s, s));
         if (sig[j] > smax) smax = sig[j];
     }
     float cut = ((float)s * FLT_EPSILON) * smax;
     for (int64_t r = 0; r < s; ++r) z[r] = 0.0f;
     for (int64_t j = 0; j < s; ++j) {
         if (!(sig[j] > cut)) continue;
-        float coef = (tree_dotf(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
+        float coef = (sdotf(B + j, s, rhs0, 1, s) / sig[j]) / sig[j];
         for (int64_t r = 0; r < s; ++r) z[r] = fmaf(V[r * s + j], coef, z[r]);
     }
     free(B); free(V); free(sig);

@@ -681,3 +681,133 @@ def test_batched_splitting_is_per_system():
         # coarse offsets count the C points of the systems before
         c = np.concatenate([[0], np.cumsum([int((cf[offs[k]:offs[k + 1]] == 1).sum()) for k in range(len(systems))])])
         assert np.array_equal(H.seg(1), c)
+
+
+# --------------------------------------------------------------------------------------
+# batched outer loops (independent systems in one block-diagonal hierarchy)
+# --------------------------------------------------------------------------------------
+
+def _batch(count=4, lo=8, hi=14, seed=3):
+    systems = W.batched_fd(count=count, side_lo=lo, side_hi=hi, seed=seed)
+    A, offs = W.block_diagonal(systems)
+    return systems, A, offs
+
+
+def _system_precond(H, n, a, b):
+    """Dense matrix of the preconditioner restricted to the rows/columns [a, b) of one system;
+    also checks that the block-diagonal hierarchy leaves every other system untouched."""
+    cols = []
+    for j in range(a, b):
+        e = np.zeros(n)
+        e[j] = 1.0
+        z = H.precond(e)
+        assert not np.any(z[:a]) and not np.any(z[b:])
+        cols.append(z[a:b])
+    return np.stack(cols, 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_stationary_is_per_system_refinement(prec):
+    """Stationary refinement on a batch: each system follows x <- x + M_q^{-1} (b_q - A_q x) on its own
+    and stops once its own relative residual is <= tol; the result solves each system (sparse LU)."""
+    systems, A, offs = _batch()
+    H = O.Hierarchy(A, seg=offs, prec=prec)
+    tol = 1e-10
+    x, rep = H.solve_batched(A.b, tol=tol, cycle=0)
+    assert rep["status"] == 0
+    for q, s in enumerate(systems):
+        a, b = offs[q], offs[q + 1]
+        Aq = s.to_scipy().toarray()
+        Mq = _system_precond(H, A.n, a, b)
+        xr = np.zeros(s.n)
+        k = 0
+        while np.linalg.norm(s.b - Aq @ xr) / np.linalg.norm(s.b) > tol:
+            xr = xr + Mq @ (s.b - Aq @ xr)
+            k += 1
+            assert k <= 500
+        assert rep["iters"][q] == k
+        np.testing.assert_allclose(x[a:b], xr, rtol=0, atol=1e-9 * np.abs(xr).max())
+        ref = spla.spsolve(s.to_scipy().tocsc(), s.b)
+        assert np.linalg.norm(x[a:b] - ref) <= 1e-7 * np.linalg.norm(ref)
+        relq = np.linalg.norm(s.b - Aq @ x[a:b]) / np.linalg.norm(s.b)
+        assert relq <= tol and rep["rel"][q] == pytest.approx(relq, rel=1e-6)
+
+
+def test_batched_fgmres_minimal_residual_per_system():
+    """FGMRES on a batch with a fixed preconditioner: iterate k of system q minimises
+    ||b_q - A_q x|| over M_q K_k(A_q M_q, b_q) (zero initial guess), whatever the other systems do."""
+    systems, A, offs = _batch(count=3, seed=4)
+    H = O.Hierarchy(A, seg=offs, cf_mode=O.CF_PMIS)
+    mats = [(s.to_scipy().toarray(), _system_precond(H, A.n, offs[q], offs[q + 1])) for q, s in enumerate(systems)]
+    for k in (1, 2, 3):
+        x, rep = H.solve_batched(A.b, tol=0.0, cycle=1, max_iter=k)
+        for q, s in enumerate(systems):
+            Aq, Mq = mats[q]
+            AM = Aq @ Mq
+            Kb = [s.b]
+            for _ in range(k - 1):
+                Kb.append(AM @ Kb[-1])
+            Q, _ = np.linalg.qr(np.stack(Kb, 1))
+            y, *_ = np.linalg.lstsq(AM @ Q, s.b, rcond=None)
+            best = np.linalg.norm(s.b - AM @ Q @ y)
+            got = np.linalg.norm(s.b - Aq @ x[offs[q]:offs[q + 1]])
+            assert rep["iters"][q] == k
+            assert got == pytest.approx(best, rel=1e-6, abs=1e-14)
+    x, rep = H.solve_batched(A.b, tol=1e-10, cycle=1)
+    assert rep["status"] == 0
+    for q, s in enumerate(systems):
+        ref = spla.spsolve(s.to_scipy().tocsc(), s.b)
+        assert np.linalg.norm(x[offs[q]:offs[q + 1]] - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+# --------------------------------------------------------------------------------------
+# the FP32 cycle of mixed precision (north-star pattern 1), restated in numpy float32
+# --------------------------------------------------------------------------------------
+
+def _f32_two_level_cycle(A, cf, R, P, K, b, seq):
+    """One V-cycle (post-relaxation, zero initial guess) of a two-level hierarchy in float32:
+    b rounded to float; b_c = R b; the coarse system solved in FP64 and rounded to float;
+    x = P x_c; then the Jacobi sweeps of seq (all updates of a sweep read the same old x)."""
+    f = np.float32
+    A32, R32, P32 = (M.astype(f).toarray() for M in (A, R, P))
+    dinv = (1.0 / A.diagonal()).astype(f)
+    b32 = b.astype(f)
+    bc = R32 @ b32
+    xc = np.linalg.solve(K.toarray(), bc.astype(np.float64)).astype(f)
+    x = P32 @ xc
+    for tgt in seq:
+        r = b32 - A32 @ x
+        x = np.where(cf == tgt, x + dinv * r, x).astype(f)
+    assert x.dtype == f
+    return x
+
+
+@pytest.mark.parametrize("relax,seq", [(O.RELAX_FFC, (0, 0, 1)), (O.RELAX_FCF, (0, 1, 0)), (O.RELAX_FF, (0, 0))])
+def test_fp32_cycle_matches_numpy_float32(relax, seq):
+    """Mixed precision: the oracle's FP32 two-level cycle against the same cycle in numpy float32,
+    entry by entry (a wrong sweep order moves entries by about 5e-4 of the largest here). The cut
+    between precisions: R holds FP32 values and the cycle returns FP32 values, which the FP64 cycle
+    does not."""
+    s = W.config("fd2d_64", scale=13)                     # n = 169
+    kw = dict(cf_mode=O.CF_RS, max_levels=2, coarse_max=s.n - 1, relax=relax, lump_tol=0.0)
+    H32 = O.Hierarchy(s, prec=1, **kw)
+    H64 = O.Hierarchy(s, prec=0, **kw)
+    assert len(H32.levels) == 2
+    L0, L1 = H32.levels
+    n, nc = L0.n, L0.nc
+    A = csr_to_scipy(L0.A, (n, n))
+    R = csr_to_scipy(L0.R, (nc, n))
+    P = csr_to_scipy(L0.P, (n, nc))
+    K = csr_to_scipy(L1.A, (nc, nc))
+    assert np.array_equal(R.data.astype(np.float32).astype(np.float64), R.data)   # FP32 local solves
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        v = rng.uniform(-1, 1, n)
+        ref = _f32_two_level_cycle(A, L0.cf, R, P, K, v, seq).astype(np.float64)
+        z = H32.precond(v)
+        scale = np.abs(ref).max()
+        assert np.abs(z - ref).max() <= 1e-6 * scale
+        assert np.array_equal(z.astype(np.float32).astype(np.float64), z)
+        z64 = H64.precond(v)
+        assert not np.array_equal(z64.astype(np.float32).astype(np.float64), z64)
+        assert np.abs(z64 - ref).max() <= 1e-5 * scale
