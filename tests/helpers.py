@@ -72,3 +72,12 @@ def compare_hierarchies(G, H, val_tol):
             worst[f"{name}{l}"] = row_rel(rp, val, O[2])
             assert worst[f"{name}{l}"] <= val_tol, f"level {l}: {name} values differ by {worst[f'{name}{l}']:.3e}"
     return worst
+
+
+def entrywise_rel(z, zo):
+    """max over entries of |z - zo| / max |zo| (0 for an empty vector)."""
+    z = np.asarray(z, np.float64)
+    zo = np.asarray(zo, np.float64)
+    if zo.size == 0:
+        return 0.0
+    return float(np.abs(z - zo).max() / max(np.abs(zo).max(), 1e-300))

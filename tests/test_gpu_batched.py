@@ -10,7 +10,7 @@ import scipy.sparse.linalg as spla
 
 import workloads as W
 from oracle import oracle as O
-from tests.helpers import compare_hierarchies
+from tests.helpers import compare_hierarchies, entrywise_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +96,7 @@ def test_batch_setup_solve_convenience(lair):
 
 @pytest.mark.parametrize("count", [4, 10])
 def test_batched_vcycle_matches_oracle(lair, count):
-    """One V-cycle on a batch equals the oracle's bit for bit (FP32 cycle within 1e-5)."""
+    """One V-cycle on a batch equals the oracle's entry by entry (FP32 cycle: within 1e-5 of the largest entry)."""
     import torch
     systems, A, offs = batch(count, 16, 96)
     G = lair.Hierarchy.batched(torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
@@ -106,4 +106,4 @@ def test_batched_vcycle_matches_oracle(lair, count):
     z = G.precond(torch.from_numpy(v).cuda()).cpu().numpy()
     zo = H.precond(v)
     assert np.isfinite(z).all()
-    assert np.linalg.norm(z - zo) <= 1e-5 * np.linalg.norm(zo)
+    assert entrywise_rel(z, zo) <= 1e-5

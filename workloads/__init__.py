@@ -429,3 +429,13 @@ def config(name: str, scale: int | None = None):
     if name == "fd3d_192":
         return fd_adr_3d(scale or 192, (1.0, 0.7, 0.4), 1e-5, 0.05, b_seed=0)
     raise KeyError(name)
+
+
+# Solver options of the benchmark workloads (shared by bench.py and the full-size parity tests).
+# Keys are lair.Hierarchy keyword arguments; no arithmetic here.
+BENCH_OPTIONS = {
+    "dg_p2_256": dict(opts=dict(distance=2, interp=1, strength_abs=1, block_size=6, cf_mode=1), tol=1e-8,
+                      cycle="fgmres"),
+    "batched_512": dict(opts=dict(distance=1), tol=1e-8, cycle="fgmres", batched=True),
+    "fd3d_192": dict(opts=dict(distance=1), tol=1e-8, cycle="stationary"),
+}
