@@ -39,6 +39,42 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Loops whose iterations are independent (one row, one C point or one index block
+ * each, writing only their own outputs) may run on several host threads when the
+ * file is built with OpenMP; every result is the same bits for any thread count,
+ * since no floating-point sum crosses iterations. Reductions, the classical first
+ * pass over the whole graph, PMIS and the Krylov loops stay sequential. */
+#ifdef _OPENMP
+#define ORA_PARALLEL_FOR _Pragma("omp parallel for schedule(dynamic, 64)")
+#define ORA_PARALLEL_FOR_EACH _Pragma("omp parallel for schedule(dynamic, 1)")
+#define ORA_PARALLEL _Pragma("omp parallel")
+#define ORA_FOR _Pragma("omp for schedule(dynamic, 64)")
+#else
+#define ORA_PARALLEL_FOR
+#define ORA_PARALLEL_FOR_EACH
+#define ORA_PARALLEL
+#define ORA_FOR
+#endif
+
+void ora_set_threads(int t) {
+#ifdef _OPENMP
+    omp_set_num_threads(t > 0 ? t : omp_get_num_procs());
+#else
+    (void)t;
+#endif
+}
+
+int ora_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define ORA_OK 0
 #define ORA_ERR_ARG 1
@@ -155,6 +191,7 @@ static int cmp_i32(const void *a, const void *b) {
 /* ------------------------------------------------------------------------- */
 void ora_strength(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                   double theta, int absmode, uint8_t *strong) {
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         double m = 0.0;
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
@@ -295,13 +332,26 @@ static void cf_rs_block(const ograph *S, const ograph *ST, int64_t b0, int64_t b
 static void cf_rs_blocked_seg(const ograph *S, const ograph *ST, int64_t B, const int64_t *seg, int nseg, int8_t *cf) {
     int64_t n = S->n;
     int64_t *lam = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    if (!seg || nseg <= 0) {
-        for (int64_t b0 = 0; b0 < n; b0 += B) cf_rs_block(S, ST, b0, b0 + B < n ? b0 + B : n, cf, lam);
-    } else {
-        for (int q = 0; q < nseg; ++q)
-            for (int64_t b0 = seg[q]; b0 < seg[q + 1]; b0 += B)
-                cf_rs_block(S, ST, b0, b0 + B < seg[q + 1] ? b0 + B : seg[q + 1], cf, lam);
+    /* the blocks in index order (each block touches only its own points, so they may run in any order) */
+    int64_t nb = 0, cap = 16;
+    int64_t *b0s = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap), *b1s = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int nq = (seg && nseg > 0) ? nseg : 1;
+    for (int q = 0; q < nq; ++q) {
+        int64_t lo = (seg && nseg > 0) ? seg[q] : 0, hi = (seg && nseg > 0) ? seg[q + 1] : n;
+        for (int64_t b0 = lo; b0 < hi; b0 += B) {
+            if (nb == cap) {
+                cap *= 2;
+                b0s = (int64_t *)realloc(b0s, sizeof(int64_t) * (size_t)cap);
+                b1s = (int64_t *)realloc(b1s, sizeof(int64_t) * (size_t)cap);
+            }
+            b0s[nb] = b0;
+            b1s[nb] = b0 + B < hi ? b0 + B : hi;
+            nb++;
+        }
     }
+    ORA_PARALLEL_FOR_EACH
+    for (int64_t t = 0; t < nb; ++t) cf_rs_block(S, ST, b0s[t], b1s[t], cf, lam);
+    free(b0s); free(b1s);
     free(lam);
 }
 
@@ -421,51 +471,66 @@ static int64_t sort_unique(int32_t *t, int64_t m) {
     return u;
 }
 
+/* the set of C point i in tmp (grown as needed); returns its size */
+static int64_t neighbourhood_of(const ograph *G, const int8_t *cf, int distance, int64_t i, int32_t **tmp_,
+                                int64_t *tcap_, int32_t **nxt_, int64_t *ncap_) {
+    int32_t *tmp = *tmp_, *nxt = *nxt_;
+    int64_t tcap = *tcap_, ncap = *ncap_;
+    /* distance 1 */
+    int64_t need = G->rp[i + 1] - G->rp[i];
+    if (need > tcap) { tcap = need + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
+    int64_t t = 0;
+    for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p)
+        if (cf[G->col[p]] == CF_F) tmp[t++] = G->col[p];
+    t = sort_unique(tmp, t);
+    /* each further distance: the set and the F points of G_j for every j in it */
+    for (int d = 2; d <= distance; ++d) {
+        need = t;
+        for (int64_t a = 0; a < t; ++a) need += G->rp[tmp[a] + 1] - G->rp[tmp[a]];
+        if (need > ncap) { ncap = need + 16; nxt = (int32_t *)realloc(nxt, sizeof(int32_t) * (size_t)ncap); }
+        int64_t m = 0;
+        for (int64_t a = 0; a < t; ++a) {
+            int64_t j = tmp[a];
+            nxt[m++] = (int32_t)j;
+            for (int64_t q = G->rp[j]; q < G->rp[j + 1]; ++q) {
+                int64_t k = G->col[q];
+                if (cf[k] == CF_F && k != i) nxt[m++] = (int32_t)k;
+            }
+        }
+        m = sort_unique(nxt, m);
+        if (m > tcap) { tcap = m + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
+        memcpy(tmp, nxt, sizeof(int32_t) * (size_t)m);
+        t = m;
+    }
+    *tmp_ = tmp; *nxt_ = nxt; *tcap_ = tcap; *ncap_ = ncap;
+    return t;
+}
+
 static int build_neighbourhoods(const ograph *G, const int8_t *cf, int distance,
                                 int64_t nc, const int64_t *cpts, int64_t **out_rp, int32_t **out_col) {
     int64_t *rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
-    int64_t cap = 1024, len = 0;
-    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
-    int32_t *tmp = NULL, *nxt = NULL;
-    int64_t tcap = 0, ncap = 0;
-    for (int64_t c = 0; c < nc; ++c) {
-        int64_t i = cpts[c];
-        /* distance 1 */
-        int64_t need = G->rp[i + 1] - G->rp[i];
-        if (need > tcap) { tcap = need + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
-        int64_t t = 0;
-        for (int64_t p = G->rp[i]; p < G->rp[i + 1]; ++p)
-            if (cf[G->col[p]] == CF_F) tmp[t++] = G->col[p];
-        t = sort_unique(tmp, t);
-        /* each further distance: the set and the F points of G_j for every j in it */
-        for (int d = 2; d <= distance; ++d) {
-            need = t;
-            for (int64_t a = 0; a < t; ++a) need += G->rp[tmp[a] + 1] - G->rp[tmp[a]];
-            if (need > ncap) { ncap = need + 16; nxt = (int32_t *)realloc(nxt, sizeof(int32_t) * (size_t)ncap); }
-            int64_t m = 0;
-            for (int64_t a = 0; a < t; ++a) {
-                int64_t j = tmp[a];
-                nxt[m++] = (int32_t)j;
-                for (int64_t q = G->rp[j]; q < G->rp[j + 1]; ++q) {
-                    int64_t k = G->col[q];
-                    if (cf[k] == CF_F && k != i) nxt[m++] = (int32_t)k;
-                }
-            }
-            m = sort_unique(nxt, m);
-            if (m > tcap) { tcap = m + 16; tmp = (int32_t *)realloc(tmp, sizeof(int32_t) * (size_t)tcap); }
-            memcpy(tmp, nxt, sizeof(int32_t) * (size_t)m);
-            t = m;
+    int32_t **rows = (int32_t **)malloc(sizeof(int32_t *) * (size_t)(nc > 0 ? nc : 1));
+    ORA_PARALLEL
+    {
+        int32_t *tmp = NULL, *nxt = NULL;
+        int64_t tcap = 0, ncap = 0;
+        ORA_FOR
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t t = neighbourhood_of(G, cf, distance, cpts[c], &tmp, &tcap, &nxt, &ncap);
+            rows[c] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(t > 0 ? t : 1));
+            memcpy(rows[c], tmp, sizeof(int32_t) * (size_t)t);
+            rp[c + 1] = t;
         }
-        if (len + t > cap) {
-            while (len + t > cap) cap *= 2;
-            col = (int32_t *)realloc(col, sizeof(int32_t) * (size_t)cap);
-        }
-        memcpy(col + len, tmp, sizeof(int32_t) * (size_t)t);
-        len += t;
-        rp[c + 1] = len;
+        free(tmp);
+        free(nxt);
     }
-    free(tmp);
-    free(nxt);
+    for (int64_t c = 0; c < nc; ++c) rp[c + 1] += rp[c];
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rp[nc] > 0 ? rp[nc] : 1));
+    for (int64_t c = 0; c < nc; ++c) {
+        memcpy(col + rp[c], rows[c], sizeof(int32_t) * (size_t)(rp[c + 1] - rp[c]));
+        free(rows[c]);
+    }
+    free(rows);
     *out_rp = rp;
     *out_col = col;
     return ORA_OK;
@@ -686,51 +751,55 @@ static int build_lair_R(const ocsr *A, const int8_t *cf, const int64_t *cidx, in
     if (csr_alloc(R, nc, A->nr, nnz)) return ORA_ERR_OOM;
     int64_t smax = 0;
     for (int64_t c = 0; c < nc; ++c) if (nb_rp[c + 1] - nb_rp[c] > smax) smax = nb_rp[c + 1] - nb_rp[c];
-    double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
-    double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
-    double *z = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
-    float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
-    float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
-    float *zf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
-    int64_t p = 0;
+    for (int64_t c = 0; c <= nc; ++c) R->rp[c] = nb_rp[c] + c;     /* row c: its set and the C point itself */
     (void)cf; (void)cidx;
-    for (int64_t c = 0; c < nc; ++c) {
-        int64_t i = cpts[c];
-        const int32_t *nb = nb_col + nb_rp[c];
-        int64_t s = nb_rp[c + 1] - nb_rp[c];
-        for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
-        for (int64_t r = 0; r < s; ++r) rhs[r] = 0.0;
-        for (int64_t cc = 0; cc < s; ++cc) {
-            int64_t row = nb[cc];
-            for (int64_t k = A->rp[row]; k < A->rp[row + 1]; ++k) {
-                int64_t r = find_pos(nb, s, A->col[k]);
-                if (r >= 0) M[r * s + cc] = A->val[k];
+    ORA_PARALLEL
+    {
+        double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
+        double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+        double *z = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+        float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
+        float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+        float *zf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+        ORA_FOR
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t i = cpts[c];
+            const int32_t *nb = nb_col + nb_rp[c];
+            int64_t s = nb_rp[c + 1] - nb_rp[c];
+            for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
+            for (int64_t r = 0; r < s; ++r) rhs[r] = 0.0;
+            for (int64_t cc = 0; cc < s; ++cc) {
+                int64_t row = nb[cc];
+                for (int64_t k = A->rp[row]; k < A->rp[row + 1]; ++k) {
+                    int64_t r = find_pos(nb, s, A->col[k]);
+                    if (r >= 0) M[r * s + cc] = A->val[k];
+                }
             }
+            for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+                int64_t r = find_pos(nb, s, A->col[k]);
+                if (r >= 0) rhs[r] = -A->val[k];
+            }
+            int ls;
+            if (prec == 0) {
+                ls = ora_local_solve(s, M, rhs, z);
+            } else {
+                for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
+                for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
+                ls = ora_local_solve_f32(s, Mf, rf, zf);
+                for (int64_t r = 0; r < s; ++r) z[r] = (double)zf[r];
+            }
+            if (lsflag) lsflag[c] = (uint8_t)ls;
+            /* merge {nb, z} with (i, 1) in ascending column order */
+            int64_t p = R->rp[c];
+            int placed = 0;
+            for (int64_t r = 0; r < s; ++r) {
+                if (!placed && i < nb[r]) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; placed = 1; }
+                R->col[p] = nb[r]; R->val[p] = z[r]; p++;
+            }
+            if (!placed) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; }
         }
-        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
-            int64_t r = find_pos(nb, s, A->col[k]);
-            if (r >= 0) rhs[r] = -A->val[k];
-        }
-        int ls;
-        if (prec == 0) {
-            ls = ora_local_solve(s, M, rhs, z);
-        } else {
-            for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
-            for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
-            ls = ora_local_solve_f32(s, Mf, rf, zf);
-            for (int64_t r = 0; r < s; ++r) z[r] = (double)zf[r];
-        }
-        if (lsflag) lsflag[c] = (uint8_t)ls;
-        /* merge {nb, z} with (i, 1) in ascending column order */
-        int placed = 0;
-        for (int64_t r = 0; r < s; ++r) {
-            if (!placed && i < nb[r]) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; placed = 1; }
-            R->col[p] = nb[r]; R->val[p] = z[r]; p++;
-        }
-        if (!placed) { R->col[p] = (int32_t)i; R->val[p] = 1.0; p++; }
-        R->rp[c + 1] = p;
+        free(M); free(rhs); free(z); free(Mf); free(rf); free(zf);
     }
-    free(M); free(rhs); free(z); free(Mf); free(rf); free(zf);
     return ORA_OK;
 }
 
@@ -871,50 +940,55 @@ static int build_P_laip_on(const ocsr *A, int64_t nc, const int64_t *cpts, const
     coo_ent *ent = (coo_ent *)malloc(sizeof(coo_ent) * (size_t)(total > 0 ? total : 1));
     int64_t smax = 0;
     for (int64_t c = 0; c < nc; ++c) if (q_rp[c + 1] - q_rp[c] > smax) smax = q_rp[c + 1] - q_rp[c];
-    double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
-    double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
-    double *w = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
-    float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
-    float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
-    float *wf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
-    int64_t e = 0;
-    for (int64_t c = 0; c < nc; ++c) {
-        int64_t ci = cpts[c];
-        const int32_t *Q = q_col + q_rp[c];
-        int64_t s = q_rp[c + 1] - q_rp[c];
-        for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
-        for (int64_t r = 0; r < s; ++r) {
-            int64_t jr = Q[r];
-            for (int64_t k = A->rp[jr]; k < A->rp[jr + 1]; ++k) {
-                int64_t q = find_pos(Q, s, A->col[k]);
-                if (q >= 0) M[r * s + q] = A->val[k];
+    ORA_PARALLEL
+    {
+        double *M = (double *)malloc(sizeof(double) * (size_t)(smax * smax + 1));
+        double *rhs = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+        double *w = (double *)malloc(sizeof(double) * (size_t)(smax + 1));
+        float *Mf = (float *)malloc(sizeof(float) * (size_t)(smax * smax + 1));
+        float *rf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+        float *wf = (float *)malloc(sizeof(float) * (size_t)(smax + 1));
+        ORA_FOR
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t ci = cpts[c];
+            const int32_t *Q = q_col + q_rp[c];
+            int64_t s = q_rp[c + 1] - q_rp[c];
+            for (int64_t k = 0; k < s * s; ++k) M[k] = 0.0;
+            for (int64_t r = 0; r < s; ++r) {
+                int64_t jr = Q[r];
+                for (int64_t k = A->rp[jr]; k < A->rp[jr + 1]; ++k) {
+                    int64_t q = find_pos(Q, s, A->col[k]);
+                    if (q >= 0) M[r * s + q] = A->val[k];
+                }
+                double a;
+                find_entry(A, jr, ci, &a);
+                rhs[r] = -a;
             }
-            double a;
-            find_entry(A, jr, ci, &a);
-            rhs[r] = -a;
+            int ls;
+            if (prec == 0) {
+                ls = ora_local_solve(s, M, rhs, w);
+            } else {
+                for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
+                for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
+                ls = ora_local_solve_f32(s, Mf, rf, wf);
+                for (int64_t r = 0; r < s; ++r) w[r] = (double)wf[r];
+            }
+            if (lsflag) lsflag[c] = (uint8_t)ls;
+            int64_t e = q_rp[c] + c;                 /* column c's entries: its set, then its C point */
+            for (int64_t r = 0; r < s; ++r) ent[e++] = (coo_ent){Q[r], (int32_t)c, w[r]};
+            ent[e++] = (coo_ent){ci, (int32_t)c, 1.0};
         }
-        int ls;
-        if (prec == 0) {
-            ls = ora_local_solve(s, M, rhs, w);
-        } else {
-            for (int64_t k = 0; k < s * s; ++k) Mf[k] = (float)M[k];
-            for (int64_t r = 0; r < s; ++r) rf[r] = (float)rhs[r];
-            ls = ora_local_solve_f32(s, Mf, rf, wf);
-            for (int64_t r = 0; r < s; ++r) w[r] = (double)wf[r];
-        }
-        if (lsflag) lsflag[c] = (uint8_t)ls;
-        for (int64_t r = 0; r < s; ++r) ent[e++] = (coo_ent){Q[r], (int32_t)c, w[r]};
-        ent[e++] = (coo_ent){ci, (int32_t)c, 1.0};
+        free(M); free(rhs); free(w); free(Mf); free(rf); free(wf);
     }
-    qsort(ent, (size_t)e, sizeof(coo_ent), cmp_coo);
-    if (csr_alloc(P, n, nc, e)) return ORA_ERR_OOM;
-    for (int64_t k = 0; k < e; ++k) {
+    qsort(ent, (size_t)total, sizeof(coo_ent), cmp_coo);
+    if (csr_alloc(P, n, nc, total)) return ORA_ERR_OOM;
+    for (int64_t k = 0; k < total; ++k) {
         P->rp[ent[k].row + 1]++;
         P->col[k] = ent[k].col;
         P->val[k] = ent[k].val;
     }
     for (int64_t i = 0; i < n; ++i) P->rp[i + 1] += P->rp[i];
-    free(ent); free(M); free(rhs); free(w); free(Mf); free(rf); free(wf);
+    free(ent);
     return ORA_OK;
 }
 
@@ -937,36 +1011,51 @@ static int build_P_laip(const ocsr *A, const ograph *ST, const int8_t *cf, int64
 /* ------------------------------------------------------------------------- */
 static int spgemm(const ocsr *X, const ocsr *Y, ocsr *Z) {
     int64_t nr = X->nr, ncol = Y->nc;
-    double *acc = (double *)malloc(sizeof(double) * (size_t)(ncol > 0 ? ncol : 1));
-    int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncol > 0 ? ncol : 1));
-    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ncol > 0 ? ncol : 1));
-    for (int64_t j = 0; j < ncol; ++j) mark[j] = -1;
-    int64_t cap = X->rp[nr] + Y->rp[Y->nr] + 16, len = 0;
     Z->nr = nr; Z->nc = ncol;
     Z->rp = (int64_t *)calloc((size_t)nr + 1, sizeof(int64_t));
-    Z->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap);
-    Z->val = (double *)malloc(sizeof(double) * (size_t)cap);
-    for (int64_t a = 0; a < nr; ++a) {
-        int64_t cnt = 0;
-        for (int64_t p = X->rp[a]; p < X->rp[a + 1]; ++p) {
-            int64_t k = X->col[p];
-            double x = X->val[p];
-            for (int64_t q = Y->rp[k]; q < Y->rp[k + 1]; ++q) {
-                int64_t l = Y->col[q];
-                if (mark[l] != a) { mark[l] = a; acc[l] = 0.0; list[cnt++] = (int32_t)l; }
-                acc[l] = fma(x, Y->val[q], acc[l]);
-            }
+    /* pass 1: the number of distinct columns of every row */
+    ORA_PARALLEL
+    {
+        int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncol > 0 ? ncol : 1));
+        for (int64_t j = 0; j < ncol; ++j) mark[j] = -1;
+        ORA_FOR
+        for (int64_t a = 0; a < nr; ++a) {
+            int64_t cnt = 0;
+            for (int64_t p = X->rp[a]; p < X->rp[a + 1]; ++p)
+                for (int64_t q = Y->rp[X->col[p]]; q < Y->rp[X->col[p] + 1]; ++q)
+                    if (mark[Y->col[q]] != a) { mark[Y->col[q]] = a; cnt++; }
+            Z->rp[a + 1] = cnt;
         }
-        qsort(list, (size_t)cnt, sizeof(int32_t), cmp_i32);
-        if (len + cnt > cap) {
-            while (len + cnt > cap) cap *= 2;
-            Z->col = (int32_t *)realloc(Z->col, sizeof(int32_t) * (size_t)cap);
-            Z->val = (double *)realloc(Z->val, sizeof(double) * (size_t)cap);
-        }
-        for (int64_t t = 0; t < cnt; ++t) { Z->col[len] = list[t]; Z->val[len] = acc[list[t]]; len++; }
-        Z->rp[a + 1] = len;
+        free(mark);
     }
-    free(acc); free(mark); free(list);
+    for (int64_t a = 0; a < nr; ++a) Z->rp[a + 1] += Z->rp[a];
+    int64_t len = Z->rp[nr];
+    Z->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(len > 0 ? len : 1));
+    Z->val = (double *)malloc(sizeof(double) * (size_t)(len > 0 ? len : 1));
+    /* pass 2: entry (a, l) starts at 0 and adds x_ak * y_kl with fma for k in ascending order */
+    ORA_PARALLEL
+    {
+        double *acc = (double *)malloc(sizeof(double) * (size_t)(ncol > 0 ? ncol : 1));
+        int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ncol > 0 ? ncol : 1));
+        for (int64_t j = 0; j < ncol; ++j) mark[j] = -1;
+        ORA_FOR
+        for (int64_t a = 0; a < nr; ++a) {
+            int32_t *list = Z->col + Z->rp[a];
+            int64_t cnt = 0;
+            for (int64_t p = X->rp[a]; p < X->rp[a + 1]; ++p) {
+                int64_t k = X->col[p];
+                double x = X->val[p];
+                for (int64_t q = Y->rp[k]; q < Y->rp[k + 1]; ++q) {
+                    int64_t l = Y->col[q];
+                    if (mark[l] != a) { mark[l] = a; acc[l] = 0.0; list[cnt++] = (int32_t)l; }
+                    acc[l] = fma(x, Y->val[q], acc[l]);
+                }
+            }
+            qsort(list, (size_t)cnt, sizeof(int32_t), cmp_i32);
+            for (int64_t t = 0; t < cnt; ++t) Z->val[Z->rp[a] + t] = acc[list[t]];
+        }
+        free(acc); free(mark);
+    }
     return ORA_OK;
 }
 
@@ -1851,6 +1940,7 @@ int ora_refresh(ohier *H, int64_t n, const int64_t *rp, const int32_t *col, cons
 /* Row products accumulate with fma in ascending column order.                 */
 /* ------------------------------------------------------------------------- */
 static void spmv64(const ocsr *A, const double *x, double *y) {
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < A->nr; ++i) {
         double acc = 0.0;
         for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) acc = fma(A->val[k], x[A->col[k]], acc);
@@ -1906,6 +1996,7 @@ static void sweep32_nodal(const olevel *L, int64_t k, int target, const float *b
 
 static void sweep64(const olevel *L, int target, const double *b, const double *x, double *xo) {
     const ocsr *A = &L->A;
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < A->nr; ++i) {
         if (L->cf[i] != target) { xo[i] = x[i]; continue; }
         double acc = 0.0;
@@ -1935,6 +2026,7 @@ static void cycle64(ohier *H, int l, const double *b, double *x) {
 }
 
 static void spmv32(int64_t nr, const int64_t *rp, const int32_t *col, const float *val, const float *x, float *y) {
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < nr; ++i) {
         float acc = 0.0f;
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) acc = fmaf(val[k], x[col[k]], acc);
@@ -1965,6 +2057,7 @@ static void cycle32(ohier *H, int l, const float *b, float *x) {
             memcpy(x, t, sizeof(float) * (size_t)n);
             continue;
         }
+        ORA_PARALLEL_FOR
         for (int64_t i = 0; i < n; ++i) {
             if (L->cf[i] != tgt) { t[i] = x[i]; continue; }
             float acc = 0.0f;
@@ -2005,6 +2098,7 @@ static double dot(int64_t n, const double *x, const double *y) {
 }
 
 static void residual(const ocsr *A, const double *b, const double *x, double *r) {
+    ORA_PARALLEL_FOR
     for (int64_t i = 0; i < A->nr; ++i) {
         double acc = 0.0;
         for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) acc = fma(A->val[k], x[A->col[k]], acc);

@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 and by the CPU-baseline leg of ``bench.py``. The product path never loads it.
 
-The oracle is single-threaded FP64 C compiled with ``-ffp-contract=off`` so that
-only the explicit ``fma()`` calls of the source fuse operations.
+The oracle is FP64 C compiled with ``-ffp-contract=off`` so that only the explicit
+``fma()`` calls of the source fuse operations. Built with OpenMP where the compiler
+has it: loops over independent rows, C points and index blocks may then use several
+host threads (``set_threads``); every result is bit-identical for any thread count.
 """
 from __future__ import annotations
 
@@ -28,11 +30,24 @@ STATUS = {0: "OK", 1: "ARG", 5: "ZERO_DIAG", 6: "STALLED", 7: "NOT_CONVERGED", 8
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (portable flags only: the same source builds on x86_64 and aarch64)."""
+    """Compile the oracle (portable flags only: the same source builds on x86_64 and aarch64;
+    no -march=native, so the same code runs on both). OpenMP if gcc has it, else serial."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", LIB, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", LIB, SRC, "-lm"]
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base, check=True)
     return LIB
+
+
+def set_threads(t: int | None = None) -> int:
+    """Host threads for the oracle's independent loops (None: every core); returns the count in use."""
+    lib().ora_set_threads(0 if t is None else int(t))
+    return threads()
+
+
+def threads() -> int:
+    return int(lib().ora_get_threads())
 
 
 class Opts(C.Structure):
@@ -90,6 +105,8 @@ def lib():
         L.ora_refresh.restype = C.c_int
         L.ora_refresh.argtypes = [p, C.c_int64, p, p, p]
         L.ora_transpose.argtypes = [C.c_int64, p, p, p, p, p, p]
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_get_threads.restype = C.c_int
         _lib = L
     return _lib
 

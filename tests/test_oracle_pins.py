@@ -811,3 +811,32 @@ def test_fp32_cycle_matches_numpy_float32(relax, seq):
         z64 = H64.precond(v)
         assert not np.array_equal(z64.astype(np.float32).astype(np.float64), z64)
         assert np.abs(z64 - ref).max() <= 1e-5 * scale
+
+
+# --------------------------------------------------------------------------------------
+# host threads: the oracle's independent loops give the same bits for any thread count
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,scale,kw", [
+    ("fd3d_192", 14, dict(distance=1, prec=1)),
+    ("dg_p2_256", 6, dict(distance=2, interp=1, strength_abs=1, block_size=6, cf_mode=O.CF_PMIS)),
+    ("fd2d_64", 30, dict(distance=2, cf_mode=O.CF_AUTO, rs_block=100)),
+])
+def test_oracle_thread_count_does_not_change_results(name, scale, kw):
+    s = W.config(name, scale=scale)
+    before = O.threads()
+    out = []
+    try:
+        for t in (1, 4):
+            O.set_threads(t)
+            H = O.Hierarchy(s, **kw)
+            x, rep = H.solve(s.b, tol=1e-10, cycle=1)
+            out.append((H, x, rep["iters"]))
+    finally:
+        O.set_threads(before)
+    (H1, x1, i1), (H4, x4, i4) = out
+    assert i1 == i4 and np.array_equal(x1, x4)
+    for L1, L4 in zip(H1.levels, H4.levels):
+        for a, b in ((L1.A, L4.A), (L1.R, L4.R), (L1.P, L4.P)):
+            if a is not None:
+                assert all(np.array_equal(u, v) for u, v in zip(a, b))
