@@ -14,8 +14,8 @@ path measured the same way beside it. `value` is timed with CUDA events on the
 library's stream with the matrix and right-hand side already in HBM; `e2e` goes
 through the same C ABI with pinned host buffers, copies included.
 
---impl reference times the CPU oracle (plain single-threaded FP64 C) on a bounded
-sample of the same workload family (the 64 x 64 mesh of the same discretisation).
+--impl reference times the CPU oracle (plain FP64 C, OpenMP over independent rows) on
+the host's cores, on a bounded sample of the same workload (the 3D workload at 96^3).
 """
 from __future__ import annotations
 
@@ -44,8 +44,11 @@ _DESC = {
     "fd3d_192": "3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1; "
                 "FP32 cycle in FP64 stationary refinement, tol 1e-8",
 }
-_SAMPLE_SCALE = {"dg_p2_256": 64, "batched_512": 8, "fd3d_192": 40}
-WORKLOADS = {k: dict(_W.BENCH_OPTIONS[k], desc=_DESC[k], sample_scale=_SAMPLE_SCALE[k]) for k in _DESC}
+# CPU oracle: one-thread sample scale (about 10 s), and the reference arm's sample (None: full size)
+_SAMPLE_SCALE = {"dg_p2_256": 128, "batched_512": 8, "fd3d_192": 64}
+_REFERENCE_SCALE = {"dg_p2_256": None, "batched_512": 16, "fd3d_192": 96}
+WORKLOADS = {k: dict(_W.BENCH_OPTIONS[k], desc=_DESC[k], sample_scale=_SAMPLE_SCALE[k],
+                     reference_scale=_REFERENCE_SCALE[k]) for k in _DESC}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -159,66 +162,74 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------------
-def oracle_sample(workload, budget_s=12.0, min_reps=1, max_reps=100):
+def oracle_opts(opts):
+    """The oracle's option names for a set of lair.Hierarchy keyword arguments (mixed precision)."""
+    from oracle import oracle as O
+    fields = {f for f, _ in O.Opts._fields_}
+    out = {k: v for k, v in opts.items() if k in fields}
+    out["prec"] = 1
+    return out
+
+
+def oracle_run(workload, opts, scale=None, threads=None, budget_s=0.0, max_reps=100):
+    """Set-up + solve by the CPU oracle (mixed mode) on the workload at `scale` (None: full size), on
+    `threads` host threads (None: every core); repeated until `budget_s` seconds are spent (at least once).
+    Returns the rate, the iterations and the last solution."""
     import numpy as np
     import workloads as W
     from oracle import oracle as O
     wl = WORKLOADS[workload]
-    s = W.config(workload, scale=wl["sample_scale"])
+    s = W.config(workload, scale=scale)
     offs = None
     if wl.get("batched"):
         s, offs = W.block_diagonal(s)
-    kw = dict(wl["opts"])
-    okw = dict(distance=kw["distance"], prec=1)
-    if "cf_mode" in kw:
-        okw["cf_mode"] = kw["cf_mode"]
-    if "interp" in kw:
-        okw["interp"] = kw["interp"]
-    if "strength_abs" in kw:
-        okw["strength_abs"] = kw["strength_abs"]
-    if "block_size" in kw:
-        okw["block_size"] = kw["block_size"]
+    okw = oracle_opts(opts)
     O.build()
-    reps, total, iters = 0, 0.0, 0
-    while reps < min_reps or (total < budget_s and reps < max_reps):
-        t0 = time.perf_counter()
-        if offs is None:
-            H = O.Hierarchy(s, **okw)
-            x, rep = H.solve(s.b, tol=wl["tol"], cycle=0 if wl.get("cycle") == "stationary" else 1)
-        else:
-            H = O.Hierarchy(s, seg=offs, **okw)
-            x, rep = H.solve_batched(s.b, tol=wl["tol"], cycle=1)
-        total += time.perf_counter() - t0
-        assert rep["status"] == 0, rep
-        iters = rep["iters"] if offs is None else int(np.max(rep["iters"]))
-        H.close()
-        reps += 1
-    return dict(n=s.n, reps=reps, seconds=total, value=s.n * reps / total, iters=iters,
-                sample=f"{workload} family at mesh side {wl['sample_scale']} (n={s.n}), set-up + solve, mixed mode, "
-                       f"{reps} repetitions, {total:.1f} s")
+    used = O.set_threads(threads)
+    reps, total, iters, x = 0, 0.0, 0, None
+    try:
+        while reps < 1 or (total < budget_s and reps < max_reps):
+            t0 = time.perf_counter()
+            if offs is None:
+                H = O.Hierarchy(s, **okw)
+                x, rep = H.solve(s.b, tol=wl["tol"], cycle=0 if wl.get("cycle") == "stationary" else 1)
+            else:
+                H = O.Hierarchy(s, seg=offs, **okw)
+                x, rep = H.solve_batched(s.b, tol=wl["tol"], cycle=1)
+            total += time.perf_counter() - t0
+            assert rep["status"] == 0, rep
+            iters = rep["iters"] if offs is None else int(np.max(rep["iters"]))
+            H.close()
+            reps += 1
+    finally:
+        O.set_threads(None)
+    where = "full size" if scale is None else f"mesh side {scale}"
+    return dict(n=s.n, reps=reps, seconds=total, value=s.n * reps / total, iters=iters, threads=used, x=x,
+                sample=f"{workload} at {where} (n={s.n}), set-up + solve, mixed mode, {used} host thread(s), "
+                       f"{reps} run(s), {total:.1f} s")
 
 
 def reference_arm(args, dist):
+    """The oracle as it stands on the host's cores, on a bounded sample of the workload (the 3D workload at
+    96^3, the DG workload at full size, 16 batched systems), one set-up + solve per step."""
     if dist.rank != 0:
         return
     wl = WORKLOADS[args.workload]
+    scale = wl["reference_scale"]
     for _ in range(args.warmup):
-        oracle_sample(args.workload, budget_s=0.0)
+        oracle_run(args.workload, wl["opts"], scale=scale)
     times = []
-    n = None
     for _ in range(args.steps):
-        r = oracle_sample(args.workload, budget_s=0.0)
+        r = oracle_run(args.workload, wl["opts"], scale=scale)
         times.append(r["seconds"])
-        n = r["n"]
-        sample = r["sample"]
     t = sum(times) / len(times)
-    v = n / t
+    v = r["n"] / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "unknowns/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 local solves and cycle)", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "reference_sample": sample},
-            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
-                             "sample": sample.rsplit(",", 2)[0]},
+            "config": {"workload": args.workload, "desc": wl["desc"], "reference_sample": r["sample"]},
+            "cpu_baseline": {"value": v, "unit": "unknowns/s", "cores": r["threads"], "nproc": os.cpu_count(),
+                             "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": v, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -472,10 +483,21 @@ def main():
                               for k, v in timers.items() if not k.startswith("setup_")}}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
+    # all host cores on the full workload where it runs in about half a minute (not the batched one: the oracle
+    # solves its systems one after another over the whole block-diagonal cycle), the error of the GPU's mixed
+    # solution against the oracle's there; one thread on a smaller sample of the same family
     cpu = None
+    err_vs_oracle = None
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
-        r = oracle_sample(args.workload, budget_s=12.0)
-        cpu = {"value": r["value"], "unit": "unknowns/s", "cores": 1, "kind": "oracle", "sample": r["sample"]}
+        full = None if wl.get("batched") else oracle_run(args.workload, wl["opts"])
+        one = oracle_run(args.workload, wl["opts"], scale=wl["sample_scale"], threads=1, budget_s=10.0)
+        main_r = full or oracle_run(args.workload, wl["opts"], scale=wl["reference_scale"])
+        cpu = {"value": main_r["value"], "unit": "unknowns/s", "cores": main_r["threads"], "nproc": os.cpu_count(),
+               "kind": "oracle", "sample": main_r["sample"], "iters": main_r["iters"],
+               "one_thread": {"value": one["value"], "unit": "unknowns/s", "cores": 1, "sample": one["sample"]}}
+        if full is not None:
+            xo = full["x"]
+            err_vs_oracle = float(np.linalg.norm(x_mixed - xo) / np.linalg.norm(xo))
 
     value = dist.world * n / (ms_mixed / 1e3)
     line = {
@@ -491,6 +513,7 @@ def main():
                  "iters": it64, "final_rel": max(rel64)},
         "mixed_over_fp64": ms64 / ms_mixed,
         "err_vs_fp64": err_vs_fp64,
+        "err_vs_oracle": err_vs_oracle,
         "cold_setup_ms": su_cold[0] if su_cold else None,
         "hierarchy": hier,
         "setup_phases_ms": {k[len("setup_"):]: v[1] / args.steps for k, v in timers.items() if k.startswith("setup_")},
