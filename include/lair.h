@@ -93,7 +93,8 @@ typedef struct {
 
 typedef struct {
     int cf_mode;              /* lair_cf_mode (default AUTO) */
-    const int8_t *cf_user;    /* LAIR_CF_USER: host array of n entries, 1 = C, 0 = F */
+    const int8_t *cf_user;    /* LAIR_CF_USER: host array of n entries, nonzero = C, 0 = F; with nodal = k
+                                 the k entries of every node must agree (else LAIR_ERR_INVALID_ARG) */
     int distance;             /* restriction/interpolation neighbourhood distance, 1 to 4 (Sec. 3.1, Sec. 4:
                                  each step adds the strong F neighbours of the previous set) */
     double theta;             /* strength threshold for the neighbourhoods (Sec. 4, N_i) */
@@ -127,6 +128,11 @@ typedef struct {
                                  choices are cached for the process by view shape, so later hierarchies of
                                  similar levels reuse them. Results do not depend on it. 0: the fixed default
                                  schedule everywhere. */
+    int wait_polls;           /* bound on the polls of every device-side wait (the grid barriers of the
+                                 cooperative PMIS kernel, levels above 8192 points); 0 (default): 4,194,304
+                                 polls of at least 64 ns. A wait that runs out makes the call return
+                                 LAIR_ERR_DEVICE_TIMEOUT; every block of the kernel returns and the CUDA
+                                 context stays usable. Small values exist to test that path. */
 } lair_options;
 
 typedef struct {

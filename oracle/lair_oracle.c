@@ -1751,6 +1751,11 @@ ohier *ora_setup(int64_t n, const int64_t *rp, const int32_t *col, const double 
         *status = ORA_ERR_ARG;
         return H;
     }
+    if (opts->nodal > 1 && opts->cf_mode == 2 && opts->cf_user) {
+        /* a node's unknowns share one label: its k entries of the user splitting must agree */
+        for (int64_t i = 0; i < n; ++i)
+            if ((opts->cf_user[i] != 0) != (opts->cf_user[i - i % opts->nodal] != 0)) { *status = ORA_ERR_ARG; return H; }
+    }
     if (opts->block_size > 1) nnz = ora_block_scale_nnz(n, rp, col, opts->block_size);
     if (csr_alloc(A0, n, n, nnz)) { *status = ORA_ERR_OOM; return H; }
     if (opts->block_size > 1) {

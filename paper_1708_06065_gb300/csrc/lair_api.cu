@@ -712,11 +712,20 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         int2 *bd;
         TRY(t.get(&bd, blocks.size()));
         CU(cudaMemcpyAsync(bd, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice, h->s));
-        int *mx, maxin = 0;
-        TRY(new_counts(h, t, &mx, 1));
-        launch_rs_count(bd, (int)blocks.size(), Scf, mx, h->s);
-        TRY(read_ints(h, mx, 1, &maxin));   // also keeps the host block list alive until its copy is done
-        CU(launch_rs(n, bd, (int)blocks.size(), Bmax, maxin, Scf, STcf, cf, h->status, h->s));
+        // in-block entries of S, largest in-block row lengths of S and ST: they size the bucket queue
+        int *mx, deg[3] = {0, 0, 0};
+        TRY(new_counts(h, t, &mx, 3));
+        launch_rs_degrees(bd, (int)blocks.size(), Scf, STcf, mx, h->s);
+        TRY(read_ints(h, mx, 3, deg));   // also keeps the host block list alive until its copy is done
+        int nb = 8;
+        while (nb < 2 * deg[2] + 1) nb *= 2;
+        const long long dl = 32 + (long long)deg[1] * (1 + deg[2]);
+        if (Bmax <= RSB_MAX_N && nb <= 256 && dl <= RSB_MAX_DIRTY &&
+            rsb_smem_bytes(Bmax, nb, (int)dl) <= (size_t)200 * 1024) {
+            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, Scf, STcf, cf, h->status, h->s));
+        } else {
+            CU(launch_rs(n, bd, (int)blocks.size(), Bmax, deg[0], Scf, STcf, cf, h->status, h->s));
+        }
     } else {
         double *w;
         int8_t *newc;
@@ -725,7 +734,7 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         TRY(t.get(&newc, (size_t)n));
         TRY(new_counts(h, t, &und, 4));
         launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, cf, h->s);
-        CU(launch_pmis_all(n, Scf, STcf, w, cf, newc, und, h->status, h->s));
+        CU(launch_pmis_all(n, Scf, STcf, w, cf, newc, und, h->status, o.wait_polls, h->s));
     }
     return LAIR_OK;
 }
@@ -2469,6 +2478,7 @@ static lair_status check_options(lair_handle *h, const lair_options *o) {
         return fail(h, LAIR_ERR_INVALID_ARG, "restriction %d", o->restriction);
     if (o->nodal < 0) return fail(h, LAIR_ERR_INVALID_ARG, "nodal %d", o->nodal);
     if (o->autotune < 0 || o->autotune > 1) return fail(h, LAIR_ERR_INVALID_ARG, "autotune %d", o->autotune);
+    if (o->wait_polls < 0) return fail(h, LAIR_ERR_INVALID_ARG, "wait_polls %d", o->wait_polls);
     if (o->nodal > NODAL_MAX) return fail(h, LAIR_ERR_UNSUPPORTED, "nodal <= %d", NODAL_MAX);
     if (o->nodal > 1 && o->block_size > 1)
         return fail(h, LAIR_ERR_INVALID_ARG, "nodal and block_size exclude each other");
@@ -2498,6 +2508,14 @@ lair_status lair_setup(const lair_csr *A, const lair_options *o, lair_handle **o
     if (h->o.block_size > 1 && A->n % h->o.block_size)
         return fail(h, LAIR_ERR_INVALID_ARG, "n is not a multiple of block_size");
     if (h->o.nodal > 1 && A->n % h->o.nodal) return fail(h, LAIR_ERR_INVALID_ARG, "n is not a multiple of nodal");
+    if (h->o.nodal > 1 && h->o.cf_mode == LAIR_CF_USER) {
+        // a node's unknowns share one label: every node's k entries must agree (as C or F)
+        const int k = h->o.nodal;
+        for (int64_t I = 0; I < A->n / k; ++I)
+            for (int u = 1; u < k; ++u)
+                if ((h->o.cf_user[I * k + u] != 0) != (h->o.cf_user[I * k] != 0))
+                    return fail(h, LAIR_ERR_INVALID_ARG, "cf_user: the %d entries of node %lld differ", k, (long long)I);
+    }
     h->s = (cudaStream_t)h->o.stream;
     if (!h->s) {
         // a blocking stream: ordered with the legacy default stream, and capturable into graphs

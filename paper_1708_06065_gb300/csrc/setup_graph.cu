@@ -249,12 +249,10 @@ __device__ __forceinline__ bool beats(double wi, int i, double wj, int j) {
 // would beat each other), so marking C and F in one pass is race-free. A decided point's
 // weight is set to -1, so the select pass reads one array per neighbour.
 // ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2 + r % 2] undecided count of round r
-// (zero on entry). Every barrier wait is bounded; a wait that gives up sets
-// LAIR_ERR_DEVICE_TIMEOUT and the block returns.
+// (zero on entry). Every barrier wait is bounded by `limit` polls; a wait that gives up sets
+// LAIR_ERR_DEVICE_TIMEOUT and the block returns (so do the others at their next barrier).
 // -------------------------------------------------------------------------------------
-constexpr long long GRID_SPIN_LIMIT = 1ll << 22;
-
-__device__ bool grid_barrier(int *ctl, int *status) {
+__device__ bool grid_barrier(int *ctl, int *status, long long limit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -269,7 +267,7 @@ __device__ bool grid_barrier(int *ctl, int *status) {
         } else {
             long long spins = 0;
             while (*gen == g) {
-                if (++spins > GRID_SPIN_LIMIT) {
+                if (++spins > limit) {
                     set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
                     ok = 0;
                     break;
@@ -352,7 +350,7 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_cluster(int n, Graph S, G
 
 __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Graph ST, double *w,
                                                    int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
-                                                   int *status) {
+                                                   int *status, long long limit) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (int round = 0; round <= n; ++round) {
@@ -369,7 +367,7 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Grap
         }
         local = __reduce_add_sync(0xffffffffu, local);
         if (lane_id() == 0 && local) atomicAdd(ctl + 2 + (round & 1), local);
-        if (!grid_barrier(ctl, status)) return;
+        if (!grid_barrier(ctl, status, limit)) return;
         const int und = *(volatile int *)(ctl + 2 + (round & 1));
         if (und == 0) return;
         if (t0 == 0) ctl[2 + ((round + 1) & 1)] = 0;   // nobody adds to it before the next barrier
@@ -385,7 +383,7 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Grap
                 }
             }
         }
-        if (!grid_barrier(ctl, status)) return;
+        if (!grid_barrier(ctl, status, limit)) return;
     }
 }
 
@@ -625,6 +623,225 @@ __global__ void __launch_bounds__(32) k_rs_count(const int2 *__restrict__ blocks
     if (threadIdx.x == 0) atomicMax(maxcnt, c);
 }
 
+// per block: the in-block entries of S (for staging), and the largest in-block row lengths of S and ST;
+// out[0..2] take the maxima over all blocks
+__global__ void __launch_bounds__(32) k_rs_degrees(const int2 *__restrict__ blocks, Graph S, Graph ST,
+                                                   int *__restrict__ out) {
+    const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
+    int c = 0, ms = 0, mt = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += 32) {
+        int ds = 0, dt = 0;
+        for (int p = S.rp[i]; p < S.rp[i + 1]; ++p) ds += (S.col[p] >= b0 && S.col[p] < b1);
+        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) dt += (ST.col[p] >= b0 && ST.col[p] < b1);
+        c += ds;
+        ms = max(ms, ds);
+        mt = max(mt, dt);
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    ms = __reduce_max_sync(0xffffffffu, ms);
+    mt = __reduce_max_sync(0xffffffffu, mt);
+    if (threadIdx.x == 0) {
+        atomicMax(&out[0], c);
+        atomicMax(&out[1], ms);
+        atomicMax(&out[2], mt);
+    }
+}
+
+// -------------------------------------------------------------------------------------
+// The same first pass with a bucket queue, for blocks of at most RSB_MAX_N points whose lambda
+// stays below nb buckets (lambda_k <= 2 |ST_k n block|: it starts at the in-block count and each
+// dependant adds one when it becomes F). Bucket b is a bitmap over the block of the undecided
+// points with lambda = b, so the point to take (largest lambda, then smallest index) is the lowest
+// set bit of the highest non-empty bucket. The graphs are read through the cache; shared memory
+// holds only the buckets and per-point bytes, so many blocks run on one SM at once. A step:
+//   1. find i, which becomes C;
+//   2. its undecided in-block dependants (ST_i) become F and leave their buckets;
+//   3. lambda_k += 1 for undecided in-block k in S_j of every new F point j and lambda_k -= 1 for
+//      undecided in-block k in S_i (byte atomics on lambda; each changed k is listed once);
+//   4. every listed k moves from the bucket of its previous lambda to that of its new one.
+// The sequence of points taken is the one of the tree version above (and of the oracle).
+// -------------------------------------------------------------------------------------
+struct RsbLayout {
+    int W;                                // bitmap words per bucket (a multiple of 128)
+    size_t bm, cnt, dflag, dlist, lam, bkt, cf, total;   // byte offsets in dynamic shared memory
+};
+
+__host__ __device__ inline size_t rsb_round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline RsbLayout rsb_layout(int n, int nb, int dl) {
+    RsbLayout L;
+    L.W = (((n + 31) / 32) + 127) / 128 * 128;
+    size_t o = 0;
+    L.bm = o;    o += rsb_round16((size_t)nb * L.W * sizeof(unsigned));
+    L.cnt = o;   o += rsb_round16((size_t)nb * sizeof(int));
+    L.dflag = o; o += rsb_round16((size_t)L.W * sizeof(unsigned));
+    L.dlist = o; o += rsb_round16((size_t)dl * sizeof(int));
+    L.lam = o;   o += rsb_round16((size_t)n);          // one byte per point, updated by 32-bit atomics
+    L.bkt = o;   o += rsb_round16((size_t)n);
+    L.cf = o;    o += rsb_round16((size_t)n);
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ blocks, Graph S, Graph ST, int nb, int dl,
+                                                  int8_t *__restrict__ cf_out, int *status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int ndirty;
+    const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
+    const int n = b1 - b0;
+    const RsbLayout Lo = rsb_layout(n, nb, dl);
+    const int W = Lo.W;
+    unsigned *bm = reinterpret_cast<unsigned *>(smem + Lo.bm);
+    int *cnt = reinterpret_cast<int *>(smem + Lo.cnt);
+    unsigned *dflag = reinterpret_cast<unsigned *>(smem + Lo.dflag);
+    int *dlist = reinterpret_cast<int *>(smem + Lo.dlist);
+    unsigned *lamw = reinterpret_cast<unsigned *>(smem + Lo.lam);     // byte k of the block: lambda_k
+    uint8_t *bkt = smem + Lo.bkt;                                     // the bucket that holds k
+    int8_t *cf = reinterpret_cast<int8_t *>(smem + Lo.cf);
+    const unsigned lane = threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+
+    for (int e = lane; e < nb * W; e += 32) bm[e] = 0u;
+    for (int e = lane; e < nb; e += 32) cnt[e] = 0;
+    for (int e = lane; e < W; e += 32) dflag[e] = 0u;
+    for (int e = lane; e < (n + 3) / 4; e += 32) lamw[e] = 0u;
+    if (lane == 0) ndirty = 0;
+    __syncwarp();
+    int top = 0;
+    for (int li = lane; li < n; li += 32) {
+        const int i = b0 + li;
+        int lam = 0;
+        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) lam += (ST.col[p] >= b0 && ST.col[p] < b1);
+        const bool iso = (S.rp[i + 1] == S.rp[i]) && (ST.rp[i + 1] == ST.rp[i]);
+        cf[li] = iso ? CF_F : CF_U;
+        bkt[li] = 0;
+        if (iso) continue;
+        if (lam >= nb) {                       // the host sized nb above every reachable lambda
+            set_status(status, LAIR_ERR_ARENA_OVERFLOW);
+            lam = nb - 1;
+        }
+        atomicAdd(&lamw[li >> 2], (unsigned)lam << (8 * (li & 3)));
+        bkt[li] = (uint8_t)lam;
+        atomicOr(&bm[lam * W + (li >> 5)], 1u << (li & 31));
+        atomicAdd(&cnt[lam], 1);
+        top = max(top, lam);
+    }
+    top = __reduce_max_sync(FULL, top);
+    __syncwarp();
+    const int per = W / 32;                    // bitmap words scanned by each lane (4 or more, contiguous)
+    for (int step = 0; step <= n; ++step) {
+        // 1. the highest non-empty bucket at or below top, then its lowest set bit
+        int b = -1;
+        for (int t0 = top; t0 >= 0; t0 -= 32) {
+            const int c = t0 - (int)lane;
+            const unsigned m = __ballot_sync(FULL, c >= 0 && cnt[c] > 0);
+            if (m) {
+                b = t0 - (__ffs(m) - 1);
+                break;
+            }
+        }
+        if (b < 0) break;
+        top = b;
+        const unsigned *row = bm + (size_t)b * W + (size_t)lane * per;
+        int fw = -1;
+        unsigned fv = 0u;
+        for (int r = 0; r < per && fw < 0; r += 4) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(row + r);
+            if (q.x) { fw = r; fv = q.x; }
+            else if (q.y) { fw = r + 1; fv = q.y; }
+            else if (q.z) { fw = r + 2; fv = q.z; }
+            else if (q.w) { fw = r + 3; fv = q.w; }
+        }
+        const unsigned fm = __ballot_sync(FULL, fw >= 0);
+        if (fm == 0u) {                        // a count without its bit: cannot happen
+            if (lane == 0) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+            break;
+        }
+        const int src = __ffs(fm) - 1;
+        fw = __shfl_sync(FULL, fw, src) + src * per;
+        fv = __shfl_sync(FULL, fv, src);
+        const int li = 32 * fw + __ffs(fv) - 1;
+        const int i = b0 + li;
+        // 2. i becomes C; its undecided in-block dependants become F (new in this step)
+        if (lane == 0) {
+            cf[li] = CF_C;
+            atomicAnd(&bm[b * W + (li >> 5)], ~(1u << (li & 31)));
+            atomicSub(&cnt[b], 1);
+        }
+        const int sb = ST.rp[i], se = ST.rp[i + 1];
+        for (int p = sb + (int)lane; p < se; p += 32) {
+            const int j = ST.col[p] - b0;
+            if (j >= 0 && j < n && cf[j] == CF_U) {
+                cf[j] = CF_NEWF;
+                const int bj = bkt[j];
+                atomicAnd(&bm[bj * W + (j >> 5)], ~(1u << (j & 31)));
+                atomicSub(&cnt[bj], 1);
+            }
+        }
+        __syncwarp();
+        // 3. lambda updates; the first touch of a point lists it
+        auto touch = [&](int k, bool inc) {
+            const unsigned sh = 8u * (unsigned)(k & 3);
+            atomicAdd(&lamw[k >> 2], inc ? (1u << sh) : (0u - (1u << sh)));
+            const unsigned bit = 1u << (k & 31);
+            if (!(atomicOr(&dflag[k >> 5], bit) & bit)) {
+                const int pos = atomicAdd(&ndirty, 1);
+                if (pos < dl) dlist[pos] = k;
+                else set_status(status, LAIR_ERR_ARENA_OVERFLOW);
+            }
+        };
+        for (int p = sb + (int)lane; p < se; p += 32) {
+            const int j = ST.col[p] - b0;
+            if (j < 0 || j >= n || cf[j] != CF_NEWF) continue;
+            for (int q = S.rp[b0 + j]; q < S.rp[b0 + j + 1]; ++q) {
+                const int k = S.col[q] - b0;
+                if (k >= 0 && k < n && cf[k] == CF_U) touch(k, true);
+            }
+        }
+        for (int q = S.rp[i] + (int)lane; q < S.rp[i + 1]; q += 32) {
+            const int k = S.col[q] - b0;
+            if (k >= 0 && k < n && cf[k] == CF_U) touch(k, false);
+        }
+        __syncwarp();
+        // 4. listed points change bucket
+        const int nd = min(ndirty, dl);
+        int hi = 0;
+        for (int d = lane; d < nd; d += 32) {
+            const int k = dlist[d];
+            const unsigned bit = 1u << (k & 31);
+            atomicAnd(&dflag[k >> 5], ~bit);
+            const int lam = (int)((lamw[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            const int ob = bkt[k];
+            if (lam == ob) continue;
+            if (lam >= nb) {
+                set_status(status, LAIR_ERR_ARENA_OVERFLOW);
+                continue;
+            }
+            atomicAnd(&bm[ob * W + (k >> 5)], ~bit);
+            atomicOr(&bm[lam * W + (k >> 5)], bit);
+            atomicSub(&cnt[ob], 1);
+            atomicAdd(&cnt[lam], 1);
+            bkt[k] = (uint8_t)lam;
+            hi = max(hi, lam);
+        }
+        top = max(top, (int)__reduce_max_sync(FULL, (unsigned)hi));
+        __syncwarp();
+        if (lane == 0) ndirty = 0;
+        for (int p = sb + (int)lane; p < se; p += 32) {
+            const int j = ST.col[p] - b0;
+            if (j >= 0 && j < n && cf[j] == CF_NEWF) cf[j] = CF_F;
+        }
+        __syncwarp();
+    }
+    for (int li = lane; li < n; li += 32) {
+        const int8_t c = cf[li];
+        if (c != CF_C && c != CF_F) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+        cf_out[b0 + li] = c;
+    }
+}
+
+size_t rsb_smem_bytes(int n, int nb, int dl) { return rsb_layout(n, nb, dl).total; }
+
 // shared memory of one block: the fixed part (keys, tree, splitting, row offsets) plus room for
 // both staged in-block graphs of the fullest block, up to RS_SMEM_MAX bytes in all (blocks that
 // do not fit then read their graphs from global memory)
@@ -850,7 +1067,8 @@ void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *
 
 // ctl: 4 ints, zero
 cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
-                            int *status, cudaStream_t s) {
+                            int *status, int wait_polls, cudaStream_t s) {
+    long long limit = wait_polls > 0 ? (long long)wait_polls : GRID_WAIT_POLLS;
     if (n <= PMIS_CLUSTER * PMIS_THREADS) {
         const int c = n > 0 ? (n + PMIS_THREADS - 1) / PMIS_THREADS : 1;
         cudaLaunchConfig_t cfg = {};
@@ -879,7 +1097,8 @@ cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, i
     int grid = sms;
     const int need = (n + PMIS_THREADS - 1) / PMIS_THREADS;
     if (grid > need) grid = need > 0 ? need : 1;
-    void *args[] = {(void *)&n, (void *)&S, (void *)&ST, (void *)&w, (void *)&cf, (void *)&newc, (void *)&ctl, (void *)&status};
+    void *args[] = {(void *)&n,   (void *)&S,    (void *)&ST,     (void *)&w,    (void *)&cf,
+                    (void *)&newc, (void *)&ctl, (void *)&status, (void *)&limit};
     e = cudaLaunchCooperativeKernel((const void *)k_pmis_coop, dim3(grid), dim3(PMIS_THREADS), args, 0, s);
     count_launch();
     return e;
@@ -890,6 +1109,21 @@ cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, i
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s) {
     k_rs_count<<<nblocks, 32, 0, s>>>(blocks, S, maxcnt);
     count_launch();
+}
+
+void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Graph &ST, int *out, cudaStream_t s) {
+    k_rs_degrees<<<nblocks, 32, 0, s>>>(blocks, S, ST, out);
+    count_launch();
+}
+
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
+                             const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
+    const size_t bytes = rsb_smem_bytes(Bmax, nb, dl);
+    cudaError_t e = cudaFuncSetAttribute(k_rs_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_rs_bucket<<<nblocks, 32, bytes, s>>>(blocks, S, ST, nb, dl, cf, status);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,

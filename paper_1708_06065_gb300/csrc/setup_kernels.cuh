@@ -26,9 +26,19 @@ void launch_transpose_scatter(int nr, const int *rp, const int *col, const doubl
                               int *tcol, double *tval, cudaStream_t s);
 void launch_sort_rows(int nr, const int *rp, int *col, double *val, int *lists, cudaStream_t s);
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
+// every grid-barrier wait of the cooperative PMIS kernel gives up after wait_polls polls (0: GRID_WAIT_POLLS)
+constexpr long long GRID_WAIT_POLLS = 1ll << 22;
 cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
-                            int *status, cudaStream_t s);
+                            int *status, int wait_polls, cudaStream_t s);
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s);
+// bucket-queue first pass: blocks of at most RSB_MAX_N points, lambda below nb <= 256 buckets, at most dl points
+// whose lambda changes in one step
+constexpr int RSB_MAX_N = 8192;
+constexpr int RSB_MAX_DIRTY = 8192;
+void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Graph &ST, int *out, cudaStream_t s);
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
+                             const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
+size_t rsb_smem_bytes(int n, int nb, int dl);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
                       int8_t *cf, int *status, cudaStream_t s);
 size_t rs_smem_bytes(int n, int max_inblock);

@@ -46,7 +46,7 @@ class lair_options(C.Structure):
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("block_size", C.c_int),
                 ("rs_block", C.c_int), ("pmis_seed", C.c_uint64), ("fgmres_restart", C.c_int),
                 ("stream", C.c_void_p), ("timing", C.c_int), ("restriction", C.c_int),
-                ("nodal", C.c_int), ("autotune", C.c_int)]
+                ("nodal", C.c_int), ("autotune", C.c_int), ("wait_polls", C.c_int)]
 
 
 class lair_report(C.Structure):

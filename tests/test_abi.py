@@ -64,6 +64,7 @@ def test_setup_rejects_bad_arguments_without_a_gpu():
     (dict(nodal=2, restriction=1), 13, b"lAIR"),
     (dict(nodal=3), 1, b"multiple of nodal"),      # n = 4 is not a multiple of 3
     (dict(autotune=2), 1, b"autotune"),
+    (dict(wait_polls=-1), 1, b"wait_polls"),
 ])
 def test_setup_rejects_option_combinations_without_a_gpu(kw, code, word):
     """Option checks run before any device call: unknown values, nodal with block scaling or the Neumann
@@ -95,3 +96,26 @@ def test_refresh_rejects_a_handle_without_a_hierarchy():
     assert lair.lib.lair_refresh(h, val) == 1
     assert b"no hierarchy" in lair.lib.lair_last_error(h)
     lair.lib.lair_free(h)
+
+
+def test_nodal_user_splitting_must_agree_within_nodes():
+    """With nodal = k the k unknowns of a node share one label: a user splitting that gives a node's unknowns
+    different labels is rejected before any device call, by the library and by the oracle alike."""
+    import numpy as np
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    from oracle import oracle as O
+    import workloads as W
+    cfu = np.array([1, 1, 0, 0, 1, 0], np.int8)           # node 2 (unknowns 4, 5) disagrees
+    h = ctypes.c_void_p()
+    o = lair.options(nodal=2, cf_mode=lair.CF_USER)
+    o.cf_user = cfu.ctypes.data_as(ctypes.c_void_p).value
+    A = lair.lair_csr(6, 6, None, None, None, 0)
+    assert lair.lib.lair_setup(ctypes.byref(A), ctypes.byref(o), ctypes.byref(h)) == 1
+    assert b"node 2" in lair.lib.lair_last_error(h)
+    lair.lib.lair_free(h)
+    s = W.upwind_chain(6)
+    assert O.Hierarchy(s, cf_user=cfu, nodal=2).status == 1
+    cfu[5] = 1
+    assert O.Hierarchy(s, cf_user=cfu, nodal=2).status == 0

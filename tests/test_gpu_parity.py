@@ -339,3 +339,18 @@ def test_degenerate_systems(lair, kind):
     xr = np.linalg.solve(s.to_scipy().toarray(), s.b)
     assert rep.status == 0
     assert np.abs(x - xr).max() <= 1e-10 * max(1.0, np.abs(xr).max())
+
+
+def test_pmis_grid_barrier_wait_gives_up(lair):
+    """Every wait of the cooperative PMIS kernel is bounded. With a bound of one poll the first block at
+    a grid barrier gives up, every block returns, lair_setup reports LAIR_ERR_DEVICE_TIMEOUT, and the
+    context stays usable: the same set-up with the default bound then succeeds and solves."""
+    s = W.config("fd2d_64", scale=128)          # 16,384 points: above the thread-block-cluster PMIS size
+    with pytest.raises(lair.LairError) as e:
+        lair.Hierarchy.from_system(s, device=True, cf_mode=1, wait_polls=1)
+    assert e.value.status == 11
+    G = lair.Hierarchy.from_system(s, device=True, cf_mode=1)
+    H = O.Hierarchy(s, cf_mode=O.CF_PMIS)
+    compare_hierarchies(G, H, TOL64)
+    x, rep = G.solve(s.b.copy(), tol=1e-10)
+    assert rep.status == 0
