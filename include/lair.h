@@ -283,7 +283,10 @@ lair_status lair_kernel_timers(const lair_handle *h, lair_kernel_timer *out, int
  * of an earlier call leaks in, but all calls share the array: calls that may overlap on the
  * GPU (different streams, or different host threads) race and must be serialised by the
  * caller. The first call on a device looks up the array's device address; make that first
- * call before any stream capture. Returns LAIR_ERR_INVALID_ARG for NULL pointers or s < 1. */
+ * call before any stream capture. The address is kept for the life of the process: after
+ * cudaDeviceReset() of a device the entry point must not be used on that device again.
+ * Returns LAIR_ERR_INVALID_ARG for NULL pointers or s < 1, and LAIR_ERR_CUDA, without
+ * launching, if an earlier CUDA error is still pending on the calling thread. */
 lair_status lair_local_solve_noalloc(int64_t nsys, int32_t s, const double *M, const double *rhs, double *z,
                                      uint8_t *ls_flag, void *stream);
 

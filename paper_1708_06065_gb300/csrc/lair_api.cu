@@ -14,6 +14,7 @@
 #include <cstring>
 #include <algorithm>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <tuple>
 #include <string>
@@ -26,6 +27,24 @@ namespace lair {
 void plus_one(int n, const int *a, int *b, cudaStream_t s);
 void count_flags(int n, const uint8_t *f, int *out, cudaStream_t s);
 void normalize_cf(int n, int8_t *cf, cudaStream_t s);
+
+int device_sms() {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cache[MAXDEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        cudaGetLastError();
+        return 152;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        v = 152;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 static thread_local long long *g_launches = nullptr;
 void count_launch(int k) {
@@ -1436,8 +1455,9 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, int2> g_tune;
-const int2 kTuneCandidates[] = {{256, 152 * 16}, {256, 152 * 4}, {256, 152 * 8},  {256, 152 * 32},
-                                {128, 152 * 8},  {128, 152 * 16}, {128, 152 * 32}, {128, 152 * 64}};
+// (threads per block, grid cap in blocks per SM); the first is the default schedule
+const int2 kTuneCandidates[] = {{256, 16}, {256, 4}, {256, 8},  {256, 32},
+                                {128, 8},  {128, 16}, {128, 32}, {128, 64}};
 }  // namespace
 
 template <class T>
@@ -1485,8 +1505,10 @@ static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0
             cleared = true;
         }
         float best = 3.4e38f, base = 3.4e38f;
-        int2 pick = kTuneCandidates[0];
-        for (const int2 &cand : kTuneCandidates) {
+        const int sms = device_sms();
+        int2 pick = make_int2(kTuneCandidates[0].x, kTuneCandidates[0].y * sms);
+        for (const int2 &c : kTuneCandidates) {
+            const int2 cand = make_int2(c.x, c.y * sms);
             v.tb = cand.x;
             v.grid = cand.y;
             run(kind);   // warm
@@ -1500,13 +1522,13 @@ static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0
                 CU(cudaEventElapsedTime(&ms, e0, e1));
                 tmin = std::min(tmin, ms);
             }
-            if (&cand == kTuneCandidates) base = tmin;   // the default schedule
+            if (&c == kTuneCandidates) base = tmin;   // the default schedule
             if (tmin < best) {
                 best = tmin;
                 pick = cand;
             }
         }
-        if (!(best < 0.95f * base)) pick = kTuneCandidates[0];
+        if (!(best < 0.95f * base)) pick = make_int2(kTuneCandidates[0].x, kTuneCandidates[0].y * sms);
         v.tb = pick.x;
         v.grid = pick.y;
         std::lock_guard<std::mutex> g(g_tune_mu);

@@ -97,7 +97,10 @@ __device__ __forceinline__ void warp_bitonic(int (&key)[R], double (&val)[R], in
 // host-side launch helpers (defined in lair_api.cu)
 // -------------------------------------------------------------------------------------
 void count_launch(int k = 1);
-inline int grid_for(long long work, int block, int max_blocks = 152 * 32) {
+// streaming multiprocessors of the current device (read once per device; 152 on a GB300)
+int device_sms();
+inline int grid_for(long long work, int block, int max_blocks = 0) {
+    if (max_blocks <= 0) max_blocks = device_sms() * 32;
     long long g = (work + block - 1) / block;
     if (g < 1) g = 1;
     if (g > max_blocks) g = max_blocks;

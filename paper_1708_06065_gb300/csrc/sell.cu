@@ -237,7 +237,7 @@ void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s) {
     if (v.nrows <= 0) return;
     // every row is one thread's, so the schedule (block size, grid cap) never changes the result
     const int tb = v.tb > 0 ? v.tb : 256;
-    k_sell_spmv<T><<<grid_for(v.nrows, tb, v.grid > 0 ? v.grid : 152 * 16), tb, 0, s>>>(v, x, y);
+    k_sell_spmv<T><<<grid_for(v.nrows, tb, v.grid > 0 ? v.grid : device_sms() * 16), tb, 0, s>>>(v, x, y);
     count_launch();
 }
 
@@ -245,7 +245,7 @@ template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s) {
     if (v.nrows + ncopy <= 0) return;
     const int tb = v.tb > 0 ? v.tb : 256;
-    k_sell_sweep<T><<<grid_for((long long)v.nrows + ncopy, tb, v.grid > 0 ? v.grid : 152 * 16), tb, 0, s>>>(
+    k_sell_sweep<T><<<grid_for((long long)v.nrows + ncopy, tb, v.grid > 0 ? v.grid : device_sms() * 16), tb, 0, s>>>(
         v, copy, ncopy, b, x, xo);
     count_launch();
 }

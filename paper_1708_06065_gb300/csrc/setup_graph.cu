@@ -1055,8 +1055,8 @@ void launch_transpose_scatter(int nr, const int *rp, const int *col, const doubl
 void launch_sort_rows(int nr, const int *rp, int *col, double *val, int *lists, cudaStream_t s) {
     if (nr <= 0) return;
     k_sort_rows<<<grid_for(nr, 128), 128, 0, s>>>(nr, rp, col, val, lists);
-    k_sort_rows_warp<<<152 * 8, 256, 0, s>>>(nr, rp, col, val, lists);
-    k_sort_rows_cta<<<152 * 2, SORT_CTA_THREADS, 0, s>>>(nr, rp, col, val, lists);
+    k_sort_rows_warp<<<device_sms() * 8, 256, 0, s>>>(nr, rp, col, val, lists);
+    k_sort_rows_cta<<<device_sms() * 2, SORT_CTA_THREADS, 0, s>>>(nr, rp, col, val, lists);
     count_launch(3);
 }
 

@@ -13,7 +13,7 @@ struct SellView {
     void *val = nullptr;        // float or double
     int *row = nullptr;         // view row -> matrix row
     void *dinv = nullptr;       // Jacobi diagonal per view row (sweep views), same type as val
-    int tb = 0, grid = 0;       // launch schedule picked by the autotuner (0: 256 threads, grid capped at 152 * 16)
+    int tb = 0, grid = 0;       // launch schedule picked by the autotuner (0: 256 threads, grid capped at 16 blocks per SM)
 };
 
 // ---- setup_graph.cu -------------------------------------------------------------------

@@ -549,7 +549,7 @@ static void local_solves_t(const LocalArgs &a, int nc, const int *lists, const i
     if (counts_host[1] > 0) {
         const size_t bytes = 4 * sizeof(T) * (2 * 32 * 32 + 3 * 32);
         cudaFuncSetAttribute(k_local_warp<T, SHARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        k_local_warp<T, SHARED><<<grid_for(counts_host[1], 4, 152 * 8), 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
+        k_local_warp<T, SHARED><<<grid_for(counts_host[1], 4, device_sms() * 8), 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
         count_launch();
     }
     if (counts_host[2] > 0) {
@@ -944,6 +944,9 @@ extern "C" lair_status lair_local_solve_noalloc(int64_t nsys, int32_t s, const d
         }
         scratch = g_noalloc_ptr[dev];
     }
+    // an error left pending by earlier CUDA calls of this thread is reported as it is (not cleared), so
+    // that a failure after the launch below belongs to this launch
+    if (cudaPeekAtLastError() != cudaSuccess) return LAIR_ERR_CUDA;
     const int grid = nsys < NOALLOC_SLOTS ? (int)nsys : NOALLOC_SLOTS;
     k_local_cta_dense<<<grid, 256, 0, (cudaStream_t)stream>>>((long long)nsys, s, M, rhs, z, ls_flag, scratch);
     return cudaGetLastError() == cudaSuccess ? LAIR_OK : LAIR_ERR_CUDA;

@@ -303,7 +303,7 @@ __global__ void k_block_apply_t(int n, int k, const T *__restrict__ inv, const T
 template <class T>
 void block_apply_t(int n, int k, const T *inv, const T *b, T *out, cudaStream_t s) {
     if (n <= 0) return;
-    k_block_apply_t<T><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, k, inv, b, out);
+    k_block_apply_t<T><<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, k, inv, b, out);
     count_launch();
 }
 

@@ -577,7 +577,7 @@ template <int CAP, int WARPS, bool FUSE>
 static void launch_spgemm_bin(const SpgemmArgs &g, const int *list, const int *count_dev, int count, cudaStream_t s) {
     const size_t bytes = (size_t)WARPS * spgemm_warp_bytes<CAP>();
     cudaFuncSetAttribute(k_spgemm_warp<CAP, WARPS, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    int grid = grid_for(count, WARPS, 152 * 16);
+    int grid = grid_for(count, WARPS, device_sms() * 16);
     k_spgemm_warp<CAP, WARPS, FUSE><<<grid, 32 * WARPS, bytes, s>>>(g, list, count_dev);
     count_launch();
 }
@@ -607,12 +607,12 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
         count_launch();
     }
     if (counts_host[SPGEMM_BIN_MERGE] > 0) {
-        k_spgemm_merge<SPGEMM_MERGE_K><<<grid_for(counts_host[SPGEMM_BIN_MERGE], 256, 152 * 16), 256, 0, s>>>(
+        k_spgemm_merge<SPGEMM_MERGE_K><<<grid_for(counts_host[SPGEMM_BIN_MERGE], 256, device_sms() * 16), 256, 0, s>>>(
             g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE);
         count_launch();
     }
     if (counts_host[SPGEMM_BIN_MERGE2] > 0) {
-        k_spgemm_merge<SPGEMM_MERGE_K2><<<grid_for(counts_host[SPGEMM_BIN_MERGE2], 128, 152 * 32), 128, 0, s>>>(
+        k_spgemm_merge<SPGEMM_MERGE_K2><<<grid_for(counts_host[SPGEMM_BIN_MERGE2], 128, device_sms() * 32), 128, 0, s>>>(
             g, lists + SPGEMM_BIN_MERGE2 * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE2);
         count_launch();
     }

@@ -82,7 +82,7 @@ template <class T>
 void spmv(const DCsr &A, const T *x, T *y, cudaStream_t s) {
     if (A.nr == 0) return;
     int G = pick_group<T>(A);
-    int grid = grid_for((long long)A.nr * G, 256, 152 * 16);
+    int grid = grid_for((long long)A.nr * G, 256, device_sms() * 16);
     const T *v = vals_of<T>(A);
     switch (G) {
         case 1: k_spmv<1, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, x, y); break;
@@ -99,7 +99,7 @@ template <class T>
 void sweep(const DCsr &A, const int8_t *cf, int target, const T *dinv, const T *b, const T *x, T *xo, cudaStream_t s) {
     if (A.nr == 0) return;
     int G = pick_group<T>(A);
-    int grid = grid_for((long long)A.nr * G, 256, 152 * 16);
+    int grid = grid_for((long long)A.nr * G, 256, device_sms() * 16);
     const T *v = vals_of<T>(A);
     switch (G) {
         case 1: k_sweep<1, T><<<grid, 256, 0, s>>>(A.nr, A.rp, A.col, v, cf, target, dinv, b, x, xo); break;
@@ -276,7 +276,7 @@ __global__ void k_sub_combo(int n, int m, const double *__restrict__ X, long lon
 }
 
 void sub_combo(int n, int m, const double *X, long long ldx, const double *h, double *w, cudaStream_t s) {
-    k_sub_combo<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, m, X, ldx, h, w);
+    k_sub_combo<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, m, X, ldx, h, w);
     count_launch();
 }
 
@@ -291,7 +291,7 @@ __global__ void k_add_combo(int n, int m, const double *__restrict__ Z, long lon
 }
 
 void add_combo(int n, int m, const double *Z, long long ldz, const double *y, double *x, cudaStream_t s) {
-    k_add_combo<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, m, Z, ldz, y, x);
+    k_add_combo<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, m, Z, ldz, y, x);
     count_launch();
 }
 
@@ -379,7 +379,7 @@ __global__ void k_scale_by_norm(int n, const double *__restrict__ v, const doubl
 }
 
 void scale_by_norm(int n, const double *v, const double *nrm2, double *out, cudaStream_t s) {
-    k_scale_by_norm<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, v, nrm2, out);
+    k_scale_by_norm<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, v, nrm2, out);
     count_launch();
 }
 
@@ -401,10 +401,10 @@ __global__ void k_axpy_d(int n, const double *__restrict__ e, double *__restrict
         x[i] += e[i];
 }
 
-void d2f(int n, const double *a, float *b, cudaStream_t s) { k_d2f<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, a, b); count_launch(); }
-void f2d(int n, const float *a, double *b, cudaStream_t s) { k_f2d<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, a, b); count_launch(); }
-void axpy_f(int n, const float *e, double *x, cudaStream_t s) { k_axpy_f<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, e, x); count_launch(); }
-void axpy_d(int n, const double *e, double *x, cudaStream_t s) { k_axpy_d<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, e, x); count_launch(); }
+void d2f(int n, const double *a, float *b, cudaStream_t s) { k_d2f<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, a, b); count_launch(); }
+void f2d(int n, const float *a, double *b, cudaStream_t s) { k_f2d<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, a, b); count_launch(); }
+void axpy_f(int n, const float *e, double *x, cudaStream_t s) { k_axpy_f<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, e, x); count_launch(); }
+void axpy_d(int n, const double *e, double *x, cudaStream_t s) { k_axpy_d<<<grid_for(n, 256, device_sms() * 8), 256, 0, s>>>(n, e, x); count_launch(); }
 
 // adjoint gradient on the pattern of A: g[k] = -lambda_i x_j
 __global__ void k_grad_A(int n, const int *__restrict__ rp, const int *__restrict__ col, const double *__restrict__ lam,

@@ -30,8 +30,26 @@ def local_systems(s, R, cf):
     return out
 
 
-def test_local_solve_noalloc_matches_setup_rows():
+def noalloc_solve(lair, Ms, rhss):
+    """One call of the allocation-free entry point on device copies of the given systems."""
     import torch
+    nsys, size = len(Ms), len(rhss[0])
+    M = torch.from_numpy(np.stack(Ms)).cuda().contiguous()
+    b = torch.from_numpy(np.stack(rhss)).cuda().contiguous()
+    z = torch.full((nsys, size), np.nan, dtype=torch.float64, device="cuda")
+    flags = torch.full((nsys,), 7, dtype=torch.uint8, device="cuda")
+    st = lair.lib.lair_local_solve_noalloc(nsys, int(size), M.data_ptr(), b.data_ptr(), z.data_ptr(),
+                                           flags.data_ptr(), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    return z.cpu().numpy(), flags.cpu().numpy()
+
+
+@pytest.mark.parametrize("band", ["cta", "warp_and_thread"])
+def test_local_solve_noalloc_matches_setup_rows(band):
+    """Two calls in a row, each with every system of one size, against the rows of R that lair_setup built
+    through the existing entry point: the same routine, so the same bits. Sizes above 32 are solved by
+    CTA teams in the set-up, sizes up to 32 by warp or thread teams there."""
     import __graft_entry__ as g
     g.build()
     from paper_1708_06065_gb300 import lair
@@ -42,29 +60,45 @@ def test_local_solve_noalloc_matches_setup_rows():
     cf, _, ls_R, _ = G.export_cf(0)
     systems = local_systems(s, R, cf)
     sizes = np.array([len(nb) for _, nb, _, _ in systems])
-    # two calls in a row, with the two most frequent sizes above 32 (the CTA-team range)
-    big = [v for v in np.unique(sizes) if 32 < v <= 64]
-    big.sort(key=lambda v: -(sizes == v).sum())
-    assert len(big) >= 2
-    for size in big[:2]:
+    lo, hi = (32, 64) if band == "cta" else (0, 32)
+    picked = [v for v in np.unique(sizes) if lo < v <= hi]
+    picked.sort(key=lambda v: -(sizes == v).sum())
+    assert len(picked) >= 2
+    for size in picked[:2]:
         group = [t for t in systems if len(t[1]) == size]
-        M = torch.from_numpy(np.stack([t[2] for t in group])).cuda().contiguous()
-        b = torch.from_numpy(np.stack([t[3] for t in group])).cuda().contiguous()
-        z = torch.full((len(group), size), np.nan, dtype=torch.float64, device="cuda")
-        flags = torch.full((len(group),), 7, dtype=torch.uint8, device="cuda")
-        st = lair.lib.lair_local_solve_noalloc(len(group), int(size), M.data_ptr(), b.data_ptr(), z.data_ptr(),
-                                               flags.data_ptr(), None)
-        assert st == 0
-        torch.cuda.synchronize()
-        zh = z.cpu().numpy()
-        fh = flags.cpu().numpy()
+        zh, fh = noalloc_solve(lair, [t[2] for t in group], [t[3] for t in group])
         for k, (c, nb, _, _) in enumerate(group):
             row = slice(R[0][c], R[0][c + 1])
             cols, vals = R[1][row], R[2][row]
             ref = vals[np.isin(cols, nb)]
-            scale = np.abs(ref).max()
-            assert np.abs(zh[k] - ref).max() <= 1e-12 * scale, (size, c)
+            assert np.array_equal(zh[k], ref), (size, c, np.abs(zh[k] - ref).max())
             assert fh[k] == ls_R[c]
+
+
+def test_local_solve_noalloc_singular_systems_take_least_squares():
+    """Systems with a duplicated column are singular: the flag is set and z is the minimum-norm
+    least-squares solution (Sec. 3.1 footnote), compared with numpy's and with the oracle's."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_1708_06065_gb300 import lair
+    from oracle import oracle as O
+
+    rng = np.random.default_rng(3)
+    for size in (5, 40):
+        Ms, rhss = [], []
+        for _ in range(3):
+            M = rng.uniform(-1, 1, (size, size)) + size * np.eye(size)
+            M[:, size - 1] = M[:, 1]                         # a repeated column: rank size - 1
+            Ms.append(M)
+            rhss.append(rng.uniform(-1, 1, size))
+        zh, fh = noalloc_solve(lair, Ms, rhss)
+        for k in range(len(Ms)):
+            assert fh[k] == 1
+            ref = np.linalg.lstsq(Ms[k], rhss[k], rcond=None)[0]
+            assert np.abs(zh[k] - ref).max() <= 1e-10 * np.abs(ref).max()
+            zo, ls = O.local_solve(Ms[k], rhss[k])
+            assert ls
+            assert np.abs(zh[k] - zo).max() <= 1e-12 * np.abs(zo).max()
 
 
 def test_local_solve_noalloc_rejects_oversized_and_bad_arguments():
