@@ -63,6 +63,8 @@ def parse():
                    help="override a solver option of the workload (lair.Hierarchy keyword, numeric value)")
     p.add_argument("--cycle", default=None, choices=["fgmres", "stationary"],
                    help="outer iteration (default: the workload's, FGMRES(30))")
+    p.add_argument("--timing", type=int, default=1, choices=[1, 2],
+                   help="2: also time every set-up phase per level (setup_phases_ms gets one entry per phase and level)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-refresh", action="store_true", help="skip the time-stepping (refresh + solve) measurement")
@@ -353,7 +355,7 @@ def main():
             ev0.record(stream)
             if offs is not None:
                 if host is None:
-                    G = lair.Hierarchy.batched(rp, col, val, offs, precision=precision, stream=stream, timing=1,
+                    G = lair.Hierarchy.batched(rp, col, val, offs, precision=precision, stream=stream, timing=args.timing,
                                                **wl["opts"])
                     evm.record(stream)
                     with torch.cuda.stream(stream):
@@ -362,14 +364,14 @@ def main():
                 else:
                     hrp, hcol, hval, hb, hx = host
                     hx.zero_()
-                    G = lair.Hierarchy.batched(hrp, hcol, hval, offs, precision=precision, stream=stream, timing=1,
+                    G = lair.Hierarchy.batched(hrp, hcol, hval, offs, precision=precision, stream=stream, timing=args.timing,
                                                **wl["opts"])
                     evm.record(stream)
                     _, sys_its, rls, st = G.solve_batched(hb, hx, tol=wl["tol"], cycle=cycle, max_iter=2000)
                 rep = lair.Report(st, int(sys_its.max()), float(rls.max()), 0.0, 0.0, 0, 0, 0, 0.0, 0.0)
                 last_batch[:] = [mine, sys_its, rls]
             elif host is None:
-                G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=1, **wl["opts"])
+                G = lair.Hierarchy(rp, col, val, precision=precision, stream=stream, timing=args.timing, **wl["opts"])
                 evm.record(stream)
                 with torch.cuda.stream(stream):
                     x.zero_()
@@ -377,7 +379,7 @@ def main():
             else:
                 hrp, hcol, hval, hb, hx = host
                 hx.zero_()
-                G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=1, **wl["opts"])
+                G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=args.timing, **wl["opts"])
                 evm.record(stream)
                 _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=cycle, max_iter=500)
             ev1.record(stream)

@@ -5,7 +5,6 @@
 // allocations. The V-cycle of each hierarchy is captured once into a CUDA graph and
 // replayed for every preconditioner application; the outer FP64 loop synchronises
 // once per iteration (to read a norm or one Hessenberg column).
-#include <cub/device/device_scan.cuh>
 
 #include <chrono>
 #include <cmath>
@@ -455,15 +454,13 @@ static lair_status scan(lair_handle *h, const int *cnt, int *out, int n, int *to
         if (total) TRY(read_ints(h, out + n, 1, total));
         return LAIR_OK;
     }
-    size_t need = 0;
-    CU(cub::DeviceScan::ExclusiveSum(nullptr, need, cnt, out, n + 1, h->s));
+    const size_t need = scan_state_bytes((long long)n + 1);
     if (need > h->scan_tmp_bytes) {
         if (h->scan_tmp) CU(cudaFreeAsync(h->scan_tmp, h->s));
         CU(cudaMallocAsync(&h->scan_tmp, need, h->s));
         h->scan_tmp_bytes = need;
     }
-    CU(cub::DeviceScan::ExclusiveSum(h->scan_tmp, need, cnt, out, n + 1, h->s));
-    count_launch(2);
+    CU(launch_scan((long long)n + 1, cnt, out, h->scan_tmp, h->status, h->s));
     if (total) TRY(read_ints(h, out + n, 1, total));
     return LAIR_OK;
 }
@@ -740,8 +737,8 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         while (nb < 2 * deg[2] + 1) nb *= 2;
         const long long dl = 32 + (long long)deg[1] * (1 + deg[2]);
         if (Bmax <= RSB_MAX_N && nb <= 256 && dl <= RSB_MAX_DIRTY &&
-            rsb_smem_bytes(Bmax, nb, (int)dl) <= (size_t)200 * 1024) {
-            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, Scf, STcf, cf, h->status, h->s));
+            rsb_smem_bytes(Bmax, nb, (int)dl, 0) <= (size_t)200 * 1024) {
+            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, deg[0], Scf, STcf, cf, h->status, h->s));
         } else {
             CU(launch_rs(n, bd, (int)blocks.size(), Bmax, deg[0], Scf, STcf, cf, h->status, h->s));
         }

@@ -107,8 +107,5 @@ inline int grid_for(long long work, int block, int max_blocks = 0) {
     return (int)g;
 }
 
-// exclusive scan of n ints (out may alias in); returns the total through *total_dev (device int) if given
-cudaError_t scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s, void *&tmp,
-                           size_t &tmp_bytes);
 
 }  // namespace lair

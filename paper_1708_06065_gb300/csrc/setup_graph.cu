@@ -683,58 +683,30 @@ __host__ __device__ inline RsbLayout rsb_layout(int n, int nb, int dl) {
     return L;
 }
 
-__global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ blocks, Graph S, Graph ST, int nb, int dl,
-                                                  int8_t *__restrict__ cf_out, int *status) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int ndirty;
-    const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
-    const int n = b1 - b0;
-    const RsbLayout Lo = rsb_layout(n, nb, dl);
-    const int W = Lo.W;
-    unsigned *bm = reinterpret_cast<unsigned *>(smem + Lo.bm);
-    int *cnt = reinterpret_cast<int *>(smem + Lo.cnt);
-    unsigned *dflag = reinterpret_cast<unsigned *>(smem + Lo.dflag);
-    int *dlist = reinterpret_cast<int *>(smem + Lo.dlist);
-    unsigned *lamw = reinterpret_cast<unsigned *>(smem + Lo.lam);     // byte k of the block: lambda_k
-    uint8_t *bkt = smem + Lo.bkt;                                     // the bucket that holds k
-    int8_t *cf = reinterpret_cast<int8_t *>(smem + Lo.cf);
+struct RsbShared {
+    unsigned *bm;      // nb bitmaps of W words
+    int *cnt;          // points per bucket
+    unsigned *dflag;   // listed in this step
+    int *dlist;        // points whose lambda changed in this step
+    unsigned *lamw;    // byte k: lambda_k
+    uint8_t *bkt;      // the bucket that holds k
+    int8_t *cf;
+    int *ndirty;
+};
+
+// the steps of the bucket-queue first pass over in-block views of S and ST (local indices)
+template <class V>
+__device__ void rsb_steps(int n, int nb, int W, int dl, int top, const V &Sv, const V &STv, const RsbShared &q,
+                          int *status) {
     const unsigned lane = threadIdx.x;
     const unsigned FULL = 0xffffffffu;
-
-    for (int e = lane; e < nb * W; e += 32) bm[e] = 0u;
-    for (int e = lane; e < nb; e += 32) cnt[e] = 0;
-    for (int e = lane; e < W; e += 32) dflag[e] = 0u;
-    for (int e = lane; e < (n + 3) / 4; e += 32) lamw[e] = 0u;
-    if (lane == 0) ndirty = 0;
-    __syncwarp();
-    int top = 0;
-    for (int li = lane; li < n; li += 32) {
-        const int i = b0 + li;
-        int lam = 0;
-        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) lam += (ST.col[p] >= b0 && ST.col[p] < b1);
-        const bool iso = (S.rp[i + 1] == S.rp[i]) && (ST.rp[i + 1] == ST.rp[i]);
-        cf[li] = iso ? CF_F : CF_U;
-        bkt[li] = 0;
-        if (iso) continue;
-        if (lam >= nb) {                       // the host sized nb above every reachable lambda
-            set_status(status, LAIR_ERR_ARENA_OVERFLOW);
-            lam = nb - 1;
-        }
-        atomicAdd(&lamw[li >> 2], (unsigned)lam << (8 * (li & 3)));
-        bkt[li] = (uint8_t)lam;
-        atomicOr(&bm[lam * W + (li >> 5)], 1u << (li & 31));
-        atomicAdd(&cnt[lam], 1);
-        top = max(top, lam);
-    }
-    top = __reduce_max_sync(FULL, top);
-    __syncwarp();
     const int per = W / 32;                    // bitmap words scanned by each lane (4 or more, contiguous)
     for (int step = 0; step <= n; ++step) {
         // 1. the highest non-empty bucket at or below top, then its lowest set bit
         int b = -1;
         for (int t0 = top; t0 >= 0; t0 -= 32) {
             const int c = t0 - (int)lane;
-            const unsigned m = __ballot_sync(FULL, c >= 0 && cnt[c] > 0);
+            const unsigned m = __ballot_sync(FULL, c >= 0 && q.cnt[c] > 0);
             if (m) {
                 b = t0 - (__ffs(m) - 1);
                 break;
@@ -742,15 +714,15 @@ __global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ block
         }
         if (b < 0) break;
         top = b;
-        const unsigned *row = bm + (size_t)b * W + (size_t)lane * per;
+        const unsigned *row = q.bm + (size_t)b * W + (size_t)lane * per;
         int fw = -1;
         unsigned fv = 0u;
         for (int r = 0; r < per && fw < 0; r += 4) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(row + r);
-            if (q.x) { fw = r; fv = q.x; }
-            else if (q.y) { fw = r + 1; fv = q.y; }
-            else if (q.z) { fw = r + 2; fv = q.z; }
-            else if (q.w) { fw = r + 3; fv = q.w; }
+            const uint4 u = *reinterpret_cast<const uint4 *>(row + r);
+            if (u.x) { fw = r; fv = u.x; }
+            else if (u.y) { fw = r + 1; fv = u.y; }
+            else if (u.z) { fw = r + 2; fv = u.z; }
+            else if (u.w) { fw = r + 3; fv = u.w; }
         }
         const unsigned fm = __ballot_sync(FULL, fw >= 0);
         if (fm == 0u) {                        // a count without its bit: cannot happen
@@ -761,86 +733,154 @@ __global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ block
         fw = __shfl_sync(FULL, fw, src) + src * per;
         fv = __shfl_sync(FULL, fv, src);
         const int li = 32 * fw + __ffs(fv) - 1;
-        const int i = b0 + li;
-        // 2. i becomes C; its undecided in-block dependants become F (new in this step)
+        // 2. li becomes C; its undecided in-block dependants become F (new in this step)
         if (lane == 0) {
-            cf[li] = CF_C;
-            atomicAnd(&bm[b * W + (li >> 5)], ~(1u << (li & 31)));
-            atomicSub(&cnt[b], 1);
+            q.cf[li] = CF_C;
+            atomicAnd(&q.bm[b * W + (li >> 5)], ~(1u << (li & 31)));
+            atomicSub(&q.cnt[b], 1);
         }
-        const int sb = ST.rp[i], se = ST.rp[i + 1];
+        const int sb = STv.beg(li), se = STv.end(li);
         for (int p = sb + (int)lane; p < se; p += 32) {
-            const int j = ST.col[p] - b0;
-            if (j >= 0 && j < n && cf[j] == CF_U) {
-                cf[j] = CF_NEWF;
-                const int bj = bkt[j];
-                atomicAnd(&bm[bj * W + (j >> 5)], ~(1u << (j & 31)));
-                atomicSub(&cnt[bj], 1);
+            const int j = STv.at(p);
+            if (j >= 0 && q.cf[j] == CF_U) {
+                q.cf[j] = CF_NEWF;
+                const int bj = q.bkt[j];
+                atomicAnd(&q.bm[bj * W + (j >> 5)], ~(1u << (j & 31)));
+                atomicSub(&q.cnt[bj], 1);
             }
         }
         __syncwarp();
         // 3. lambda updates; the first touch of a point lists it
         auto touch = [&](int k, bool inc) {
             const unsigned sh = 8u * (unsigned)(k & 3);
-            atomicAdd(&lamw[k >> 2], inc ? (1u << sh) : (0u - (1u << sh)));
+            atomicAdd(&q.lamw[k >> 2], inc ? (1u << sh) : (0u - (1u << sh)));
             const unsigned bit = 1u << (k & 31);
-            if (!(atomicOr(&dflag[k >> 5], bit) & bit)) {
-                const int pos = atomicAdd(&ndirty, 1);
-                if (pos < dl) dlist[pos] = k;
+            if (!(atomicOr(&q.dflag[k >> 5], bit) & bit)) {
+                const int pos = atomicAdd(q.ndirty, 1);
+                if (pos < dl) q.dlist[pos] = k;
                 else set_status(status, LAIR_ERR_ARENA_OVERFLOW);
             }
         };
         for (int p = sb + (int)lane; p < se; p += 32) {
-            const int j = ST.col[p] - b0;
-            if (j < 0 || j >= n || cf[j] != CF_NEWF) continue;
-            for (int q = S.rp[b0 + j]; q < S.rp[b0 + j + 1]; ++q) {
-                const int k = S.col[q] - b0;
-                if (k >= 0 && k < n && cf[k] == CF_U) touch(k, true);
+            const int j = STv.at(p);
+            if (j < 0 || q.cf[j] != CF_NEWF) continue;
+            for (int r = Sv.beg(j); r < Sv.end(j); ++r) {
+                const int k = Sv.at(r);
+                if (k >= 0 && q.cf[k] == CF_U) touch(k, true);
             }
         }
-        for (int q = S.rp[i] + (int)lane; q < S.rp[i + 1]; q += 32) {
-            const int k = S.col[q] - b0;
-            if (k >= 0 && k < n && cf[k] == CF_U) touch(k, false);
+        for (int r = Sv.beg(li) + (int)lane; r < Sv.end(li); r += 32) {
+            const int k = Sv.at(r);
+            if (k >= 0 && q.cf[k] == CF_U) touch(k, false);
         }
         __syncwarp();
         // 4. listed points change bucket
-        const int nd = min(ndirty, dl);
+        const int nd = min(*q.ndirty, dl);
         int hi = 0;
         for (int d = lane; d < nd; d += 32) {
-            const int k = dlist[d];
+            const int k = q.dlist[d];
             const unsigned bit = 1u << (k & 31);
-            atomicAnd(&dflag[k >> 5], ~bit);
-            const int lam = (int)((lamw[k >> 2] >> (8 * (k & 3))) & 0xFFu);
-            const int ob = bkt[k];
+            atomicAnd(&q.dflag[k >> 5], ~bit);
+            const int lam = (int)((q.lamw[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            const int ob = q.bkt[k];
             if (lam == ob) continue;
             if (lam >= nb) {
                 set_status(status, LAIR_ERR_ARENA_OVERFLOW);
                 continue;
             }
-            atomicAnd(&bm[ob * W + (k >> 5)], ~bit);
-            atomicOr(&bm[lam * W + (k >> 5)], bit);
-            atomicSub(&cnt[ob], 1);
-            atomicAdd(&cnt[lam], 1);
-            bkt[k] = (uint8_t)lam;
+            atomicAnd(&q.bm[ob * W + (k >> 5)], ~bit);
+            atomicOr(&q.bm[lam * W + (k >> 5)], bit);
+            atomicSub(&q.cnt[ob], 1);
+            atomicAdd(&q.cnt[lam], 1);
+            q.bkt[k] = (uint8_t)lam;
             hi = max(hi, lam);
         }
         top = max(top, (int)__reduce_max_sync(FULL, (unsigned)hi));
         __syncwarp();
-        if (lane == 0) ndirty = 0;
+        if (lane == 0) *q.ndirty = 0;
         for (int p = sb + (int)lane; p < se; p += 32) {
-            const int j = ST.col[p] - b0;
-            if (j >= 0 && j < n && cf[j] == CF_NEWF) cf[j] = CF_F;
+            const int j = STv.at(p);
+            if (j >= 0 && q.cf[j] == CF_NEWF) q.cf[j] = CF_F;
         }
         __syncwarp();
     }
+}
+
+// smem_bytes: the bucket layout for the largest block, then room to stage both in-block graphs
+// (uint16 row offsets and columns); a block whose graphs do not fit reads them through the cache
+__global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ blocks, Graph S, Graph ST, int nb, int dl,
+                                                  int8_t *__restrict__ cf_out, int *status, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int ndirty;
+    const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
+    const int n = b1 - b0;
+    const RsbLayout Lo = rsb_layout(n, nb, dl);
+    const int W = Lo.W;
+    RsbShared q;
+    q.bm = reinterpret_cast<unsigned *>(smem + Lo.bm);
+    q.cnt = reinterpret_cast<int *>(smem + Lo.cnt);
+    q.dflag = reinterpret_cast<unsigned *>(smem + Lo.dflag);
+    q.dlist = reinterpret_cast<int *>(smem + Lo.dlist);
+    q.lamw = reinterpret_cast<unsigned *>(smem + Lo.lam);
+    q.bkt = smem + Lo.bkt;
+    q.cf = reinterpret_cast<int8_t *>(smem + Lo.cf);
+    q.ndirty = &ndirty;
+    const unsigned lane = threadIdx.x;
+
+    for (int e = lane; e < nb * W; e += 32) q.bm[e] = 0u;
+    for (int e = lane; e < nb; e += 32) q.cnt[e] = 0;
+    for (int e = lane; e < W; e += 32) q.dflag[e] = 0u;
+    for (int e = lane; e < (n + 3) / 4; e += 32) q.lamw[e] = 0u;
+    if (lane == 0) ndirty = 0;
+    __syncwarp();
+    int top = 0;
     for (int li = lane; li < n; li += 32) {
-        const int8_t c = cf[li];
+        const int i = b0 + li;
+        int lam = 0;
+        for (int p = ST.rp[i]; p < ST.rp[i + 1]; ++p) lam += (ST.col[p] >= b0 && ST.col[p] < b1);
+        const bool iso = (S.rp[i + 1] == S.rp[i]) && (ST.rp[i + 1] == ST.rp[i]);
+        q.cf[li] = iso ? CF_F : CF_U;
+        q.bkt[li] = 0;
+        if (iso) continue;
+        if (lam >= nb) {                       // the host sized nb above every reachable lambda
+            set_status(status, LAIR_ERR_ARENA_OVERFLOW);
+            lam = nb - 1;
+        }
+        atomicAdd(&q.lamw[li >> 2], (unsigned)lam << (8 * (li & 3)));
+        q.bkt[li] = (uint8_t)lam;
+        atomicOr(&q.bm[lam * W + (li >> 5)], 1u << (li & 31));
+        atomicAdd(&q.cnt[lam], 1);
+        top = max(top, lam);
+    }
+    top = (int)__reduce_max_sync(0xffffffffu, (unsigned)top);
+    __syncwarp();
+    // stage both in-block graphs after the bucket layout if they fit (same entry count in each)
+    uint16_t *srp = reinterpret_cast<uint16_t *>(smem + Lo.total);
+    uint16_t *strp = srp + (n + 1);
+    uint16_t *scol = strp + (n + 1);
+    const size_t used = (size_t)(reinterpret_cast<unsigned char *>(scol) - smem);
+    const size_t cap = used < (size_t)smem_bytes ? ((size_t)smem_bytes - used) / (2 * sizeof(uint16_t)) : 0;
+    bool staged = rs_stage(S, b0, b1, srp, scol, cap);
+    if (staged) staged = rs_stage(ST, b0, b1, strp, scol + srp[n], cap);
+    if (staged) {
+        StagedView vs{srp, scol}, vt{strp, scol + srp[n]};
+        rsb_steps(n, nb, W, dl, top, vs, vt, q, status);
+    } else {
+        GlobalView vs{S.rp, S.col, b0, b1}, vt{ST.rp, ST.col, b0, b1};
+        rsb_steps(n, nb, W, dl, top, vs, vt, q, status);
+    }
+    for (int li = lane; li < n; li += 32) {
+        const int8_t c = q.cf[li];
         if (c != CF_C && c != CF_F) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
         cf_out[b0 + li] = c;
     }
 }
 
-size_t rsb_smem_bytes(int n, int nb, int dl) { return rsb_layout(n, nb, dl).total; }
+// the bucket layout of the largest block plus both staged in-block graphs of the fullest block
+size_t rsb_smem_bytes(int n, int nb, int dl, int max_inblock) {
+    return rsb_layout(n, nb, dl).total + 2 * sizeof(uint16_t) * ((size_t)n + 1) +
+           2 * sizeof(uint16_t) * (size_t)max_inblock + 16;
+}
 
 // shared memory of one block: the fixed part (keys, tree, splitting, row offsets) plus room for
 // both staged in-block graphs of the fullest block, up to RS_SMEM_MAX bytes in all (blocks that
@@ -1026,6 +1066,107 @@ void small_scan(int m, const int *in, int *out, cudaStream_t s) {
 }
 
 // -------------------------------------------------------------------------------------
+// exclusive scan of any length in one pass (decoupled look-back). A CTA takes the next tile
+// index from a counter (so every tile before it belongs to a CTA that is already running or
+// done), scans its LB_TILE entries as k_small_scan does, publishes the tile total, reads the
+// published totals and prefixes of the tiles before it 32 at a time until it meets a prefix,
+// and publishes its own inclusive prefix. state[t] packs (flag << 32) | value in one 64-bit
+// word (flag 0: nothing yet, 1: tile total, 2: inclusive prefix); state and the counter are
+// zero on entry. Every wait is bounded: one that runs out sets LAIR_ERR_DEVICE_TIMEOUT and the
+// CTA goes on with what it has.
+// -------------------------------------------------------------------------------------
+constexpr int LB_THREADS = 512;
+constexpr int LB_STRIPS = 8;
+constexpr int LB_TILE = LB_THREADS * LB_STRIPS;
+constexpr long long LB_WAIT_POLLS = 1ll << 22;
+
+__global__ void __launch_bounds__(LB_THREADS) k_scan_lookback(long long m, const int *__restrict__ in,
+                                                              int *__restrict__ out, unsigned long long *state,
+                                                              int *counter, int *status) {
+    __shared__ int wsum[LB_THREADS / 32];
+    __shared__ int tile_s, prefix_s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) tile_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const long long tile = tile_s;
+    const long long seg = tile * LB_TILE + (long long)w * 32 * LB_STRIPS + lane;
+    int v[LB_STRIPS];
+#pragma unroll
+    for (int k = 0; k < LB_STRIPS; ++k) v[k] = seg + 32 * k < m ? in[seg + 32 * k] : 0;
+    int run = 0;
+#pragma unroll
+    for (int k = 0; k < LB_STRIPS; ++k) {
+        int x = v[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        v[k] = run + x - v[k];
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) wsum[w] = run;
+    __syncthreads();
+    if (w == 0) {
+        const int sv = lane < LB_THREADS / 32 ? wsum[lane] : 0;
+        int x = sv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < LB_THREADS / 32) wsum[lane] = x - sv;
+        const int total = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) {
+            atomicExch(&state[tile], ((tile == 0 ? 2ull : 1ull) << 32) | (unsigned)total);
+        }
+        // look back over the tiles before this one
+        int excl = 0;
+        long long spins = 0;
+        for (long long hi = tile - 1; hi >= 0; hi -= 32) {
+            const long long p = hi - lane;
+            unsigned long long st = p >= 0 ? *(volatile unsigned long long *)&state[p] : (2ull << 32);
+            while (__any_sync(0xffffffffu, (st >> 32) == 0ull)) {
+                if (++spins > LB_WAIT_POLLS) {
+                    if (lane == 0) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+                    st = (2ull << 32);
+                    break;
+                }
+                __nanosleep(32);
+                if ((st >> 32) == 0ull) st = *(volatile unsigned long long *)&state[p];
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, (st >> 32) == 2ull);
+            const int stop = pm ? __ffs(pm) - 1 : 31;
+            excl += __reduce_add_sync(0xffffffffu, lane <= stop ? (unsigned)(st & 0xffffffffull) : 0u);
+            if (pm) break;
+        }
+        if (lane == 0) {
+            prefix_s = excl;
+            if (tile > 0) atomicExch(&state[tile], (2ull << 32) | (unsigned)(excl + total));
+        }
+    }
+    __syncthreads();
+    const int off = prefix_s + wsum[w];
+#pragma unroll
+    for (int k = 0; k < LB_STRIPS; ++k)
+        if (seg + 32 * k < m) out[seg + 32 * k] = off + v[k];
+}
+
+size_t scan_state_bytes(long long m) { return (size_t)((m + LB_TILE - 1) / LB_TILE) * 8 + 16; }
+
+// state: scan_state_bytes(m) bytes of scratch; out may be in (each tile reads its inputs before it writes)
+cudaError_t launch_scan(long long m, const int *in, int *out, void *state, int *status, cudaStream_t s) {
+    const long long tiles = (m + LB_TILE - 1) / LB_TILE;
+    cudaError_t e = cudaMemsetAsync(state, 0, scan_state_bytes(m), s);
+    if (e != cudaSuccess) return e;
+    unsigned long long *st = static_cast<unsigned long long *>(state);
+    int *counter = reinterpret_cast<int *>(st + tiles);
+    k_scan_lookback<<<(unsigned)(tiles > 0 ? tiles : 1), LB_THREADS, 0, s>>>(m, in, out, st, counter, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------------------------
 // host wrappers
 // -------------------------------------------------------------------------------------
 static const int TB = 256;
@@ -1116,12 +1257,14 @@ void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Gr
     count_launch();
 }
 
-cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, int max_inblock, const Graph &S,
                              const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
-    const size_t bytes = rsb_smem_bytes(Bmax, nb, dl);
+    size_t bytes = rsb_smem_bytes(Bmax, nb, dl, max_inblock);
+    const size_t floor = rsb_smem_bytes(Bmax, nb, dl, 0);
+    if (bytes > RS_SMEM_MAX) bytes = floor > RS_SMEM_MAX ? floor : RS_SMEM_MAX;   // unstaged blocks read the cache
     cudaError_t e = cudaFuncSetAttribute(k_rs_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_rs_bucket<<<nblocks, 32, bytes, s>>>(blocks, S, ST, nb, dl, cf, status);
+    k_rs_bucket<<<nblocks, 32, bytes, s>>>(blocks, S, ST, nb, dl, cf, status, (int)bytes);
     count_launch();
     return cudaGetLastError();
 }

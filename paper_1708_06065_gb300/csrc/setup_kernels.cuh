@@ -18,6 +18,9 @@ struct SellView {
 
 // ---- setup_graph.cu -------------------------------------------------------------------
 constexpr int SMALL_SCAN_MAX = 65536;   // exclusive scans up to this length run in one CTA
+// exclusive scan of m ints in one pass over many CTAs (decoupled look-back); state: scan_state_bytes(m) bytes
+size_t scan_state_bytes(long long m);
+cudaError_t launch_scan(long long m, const int *in, int *out, void *state, int *status, cudaStream_t s);
 void small_scan(int m, const int *in, int *out, cudaStream_t s);
 void launch_strength(const DCsr &A, double theta, int absmode, uint8_t *mask, int *cnt, cudaStream_t s);
 void launch_graph_fill(const DCsr &A, const uint8_t *mask, const Graph &G, cudaStream_t s);
@@ -36,9 +39,9 @@ void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcn
 constexpr int RSB_MAX_N = 8192;
 constexpr int RSB_MAX_DIRTY = 8192;
 void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Graph &ST, int *out, cudaStream_t s);
-cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, int max_inblock, const Graph &S,
                              const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
-size_t rsb_smem_bytes(int n, int nb, int dl);
+size_t rsb_smem_bytes(int n, int nb, int dl, int max_inblock);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
                       int8_t *cf, int *status, cudaStream_t s);
 size_t rs_smem_bytes(int n, int max_inblock);
