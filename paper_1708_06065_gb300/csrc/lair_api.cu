@@ -625,8 +625,8 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(t.get(&lists, (size_t)SPGEMM_BINS * nr + 1));
     TRY(new_counts(h, t, &bc, SPGEMM_BINS + 2));
     // thread-per-row merging needs many rows to keep the GPU busy; short products stay on warps
-    const bool merge = P == nullptr && nr >= SPGEMM_MERGE_MIN_ROWS;
-    launch_spgemm_classify(nr, off, X.rp, merge, lists, bc, bc + SPGEMM_BINS, h->s);
+    const bool merge = nr >= SPGEMM_MERGE_MIN_ROWS;
+    launch_spgemm_classify(nr, off, X.rp, merge, merge && P == nullptr, lists, bc, bc + SPGEMM_BINS, h->s);
     // one read-back: bin counts, largest bound, and the total bound (staging size)
     CU(cudaMemcpyAsync(bc + SPGEMM_BINS + 1, off + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
     int hc[SPGEMM_BINS + 2];

@@ -110,9 +110,11 @@ constexpr int SPGEMM_MERGE_K = 8;
 constexpr int SPGEMM_MERGE_K2 = 32;
 constexpr int SPGEMM_MERGE_MIN_ROWS = 65536;   // products with fewer rows use the warp kernels only
 void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
-void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, int *lists, int *counts, int *ubmax,
-                            cudaStream_t s);
-// true if every row of the product fits the fused one-point-P kernels (bins 0 and 1)
+// merge: rows of X with at most SPGEMM_MERGE_K entries go to the thread-per-row merge bin; merge2: rows
+// with at most SPGEMM_MERGE_K2 to the second merge bin (plain products only)
+void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int *lists, int *counts,
+                            int *ubmax, cudaStream_t s);
+// true if every row of the product fits the fused one-point-P kernels (bins 0 and 1, the first merge bin)
 bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s);
