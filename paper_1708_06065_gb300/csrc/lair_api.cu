@@ -143,6 +143,13 @@ struct lair_handle {
     int *d_batcnt = nullptr;      // device, nseg ints
     int *h_batcnt = nullptr;      // pinned, nseg ints
     lair::SegTiles segt;          // row tiles of the systems (level 0), built at the first batched solve
+    // device-side control of the batched outer loops, and a ring of running-system counts read back late
+    lair::BatchCtl bctl;
+    int bctl_m = -1;
+    static constexpr int RING = 8, LAG = 2;
+    int *d_ring = nullptr;        // device, RING ints
+    int *h_ring = nullptr;        // pinned, RING ints
+    cudaEvent_t ring_ev[RING] = {};
 };
 
 namespace lair {
@@ -515,12 +522,147 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
 }
 
 // ---------------------------------------------------------------------------------------
+// launch-schedule autotuner of the local solves (spec pattern 2): for a batch of at least
+// LOCAL_TUNE_MIN systems whose shape (precision, shared sets, Neumann series, count, mean and largest
+// size) has not been seen in this process, every candidate schedule bins and solves the batch, timed
+// best of three with CUDA events; the fastest replaces the default when it is more than 5 % faster.
+// Each system is solved by the same operations whatever team holds it, so the rows written are the
+// same bits under every candidate, and the last run leaves the right result in place.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr int LOCAL_TUNE_MIN = 65536;
+struct LocalKey {
+    int dev, fp32, shared, neumann, count, mean4, smax;
+    bool operator<(const LocalKey &o) const {
+        return std::tie(dev, fp32, shared, neumann, count, mean4, smax) <
+               std::tie(o.dev, o.fp32, o.shared, o.neumann, o.count, o.mean4, o.smax);
+    }
+};
+std::mutex g_local_tune_mu;
+std::map<LocalKey, LocalSchedule> g_local_tune;
+// (tmax, wmax, warp blocks per SM, thread-kernel block); the first is the default
+const LocalSchedule kLocalCandidates[] = {{6, 32, 8, 128}, {4, 32, 8, 128}, {0, 32, 8, 128}, {6, 32, 16, 128},
+                                          {6, 32, 4, 128}, {6, 32, 8, 64},  {6, 16, 8, 128}, {2, 32, 16, 64}};
+}  // namespace
+
+// bins the ng systems of nb_rp (stride: rows sharing one set) with schedule sch and solves them; hc gets the
+// bin counts and the largest size
+static lair_status bin_and_solve(lair_handle *h, Temps &t, const LocalArgs &a, int ng, const int *nb_rp, int stride,
+                                 int *lists, int *bcounts, const LocalSchedule &sch, void **scratch, size_t *scratch_bytes,
+                                 int hc[4]) {
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    CU(cudaMemsetAsync(bcounts, 0, sizeof(int) * 4, h->s));
+    launch_local_bin(ng, nb_rp, lists, bcounts, bcounts + 3, h->s, stride, sch.tmax, sch.wmax);
+    TRY(read_ints(h, bcounts, 4, hc));
+    if (hc[2] > 0 && local_cta_scratch_bytes(hc[3], fp32) > *scratch_bytes) {
+        unsigned char *sp;
+        *scratch_bytes = local_cta_scratch_bytes(hc[3], fp32);
+        TRY(t.get(&sp, *scratch_bytes));
+        *scratch = sp;
+    }
+    CU(launch_local_solves(a, ng, lists, bcounts, hc, hc[3], fp32, *scratch, h->s, sch));
+    return LAIR_OK;
+}
+
+// the local solves of a batch (binned once with the default schedule into lists / bcounts, hc); tuned first when
+// the autotuner is on and the batch is large and new
+static lair_status run_local_solves(lair_handle *h, Temps &t, const LocalArgs &a, int ng, const int *nb_rp, int stride,
+                                    int nnb, int *lists, int *bcounts, int hc[4], int level) {
+    const bool fp32 = h->o.precision == LAIR_MIXED;
+    void *scratch = nullptr;
+    size_t sbytes = 0;
+    if (hc[2] > 0) {
+        unsigned char *sp;
+        sbytes = local_cta_scratch_bytes(hc[3], fp32);
+        TRY(t.get(&sp, sbytes));
+        scratch = sp;
+    }
+    LocalSchedule pick;
+    bool tuned = false;
+    if (h->o.autotune && ng >= LOCAL_TUNE_MIN) {
+        int dev = 0;
+        CU(cudaGetDevice(&dev));
+        const double mean = ng ? (double)nnb / ng : 0.0;
+        const LocalKey key{dev, fp32 ? 1 : 0, stride > 1 ? 1 : 0, a.neumann_deg >= 0 ? 1 : 0,
+                           (int)std::floor(4.0 * std::log2((double)ng)), (int)std::lround(4.0 * mean),
+                           hc[3] > 0 ? (int)std::ceil(std::log2((double)hc[3])) : 0};
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> g(g_local_tune_mu);
+            auto it = g_local_tune.find(key);
+            if (it != g_local_tune.end()) {
+                pick = it->second;
+                found = true;
+            }
+        }
+        if (found && h->o.timing) {
+            char nm[96];
+            snprintf(nm, sizeof nm, "tune_local_L%d:t%dw%dg%db%d cached", level, pick.tmax, pick.wmax,
+                     pick.warp_blocks_per_sm, pick.thread_tb);
+            h->timers[timer_slot(h, nm, 0.0)].launches += 1;
+        }
+        if (!found) {
+            cudaEvent_t e0 = get_event(h), e1 = get_event(h);
+            float best = 3.4e38f, base = 3.4e38f;
+            int bi = 0;
+            for (int ci = 0; ci < (int)(sizeof(kLocalCandidates) / sizeof(kLocalCandidates[0])); ++ci) {
+                const LocalSchedule &c = kLocalCandidates[ci];
+                int hcc[4];
+                TRY(bin_and_solve(h, t, a, ng, nb_rp, stride, lists, bcounts, c, &scratch, &sbytes, hcc));   // warm
+                float tmin = 3.4e38f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    CU(cudaEventRecord(e0, h->s));
+                    CU(launch_local_solves(a, ng, lists, bcounts, hcc, hcc[3], fp32, scratch, h->s, c));
+                    CU(cudaEventRecord(e1, h->s));
+                    CU(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CU(cudaEventElapsedTime(&ms, e0, e1));
+                    tmin = std::min(tmin, ms);
+                }
+                if (ci == 0) base = tmin;
+                if (tmin < best) {
+                    best = tmin;
+                    bi = ci;
+                }
+            }
+            h->ev_pool.push_back(e0);
+            h->ev_pool.push_back(e1);
+            if (!(best < 0.95f * base)) {
+                bi = 0;
+                best = base;
+            }
+            pick = kLocalCandidates[bi];
+            {
+                std::lock_guard<std::mutex> g(g_local_tune_mu);
+                g_local_tune[key] = pick;
+            }
+            if (h->o.timing) {
+                // the choice and its time (one timer per tuned batch: "tune_local_L<level>:t<tmax>w<wmax>g<cap>b<tb>")
+                char nm[96];
+                snprintf(nm, sizeof nm, "tune_local_L%d:t%dw%dg%db%d base=%.3fms", level, pick.tmax, pick.wmax,
+                         pick.warp_blocks_per_sm, pick.thread_tb, (double)base);
+                const int slot = timer_slot(h, nm, 0.0);
+                h->timers[slot].ms += best;
+                h->timers[slot].launches += 1;
+            }
+        }
+        tuned = true;
+    }
+    if (!tuned) {
+        CU(launch_local_solves(a, ng, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
+        return LAIR_OK;
+    }
+    int hcc[4];
+    return bin_and_solve(h, t, a, ng, nb_rp, stride, lists, bcounts, pick, &scratch, &sbytes, hcc);
+}
+
+// ---------------------------------------------------------------------------------------
 // local solves: neighbourhoods of C points in graph G, systems of matrix B, rows into out
 // ---------------------------------------------------------------------------------------
 static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts, const Graph &G, const int8_t *cf,
                               const int *brp, const int *bcol, const double *bval, int **out_rp, int **out_col,
                               double **out_val, float **out_val32, uint8_t *lsflag, int *out_nnz, bool keep,
-                              int neumann_deg = -1) {
+                              int neumann_deg = -1, int level = -1) {
     const int distance = h->o.distance, d0 = distance < 2 ? distance : 2;
     int *ub, *off, *tmp, *cnt, *nb_rp, *nb_col;
     TRY(new_counts(h, t, &ub, nc));
@@ -589,14 +731,8 @@ static lair_status local_rows(lair_handle *h, Temps &t, int nc, const int *cpts,
         TRY(t.get(&ocol, (size_t)nout));
         TRY(t.get(&oval, (size_t)nout));
     }
-    void *scratch = nullptr;
-    if (hc[2] > 0) {
-        unsigned char *sp;
-        TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
-        scratch = sp;
-    }
     LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg};
-    CU(launch_local_solves(a, nc, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
+    TRY(run_local_solves(h, t, a, nc, nb_rp, 1, nnb, lists, bcounts, hc, level));
     *out_nnz = nout;
     *out_rp = orp;
     *out_col = ocol;
@@ -737,8 +873,8 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         while (nb < 2 * deg[2] + 1) nb *= 2;
         const long long dl = 32 + (long long)deg[1] * (1 + deg[2]);
         if (Bmax <= RSB_MAX_N && nb <= 256 && dl <= RSB_MAX_DIRTY &&
-            rsb_smem_bytes(Bmax, nb, (int)dl, 0) <= (size_t)200 * 1024) {
-            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, deg[0], Scf, STcf, cf, h->status, h->s));
+            rsb_smem_bytes(Bmax, nb, (int)dl) <= (size_t)200 * 1024) {
+            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, Scf, STcf, cf, h->status, h->s));
         } else {
             CU(launch_rs(n, bd, (int)blocks.size(), Bmax, deg[0], Scf, STcf, cf, h->status, h->s));
         }
@@ -843,10 +979,10 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         TRY(t.get(&all, (size_t)A.nnz));
         TRY(build_strength_graph(h, t, A, 0.0, all, GA, 1));
         TRY(local_rows(h, t, nc, cpts, GA, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
-                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true, o.distance - 1));
+                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true, o.distance - 1, l));
     } else {
         TRY(local_rows(h, t, nc, cpts, S, L.cf, A.rp, A.col, A.val, &L.R.rp, &L.R.col, &L.R.val,
-                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true));
+                       fp32 ? &L.R.val32 : nullptr, L.lsR, &L.R.nnz, true, -1, l));
     }
 
     // ---- interpolation
@@ -878,7 +1014,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         double *wval;
         int wnnz = 0;
         TRY(local_rows(h, t, nc, cpts, ST, L.cf, atrp, atcol, atval, &wrp, &wcol, &wval, nullptr, L.lsP, &wnnz,
-                       false));
+                       false, -1, l));
         TRY(transpose(h, t, nc, n, wnnz, wrp, wcol, wval, &L.P.rp, &L.P.col, &L.P.val, true));
         L.P.nnz = wnnz;
         if (fp32) {
@@ -1722,7 +1858,6 @@ static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cp
                                  int nnz, const int *brp, const int *bcol, const double *bval, int *ocol, double *oval,
                                  float *oval32, uint8_t *lsflag, int neumann_deg, int rows_per) {
     if (nc <= 0) return LAIR_OK;
-    const bool fp32 = h->o.precision == LAIR_MIXED;
     int *nb_rp, *nb_col, *lists, *bcounts;
     TRY(t.get(&nb_rp, (size_t)nc + 1));
     TRY(t.get(&nb_col, (size_t)(nnz - nc) + 1));
@@ -1734,15 +1869,8 @@ static lair_status local_rows_on(lair_handle *h, Temps &t, int nc, const int *cp
     launch_local_bin(ng, nb_rp, lists, bcounts, bcounts + 3, h->s, rows_per);
     int hc[4];
     TRY(read_ints(h, bcounts, 4, hc));
-    void *scratch = nullptr;
-    if (hc[2] > 0) {
-        unsigned char *sp;
-        TRY(t.get(&sp, local_cta_scratch_bytes(hc[3], fp32)));
-        scratch = sp;
-    }
     LocalArgs a{cpts, nb_rp, nb_col, brp, bcol, bval, ocol, oval, oval32, lsflag, neumann_deg, rows_per};
-    CU(launch_local_solves(a, ng, lists, bcounts, hc, hc[3], fp32, scratch, h->s));
-    return LAIR_OK;
+    return run_local_solves(h, t, a, ng, nb_rp, rows_per, nnz - nc, lists, bcounts, hc, -1);
 }
 
 static lair_status refresh_level(lair_handle *h, Hier &H, int l) {
@@ -2083,6 +2211,82 @@ static lair_status ensure_tiles(lair_handle *h, const Level &L0) {
 
 // batched systems: stationary refinement where every system is tested on its own relative
 // residual and stops being updated once it is <= tol (the cycle itself acts on all systems)
+// the device-side state of the batched outer loops, for FGMRES(m) (m = 0: stationary refinement only)
+static lair_status ensure_batch_ctl(lair_handle *h, int m) {
+    const int nseg = h->nseg;
+    BatchCtl &c = h->bctl;
+    if (!c.bn) {
+        double *bn;
+        TRY(dalloc(h, &bn, (size_t)nseg));
+        c.bn = bn;
+        TRY(dalloc(h, &c.rl, (size_t)nseg));
+        TRY(dalloc(h, &c.its, (size_t)nseg));
+        TRY(dalloc(h, &c.jd, (size_t)nseg));
+        TRY(dalloc(h, &c.run, (size_t)nseg));
+        TRY(dalloc(h, &c.done, (size_t)nseg));
+        TRY(dalloc(h, &c.nan, 1));
+        TRY(dalloc(h, &h->d_ring, (size_t)lair_handle::RING));
+        CU(cudaMallocHost(&h->h_ring, sizeof(int) * lair_handle::RING));
+        for (cudaEvent_t &e : h->ring_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c.nseg = nseg;
+    }
+    if (m > h->bctl_m) {
+        TRY(dalloc(h, &c.g, (size_t)nseg * (m + 1)));
+        TRY(dalloc(h, &c.cs, (size_t)nseg * m));
+        TRY(dalloc(h, &c.sn, (size_t)nseg * m));
+        TRY(dalloc(h, &c.Hm, (size_t)nseg * (m + 1) * m));
+        h->bctl_m = m;
+    }
+    c.m = m;
+    return LAIR_OK;
+}
+
+// the running-system count of step k: zeroed, filled by the step's control kernel, copied back without waiting
+static int *ring_slot(lair_handle *h, long long k) { return h->d_ring + (int)(k % lair_handle::RING); }
+
+static lair_status ring_post(lair_handle *h, long long k) {
+    const int r = (int)(k % lair_handle::RING);
+    CU(cudaMemcpyAsync(h->h_ring + r, h->d_ring + r, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CU(cudaEventRecord(h->ring_ev[r], h->s));
+    return LAIR_OK;
+}
+
+// the count of step k, which was queued LAG steps ago and is normally complete already
+static lair_status ring_read(lair_handle *h, long long k, int *out) {
+    const int r = (int)(k % lair_handle::RING);
+    CU(cudaEventSynchronize(h->ring_ev[r]));
+    *out = h->h_ring[r];
+    return LAIR_OK;
+}
+
+static lair_status batch_finish(lair_handle *h, double tol, int *iters, double *rel) {
+    const int nseg = h->nseg;
+    std::vector<int> its(nseg);
+    std::vector<double> rl(nseg);
+    int nan = 0;
+    CU(cudaMemcpyAsync(its.data(), h->bctl.its, sizeof(int) * nseg, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaMemcpyAsync(rl.data(), h->bctl.rl, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
+    CU(cudaMemcpyAsync(&nan, h->bctl.nan, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    flush_timers(h);
+    lair_status st = nan ? LAIR_ERR_NAN : LAIR_OK;
+    int worst = -1;
+    for (int q = 0; q < nseg; ++q) {
+        if (iters) iters[q] = its[q];
+        if (rel) rel[q] = rl[q];
+        if (st == LAIR_OK && !(rl[q] <= tol)) {
+            st = LAIR_ERR_NOT_CONVERGED;
+            worst = q;
+        }
+    }
+    if (worst >= 0) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
+    return st;
+}
+
+// batched systems, stationary refinement per system: every iteration the residual of the running systems,
+// a per-system stopping test on the device, one V-cycle of the whole batch and the update of the running
+// systems. The host reads the running-system count of an iteration LAG iterations later (without draining
+// the stream) and stops once it is zero; the iterations queued meanwhile change nothing.
 static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
                                      int *iters, double *rel) {
     Level &L0 = H.lev[0];
@@ -2091,55 +2295,37 @@ static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, d
     const bool mixed = h->o.precision == LAIR_MIXED;
     TRY(ensure_work(h, n, 0));
     TRY(ensure_tiles(h, L0));
-    double *nrm;
-    uint8_t *act;
-    {
-        // device scratch for the per-system norms and flags lives in the handle's FP64 work area
-        nrm = h->part;                                  // RED_PARTS * 33 doubles >= nseg
-        act = reinterpret_cast<uint8_t *>(h->part + (size_t)RED_PARTS * 16);
-    }
+    TRY(ensure_batch_ctl(h, 0));
     if ((size_t)nseg > (size_t)RED_PARTS * 16) return fail(h, LAIR_ERR_UNSUPPORTED, "at most %d systems", RED_PARTS * 16);
-    std::vector<double> bn(nseg), rl(nseg, 0.0);
-    std::vector<int> its(nseg, 0);
-    std::vector<uint8_t> active(nseg, 1);
+    double *nrm = h->part;                                  // RED_PARTS * 33 doubles >= nseg
+    BatchCtl c = h->bctl;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    SegTiles sta = h->segt;
+    sta.active = c.run;
     seg_norm2(h->segt, b, nrm, h->s);
-    CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-    CU(cudaStreamSynchronize(h->s));
-    for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
-    lair_status st = LAIR_OK;
-    for (int it = 0;; ++it) {
-        double *r = mixed ? h->wr : L0.b64;
-        seg_residual(A, h->segt, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
-        CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-        CU(cudaStreamSynchronize(h->s));
-        flush_timers(h);
-        int any = 0;
-        for (int q = 0; q < nseg; ++q) {
-            if (!active[q]) continue;
-            rl[q] = std::sqrt(h->h_seg[q]) / bn[q];
-            if (!std::isfinite(rl[q])) { st = LAIR_ERR_NAN; active[q] = 0; continue; }
-            if (rl[q] <= tol || it >= max_iter) active[q] = 0;
-            else any = 1;
+    bat_bnorm(nseg, nrm, const_cast<double *>(c.bn), h->s);
+    CU(cudaMemsetAsync(c.its, 0, sizeof(int) * nseg, h->s));
+    CU(cudaMemsetAsync(c.run, 1, (size_t)nseg, h->s));
+    CU(cudaMemsetAsync(c.nan, 0, sizeof(int), h->s));
+    for (long long it = 0; it <= (long long)max_iter + lair_handle::LAG + 1; ++it) {
+        if (it >= lair_handle::LAG) {
+            int running = 0;
+            TRY(ring_read(h, it - lair_handle::LAG, &running));
+            if (running == 0) break;
         }
-        if (!any) break;
-        for (int q = 0; q < nseg; ++q) h->h_act[q] = active[q];
-        CU(cudaMemcpyAsync(act, h->h_act, nseg, cudaMemcpyHostToDevice, h->s));
+        double *r = mixed ? h->wr : L0.b64;
+        seg_residual(A, sta, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
+        CU(cudaMemsetAsync(ring_slot(h, it), 0, sizeof(int), h->s));
+        bat_stat_check(c, nrm, (int)std::min<long long>(it, max_iter), ring_slot(h, it), h->s);
+        TRY(ring_post(h, it));
         CU(cudaGraphLaunch(H.graph, h->s));
         count_launch(H.graph_nodes);
         h->graph_pending = h->o.timing;
-        if (mixed) seg_axpy<float>(h->segt, act, L0.x32[L0.xfinal], x, h->s);
-        else seg_axpy<double>(h->segt, act, L0.x64[L0.xfinal], x, h->s);
-        for (int q = 0; q < nseg; ++q) its[q] += active[q];
+        if (mixed) seg_axpy<float>(h->segt, c.run, L0.x32[L0.xfinal], x, h->s);
+        else seg_axpy<double>(h->segt, c.run, L0.x64[L0.xfinal], x, h->s);
     }
-    CU(cudaStreamSynchronize(h->s));
-    int worst = 0;
-    for (int q = 0; q < nseg; ++q) {
-        if (iters) iters[q] = its[q];
-        if (rel) rel[q] = rl[q];
-        if (st == LAIR_OK && !(rl[q] <= tol)) { st = LAIR_ERR_NOT_CONVERGED; worst = q; }
-    }
-    if (st == LAIR_ERR_NOT_CONVERGED) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
-    return st;
+    return batch_finish(h, tol, iters, rel);
 }
 
 // batched systems, right-preconditioned FGMRES(m) per system in lockstep: one Arnoldi step for
@@ -2147,65 +2333,46 @@ static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, d
 // system with its own Givens rotations, stopping test and restarts
 static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
                                         int *iters, double *rel) {
-    constexpr int HS = 32;
+    constexpr int HS = BATCH_HS;
     Level &L0 = H.lev[0];
     const DCsr &A = L0.A;
     const int n = A.nr, nseg = h->nseg;
     const int m = h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30;
     TRY(ensure_work(h, n, m));
     TRY(ensure_tiles(h, L0));
-    if (!h->d_bat) {
-        TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
-        TRY(dalloc(h, &h->d_batcnt, (size_t)nseg));
-        CU(cudaMallocHost(&h->h_bat, sizeof(double) * nseg * HS));
-        CU(cudaMallocHost(&h->h_batcnt, sizeof(int) * nseg));
-    }
+    TRY(ensure_batch_ctl(h, m));
+    if (!h->d_bat) TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
     double *hsum = h->d_bat, *hbuf = hsum + (size_t)nseg * HS, *ydev = hbuf + (size_t)nseg * HS,
            *nrm = ydev + (size_t)nseg * HS;
     double *V = h->V, *Z = h->Z;
-    // the Arnoldi kernels skip the tiles of systems that are not running
-    uint8_t *dact;
-    TRY(dalloc(h, &dact, (size_t)nseg));
-    SegTiles sta = h->segt;
-    sta.active = dact;
-    auto upload_running = [&](const std::vector<char> &run) -> lair_status {
-        CU(cudaStreamSynchronize(h->s));   // h_act may still feed the previous copy
-        for (int q = 0; q < nseg; ++q) h->h_act[q] = run[q] ? 1 : 0;
-        CU(cudaMemcpyAsync(dact, h->h_act, (size_t)nseg, cudaMemcpyHostToDevice, h->s));
-        return LAIR_OK;
-    };
-    std::vector<double> bn(nseg), rl(nseg, 0.0), beta(nseg);
-    std::vector<int> its(nseg, 0), jd(nseg, 0);
-    std::vector<char> done(nseg, 0), running(nseg, 0);
-    std::vector<double> Hm((size_t)nseg * (m + 1) * m), cs((size_t)nseg * m), sn((size_t)nseg * m), g((size_t)nseg * (m + 1));
+    BatchCtl c = h->bctl;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    SegTiles sta = h->segt;   // the Arnoldi kernels skip the tiles of systems that are not running
+    sta.active = c.run;
     seg_norm2(h->segt, b, nrm, h->s);
-    CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-    CU(cudaStreamSynchronize(h->s));
-    for (int q = 0; q < nseg; ++q) bn[q] = h->h_seg[q] > 0.0 ? std::sqrt(h->h_seg[q]) : 1.0;
-    lair_status st = LAIR_OK;
-    for (;;) {
+    bat_bnorm(nseg, nrm, const_cast<double *>(c.bn), h->s);
+    CU(cudaMemsetAsync(c.its, 0, sizeof(int) * nseg, h->s));
+    CU(cudaMemsetAsync(c.done, 0, (size_t)nseg, h->s));
+    CU(cudaMemsetAsync(c.nan, 0, sizeof(int), h->s));
+    long long step = 0;   // ring position
+    for (int restart = 0; restart <= max_iter; ++restart) {
         seg_residual(A, h->segt, b, x, V, nullptr, nrm, h->s);
-        CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-        CU(cudaStreamSynchronize(h->s));
+        CU(cudaMemsetAsync(ring_slot(h, step), 0, sizeof(int), h->s));
+        bat_fg_restart(c, nrm, ring_slot(h, step), h->s);
+        TRY(ring_post(h, step));
+        int running = 0;
+        TRY(ring_read(h, step, &running));   // one wait per restart
+        ++step;
         flush_timers(h);
-        int any = 0;
-        for (int q = 0; q < nseg; ++q) {
-            beta[q] = std::sqrt(h->h_seg[q]);
-            rl[q] = beta[q] / bn[q];
-            if (!std::isfinite(rl[q])) { st = LAIR_ERR_NAN; done[q] = 1; }
-            if (rl[q] <= tol || its[q] >= max_iter) done[q] = 1;
-            running[q] = !done[q];
-            jd[q] = 0;
-            any |= running[q];
-            if (running[q]) {
-                std::fill(&g[(size_t)q * (m + 1)], &g[(size_t)q * (m + 1)] + (m + 1), 0.0);
-                g[(size_t)q * (m + 1)] = beta[q];
-            }
-        }
-        if (!any) break;
-        TRY(upload_running(running));
+        if (running == 0) break;
         seg_scale(sta, V, nrm, V, h->s);
+        const long long first = step;
         for (int j = 0; j < m; ++j) {
+            if (step - first >= lair_handle::LAG) {
+                TRY(ring_read(h, step - lair_handle::LAG, &running));
+                if (running == 0) break;
+            }
             double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
             TRY(precond(h, H, vj, zj));
             int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
@@ -2218,66 +2385,16 @@ static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b
             }
             seg_norm2(sta, w, nrm, h->s);
             seg_scale(sta, w, nrm, w, h->s);
-            CU(cudaMemcpyAsync(h->h_bat, hsum, sizeof(double) * (size_t)nseg * HS, cudaMemcpyDeviceToHost, h->s));
-            CU(cudaMemcpyAsync(h->h_seg, nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-            CU(cudaStreamSynchronize(h->s));
-            flush_timers(h);
-            int still = 0;
-            for (int q = 0; q < nseg; ++q) {
-                if (!running[q]) continue;
-                double hc[HS + 1];
-                for (int k = 0; k <= j; ++k) hc[k] = h->h_bat[(size_t)q * HS + k];
-                const double hn = std::sqrt(h->h_seg[q]);
-                hc[j + 1] = hn;
-                double *csq = &cs[(size_t)q * m], *snq = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
-                for (int k = 0; k < j; ++k) {
-                    double t = csq[k] * hc[k] + snq[k] * hc[k + 1];
-                    hc[k + 1] = -snq[k] * hc[k] + csq[k] * hc[k + 1];
-                    hc[k] = t;
-                }
-                double den = std::sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
-                csq[j] = den > 0.0 ? hc[j] / den : 1.0;
-                snq[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
-                hc[j] = den;
-                gq[j + 1] = -snq[j] * gq[j];
-                gq[j] = csq[j] * gq[j];
-                for (int k = 0; k <= j; ++k) Hm[(size_t)q * (m + 1) * m + (size_t)k * m + j] = hc[k];
-                its[q] += 1;
-                const double est = std::fabs(gq[j + 1]) / bn[q];
-                if (est <= tol || hn == 0.0 || !std::isfinite(est) || its[q] >= max_iter || j == m - 1) {
-                    running[q] = 0;
-                    jd[q] = j + 1;
-                } else {
-                    still = 1;
-                }
-            }
-            if (!still) break;
-            TRY(upload_running(running));
+            CU(cudaMemsetAsync(ring_slot(h, step), 0, sizeof(int), h->s));
+            bat_fg_givens(c, j, hsum, nrm, ring_slot(h, step), h->s);
+            TRY(ring_post(h, step));
+            ++step;
         }
-        // per-system least-squares solutions y and the update x += Z y
-        for (int q = 0; q < nseg; ++q) {
-            h->h_batcnt[q] = jd[q];
-            const double *Hq = &Hm[(size_t)q * (m + 1) * m], *gq = &g[(size_t)q * (m + 1)];
-            double *yq = h->h_bat + (size_t)q * HS;
-            for (int k = jd[q] - 1; k >= 0; --k) {
-                double acc = gq[k];
-                for (int c = k + 1; c < jd[q]; ++c) acc -= Hq[(size_t)k * m + c] * yq[c];
-                yq[k] = acc / Hq[(size_t)k * m + k];
-            }
-        }
-        CU(cudaMemcpyAsync(ydev, h->h_bat, sizeof(double) * (size_t)nseg * HS, cudaMemcpyHostToDevice, h->s));
-        CU(cudaMemcpyAsync(h->d_batcnt, h->h_batcnt, sizeof(int) * nseg, cudaMemcpyHostToDevice, h->s));
-        seg_add_combo(h->segt, h->d_batcnt, Z, n, HS, ydev, x, h->s);
+        // per-system least-squares solutions y and the update x += Z y of the systems that ran
+        bat_fg_solve_y(c, ydev, h->s);
+        seg_add_combo(h->segt, c.jd, Z, n, HS, ydev, x, h->s);
     }
-    CU(cudaStreamSynchronize(h->s));
-    int worst = -1;
-    for (int q = 0; q < nseg; ++q) {
-        if (iters) iters[q] = its[q];
-        if (rel) rel[q] = rl[q];
-        if (st == LAIR_OK && !(rl[q] <= tol)) { st = LAIR_ERR_NOT_CONVERGED; worst = q; }
-    }
-    if (worst >= 0) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
-    return st;
+    return batch_finish(h, tol, iters, rel);
 }
 
 static void fill_report(lair_handle *h, Hier &H, lair_report *rep) {
@@ -2800,6 +2917,9 @@ void lair_free(lair_handle *h) {
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->own) cudaStreamDestroy(h->own);
     if (h->h_bat) cudaFreeHost(h->h_bat);
+    if (h->h_ring) cudaFreeHost(h->h_ring);
+    for (cudaEvent_t e : h->ring_ev)
+        if (e) cudaEventDestroy(e);
     if (h->h_batcnt) cudaFreeHost(h->h_batcnt);
     if (h->h_seg) cudaFreeHost(h->h_seg);
     if (h->h_act) cudaFreeHost(h->h_act);

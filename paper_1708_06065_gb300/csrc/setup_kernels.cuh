@@ -39,9 +39,9 @@ void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcn
 constexpr int RSB_MAX_N = 8192;
 constexpr int RSB_MAX_DIRTY = 8192;
 void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Graph &ST, int *out, cudaStream_t s);
-cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, int max_inblock, const Graph &S,
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
                              const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
-size_t rsb_smem_bytes(int n, int nb, int dl, int max_inblock);
+size_t rsb_smem_bytes(int n, int nb, int dl);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
                       int8_t *cf, int *status, cudaStream_t s);
 size_t rs_smem_bytes(int n, int max_inblock);
@@ -76,9 +76,21 @@ struct LocalArgs {
 constexpr int LOCAL_CTA_GRID = 152 * 2;
 // bins of the local systems by size (s <= 6, <= 32, larger); with stride > 1 entry c of the lists is the group
 // of rows c * stride .. c * stride + stride - 1 (one set), sized by its first row
-void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride = 1);
+// launch schedule of the local solves: systems of size s <= tmax go to one thread each, tmax < s <= wmax to
+// one warp each, larger ones to one CTA each; grid caps and block size of those kernels. Every system is
+// solved by the same sequence of operations whatever team takes it, so results do not depend on it.
+constexpr int THREAD_SMAX = 6;    // largest system a thread team holds in registers
+struct LocalSchedule {
+    int tmax = THREAD_SMAX;       // 0..THREAD_SMAX
+    int wmax = 32;                // tmax..32
+    int warp_blocks_per_sm = 8;   // grid cap of the warp kernel (4 warps per block)
+    int thread_tb = 128;          // threads per block of the thread kernel
+};
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride = 1,
+                      int tmax = THREAD_SMAX, int wmax = 32);
 cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
-                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s);
+                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s,
+                                const LocalSchedule &sch = LocalSchedule());
 size_t local_cta_scratch_bytes(int smax, bool fp32);
 void launch_onepoint(int phase, const DCsr &A, const uint8_t *mask, const int8_t *cf, const int *cidx, int absmode,
                      int *choice, int *cnt, DCsr *P, cudaStream_t s);
@@ -221,5 +233,24 @@ void seg_add_combo(const SegTiles &st, const int *cnt, const double *Z, long lon
                    cudaStream_t s);
 void seg_scale(const SegTiles &st, const double *v, const double *nrm2, double *out, cudaStream_t s);
 void gather_int(int m, const int *idx, const int *src, int *out, cudaStream_t s);
+// device-side state of the batched outer loops (one entry per system; see solve_kernels.cu)
+constexpr int BATCH_HS = 32;      // Hessenberg column stride: restart lengths up to 31
+struct BatchCtl {
+    int nseg = 0, m = 0, hs = BATCH_HS, max_iter = 0;
+    double tol = 0.0;
+    const double *bn = nullptr;   // ||b_q|| (1 where b_q = 0)
+    double *rl = nullptr;         // relative residual at the last check
+    int *its = nullptr;           // cycles applied
+    uint8_t *run = nullptr;       // still iterating (the tile kernels' active flags)
+    uint8_t *done = nullptr;      // FGMRES: stopped for good
+    int *jd = nullptr;            // FGMRES: steps of the current restart
+    double *g = nullptr, *cs = nullptr, *sn = nullptr, *Hm = nullptr;   // FGMRES: (m + 1), m, m, (m + 1) m each
+    int *nan = nullptr;           // set when a norm is not finite
+};
+void bat_bnorm(int nseg, const double *nrm2, double *bn, cudaStream_t s);
+void bat_stat_check(const BatchCtl &c, const double *nrm2, int it, int *count, cudaStream_t s);
+void bat_fg_restart(const BatchCtl &c, const double *nrm2, int *count, cudaStream_t s);
+void bat_fg_givens(const BatchCtl &c, int j, const double *hsum, const double *nrm2w, int *count, cudaStream_t s);
+void bat_fg_solve_y(const BatchCtl &c, double *y, cudaStream_t s);
 
 }  // namespace lair

@@ -466,8 +466,6 @@ __device__ void solve_rows_shared(const Team &tm, const LocalArgs &a, int q, T *
 // ---------------------------------------------------------------------------------------
 // bin kernels
 // ---------------------------------------------------------------------------------------
-constexpr int THREAD_SMAX = 6;
-
 // SHARED: the lists hold groups of rows that share one set (solve_rows_shared); a separate instantiation,
 // so that the one-row kernels keep their register budget
 template <class T, bool SHARED>
@@ -511,7 +509,7 @@ __global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__res
 }
 
 __global__ void k_local_bin(int nc, int group, const int *__restrict__ nb_rp, int *__restrict__ lists,
-                            int *__restrict__ counts, int *__restrict__ smax) {
+                            int *__restrict__ counts, int *__restrict__ smax, int tmax, int wmax) {
     const unsigned lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     int local_max = 0;
@@ -519,7 +517,7 @@ __global__ void k_local_bin(int nc, int group, const int *__restrict__ nb_rp, in
         const int c = (int)(base + lane);
         const bool act = c < nc;
         const int s = act ? nb_rp[(long long)c * group + 1] - nb_rp[(long long)c * group] : 0;
-        const int b = s <= THREAD_SMAX ? 0 : (s <= 32 ? 1 : 2);
+        const int b = s <= tmax ? 0 : (s <= wmax ? 1 : 2);
         local_max = max(local_max, s);
         for (int bb = 0; bb < 3; ++bb) {       // one atomic per warp and bin
             const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
@@ -534,22 +532,27 @@ __global__ void k_local_bin(int nc, int group, const int *__restrict__ nb_rp, in
     if (lane == 0 && local_max > 0) atomicMax(smax, local_max);
 }
 
-void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride) {
-    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, stride, nb_rp, lists, counts, smax);
+void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride,
+                      int tmax, int wmax) {
+    tmax = tmax < 0 ? 0 : (tmax > THREAD_SMAX ? THREAD_SMAX : tmax);
+    wmax = wmax < tmax ? tmax : (wmax > 32 ? 32 : wmax);
+    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, stride, nb_rp, lists, counts, smax, tmax, wmax);
     count_launch();
 }
 
 template <class T, bool SHARED>
 static void local_solves_t(const LocalArgs &a, int nc, const int *lists, const int *counts_dev, const int counts_host[3],
-                           int smax, void *scratch, cudaStream_t s) {
+                           int smax, void *scratch, cudaStream_t s, const LocalSchedule &sch) {
     if (counts_host[0] > 0) {
-        k_local_thread<T, SHARED><<<grid_for(counts_host[0], 128), 128, 0, s>>>(a, lists, counts_dev);
+        const int tb = sch.thread_tb > 0 ? sch.thread_tb : 128;
+        k_local_thread<T, SHARED><<<grid_for(counts_host[0], tb), tb, 0, s>>>(a, lists, counts_dev);
         count_launch();
     }
     if (counts_host[1] > 0) {
         const size_t bytes = 4 * sizeof(T) * (2 * 32 * 32 + 3 * 32);
         cudaFuncSetAttribute(k_local_warp<T, SHARED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        k_local_warp<T, SHARED><<<grid_for(counts_host[1], 4, device_sms() * 8), 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
+        const int cap = device_sms() * (sch.warp_blocks_per_sm > 0 ? sch.warp_blocks_per_sm : 8);
+        k_local_warp<T, SHARED><<<grid_for(counts_host[1], 4, cap), 128, bytes, s>>>(a, lists + nc, counts_dev + 1);
         count_launch();
     }
     if (counts_host[2] > 0) {
@@ -560,14 +563,15 @@ static void local_solves_t(const LocalArgs &a, int nc, const int *lists, const i
 }
 
 cudaError_t launch_local_solves(const LocalArgs &a, int nc, const int *lists, const int *counts_dev,
-                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s) {
+                                const int counts_host[3], int smax, bool fp32, void *scratch, cudaStream_t s,
+                                const LocalSchedule &sch) {
     const bool shared = a.rows_per > 1;
     if (fp32) {
-        if (shared) local_solves_t<float, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
-        else local_solves_t<float, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
+        if (shared) local_solves_t<float, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s, sch);
+        else local_solves_t<float, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s, sch);
     } else {
-        if (shared) local_solves_t<double, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
-        else local_solves_t<double, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s);
+        if (shared) local_solves_t<double, true>(a, nc, lists, counts_dev, counts_host, smax, scratch, s, sch);
+        else local_solves_t<double, false>(a, nc, lists, counts_dev, counts_host, smax, scratch, s, sch);
     }
     return cudaGetLastError();
 }

@@ -583,6 +583,131 @@ __global__ void __launch_bounds__(256) k_tile_axpy(SegTiles st, const uint8_t *_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// device-side control of the batched outer loops: one thread per system decides, from the
+// per-system norms the tile kernels reduced, whether the system goes on, and keeps its Krylov
+// state; the flags feed the tile kernels (SegTiles.active) of the next step directly, so the
+// host never has to read a norm to continue. count (zero on entry) receives the number of
+// systems still running. The arithmetic of the stopping tests and Givens rotations is the
+// oracle's (separate roundings, no fused operations).
+// ---------------------------------------------------------------------------------------
+__global__ void k_bat_bnorm(int nseg, const double *__restrict__ nrm2, double *__restrict__ bn) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nseg) bn[q] = nrm2[q] > 0.0 ? sqrt(nrm2[q]) : 1.0;
+}
+
+// stationary refinement, iteration it: from ||r_q||^2, deactivate converged systems; count the running ones
+// (each running system then receives one more cycle)
+__global__ void k_bat_stat_check(BatchCtl c, const double *__restrict__ nrm2, int it, int *count) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c.nseg || !c.run[q]) return;
+    const double r = __ddiv_rn(sqrt(nrm2[q]), c.bn[q]);
+    c.rl[q] = r;
+    if (!isfinite(r)) {
+        *c.nan = 1;
+        c.run[q] = 0;
+        return;
+    }
+    if (r <= c.tol || it >= c.max_iter) {
+        c.run[q] = 0;
+        return;
+    }
+    c.its[q] += 1;
+    atomicAdd(count, 1);
+}
+
+// FGMRES restart: beta = ||r_q||, the stopping test on it, g = beta e_1 for the systems that go on
+__global__ void k_bat_fg_restart(BatchCtl c, const double *__restrict__ nrm2, int *count) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c.nseg) return;
+    c.jd[q] = 0;
+    const double beta = sqrt(nrm2[q]);
+    const double r = __ddiv_rn(beta, c.bn[q]);
+    c.rl[q] = r;
+    if (!isfinite(r)) {
+        *c.nan = 1;
+        c.done[q] = 1;
+    }
+    if (r <= c.tol || c.its[q] >= c.max_iter) c.done[q] = 1;
+    c.run[q] = c.done[q] ? 0 : 1;
+    if (!c.run[q]) return;
+    double *g = c.g + (size_t)q * (c.m + 1);
+    for (int k = 0; k <= c.m; ++k) g[k] = 0.0;
+    g[0] = beta;
+    atomicAdd(count, 1);
+}
+
+// FGMRES step j of every running system: the new Hessenberg column (the Gram-Schmidt sums h[q * hs + k],
+// k <= j, and ||w||), the earlier rotations applied to it, a new rotation, the residual estimate and the
+// stopping test; a system that stops keeps its step count in jd
+__global__ void k_bat_fg_givens(BatchCtl c, int j, const double *__restrict__ hsum, const double *__restrict__ nrm2w,
+                                int *count) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c.nseg || !c.run[q]) return;
+    const int m = c.m;
+    double hc[BATCH_HS + 1];
+    for (int k = 0; k <= j; ++k) hc[k] = hsum[(size_t)q * c.hs + k];
+    const double hn = sqrt(nrm2w[q]);
+    hc[j + 1] = hn;
+    double *cs = c.cs + (size_t)q * m, *sn = c.sn + (size_t)q * m, *g = c.g + (size_t)q * (m + 1);
+    double *Hq = c.Hm + (size_t)q * (m + 1) * m;
+    for (int k = 0; k < j; ++k) {
+        const double t = __dadd_rn(__dmul_rn(cs[k], hc[k]), __dmul_rn(sn[k], hc[k + 1]));
+        hc[k + 1] = __dadd_rn(__dmul_rn(-sn[k], hc[k]), __dmul_rn(cs[k], hc[k + 1]));
+        hc[k] = t;
+    }
+    const double den = sqrt(__dadd_rn(__dmul_rn(hc[j], hc[j]), __dmul_rn(hc[j + 1], hc[j + 1])));
+    cs[j] = den > 0.0 ? __ddiv_rn(hc[j], den) : 1.0;
+    sn[j] = den > 0.0 ? __ddiv_rn(hc[j + 1], den) : 0.0;
+    hc[j] = den;
+    g[j + 1] = __dmul_rn(-sn[j], g[j]);
+    g[j] = __dmul_rn(cs[j], g[j]);
+    for (int k = 0; k <= j; ++k) Hq[(size_t)k * m + j] = hc[k];
+    c.its[q] += 1;
+    const double est = __ddiv_rn(fabs(g[j + 1]), c.bn[q]);
+    if (est <= c.tol || hn == 0.0 || !isfinite(est) || c.its[q] >= c.max_iter || j == m - 1) {
+        c.run[q] = 0;
+        c.jd[q] = j + 1;
+    } else {
+        atomicAdd(count, 1);
+    }
+}
+
+// y_q = H_q^{-1} g_q (upper triangular, jd_q x jd_q) for the update x += Z y
+__global__ void k_bat_fg_solve_y(BatchCtl c, double *__restrict__ y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c.nseg) return;
+    const int jd = c.jd[q], m = c.m;
+    const double *Hq = c.Hm + (size_t)q * (m + 1) * m, *g = c.g + (size_t)q * (m + 1);
+    double *yq = y + (size_t)q * c.hs;
+    for (int k = jd - 1; k >= 0; --k) {
+        double acc = g[k];
+        for (int cc = k + 1; cc < jd; ++cc) acc = __dsub_rn(acc, __dmul_rn(Hq[(size_t)k * m + cc], yq[cc]));
+        yq[k] = __ddiv_rn(acc, Hq[(size_t)k * m + k]);
+    }
+}
+
+void bat_bnorm(int nseg, const double *nrm2, double *bn, cudaStream_t s) {
+    k_bat_bnorm<<<(nseg + 127) / 128, 128, 0, s>>>(nseg, nrm2, bn);
+    count_launch();
+}
+void bat_stat_check(const BatchCtl &c, const double *nrm2, int it, int *count, cudaStream_t s) {
+    k_bat_stat_check<<<(c.nseg + 127) / 128, 128, 0, s>>>(c, nrm2, it, count);
+    count_launch();
+}
+void bat_fg_restart(const BatchCtl &c, const double *nrm2, int *count, cudaStream_t s) {
+    k_bat_fg_restart<<<(c.nseg + 127) / 128, 128, 0, s>>>(c, nrm2, count);
+    count_launch();
+}
+void bat_fg_givens(const BatchCtl &c, int j, const double *hsum, const double *nrm2w, int *count, cudaStream_t s) {
+    k_bat_fg_givens<<<(c.nseg + 127) / 128, 128, 0, s>>>(c, j, hsum, nrm2w, count);
+    count_launch();
+}
+void bat_fg_solve_y(const BatchCtl &c, double *y, cudaStream_t s) {
+    k_bat_fg_solve_y<<<(c.nseg + 127) / 128, 128, 0, s>>>(c, y);
+    count_launch();
+}
+
 static int seg_grid(const SegTiles &st) { return st.ntiles < SEG_GRID ? (st.ntiles > 0 ? st.ntiles : 1) : SEG_GRID; }
 
 static void seg_reduce(const SegTiles &st, int pw, int m, int hs, int k0, double *out, double *acc, cudaStream_t s) {

@@ -2,7 +2,8 @@
 
 The DG workload at full size (786,432 unknowns: PMIS through the cooperative kernel, distance-2
 neighbourhoods with CTA-team local solves on the coarse levels, one-point P, block scaling,
-mixed precision); the 3D FD workload at 96^3 (884,736 unknowns, blocked first pass, lAIP); and
+mixed precision); the 3D FD workload at 96^3 (884,736 unknowns, PMIS, one-point P with the
+thread-per-row fused Galerkin product); and
 the first 16 systems of the batched workload (sides up to 243). Every level's integer structure
 must equal the oracle's bit for bit and its values must agree within 1e-5 of the row's largest
 entry (FP32 local solves); one V-cycle is compared entry by entry, within 1e-5 of the largest
@@ -33,7 +34,7 @@ def lair():
 
 def oracle_kw(kw):
     m = dict(cf_mode="cf_mode", distance="distance", strength_abs="strength_abs", interp="interp",
-             block_size="block_size", precision="prec")
+             block_size="block_size", precision="prec", lump_tol="lump_tol", theta="theta")
     return {m[k]: v for k, v in kw.items()}
 
 
