@@ -63,9 +63,12 @@ def parse():
                    help="override a solver option of the workload (lair.Hierarchy keyword, numeric value)")
     p.add_argument("--cycle", default=None, choices=["fgmres", "stationary"],
                    help="outer iteration (default: the workload's, FGMRES(30))")
+    p.add_argument("--scale", type=int, default=None,
+                   help="grid side (mesh side, system count) of a smaller case of the workload, for profiling")
     p.add_argument("--timing", type=int, default=1, choices=[1, 2],
                    help="2: also time every set-up phase per level (setup_phases_ms gets one entry per phase and level)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison (profiling runs)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-refresh", action="store_true", help="skip the time-stepping (refresh + solve) measurement")
     p.add_argument("--nodal", action="store_true",
@@ -298,7 +301,7 @@ def main():
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
     wl = WORKLOADS[args.workload]
-    s = W.config(args.workload)
+    s = W.config(args.workload, scale=args.scale)
     offs = None
     sharded = bool(wl.get("batched")) and dist.world > 1
     if wl.get("batched"):
@@ -416,11 +419,14 @@ def main():
     x_mixed = x.cpu().numpy()
 
     # ---- plain FP64 path, same protocol
-    run_steps(1, lair.FP64, False)
-    t64, it64, rel64, _, _, su64 = run_steps(args.steps, lair.FP64, True)
-    ms64 = dist.max(sum(t64) / len(t64))
-    x_fp64 = x.cpu().numpy()
-    err_vs_fp64 = float(np.linalg.norm(x_mixed - x_fp64) / np.linalg.norm(x_fp64))
+    ms64 = err_vs_fp64 = None
+    t64 = it64 = rel64 = su64 = None
+    if not args.no_fp64:
+        run_steps(1, lair.FP64, False)
+        t64, it64, rel64, _, _, su64 = run_steps(args.steps, lair.FP64, True)
+        ms64 = dist.max(sum(t64) / len(t64))
+        x_fp64 = x.cpu().numpy()
+        err_vs_fp64 = float(np.linalg.norm(x_mixed - x_fp64) / np.linalg.norm(x_fp64))
 
     # ---- end to end through host buffers (pinned), mixed
     e2e = None
@@ -502,7 +508,7 @@ def main():
     cpu = None
     err_vs_oracle = None
     if not args.no_cpu and dist.rank == 0 and dist.world == 1:
-        full = None if wl.get("batched") else oracle_run(args.workload, wl["opts"])
+        full = None if wl.get("batched") else oracle_run(args.workload, wl["opts"], scale=args.scale)
         one = oracle_run(args.workload, wl["opts"], scale=wl["sample_scale"], threads=1, budget_s=10.0)
         main_r = full or oracle_run(args.workload, wl["opts"], scale=wl["reference_scale"])
         cpu = {"value": main_r["value"], "unit": "unknowns/s", "cores": main_r["threads"], "nproc": os.cpu_count(),
@@ -531,14 +537,15 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
         "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f32 cycle + f64 outer (mixed)", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "nnz": nnz, "parallelism": "systems split by LPT" if sharded else "replicas", "sharded_batch": batch,
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "nnz": nnz, "scale": args.scale, "parallelism": "systems split by LPT" if sharded else "replicas", "sharded_batch": batch,
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB written before every step (untimed); matrix alone is "
                          f"{(nnz * 12 + n * 8) / 1e6:.0f} MB > 129 MB L2"},
         "mixed": {"value": value, "ms_per_step": ms_mixed, "setup_ms": dist.max(sum(su_mixed) / len(su_mixed)),
                   "iters": it_mixed, "final_rel": max(rel_mixed)},
-        "fp64": {"value": n_job / (ms64 / 1e3), "ms_per_step": ms64, "setup_ms": dist.max(sum(su64) / len(su64)),
-                 "iters": it64, "final_rel": max(rel64)},
-        "mixed_over_fp64": ms64 / ms_mixed,
+        "fp64": None if ms64 is None else {"value": n_job / (ms64 / 1e3), "ms_per_step": ms64,
+                                           "setup_ms": dist.max(sum(su64) / len(su64)), "iters": it64,
+                                           "final_rel": max(rel64)},
+        "mixed_over_fp64": None if ms64 is None else ms64 / ms_mixed,
         "err_vs_fp64": err_vs_fp64,
         "err_vs_oracle": err_vs_oracle,
         "cold_setup_ms": su_cold[0] if su_cold else None,

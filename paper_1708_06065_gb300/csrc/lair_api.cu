@@ -762,7 +762,8 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
     TRY(new_counts(h, t, &bc, SPGEMM_BINS + 2));
     // thread-per-row merging needs many rows to keep the GPU busy; short products stay on warps
     const bool merge = nr >= SPGEMM_MERGE_MIN_ROWS;
-    launch_spgemm_classify(nr, off, X.rp, merge, merge && P == nullptr, lists, bc, bc + SPGEMM_BINS, h->s);
+    launch_spgemm_classify(nr, off, X.rp, merge, merge && P == nullptr, P ? SPGEMM_P1_CAP : 0x7fffffff, lists, bc,
+                           bc + SPGEMM_BINS, h->s);
     // one read-back: bin counts, largest bound, and the total bound (staging size)
     CU(cudaMemcpyAsync(bc + SPGEMM_BINS + 1, off + nr, sizeof(int), cudaMemcpyDeviceToDevice, h->s));
     int hc[SPGEMM_BINS + 2];
@@ -1587,10 +1588,11 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int2> g_tune;
-// (threads per block, grid cap in blocks per SM); the first is the default schedule
-const int2 kTuneCandidates[] = {{256, 16}, {256, 4}, {256, 8},  {256, 32},
-                                {128, 8},  {128, 16}, {128, 32}, {128, 64}};
+std::map<TuneKey, int3> g_tune;
+// (threads per block, grid cap in blocks per SM, rows per thread); the first is the default schedule
+const int3 kTuneCandidates[] = {{256, 16, 1}, {256, 4, 1}, {256, 8, 1},  {256, 32, 1}, {128, 8, 1},
+                                {128, 16, 1}, {128, 32, 1}, {128, 64, 1}, {256, 16, 2}, {256, 32, 2},
+                                {128, 32, 2}, {128, 64, 2}};
 }  // namespace
 
 template <class T>
@@ -1626,6 +1628,7 @@ static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0
             if (it != g_tune.end()) {
                 v.tb = it->second.x;
                 v.grid = it->second.y;
+                v.rpt = it->second.z;
                 continue;
             }
         }
@@ -1639,11 +1642,12 @@ static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0
         }
         float best = 3.4e38f, base = 3.4e38f;
         const int sms = device_sms();
-        int2 pick = make_int2(kTuneCandidates[0].x, kTuneCandidates[0].y * sms);
-        for (const int2 &c : kTuneCandidates) {
-            const int2 cand = make_int2(c.x, c.y * sms);
+        int3 pick = make_int3(kTuneCandidates[0].x, kTuneCandidates[0].y * sms, kTuneCandidates[0].z);
+        for (const int3 &c : kTuneCandidates) {
+            const int3 cand = make_int3(c.x, c.y * sms, c.z);
             v.tb = cand.x;
             v.grid = cand.y;
+            v.rpt = cand.z;
             run(kind);   // warm
             float tmin = 3.4e38f;
             for (int rep = 0; rep < 5; ++rep) {
@@ -1661,9 +1665,10 @@ static lair_status autotune_level(lair_handle *h, Hier &H, int l, cudaEvent_t e0
                 pick = cand;
             }
         }
-        if (!(best < 0.95f * base)) pick = make_int2(kTuneCandidates[0].x, kTuneCandidates[0].y * sms);
+        if (!(best < 0.95f * base)) pick = make_int3(kTuneCandidates[0].x, kTuneCandidates[0].y * sms, kTuneCandidates[0].z);
         v.tb = pick.x;
         v.grid = pick.y;
+        v.rpt = pick.z;
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune[key] = pick;
     }

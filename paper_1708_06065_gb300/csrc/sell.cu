@@ -123,45 +123,93 @@ __global__ void k_sell_fill_multi(const SellDesc *__restrict__ d, int p0, int p1
     }
 }
 
-// y[row[r]] = (view row r) . x
-template <class T>
+// y[row[r]] = (view row r) . x. RPT rows per thread: the thread of lane l in group g takes row l of each of
+// the slices g RPT, ..., g RPT + RPT - 1, so every load of a warp stays coalesced and a thread keeps RPT
+// independent sums in flight; each row is still summed alone in column order.
+template <class T, int RPT>
 __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restrict__ x, T *__restrict__ y) {
     const int *__restrict__ sptr = v.slice_ptr;
     const int *__restrict__ scol = v.col;
     const T *__restrict__ sval = static_cast<const T *>(v.val);
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < v.nrows; r += gridDim.x * blockDim.x) {
-        const int s = r >> 5;
-        const int base = __ldg(sptr + s) + (r & 31);
-        const int len = (__ldg(sptr + s + 1) - __ldg(sptr + s)) >> 5;
-        T acc = T(0);
+    const int nsl = (v.nrows + 31) >> 5;
+    const long long nthr = (long long)((nsl + RPT - 1) / RPT) * 32;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < nthr; u += (long long)gridDim.x * blockDim.x) {
+        const int lane = (int)(u & 31), s0 = (int)(u >> 5) * RPT;
+        int base[RPT], len[RPT], r[RPT];
+        int lmax = 0;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            r[k] = (s0 + k) * 32 + lane;
+            base[k] = 0;
+            len[k] = 0;
+            if (s0 + k < nsl) {
+                const int a = __ldg(sptr + s0 + k);
+                base[k] = a + lane;
+                len[k] = (__ldg(sptr + s0 + k + 1) - a) >> 5;
+            }
+            lmax = max(lmax, len[k]);
+        }
+        T acc[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) acc[k] = T(0);
 #pragma unroll 4
-        for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), __ldg(x + __ldg(scol + base + 32 * j)), acc);
-        y[v.row[r]] = acc;
+        for (int j = 0; j < lmax; ++j)
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (j < len[k])
+                    acc[k] = fma(__ldg(sval + base[k] + 32 * j), __ldg(x + __ldg(scol + base[k] + 32 * j)), acc[k]);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            if (r[k] < v.nrows) y[v.row[r[k]]] = acc[k];
     }
 }
 
-// one Jacobi sweep over the view's rows (x_i + d_i (b_i - A_i x)); threads beyond the view copy
-// the entries of the other rows (copy[], ncopy of them) from x to xo
-template <class T>
+// one Jacobi sweep over the view's rows (x_i + d_i (b_i - A_i x)), RPT rows per thread as above; then the
+// entries of the other rows (copy[], ncopy of them) are copied from x to xo, one per thread
+template <class T, int RPT>
 __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__restrict__ copy, int ncopy,
                                                     const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xo) {
     const int *__restrict__ sptr = v.slice_ptr;
     const int *__restrict__ scol = v.col;
     const T *__restrict__ sval = static_cast<const T *>(v.val);
     const T *__restrict__ sd = static_cast<const T *>(v.dinv);
-    const int total = v.nrows + ncopy;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
-        if (r < v.nrows) {
-            const int s = r >> 5;
-            const int base = __ldg(sptr + s) + (r & 31);
-            const int len = (__ldg(sptr + s + 1) - __ldg(sptr + s)) >> 5;
-            T acc = T(0);
+    const int nsl = (v.nrows + 31) >> 5;
+    const long long nthr = (long long)((nsl + RPT - 1) / RPT) * 32;
+    const long long total = nthr + ncopy;
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total; u += (long long)gridDim.x * blockDim.x) {
+        if (u < nthr) {
+            const int lane = (int)(u & 31), s0 = (int)(u >> 5) * RPT;
+            int base[RPT], len[RPT], r[RPT];
+            int lmax = 0;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                r[k] = (s0 + k) * 32 + lane;
+                base[k] = 0;
+                len[k] = 0;
+                if (s0 + k < nsl) {
+                    const int a = __ldg(sptr + s0 + k);
+                    base[k] = a + lane;
+                    len[k] = (__ldg(sptr + s0 + k + 1) - a) >> 5;
+                }
+                lmax = max(lmax, len[k]);
+            }
+            T acc[RPT];
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) acc[k] = T(0);
 #pragma unroll 4
-            for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), __ldg(x + __ldg(scol + base + 32 * j)), acc);
-            const int i = v.row[r];
-            xo[i] = fma(sd[r], b[i] - acc, x[i]);
+            for (int j = 0; j < lmax; ++j)
+#pragma unroll
+                for (int k = 0; k < RPT; ++k)
+                    if (j < len[k])
+                        acc[k] = fma(__ldg(sval + base[k] + 32 * j), __ldg(x + __ldg(scol + base[k] + 32 * j)), acc[k]);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (r[k] < v.nrows) {
+                    const int i = v.row[r[k]];
+                    xo[i] = fma(sd[r[k]], b[i] - acc[k], x[i]);
+                }
         } else {
-            const int j = copy[r - v.nrows];
+            const int j = copy[u - nthr];
             xo[j] = x[j];
         }
     }
@@ -235,9 +283,13 @@ void launch_sell_fill_multi(const SellDesc *d, int p0, int p1, int lin_beg, int 
 template <class T>
 void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s) {
     if (v.nrows <= 0) return;
-    // every row is one thread's, so the schedule (block size, grid cap) never changes the result
+    // every row is summed alone by one thread, so the schedule (block size, grid cap, rows per thread) never
+    // changes the result
     const int tb = v.tb > 0 ? v.tb : 256;
-    k_sell_spmv<T><<<grid_for(v.nrows, tb, v.grid > 0 ? v.grid : device_sms() * 16), tb, 0, s>>>(v, x, y);
+    const int cap = v.grid > 0 ? v.grid : device_sms() * 16;
+    const long long nsl = (v.nrows + 31) / 32;
+    if (v.rpt == 2) k_sell_spmv<T, 2><<<grid_for((nsl + 1) / 2 * 32, tb, cap), tb, 0, s>>>(v, x, y);
+    else k_sell_spmv<T, 1><<<grid_for(nsl * 32, tb, cap), tb, 0, s>>>(v, x, y);
     count_launch();
 }
 
@@ -245,8 +297,12 @@ template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s) {
     if (v.nrows + ncopy <= 0) return;
     const int tb = v.tb > 0 ? v.tb : 256;
-    k_sell_sweep<T><<<grid_for((long long)v.nrows + ncopy, tb, v.grid > 0 ? v.grid : device_sms() * 16), tb, 0, s>>>(
-        v, copy, ncopy, b, x, xo);
+    const int cap = v.grid > 0 ? v.grid : device_sms() * 16;
+    const long long nsl = (v.nrows + 31) / 32;
+    if (v.rpt == 2)
+        k_sell_sweep<T, 2><<<grid_for((nsl + 1) / 2 * 32 + ncopy, tb, cap), tb, 0, s>>>(v, copy, ncopy, b, x, xo);
+    else
+        k_sell_sweep<T, 1><<<grid_for(nsl * 32 + ncopy, tb, cap), tb, 0, s>>>(v, copy, ncopy, b, x, xo);
     count_launch();
 }
 

@@ -14,6 +14,7 @@ struct SellView {
     int *row = nullptr;         // view row -> matrix row
     void *dinv = nullptr;       // Jacobi diagonal per view row (sweep views), same type as val
     int tb = 0, grid = 0;       // launch schedule picked by the autotuner (0: 256 threads, grid capped at 16 blocks per SM)
+    int rpt = 1;                // rows per thread (1 or 2: rows of two consecutive slices, same lane)
 };
 
 // ---- setup_graph.cu -------------------------------------------------------------------
@@ -124,8 +125,11 @@ constexpr int SPGEMM_MERGE_MIN_ROWS = 65536;   // products with fewer rows use t
 void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, int *ub, cudaStream_t s);
 // merge: rows of X with at most SPGEMM_MERGE_K entries go to the thread-per-row merge bin; merge2: rows
 // with at most SPGEMM_MERGE_K2 to the second merge bin (plain products only)
-void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int *lists, int *counts,
-                            int *ubmax, cudaStream_t s);
+// (and, for the first merge bin, a bound of at most merge_ub_max products)
+void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int merge_ub_max,
+                            int *lists, int *counts, int *ubmax, cudaStream_t s);
+constexpr int SPGEMM_P1_CAP = 64;       // fused one-point merge: at most this many products per row
+constexpr int SPGEMM_P1_THREADS = 64;   // threads per block (their lists fill 48 KB of shared memory)
 // true if every row of the product fits the fused one-point-P kernels (bins 0 and 1, the first merge bin)
 bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,

@@ -30,7 +30,7 @@ __global__ void k_spgemm_ub(int nr, const int *__restrict__ xrp, const int *__re
 __device__ __forceinline__ int spgemm_bin(int u) { return u <= 128 ? 0 : (u <= 512 ? 1 : (u <= WARP_CAP / 2 ? 2 : 3)); }
 
 __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, const int *__restrict__ xrp, bool merge,
-                                  bool merge2, int *__restrict__ lists, int *__restrict__ counts,
+                                  bool merge2, int merge_ub_max, int *__restrict__ lists, int *__restrict__ counts,
                                   int *__restrict__ ubmax) {
     const unsigned lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -39,7 +39,7 @@ __global__ void k_spgemm_classify(int nr, const int *__restrict__ off, const int
         const bool act = a < nr;
         const int u = act ? off[a + 1] - off[a] : 0;
         const int xl = act ? xrp[a + 1] - xrp[a] : 0;
-        const int b = (merge && xl <= SPGEMM_MERGE_K) ? SPGEMM_BIN_MERGE
+        const int b = (merge && xl <= SPGEMM_MERGE_K && u <= merge_ub_max) ? SPGEMM_BIN_MERGE
                     : (merge2 && xl <= SPGEMM_MERGE_K2) ? SPGEMM_BIN_MERGE2 : spgemm_bin(u);
         for (int bb = 0; bb < SPGEMM_BINS; ++bb) {       // one atomic per warp and bin
             const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
@@ -107,50 +107,83 @@ __global__ void __launch_bounds__(K <= 8 ? 256 : 128) k_spgemm_merge(SpgemmArgs 
 }
 
 // The fused triple product X Y P for a one-point P (at most one entry per row), one thread per row of X
-// with at most K entries: row a of X Y is merged into the staging area in column order as above; its
-// entries (l, v), in ascending l, then add fma(v, p_l, .) to column P(l) of the result, kept in the same
-// staging area (each entry read adds at most one result column, so the results never overtake the
-// entries still to be read) and finally put in column order by insertion. Every result entry thus
+// with at most K entries and a bound ub <= SPGEMM_P1_CAP: row a of X Y is merged in column order as above,
+// and each entry (l, v), in ascending l, adds fma(v, p_l, .) to column P(l) of the result, which the thread
+// keeps as a short list in its own column of shared memory (entry e at e * blockDim + thread: no bank
+// conflicts); the list is put in column order by insertion and written out. Every result entry thus
 // receives its terms in ascending l, starting from 0: the fma sequence of the hashed fused kernels.
 template <int K>
-__global__ void __launch_bounds__(256) k_spgemm_merge_p1(SpgemmArgs g, const int *__restrict__ list,
-                                                         const int *__restrict__ count) {
+__global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArgs g, const int *__restrict__ list,
+                                                                       const int *__restrict__ count) {
+    __shared__ int lcol[SPGEMM_P1_CAP * SPGEMM_P1_THREADS];
+    __shared__ double lval[SPGEMM_P1_CAP * SPGEMM_P1_THREADS];
+    constexpr int T = SPGEMM_P1_THREADS;
+    int *mc = lcol + threadIdx.x;
+    double *mv = lval + threadIdx.x;
     const int n = *count;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const int a = list[t];
-        const int o = g.off[a];
-        int *col = g.tcol + o;
-        double *val = g.tval + o;
-        const int c = merge_row<K>(g, a, o);
+        const int xb = g.xrp[a], nk = g.xrp[a + 1] - xb;
+        int pos[K], end[K], cj[K];
+        double xv[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            pos[u] = 0;
+            end[u] = 0;
+            xv[u] = 0.0;
+            if (u < nk) {
+                const int k = g.xcol[xb + u];
+                pos[u] = g.yrp[k];
+                end[u] = g.yrp[k + 1];
+                xv[u] = g.xval[xb + u];
+            }
+            cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
+        }
         int nout = 0;
-        for (int e = 0; e < c; ++e) {
-            const int l = col[e];
-            const double v = val[e];
-            const int pb = g.prp[l];
-            if (g.prp[l + 1] == pb) continue;
+        for (;;) {
+            int j = 0x7fffffff;
+#pragma unroll
+            for (int u = 0; u < K; ++u) j = min(j, cj[u]);
+            if (j == 0x7fffffff) break;
+            double v = 0.0;
+#pragma unroll
+            for (int u = 0; u < K; ++u)
+                if (cj[u] == j) {
+                    v = __fma_rn(xv[u], g.yval[pos[u]], v);
+                    ++pos[u];
+                    cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
+                }
+            // (X Y)_aj = v is complete: its term of column P(j)
+            const int pb = g.prp[j];
+            if (g.prp[j + 1] == pb) continue;
             const int b = g.pcol[pb];
             const double pv = g.pval[pb];
             int f = 0;
-            while (f < nout && col[f] != b) ++f;
+            while (f < nout && mc[f * T] != b) ++f;
             if (f == nout) {
-                col[f] = b;
-                val[f] = __fma_rn(v, pv, 0.0);
+                mc[f * T] = b;
+                mv[f * T] = __fma_rn(v, pv, 0.0);
                 ++nout;
             } else {
-                val[f] = __fma_rn(v, pv, val[f]);
+                mv[f * T] = __fma_rn(v, pv, mv[f * T]);
             }
         }
         for (int x = 1; x < nout; ++x) {
-            const int kc = col[x];
-            const double kv = val[x];
+            const int kc = mc[x * T];
+            const double kv = mv[x * T];
             int y = x - 1;
-            while (y >= 0 && col[y] > kc) {
-                col[y + 1] = col[y];
-                val[y + 1] = val[y];
+            while (y >= 0 && mc[y * T] > kc) {
+                mc[(y + 1) * T] = mc[y * T];
+                mv[(y + 1) * T] = mv[y * T];
                 --y;
             }
-            col[y + 1] = kc;
-            val[y + 1] = kv;
+            mc[(y + 1) * T] = kc;
+            mv[(y + 1) * T] = kv;
+        }
+        const int o = g.off[a];
+        for (int e = 0; e < nout; ++e) {
+            g.tcol[o + e] = mc[e * T];
+            g.tval[o + e] = mv[e * T];
         }
         g.cnt[a] = nout;
     }
@@ -622,9 +655,10 @@ void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, i
     count_launch();
 }
 
-void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int *lists, int *counts,
-                            int *ubmax, cudaStream_t s) {
-    k_spgemm_classify<<<grid_for(nr, 256), 256, 0, s>>>(nr, off, xrp, merge, merge2, lists, counts, ubmax);
+void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int merge_ub_max,
+                            int *lists, int *counts, int *ubmax, cudaStream_t s) {
+    k_spgemm_classify<<<grid_for(nr, 256), 256, 0, s>>>(nr, off, xrp, merge, merge2, merge_ub_max, lists, counts,
+                                                        ubmax);
     count_launch();
 }
 
@@ -649,9 +683,9 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
         if (counts_host[0] > 0) launch_spgemm_bin<256, 8, true>(g, lists, counts_dev, counts_host[0], s);
         if (counts_host[1] > 0) launch_spgemm_bin<1024, 4, true>(g, lists + nr, counts_dev + 1, counts_host[1], s);
         if (counts_host[SPGEMM_BIN_MERGE] > 0) {
-            k_spgemm_merge_p1<SPGEMM_MERGE_K><<<grid_for(counts_host[SPGEMM_BIN_MERGE], 256, device_sms() * 16), 256, 0,
-                                                s>>>(g, lists + SPGEMM_BIN_MERGE * (size_t)nr,
-                                                     counts_dev + SPGEMM_BIN_MERGE);
+            k_spgemm_merge_p1<SPGEMM_MERGE_K>
+                <<<grid_for(counts_host[SPGEMM_BIN_MERGE], SPGEMM_P1_THREADS, device_sms() * 4), SPGEMM_P1_THREADS, 0, s>>>(
+                    g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE);
             count_launch();
         }
         return cudaGetLastError();
