@@ -3,7 +3,7 @@
 
 Workload (default): the 3D steady advection-diffusion-reaction system, upwind FD on a
 192^3 grid (7,077,888 unknowns, 7-point stencil), velocity (1, 0.7, 0.4)/|.|, eps 1e-5,
-c 0.05; lAIR distance 1, PMIS splitting, one-point interpolation, lumping 0.01; FP32
+c 0.05; lAIR distance 1, PMIS splitting, one-point interpolation, lumping 0.05; FP32
 V-cycle inside FP64 stationary refinement to a relative residual of 1e-8 -- the largest single-GPU
 configuration. --workload dg_p2_256 (2D DG-P2, 786,432 unknowns) and batched_512 (512
 independent 2D systems) are the other two. A step is set-up + solve of that system
@@ -42,7 +42,7 @@ _DESC = {
                    "seed 2 (n~12.8M in all); one block-diagonal lAIR hierarchy (distance 1), per-system FGMRES(30) "
                    "with FP32 cycle, per-system tol 1e-8",
     "fd3d_192": "3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1, "
-                "PMIS splitting, one-point P, lumping 0.01; FP32 cycle in FP64 stationary refinement, tol 1e-8",
+                "PMIS splitting, one-point P, lumping 0.05; FP32 cycle in FP64 stationary refinement, tol 1e-8",
 }
 # CPU oracle: one-thread sample scale (about 10 s), and the reference arm's sample (None: full size)
 _SAMPLE_SCALE = {"dg_p2_256": 128, "batched_512": 8, "fd3d_192": 64}

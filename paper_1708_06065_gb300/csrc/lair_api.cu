@@ -790,6 +790,11 @@ static lair_status spgemm(lair_handle *h, Temps &t, const DCsr &X, const DCsr &Y
         g.prp = P->rp;
         g.pcol = P->col;
         g.pval = P->val;
+        g.pn = P->nr;
+        if (hc[SPGEMM_BIN_MERGE] > 0) {
+            TRY(t.get(&g.pmap_col, (size_t)P->nr + 1));
+            TRY(t.get(&g.pmap_val, (size_t)P->nr + 1));
+        }
         if (timed >= 0) h->prod_fused = true;
     }
     int tp = -1;

@@ -113,6 +113,9 @@ struct SpgemmArgs {
     // fused third factor (one-point P: at most one entry per row); NULL for a plain product
     const int *prp = nullptr, *pcol = nullptr;
     const double *pval = nullptr;
+    int pn = 0;                          // rows of P
+    int *pmap_col = nullptr;             // scratch, pn entries: P's row as a direct map (thread-per-row fused kernel)
+    double *pmap_val = nullptr;
 };
 constexpr int SPGEMM_CTA_GRID = 152;
 constexpr int SPGEMM_BINS = 6;      // three warp bins by row bound, the CTA bin, two merge bins

@@ -107,14 +107,19 @@ __global__ void __launch_bounds__(K <= 8 ? 256 : 128) k_spgemm_merge(SpgemmArgs 
 }
 
 // The fused triple product X Y P for a one-point P (at most one entry per row), one thread per row of X
-// with at most K entries and a bound ub <= SPGEMM_P1_CAP: row a of X Y is merged in column order as above,
-// and each entry (l, v), in ascending l, adds fma(v, p_l, .) to column P(l) of the result, which the thread
-// keeps as a short list in its own column of shared memory (entry e at e * blockDim + thread: no bank
-// conflicts); the list is put in column order by insertion and written out. Every result entry thus
-// receives its terms in ascending l, starting from 0: the fma sequence of the hashed fused kernels.
+// with at most K entries and a bound ub <= SPGEMM_P1_CAP. Row a of X Y is merged in column order as above
+// into the thread's own column of shared memory (entry e at e * blockDim + thread: no bank conflicts). Its
+// entries (l, v) are then taken in ascending l, four at a time, with P's row l read from the direct map
+// (pmap_col[l], pmap_val[l]: -1 / 0 for an empty row) so that the four reads are in flight together; each
+// adds fma(v, p_l, .) to column P(l) of the result, kept in the same shared list (an entry read adds at
+// most one result column, so results never overtake entries still to be read). The list is put in column
+// order by insertion and written out. Every result entry thus receives its terms in ascending l, starting
+// from 0: the fma sequence of the hashed fused kernels.
 template <int K>
 __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArgs g, const int *__restrict__ list,
-                                                                       const int *__restrict__ count) {
+                                                                       const int *__restrict__ count,
+                                                                       const int *__restrict__ pmap_col,
+                                                                       const double *__restrict__ pmap_val) {
     __shared__ int lcol[SPGEMM_P1_CAP * SPGEMM_P1_THREADS];
     __shared__ double lval[SPGEMM_P1_CAP * SPGEMM_P1_THREADS];
     constexpr int T = SPGEMM_P1_THREADS;
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArg
             }
             cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
         }
-        int nout = 0;
+        int c = 0;
         for (;;) {
             int j = 0x7fffffff;
 #pragma unroll
@@ -153,19 +158,34 @@ __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArg
                     ++pos[u];
                     cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
                 }
-            // (X Y)_aj = v is complete: its term of column P(j)
-            const int pb = g.prp[j];
-            if (g.prp[j + 1] == pb) continue;
-            const int b = g.pcol[pb];
-            const double pv = g.pval[pb];
-            int f = 0;
-            while (f < nout && mc[f * T] != b) ++f;
-            if (f == nout) {
-                mc[f * T] = b;
-                mv[f * T] = __fma_rn(v, pv, 0.0);
-                ++nout;
-            } else {
-                mv[f * T] = __fma_rn(v, pv, mv[f * T]);
+            mc[c * T] = j;
+            mv[c * T] = v;
+            ++c;
+        }
+        int nout = 0;
+        for (int e0 = 0; e0 < c; e0 += 4) {
+            int bq[4];
+            double vq[4], pq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int l = e0 + q < c ? mc[(e0 + q) * T] : -1;
+                vq[q] = e0 + q < c ? mv[(e0 + q) * T] : 0.0;
+                bq[q] = l >= 0 ? pmap_col[l] : -1;
+                pq[q] = l >= 0 ? pmap_val[l] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int b = bq[q];
+                if (b < 0) continue;
+                int f = 0;
+                while (f < nout && mc[f * T] != b) ++f;
+                if (f == nout) {
+                    mc[f * T] = b;
+                    mv[f * T] = __fma_rn(vq[q], pq[q], 0.0);
+                    ++nout;
+                } else {
+                    mv[f * T] = __fma_rn(vq[q], pq[q], mv[f * T]);
+                }
             }
         }
         for (int x = 1; x < nout; ++x) {
@@ -186,6 +206,17 @@ __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArg
             g.tval[o + e] = mv[e * T];
         }
         g.cnt[a] = nout;
+    }
+}
+
+// direct map of a P with at most one entry per row: (column, value) of row l, or (-1, 0)
+__global__ void k_p1_map(int n, const int *__restrict__ prp, const int *__restrict__ pcol, const double *__restrict__ pval,
+                         int *__restrict__ mcol, double *__restrict__ mval) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const int b = prp[l];
+        const bool has = prp[l + 1] > b;
+        mcol[l] = has ? pcol[b] : -1;
+        mval[l] = has ? pval[b] : 0.0;
     }
 }
 
@@ -683,10 +714,12 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
         if (counts_host[0] > 0) launch_spgemm_bin<256, 8, true>(g, lists, counts_dev, counts_host[0], s);
         if (counts_host[1] > 0) launch_spgemm_bin<1024, 4, true>(g, lists + nr, counts_dev + 1, counts_host[1], s);
         if (counts_host[SPGEMM_BIN_MERGE] > 0) {
+            if (!g.pmap_col || !g.pmap_val) return cudaErrorInvalidValue;
+            k_p1_map<<<grid_for(g.pn, 256), 256, 0, s>>>(g.pn, g.prp, g.pcol, g.pval, g.pmap_col, g.pmap_val);
             k_spgemm_merge_p1<SPGEMM_MERGE_K>
                 <<<grid_for(counts_host[SPGEMM_BIN_MERGE], SPGEMM_P1_THREADS, device_sms() * 4), SPGEMM_P1_THREADS, 0, s>>>(
-                    g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE);
-            count_launch();
+                    g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE, g.pmap_col, g.pmap_val);
+            count_launch(2);
         }
         return cudaGetLastError();
     }
