@@ -123,6 +123,10 @@ __global__ void k_sell_fill_multi(const SellDesc *__restrict__ d, int p0, int p1
     }
 }
 
+// The matrix entries, the Jacobi diagonal and b are read once per launch: they are loaded with the
+// streaming (evict-first) policy, so that they pass through L2 without pushing out x, which every row
+// gathers from and which stays in L2 from one kernel of the cycle to the next.
+//
 // y[row[r]] = (view row r) . x. RPT rows per thread: the thread of lane l in group g takes row l of each of
 // the slices g RPT, ..., g RPT + RPT - 1, so every load of a warp stays coalesced and a thread keeps RPT
 // independent sums in flight; each row is still summed alone in column order.
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restri
 #pragma unroll
             for (int k = 0; k < RPT; ++k)
                 if (j < len[k])
-                    acc[k] = fma(__ldg(sval + base[k] + 32 * j), __ldg(x + __ldg(scol + base[k] + 32 * j)), acc[k]);
+                    acc[k] = fma(__ldcs(sval + base[k] + 32 * j), __ldg(x + __ldcs(scol + base[k] + 32 * j)), acc[k]);
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
             if (r[k] < v.nrows) y[v.row[r[k]]] = acc[k];
@@ -201,12 +205,12 @@ __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__res
 #pragma unroll
                 for (int k = 0; k < RPT; ++k)
                     if (j < len[k])
-                        acc[k] = fma(__ldg(sval + base[k] + 32 * j), __ldg(x + __ldg(scol + base[k] + 32 * j)), acc[k]);
+                        acc[k] = fma(__ldcs(sval + base[k] + 32 * j), __ldg(x + __ldcs(scol + base[k] + 32 * j)), acc[k]);
 #pragma unroll
             for (int k = 0; k < RPT; ++k)
                 if (r[k] < v.nrows) {
                     const int i = v.row[r[k]];
-                    xo[i] = fma(sd[r[k]], b[i] - acc[k], x[i]);
+                    xo[i] = fma(__ldcs(sd + r[k]), __ldcs(b + i) - acc[k], x[i]);
                 }
         } else {
             const int j = copy[u - nthr];
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_sell_residual(SellView v, const
         const int len = (__ldg(sptr + sl + 1) - __ldg(sptr + sl)) >> 5;
         double acc = 0.0;
 #pragma unroll 4
-        for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), __ldg(x + __ldg(scol + base + 32 * j)), acc);
+        for (int j = 0; j < len; ++j) acc = fma(__ldcs(sval + base + 32 * j), __ldg(x + __ldcs(scol + base + 32 * j)), acc);
         const int i = v.row[q];
         const double ri = b[i] - acc;
         r[i] = ri;

@@ -131,8 +131,8 @@ void launch_spgemm_ub(int nr, const int *xrp, const int *xcol, const int *yrp, i
 // (and, for the first merge bin, a bound of at most merge_ub_max products)
 void launch_spgemm_classify(int nr, const int *off, const int *xrp, bool merge, bool merge2, int merge_ub_max,
                             int *lists, int *counts, int *ubmax, cudaStream_t s);
-constexpr int SPGEMM_P1_CAP = 64;       // fused one-point merge: at most this many products per row
-constexpr int SPGEMM_P1_THREADS = 64;   // threads per block (their lists fill 48 KB of shared memory)
+constexpr int SPGEMM_P1_CAP = 32;       // fused one-point merge: at most this many products per row
+constexpr int SPGEMM_P1_THREADS = 128;  // threads per block (their result lists fill 48 KB of shared memory)
 // true if every row of the product fits the fused one-point-P kernels (bins 0 and 1, the first merge bin)
 bool spgemm_can_fuse(const int counts_host[SPGEMM_BINS]);
 cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, const int *counts_dev,

@@ -107,14 +107,16 @@ __global__ void __launch_bounds__(K <= 8 ? 256 : 128) k_spgemm_merge(SpgemmArgs 
 }
 
 // The fused triple product X Y P for a one-point P (at most one entry per row), one thread per row of X
-// with at most K entries and a bound ub <= SPGEMM_P1_CAP. Row a of X Y is merged in column order as above
-// into the thread's own column of shared memory (entry e at e * blockDim + thread: no bank conflicts). Its
-// entries (l, v) are then taken in ascending l, four at a time, with P's row l read from the direct map
-// (pmap_col[l], pmap_val[l]: -1 / 0 for an empty row) so that the four reads are in flight together; each
-// adds fma(v, p_l, .) to column P(l) of the result, kept in the same shared list (an entry read adds at
-// most one result column, so results never overtake entries still to be read). The list is put in column
-// order by insertion and written out. Every result entry thus receives its terms in ascending l, starting
-// from 0: the fma sequence of the hashed fused kernels.
+// with at most K entries and a bound ub <= SPGEMM_P1_CAP. Row a of X Y is merged in column order as above;
+// each finished entry (l, v), in ascending l, looks up P's row l in the direct map (pmap_col[l],
+// pmap_val[l]: -1 / 0 for an empty row) and waits in a register queue of P1_LAG entries, so that the
+// lookup is in flight while the merge goes on; the entry leaving the queue adds fma(v, p_l, .) to column
+// P(l) of the result, a short list in the thread's own column of shared memory (entry e at
+// e * blockDim + thread: no bank conflicts). The list is put in column order by insertion and written
+// out. Every result entry thus receives its terms in ascending l, starting from 0: the fma sequence of
+// the hashed fused kernels. The result has at most ub entries, so the list holds SPGEMM_P1_CAP.
+constexpr int P1_LAG = 4;
+
 template <int K>
 __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArgs g, const int *__restrict__ list,
                                                                        const int *__restrict__ count,
@@ -144,7 +146,28 @@ __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArg
             }
             cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
         }
-        int c = 0;
+        int nout = 0;
+        // the queue: slot 0 is the oldest; qb < -1 marks an empty slot
+        int qb[P1_LAG];
+        double qv[P1_LAG], qp[P1_LAG];
+#pragma unroll
+        for (int q = 0; q < P1_LAG; ++q) {
+            qb[q] = -2;
+            qv[q] = 0.0;
+            qp[q] = 0.0;
+        }
+        auto add = [&](int b, double v, double pv) {
+            if (b < 0) return;
+            int f = 0;
+            while (f < nout && mc[f * T] != b) ++f;
+            if (f == nout) {
+                mc[f * T] = b;
+                mv[f * T] = __fma_rn(v, pv, 0.0);
+                ++nout;
+            } else {
+                mv[f * T] = __fma_rn(v, pv, mv[f * T]);
+            }
+        };
         for (;;) {
             int j = 0x7fffffff;
 #pragma unroll
@@ -158,36 +181,20 @@ __global__ void __launch_bounds__(SPGEMM_P1_THREADS) k_spgemm_merge_p1(SpgemmArg
                     ++pos[u];
                     cj[u] = pos[u] < end[u] ? g.ycol[pos[u]] : 0x7fffffff;
                 }
-            mc[c * T] = j;
-            mv[c * T] = v;
-            ++c;
-        }
-        int nout = 0;
-        for (int e0 = 0; e0 < c; e0 += 4) {
-            int bq[4];
-            double vq[4], pq[4];
+            // the oldest entry leaves the queue; (j, v) enters with its lookup issued now
+            add(qb[0], qv[0], qp[0]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int l = e0 + q < c ? mc[(e0 + q) * T] : -1;
-                vq[q] = e0 + q < c ? mv[(e0 + q) * T] : 0.0;
-                bq[q] = l >= 0 ? pmap_col[l] : -1;
-                pq[q] = l >= 0 ? pmap_val[l] : 0.0;
+            for (int q = 0; q + 1 < P1_LAG; ++q) {
+                qb[q] = qb[q + 1];
+                qv[q] = qv[q + 1];
+                qp[q] = qp[q + 1];
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int b = bq[q];
-                if (b < 0) continue;
-                int f = 0;
-                while (f < nout && mc[f * T] != b) ++f;
-                if (f == nout) {
-                    mc[f * T] = b;
-                    mv[f * T] = __fma_rn(vq[q], pq[q], 0.0);
-                    ++nout;
-                } else {
-                    mv[f * T] = __fma_rn(vq[q], pq[q], mv[f * T]);
-                }
-            }
+            qb[P1_LAG - 1] = pmap_col[j];
+            qp[P1_LAG - 1] = pmap_val[j];
+            qv[P1_LAG - 1] = v;
         }
+#pragma unroll
+        for (int q = 0; q < P1_LAG; ++q) add(qb[q], qv[q], qp[q]);
         for (int x = 1; x < nout; ++x) {
             const int kc = mc[x * T];
             const double kv = mv[x * T];
@@ -717,7 +724,7 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
             if (!g.pmap_col || !g.pmap_val) return cudaErrorInvalidValue;
             k_p1_map<<<grid_for(g.pn, 256), 256, 0, s>>>(g.pn, g.prp, g.pcol, g.pval, g.pmap_col, g.pmap_val);
             k_spgemm_merge_p1<SPGEMM_MERGE_K>
-                <<<grid_for(counts_host[SPGEMM_BIN_MERGE], SPGEMM_P1_THREADS, device_sms() * 4), SPGEMM_P1_THREADS, 0, s>>>(
+                <<<grid_for(counts_host[SPGEMM_BIN_MERGE], SPGEMM_P1_THREADS, device_sms() * 8), SPGEMM_P1_THREADS, 0, s>>>(
                     g, lists + SPGEMM_BIN_MERGE * (size_t)nr, counts_dev + SPGEMM_BIN_MERGE, g.pmap_col, g.pmap_val);
             count_launch(2);
         }
