@@ -301,7 +301,7 @@ __device__ __forceinline__ bool pmis_beats_all(double wi, int i, int b, int e, c
     return true;
 }
 
-constexpr int PMIS_THREADS = 1024;   // one CTA per SM keeps the grid barrier short
+constexpr int PMIS_THREADS = 1024;   // few large CTAs keep the grid barrier short
 constexpr int PMIS_CLUSTER = 8;      // levels of at most 8 * 1024 points: one cluster, one point per thread
 
 // The PMIS rounds of a small level in one thread-block cluster: the same rounds as k_pmis_coop,
@@ -1218,7 +1218,8 @@ cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    int grid = sms;
+    // two CTAs per SM where they fit: twice the loads in flight in each round, for two barrier arrivals per SM
+    int grid = sms * (per_sm < 2 ? per_sm : 2);
     const int need = (n + PMIS_THREADS - 1) / PMIS_THREADS;
     if (grid > need) grid = need > 0 ? need : 1;
     void *args[] = {(void *)&n,   (void *)&S,    (void *)&ST,     (void *)&w,    (void *)&cf,
