@@ -41,12 +41,17 @@ _DESC = {
     "batched_512": "512 independent 2D upwind FD systems, side U{32..256}, angle U(0,2pi), log10 eps U(-6,0), c U(0,1), "
                    "seed 2 (n~12.8M in all); one block-diagonal lAIR hierarchy (distance 1), per-system FGMRES(30) "
                    "with FP32 cycle, per-system tol 1e-8",
+    "fd2d_64": "2D upwind FD 64x64 (n=4096, 5-pt), angle 3pi/16, eps 1e-4, c 0.1; lAIR distance 1, theta 0.25, "
+               "classical first pass; V-cycles with F-F-C Jacobi in stationary refinement to 1e-10",
+    "adjoint_fd2d_512": "2D upwind FD 512x512 (n=262144), C1's coefficients; forward solve, adjoint solve A^T lam = "
+                        "x - x* (x* ~ N(0,1) seed 1) on a hierarchy for A^T, gradient -lam_i x_j on A's pattern; "
+                        "lAIR distance 1, FGMRES(30), tol 1e-8",
     "fd3d_192": "3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1, "
                 "PMIS splitting, one-point P, lumping 0.05; FP32 cycle in FP64 stationary refinement, tol 1e-8",
 }
 # CPU oracle: one-thread sample scale (about 10 s), and the reference arm's sample (None: full size)
-_SAMPLE_SCALE = {"dg_p2_256": 128, "batched_512": 8, "fd3d_192": 64}
-_REFERENCE_SCALE = {"dg_p2_256": None, "batched_512": 16, "fd3d_192": 96}
+_SAMPLE_SCALE = {"dg_p2_256": 128, "batched_512": 8, "fd3d_192": 64, "fd2d_64": None, "adjoint_fd2d_512": 256}
+_REFERENCE_SCALE = {"dg_p2_256": None, "batched_512": 16, "fd3d_192": 96, "fd2d_64": None, "adjoint_fd2d_512": None}
 WORKLOADS = {k: dict(_W.BENCH_OPTIONS[k], desc=_DESC[k], sample_scale=_SAMPLE_SCALE[k],
                      reference_scale=_REFERENCE_SCALE[k]) for k in _DESC}
 L2_FLUSH_BYTES = 512 << 20
@@ -198,6 +203,16 @@ def oracle_run(workload, opts, scale=None, threads=None, budget_s=0.0, max_reps=
             if offs is None:
                 H = O.Hierarchy(s, **okw)
                 x, rep = H.solve(s.b, tol=wl["tol"], cycle=0 if wl.get("cycle") == "stationary" else 1)
+                if wl.get("adjoint"):
+                    # the adjoint solve on a hierarchy for A^T, and the gradient with respect to A's nonzeros
+                    g = x - s.meta["x_star"]
+                    trp, tcol, tval = O.transpose(s)
+                    HT = O.Hierarchy(W.CsrSystem(s.n, trp, tcol, tval, g), **okw)
+                    lam, rep_t = HT.solve(g, tol=wl["tol"], cycle=1)
+                    assert rep_t["status"] == 0, rep_t
+                    rows = np.repeat(np.arange(s.n), np.diff(s.row_ptr))
+                    _ = -lam[rows] * x[s.col]
+                    HT.close()
             else:
                 H = O.Hierarchy(s, seg=offs, **okw)
                 x, rep = H.solve_batched(s.b, tol=wl["tol"], cycle=1)
@@ -320,6 +335,11 @@ def main():
     val = torch.from_numpy(s.val).to(dev)
     b = torch.from_numpy(s.b).to(dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
+    adj = None
+    if wl.get("adjoint"):
+        # x*, the adjoint solution and the gradient with respect to A's nonzeros
+        adj = dict(xs=torch.from_numpy(s.meta["x_star"]).to(dev), lam=torch.zeros(n, dtype=torch.float64, device=dev),
+                   gA=torch.zeros(nnz, dtype=torch.float64, device=dev))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
@@ -379,12 +399,28 @@ def main():
                 with torch.cuda.stream(stream):
                     x.zero_()
                 _, rep = G.solve(b, x, tol=wl["tol"], cycle=cycle, max_iter=500)
+                if adj is not None:
+                    with torch.cuda.stream(stream):
+                        g = x - adj["xs"]
+                        adj["lam"].zero_()
+                    _, rep_t = G.adjoint(g, adj["lam"], tol=wl["tol"], cycle=cycle, max_iter=500)
+                    G.grad_A(adj["lam"], x, adj["gA"])
+                    if rep_t.status != 0:
+                        raise RuntimeError(f"adjoint solve did not converge: {rep_t}")
             else:
-                hrp, hcol, hval, hb, hx = host
+                hrp, hcol, hval, hb, hx = host[:5]
                 hx.zero_()
                 G = lair.Hierarchy(hrp, hcol, hval, precision=precision, stream=stream, timing=args.timing, **wl["opts"])
                 evm.record(stream)
                 _, rep = G.solve(hb, hx, tol=wl["tol"], cycle=cycle, max_iter=500)
+                if adj is not None:
+                    hxs, hlam, hgA = host[5:]
+                    hg = (hx - hxs).numpy()
+                    hlam.zero_()
+                    _, rep_t = G.adjoint(hg, hlam.numpy(), tol=wl["tol"], cycle=cycle, max_iter=500)
+                    G.grad_A(hlam.numpy(), hx.numpy(), hgA.numpy())
+                    if rep_t.status != 0:
+                        raise RuntimeError(f"adjoint solve did not converge: {rep_t}")
             ev1.record(stream)
             ev1.synchronize()
             if rep.status != 0:
@@ -433,12 +469,17 @@ def main():
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory()
         host = (pin(s.row_ptr), pin(s.col), pin(s.val), pin(s.b), torch.zeros(n, dtype=torch.float64).pin_memory())
+        if adj is not None:
+            host = host + (pin(s.meta["x_star"]), torch.zeros(n, dtype=torch.float64).pin_memory(),
+                           torch.zeros(nnz, dtype=torch.float64).pin_memory())
         run_steps(1, lair.MIXED, False, host=host)
         te, _, _, _, _, _ = run_steps(args.steps, lair.MIXED, True, host=host)
         mse = dist.max(sum(te) / len(te))
         e2e = {"value": n_job / (mse / 1e3), "unit": "unknowns/s",
-               "h2d_bytes_per_step": int((n + 1) * 8 + nnz * 4 + nnz * 8 + 2 * n * 8),
-               "d2h_bytes_per_step": int(n * 8), "ms_per_step": mse}
+               "h2d_bytes_per_step": int((n + 1) * 8 + nnz * 4 + nnz * 8 + 2 * n * 8) +
+                                     (int(2 * n * 8) if adj is not None else 0),
+               "d2h_bytes_per_step": int(n * 8) + (int(n * 8 + nnz * 8) if adj is not None else 0),
+               "ms_per_step": mse}
 
     # ---- reuse across time steps (backward Euler, I + dt S with a changing dt): one hierarchy, refreshed with
     # new values on the same pattern before every solve; alternates between the workload's matrix and one with

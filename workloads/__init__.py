@@ -440,4 +440,8 @@ BENCH_OPTIONS = {
     # PMIS and one-point P with lumping 0.05: the fastest set-up + solve measured for this system (the blocked
     # classical first pass, approximate ideal interpolation and smaller lumping thresholds are slower; 0.12 diverges)
     "fd3d_192": dict(opts=dict(distance=1, cf_mode=1, interp=1, lump_tol=0.05), tol=1e-8, cycle="stationary"),
+    # the 64 x 64 system with the exact classical first pass, FP64 V-cycles to 1e-10
+    "fd2d_64": dict(opts=dict(distance=1, cf_mode=0), tol=1e-10, cycle="stationary"),
+    # forward solve, then the adjoint solve on A^T and the gradient with respect to A's nonzeros
+    "adjoint_fd2d_512": dict(opts=dict(distance=1), tol=1e-8, cycle="fgmres", adjoint=True),
 }
