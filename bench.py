@@ -39,8 +39,8 @@ _DESC = {
                  "dt=h, block-diagonal scaling; lAIR distance 2, one-point P, |a| strength 0.25, PMIS splitting; "
                  "FP32 cycle in FP64 FGMRES(30), tol 1e-8",
     "batched_512": "512 independent 2D upwind FD systems, side U{32..256}, angle U(0,2pi), log10 eps U(-6,0), c U(0,1), "
-                   "seed 2 (n~12.8M in all); one block-diagonal lAIR hierarchy (distance 1), per-system FGMRES(30) "
-                   "with FP32 cycle, per-system tol 1e-8",
+                   "seed 2 (n~12.7M in all); one block-diagonal lAIR hierarchy (distance 1, PMIS, one-point P, lumping "
+                   "0.05), per-system FGMRES(30) with FP32 cycle, per-system tol 1e-8",
     "fd2d_64": "2D upwind FD 64x64 (n=4096, 5-pt), angle 3pi/16, eps 1e-4, c 0.1; lAIR distance 1, theta 0.25, "
                "classical first pass; V-cycles with F-F-C Jacobi in stationary refinement to 1e-10",
     "adjoint_fd2d_512": "2D upwind FD 512x512 (n=262144), C1's coefficients; forward solve, adjoint solve A^T lam = "
