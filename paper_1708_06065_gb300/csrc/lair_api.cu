@@ -880,7 +880,7 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         const long long dl = 32 + (long long)deg[1] * (1 + deg[2]);
         if (Bmax <= RSB_MAX_N && nb <= 256 && dl <= RSB_MAX_DIRTY &&
             rsb_smem_bytes(Bmax, nb, (int)dl) <= (size_t)200 * 1024) {
-            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, Scf, STcf, cf, h->status, h->s));
+            CU(launch_rs_bucket(bd, (int)blocks.size(), Bmax, nb, (int)dl, deg[0], Scf, STcf, cf, h->status, h->s));
         } else {
             CU(launch_rs(n, bd, (int)blocks.size(), Bmax, deg[0], Scf, STcf, cf, h->status, h->s));
         }

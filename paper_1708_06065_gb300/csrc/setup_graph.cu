@@ -806,10 +806,13 @@ __device__ void rsb_steps(int n, int nb, int W, int dl, int top, const V &Sv, co
     }
 }
 
-// The graphs are read through the cache: staging them in shared memory (as the tree version does) was
-// measured slower here, since the fewer blocks per SM hid less of each step's latency.
+// smem_bytes: the bucket layout of the largest block, plus (stage != 0) room to stage both in-block graphs
+// (uint16 row offsets and columns) so that each step reads shared memory only. Staging pays when the level
+// has at most one block per SM; with more blocks it costs occupancy, which hides more of each step's
+// latency than the staging saves (measured), and the graphs are read through the cache.
 __global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ blocks, Graph S, Graph ST, int nb, int dl,
-                                                  int8_t *__restrict__ cf_out, int *status) {
+                                                  int8_t *__restrict__ cf_out, int *status, int stage,
+                                                  int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int ndirty;
     const int b0 = blocks[blockIdx.x].x, b1 = blocks[blockIdx.x].y;
@@ -854,8 +857,23 @@ __global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ block
     }
     top = (int)__reduce_max_sync(0xffffffffu, (unsigned)top);
     __syncwarp();
-    GlobalView vs{S.rp, S.col, b0, b1}, vt{ST.rp, ST.col, b0, b1};
-    rsb_steps(n, nb, W, dl, top, vs, vt, q, status);
+    bool staged = false;
+    uint16_t *srp = reinterpret_cast<uint16_t *>(smem + Lo.total);
+    uint16_t *strp = srp + (n + 1);
+    uint16_t *scol = strp + (n + 1);
+    if (stage) {
+        const size_t used = (size_t)(reinterpret_cast<unsigned char *>(scol) - smem);
+        const size_t cap = used < (size_t)smem_bytes ? ((size_t)smem_bytes - used) / (2 * sizeof(uint16_t)) : 0;
+        staged = rs_stage(S, b0, b1, srp, scol, cap);
+        if (staged) staged = rs_stage(ST, b0, b1, strp, scol + srp[n], cap);
+    }
+    if (staged) {
+        StagedView vs{srp, scol}, vt{strp, scol + srp[n]};
+        rsb_steps(n, nb, W, dl, top, vs, vt, q, status);
+    } else {
+        GlobalView vs{S.rp, S.col, b0, b1}, vt{ST.rp, ST.col, b0, b1};
+        rsb_steps(n, nb, W, dl, top, vs, vt, q, status);
+    }
     for (int li = lane; li < n; li += 32) {
         const int8_t c = q.cf[li];
         if (c != CF_C && c != CF_F) set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
@@ -864,6 +882,11 @@ __global__ void __launch_bounds__(32) k_rs_bucket(const int2 *__restrict__ block
 }
 
 size_t rsb_smem_bytes(int n, int nb, int dl) { return rsb_layout(n, nb, dl).total; }
+
+// the bytes to stage both in-block graphs of the fullest block as well
+static size_t rsb_stage_bytes(int n, int max_inblock) {
+    return 2 * sizeof(uint16_t) * ((size_t)n + 1) + 2 * sizeof(uint16_t) * (size_t)max_inblock + 16;
+}
 
 // shared memory of one block: the fixed part (keys, tree, splitting, row offsets) plus room for
 // both staged in-block graphs of the fullest block, up to RS_SMEM_MAX bytes in all (blocks that
@@ -1241,12 +1264,18 @@ void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Gr
     count_launch();
 }
 
-cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
-                             const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
-    const size_t bytes = rsb_smem_bytes(Bmax, nb, dl);
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, int max_inblock,
+                             const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s) {
+    size_t bytes = rsb_smem_bytes(Bmax, nb, dl);
+    int stage = 0;
+    if (nblocks <= device_sms()) {
+        const size_t want = bytes + rsb_stage_bytes(Bmax, max_inblock);
+        stage = 1;
+        bytes = want < (size_t)RS_SMEM_MAX ? want : (bytes > (size_t)RS_SMEM_MAX ? bytes : (size_t)RS_SMEM_MAX);
+    }
     cudaError_t e = cudaFuncSetAttribute(k_rs_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_rs_bucket<<<nblocks, 32, bytes, s>>>(blocks, S, ST, nb, dl, cf, status);
+    k_rs_bucket<<<nblocks, 32, bytes, s>>>(blocks, S, ST, nb, dl, cf, status, stage, (int)bytes);
     count_launch();
     return cudaGetLastError();
 }

@@ -40,8 +40,10 @@ void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcn
 constexpr int RSB_MAX_N = 8192;
 constexpr int RSB_MAX_DIRTY = 8192;
 void launch_rs_degrees(const int2 *blocks, int nblocks, const Graph &S, const Graph &ST, int *out, cudaStream_t s);
-cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, const Graph &S,
-                             const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
+// (levels of at most one block per SM stage the in-block graphs in shared memory; max_inblock: the largest
+// in-block entry count of S)
+cudaError_t launch_rs_bucket(const int2 *blocks, int nblocks, int Bmax, int nb, int dl, int max_inblock,
+                             const Graph &S, const Graph &ST, int8_t *cf, int *status, cudaStream_t s);
 size_t rsb_smem_bytes(int n, int nb, int dl);
 cudaError_t launch_rs(int n, const int2 *blocks, int nblocks, int Bmax, int max_inblock, const Graph &S, const Graph &ST,
                       int8_t *cf, int *status, cudaStream_t s);
