@@ -45,7 +45,7 @@ _DESC = {
                "classical first pass; V-cycles with F-F-C Jacobi in stationary refinement to 1e-10",
     "adjoint_fd2d_512": "2D upwind FD 512x512 (n=262144), C1's coefficients; forward solve, adjoint solve A^T lam = "
                         "x - x* (x* ~ N(0,1) seed 1) on a hierarchy for A^T, gradient -lam_i x_j on A's pattern; "
-                        "lAIR distance 1, FGMRES(30), tol 1e-8",
+                        "lAIR distance 1, PMIS, one-point P, lumping 0.05, FGMRES(30), tol 1e-8",
     "fd3d_192": "3D upwind FD 192^3 (n=7077888, 7-pt), velocity (1,.7,.4)/|.|, eps 1e-5, c 0.05; lAIR distance 1, "
                 "PMIS splitting, one-point P, lumping 0.05; FP32 cycle in FP64 stationary refinement, tol 1e-8",
 }

@@ -348,7 +348,28 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_cluster(int n, Graph S, G
     cluster.sync();   // no CTA leaves while another may still read its counter
 }
 
-__global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Graph ST, double *w,
+// true if w_i beats the weight of every undecided neighbour in S_i and in ST_i: the two rows are read side by
+// side, two entries of each at a time, so that a point waits on one chain of loads instead of two
+__device__ __forceinline__ bool pmis_beats_both(double wi, int i, const Graph &S, const Graph &ST, const double *w) {
+    const int sb = S.rp[i], se = S.rp[i + 1], tb = ST.rp[i], te = ST.rp[i + 1];
+    for (int k = 0; sb + k < se || tb + k < te; k += 2) {
+        int j[4];
+        double wj[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            j[u] = sb + k + u < se ? S.col[sb + k + u] : -1;
+            j[2 + u] = tb + k + u < te ? ST.col[tb + k + u] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wj[u] = j[u] >= 0 ? w[j[u]] : -1.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (wj[u] >= 0.0 && !beats(wi, i, wj[u], j[u])) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(PMIS_THREADS, 2) k_pmis_coop(int n, Graph S, Graph ST, double *w,
                                                    int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
                                                    int *status, long long limit) {
     const int stride = gridDim.x * blockDim.x;
@@ -360,8 +381,7 @@ __global__ void __launch_bounds__(PMIS_THREADS) k_pmis_coop(int n, Graph S, Grap
             const double wi = w[i];
             if (wi >= 0.0) {
                 ++local;
-                nc = pmis_beats_all<false>(wi, i, S.rp[i], S.rp[i + 1], S.col, w) &&
-                     pmis_beats_all<false>(wi, i, ST.rp[i], ST.rp[i + 1], ST.col, w);
+                nc = pmis_beats_both(wi, i, S, ST, w);
             }
             newc[i] = nc;
         }

@@ -1066,7 +1066,10 @@ void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *
     if (n <= DENSE_SMEM_N) {
         size_t bytes = sizeof(double) * ((size_t)n * n + 32 * (size_t)n) + sizeof(int) * (size_t)n;
         cudaFuncSetAttribute(k_dense_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        k_dense_small<<<1, 1024, bytes, s>>>(n, A.rp, A.col, A.val, Ainv, status);
+        // every column of the elimination costs a few block barriers: fewer warps make them cheaper, and a
+        // coarsest level of a few hundred unknowns has little work per column
+        const int tb = n <= 64 ? 128 : (n <= 160 ? 256 : 1024);
+        k_dense_small<<<1, tb, bytes, s>>>(n, A.rp, A.col, A.val, Ainv, status);
         count_launch();
         return;
     }
