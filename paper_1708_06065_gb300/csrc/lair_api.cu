@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <map>
 #include <atomic>
+#include <type_traits>
 #include <mutex>
 #include <tuple>
 #include <string>
@@ -1552,7 +1553,14 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     if (tm) tend(h, t, true);
     record_cycle<T>(h, H, l + 1);
     t = tm ? tbegin(h, "L0_interp", bytes_spmv(L.P, sv), true) : -1;
-    sell_spmv<T>(L.Pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    if (h->o.interp == LAIR_P_ONEPOINT || h->o.nodal > 1) {
+        // at most one entry per row of P: the direct kernel on P's CSR, rows in their own order
+        const T *pv = std::is_same<T, float>::value ? reinterpret_cast<const T *>(L.P.val32)
+                                                    : reinterpret_cast<const T *>(L.P.val);
+        p1_interp<T>(L.P.nr, L.P.rp, L.P.col, pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    } else {
+        sell_spmv<T>(L.Pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    }
     if (tm) tend(h, t, true);
     int cur = 0;
     const int n = L.A.nr, nc = L.nc;

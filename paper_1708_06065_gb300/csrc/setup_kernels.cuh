@@ -216,6 +216,9 @@ void launch_sell_fill_multi(const SellDesc *d, int p0, int p1, int lin_beg, int 
 template <class T> void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s);
 template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);
+// x = P x_c for a P with at most one entry per row, from P's CSR (values in the cycle's precision)
+template <class T>
+void p1_interp(int n, const int *rp, const int *col, const T *val, const T *xc, T *x, cudaStream_t s);
 // batched systems: per-system residual r = b - A x (rows seg[q]..seg[q+1]), its squared norm, optional FP32 copy
 // Row tiles of a batch of systems: tile t is system tile[t].x, rows [tile[t].y, tile[t].z);
 // the tiles of system q are first[q] .. first[q + 1] - 1; part holds SEG_TILE_PARTS doubles per tile.

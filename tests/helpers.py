@@ -26,19 +26,22 @@ def max_rel(a, b):
 
 
 def row_rel(rp, a, b):
-    """max over rows of max|a - b| / max|b| within the row"""
-    worst = 0.0
-    d = np.abs(np.asarray(a) - np.asarray(b))
-    m = np.abs(np.asarray(b))
-    for i in range(len(rp) - 1):
-        s, e = rp[i], rp[i + 1]
-        if e > s:
-            sc = m[s:e].max()
-            if sc > 0:
-                worst = max(worst, d[s:e].max() / sc)
-            elif d[s:e].max() > 0:
-                worst = np.inf
-    return worst
+    """max over rows of max|a - b| / max|b| within the row (inf where a row of b is zero and a differs)"""
+    rp = np.asarray(rp, np.int64)
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+    m = np.abs(np.asarray(b, np.float64))
+    lens = np.diff(rp)
+    rows = np.nonzero(lens > 0)[0]
+    if rows.size == 0:
+        return 0.0
+    starts = rp[rows]
+    dmax = np.maximum.reduceat(d, starts)
+    mmax = np.maximum.reduceat(m, starts)
+    # reduceat over starts of non-empty rows: each segment runs to the next start, which is this row's end
+    if np.any((mmax == 0) & (dmax > 0)):
+        return np.inf
+    ok = mmax > 0
+    return float((dmax[ok] / mmax[ok]).max()) if ok.any() else 0.0
 
 
 def compare_hierarchies(G, H, val_tol):

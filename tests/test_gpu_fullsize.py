@@ -2,8 +2,8 @@
 
 The DG workload at full size (786,432 unknowns: PMIS through the cooperative kernel, distance-2
 neighbourhoods with CTA-team local solves on the coarse levels, one-point P, block scaling,
-mixed precision); the 3D FD workload at 96^3 (884,736 unknowns, PMIS, one-point P with the
-thread-per-row fused Galerkin product); and
+mixed precision); the 3D FD workload at 96^3 and at its full 192^3 (7,077,888 unknowns, PMIS,
+one-point P with the thread-per-row fused Galerkin product); and
 the first 16 systems of the batched workload (sides up to 243). Every level's integer structure
 must equal the oracle's bit for bit and its values must agree within 1e-5 of the row's largest
 entry (FP32 local solves); one V-cycle is compared entry by entry, within 1e-5 of the largest
@@ -61,8 +61,9 @@ def check_cycle(G, H, n, seed):
     assert err <= TOL32, err
 
 
-@pytest.mark.parametrize("name,scale", [("dg_p2_256", None), ("fd3d_192", 96)])
+@pytest.mark.parametrize("name,scale", [("dg_p2_256", None), ("fd3d_192", 96), ("fd3d_192", None)])
 def test_full_size_hierarchy_and_cycle(lair, name, scale):
+    """The 3D system at 96^3 and at its full 192^3 (7,077,888 unknowns, the bench's default workload)."""
     s = W.config(name, scale=scale)
     kw = dict(W.BENCH_OPTIONS[name]["opts"], precision=lair.MIXED)
     G = device_hierarchy(lair, s, **kw)
