@@ -52,6 +52,14 @@ __global__ void __launch_bounds__(SELL_WINDOW) k_sell_sort_multi(const SellDesc 
         key[t] = ((unsigned long long)(0x7fffffff - (v.rp[i + 1] - v.rp[i])) << 32) | (unsigned)t;
     }
     __syncthreads();
+    // a window already in non-increasing row length (every row of a stencil's interior) keeps its order: the
+    // stable sort would return it unchanged
+    const unsigned kt = (unsigned)(key[t] >> 32);
+    const bool in_order = t + 1 >= cnt || kt <= (unsigned)(key[t + 1] >> 32);
+    if (__syncthreads_and(in_order)) {
+        if (t < cnt) v.row_out[w0 + t] = rid[t];
+        return;
+    }
     for (int k = 2; k <= SELL_WINDOW; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
             const int o = t ^ j;
