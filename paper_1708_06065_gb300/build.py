@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build", "lair")
 LIB = os.path.join(PKG, "liblair.so")
 SOURCES = ["setup_graph.cu", "setup_local.cu", "setup_rap.cu", "setup_nodal.cu", "solve_kernels.cu", "sell.cu",
-           "lair_api.cu"]
+           "lair_api.cu", "lair_solve.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

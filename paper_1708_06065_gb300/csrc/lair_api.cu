@@ -1,32 +1,14 @@
-// lair_api.cu -- host orchestration and the C ABI declared in include/lair.h.
+// lair_api.cu -- set-up orchestration (Sec. 2.1 and Sec. 4, level by level) and the C ABI declared
+// in include/lair.h; the outer iterations are in lair_solve.cu.
 //
 // Set-up runs level by level on the handle's stream; the host reads back only a few
 // sizes per level (coarse count, pattern sizes, bin counts) to size the next
 // allocations. The V-cycle of each hierarchy is captured once into a CUDA graph and
-// replayed for every preconditioner application; the outer FP64 loop synchronises
-// once per iteration (to read a norm or one Hessenberg column).
+// replayed for every preconditioner application.
 
-#include <chrono>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <algorithm>
-#include <map>
-#include <atomic>
-#include <type_traits>
-#include <mutex>
-#include <tuple>
-#include <string>
-#include <vector>
-
-#include "setup_kernels.cuh"
+#include "lair_host.cuh"
 
 namespace lair {
-
-void plus_one(int n, const int *a, int *b, cudaStream_t s);
-void count_flags(int n, const uint8_t *f, int *out, cudaStream_t s);
-void normalize_cf(int n, int8_t *cf, cudaStream_t s);
 
 int device_sms() {
     constexpr int MAXDEV = 64;
@@ -51,150 +33,7 @@ void count_launch(int k) {
     if (g_launches) *g_launches += k;
 }
 
-// ---------------------------------------------------------------------------------------
-// handle
-// ---------------------------------------------------------------------------------------
-struct Level {
-    DCsr A;
-    int8_t *cf = nullptr;
-    uint8_t *strong = nullptr;
-    int nc = 0;
-    int *cidx = nullptr;
-    DCsr R, P;
-    uint8_t *lsR = nullptr, *lsP = nullptr;
-    double *dinv = nullptr;
-    float *dinv32 = nullptr;
-    double *b64 = nullptr, *x64[2] = {nullptr, nullptr};
-    float *b32 = nullptr, *x32[2] = {nullptr, nullptr};
-    int xfinal = 0;         // which x buffer holds the cycle's result on this level
-    bool coarsest = false;
-    double *Ainv = nullptr;
-    long long nF = 0, nnzF = 0, nC = 0, nnzC = 0;   // rows and entries by kind (for byte counts)
-    std::vector<int> seg_h;   // batched systems: first row of every system on this level, nseg + 1 entries
-    int *seg_d = nullptr;
-    // cycle storage: sliced-ELL views of the F rows and C rows of A, of R and of P (cycle precision)
-    int *frows = nullptr, *crows = nullptr;
-    SellView AF, AC, Rv, Pv;
-    SellView A64;             // level 0: all rows of A in FP64 for the outer iteration
-    // nodal hierarchy (k x k blocks): block Jacobi as point Jacobi on Ahat = D^{-1} A (diagonal blocks
-    // inverted, diagonal exactly 1) with right-hand side D^{-1} b; binv holds the k x k inverses
-    DCsr Ahat;
-    double *binv = nullptr, *dinv_hat = nullptr, *bh64 = nullptr;
-    float *binv32 = nullptr, *dinv_hat32 = nullptr, *bh32 = nullptr;
-};
-
-struct Hier {
-    std::vector<Level> lev;
-    int bs = 0;
-    double *blk_inv = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int graph_nodes = 0;
-    long long singular_R = 0, singular_P = 0;
-    double setup_ms = 0.0;
-    // the sliced-ELL fill descriptors of all views (device), kept so that a refresh refills the views in place
-    SellDesc *sell_desc = nullptr;
-    int sell_gp[3] = {0, 0, 0}, sell_glin[3] = {0, 0, 0};
-};
-
-}  // namespace lair
-
-struct lair_handle {
-    lair_options o;
-    cudaStream_t s = nullptr;
-    cudaStream_t own = nullptr;   // created when the caller gives no stream
-    lair::DCsr A_in;              // the caller's matrix on the device (unscaled, unlumped)
-    lair::Hier H;
-    lair::Hier *HT = nullptr;     // adjoint hierarchy, built on demand
-    int *status = nullptr;        // device status word
-    int *h_int = nullptr;         // pinned host scratch
-    double *h_dbl = nullptr;
-    void *scan_tmp = nullptr;
-    size_t scan_tmp_bytes = 0;
-    std::vector<void *> allocs;   // everything owned by the handle
-    int *prod_nnz = nullptr;      // device: entry counts of the timed level-0 products (timing only)
-    bool prod_fused = false;      // level 0 formed R A P in one pass
-    // bump arenas over large device chunks (owned through allocs): set-up temporaries (stack
-    // discipline, see Temps) and small long-lived arrays; each allocation is 256-byte aligned
-    struct Chunk { char *p; size_t size; size_t used; };
-    std::vector<Chunk> tmp_chunks;
-    int tmp_cur = -1, tmp_depth = 0;
-    Chunk keep_chunk{nullptr, 0, 0};
-    // outer-iteration work (FP64)
-    double *wb = nullptr, *wx = nullptr, *wr = nullptr, *part = nullptr, *dsc = nullptr;
-    double *V = nullptr, *Z = nullptr;
-    int fg_m = 0;
-    std::string err;
-    long long launches = 0;
-    // kernel timing (options.timing)
-    struct Timer { std::string name; long long launches = 0; double ms = 0.0; double bytes = 0.0; };
-    struct Pending { int slot; cudaEvent_t a, b; bool closed; int id; };
-    int next_timer_id = 0;
-    std::vector<Timer> timers;
-    std::vector<Pending> pending;        // events recorded by direct launches, read at the next sync
-    std::vector<Pending> graph_events;   // events inside the captured cycle graph
-    std::vector<cudaEvent_t> ev_pool;
-    bool graph_pending = false;
-    // batched systems (block-diagonal input)
-    int nseg = 0;
-    std::vector<int> seg0;
-    double *h_seg = nullptr;      // pinned, nseg doubles
-    uint8_t *h_act = nullptr;     // pinned, nseg bytes
-    double *h_bat = nullptr;      // pinned, nseg * 32 doubles (per-system Hessenberg columns)
-    double *d_bat = nullptr;      // device, nseg * (3 * 32 + 1) doubles: sums, pass values, y, norms
-    int *d_batcnt = nullptr;      // device, nseg ints
-    int *h_batcnt = nullptr;      // pinned, nseg ints
-    lair::SegTiles segt;          // row tiles of the systems (level 0), built at the first batched solve
-    // device-side control of the batched outer loops, and a ring of running-system counts read back late
-    lair::BatchCtl bctl;
-    int bctl_m = -1;
-    static constexpr int RING = 8, LAG = 2;
-    int *d_ring = nullptr;        // device, RING ints
-    int *h_ring = nullptr;        // pinned, RING ints
-    cudaEvent_t ring_ev[RING] = {};
-};
-
-namespace lair {
-
-static lair_status fail(lair_handle *h, lair_status st, const char *fmt, ...) {
-    if (h) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        h->err = buf;
-    }
-    return st;
-}
-
-#define CU(call)                                                                                       \
-    do {                                                                                               \
-        cudaError_t e_ = (call);                                                                       \
-        if (e_ != cudaSuccess) {                                                                       \
-            if (e_ == cudaErrorMemoryAllocation) return fail(h, LAIR_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
-            return fail(h, LAIR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                   \
-        }                                                                                              \
-    } while (0)
-
-#define TRY(expr)                          \
-    do {                                   \
-        lair_status st_ = (expr);          \
-        if (st_ != LAIR_OK) return st_;    \
-    } while (0)
-
-constexpr size_t ARENA_ALIGN = 256;
-constexpr size_t KEEP_CHUNK = (size_t)32 << 20;      // long-lived arrays up to KEEP_CHUNK / 8 share chunks
-constexpr size_t TMP_CHUNK_MIN = (size_t)64 << 20;
-
-static size_t arena_round(size_t bytes) { return (bytes + ARENA_ALIGN - 1) & ~(ARENA_ALIGN - 1); }
-
-// The library's own stream-ordered pool per device: memory freed by one handle stays reserved
-// (up to POOL_KEEP bytes) for the next one instead of going back to the driver at every
-// synchronisation, and the device's default pool is left as the caller configured it.
-constexpr unsigned long long POOL_KEEP = 16ull << 30;
-constexpr int POOL_DEVICES = 64;
-
-static cudaError_t lair_pool(cudaMemPool_t *out) {
+cudaError_t lair_pool(cudaMemPool_t *out) {
     static std::mutex mu;
     static cudaMemPool_t pools[POOL_DEVICES] = {};
     int dev = 0;
@@ -220,12 +59,10 @@ static cudaError_t lair_pool(cudaMemPool_t *out) {
     return cudaSuccess;
 }
 
-// pinned host scratch of HOST_BLOCK bytes per handle, recycled between handles
-constexpr size_t HOST_BLOCK = 1024;
 static std::mutex g_host_mu;
 static std::vector<void *> g_host_free;
 
-static cudaError_t host_block_get(void **p) {
+cudaError_t host_block_get(void **p) {
     {
         std::lock_guard<std::mutex> lock(g_host_mu);
         if (!g_host_free.empty()) {
@@ -237,248 +74,11 @@ static cudaError_t host_block_get(void **p) {
     return cudaMallocHost(p, HOST_BLOCK);
 }
 
-static void host_block_put(void *p) {
+void host_block_put(void *p) {
     if (!p) return;
     std::lock_guard<std::mutex> lock(g_host_mu);
     g_host_free.push_back(p);
 }
-
-static lair_status raw_alloc(lair_handle *h, void **p, size_t bytes) {
-    cudaMemPool_t pool;
-    cudaError_t e = lair_pool(&pool);
-    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, h->s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, LAIR_ERR_OOM, "device allocation of %zu bytes failed", bytes);
-    }
-    return LAIR_OK;
-}
-
-// keep = true: owned by the handle until lair_free (small arrays share chunks);
-// keep = false: plain stream-ordered allocation, released with dfree
-template <class T>
-static lair_status dalloc(lair_handle *h, T **p, size_t n, bool keep = true) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    const size_t bytes = arena_round(n * sizeof(T));
-    void *q = nullptr;
-    if (keep && bytes <= KEEP_CHUNK / 8) {
-        auto &c = h->keep_chunk;
-        if (!c.p || c.used + bytes > c.size) {
-            void *np = nullptr;
-            TRY(raw_alloc(h, &np, KEEP_CHUNK));
-            h->allocs.push_back(np);
-            c = lair_handle::Chunk{static_cast<char *>(np), KEEP_CHUNK, 0};
-        }
-        q = c.p + c.used;
-        c.used += bytes;
-    } else {
-        TRY(raw_alloc(h, &q, bytes));
-        if (keep) h->allocs.push_back(q);
-    }
-    *p = static_cast<T *>(q);
-    return LAIR_OK;
-}
-
-static void dfree(lair_handle *h, void *p) {
-    if (p) cudaFreeAsync(p, h->s);
-}
-
-// Set-up temporaries. The innermost live Temps bumps through the handle's temporary chunks and
-// gives everything back at once when it goes out of scope; memory is reused only by work issued
-// later on the same stream. A Temps that is not the innermost one allocates plainly instead.
-struct Temps {
-    lair_handle *h;
-    int depth, mark_cur;
-    size_t mark_used;
-    std::vector<void *> raw;
-    explicit Temps(lair_handle *hh) : h(hh) {
-        depth = ++h->tmp_depth;
-        mark_cur = h->tmp_cur;
-        mark_used = h->tmp_cur >= 0 ? h->tmp_chunks[h->tmp_cur].used : 0;
-    }
-    template <class T> lair_status get(T **p, size_t n) {
-        if (n == 0) n = 1;
-        const size_t bytes = arena_round(n * sizeof(T));
-        if (depth != h->tmp_depth) {
-            void *q = nullptr;
-            TRY(raw_alloc(h, &q, bytes));
-            raw.push_back(q);
-            *p = static_cast<T *>(q);
-            return LAIR_OK;
-        }
-        auto &ch = h->tmp_chunks;
-        if (h->tmp_cur < 0 || ch[h->tmp_cur].used + bytes > ch[h->tmp_cur].size) {
-            // the next chunk if it is large enough, else a new one in its place
-            const int nx = h->tmp_cur + 1;
-            if (nx < (int)ch.size() && ch[nx].size >= bytes) {
-                ch[nx].used = 0;
-            } else {
-                size_t sz = TMP_CHUNK_MIN;
-                if (2 * bytes > sz) sz = 2 * bytes;
-                void *np = nullptr;
-                TRY(raw_alloc(h, &np, sz));
-                h->allocs.push_back(np);
-                ch.insert(ch.begin() + nx, lair_handle::Chunk{static_cast<char *>(np), sz, 0});
-            }
-            h->tmp_cur = nx;
-        }
-        auto &c = ch[h->tmp_cur];
-        *p = reinterpret_cast<T *>(c.p + c.used);
-        c.used += bytes;
-        return LAIR_OK;
-    }
-    ~Temps() {
-        for (void *q : raw) dfree(h, q);
-        if (depth == h->tmp_depth) {
-            h->tmp_cur = mark_cur;
-            if (mark_cur >= 0) h->tmp_chunks[mark_cur].used = mark_used;
-        }
-        --h->tmp_depth;
-    }
-};
-
-static void flush_timers(lair_handle *h);
-
-static lair_status sync_status(lair_handle *h) {
-    CU(cudaMemcpyAsync(h->h_int, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    CU(cudaStreamSynchronize(h->s));
-    flush_timers(h);
-    int st = h->h_int[0];
-    if (st != 0) {
-        CU(cudaMemsetAsync(h->status, 0, sizeof(int), h->s));
-        return fail(h, (lair_status)st, "device reported %s", lair_status_string((lair_status)st));
-    }
-    return LAIR_OK;
-}
-
-// read n device ints into pageable host memory (any n)
-static lair_status read_ints_big(lair_handle *h, const int *d, int n, int *out) {
-    CU(cudaMemcpyAsync(out, d, sizeof(int) * n, cudaMemcpyDeviceToHost, h->s));
-    return sync_status(h);
-}
-
-static lair_status read_ints(lair_handle *h, const int *d, int n, int *out) {
-    CU(cudaMemcpyAsync(h->h_int + 1, d, sizeof(int) * n, cudaMemcpyDeviceToHost, h->s));
-    TRY(sync_status(h));
-    memcpy(out, h->h_int + 1, sizeof(int) * n);
-    return LAIR_OK;
-}
-
-// ---------------------------------------------------------------------------------------
-// kernel timers: events around selected launches, read back at the next host sync
-// ---------------------------------------------------------------------------------------
-static int timer_slot(lair_handle *h, const std::string &name, double bytes) {
-    for (size_t i = 0; i < h->timers.size(); ++i)
-        if (h->timers[i].name == name) return (int)i;
-    lair_handle::Timer t;
-    t.name = name;
-    t.bytes = bytes;
-    h->timers.push_back(t);
-    return (int)h->timers.size() - 1;
-}
-
-static cudaEvent_t get_event(lair_handle *h) {
-    if (!h->ev_pool.empty()) {
-        cudaEvent_t e = h->ev_pool.back();
-        h->ev_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// begin/end around one launch; in_graph: the events become nodes of the graph being captured
-// returns the index of the event pair (for tend), or -1 when timing is off
-// set-up phase timer name; with timing >= 2 every level gets its own timer
-static std::string phase_name(const lair_handle *h, const char *phase, int level) {
-    std::string s = std::string("setup_") + phase;
-    if (h->o.timing >= 2 && level >= 0) s += "_L" + std::to_string(level);
-    return s;
-}
-
-static int tbegin(lair_handle *h, const std::string &name, double bytes, bool in_graph = false) {
-    if (!h->o.timing) return -1;
-    int slot = timer_slot(h, name, bytes);
-    lair_handle::Pending p{slot, get_event(h), get_event(h), false, h->next_timer_id++};
-    // inside stream capture only an external record becomes an event node of the graph
-    if (in_graph) cudaEventRecordWithFlags(p.a, h->s, cudaEventRecordExternal);
-    else cudaEventRecord(p.a, h->s);
-    auto &v = in_graph ? h->graph_events : h->pending;
-    v.push_back(p);
-    return p.id;
-}
-
-static void tend(lair_handle *h, int id, bool in_graph = false) {
-    if (id < 0) return;
-    auto &v = in_graph ? h->graph_events : h->pending;
-    for (size_t q = v.size(); q-- > 0;) {
-        if (v[q].id != id) continue;
-        if (in_graph) cudaEventRecordWithFlags(v[q].b, h->s, cudaEventRecordExternal);
-        else cudaEventRecord(v[q].b, h->s);
-        v[q].closed = true;
-        return;
-    }
-}
-
-// call only after the stream has been synchronised
-static void flush_timers(lair_handle *h) {
-    if (!h->o.timing) return;
-    // pairs still open (a region spanning this synchronisation) stay pending
-    std::vector<lair_handle::Pending> open;
-    for (auto &p : h->pending) {
-        if (!p.closed) {
-            open.push_back(p);
-            continue;
-        }
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            h->timers[p.slot].ms += ms;
-            h->timers[p.slot].launches += 1;
-        }
-        h->ev_pool.push_back(p.a);
-        h->ev_pool.push_back(p.b);
-    }
-    h->pending.swap(open);
-    if (h->graph_pending) {
-        for (auto &p : h->graph_events) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-                h->timers[p.slot].ms += ms;
-                h->timers[p.slot].launches += 1;
-            }
-        }
-        h->graph_pending = false;
-    }
-    cudaGetLastError();
-}
-
-// exclusive scan of cnt[0..n) into out[0..n] (out[n] = total); returns the total
-static lair_status scan(lair_handle *h, const int *cnt, int *out, int n, int *total) {
-    // cnt must have n+1 entries with cnt[n] = 0
-    if (n + 1 <= SMALL_SCAN_MAX) {
-        small_scan(n + 1, cnt, out, h->s);
-        if (total) TRY(read_ints(h, out + n, 1, total));
-        return LAIR_OK;
-    }
-    const size_t need = scan_state_bytes((long long)n + 1);
-    if (need > h->scan_tmp_bytes) {
-        if (h->scan_tmp) CU(cudaFreeAsync(h->scan_tmp, h->s));
-        CU(cudaMallocAsync(&h->scan_tmp, need, h->s));
-        h->scan_tmp_bytes = need;
-    }
-    CU(launch_scan((long long)n + 1, cnt, out, h->scan_tmp, h->status, h->s));
-    if (total) TRY(read_ints(h, out + n, 1, total));
-    return LAIR_OK;
-}
-
-static lair_status new_counts(lair_handle *h, Temps &t, int **p, int n) {
-    TRY(t.get(p, (size_t)n + 1));
-    CU(cudaMemsetAsync(*p, 0, sizeof(int) * ((size_t)n + 1), h->s));
-    return LAIR_OK;
-}
-
 // ---------------------------------------------------------------------------------------
 // graphs and transposes
 // ---------------------------------------------------------------------------------------
@@ -1532,9 +1132,6 @@ static double bytes_sweep(const Level &L, int target, double sv) {
     double nT = target == CF_F ? (double)L.nF : (double)L.nC, nnzT = target == CF_F ? (double)L.nnzF : (double)L.nnzC;
     return nnzT * (sv + 4.0) + nT * (4.0 + 3.0 * sv) + (double)L.A.nr * sv;
 }
-static double bytes_spmv(const DCsr &M, double sv) {
-    return (double)M.nnz * (sv + 4.0) + (double)M.nr * (4.0 + sv) + (double)M.nc * sv;
-}
 
 template <class T>
 static void record_cycle(lair_handle *h, Hier &H, int l) {
@@ -1553,8 +1150,9 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     if (tm) tend(h, t, true);
     record_cycle<T>(h, H, l + 1);
     t = tm ? tbegin(h, "L0_interp", bytes_spmv(L.P, sv), true) : -1;
-    if (h->o.interp == LAIR_P_ONEPOINT || h->o.nodal > 1) {
-        // at most one entry per row of P: the direct kernel on P's CSR, rows in their own order
+    if (h->o.interp == LAIR_P_ONEPOINT) {
+        // at most one entry per row of P (one-point, or the identity blocks of the nodal one-point P): the direct
+        // kernel on P's CSR, rows in their own order
         const T *pv = std::is_same<T, float>::value ? reinterpret_cast<const T *>(L.P.val32)
                                                     : reinterpret_cast<const T *>(L.P.val);
         p1_interp<T>(L.P.nr, L.P.rp, L.P.col, pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
@@ -2005,457 +1603,6 @@ static lair_status refresh_hierarchy(lair_handle *h, Hier &H, const DCsr &Ain) {
 // ---------------------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------------------
-static bool is_device_ptr(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// z = M^{-1} v (one cycle, zero initial guess); v, z: FP64 device vectors of length n0
-static lair_status precond(lair_handle *h, Hier &H, const double *v, double *z) {
-    Level &L = H.lev[0];
-    const int n = L.A.nr;
-    if (h->o.precision == LAIR_MIXED) {
-        d2f(n, v, L.b32, h->s);
-        CU(cudaGraphLaunch(H.graph, h->s));
-        count_launch(H.graph_nodes);
-        h->graph_pending = h->o.timing;
-        f2d(n, L.x32[L.xfinal], z, h->s);
-    } else {
-        CU(cudaMemcpyAsync(L.b64, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-        CU(cudaGraphLaunch(H.graph, h->s));
-        count_launch(H.graph_nodes);
-        h->graph_pending = h->o.timing;
-        CU(cudaMemcpyAsync(z, L.x64[L.xfinal], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-    }
-    return LAIR_OK;
-}
-
-static lair_status ensure_work(lair_handle *h, int n, int m) {
-    if (!h->wb) {
-        TRY(dalloc(h, &h->wb, (size_t)n));
-        TRY(dalloc(h, &h->wx, (size_t)n));
-        TRY(dalloc(h, &h->wr, (size_t)n));
-        TRY(dalloc(h, &h->part, (size_t)RED_PARTS * 33));
-        TRY(dalloc(h, &h->dsc, (size_t)256));
-    }
-    if (m > 0 && h->fg_m < m) {
-        TRY(dalloc(h, &h->V, (size_t)n * (m + 1)));
-        TRY(dalloc(h, &h->Z, (size_t)n * m));
-        h->fg_m = m;
-    }
-    return LAIR_OK;
-}
-
-static lair_status norm2_dev(lair_handle *h, int n, const double *v, double *out_dev, double *out_host) {
-    multidot(n, 1, v, n, v, h->part, out_dev, nullptr, h->s);
-    if (out_host) {
-        CU(cudaMemcpyAsync(h->h_dbl, out_dev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-        CU(cudaStreamSynchronize(h->s));
-        flush_timers(h);
-        *out_host = h->h_dbl[0];
-    }
-    return LAIR_OK;
-}
-
-// solve A0 x = b on hierarchy H (device vectors b, x of length n; b already scaled)
-static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int cycle, int max_iter,
-                             lair_report *rep) {
-    Level &L0 = H.lev[0];
-    const DCsr &A = L0.A;
-    const int n = A.nr;
-    const int m = cycle == LAIR_CYCLE_FGMRES ? (h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30) : 0;
-    if (m > 31) return fail(h, LAIR_ERR_INVALID_ARG, "fgmres_restart must be <= 31");
-    TRY(ensure_work(h, n, m));
-    double bn2 = 0.0;
-    TRY(norm2_dev(h, n, b, h->dsc, &bn2));
-    double bn = std::sqrt(bn2);
-    if (bn == 0.0) bn = 1.0;
-    int it = 0, nh = 0;
-    auto hist = [&](double v) {
-        if (rep && rep->hist && nh < rep->hist_cap) rep->hist[nh] = v;
-        ++nh;
-    };
-    const bool mixed = h->o.precision == LAIR_MIXED;
-    double rel = 0.0;
-    lair_status st = LAIR_ERR_NOT_CONVERGED;
-    if (cycle == LAIR_CYCLE_STATIONARY) {
-        for (;;) {
-            // r = b - A x written straight into the cycle's input buffer
-            double *r = mixed ? h->wr : L0.b64;
-            int tr = tbegin(h, "outer_residual", (double)A.nnz * 12.0 + (double)n * (4.0 + 24.0 + (mixed ? 4.0 : 0.0)));
-            sell_residual(L0.A64, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
-            tend(h, tr);
-            finish_partials(1, h->part, h->dsc, h->s);
-            CU(cudaMemcpyAsync(h->h_dbl, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-            CU(cudaStreamSynchronize(h->s));
-
-            flush_timers(h);
-            rel = std::sqrt(h->h_dbl[0]) / bn;
-            hist(rel);
-            if (!std::isfinite(rel)) { st = LAIR_ERR_NAN; break; }
-            if (rel <= tol) { st = LAIR_OK; break; }
-            if (it >= max_iter) break;
-            CU(cudaGraphLaunch(H.graph, h->s));
-            count_launch(H.graph_nodes);
-            h->graph_pending = h->o.timing;
-            if (mixed) axpy_f(n, L0.x32[L0.xfinal], x, h->s);
-            else axpy_d(n, L0.x64[L0.xfinal], x, h->s);
-            ++it;
-        }
-    } else {
-        double *V = h->V, *Z = h->Z;
-        std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), hc(m + 2), y(m + 1);
-        // device scalars: |r|^2 at 1, Hessenberg column at 8 (32), the two CGS2 projections at 48 (64), y at 112 (32)
-        double *hsum = h->dsc + 8, *hbuf = h->dsc + 48, *nrm = h->dsc + 1, *ydev = h->dsc + 112;
-        sell_residual(L0.A64, b, x, V, nullptr, h->part, h->s);
-        finish_partials(1, h->part, nrm, h->s);
-        CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-        CU(cudaStreamSynchronize(h->s));
-
-        flush_timers(h);
-        double beta = std::sqrt(h->h_dbl[0]);
-        rel = beta / bn;
-        hist(rel);
-        while (std::isfinite(rel) && rel > tol && it < max_iter) {
-            scale_by_norm(n, V, nrm, V, h->s);
-            std::fill(g.begin(), g.end(), 0.0);
-            g[0] = beta;
-            int jdone = 0;
-            for (int j = 0; j < m && it < max_iter; ++j) {
-                double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
-                TRY(precond(h, H, vj, zj));
-                ++it;
-                int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
-                sell_spmv<double>(L0.A64, zj, w, h->s);
-                tend(h, ts);
-                CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (j + 1), h->s));
-                int to = tbegin(h, "outer_cgs2", 8.0 * n * (3.0 * (j + 2) + 4.0));
-                cgs_pass(1, n, j + 1, V, n, nullptr, w, h->part, h->s);
-                finish_partials_acc(j + 1, h->part, hbuf, hsum, h->s);
-                cgs_pass(2, n, j + 1, V, n, hbuf, w, h->part, h->s);
-                finish_partials_acc(j + 1, h->part, hbuf + 32, hsum, h->s);
-                cgs_pass(3, n, j + 1, V, n, hbuf + 32, w, h->part, h->s);
-                finish_partials(1, h->part, nrm, h->s);
-                scale_by_norm(n, w, nrm, w, h->s);
-                tend(h, to);
-                CU(cudaMemcpyAsync(h->h_dbl, hsum, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->s));
-                CU(cudaMemcpyAsync(h->h_dbl + 40, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-                CU(cudaStreamSynchronize(h->s));
-
-                flush_timers(h);
-                for (int k = 0; k <= j; ++k) hc[k] = h->h_dbl[k];
-                double hn = std::sqrt(h->h_dbl[40]);
-                hc[j + 1] = hn;
-                for (int k = 0; k < j; ++k) {
-                    double t = cs[k] * hc[k] + sn[k] * hc[k + 1];
-                    hc[k + 1] = -sn[k] * hc[k] + cs[k] * hc[k + 1];
-                    hc[k] = t;
-                }
-                double den = std::sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
-                cs[j] = den > 0.0 ? hc[j] / den : 1.0;
-                sn[j] = den > 0.0 ? hc[j + 1] / den : 0.0;
-                hc[j] = den;
-                g[j + 1] = -sn[j] * g[j];
-                g[j] = cs[j] * g[j];
-                for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hc[k];
-                double est = std::fabs(g[j + 1]) / bn;
-                hist(est);
-                jdone = j + 1;
-                if (est <= tol || hn == 0.0 || !std::isfinite(est)) break;
-            }
-            for (int k = jdone - 1; k >= 0; --k) {
-                double acc = g[k];
-                for (int c = k + 1; c < jdone; ++c) acc -= Hm[(size_t)k * m + c] * y[c];
-                y[k] = acc / Hm[(size_t)k * m + k];
-            }
-            CU(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * jdone, cudaMemcpyHostToDevice, h->s));
-            add_combo(n, jdone, Z, n, ydev, x, h->s);
-            sell_residual(L0.A64, b, x, V, nullptr, h->part, h->s);
-            finish_partials(1, h->part, nrm, h->s);
-            CU(cudaMemcpyAsync(h->h_dbl, nrm, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-            CU(cudaStreamSynchronize(h->s));
-
-            flush_timers(h);
-            beta = std::sqrt(h->h_dbl[0]);
-            rel = beta / bn;
-        }
-        if (!std::isfinite(rel)) st = LAIR_ERR_NAN;
-        else if (rel <= tol) st = LAIR_OK;
-    }
-    CU(cudaStreamSynchronize(h->s));
-    if (rep) {
-        rep->iters = it;
-        rep->final_rel = rel;
-        rep->hist_len = nh < rep->hist_cap ? nh : rep->hist_cap;
-    }
-    if (st == LAIR_ERR_NOT_CONVERGED) fail(h, st, "not converged: relative residual %.3e after %d cycles", rel, it);
-    if (st == LAIR_ERR_NAN) fail(h, st, "residual became NaN/Inf after %d cycles", it);
-    return st;
-}
-
-// row tiles of the batch's systems at level 0 (SEG_TILE rows at most, never across systems)
-static lair_status ensure_tiles(lair_handle *h, const Level &L0) {
-    if (h->segt.tile) return LAIR_OK;
-    const std::vector<int> &seg = L0.seg_h;
-    const int nseg = (int)seg.size() - 1;
-    std::vector<int4> tiles;
-    std::vector<int> first(nseg + 1);
-    for (int q = 0; q < nseg; ++q) {
-        first[q] = (int)tiles.size();
-        for (int b0 = seg[q]; b0 < seg[q + 1]; b0 += SEG_TILE)
-            tiles.push_back(make_int4(q, b0, b0 + SEG_TILE < seg[q + 1] ? b0 + SEG_TILE : seg[q + 1], 0));
-    }
-    first[nseg] = (int)tiles.size();
-    int4 *dt;
-    int *df;
-    double *dp;
-    TRY(dalloc(h, &dt, tiles.size() + 1));
-    TRY(dalloc(h, &df, (size_t)nseg + 1));
-    TRY(dalloc(h, &dp, (tiles.size() + 1) * (size_t)SEG_TILE_PARTS));
-    if (!tiles.empty()) CU(cudaMemcpyAsync(dt, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, h->s));
-    CU(cudaMemcpyAsync(df, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, h->s));
-    CU(cudaStreamSynchronize(h->s));   // the host vectors are copied from pageable memory
-    h->segt.tile = dt;
-    h->segt.ntiles = (int)tiles.size();
-    h->segt.first = df;
-    h->segt.nseg = nseg;
-    h->segt.part = dp;
-    return LAIR_OK;
-}
-
-// batched systems: stationary refinement where every system is tested on its own relative
-// residual and stops being updated once it is <= tol (the cycle itself acts on all systems)
-// the device-side state of the batched outer loops, for FGMRES(m) (m = 0: stationary refinement only)
-static lair_status ensure_batch_ctl(lair_handle *h, int m) {
-    const int nseg = h->nseg;
-    BatchCtl &c = h->bctl;
-    if (!c.bn) {
-        double *bn;
-        TRY(dalloc(h, &bn, (size_t)nseg));
-        c.bn = bn;
-        TRY(dalloc(h, &c.rl, (size_t)nseg));
-        TRY(dalloc(h, &c.its, (size_t)nseg));
-        TRY(dalloc(h, &c.jd, (size_t)nseg));
-        TRY(dalloc(h, &c.run, (size_t)nseg));
-        TRY(dalloc(h, &c.done, (size_t)nseg));
-        TRY(dalloc(h, &c.nan, 1));
-        TRY(dalloc(h, &h->d_ring, (size_t)lair_handle::RING));
-        CU(cudaMallocHost(&h->h_ring, sizeof(int) * lair_handle::RING));
-        for (cudaEvent_t &e : h->ring_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        c.nseg = nseg;
-    }
-    if (m > h->bctl_m) {
-        TRY(dalloc(h, &c.g, (size_t)nseg * (m + 1)));
-        TRY(dalloc(h, &c.cs, (size_t)nseg * m));
-        TRY(dalloc(h, &c.sn, (size_t)nseg * m));
-        TRY(dalloc(h, &c.Hm, (size_t)nseg * (m + 1) * m));
-        h->bctl_m = m;
-    }
-    c.m = m;
-    return LAIR_OK;
-}
-
-// the running-system count of step k: zeroed, filled by the step's control kernel, copied back without waiting
-static int *ring_slot(lair_handle *h, long long k) { return h->d_ring + (int)(k % lair_handle::RING); }
-
-static lair_status ring_post(lair_handle *h, long long k) {
-    const int r = (int)(k % lair_handle::RING);
-    CU(cudaMemcpyAsync(h->h_ring + r, h->d_ring + r, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    CU(cudaEventRecord(h->ring_ev[r], h->s));
-    return LAIR_OK;
-}
-
-// the count of step k, which was queued LAG steps ago and is normally complete already
-static lair_status ring_read(lair_handle *h, long long k, int *out) {
-    const int r = (int)(k % lair_handle::RING);
-    CU(cudaEventSynchronize(h->ring_ev[r]));
-    *out = h->h_ring[r];
-    return LAIR_OK;
-}
-
-static lair_status batch_finish(lair_handle *h, double tol, int *iters, double *rel) {
-    const int nseg = h->nseg;
-    std::vector<int> its(nseg);
-    std::vector<double> rl(nseg);
-    int nan = 0;
-    CU(cudaMemcpyAsync(its.data(), h->bctl.its, sizeof(int) * nseg, cudaMemcpyDeviceToHost, h->s));
-    CU(cudaMemcpyAsync(rl.data(), h->bctl.rl, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->s));
-    CU(cudaMemcpyAsync(&nan, h->bctl.nan, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    CU(cudaStreamSynchronize(h->s));
-    flush_timers(h);
-    lair_status st = nan ? LAIR_ERR_NAN : LAIR_OK;
-    int worst = -1;
-    for (int q = 0; q < nseg; ++q) {
-        if (iters) iters[q] = its[q];
-        if (rel) rel[q] = rl[q];
-        if (st == LAIR_OK && !(rl[q] <= tol)) {
-            st = LAIR_ERR_NOT_CONVERGED;
-            worst = q;
-        }
-    }
-    if (worst >= 0) fail(h, st, "system %d not converged: relative residual %.3e", worst, rl[worst]);
-    return st;
-}
-
-// batched systems, stationary refinement per system: every iteration the residual of the running systems,
-// a per-system stopping test on the device, one V-cycle of the whole batch and the update of the running
-// systems. The host reads the running-system count of an iteration LAG iterations later (without draining
-// the stream) and stops once it is zero; the iterations queued meanwhile change nothing.
-static lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
-                                     int *iters, double *rel) {
-    Level &L0 = H.lev[0];
-    const DCsr &A = L0.A;
-    const int n = A.nr, nseg = h->nseg;
-    const bool mixed = h->o.precision == LAIR_MIXED;
-    TRY(ensure_work(h, n, 0));
-    TRY(ensure_tiles(h, L0));
-    TRY(ensure_batch_ctl(h, 0));
-    if ((size_t)nseg > (size_t)RED_PARTS * 16) return fail(h, LAIR_ERR_UNSUPPORTED, "at most %d systems", RED_PARTS * 16);
-    double *nrm = h->part;                                  // RED_PARTS * 33 doubles >= nseg
-    BatchCtl c = h->bctl;
-    c.tol = tol;
-    c.max_iter = max_iter;
-    SegTiles sta = h->segt;
-    sta.active = c.run;
-    seg_norm2(h->segt, b, nrm, h->s);
-    bat_bnorm(nseg, nrm, const_cast<double *>(c.bn), h->s);
-    CU(cudaMemsetAsync(c.its, 0, sizeof(int) * nseg, h->s));
-    CU(cudaMemsetAsync(c.run, 1, (size_t)nseg, h->s));
-    CU(cudaMemsetAsync(c.nan, 0, sizeof(int), h->s));
-    for (long long it = 0; it <= (long long)max_iter + lair_handle::LAG + 1; ++it) {
-        if (it >= lair_handle::LAG) {
-            int running = 0;
-            TRY(ring_read(h, it - lair_handle::LAG, &running));
-            if (running == 0) break;
-        }
-        double *r = mixed ? h->wr : L0.b64;
-        seg_residual(A, sta, b, x, r, mixed ? L0.b32 : nullptr, nrm, h->s);
-        CU(cudaMemsetAsync(ring_slot(h, it), 0, sizeof(int), h->s));
-        bat_stat_check(c, nrm, (int)std::min<long long>(it, max_iter), ring_slot(h, it), h->s);
-        TRY(ring_post(h, it));
-        CU(cudaGraphLaunch(H.graph, h->s));
-        count_launch(H.graph_nodes);
-        h->graph_pending = h->o.timing;
-        if (mixed) seg_axpy<float>(h->segt, c.run, L0.x32[L0.xfinal], x, h->s);
-        else seg_axpy<double>(h->segt, c.run, L0.x64[L0.xfinal], x, h->s);
-    }
-    return batch_finish(h, tol, iters, rel);
-}
-
-// batched systems, right-preconditioned FGMRES(m) per system in lockstep: one Arnoldi step for
-// every running system per iteration (classical Gram-Schmidt twice on each system's rows), each
-// system with its own Givens rotations, stopping test and restarts
-static lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b, double *x, double tol, int max_iter,
-                                        int *iters, double *rel) {
-    constexpr int HS = BATCH_HS;
-    Level &L0 = H.lev[0];
-    const DCsr &A = L0.A;
-    const int n = A.nr, nseg = h->nseg;
-    const int m = h->o.fgmres_restart > 0 ? h->o.fgmres_restart : 30;
-    TRY(ensure_work(h, n, m));
-    TRY(ensure_tiles(h, L0));
-    TRY(ensure_batch_ctl(h, m));
-    if (!h->d_bat) TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
-    double *hsum = h->d_bat, *hbuf = hsum + (size_t)nseg * HS, *ydev = hbuf + (size_t)nseg * HS,
-           *nrm = ydev + (size_t)nseg * HS;
-    double *V = h->V, *Z = h->Z;
-    BatchCtl c = h->bctl;
-    c.tol = tol;
-    c.max_iter = max_iter;
-    SegTiles sta = h->segt;   // the Arnoldi kernels skip the tiles of systems that are not running
-    sta.active = c.run;
-    seg_norm2(h->segt, b, nrm, h->s);
-    bat_bnorm(nseg, nrm, const_cast<double *>(c.bn), h->s);
-    CU(cudaMemsetAsync(c.its, 0, sizeof(int) * nseg, h->s));
-    CU(cudaMemsetAsync(c.done, 0, (size_t)nseg, h->s));
-    CU(cudaMemsetAsync(c.nan, 0, sizeof(int), h->s));
-    long long step = 0;   // ring position
-    for (int restart = 0; restart <= max_iter; ++restart) {
-        seg_residual(A, h->segt, b, x, V, nullptr, nrm, h->s);
-        CU(cudaMemsetAsync(ring_slot(h, step), 0, sizeof(int), h->s));
-        bat_fg_restart(c, nrm, ring_slot(h, step), h->s);
-        TRY(ring_post(h, step));
-        int running = 0;
-        TRY(ring_read(h, step, &running));   // one wait per restart
-        ++step;
-        flush_timers(h);
-        if (running == 0) break;
-        seg_scale(sta, V, nrm, V, h->s);
-        const long long first = step;
-        for (int j = 0; j < m; ++j) {
-            if (step - first >= lair_handle::LAG) {
-                TRY(ring_read(h, step - lair_handle::LAG, &running));
-                if (running == 0) break;
-            }
-            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n, *w = V + (size_t)(j + 1) * n;
-            TRY(precond(h, H, vj, zj));
-            int ts = tbegin(h, "outer_spmv", bytes_spmv(A, 8.0));
-            sell_spmv<double>(L0.A64, zj, w, h->s);
-            tend(h, ts);
-            CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (size_t)nseg * HS, h->s));
-            for (int pass = 0; pass < 2; ++pass) {
-                seg_multidot(sta, j + 1, V, n, w, HS, hbuf, hsum, h->s);
-                seg_sub_combo(sta, j + 1, V, n, HS, hbuf, w, h->s);
-            }
-            seg_norm2(sta, w, nrm, h->s);
-            seg_scale(sta, w, nrm, w, h->s);
-            CU(cudaMemsetAsync(ring_slot(h, step), 0, sizeof(int), h->s));
-            bat_fg_givens(c, j, hsum, nrm, ring_slot(h, step), h->s);
-            TRY(ring_post(h, step));
-            ++step;
-        }
-        // per-system least-squares solutions y and the update x += Z y of the systems that ran
-        bat_fg_solve_y(c, ydev, h->s);
-        seg_add_combo(h->segt, c.jd, Z, n, HS, ydev, x, h->s);
-    }
-    return batch_finish(h, tol, iters, rel);
-}
-
-static void fill_report(lair_handle *h, Hier &H, lair_report *rep) {
-    if (!rep) return;
-    rep->setup_ms = H.setup_ms;
-    rep->nlevels = (int)H.lev.size();
-    rep->singular_R = H.singular_R;
-    rep->singular_P = H.singular_P;
-    double nnz0 = (double)H.lev[0].A.nnz, tot = 0.0, cyc = 0.0;
-    for (auto &L : H.lev) {
-        tot += L.A.nnz;
-        if (!L.coarsest) cyc += 3.0 * L.A.nnz + L.R.nnz + L.P.nnz;
-        else cyc += (double)L.A.nr * L.A.nr;
-    }
-    rep->op_complexity = tot / nnz0;
-    rep->cycle_complexity = cyc / nnz0;
-}
-
-static lair_status run_solve(lair_handle *h, Hier &H, const double *b, double *x, double tol, int cycle, int max_iter,
-                             lair_report *rep, bool scale) {
-    auto t0 = std::chrono::steady_clock::now();
-    const int n = H.lev[0].A.nr;
-    TRY(ensure_work(h, n, 0));
-    const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-    double *db = h->wb, *dx = h->wx;
-    if (bdev) CU(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-    else CU(cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
-    if (xdev) CU(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-    else CU(cudaMemcpyAsync(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
-    if (scale && H.bs > 1) {
-        launch_block_apply(n / H.bs, H.bs, H.blk_inv, db, h->wr, h->s);
-        CU(cudaMemcpyAsync(db, h->wr, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-    }
-    lair_status st = solve_dev(h, H, db, dx, tol, cycle, max_iter, rep);
-    if (st != LAIR_OK && st != LAIR_ERR_NOT_CONVERGED) return st;
-    if (xdev) CU(cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->s));
-    else CU(cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
-    CU(cudaStreamSynchronize(h->s));
-    fill_report(h, H, rep);
-    if (rep) rep->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return st;
-}
-
 // ---------------------------------------------------------------------------------------
 // input: copy and check the caller's CSR
 // ---------------------------------------------------------------------------------------
