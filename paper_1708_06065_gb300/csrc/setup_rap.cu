@@ -972,17 +972,16 @@ __global__ void k_dense_inverse(int n, const double *__restrict__ LU, const int 
     }
 }
 
-// small coarsest levels (n <= DENSE_SMEM_N): the LU and the inverse entirely in shared memory,
-// one CTA; each warp then forms columns of the inverse from the factors
+// small coarsest levels (n <= DENSE_SMEM_N): the LU factorisation entirely in shared memory, one CTA, written
+// out with its row permutation for k_dense_inv_cols
 constexpr int DENSE_SMEM_N = 128;
 
-__global__ void __launch_bounds__(1024) k_dense_small(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                      const double *__restrict__ val, double *__restrict__ Ainv,
-                                                      int *status) {
+__global__ void __launch_bounds__(256) k_dense_small(int n, const int *__restrict__ rp, const int *__restrict__ col,
+                                                      const double *__restrict__ val, double *__restrict__ LU,
+                                                      int *__restrict__ perm_out, int *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double *D = reinterpret_cast<double *>(smem);            // n x n
-    double *X = D + (size_t)n * n;                           // 32 warps x n
-    int *perm = reinterpret_cast<int *>(X + (size_t)32 * n);
+    double *D = reinterpret_cast<double *>(smem);  // n x n
+    int *perm = reinterpret_cast<int *>(D + (size_t)n * n);
     __shared__ double bv[32];
     __shared__ int bi[32];
     __shared__ int bad;
@@ -1036,41 +1035,62 @@ __global__ void __launch_bounds__(1024) k_dense_small(int n, const int *__restri
         __syncthreads();
     }
     __syncthreads();
+    // a singular matrix leaves perm_out at -1, which k_dense_inv_cols reads as "skip"
+    if (threadIdx.x == 0 && bad) perm_out[0] = -1;
     if (bad) return;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double *x = X + (size_t)wid * n;
-    for (int t = wid; t < n; t += nw) {
-        for (int r = lane; r < n; r += 32) x[r] = perm[r] == t ? 1.0 : 0.0;
-        __syncwarp();
-        for (int k = 0; k < n; ++k) {
-            const double xk = x[k];
-            for (int r = k + 1 + lane; r < n; r += 32) x[r] = fma(-D[r * n + k], xk, x[r]);
-            __syncwarp();
-        }
-        for (int c = n - 1; c >= 0; --c) {
-            if (lane == 0) x[c] = x[c] / D[c * n + c];
-            __syncwarp();
-            const double xc = x[c];
-            for (int r = lane; r < c; r += 32) x[r] = fma(-D[r * n + c], xc, x[r]);
-            __syncwarp();
-        }
-        for (int r = lane; r < n; r += 32) Ainv[(size_t)r * n + t] = x[r];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) LU[e] = D[e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm_out[i] = perm[i];
+}
+
+// columns of the inverse from the factors P A = L U: each warp owns DINV_COLS columns, DINV_ROWS lanes per
+// column take the rows of every substitution step. The device's FP64 pipe serves whole warps, so this keeps
+// the lanes full (a warp per column left most of them idle in the short steps, and a lane per division left 31
+// of 32 idle) and spreads the columns over n / DINV_COLS SMs. Per element the operations and their order are
+// those of the LU solve with e_t as right-hand side: forward x_r -= l_rk x_k, then x_c /= u_cc and
+// x_r -= u_rc x_c for r < c.
+constexpr int DINV_COLS = 4, DINV_ROWS = 32 / DINV_COLS;
+
+__global__ void __launch_bounds__(32) k_dense_inv_cols(int n, const double *__restrict__ LU,
+                                                       const int *__restrict__ perm, double *__restrict__ Ainv) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *x = reinterpret_cast<double *>(smem);  // n x DINV_COLS, row-major
+    if (perm[0] < 0) return;
+    const int lane = threadIdx.x, cg = lane / DINV_ROWS, rl = lane % DINV_ROWS;
+    const int t = blockIdx.x * DINV_COLS + cg;
+    for (int r = rl; r < n; r += DINV_ROWS) x[r * DINV_COLS + cg] = perm[r] == t ? 1.0 : 0.0;
+    __syncwarp();
+    for (int k = 0; k < n; ++k) {
+        const double xk = x[k * DINV_COLS + cg];
+        for (int r = k + 1 + rl; r < n; r += DINV_ROWS)
+            x[r * DINV_COLS + cg] = fma(-LU[(size_t)r * n + k], xk, x[r * DINV_COLS + cg]);
         __syncwarp();
     }
+    for (int c = n - 1; c >= 0; --c) {
+        const double xc = x[c * DINV_COLS + cg] / LU[(size_t)c * n + c];
+        __syncwarp();
+        if (rl == 0) x[c * DINV_COLS + cg] = xc;
+        for (int r = rl; r < c; r += DINV_ROWS) x[r * DINV_COLS + cg] = fma(-LU[(size_t)r * n + c], xc, x[r * DINV_COLS + cg]);
+        __syncwarp();
+    }
+    if (t < n)
+        for (int r = rl; r < n; r += DINV_ROWS) Ainv[(size_t)r * n + t] = x[r * DINV_COLS + cg];
 }
 
 bool dense_small(int n) { return n <= DENSE_SMEM_N; }
 
 void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *status, cudaStream_t s) {
     int n = A.nr;
+    if (n <= 0) return;
     if (n <= DENSE_SMEM_N) {
-        size_t bytes = sizeof(double) * ((size_t)n * n + 32 * (size_t)n) + sizeof(int) * (size_t)n;
+        size_t bytes = sizeof(double) * (size_t)n * n + sizeof(int) * (size_t)n;
         cudaFuncSetAttribute(k_dense_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         // every column of the elimination costs a few block barriers: fewer warps make them cheaper, and a
-        // coarsest level of a few hundred unknowns has little work per column
-        const int tb = n <= 64 ? 128 : (n <= 160 ? 256 : 1024);
-        k_dense_small<<<1, tb, bytes, s>>>(n, A.rp, A.col, A.val, Ainv, status);
-        count_launch();
+        // coarsest level of a hundred unknowns has little work per column
+        const int tb = n <= 64 ? 128 : 256;
+        k_dense_small<<<1, tb, bytes, s>>>(n, A.rp, A.col, A.val, D, perm, status);
+        k_dense_inv_cols<<<(n + DINV_COLS - 1) / DINV_COLS, 32, sizeof(double) * (size_t)n * DINV_COLS, s>>>(
+            n, D, perm, Ainv);
+        count_launch(2);
         return;
     }
     k_dense_build<<<grid_for((long long)n * n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
