@@ -130,7 +130,7 @@ typedef struct {
                                  schedule everywhere. */
     int wait_polls;           /* bound on the polls of every device-side wait (the grid barriers of the
                                  cooperative PMIS kernel, levels above 8192 points); 0 (default): 4,194,304
-                                 polls of at least 64 ns. A wait that runs out makes the call return
+                                 polls of the barrier word. A wait that runs out makes the call return
                                  LAIR_ERR_DEVICE_TIMEOUT; every block of the kernel returns and the CUDA
                                  context stays usable. Small values exist to test that path. */
 } lair_options;

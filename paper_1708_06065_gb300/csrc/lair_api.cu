@@ -491,9 +491,11 @@ static lair_status split_points(lair_handle *h, Temps &t, int l, int n, const Gr
         int *und;
         TRY(t.get(&w, (size_t)n));
         TRY(t.get(&newc, (size_t)n));
+        int *lists;
+        TRY(t.get(&lists, 2 * (size_t)n));
         TRY(new_counts(h, t, &und, 4));
         launch_pmis_init(n, STcf, o.pmis_seed + (uint64_t)l, w, cf, h->s);
-        CU(launch_pmis_all(n, Scf, STcf, w, cf, newc, und, h->status, o.wait_polls, h->s));
+        CU(launch_pmis_all(n, Scf, STcf, w, cf, newc, lists, und, h->status, o.wait_polls, h->s));
     }
     return LAIR_OK;
 }

@@ -45,6 +45,44 @@ __device__ __forceinline__ void set_status(int *st, int code) {
 }
 
 // -------------------------------------------------------------------------------------
+// grid-wide barrier for kernels whose blocks are all resident (cooperative launches), on one
+// monotonic arrival counter *ctl (zero at launch): barrier b is passed once the counter reaches
+// b * gridDim.x. Arrival is an acquire-release atomic and the wait an acquire load, so the
+// barrier orders the blocks' memory operations without separate fences and nothing is reset
+// between barriers. `passed` is thread 0's running target (zero at kernel start). A wait gives
+// up after `limit` polls, or as soon as another block has reported LAIR_ERR_DEVICE_TIMEOUT; it
+// then reports LAIR_ERR_DEVICE_TIMEOUT and the call returns false, after which the kernel
+// returns (its other blocks do the same at their next barrier).
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned *ctl, int *status, long long limit, unsigned &passed) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        passed += gridDim.x;
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctl) : "memory");
+        if (old + 1 != passed) {
+            long long spins = 0;
+            for (;;) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctl) : "memory");
+                if ((int)(v - passed) >= 0) break;
+                ++spins;
+                if (spins > limit ||
+                    ((spins & 63) == 0 && status && *(volatile int *)status == LAIR_ERR_DEVICE_TIMEOUT)) {
+                    set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// -------------------------------------------------------------------------------------
 // warp helpers
 // -------------------------------------------------------------------------------------
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }

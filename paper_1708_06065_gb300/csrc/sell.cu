@@ -35,51 +35,102 @@ __device__ __forceinline__ int find_desc(const SellDesc *__restrict__ d, int nd,
     return lo;
 }
 
-// one CTA per window: order the window's rows by decreasing length (stable)
-__global__ void __launch_bounds__(SELL_WINDOW) k_sell_sort_multi(const SellDesc *__restrict__ d, int nd) {
-    // keys (INT_MAX - length, position) in a bitonic network: decreasing length, ties by position
-    __shared__ unsigned long long key[SELL_WINDOW];
-    __shared__ int rid[SELL_WINDOW];
-    const int p = find_desc(d, nd, blockIdx.x, 0);
-    const SellDesc v = d[p];
-    const int w0 = (blockIdx.x - v.win0) * SELL_WINDOW;
-    const int t = threadIdx.x;
-    const int cnt = min(SELL_WINDOW, v.nrows - w0);
-    key[t] = ~0ull;
-    if (t < cnt) {
-        const int i = v.rows_in ? v.rows_in[w0 + t] : w0 + t;
-        rid[t] = i;
-        key[t] = ((unsigned long long)(0x7fffffff - (v.rp[i + 1] - v.rp[i])) << 32) | (unsigned)t;
-    }
-    __syncthreads();
-    // a window already in non-increasing row length (every row of a stencil's interior) keeps its order: the
-    // stable sort would return it unchanged
-    const unsigned kt = (unsigned)(key[t] >> 32);
-    const bool in_order = t + 1 >= cnt || kt <= (unsigned)(key[t + 1] >> 32);
-    if (__syncthreads_and(in_order)) {
-        if (t < cnt) v.row_out[w0 + t] = rid[t];
-        return;
-    }
-    for (int k = 2; k <= SELL_WINDOW; k <<= 1)
+// Ascending bitonic sort of 32 R distinct keys held by a warp, element e = 32 r + lane in key[r]: exchanges at
+// distance < 32 through shuffles, the others inside a lane's registers (compile-time indices only).
+template <int R>
+__device__ __forceinline__ void warp_sort_keys(unsigned (&key)[R], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
-            const int o = t ^ j;
-            if (o > t) {
-                const unsigned long long a = key[t], b = key[o];
-                if (((t & k) == 0) ? a > b : a < b) {
-                    key[t] = b;
-                    key[o] = a;
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int r2 = r ^ (j >> 5);
+                    if (r2 > r) {
+                        const bool up = ((32 * r + lane) & k) == 0;
+                        if (up ? key[r] > key[r2] : key[r] < key[r2]) {
+                            const unsigned t = key[r];
+                            key[r] = key[r2];
+                            key[r2] = t;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned pk = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const bool up = ((32 * r + lane) & k) == 0, lower = (lane & j) == 0;
+                    if (lower == up ? pk < key[r] : pk > key[r]) key[r] = pk;
                 }
             }
-            __syncthreads();
         }
-    if (t < cnt) v.row_out[w0 + t] = rid[(int)(key[t] & 0xffffffffu)];
+    }
+}
+
+constexpr int SORT_WARPS = 8;                 // windows in flight per CTA (one per warp)
+constexpr int SELL_RPL = SELL_WINDOW / 32;    // rows of a window per lane
+
+// Order the rows of every window by decreasing length (ties: window position), one warp per window: row t of
+// the window is lane t % 32's entry t / 32, so the loads of a window are coalesced and every lane has eight
+// independent row lengths in flight. A window already in non-increasing order (the interior of a stencil)
+// is written as it is; the others go through a register bitonic sort of (length, position) keys.
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_sell_sort_multi(const SellDesc *__restrict__ d, int nd,
+                                                                     int nwin) {
+    __shared__ int stage[SORT_WARPS][SELL_WINDOW];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    for (int w = blockIdx.x * SORT_WARPS + wq; w < nwin; w += gridDim.x * SORT_WARPS) {
+        const int p = find_desc(d, nd, w, 0);
+        const int *rows_in = d[p].rows_in, *rp = d[p].rp;
+        int *row_out = d[p].row_out;
+        const int w0 = (w - d[p].win0) * SELL_WINDOW;
+        const int cnt = min(SELL_WINDOW, d[p].nrows - w0);
+        int rid[SELL_RPL], len[SELL_RPL];
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k) {
+            const int t = 32 * k + lane;
+            rid[k] = t < cnt ? (rows_in ? rows_in[w0 + t] : w0 + t) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k) len[k] = rid[k] >= 0 ? rp[rid[k] + 1] - rp[rid[k]] : -1;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k) {
+            const int down = __shfl_down_sync(0xffffffffu, len[k], 1);
+            const int wrap = __shfl_sync(0xffffffffu, k + 1 < SELL_RPL ? len[k + 1 < SELL_RPL ? k + 1 : k] : 0, 0);
+            const int next = lane < 31 ? down : (k + 1 < SELL_RPL ? wrap : -1);
+            if (32 * k + lane + 1 < cnt && len[k] < next) ok = false;
+        }
+        if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+            for (int k = 0; k < SELL_RPL; ++k)
+                if (32 * k + lane < cnt) row_out[w0 + 32 * k + lane] = rid[k];
+            continue;
+        }
+        // keys: (2^23 - 1 - length) in the high bits, the window position in the low 8; padding last
+        unsigned key[SELL_RPL];
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k) {
+            const int t = 32 * k + lane;
+            stage[wq][t] = rid[k];
+            key[k] = t < cnt ? ((unsigned)(0x7fffff - min(len[k], 0x7fffff)) << 8) | (unsigned)t : 0xffffffffu;
+        }
+        __syncwarp();
+        warp_sort_keys<SELL_RPL>(key, lane);
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k)
+            if (32 * k + lane < cnt) row_out[w0 + 32 * k + lane] = stage[wq][key[k] & 0xffu];
+        __syncwarp();
+    }
 }
 
 // slice lengths in entries (32 x longest row of the slice), one warp per slice; also their
-// 64-bit sum per group, so that an int overflow of the offsets is caught on the host
+// 64-bit sum per group (two groups: FP32 and FP64 views), so that an int overflow of the offsets is caught on
+// the host. Each warp adds its own sums once at the end.
 __global__ void k_sell_len_multi(const SellDesc *__restrict__ d, int nd, int nlin, int *__restrict__ cnt,
                                  unsigned long long *__restrict__ gsum) {
     const int lane = threadIdx.x & 31;
+    unsigned long long s0 = 0, s1 = 0;
     for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nlin; q += (gridDim.x * blockDim.x) >> 5) {
         const int p = find_desc(d, nd, q, 1);
         const SellDesc &v = d[p];
@@ -93,8 +144,13 @@ __global__ void k_sell_len_multi(const SellDesc *__restrict__ d, int nd, int nli
         l = __reduce_max_sync(0xffffffffu, l);
         if (lane == 0) {
             cnt[v.sl0 + sl] = 32 * l;
-            atomicAdd(&gsum[v.group], 32ull * (unsigned long long)l);
+            if (v.group == 0) s0 += 32ull * (unsigned long long)l;
+            else s1 += 32ull * (unsigned long long)l;
         }
+    }
+    if (lane == 0) {
+        if (s0) atomicAdd(&gsum[0], s0);
+        if (s1) atomicAdd(&gsum[1], s1);
     }
 }
 
@@ -301,7 +357,7 @@ void launch_frows(int n, const int8_t *cf, const int *cscan, int *frows, cudaStr
 void launch_sell_prepare_multi(const SellDesc *d, int nd, int nwin, int nlin, int *cnt, unsigned long long *gsum,
                                cudaStream_t s) {
     if (nwin <= 0) return;
-    k_sell_sort_multi<<<nwin, SELL_WINDOW, 0, s>>>(d, nd);
+    k_sell_sort_multi<<<grid_for((long long)nwin, SORT_WARPS, device_sms() * 16), 32 * SORT_WARPS, 0, s>>>(d, nd, nwin);
     k_sell_len_multi<<<grid_for((long long)nlin * 32, 256), 256, 0, s>>>(d, nd, nlin, cnt, gsum);
     count_launch(2);
 }

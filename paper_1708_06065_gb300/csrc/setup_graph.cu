@@ -242,45 +242,14 @@ __device__ __forceinline__ bool beats(double wi, int i, double wj, int j) {
 }
 
 // -------------------------------------------------------------------------------------
-// All PMIS rounds of a level in one cooperative launch. A round: every undecided point whose
-// weight beats those of all undecided points in S_i and ST_i is selected; grid barrier; stop
-// when the select pass saw no undecided point; selected points become C and their undecided
-// dependants (ST_i) F; grid barrier. Two selected points never lie in each other's ST (they
-// would beat each other), so marking C and F in one pass is race-free. A decided point's
-// weight is set to -1, so the select pass reads one array per neighbour.
-// ctl[0] barrier arrivals, ctl[1] barrier generation, ctl[2 + r % 2] undecided count of round r
-// (zero on entry). Every barrier wait is bounded by `limit` polls; a wait that gives up sets
+// PMIS rounds. A round: every undecided point whose weight beats those of all undecided points
+// in S_i and ST_i is selected; stop when no point was undecided; selected points become C and
+// their undecided dependants (ST_i) F. A decided point's weight is set to -1, so the select
+// pass reads one array per neighbour. All rounds of a level run in one launch: one thread-block
+// cluster for small levels (k_pmis_cluster), a cooperative grid above (k_pmis_coop), whose
+// grid-barrier waits are bounded by `limit` polls; a wait that gives up sets
 // LAIR_ERR_DEVICE_TIMEOUT and the block returns (so do the others at their next barrier).
 // -------------------------------------------------------------------------------------
-__device__ bool grid_barrier(int *ctl, int *status, long long limit) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile int *gen = ctl + 1;
-        const int g = *gen;
-        __threadfence();
-        if (atomicAdd(ctl, 1) == (int)gridDim.x - 1) {
-            atomicExch(ctl, 0);
-            __threadfence();
-            atomicAdd(ctl + 1, 1);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > limit) {
-                    set_status(status, LAIR_ERR_DEVICE_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // true if w_i beats the weight of every undecided j among col[b..e) (decided points carry
 // weight -1); the neighbours are read four at a time so that their loads overlap
 // (L2: the weights are read from L2, past this SM's L1, as other CTAs update them between rounds)
@@ -369,29 +338,53 @@ __device__ __forceinline__ bool pmis_beats_both(double wi, int i, const Graph &S
     return true;
 }
 
+// All PMIS rounds of a level in one cooperative launch, one thread per candidate point. The candidates of
+// round 0 are all points; every select pass appends the points it finds undecided to a list (warp-aggregated
+// atomics, two lists used in turn), and that list is the next round's candidates and this round's marking
+// set, so rounds after the first few touch only the points still undecided. The order of a list varies from
+// run to run; the sets do not: the selection is a function of the weights alone, and two selected points never
+// lie in each other's ST (they would beat each other), so marking C and F in one pass is race-free.
+// ctl[0] the grid barrier's arrival counter, ctl[2 + r % 2] the length of round r's list (all zero on entry);
+// lists: 2 n ints.
 __global__ void __launch_bounds__(PMIS_THREADS, 2) k_pmis_coop(int n, Graph S, Graph ST, double *w,
-                                                   int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *ctl,
-                                                   int *status, long long limit) {
+                                                   int8_t *__restrict__ cf, int8_t *__restrict__ newc, int *lists,
+                                                   int *ctl, int *status, long long limit) {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    unsigned *bar = reinterpret_cast<unsigned *>(ctl);
+    unsigned passed = 0;
+    int m_in = n;
     for (int round = 0; round <= n; ++round) {
-        int local = 0;
-        for (int i = t0; i < n; i += stride) {
-            int8_t nc = 0;
-            const double wi = w[i];
-            if (wi >= 0.0) {
-                ++local;
-                nc = pmis_beats_both(wi, i, S, ST, w);
+        const int *in = round == 0 ? nullptr : lists + (size_t)((round - 1) & 1) * n;
+        int *out = lists + (size_t)(round & 1) * n;
+        int *cnt = ctl + 2 + (round & 1);
+        for (int base = t0 - lane; base < m_in; base += stride) {
+            const int idx = base + lane;
+            int i = 0;
+            double wi = -1.0;
+            if (idx < m_in) {
+                i = in ? in[idx] : idx;
+                wi = w[i];
             }
-            newc[i] = nc;
+            const bool und = wi >= 0.0;
+            const unsigned bal = __ballot_sync(0xffffffffu, und);
+            if (!bal) continue;
+            const int leader = __ffs(bal) - 1;
+            int pos = 0;
+            if (lane == leader) pos = atomicAdd(cnt, __popc(bal));
+            pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(bal & ((1u << lane) - 1u));
+            if (und) {
+                out[pos] = i;
+                newc[i] = pmis_beats_both(wi, i, S, ST, w);
+            }
         }
-        local = __reduce_add_sync(0xffffffffu, local);
-        if (lane_id() == 0 && local) atomicAdd(ctl + 2 + (round & 1), local);
-        if (!grid_barrier(ctl, status, limit)) return;
-        const int und = *(volatile int *)(ctl + 2 + (round & 1));
-        if (und == 0) return;
-        if (t0 == 0) ctl[2 + ((round + 1) & 1)] = 0;   // nobody adds to it before the next barrier
-        for (int i = t0; i < n; i += stride) {
+        if (!grid_barrier(bar, status, limit, passed)) return;
+        const int m = *(volatile int *)cnt;
+        if (m == 0) return;
+        if (t0 == 0) ctl[2 + ((round + 1) & 1)] = 0;   // read by everyone a round ago, appended to next round
+        for (int idx = t0; idx < m; idx += stride) {
+            const int i = out[idx];
             if (!newc[i]) continue;
             cf[i] = CF_C;
             w[i] = -1.0;
@@ -403,7 +396,8 @@ __global__ void __launch_bounds__(PMIS_THREADS, 2) k_pmis_coop(int n, Graph S, G
                 }
             }
         }
-        if (!grid_barrier(ctl, status, limit)) return;
+        if (!grid_barrier(bar, status, limit, passed)) return;
+        m_in = m;
     }
 }
 
@@ -1233,8 +1227,8 @@ void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *
 }
 
 // ctl: 4 ints, zero
-cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
-                            int *status, int wait_polls, cudaStream_t s) {
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *lists,
+                            int *ctl, int *status, int wait_polls, cudaStream_t s) {
     long long limit = wait_polls > 0 ? (long long)wait_polls : GRID_WAIT_POLLS;
     if (n <= PMIS_CLUSTER * PMIS_THREADS) {
         const int c = n > 0 ? (n + PMIS_THREADS - 1) / PMIS_THREADS : 1;
@@ -1265,8 +1259,8 @@ cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, i
     int grid = sms * (per_sm < 2 ? per_sm : 2);
     const int need = (n + PMIS_THREADS - 1) / PMIS_THREADS;
     if (grid > need) grid = need > 0 ? need : 1;
-    void *args[] = {(void *)&n,   (void *)&S,    (void *)&ST,     (void *)&w,    (void *)&cf,
-                    (void *)&newc, (void *)&ctl, (void *)&status, (void *)&limit};
+    void *args[] = {(void *)&n,     (void *)&S,   (void *)&ST,     (void *)&w,    (void *)&cf,
+                    (void *)&newc,  (void *)&lists, (void *)&ctl, (void *)&status, (void *)&limit};
     e = cudaLaunchCooperativeKernel((const void *)k_pmis_coop, dim3(grid), dim3(PMIS_THREADS), args, 0, s);
     count_launch();
     return e;

@@ -32,8 +32,9 @@ void launch_sort_rows(int nr, const int *rp, int *col, double *val, int *lists, 
 void launch_pmis_init(int n, const Graph &ST, uint64_t seed, double *w, int8_t *cf, cudaStream_t s);
 // every grid-barrier wait of the cooperative PMIS kernel gives up after wait_polls polls (0: GRID_WAIT_POLLS)
 constexpr long long GRID_WAIT_POLLS = 1ll << 22;
-cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *ctl,
-                            int *status, int wait_polls, cudaStream_t s);
+// lists: 2 n ints of scratch; ctl: 4 ints, zero
+cudaError_t launch_pmis_all(int n, const Graph &S, const Graph &ST, double *w, int8_t *cf, int8_t *newc, int *lists,
+                            int *ctl, int *status, int wait_polls, cudaStream_t s);
 void launch_rs_count(const int2 *blocks, int nblocks, const Graph &S, int *maxcnt, cudaStream_t s);
 // bucket-queue first pass: blocks of at most RSB_MAX_N points, lambda below nb <= 256 buckets, at most dl points
 // whose lambda changes in one step

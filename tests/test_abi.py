@@ -119,3 +119,32 @@ def test_nodal_user_splitting_must_agree_within_nodes():
     assert O.Hierarchy(s, cf_user=cfu, nodal=2).status == 1
     cfu[5] = 1
     assert O.Hierarchy(s, cf_user=cfu, nodal=2).status == 0
+
+
+def test_binding_structs_match_the_header():
+    """Every ctypes structure of the binding has the C layout of its header struct: the same size and
+    the same offset for every field (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1708_06065_gb300 import lair
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"lair_options": lair.lair_options, "lair_report": lair.lair_report,
+               "lair_level_info": lair.lair_level_info, "lair_csr": lair.lair_csr}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lair.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
