@@ -649,7 +649,7 @@ static lair_status coarsen(lair_handle *h, Hier &H, int l, const int8_t *cf_user
         int *cnt;
         double *nd;
         TRY(new_counts(h, t, &cnt, K.nr));
-        TRY(t.get(&nd, (size_t)K.nr));
+        TRY(t.get(&nd, 2 * (size_t)K.nr));
         launch_lump(0, K, klen, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
         DCsr Kl;
         Kl.nr = Kl.nc = K.nr;
@@ -1354,7 +1354,7 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
             int *cnt;
             double *nd;
             TRY(new_counts(h, t, &cnt, A.nr));
-            TRY(t.get(&nd, (size_t)A.nr));
+            TRY(t.get(&nd, 2 * (size_t)A.nr));
             if (o.nodal > 1) launch_lump_nodal(0, o.nodal, A, nullptr, o.lump_tol, cnt, nullptr, h->status, h->s);
             else launch_lump(0, A, nullptr, o.lump_tol, cnt, nd, nullptr, h->status, h->s);
             DCsr Kl;

@@ -9,6 +9,8 @@
 // The sweeps of a level then read only the rows they update (F rows, or C rows).
 #include "setup_kernels.cuh"
 
+#include <climits>
+
 namespace lair {
 
 constexpr int SELL_WINDOW = 256;
@@ -70,11 +72,13 @@ __device__ __forceinline__ void warp_sort_keys(unsigned (&key)[R], int lane) {
 
 constexpr int SORT_WARPS = 8;                 // windows in flight per CTA (one per warp)
 constexpr int SELL_RPL = SELL_WINDOW / 32;    // rows of a window per lane
+constexpr int SELL_COUNT_SORT = 16;           // windows with fewer distinct lengths than this: counting sort
 
 // Order the rows of every window by decreasing length (ties: window position), one warp per window: row t of
 // the window is lane t % 32's entry t / 32, so the loads of a window are coalesced and every lane has eight
 // independent row lengths in flight. A window already in non-increasing order (the interior of a stencil)
-// is written as it is; the others go through a register bitonic sort of (length, position) keys.
+// is written as it is, one with a narrow range of lengths goes through a counting sort by length, the others
+// through a register bitonic sort of (length, position) keys.
 __global__ void __launch_bounds__(32 * SORT_WARPS) k_sell_sort_multi(const SellDesc *__restrict__ d, int nd,
                                                                      int nwin) {
     __shared__ int stage[SORT_WARPS][SELL_WINDOW];
@@ -105,6 +109,34 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_sell_sort_multi(const SellD
 #pragma unroll
             for (int k = 0; k < SELL_RPL; ++k)
                 if (32 * k + lane < cnt) row_out[w0 + 32 * k + lane] = rid[k];
+            continue;
+        }
+        // few distinct lengths (a stencil's boundary rows): a counting sort, longest first, window order inside
+        // a length -- the same order as the stable sort, at one ballot per length and row register
+        int lo = INT_MAX, hi = -1;
+#pragma unroll
+        for (int k = 0; k < SELL_RPL; ++k)
+            if (len[k] >= 0) {
+                lo = min(lo, len[k]);
+                hi = max(hi, len[k]);
+            }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (hi - lo < SELL_COUNT_SORT) {
+            const unsigned below = (1u << lane) - 1u;
+            int pos[SELL_RPL];
+            int base = 0;
+            for (int v = hi; v >= lo; --v) {
+#pragma unroll
+                for (int k = 0; k < SELL_RPL; ++k) {
+                    const unsigned m = __ballot_sync(0xffffffffu, len[k] == v);
+                    if (len[k] == v) pos[k] = base + __popc(m & below);
+                    base += __popc(m);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SELL_RPL; ++k)
+                if (len[k] >= 0) row_out[w0 + pos[k]] = rid[k];
             continue;
         }
         // keys: (2^23 - 1 - length) in the high bits, the window position in the low 8; padding last

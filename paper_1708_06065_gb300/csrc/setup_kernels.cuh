@@ -142,8 +142,9 @@ cudaError_t launch_spgemm_rows(const SpgemmArgs &g, int nr, const int *lists, co
                                const int counts_host[SPGEMM_BINS], int ubmax, int *skeys, double *svals, cudaStream_t s);
 unsigned spgemm_big_cap(int ubmax);
 void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tval, DCsr &Z, cudaStream_t s);
-// K's rows: rp[i] .. rp[i + 1], or rp[i] .. rp[i] + len[i] when len is given
-void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
+// K's rows: rp[i] .. rp[i + 1], or rp[i] .. rp[i] + len[i] when len is given; rowst: 2 K.nr doubles (16-byte
+// aligned) written by phase 0 and read by phase 1
+void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *rowst, const DCsr *out,
                  int *status, cudaStream_t s);
 // ---- setup_nodal.cu: the nodal (block) hierarchy, nodes of k <= NODAL_MAX consecutive unknowns -------------
 constexpr int NODAL_MAX = 8;

@@ -770,53 +770,62 @@ void launch_copy_rows(int nr, const int *off, const int *tcol, const double *tva
 // ---------------------------------------------------------------------------------------
 // Row i of K is col/val[rp[i], rp[i + 1]) or, when len is given, col/val[rp[i], rp[i] + len[i]) (the
 // staging area of a product that was not compacted).
+// Lumping (Sec. 3.3): entries with |k_ij| < tol * max_k |k_ik| off the diagonal are added to the diagonal in
+// ascending column order starting from k_ii. Count: the row's maximum and diagonal in one pass, then the
+// dropped sum and the kept count; the lumped diagonal and the threshold are kept per row (rowst[2 i], [2 i + 1])
+// so that the fill reads the row once.
 __global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__restrict__ len, const int *__restrict__ col,
                              const double *__restrict__ val, double tol, int *__restrict__ cnt,
-                             double *__restrict__ newdiag, int *status) {
+                             double2 *__restrict__ rowst, int *status) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int b = rp[i], e = len ? b + len[i] : rp[i + 1];
-        double m = 0.0;
-        for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
-        double thr = __dmul_rn(tol, m);
-        double d = 0.0;
+        double m = 0.0, d = 0.0;
         bool has = false;
-        for (int k = b; k < e; ++k)
-            if (col[k] == i) { d = val[k]; has = true; }
+        for (int k = b; k < e; ++k) {
+            const double v = val[k];
+            m = fmax(m, fabs(v));
+            if (col[k] == i) {
+                d = v;
+                has = true;
+            }
+        }
         if (!has) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
+        const double thr = __dmul_rn(tol, m);
         int c = 0;
         for (int k = b; k < e; ++k) {
             if (col[k] != i && fabs(val[k]) < thr) d = __dadd_rn(d, val[k]);
             else ++c;
         }
         cnt[i] = c;
-        newdiag[i] = d;
+        rowst[i] = make_double2(d, thr);
     }
 }
 
 __global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__restrict__ len, const int *__restrict__ col,
-                            const double *__restrict__ val, double tol, const double *__restrict__ newdiag,
+                            const double *__restrict__ val, const double2 *__restrict__ rowst,
                             const int *__restrict__ orp, int *__restrict__ ocol, double *__restrict__ oval) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int b = rp[i], e = len ? b + len[i] : rp[i + 1];
-        double m = 0.0;
-        for (int k = b; k < e; ++k) m = fmax(m, fabs(val[k]));
-        double thr = __dmul_rn(tol, m);
+        const double2 st = rowst[i];
         int p = orp[i];
         for (int k = b; k < e; ++k) {
-            if (col[k] != i && fabs(val[k]) < thr) continue;
-            ocol[p] = col[k];
-            oval[p] = col[k] == i ? newdiag[i] : val[k];
+            const int j = col[k];
+            const double v = val[k];
+            if (j != i && fabs(v) < st.y) continue;
+            ocol[p] = j;
+            oval[p] = j == i ? st.x : v;
             ++p;
         }
     }
 }
 
-void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *newdiag, const DCsr *out,
+void launch_lump(int phase, const DCsr &K, const int *len, double tol, int *cnt, double *rowst, const DCsr *out,
                  int *status, cudaStream_t s) {
+    double2 *st = reinterpret_cast<double2 *>(rowst);
     if (phase == 0)
-        k_lump_count<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, tol, cnt, newdiag, status);
+        k_lump_count<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, tol, cnt, st, status);
     else
-        k_lump_fill<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, tol, newdiag, out->rp, out->col,
+        k_lump_fill<<<grid_for(K.nr, 256), 256, 0, s>>>(K.nr, K.rp, len, K.col, K.val, st, out->rp, out->col,
                                                          out->val);
     count_launch();
 }
