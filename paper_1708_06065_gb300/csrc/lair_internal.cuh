@@ -23,6 +23,10 @@ constexpr int8_t CF_F = 0;
 constexpr int8_t CF_C = 1;
 constexpr int8_t CF_U = -1;
 
+// the lumping kernels read a row of the Galerkin product ROW_CHUNK entries at a time (predicated loads, all
+// independent), so a row costs a round of memory latency per chunk instead of one per entry
+constexpr int ROW_CHUNK = 8;
+
 struct DCsr {
     int nr = 0, nc = 0, nnz = 0;
     int *rp = nullptr;

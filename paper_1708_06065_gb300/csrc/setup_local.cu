@@ -508,35 +508,81 @@ __global__ void __launch_bounds__(256) k_local_cta(LocalArgs a, const int *__res
     }
 }
 
-__global__ void k_local_bin(int nc, int group, const int *__restrict__ nb_rp, int *__restrict__ lists,
-                            int *__restrict__ counts, int *__restrict__ smax, int tmax, int wmax) {
-    const unsigned lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    int local_max = 0;
-    for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; base < nc; base += stride) {
-        const int c = (int)(base + lane);
-        const bool act = c < nc;
-        const int s = act ? nb_rp[(long long)c * group + 1] - nb_rp[(long long)c * group] : 0;
-        const int b = s <= tmax ? 0 : (s <= wmax ? 1 : 2);
-        local_max = max(local_max, s);
-        for (int bb = 0; bb < 3; ++bb) {       // one atomic per warp and bin
-            const unsigned m = __ballot_sync(0xffffffffu, act && b == bb);
-            if (!m) continue;
-            int p0 = 0;
-            if (lane == __ffs(m) - 1) p0 = atomicAdd(&counts[bb], __popc(m));
-            p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
-            if (act && b == bb) lists[(size_t)bb * nc + p0 + __popc(m & ((1u << lane) - 1u))] = c;
-        }
+constexpr int BIN_THREADS = 256;
+
+// Each block bins a contiguous chunk of the systems: pass 1 counts the chunk's systems per bin (and the largest
+// size) in shared memory and reserves the block's room in every list with one global atomic per bin; pass 2
+// writes the chunk's systems, tile by tile in index order, at ballot-and-prefix positions inside that room.
+// The lists are ordered by chunk reservation, which varies from run to run; which team solves which system
+// does not change its result.
+__global__ void __launch_bounds__(BIN_THREADS) k_local_bin(int nc, int group, const int *__restrict__ nb_rp,
+                                                           int *__restrict__ lists, int *__restrict__ counts,
+                                                           int *__restrict__ smax, int tmax, int wmax) {
+    __shared__ int s_cnt[3], s_base[3], s_max;
+    __shared__ int s_warp[BIN_THREADS / 32][3];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long per = ((long long)nc + gridDim.x - 1) / gridDim.x;
+    const long long c0 = (long long)blockIdx.x * per, c1 = min((long long)nc, c0 + per);
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    int cnt0 = 0, cnt1 = 0, cnt2 = 0, mx = 0;
+    for (long long c = c0 + threadIdx.x; c < c1; c += BIN_THREADS) {
+        const int sz = nb_rp[c * group + 1] - nb_rp[c * group];
+        cnt0 += sz <= tmax;
+        cnt1 += sz > tmax && sz <= wmax;
+        cnt2 += sz > wmax;
+        mx = max(mx, sz);
     }
-    local_max = __reduce_max_sync(0xffffffffu, local_max);
-    if (lane == 0 && local_max > 0) atomicMax(smax, local_max);
+    cnt0 = __reduce_add_sync(0xffffffffu, cnt0);
+    cnt1 = __reduce_add_sync(0xffffffffu, cnt1);
+    cnt2 = __reduce_add_sync(0xffffffffu, cnt2);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) {
+        if (cnt0) atomicAdd(&s_cnt[0], cnt0);
+        if (cnt1) atomicAdd(&s_cnt[1], cnt1);
+        if (cnt2) atomicAdd(&s_cnt[2], cnt2);
+        if (mx) atomicMax(&s_max, mx);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]) : 0;
+    if (threadIdx.x == 0 && s_max > 0) atomicMax(smax, s_max);
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    for (long long t0 = c0; t0 < c1; t0 += BIN_THREADS) {
+        const long long c = t0 + threadIdx.x;
+        const bool act = c < c1;
+        const int sz = act ? nb_rp[c * group + 1] - nb_rp[c * group] : 0;
+        const int b = sz <= tmax ? 0 : (sz <= wmax ? 1 : 2);
+        unsigned m[3];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            m[bb] = __ballot_sync(0xffffffffu, act && b == bb);
+            if (lane == 0) s_warp[wid][bb] = __popc(m[bb]);
+        }
+        __syncthreads();
+        if (act) {
+            int off = s_base[b];
+            for (int w = 0; w < wid; ++w) off += s_warp[w][b];
+            lists[(size_t)b * nc + off + __popc(m[b] & below)] = (int)c;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            int tot = 0;
+            for (int w = 0; w < BIN_THREADS / 32; ++w) tot += s_warp[w][threadIdx.x];
+            s_base[threadIdx.x] += tot;
+        }
+        __syncthreads();
+    }
 }
 
 void launch_local_bin(int nc, const int *nb_rp, int *lists, int *counts, int *smax, cudaStream_t s, int stride,
                       int tmax, int wmax) {
+    if (nc <= 0) return;
     tmax = tmax < 0 ? 0 : (tmax > THREAD_SMAX ? THREAD_SMAX : tmax);
     wmax = wmax < tmax ? tmax : (wmax > 32 ? 32 : wmax);
-    k_local_bin<<<grid_for(nc, 256), 256, 0, s>>>(nc, stride, nb_rp, lists, counts, smax, tmax, wmax);
+    k_local_bin<<<grid_for(nc, BIN_THREADS, device_sms() * 8), BIN_THREADS, 0, s>>>(nc, stride, nb_rp, lists, counts,
+                                                                                     smax, tmax, wmax);
     count_launch();
 }
 

@@ -778,23 +778,43 @@ __global__ void k_lump_count(int n, const int *__restrict__ rp, const int *__res
                              const double *__restrict__ val, double tol, int *__restrict__ cnt,
                              double2 *__restrict__ rowst, int *status) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int b = rp[i], e = len ? b + len[i] : rp[i + 1];
+        const int b = rp[i], e = len ? b + len[i] : rp[i + 1];
         double m = 0.0, d = 0.0;
         bool has = false;
-        for (int k = b; k < e; ++k) {
-            const double v = val[k];
-            m = fmax(m, fabs(v));
-            if (col[k] == i) {
-                d = v;
-                has = true;
+        for (int k0 = b; k0 < e; k0 += ROW_CHUNK) {
+            int cc[ROW_CHUNK];
+            double v[ROW_CHUNK];
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                cc[u] = k0 + u < e ? col[k0 + u] : -1;
+                v[u] = k0 + u < e ? val[k0 + u] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                m = fmax(m, fabs(v[u]));
+                if (cc[u] == i) {
+                    d = v[u];
+                    has = true;
+                }
             }
         }
         if (!has) set_status(status, LAIR_ERR_ZERO_DIAGONAL);
         const double thr = __dmul_rn(tol, m);
         int c = 0;
-        for (int k = b; k < e; ++k) {
-            if (col[k] != i && fabs(val[k]) < thr) d = __dadd_rn(d, val[k]);
-            else ++c;
+        for (int k0 = b; k0 < e; k0 += ROW_CHUNK) {
+            int cc[ROW_CHUNK];
+            double v[ROW_CHUNK];
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                cc[u] = k0 + u < e ? col[k0 + u] : i;
+                v[u] = k0 + u < e ? val[k0 + u] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                if (k0 + u >= e) break;
+                if (cc[u] != i && fabs(v[u]) < thr) d = __dadd_rn(d, v[u]);
+                else ++c;
+            }
         }
         cnt[i] = c;
         rowst[i] = make_double2(d, thr);
@@ -805,16 +825,25 @@ __global__ void k_lump_fill(int n, const int *__restrict__ rp, const int *__rest
                             const double *__restrict__ val, const double2 *__restrict__ rowst,
                             const int *__restrict__ orp, int *__restrict__ ocol, double *__restrict__ oval) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int b = rp[i], e = len ? b + len[i] : rp[i + 1];
+        const int b = rp[i], e = len ? b + len[i] : rp[i + 1];
         const double2 st = rowst[i];
         int p = orp[i];
-        for (int k = b; k < e; ++k) {
-            const int j = col[k];
-            const double v = val[k];
-            if (j != i && fabs(v) < st.y) continue;
-            ocol[p] = j;
-            oval[p] = j == i ? st.x : v;
-            ++p;
+        for (int k0 = b; k0 < e; k0 += ROW_CHUNK) {
+            int cc[ROW_CHUNK];
+            double v[ROW_CHUNK];
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                cc[u] = k0 + u < e ? col[k0 + u] : i;
+                v[u] = k0 + u < e ? val[k0 + u] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROW_CHUNK; ++u) {
+                if (k0 + u >= e) break;
+                if (cc[u] != i && fabs(v[u]) < st.y) continue;
+                ocol[p] = cc[u];
+                oval[p] = cc[u] == i ? st.x : v[u];
+                ++p;
+            }
         }
     }
 }
