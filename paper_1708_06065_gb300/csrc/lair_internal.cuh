@@ -87,6 +87,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctl, int *status, long lo
 }
 
 // -------------------------------------------------------------------------------------
+// programmatic dependent launch (the V-cycle's kernels): the kernel first lets the next kernel of the
+// stream begin launching (its blocks may be scheduled once every block of this one has started), then
+// waits until the previous kernel has completed and its writes are visible. Both are no-ops when the
+// launch does not carry the programmatic-serialization attribute (launch_pdl below).
+// -------------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// -------------------------------------------------------------------------------------
 // warp helpers
 // -------------------------------------------------------------------------------------
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -139,6 +150,22 @@ __device__ __forceinline__ void warp_bitonic(int (&key)[R], double (&val)[R], in
 // host-side launch helpers (defined in lair_api.cu)
 // -------------------------------------------------------------------------------------
 void count_launch(int k = 1);
+// a kernel that starts with pdl_enter(), launched so that it may overlap the tail of the previous kernel in
+// the stream (a programmatic edge when the stream is captured into a graph)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 // streaming multiprocessors of the current device (read once per device; 152 on a GB300)
 int device_sms();
 inline int grid_for(long long work, int block, int max_blocks = 0) {

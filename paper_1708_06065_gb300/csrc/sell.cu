@@ -228,6 +228,7 @@ __global__ void k_sell_fill_multi(const SellDesc *__restrict__ d, int p0, int p1
 // independent sums in flight; each row is still summed alone in column order.
 template <class T, int RPT>
 __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restrict__ x, T *__restrict__ y) {
+    pdl_enter();
     const int *__restrict__ sptr = v.slice_ptr;
     const int *__restrict__ scol = v.col;
     const T *__restrict__ sval = static_cast<const T *>(v.val);
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restri
 template <class T, int RPT>
 __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__restrict__ copy, int ncopy,
                                                     const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xo) {
+    pdl_enter();
     const int *__restrict__ sptr = v.slice_ptr;
     const int *__restrict__ scol = v.col;
     const T *__restrict__ sval = static_cast<const T *>(v.val);
@@ -322,6 +324,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                    const T *__restrict__ val, const T *__restrict__ xc,
                                                    T *__restrict__ x) {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int b = __ldcs(rp + i), e = __ldcs(rp + i + 1);
         x[i] = e > b ? fma(__ldcs(val + b), __ldg(xc + __ldcs(col + b)), T(0)) : T(0);
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict_
 template <class T>
 void p1_interp(int n, const int *rp, const int *col, const T *val, const T *xc, T *x, cudaStream_t s) {
     if (n <= 0) return;
-    k_p1_interp<T><<<grid_for(n, 256, device_sms() * 16), 256, 0, s>>>(n, rp, col, val, xc, x);
+    launch_pdl(k_p1_interp<T>, grid_for(n, 256, device_sms() * 16), 256, 0, s, n, rp, col, val, xc, x);
     count_launch();
 }
 template void p1_interp<float>(int, const int *, const int *, const float *, const float *, float *, cudaStream_t);
@@ -410,8 +413,8 @@ void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s) {
     const int tb = v.tb > 0 ? v.tb : 256;
     const int cap = v.grid > 0 ? v.grid : device_sms() * 16;
     const long long nsl = (v.nrows + 31) / 32;
-    if (v.rpt == 2) k_sell_spmv<T, 2><<<grid_for((nsl + 1) / 2 * 32, tb, cap), tb, 0, s>>>(v, x, y);
-    else k_sell_spmv<T, 1><<<grid_for(nsl * 32, tb, cap), tb, 0, s>>>(v, x, y);
+    if (v.rpt == 2) launch_pdl(k_sell_spmv<T, 2>, grid_for((nsl + 1) / 2 * 32, tb, cap), tb, 0, s, v, x, y);
+    else launch_pdl(k_sell_spmv<T, 1>, grid_for(nsl * 32, tb, cap), tb, 0, s, v, x, y);
     count_launch();
 }
 
@@ -422,9 +425,9 @@ void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const
     const int cap = v.grid > 0 ? v.grid : device_sms() * 16;
     const long long nsl = (v.nrows + 31) / 32;
     if (v.rpt == 2)
-        k_sell_sweep<T, 2><<<grid_for((nsl + 1) / 2 * 32 + ncopy, tb, cap), tb, 0, s>>>(v, copy, ncopy, b, x, xo);
+        launch_pdl(k_sell_sweep<T, 2>, grid_for((nsl + 1) / 2 * 32 + ncopy, tb, cap), tb, 0, s, v, copy, ncopy, b, x, xo);
     else
-        k_sell_sweep<T, 1><<<grid_for(nsl * 32 + ncopy, tb, cap), tb, 0, s>>>(v, copy, ncopy, b, x, xo);
+        launch_pdl(k_sell_sweep<T, 1>, grid_for(nsl * 32 + ncopy, tb, cap), tb, 0, s, v, copy, ncopy, b, x, xo);
     count_launch();
 }
 

@@ -122,6 +122,7 @@ template void sweep<float>(const DCsr &, const int8_t *, int, const float *, con
 // coarsest level: y = Ainv b (dense, FP64), with the input/output in T
 template <class T>
 __global__ void k_dense_apply(int n, const double *__restrict__ Ainv, const T *__restrict__ b, T *__restrict__ y) {
+    pdl_enter();
     int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     int nw = (gridDim.x * blockDim.x) >> 5;
@@ -135,7 +136,7 @@ __global__ void k_dense_apply(int n, const double *__restrict__ Ainv, const T *_
 
 template <class T>
 void dense_apply(int n, const double *Ainv, const T *b, T *y, cudaStream_t s) {
-    k_dense_apply<T><<<grid_for((long long)n * 32, 256), 256, 0, s>>>(n, Ainv, b, y);
+    launch_pdl(k_dense_apply<T>, grid_for((long long)n * 32, 256), 256, 0, s, n, Ainv, b, y);
     count_launch();
 }
 template void dense_apply<double>(int, const double *, const double *, double *, cudaStream_t);
