@@ -1046,7 +1046,8 @@ static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan>
         plans.push_back(SellPlan{&L.AF, Ar, L.frows, n - nc, dv, fp32});
         plans.push_back(SellPlan{&L.AC, Ar, L.crows, nc, dv, fp32});
         plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
-        plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
+        // one-point P is applied from its column array (p1col), without a view
+        if (h->o.interp != LAIR_P_ONEPOINT) plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
     }
     if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
 }
@@ -1151,13 +1152,12 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     sell_spmv<T>(L.Rv, B::b(L), B::b(C), h->s);
     if (tm) tend(h, t, true);
     record_cycle<T>(h, H, l + 1);
-    t = tm ? tbegin(h, "L0_interp", bytes_spmv(L.P, sv), true) : -1;
-    if (h->o.interp == LAIR_P_ONEPOINT) {
-        // at most one entry per row of P (one-point, or the identity blocks of the nodal one-point P): the direct
-        // kernel on P's CSR, rows in their own order
-        const T *pv = std::is_same<T, float>::value ? reinterpret_cast<const T *>(L.P.val32)
-                                                    : reinterpret_cast<const T *>(L.P.val);
-        p1_interp<T>(L.P.nr, L.P.rp, L.P.col, pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
+    const bool p1 = h->o.interp == LAIR_P_ONEPOINT && L.p1col;
+    t = tm ? tbegin(h, "L0_interp", p1 ? bytes_p1(L.P, sv) : bytes_spmv(L.P, sv), true) : -1;
+    if (p1) {
+        // at most one entry per row of P, every entry 1 (one-point, or the identity blocks of the nodal one-point
+        // P): the direct kernel on the dense column array, rows in their own order
+        p1_interp<T>(L.P.nr, L.p1col, B::x(C, C.xfinal), B::x(L, 0), h->s);
     } else {
         sell_spmv<T>(L.Pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
     }
@@ -1444,6 +1444,12 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
     }
     {
         int tv = tbegin(h, "setup_views", 0.0);
+        if (o.interp == LAIR_P_ONEPOINT)
+            for (auto &L : H.lev) {
+                if (L.coarsest || !L.P.rp) continue;
+                TRY(dalloc(h, &L.p1col, (size_t)L.P.nr));
+                launch_p1_cols(L.P.nr, L.P.rp, L.P.col, L.p1col, h->s);
+            }
         std::vector<SellPlan> plans;
         for (int l = 0; l < (int)H.lev.size(); ++l) add_view_plans(h, H, l, plans);
         TRY(build_sells(h, H, plans));

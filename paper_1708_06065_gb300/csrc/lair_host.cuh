@@ -52,6 +52,7 @@ struct Level {
     int *frows = nullptr, *crows = nullptr;
     SellView AF, AC, Rv, Pv;
     SellView A64;             // level 0: all rows of A in FP64 for the outer iteration
+    int *p1col = nullptr;     // one-point P (every entry 1): the coarse column of each row's entry, -1 without one
     // nodal hierarchy (k x k blocks): block Jacobi as point Jacobi on Ahat = D^{-1} A (diagonal blocks
     // inverted, diagonal exactly 1) with right-hand side D^{-1} b; binv holds the k x k inverses
     DCsr Ahat;
@@ -416,6 +417,10 @@ static inline lair_status new_counts(lair_handle *h, Temps &t, int **p, int n) {
 
 static inline double bytes_spmv(const DCsr &M, double sv) {
     return (double)M.nnz * (sv + 4.0) + (double)M.nr * (4.0 + sv) + (double)M.nc * sv;
+}
+// x = P x_c with one-point P from its column array: a column per row, a gathered x_c per entry, x written
+static inline double bytes_p1(const DCsr &P, double sv) {
+    return (double)P.nr * (4.0 + sv) + (double)P.nnz * sv;
 }
 
 // true for device (or managed) memory

@@ -389,11 +389,10 @@ lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b, doubl
             sell_spmv<double>(L0.A64, zj, w, h->s);
             tend(h, ts);
             CU(cudaMemsetAsync(hsum, 0, sizeof(double) * (size_t)nseg * HS, h->s));
-            for (int pass = 0; pass < 2; ++pass) {
-                seg_multidot(sta, j + 1, V, n, w, HS, hbuf, hsum, h->s);
-                seg_sub_combo(sta, j + 1, V, n, HS, hbuf, w, h->s);
-            }
-            seg_norm2(sta, w, nrm, h->s);
+            // CGS2 in three streaming passes over V: dots; update and dots; update and norm
+            seg_cgs_pass(sta, 1, j + 1, V, n, HS, nullptr, w, hbuf, hsum, h->s);
+            seg_cgs_pass(sta, 2, j + 1, V, n, HS, hbuf, w, hbuf, hsum, h->s);
+            seg_cgs_pass(sta, 3, j + 1, V, n, HS, hbuf, w, nrm, nullptr, h->s);
             seg_scale(sta, w, nrm, w, h->s);
             CU(cudaMemsetAsync(ring_slot(h, step), 0, sizeof(int), h->s));
             bat_fg_givens(c, j, hsum, nrm, ring_slot(h, step), h->s);

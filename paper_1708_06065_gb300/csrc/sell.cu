@@ -317,28 +317,40 @@ __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__res
     }
 }
 
-// x = P x_c for a P with at most one entry per row (one-point interpolation, or the identity blocks of the
-// nodal hierarchy), straight from P's CSR in row order: one gather per row, coalesced reads of P and writes
-// of x. Row i gets fma(p_i, x_c[j_i], 0), or 0 without an entry: the bits of the sliced-ELL product.
+// One-point interpolation (one-point P, or the identity blocks of the nodal hierarchy: at most one entry per
+// row, every entry 1): x_i = x_c[col_i] + 0, or 0 for a row without an entry -- the bits of fma(1, x_c[col_i], 0)
+// that the sliced-ELL product gives (a -0 becomes +0). One column per row from the dense column array, one
+// gather, one write: coalesced everywhere but the gather.
 template <class T>
-__global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                   const T *__restrict__ val, const T *__restrict__ xc,
+__global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict__ p1col, const T *__restrict__ xc,
                                                    T *__restrict__ x) {
     pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int b = __ldcs(rp + i), e = __ldcs(rp + i + 1);
-        x[i] = e > b ? fma(__ldcs(val + b), __ldg(xc + __ldcs(col + b)), T(0)) : T(0);
+        const int c = __ldcs(p1col + i);
+        x[i] = c >= 0 ? __ldg(xc + c) + T(0) : T(0);
     }
 }
 
 template <class T>
-void p1_interp(int n, const int *rp, const int *col, const T *val, const T *xc, T *x, cudaStream_t s) {
+void p1_interp(int n, const int *p1col, const T *xc, T *x, cudaStream_t s) {
     if (n <= 0) return;
-    launch_pdl(k_p1_interp<T>, grid_for(n, 256, device_sms() * 16), 256, 0, s, n, rp, col, val, xc, x);
+    launch_pdl(k_p1_interp<T>, grid_for(n, 256, device_sms() * 16), 256, 0, s, n, p1col, xc, x);
     count_launch();
 }
-template void p1_interp<float>(int, const int *, const int *, const float *, const float *, float *, cudaStream_t);
-template void p1_interp<double>(int, const int *, const int *, const double *, const double *, double *, cudaStream_t);
+template void p1_interp<float>(int, const int *, const float *, float *, cudaStream_t);
+template void p1_interp<double>(int, const int *, const double *, double *, cudaStream_t);
+
+// the dense column array of a P with at most one entry per row
+__global__ void k_p1_cols(int n, const int *__restrict__ rp, const int *__restrict__ col, int *__restrict__ p1col) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p1col[i] = rp[i + 1] > rp[i] ? col[rp[i]] : -1;
+}
+
+void launch_p1_cols(int n, const int *rp, const int *col, int *p1col, cudaStream_t s) {
+    if (n <= 0) return;
+    k_p1_cols<<<grid_for(n, 256), 256, 0, s>>>(n, rp, col, p1col);
+    count_launch();
+}
 
 // r = b - A x over all rows of an FP64 view of A (optional FP32 copy of r), and the block partial
 // of |r|^2 in part[blockIdx.x] (gridDim.x = RED_PARTS blocks, summed by finish_partials)

@@ -218,9 +218,10 @@ void launch_sell_fill_multi(const SellDesc *d, int p0, int p1, int lin_beg, int 
 template <class T> void sell_spmv(const SellView &v, const T *x, T *y, cudaStream_t s);
 template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);
-// x = P x_c for a P with at most one entry per row, from P's CSR (values in the cycle's precision)
-template <class T>
-void p1_interp(int n, const int *rp, const int *col, const T *val, const T *xc, T *x, cudaStream_t s);
+// x = P x_c for a P with at most one entry per row, every entry 1 (one-point interpolation), from its dense
+// column array (-1: no entry), which launch_p1_cols builds from P's CSR
+template <class T> void p1_interp(int n, const int *p1col, const T *xc, T *x, cudaStream_t s);
+void launch_p1_cols(int n, const int *rp, const int *col, int *p1col, cudaStream_t s);
 // batched systems: per-system residual r = b - A x (rows seg[q]..seg[q+1]), its squared norm, optional FP32 copy
 // Row tiles of a batch of systems: tile t is system tile[t].x, rows [tile[t].y, tile[t].z);
 // the tiles of system q are first[q] .. first[q + 1] - 1; part holds SEG_TILE_PARTS doubles per tile.
@@ -233,16 +234,17 @@ struct SegTiles {
     const uint8_t *active = nullptr;   // if set, tiles of systems with active[q] == 0 are skipped
 };
 constexpr int SEG_TILE = 4096;
-constexpr int SEG_TILE_PARTS = 8;
+constexpr int SEG_TILE_PARTS = 32;   // partial sums per tile: the dots of a CGS2 pass (restart <= 31)
 void seg_residual(const DCsr &A, const SegTiles &st, const double *b, const double *x, double *r, float *r32,
                   double *norm2, cudaStream_t s);
 void seg_norm2(const SegTiles &st, const double *v, double *norm2, cudaStream_t s);
 template <class T>
 void seg_axpy(const SegTiles &st, const uint8_t *active, const T *e, double *x, cudaStream_t s);
-void seg_multidot(const SegTiles &st, int m, const double *X, long long ldx, const double *w, int hs, double *out,
-                  double *acc, cudaStream_t s);
-void seg_sub_combo(const SegTiles &st, int m, const double *X, long long ldx, int hs, const double *h, double *w,
-                   cudaStream_t s);
+// one pass of the batched CGS2 step (see k_tile_cgs) over the m <= 31 columns of X, then the per-system sums:
+// passes 1 and 2 write the m dots of every running system to out[q * hs + k] and add them to acc[q * hs + k],
+// pass 3 writes the squared norm of the new w to out[q]
+void seg_cgs_pass(const SegTiles &st, int pass, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+                  double *out, double *acc, cudaStream_t s);
 void seg_add_combo(const SegTiles &st, const int *cnt, const double *Z, long long ldz, int hs, const double *y, double *x,
                    cudaStream_t s);
 void seg_scale(const SegTiles &st, const double *v, const double *nrm2, double *out, cudaStream_t s);

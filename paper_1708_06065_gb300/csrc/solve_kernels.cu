@@ -428,7 +428,6 @@ void grad_A(const DCsr &A, const double *lam, const double *x, double *g, cudaSt
 // many SMs. Reductions write one partial per tile; seg_reduce then sums the partials of each
 // system in tile order (one warp per system), so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------------------
-constexpr int SEG_MD = SEG_TILE_PARTS;   // columns per multidot launch
 constexpr int SEG_GRID = 152 * 8;
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -476,34 +475,57 @@ __global__ void __launch_bounds__(256) k_tile_norm2(SegTiles st, const double *_
     }
 }
 
-// part[t * SEG_MD + k] = sum over the tile's rows of X_{k0+k}[i] w[i], k < m (m <= SEG_MD)
-__global__ void __launch_bounds__(256) k_tile_multidot(SegTiles st, int k0, int m, const double *__restrict__ X,
-                                                       long long ldx, const double *__restrict__ w) {
-    __shared__ double red[8][SEG_MD];
-    const double *Xk = X + (long long)k0 * ldx;
+// One pass of the batched CGS2 step over the tiles of the running systems (m <= 31 and m <= MM <= SEG_TILE_PARTS
+// columns of X, h per system at h[q * hs]), each thread loading X_k[i] once for both of its uses:
+//   PASS 1: part[t][k] = X_k . w over the tile
+//   PASS 2: w <- w - sum_k h_k X_k, then part[t][k] = X_k . w (the new w)
+//   PASS 3: w <- w - sum_k h_k X_k, then part[t][0] = w . w
+// The update accumulates fma(-h_k, X_k[i], .) in ascending k and every partial is a warp sum followed by the
+// sum over the warps in order, as in k_tile_norm2.
+template <int MM, int PASS>
+__global__ void __launch_bounds__(256) k_tile_cgs(SegTiles st, int m, const double *__restrict__ X, long long ldx,
+                                                  int hs, const double *__restrict__ h, double *__restrict__ w) {
+    __shared__ double red[8][MM];
+    __shared__ double hsh[MM];
     for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
         const int4 tl = st.tile[t];
         if (st.active && !st.active[tl.x]) continue;
-        double acc[SEG_MD];
+        if (PASS > 1 && (int)threadIdx.x < MM) hsh[threadIdx.x] = (int)threadIdx.x < m ? h[(size_t)tl.x * hs + threadIdx.x] : 0.0;
+        __syncthreads();
+        double acc[PASS < 3 ? MM : 1];
 #pragma unroll
-        for (int k = 0; k < SEG_MD; ++k) acc[k] = 0.0;
+        for (int k = 0; k < (PASS < 3 ? MM : 1); ++k) acc[k] = 0.0;
         for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
-            const double wi = w[i];
+            double x[MM];
 #pragma unroll
-            for (int k = 0; k < SEG_MD; ++k)
-                if (k < m) acc[k] = fma(Xk[k * ldx + i], wi, acc[k]);
+            for (int k = 0; k < MM; ++k) x[k] = k < m ? X[k * ldx + i] : 0.0;
+            double v = w[i];
+            if (PASS > 1) {
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (k < m) v = fma(-hsh[k], x[k], v);
+                w[i] = v;
+            }
+            if (PASS < 3) {
+#pragma unroll
+                for (int k = 0; k < (PASS < 3 ? MM : 1); ++k)
+                    if (k < m) acc[k] = fma(x[k], v, acc[k]);
+            } else {
+                acc[0] = fma(v, v, acc[0]);
+            }
         }
+        const int nout = PASS < 3 ? m : 1;
 #pragma unroll
-        for (int k = 0; k < SEG_MD; ++k)
-            if (k < m) {
+        for (int k = 0; k < (PASS < 3 ? MM : 1); ++k)
+            if (k < nout) {
                 const double v = warp_sum(acc[k]);
                 if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
             }
         __syncthreads();
-        if ((int)threadIdx.x < m) {
+        if ((int)threadIdx.x < nout) {
             double s2 = 0.0;
             for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s2 += red[ww][threadIdx.x];
-            st.part[(size_t)t * SEG_MD + threadIdx.x] = s2;
+            st.part[(size_t)t * SEG_TILE_PARTS + threadIdx.x] = s2;
         }
         __syncthreads();
     }
@@ -525,21 +547,6 @@ __global__ void __launch_bounds__(256) k_seg_reduce(SegTiles st, int pw, int m, 
                 out[(size_t)q * hs + k0 + k] = v;
                 if (acc_out) acc_out[(size_t)q * hs + k0 + k] += v;
             }
-        }
-    }
-}
-
-// w_i -= sum_{k < m} h[q * hs + k] X_k[i] for the rows of system q
-__global__ void __launch_bounds__(256) k_tile_sub_combo(SegTiles st, int m, const double *__restrict__ X, long long ldx,
-                                                        int hs, const double *__restrict__ h, double *__restrict__ w) {
-    for (int t = blockIdx.x; t < st.ntiles; t += gridDim.x) {
-        const int4 tl = st.tile[t];
-        if (st.active && !st.active[tl.x]) continue;
-        const double *hq = h + (size_t)tl.x * hs;
-        for (int i = tl.y + threadIdx.x; i < tl.z; i += blockDim.x) {
-            double v = w[i];
-            for (int k = 0; k < m; ++k) v = fma(-hq[k], X[k * ldx + i], v);
-            w[i] = v;
         }
     }
 }
@@ -716,20 +723,24 @@ static void seg_reduce(const SegTiles &st, int pw, int m, int hs, int k0, double
     count_launch();
 }
 
-void seg_multidot(const SegTiles &st, int m, const double *X, long long ldx, const double *w, int hs, double *out,
-                  double *acc, cudaStream_t s) {
-    for (int k0 = 0; k0 < m; k0 += SEG_MD) {
-        const int mm = m - k0 < SEG_MD ? m - k0 : SEG_MD;
-        k_tile_multidot<<<seg_grid(st), 256, 0, s>>>(st, k0, mm, X, ldx, w);
-        count_launch();
-        seg_reduce(st, SEG_MD, mm, hs, k0, out, acc, s);
-    }
-}
-void seg_sub_combo(const SegTiles &st, int m, const double *X, long long ldx, int hs, const double *h, double *w,
-                   cudaStream_t s) {
-    k_tile_sub_combo<<<seg_grid(st), 256, 0, s>>>(st, m, X, ldx, hs, h, w);
+template <int MM>
+static void seg_cgs_mm(const SegTiles &st, int pass, int m, const double *X, long long ldx, int hs, const double *h,
+                       double *w, cudaStream_t s) {
+    if (pass == 1) k_tile_cgs<MM, 1><<<seg_grid(st), 256, 0, s>>>(st, m, X, ldx, hs, h, w);
+    else if (pass == 2) k_tile_cgs<MM, 2><<<seg_grid(st), 256, 0, s>>>(st, m, X, ldx, hs, h, w);
+    else k_tile_cgs<MM, 3><<<seg_grid(st), 256, 0, s>>>(st, m, X, ldx, hs, h, w);
     count_launch();
 }
+
+void seg_cgs_pass(const SegTiles &st, int pass, int m, const double *X, long long ldx, int hs, const double *h, double *w,
+                  double *out, double *acc, cudaStream_t s) {
+    if (m <= 8) seg_cgs_mm<8>(st, pass, m, X, ldx, hs, h, w, s);
+    else if (m <= 16) seg_cgs_mm<16>(st, pass, m, X, ldx, hs, h, w, s);
+    else seg_cgs_mm<32>(st, pass, m, X, ldx, hs, h, w, s);
+    if (pass < 3) seg_reduce(st, SEG_TILE_PARTS, m, hs, 0, out, acc, s);
+    else seg_reduce(st, SEG_TILE_PARTS, 1, 1, 0, out, nullptr, s);
+}
+
 void seg_add_combo(const SegTiles &st, const int *cnt, const double *Z, long long ldz, int hs, const double *y, double *x,
                    cudaStream_t s) {
     k_tile_add_combo<<<seg_grid(st), 256, 0, s>>>(st, cnt, Z, ldz, hs, y, x);
