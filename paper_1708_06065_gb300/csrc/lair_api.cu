@@ -920,6 +920,7 @@ struct SellPlan {
     int nrows;
     const double *dinv;   // NULL: no diagonal
     bool fp32;
+    const int *seg = nullptr;   // batched systems: first row of every system in the view rows' numbering
 };
 
 static lair_status build_sells(lair_handle *h, Hier &H, std::vector<SellPlan> &plans) {
@@ -950,6 +951,15 @@ static lair_status build_sells(lair_handle *h, Hier &H, std::vector<SellPlan> &p
             d.lin0 = lin;
             d.sl0 = sl;
             d.group = g;
+            if (p.seg && h->sys_run) {
+                int *ss;
+                TRY(dalloc(h, &ss, (size_t)nsl));
+                d.seg = p.seg;
+                d.nseg = h->nseg;
+                d.slice_sys = ss;
+                v.slice_sys = ss;
+                v.run = h->sys_run;
+            }
             hd.push_back(d);
             hp.push_back(&p);
             win += (p.nrows + 255) / 256;
@@ -1043,12 +1053,16 @@ static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan>
         const bool nodal = h->o.nodal > 1;
         const DCsr *Ar = nodal ? &L.Ahat : &L.A;
         const double *dv = nodal ? L.dinv_hat : L.dinv;
-        plans.push_back(SellPlan{&L.AF, Ar, L.frows, n - nc, dv, fp32});
-        plans.push_back(SellPlan{&L.AC, Ar, L.crows, nc, dv, fp32});
-        plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32});
+        const int *sc = l + 1 < (int)H.lev.size() ? H.lev[l + 1].seg_d : nullptr;
+        plans.push_back(SellPlan{&L.AF, Ar, L.frows, n - nc, dv, fp32, L.seg_d});
+        plans.push_back(SellPlan{&L.AC, Ar, L.crows, nc, dv, fp32, L.seg_d});
+        plans.push_back(SellPlan{&L.Rv, &L.R, nullptr, L.R.nr, nullptr, fp32, sc});
         // one-point P is applied from its column array (p1col), without a view
-        if (h->o.interp != LAIR_P_ONEPOINT) plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32});
+        if (h->o.interp != LAIR_P_ONEPOINT)
+            plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32, L.seg_d});
     }
+    // the outer FP64 product runs on every system: the Krylov vectors of stopped systems, which enter the next
+    // cycle's input, stay finite values computed in this solve
     if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
 }
 
@@ -1157,7 +1171,8 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
     if (p1) {
         // at most one entry per row of P, every entry 1 (one-point, or the identity blocks of the nodal one-point
         // P): the direct kernel on the dense column array, rows in their own order
-        p1_interp<T>(L.P.nr, L.p1col, B::x(C, C.xfinal), B::x(L, 0), h->s);
+        p1_interp<T>(L.P.nr, L.p1col, L.blk_sys, L.blk_sys ? h->sys_run : nullptr, B::x(C, C.xfinal), B::x(L, 0),
+                     h->s);
     } else {
         sell_spmv<T>(L.Pv, B::x(C, C.xfinal), B::x(L, 0), h->s);
     }
@@ -1444,11 +1459,19 @@ static lair_status build_hierarchy(lair_handle *h, Hier &H, const DCsr &A0, cons
     }
     {
         int tv = tbegin(h, "setup_views", 0.0);
+        if (h->nseg > 0 && !h->sys_run) {
+            TRY(dalloc(h, &h->sys_run, (size_t)h->nseg));
+            CU(cudaMemsetAsync(h->sys_run, 1, (size_t)h->nseg, h->s));
+        }
         if (o.interp == LAIR_P_ONEPOINT)
             for (auto &L : H.lev) {
                 if (L.coarsest || !L.P.rp) continue;
                 TRY(dalloc(h, &L.p1col, (size_t)L.P.nr));
                 launch_p1_cols(L.P.nr, L.P.rp, L.P.col, L.p1col, h->s);
+                if (L.seg_d && h->sys_run) {
+                    TRY(dalloc(h, &L.blk_sys, (size_t)(L.P.nr + 31) / 32));
+                    launch_blk_sys(L.P.nr, L.seg_d, h->nseg, L.blk_sys, h->s);
+                }
             }
         std::vector<SellPlan> plans;
         for (int l = 0; l < (int)H.lev.size(); ++l) add_view_plans(h, H, l, plans);

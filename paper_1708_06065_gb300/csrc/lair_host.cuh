@@ -53,6 +53,7 @@ struct Level {
     SellView AF, AC, Rv, Pv;
     SellView A64;             // level 0: all rows of A in FP64 for the outer iteration
     int *p1col = nullptr;     // one-point P (every entry 1): the coarse column of each row's entry, -1 without one
+    int *blk_sys = nullptr;   // batched systems: the system of every 32-row block of the level (-1: several)
     // nodal hierarchy (k x k blocks): block Jacobi as point Jacobi on Ahat = D^{-1} A (diagonal blocks
     // inverted, diagonal exactly 1) with right-hand side D^{-1} b; binv holds the k x k inverses
     DCsr Ahat;
@@ -113,6 +114,9 @@ struct lair_handle {
     bool graph_pending = false;
     // batched systems (block-diagonal input)
     int nseg = 0;
+    // batched systems: per-system run flags read by the cycle's kernels (slices and blocks of systems that have
+    // stopped are skipped); all 1 outside the batched outer loops, which steer them
+    uint8_t *sys_run = nullptr;
     std::vector<int> seg0;
     double *h_seg = nullptr;      // pinned, nseg doubles
     uint8_t *h_act = nullptr;     // pinned, nseg bytes

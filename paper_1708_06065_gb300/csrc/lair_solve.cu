@@ -232,7 +232,9 @@ static lair_status ensure_batch_ctl(lair_handle *h, int m) {
         TRY(dalloc(h, &c.rl, (size_t)nseg));
         TRY(dalloc(h, &c.its, (size_t)nseg));
         TRY(dalloc(h, &c.jd, (size_t)nseg));
-        TRY(dalloc(h, &c.run, (size_t)nseg));
+        // the run flags are the ones the cycle's kernels read (set-up allocates them with the views)
+        if (h->sys_run) c.run = h->sys_run;
+        else TRY(dalloc(h, &c.run, (size_t)nseg));
         TRY(dalloc(h, &c.done, (size_t)nseg));
         TRY(dalloc(h, &c.nan, 1));
         TRY(dalloc(h, &h->d_ring, (size_t)lair_handle::RING));
@@ -248,6 +250,23 @@ static lair_status ensure_batch_ctl(lair_handle *h, int m) {
         h->bctl_m = m;
     }
     c.m = m;
+    return LAIR_OK;
+}
+
+// The cycle's kernels skip the rows of stopped systems, whose cycle buffers then keep older values; the
+// coarsest level's dense inverse multiplies those by exact zeros. Every buffer is cleared when a batched solve
+// starts, so those values are always finite ones from this solve.
+static lair_status clear_cycle_buffers(lair_handle *h, Hier &H) {
+    for (Level &L : H.lev) {
+        const size_t n = (size_t)L.A.nr;
+        if (h->o.precision == LAIR_MIXED) {
+            CU(cudaMemsetAsync(L.b32, 0, sizeof(float) * n, h->s));
+            for (float *x : L.x32) CU(cudaMemsetAsync(x, 0, sizeof(float) * n, h->s));
+        } else {
+            CU(cudaMemsetAsync(L.b64, 0, sizeof(double) * n, h->s));
+            for (double *x : L.x64) CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->s));
+        }
+    }
     return LAIR_OK;
 }
 
@@ -271,6 +290,8 @@ static lair_status ring_read(lair_handle *h, long long k, int *out) {
 
 static lair_status batch_finish(lair_handle *h, double tol, int *iters, double *rel) {
     const int nseg = h->nseg;
+    // every system runs again in cycles outside the batched loops
+    CU(cudaMemsetAsync(h->bctl.run, 1, (size_t)nseg, h->s));
     std::vector<int> its(nseg);
     std::vector<double> rl(nseg);
     int nan = 0;
@@ -306,6 +327,7 @@ lair_status solve_batched_dev(lair_handle *h, Hier &H, const double *b, double *
     TRY(ensure_work(h, n, 0));
     TRY(ensure_tiles(h, L0));
     TRY(ensure_batch_ctl(h, 0));
+    TRY(clear_cycle_buffers(h, H));
     if ((size_t)nseg > (size_t)RED_PARTS * 16) return fail(h, LAIR_ERR_UNSUPPORTED, "at most %d systems", RED_PARTS * 16);
     double *nrm = h->part;                                  // RED_PARTS * 33 doubles >= nseg
     BatchCtl c = h->bctl;
@@ -351,6 +373,7 @@ lair_status solve_batched_fgmres(lair_handle *h, Hier &H, const double *b, doubl
     TRY(ensure_work(h, n, m));
     TRY(ensure_tiles(h, L0));
     TRY(ensure_batch_ctl(h, m));
+    TRY(clear_cycle_buffers(h, H));
     if (!h->d_bat) TRY(dalloc(h, &h->d_bat, (size_t)nseg * (3 * HS + 1)));
     double *hsum = h->d_bat, *hbuf = hsum + (size_t)nseg * HS, *ydev = hbuf + (size_t)nseg * HS,
            *nrm = ydev + (size_t)nseg * HS;

@@ -156,6 +156,17 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_sell_sort_multi(const SellD
     }
 }
 
+// batched systems: the system of row i (the last q with seg[q] <= i)
+__device__ __forceinline__ int system_of(const int *__restrict__ seg, int nseg, int i) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // slice lengths in entries (32 x longest row of the slice), one warp per slice; also their
 // 64-bit sum per group (two groups: FP32 and FP64 views), so that an int overflow of the offsets is caught on
 // the host. Each warp adds its own sums once at the end.
@@ -168,12 +179,19 @@ __global__ void k_sell_len_multi(const SellDesc *__restrict__ d, int nd, int nli
         const SellDesc &v = d[p];
         const int sl = q - v.lin0;
         const int r = sl * 32 + lane;
-        int l = 0;
+        int l = 0, sy = -2;
         if (r < v.nrows) {
             const int i = v.row_out[r];
             l = v.rp[i + 1] - v.rp[i];
+            if (v.nseg > 0) sy = system_of(v.seg, v.nseg, i);
         }
         l = __reduce_max_sync(0xffffffffu, l);
+        if (v.nseg > 0) {
+            // the slice's system when all its rows share one (lane 0 always holds a row)
+            const int sy0 = __shfl_sync(0xffffffffu, sy, 0);
+            const bool one = __all_sync(0xffffffffu, sy == -2 || sy == sy0);
+            if (lane == 0) v.slice_sys[sl] = one ? sy0 : -1;
+        }
         if (lane == 0) {
             cnt[v.sl0 + sl] = 32 * l;
             if (v.group == 0) s0 += 32ull * (unsigned long long)l;
@@ -240,10 +258,15 @@ __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restri
         int lmax = 0;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            r[k] = (s0 + k) * 32 + lane;
+            bool on = s0 + k < nsl;
+            if (on && v.run) {
+                const int q = v.slice_sys[s0 + k];
+                on = q < 0 || v.run[q];
+            }
+            r[k] = on ? (s0 + k) * 32 + lane : v.nrows;
             base[k] = 0;
             len[k] = 0;
-            if (s0 + k < nsl) {
+            if (on) {
                 const int a = __ldg(sptr + s0 + k);
                 base[k] = a + lane;
                 len[k] = (__ldg(sptr + s0 + k + 1) - a) >> 5;
@@ -285,10 +308,15 @@ __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__res
             int lmax = 0;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                r[k] = (s0 + k) * 32 + lane;
+                bool on = s0 + k < nsl;
+                if (on && v.run) {
+                    const int q = v.slice_sys[s0 + k];
+                    on = q < 0 || v.run[q];
+                }
+                r[k] = on ? (s0 + k) * 32 + lane : v.nrows;
                 base[k] = 0;
                 len[k] = 0;
-                if (s0 + k < nsl) {
+                if (on) {
                     const int a = __ldg(sptr + s0 + k);
                     base[k] = a + lane;
                     len[k] = (__ldg(sptr + s0 + k + 1) - a) >> 5;
@@ -322,23 +350,43 @@ __global__ void __launch_bounds__(256) k_sell_sweep(SellView v, const int *__res
 // that the sliced-ELL product gives (a -0 becomes +0). One column per row from the dense column array, one
 // gather, one write: coalesced everywhere but the gather.
 template <class T>
-__global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict__ p1col, const T *__restrict__ xc,
-                                                   T *__restrict__ x) {
+__global__ void __launch_bounds__(256) k_p1_interp(int n, const int *__restrict__ p1col, const int *__restrict__ blk_sys,
+                                                   const uint8_t *run, const T *__restrict__ xc, T *__restrict__ x) {
     pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (run) {
+            const int q = blk_sys[i >> 5];
+            if (q >= 0 && !run[q]) continue;
+        }
         const int c = __ldcs(p1col + i);
         x[i] = c >= 0 ? __ldg(xc + c) + T(0) : T(0);
     }
 }
 
 template <class T>
-void p1_interp(int n, const int *p1col, const T *xc, T *x, cudaStream_t s) {
+void p1_interp(int n, const int *p1col, const int *blk_sys, const uint8_t *run, const T *xc, T *x, cudaStream_t s) {
     if (n <= 0) return;
-    launch_pdl(k_p1_interp<T>, grid_for(n, 256, device_sms() * 16), 256, 0, s, n, p1col, xc, x);
+    launch_pdl(k_p1_interp<T>, grid_for(n, 256, device_sms() * 16), 256, 0, s, n, p1col, blk_sys, run, xc, x);
     count_launch();
 }
-template void p1_interp<float>(int, const int *, const float *, float *, cudaStream_t);
-template void p1_interp<double>(int, const int *, const double *, double *, cudaStream_t);
+template void p1_interp<float>(int, const int *, const int *, const uint8_t *, const float *, float *, cudaStream_t);
+template void p1_interp<double>(int, const int *, const int *, const uint8_t *, const double *, double *,
+                                cudaStream_t);
+
+// the system of every 32-row block: that of its first row when its last row has the same one, else -1
+__global__ void k_blk_sys(int n, const int *__restrict__ seg, int nseg, int *__restrict__ blk_sys) {
+    const int nb = (n + 31) >> 5;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int q0 = system_of(seg, nseg, 32 * b), q1 = system_of(seg, nseg, min(32 * b + 31, n - 1));
+        blk_sys[b] = q0 == q1 ? q0 : -1;
+    }
+}
+
+void launch_blk_sys(int n, const int *seg, int nseg, int *blk_sys, cudaStream_t s) {
+    if (n <= 0) return;
+    k_blk_sys<<<grid_for((n + 31) / 32, 256), 256, 0, s>>>(n, seg, nseg, blk_sys);
+    count_launch();
+}
 
 // the dense column array of a P with at most one entry per row
 __global__ void k_p1_cols(int n, const int *__restrict__ rp, const int *__restrict__ col, int *__restrict__ p1col) {

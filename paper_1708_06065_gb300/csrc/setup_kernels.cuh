@@ -15,6 +15,10 @@ struct SellView {
     void *dinv = nullptr;       // Jacobi diagonal per view row (sweep views), same type as val
     int tb = 0, grid = 0;       // launch schedule picked by the autotuner (0: 256 threads, grid capped at 16 blocks per SM)
     int rpt = 1;                // rows per thread (1 or 2: rows of two consecutive slices, same lane)
+    // batched systems: the system of every slice (-1: rows of several systems) and the per-system run flags;
+    // slices of a stopped system are skipped (their outputs keep older values). NULL: every slice runs.
+    const int *slice_sys = nullptr;
+    const uint8_t *run = nullptr;
 };
 
 // ---- setup_graph.cu -------------------------------------------------------------------
@@ -208,6 +212,9 @@ struct SellDesc {
     const double *val, *dinv;
     int *row_out;            // view row -> matrix row (rows sorted by length inside windows)
     int nrows, win0, lin0, sl0, group;
+    const int *seg;          // batched systems: first matrix row of every system (nseg + 1 entries)
+    int nseg;                // (0: not batched)
+    int *slice_sys;          // out: the system of every slice, -1 when its rows belong to several
     const int *slice_ptr;    // filled in before the fill pass
     int *scol;
     void *sval, *sdinv;
@@ -220,7 +227,12 @@ template <class T>
 void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x, T *xo, cudaStream_t s);
 // x = P x_c for a P with at most one entry per row, every entry 1 (one-point interpolation), from its dense
 // column array (-1: no entry), which launch_p1_cols builds from P's CSR
-template <class T> void p1_interp(int n, const int *p1col, const T *xc, T *x, cudaStream_t s);
+// blk_sys / run (batched systems, else NULL): the system of every 32-row block (-1: several) and the run flags;
+// blocks of stopped systems are skipped
+template <class T>
+void p1_interp(int n, const int *p1col, const int *blk_sys, const uint8_t *run, const T *xc, T *x, cudaStream_t s);
+// the system of every 32-row block of a level (seg: first row of every system, nseg + 1 entries)
+void launch_blk_sys(int n, const int *seg, int nseg, int *blk_sys, cudaStream_t s);
 void launch_p1_cols(int n, const int *rp, const int *col, int *p1col, cudaStream_t s);
 // batched systems: per-system residual r = b - A x (rows seg[q]..seg[q+1]), its squared norm, optional FP32 copy
 // Row tiles of a batch of systems: tile t is system tile[t].x, rows [tile[t].y, tile[t].z);
