@@ -528,9 +528,9 @@ def main():
     peak, peak_src = load_peaks()
     # single-kernel timers only (the V-cycle, CGS2 and residual regions span several kernels)
     multi = ("vcycle", "outer_cgs2", "outer_residual")
-    # batched systems: the cycle kernels skip the slices of systems that have stopped, so their whole-batch byte
-    # counts overstate what a launch moves; they are listed but not taken as the roofline
-    skipping = ("L0_restrict", "L0_interp", "L0_sweep_F", "L0_sweep_C") if wl.get("batched") else ()
+    # batched systems: the cycle kernels and the FP64 product skip the slices of systems that have stopped, so
+    # their whole-batch byte counts overstate what a launch moves; they are listed but not taken as the roofline
+    skipping = ("L0_restrict", "L0_interp", "L0_sweep_F", "L0_sweep_C", "outer_spmv") if wl.get("batched") else ()
     kern = [(v[1], k, v) for k, v in timers.items()
             if k not in multi and k not in skipping and not k.startswith("setup_") and v[0] > 0]
     roof = None

@@ -921,6 +921,7 @@ struct SellPlan {
     const double *dinv;   // NULL: no diagonal
     bool fp32;
     const int *seg = nullptr;   // batched systems: first row of every system in the view rows' numbering
+    bool zero_stopped = false;  // write 0 to the rows of stopped systems instead of skipping them
 };
 
 static lair_status build_sells(lair_handle *h, Hier &H, std::vector<SellPlan> &plans) {
@@ -959,6 +960,7 @@ static lair_status build_sells(lair_handle *h, Hier &H, std::vector<SellPlan> &p
                 d.slice_sys = ss;
                 v.slice_sys = ss;
                 v.run = h->sys_run;
+                v.zero_stopped = p.zero_stopped;
             }
             hd.push_back(d);
             hp.push_back(&p);
@@ -1061,9 +1063,9 @@ static void add_view_plans(lair_handle *h, Hier &H, int l, std::vector<SellPlan>
         if (h->o.interp != LAIR_P_ONEPOINT)
             plans.push_back(SellPlan{&L.Pv, &L.P, nullptr, L.P.nr, nullptr, fp32, L.seg_d});
     }
-    // the outer FP64 product runs on every system: the Krylov vectors of stopped systems, which enter the next
-    // cycle's input, stay finite values computed in this solve
-    if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false});
+    // the outer FP64 product writes 0 to the rows of stopped systems: their Krylov vectors, which enter the next
+    // cycle's input, stay finite values of this solve
+    if (l == 0) plans.push_back(SellPlan{&L.A64, &L.A, nullptr, L.A.nr, nullptr, false, L.seg_d, true});
 }
 
 static lair_status finish_level(lair_handle *h, Hier &H, int l) {

@@ -258,12 +258,13 @@ __global__ void __launch_bounds__(256) k_sell_spmv(SellView v, const T *__restri
         int lmax = 0;
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-            bool on = s0 + k < nsl;
+            bool on = s0 + k < nsl, zero = false;
             if (on && v.run) {
                 const int q = v.slice_sys[s0 + k];
                 on = q < 0 || v.run[q];
+                zero = !on && v.zero_stopped;   // no entries: the row's sum stays 0 and is written
             }
-            r[k] = on ? (s0 + k) * 32 + lane : v.nrows;
+            r[k] = on || zero ? (s0 + k) * 32 + lane : v.nrows;
             base[k] = 0;
             len[k] = 0;
             if (on) {

@@ -19,6 +19,7 @@ struct SellView {
     // slices of a stopped system are skipped (their outputs keep older values). NULL: every slice runs.
     const int *slice_sys = nullptr;
     const uint8_t *run = nullptr;
+    bool zero_stopped = false;  // products: write 0 to the rows of a stopped system's slices instead of skipping them
 };
 
 // ---- setup_graph.cu -------------------------------------------------------------------
