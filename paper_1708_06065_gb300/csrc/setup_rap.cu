@@ -1012,7 +1012,7 @@ __global__ void k_dense_inverse(int n, const double *__restrict__ LU, const int 
 
 // small coarsest levels (n <= DENSE_SMEM_N): the LU factorisation entirely in shared memory, one CTA, written
 // out with its row permutation for k_dense_inv_cols
-constexpr int DENSE_SMEM_N = 128;
+constexpr int DENSE_SMEM_N = 160;   // n^2 doubles + n ints: 205 KB of the 227 KB a CTA may have
 
 __global__ void __launch_bounds__(256) k_dense_small(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                       const double *__restrict__ val, double *__restrict__ LU,
@@ -1134,7 +1134,16 @@ void launch_dense_setup(const DCsr &A, double *D, int *perm, double *Ainv, int *
     k_dense_build<<<grid_for((long long)n * n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
     k_dense_scatter<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.col, A.val, D);
     k_dense_lu<<<1, 1024, 0, s>>>(n, D, perm, status);
-    k_dense_inverse<<<grid_for(n, 64), 64, 0, s>>>(n, D, perm, Ainv);
+    // the columns of the inverse over n / 4 CTAs (lanes full, as for small levels); a column per thread in the
+    // fallback when the four columns' vectors do not fit in shared memory
+    const size_t xb = sizeof(double) * (size_t)n * DINV_COLS;
+    if (xb <= (size_t)200 * 1024 &&
+        cudaFuncSetAttribute(k_dense_inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xb) == cudaSuccess) {
+        k_dense_inv_cols<<<(n + DINV_COLS - 1) / DINV_COLS, 32, xb, s>>>(n, D, perm, Ainv);
+    } else {
+        cudaGetLastError();
+        k_dense_inverse<<<grid_for(n, 64), 64, 0, s>>>(n, D, perm, Ainv);
+    }
     count_launch(4);
 }
 
