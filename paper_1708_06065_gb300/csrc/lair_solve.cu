@@ -76,10 +76,9 @@ static lair_status solve_dev(lair_handle *h, Hier &H, const double *b, double *x
     lair_status st = LAIR_ERR_NOT_CONVERGED;
     if (cycle == LAIR_CYCLE_STATIONARY) {
         for (;;) {
-            // r = b - A x written straight into the cycle's input buffer
-            double *r = mixed ? h->wr : L0.b64;
-            int tr = tbegin(h, "outer_residual", (double)A.nnz * 12.0 + (double)n * (4.0 + 24.0 + (mixed ? 4.0 : 0.0)));
-            sell_residual(L0.A64, b, x, r, mixed ? L0.b32 : nullptr, h->part, h->s);
+            // r = b - A x written straight into the cycle's input buffer (mixed: its FP32 copy only)
+            int tr = tbegin(h, "outer_residual", (double)A.nnz * 12.0 + (double)n * (4.0 + 16.0 + (mixed ? 4.0 : 8.0)));
+            sell_residual(L0.A64, b, x, mixed ? nullptr : L0.b64, mixed ? L0.b32 : nullptr, h->part, h->s);
             tend(h, tr);
             finish_partials(1, h->part, h->dsc, h->s);
             CU(cudaMemcpyAsync(h->h_dbl, h->dsc, sizeof(double), cudaMemcpyDeviceToHost, h->s));

@@ -401,7 +401,7 @@ void launch_p1_cols(int n, const int *rp, const int *col, int *p1col, cudaStream
     count_launch();
 }
 
-// r = b - A x over all rows of an FP64 view of A (optional FP32 copy of r), and the block partial
+// r = b - A x over all rows of an FP64 view of A (r and its FP32 copy each optional), and the block partial
 // of |r|^2 in part[blockIdx.x] (gridDim.x = RED_PARTS blocks, summed by finish_partials)
 constexpr int RES_THREADS = 512;
 
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_sell_residual(SellView v, const
         for (int j = 0; j < len; ++j) acc = fma(__ldcs(sval + base + 32 * j), __ldg(x + __ldcs(scol + base + 32 * j)), acc);
         const int i = v.row[q];
         const double ri = b[i] - acc;
-        r[i] = ri;
+        if (r) r[i] = ri;
         if (r32) r32[i] = (float)ri;
         ss = fma(ri, ri, ss);
     }
