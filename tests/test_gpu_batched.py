@@ -107,3 +107,37 @@ def test_batched_vcycle_matches_oracle(lair, count):
     zo = H.precond(v)
     assert np.isfinite(z).all()
     assert entrywise_rel(z, zo) <= 1e-5
+
+
+@pytest.mark.parametrize("cycle", [0, 1])
+def test_stopped_systems_leave_no_trace(lair, cycle):
+    """The cycle skips the rows of systems that have stopped. A system with b = 0 stops before its first cycle,
+    so its rows never run in that solve; the other systems still reach their tolerance against their own
+    direct solves, the zero system keeps x = 0, and a later solve on the same hierarchy gives the bits of a
+    fresh hierarchy's solve (no run flag or cycle buffer carries over)."""
+    import torch
+    systems, A, offs = batch(8, 20, 48)
+    opts = dict(cf_mode=1, interp=1, lump_tol=0.05, precision=1)
+    b = A.b.copy()
+    b[offs[2]:offs[3]] = 0.0
+    G = lair.Hierarchy.batched(torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
+                               torch.from_numpy(A.val).cuda(), offs, **opts)
+    x, its, rel, st = G.solve_batched(torch.from_numpy(b).cuda(), tol=1e-8, cycle=cycle, max_iter=2000)
+    assert st == 0 and its[2] == 0 and (rel <= 1e-8).all()
+    x = x.cpu().numpy()
+    assert not x[offs[2]:offs[3]].any()
+    for q, s in enumerate(systems):
+        if q == 2:
+            continue
+        xr = spla.spsolve(s.to_scipy().tocsc(), b[offs[q]:offs[q + 1]])
+        assert np.linalg.norm(x[offs[q]:offs[q + 1]] - xr) <= 1e-6 * np.linalg.norm(xr)
+    # a second solve on the same hierarchy: the bits of a fresh hierarchy's first solve
+    x2, its2, _, st2 = G.solve_batched(torch.from_numpy(A.b).cuda(), tol=1e-8, cycle=cycle, max_iter=2000)
+    F = lair.Hierarchy.batched(torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
+                               torch.from_numpy(A.val).cuda(), offs, **opts)
+    xf, itsf, _, stf = F.solve_batched(torch.from_numpy(A.b).cuda(), tol=1e-8, cycle=cycle, max_iter=2000)
+    assert st2 == 0 and stf == 0 and np.array_equal(its2, itsf)
+    assert torch.equal(x2, xf)
+    # and outside the batched loops every system runs again: one preconditioner application of the whole batch
+    v = torch.from_numpy(np.random.default_rng(5).uniform(-1, 1, A.n)).cuda()
+    assert torch.equal(G.precond(v), F.precond(v))
