@@ -103,6 +103,11 @@ def _load():
 lib = _load()
 
 
+def _on_device(a):
+    """True for a CUDA tensor; numpy arrays and CPU tensors (pinned or not) are host memory."""
+    return not isinstance(a, np.ndarray) and bool(getattr(a, "is_cuda", False))
+
+
 def _ptr(a):
     """Data pointer of a numpy array (host) or a torch tensor (host or device)."""
     if a is None:
@@ -161,7 +166,7 @@ class Hierarchy:
         self._h = C.c_void_p()
         n = len(row_ptr) - 1
         nnz = len(col)
-        on_dev = not isinstance(row_ptr, np.ndarray)
+        on_dev = _on_device(row_ptr)
         self._keep = [row_ptr, col, val]
         A = lair_csr(n, nnz, _ptr(row_ptr), _ptr(col), _ptr(val), int(on_dev))
         o = options(**kw)
@@ -185,7 +190,7 @@ class Hierarchy:
         self = cls.__new__(cls)
         self._h = C.c_void_p()
         self.n, self.nnz = len(row_ptr) - 1, len(col)
-        on_dev = not isinstance(row_ptr, np.ndarray)
+        on_dev = _on_device(row_ptr)
         A = lair_csr(self.n, self.nnz, _ptr(row_ptr), _ptr(col), _ptr(val), int(on_dev))
         offs = np.ascontiguousarray(sys_offsets, np.int64)
         self.nsys = len(offs) - 1
