@@ -192,7 +192,7 @@ lair_status lair_refresh(lair_handle *h, const double *val);
 lair_status lair_solve(lair_handle *h, const double *b, double *x, double tol, int cycle,
                        int max_iter, lair_report *rep);
 
-/* Batched independent systems (spec pattern 2). A is the block-diagonal matrix of
+/* Batched independent systems. A is the block-diagonal matrix of
  * nsys systems; sys_offsets (host, nsys + 1 entries, from 0 to n) gives each system's first
  * row. One hierarchy is built for the whole batch, so every set-up and cycle step is one
  * launch over all systems of all sizes; nothing couples the systems (the C/F splitting

@@ -123,7 +123,7 @@ static lair_status transpose(lair_handle *h, Temps &t, int nr, int nc, int nnz, 
 }
 
 // ---------------------------------------------------------------------------------------
-// launch-schedule autotuner of the local solves (spec pattern 2): for a batch of at least
+// launch-schedule autotuner of the local solves: for a batch of at least
 // LOCAL_TUNE_MIN systems whose shape (precision, shared sets, Neumann series, count, mean and largest
 // size) has not been seen in this process, every candidate schedule bins and solves the batch, timed
 // best of three with CUDA events; the fastest replaces the default when it is more than 5 % faster.

@@ -1,7 +1,7 @@
 // lair_solve.cu -- the outer FP64 iterations around the V-cycle: preconditioner application,
 // stationary refinement and right-preconditioned FGMRES(m) with CGS2 for one system, and the
 // batched systems' per-system refinement and FGMRES steered on the device (Sec. 4: V-cycles as
-// the preconditioner of GMRES; the mixed precision of spec pattern 1).
+// the preconditioner of GMRES; the cycle in FP32 inside the FP64 outer iteration in mixed precision).
 #include "lair_host.cuh"
 
 namespace lair {

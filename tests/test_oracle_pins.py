@@ -761,7 +761,7 @@ def test_batched_fgmres_minimal_residual_per_system():
 
 
 # --------------------------------------------------------------------------------------
-# the FP32 cycle of mixed precision (spec pattern 1), restated in numpy float32
+# the FP32 cycle of mixed precision (FP32 cycle inside the FP64 outer loop), restated in numpy float32
 # --------------------------------------------------------------------------------------
 
 def _f32_two_level_cycle(A, cf, R, P, K, b, seq):
