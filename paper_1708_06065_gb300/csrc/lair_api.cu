@@ -1163,6 +1163,22 @@ static void record_cycle(lair_handle *h, Hier &H, int l) {
         L.xfinal = 0;
         return;
     }
+    if (l == H.bottom_first) {
+        const int nl = (int)H.lev.size();
+        Level &Z = H.lev[nl - 1];
+        BottomCoarse<T> cz;
+        cz.n = Z.A.nr;
+        cz.Ainv = Z.Ainv;
+        cz.b = B::b(Z);
+        cz.x = B::x(Z, 0);
+        const int *seq = relax_seq[h->o.relax];
+        cycle_bottom<T>(static_cast<const BottomLevel<T> *>(H.bottom_desc), nl - 1 - l, cz, seq, h->s);
+        int nsw = 0;
+        while (nsw < 3 && seq[nsw] >= 0) ++nsw;
+        for (int k = l; k < nl - 1; ++k) H.lev[k].xfinal = nsw & 1;
+        Z.xfinal = 0;
+        return;
+    }
     Level &C = H.lev[l + 1];
     int t = tm ? tbegin(h, "L0_restrict", bytes_spmv(L.R, sv), true) : -1;
     sell_spmv<T>(L.Rv, B::b(L), B::b(C), h->s);
@@ -1318,7 +1334,50 @@ static lair_status autotune_views(lair_handle *h, Hier &H) {
     return st;
 }
 
+// The smallest levels (at most BOTTOM_ROWS rows, below the finest, at least one besides the coarsest) run in the
+// one-CTA bottom kernel: their descriptors in the cycle's precision, uploaded once; the views and buffers they
+// point to live as long as the hierarchy (a refresh refills them in place).
+template <class T>
+static lair_status prepare_bottom(lair_handle *h, Hier &H) {
+    using B = CycleBufs<T>;
+    H.bottom_first = -1;
+    const int nl = (int)H.lev.size();
+    // (a coarsest level of more than 512 unknowns keeps its many-CTA dense product)
+    if (h->o.nodal > 1 || nl < 3 || H.lev[nl - 1].A.nr > 512) return LAIR_OK;
+    int first = -1;
+    for (int l = 1; l <= nl - 2 && first < 0; ++l)
+        if (H.lev[l].A.nr <= BOTTOM_ROWS) first = l;
+    if (first < 0) return LAIR_OK;
+    std::vector<BottomLevel<T>> d(nl - 1 - first);
+    for (int i = 0; i < (int)d.size(); ++i) {
+        Level &L = H.lev[first + i];
+        BottomLevel<T> &t = d[i];
+        t.n = L.A.nr;
+        t.nc = L.nc;
+        t.R = L.Rv;
+        t.P = L.Pv;
+        t.AF = L.AF;
+        t.AC = L.AC;
+        t.p1col = h->o.interp == LAIR_P_ONEPOINT ? L.p1col : nullptr;
+        t.crows = L.crows;
+        t.frows = L.frows;
+        t.b = B::b(L);
+        t.x[0] = B::x(L, 0);
+        t.x[1] = B::x(L, 1);
+    }
+    const size_t bytes = sizeof(BottomLevel<T>) * d.size();
+    char *desc = nullptr;
+    TRY(dalloc(h, &desc, bytes));
+    CU(cudaMemcpyAsync(desc, d.data(), bytes, cudaMemcpyHostToDevice, h->s));
+    CU(cudaStreamSynchronize(h->s));
+    H.bottom_desc = desc;
+    H.bottom_first = first;
+    return LAIR_OK;
+}
+
 static lair_status capture_cycle(lair_handle *h, Hier &H) {
+    if (h->o.precision == LAIR_MIXED) TRY(prepare_bottom<float>(h, H));
+    else TRY(prepare_bottom<double>(h, H));
     long long dummy = 0;
     long long *saved = g_launches;
     g_launches = &dummy;

@@ -71,6 +71,10 @@ struct Hier {
     double setup_ms = 0.0;
     // the sliced-ELL fill descriptors of all views (device), kept so that a refresh refills the views in place
     SellDesc *sell_desc = nullptr;
+    // the bottom of the cycle in one CTA: levels bottom_first .. coarsest (-1: a kernel per phase everywhere);
+    // bottom_desc holds their BottomLevel descriptors in the cycle's precision
+    int bottom_first = -1;
+    void *bottom_desc = nullptr;
     int sell_gp[3] = {0, 0, 0}, sell_glin[3] = {0, 0, 0};
 };
 

@@ -374,6 +374,109 @@ template void p1_interp<float>(int, const int *, const int *, const uint8_t *, c
 template void p1_interp<double>(int, const int *, const int *, const uint8_t *, const double *, double *,
                                 cudaStream_t);
 
+// ---------------------------------------------------------------------------------------
+// The bottom of the V-cycle in one CTA: the restrictions of the smallest levels, the coarsest solve, and on the
+// way up their interpolations and F/C sweeps, with a block barrier between phases instead of a kernel boundary.
+// Every row is computed by one thread with the arithmetic of k_sell_spmv, k_sell_sweep, k_p1_interp and
+// k_dense_apply (same entries, same order), so the cycle's result is the same bits either way. Vectors written
+// in one phase and read in a later one are read with plain loads (the block's own writes, ordered by
+// __syncthreads); matrices do not change during the launch. Stopped batched systems are not skipped here.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+template <class T>
+__device__ __forceinline__ void bottom_spmv(const SellView &v, const T *x, T *y) {
+    const T *__restrict__ sval = static_cast<const T *>(v.val);
+    const long long nthr = (long long)((v.nrows + 31) >> 5) * 32;
+    for (long long u = threadIdx.x; u < nthr; u += blockDim.x) {
+        const int lane = (int)(u & 31), sl = (int)(u >> 5), r = sl * 32 + lane;
+        const int a = __ldg(v.slice_ptr + sl);
+        const int base = a + lane, len = (__ldg(v.slice_ptr + sl + 1) - a) >> 5;
+        T acc = T(0);
+        for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), x[__ldg(v.col + base + 32 * j)], acc);
+        if (r < v.nrows) y[__ldg(v.row + r)] = acc;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void bottom_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const T *x,
+                                             T *xo) {
+    const T *__restrict__ sval = static_cast<const T *>(v.val);
+    const T *__restrict__ sd = static_cast<const T *>(v.dinv);
+    const long long nthr = (long long)((v.nrows + 31) >> 5) * 32;
+    for (long long u = threadIdx.x; u < nthr + ncopy; u += blockDim.x) {
+        if (u < nthr) {
+            const int lane = (int)(u & 31), sl = (int)(u >> 5), r = sl * 32 + lane;
+            const int a = __ldg(v.slice_ptr + sl);
+            const int base = a + lane, len = (__ldg(v.slice_ptr + sl + 1) - a) >> 5;
+            T acc = T(0);
+            for (int j = 0; j < len; ++j) acc = fma(__ldg(sval + base + 32 * j), x[__ldg(v.col + base + 32 * j)], acc);
+            if (r < v.nrows) {
+                const int i = __ldg(v.row + r);
+                xo[i] = fma(__ldg(sd + r), b[i] - acc, x[i]);
+            }
+        } else {
+            const int j = __ldg(copy + (u - nthr));
+            xo[j] = x[j];
+        }
+    }
+}
+
+}  // namespace
+
+template <class T>
+__global__ void __launch_bounds__(BOTTOM_THREADS) k_cycle_bottom(const BottomLevel<T> *__restrict__ lv, int nl,
+                                                                 BottomCoarse<T> cz, int4 seq) {
+    pdl_enter();
+    const int sq[3] = {seq.x, seq.y, seq.z};
+    for (int l = 0; l < nl; ++l) {
+        bottom_spmv<T>(lv[l].R, lv[l].b, l + 1 < nl ? lv[l + 1].b : cz.b);
+        __syncthreads();
+    }
+    {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = threadIdx.x >> 5; r < cz.n; r += nw) {
+            double acc = 0.0;
+            for (int c = lane; c < cz.n; c += 32) acc = fma(__ldg(cz.Ainv + (size_t)r * cz.n + c), (double)cz.b[c], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) cz.x[r] = (T)acc;
+        }
+    }
+    for (int l = nl - 1; l >= 0; --l) {
+        const BottomLevel<T> &L = lv[l];
+        __syncthreads();
+        const T *xc = l + 1 < nl ? lv[l + 1].x[seq.w] : cz.x;
+        if (L.p1col) {
+            for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+                const int c = __ldg(L.p1col + i);
+                L.x[0][i] = c >= 0 ? xc[c] + T(0) : T(0);
+            }
+        } else {
+            bottom_spmv<T>(L.P, xc, L.x[0]);
+        }
+        int cur = 0;
+        for (int k = 0; k < 3 && sq[k] >= 0; ++k) {
+            __syncthreads();
+            if (sq[k] == CF_F) bottom_sweep<T>(L.AF, L.crows, L.nc, L.b, L.x[cur], L.x[1 - cur]);
+            else bottom_sweep<T>(L.AC, L.frows, L.n - L.nc, L.b, L.x[cur], L.x[1 - cur]);
+            cur ^= 1;
+        }
+    }
+}
+
+template <class T>
+void cycle_bottom(const BottomLevel<T> *lv, int nl, const BottomCoarse<T> &cz, const int *seq3, cudaStream_t s) {
+    int nsw = 0;
+    while (nsw < 3 && seq3[nsw] >= 0) ++nsw;
+    const int4 seq = make_int4(seq3[0], seq3[1], seq3[2], nsw & 1);
+    launch_pdl(k_cycle_bottom<T>, 1, BOTTOM_THREADS, 0, s, lv, nl, cz, seq);
+    count_launch();
+}
+template void cycle_bottom<float>(const BottomLevel<float> *, int, const BottomCoarse<float> &, const int *,
+                                  cudaStream_t);
+template void cycle_bottom<double>(const BottomLevel<double> *, int, const BottomCoarse<double> &, const int *,
+                                   cudaStream_t);
+
 // the system of every 32-row block: that of its first row when its last row has the same one, else -1
 __global__ void k_blk_sys(int n, const int *__restrict__ seg, int nseg, int *__restrict__ blk_sys) {
     const int nb = (n + 31) >> 5;

@@ -232,6 +232,26 @@ void sell_sweep(const SellView &v, const int *copy, int ncopy, const T *b, const
 // blocks of stopped systems are skipped
 template <class T>
 void p1_interp(int n, const int *p1col, const int *blk_sys, const uint8_t *run, const T *xc, T *x, cudaStream_t s);
+// the bottom of the V-cycle in one CTA (sell.cu): levels of at most BOTTOM_ROWS rows. A level: R restricts b to the
+// next level, P interpolates (sliced ELL, or the one-point column array p1col when set), AF / AC sweep the F / C
+// rows while crows / frows (nc / n - nc of them) are copied; the coarsest: x = Ainv b
+template <class T> struct BottomLevel {
+    int n = 0, nc = 0;
+    SellView R, P, AF, AC;
+    const int *p1col = nullptr;
+    const int *crows = nullptr, *frows = nullptr;
+    T *b = nullptr, *x[2] = {nullptr, nullptr};
+};
+template <class T> struct BottomCoarse {
+    int n = 0;
+    const double *Ainv = nullptr;
+    T *b = nullptr, *x = nullptr;
+};
+constexpr int BOTTOM_THREADS = 1024;
+constexpr int BOTTOM_ROWS = 1024;
+// lv: nl level descriptors in device memory; seq3: the sweep targets (CF_F / CF_C, -1 ends)
+template <class T>
+void cycle_bottom(const BottomLevel<T> *lv, int nl, const BottomCoarse<T> &cz, const int *seq3, cudaStream_t s);
 // the system of every 32-row block of a level (seg: first row of every system, nseg + 1 entries)
 void launch_blk_sys(int n, const int *seg, int nseg, int *blk_sys, cudaStream_t s);
 void launch_p1_cols(int n, const int *rp, const int *col, int *p1col, cudaStream_t s);
